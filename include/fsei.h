@@ -1,0 +1,185 @@
+/*
+ * fsei.h -- C ABI of libfsei.so: one time step of the second-order,
+ * staggered-grid, fractional-step Navier-Stokes integrator of the FSEI
+ * cardiac solver (arXiv 2103.15187), as hand-written CUDA for sm_103a.
+ *
+ * Method (Sec. 2.1, Eq. 2-3; Sec. 3.1):
+ *   * incompressible Navier-Stokes, non-dimensional, Newtonian stress
+ *     tau = 2 Re^-1 E (Sec. 2.1), body force f given per step (the immersed
+ *     boundary forcing "applied at the fractional step", Sec. 3.2);
+ *   * central second-order differences on a staggered mesh (Sec. 2.1);
+ *   * Adams-Bashforth for advection, Crank-Nicolson for viscosity,
+ *     gamma = 3/2, rho = -1/2 (Eq. 3); first step of a run: gamma = 1,
+ *     rho = 0 (no H^{n-1} yet);
+ *   * fractional step: predictor with the old pressure, pressure-increment
+ *     Poisson equation, projection, p^{n+1} = p^n + phi - beta L phi with
+ *     beta = dt / (2 Re);
+ *   * the implicit viscous operator approximately factorised into one
+ *     tridiagonal system per direction, periodic x and y handled as cyclic
+ *     systems (Sec. 3.1);
+ *   * periodic x, y; z either periodic (uniform) or bounded by no-slip walls
+ *     at z = -1, +1 with a tanh-stretched mesh (Sec. 4, Sec. 5).
+ *
+ * Field layout (all fields): contiguous row-major [nz][ny][nx], x fastest,
+ * element type double (FSEI_FP64) or float (FSEI_MIXED).  Staggering:
+ *   u at (x_i, y_{j+1/2}, zc_k), v at (x_{i+1/2}, y_j, zc_k),
+ *   w at (x_{i+1/2}, y_{j+1/2}, z_k), p at (x_{i+1/2}, y_{j+1/2}, zc_k),
+ * x_i = i lx/nx, y_j = j ly/ny, z_k the z faces, zc_k = (z_k + z_{k+1})/2.
+ * With walls w[k=0] is the bottom wall face and must hold 0; the top wall
+ * face is not stored.
+ *
+ * Ownership: the caller owns every field buffer (device memory, 16-byte
+ * aligned).  The library owns its workspace, plans and z metrics, allocated
+ * in fsei_grid_create and freed by fsei_grid_destroy.
+ *
+ * Errors: no entry point throws or aborts.  Argument, shape and alignment
+ * errors are reported at call time; asynchronous conditions found on the
+ * device (non-finite values, CFL number above 1) are reported through
+ * fsei_step_stats.flags and the status of a call that synchronises (one that
+ * asks for stats).  fsei_last_error() gives a message for the last non-OK
+ * status of the calling thread.
+ *
+ * Concurrency: a grid handle is not re-entrant; calls are ordered on the
+ * CUDA stream passed in (NULL = legacy default stream).
+ */
+#ifndef FSEI_H
+#define FSEI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FSEI_OK = 0,
+    FSEI_E_ARG = 1,         /* NULL handle/pointer, bad parameter value      */
+    FSEI_E_SHAPE = 2,       /* unsupported extent (see fsei_grid_create)     */
+    FSEI_E_UNSUPPORTED = 3, /* valid request this build does not implement   */
+    FSEI_E_NOMEM = 4,       /* device allocation failed                      */
+    FSEI_E_CUDA = 5,        /* a CUDA runtime call failed                    */
+    FSEI_E_NONFINITE = 6,   /* a NaN/Inf appeared in the new state           */
+    FSEI_E_CFL = 7,         /* CFL number of the new state above 1           */
+    FSEI_E_TIMEOUT = 8      /* a bounded device wait gave up                 */
+} fsei_status;
+
+typedef enum {
+    FSEI_FP64 = 0,  /* every stored value and every operation in double      */
+    FSEI_MIXED = 1  /* float fields, stencils, FFTs and sweeps; double for the
+                       zero and near-zero wavenumber Poisson systems and for
+                       all global reductions (dt, CFL, divergence, energy)  */
+} fsei_precision;
+
+typedef enum { FSEI_Z_PERIODIC = 0, FSEI_Z_WALLS = 1 } fsei_zbc;
+
+/* Step-statistics flags (bit set in fsei_step_stats.flags). */
+#define FSEI_FLAG_NONFINITE 1
+#define FSEI_FLAG_CFL 2
+
+typedef struct {
+    int32_t nx, ny, nz;     /* cells; nx, ny even, of the form 2^a 3^b,
+                               nx/2 >= 4, ny >= 4, 8 <= nz <= 2048; nx/2
+                               and ny at most 1024 */
+    double lx, ly;          /* periodic box lengths in x and y */
+    int32_t zbc;            /* fsei_zbc */
+    double lz;              /* periodic z: box length (uniform mesh);
+                               walls: ignored, z spans [-1, 1] */
+    double stretch;         /* walls: tanh clustering factor s,
+                               z_k = tanh(s (2k/nz - 1)) / tanh(s);
+                               0 = uniform */
+    const double *zfaces;   /* optional host array of nz+1 increasing z
+                               faces (walls only); overrides stretch */
+    int32_t prec;           /* fsei_precision */
+    double near_zero_tau;   /* FSEI_MIXED: a Poisson mode (kx, ky) is solved
+                               in double when (lambda_x + lambda_y) Lz^2 <
+                               tau, lambda the modified wavenumbers
+                               (2 - 2 cos(2 pi k / n)) / h^2, Lz the z
+                               extent; <= 0 selects 64 */
+} fsei_grid_desc;
+
+typedef struct fsei_grid_s *fsei_grid;
+
+/* Device pointers to caller-owned fields (element type per precision).
+ * hu, hv, hw hold the advection term H^{n-1} of the previous step on input
+ * and H^n on output (Eq. 3's Adams-Bashforth history).  have_prev_h = 0
+ * makes the first step of the call use gamma = 1, rho = 0; the library sets
+ * it to 1 on return. */
+typedef struct {
+    void *u, *v, *w, *p, *hu, *hv, *hw;
+    int32_t have_prev_h;
+} fsei_state;
+
+typedef struct {
+    double re;          /* Reynolds number (> 0) */
+    double dt;          /* time step when cfl <= 0 */
+    double cfl;         /* > 0: dt = cfl / max_cells(|u_c|/dx + |v_c|/dy +
+                           |w_c|/dz_k) recomputed on the device from u^n
+                           every step (u_c, v_c, w_c: two-face averages at
+                           the cell centre) */
+    double gamma, rho;  /* Adams-Bashforth weights, normally 1.5, -0.5 */
+    double fconst[3];   /* uniform body force added to f (e.g. a channel's
+                           pressure-gradient drive 2/Re in x) */
+} fsei_step_params;
+
+typedef struct {
+    double dt_used;        /* dt of the last step */
+    double cfl;            /* dt_used * max_cells(...) of the new state */
+    double max_div;        /* max over cells of |D u^{n+1}| */
+    double kinetic_energy; /* 1/2 sum u^2 dV over all staggered points */
+    int32_t flags;         /* FSEI_FLAG_* */
+} fsei_step_stats;
+
+/* Create a grid handle: z metrics, plans and workspace on the current CUDA
+ * device.  Returns FSEI_E_SHAPE for unsupported extents, FSEI_E_ARG for bad
+ * lengths or faces, FSEI_E_NOMEM if the workspace does not fit. */
+fsei_status fsei_grid_create(const fsei_grid_desc *desc, fsei_grid *out);
+
+/* Release a handle (NULL is a no-op).  Synchronises the device first. */
+void fsei_grid_destroy(fsei_grid grid);
+
+/* Bytes of device workspace the handle owns. */
+int64_t fsei_grid_workspace_bytes(fsei_grid grid);
+
+/* Advance the state by nsteps fractional steps (Eq. 3 with the
+ * approximate factorisation of Sec. 3.1).  fx, fy, fz: body force at the u,
+ * v and w points, constant over the call, or NULL for zero.  out: if not
+ * NULL, the call synchronises the stream and fills the statistics of the
+ * last step; its status then reports device flags (FSEI_E_NONFINITE first,
+ * then FSEI_E_CFL).  Without out the call is asynchronous. */
+fsei_status fsei_step(fsei_grid grid, fsei_state *state, const void *fx,
+                      const void *fy, const void *fz,
+                      const fsei_step_params *params, int32_t nsteps,
+                      void *cuda_stream, fsei_step_stats *out);
+
+/* Pressure-increment Poisson solve of the fractional step: phi with
+ * D G phi = rhs at the cell centres (D G: the compound staggered Laplacian,
+ * Neumann at walls), phi of zero volume-weighted mean.  rhs must have zero
+ * volume-weighted mean (sum rhs dz_k = 0) -- the solve pins phi at k = 0 of
+ * the (0, 0) Fourier mode and leaves that row to compatibility.  rhs and
+ * phi: device fields of the grid's element type; they may alias. */
+fsei_status fsei_poisson_solve(fsei_grid grid, const void *rhs, void *phi,
+                               void *cuda_stream);
+
+/* Per-kernel timing, for measurement tools.  While enabled, fsei_step and
+ * fsei_poisson_solve record a CUDA event pair on the call's stream around
+ * every kernel they launch.  fsei_kernel_times synchronises the device,
+ * writes for each kernel kind k < cap the summed device time in ms and the
+ * number of launches since the last call, resets the sums, and returns the
+ * number of kinds.  fsei_kernel_name(k) names kind k (NULL if out of range).
+ * Timing does not change what the kernels compute. */
+fsei_status fsei_set_kernel_timing(fsei_grid grid, int32_t enable);
+int32_t fsei_kernel_times(fsei_grid grid, double *total_ms, int64_t *launches,
+                          int32_t cap);
+const char *fsei_kernel_name(int32_t kind);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char *fsei_last_error(void);
+
+/* Library version string. */
+const char *fsei_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSEI_H */

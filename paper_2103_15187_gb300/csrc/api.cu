@@ -1,0 +1,534 @@
+// Host side of libfsei.so: the C ABI of include/fsei.h.  Builds the mesh
+// metrics, FFT twiddle tables, Fourier-mode tables and workspace of a grid,
+// and sequences the kernels of a fractional step (Sec. 2.1, Eq. 3; Sec. 3.1).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fsei.h"
+#include "kernels.cuh"
+
+using namespace fsei;
+
+namespace {
+
+thread_local std::string g_err;
+
+fsei_status fail(fsei_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+bool is_2a3b(int n) {
+    if (n < 1) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+FftPlanDev make_fft_plan(int n) {
+    FftPlanDev p;
+    memset(&p, 0, sizeof p);
+    p.n = n;
+    int m = n;
+    while (m % 4 == 0) { p.rad[p.nr++] = 4; m /= 4; }
+    while (m % 2 == 0) { p.rad[p.nr++] = 2; m /= 2; }
+    while (m % 3 == 0) { p.rad[p.nr++] = 3; m /= 3; }
+    return p;
+}
+
+// exp(-2 pi i m / n) in extended precision, rounded to double
+void twiddles(int n, int count, std::vector<double> &re, std::vector<double> &im) {
+    re.resize(count);
+    im.resize(count);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int m = 0; m < count; ++m) {
+        const long double ang = 2.0L * pi * (long double)m / (long double)n;
+        re[m] = (double)cosl(ang);
+        im[m] = (double)(-sinl(ang));
+    }
+}
+
+struct DevAllocs {
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+    cudaError_t err = cudaSuccess;
+    template <typename X> X *get(size_t count) {
+        void *p = nullptr;
+        const size_t b = (count ? count : 1) * sizeof(X);
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            err = e;
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        bytes += b;
+        return static_cast<X *>(p);
+    }
+    void release() {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+enum KernelKind {
+    KK_SPEED, KK_BEGIN, KK_RHS_X, KK_SWEEP_Y, KK_SWEEP_Z, KK_RFFT_X, KK_FFT_Y, KK_POISSON_Z,
+    KK_IFFT_Y, KK_IRFFT_X, KK_PROJECT, KK_COUNT
+};
+const char *const kKernelNames[KK_COUNT] = {
+    "speed (CFL reduction)", "step_begin (scalars + sweep plans)", "rhs_x (RHS + x sweep)",
+    "sweep_y", "sweep_z (+ u*)", "rfft_x (div + x R2C)", "fft_y (forward)",
+    "poisson_z (+ exact modes)", "fft_y (inverse)", "irfft_x (x C2R)",
+    "project (+ p update, stats)"};
+
+// Event pairs recorded around kernel launches while timing is enabled.
+struct KernelTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<int> kinds;   // kind of pending pair i (events 2i, 2i+1)
+    double ms[KK_COUNT] = {0};
+    long long n[KK_COUNT] = {0};
+    cudaEvent_t ev(size_t i) {
+        while (pool.size() <= i) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[i];
+    }
+    template <class F> void run(int kind, cudaStream_t st, F &&f) {
+        if (!on) { f(); return; }
+        const size_t i = kinds.size();
+        cudaEventRecord(ev(2 * i), st);
+        f();
+        cudaEventRecord(ev(2 * i + 1), st);
+        kinds.push_back(kind);
+    }
+    void collect() {
+        cudaDeviceSynchronize();
+        for (size_t i = 0; i < kinds.size(); ++i) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]);
+            ms[kinds[i]] += t;
+            n[kinds[i]] += 1;
+        }
+        kinds.clear();
+    }
+    ~KernelTimer() {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
+
+template <typename X> cudaError_t upload(X *dst, const std::vector<X> &src) {
+    return cudaMemcpy(dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+struct fsei_grid_s {
+    fsei_grid_desc desc;
+    int device = 0;
+    int prec = 0;
+    GridDev g;
+    DevAllocs mem;
+    Work<float> wf;
+    Work<double> wd;
+    StepScalars *sc = nullptr;      // device
+    StepScalars *sc_host = nullptr; // pinned
+    KernelTimer timer;
+};
+
+namespace {
+
+template <typename T>
+fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &lamx,
+                       const std::vector<double> &lamy, const std::vector<int> &nzm) {
+    GridDev &g = G->g;
+    DevAllocs &M = G->mem;
+    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
+    memset(&W, 0, sizeof W);
+    W.q0 = M.get<T>(ncell);
+    W.q1 = M.get<T>(ncell);
+    W.q2 = M.get<T>(ncell);
+    W.phi = M.get<T>(ncell);
+    const size_t nspec = (size_t)g.sk * g.ny * g.nz;
+    W.spec = M.get<cplx<T>>(nspec);
+    if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "workspace allocation failed (%zu bytes so far): %s", M.bytes, cudaGetErrorString(M.err));
+    cudaMemset(W.spec, 0, nspec * sizeof(cplx<T>));
+
+    // launch geometry
+    const int tsz = (int)sizeof(T);
+    W.ry = 1;
+    const int rymax = tsz == 8 ? 4 : 8;
+    for (int r = rymax; r >= 1; r /= 2)
+        if (g.ny % r == 0) { W.ry = r; break; }
+    W.tx = 128 / tsz;
+    while (W.tx > 4 && (size_t)g.nz * W.tx * tsz > 200 * 1024) W.tx /= 2;
+    while (W.tx > 4 && (size_t)g.ny * W.tx * tsz > 200 * 1024) W.tx /= 2;
+    W.tkx = 128 / (2 * tsz);
+    auto poisson_bytes = [&](int tk) { return (size_t)g.nz * tk * (2 * tsz + 2 * tsz); };
+    while (W.tkx > 2 && (poisson_bytes(W.tkx) > 200 * 1024 ||
+                         (size_t)2 * g.ny * W.tkx * 2 * tsz > 200 * 1024))
+        W.tkx /= 2;
+    W.pz_poisson = 256 / W.tkx;
+    if (W.pz_poisson > g.nz / 3) W.pz_poisson = g.nz / 3;
+    if (W.pz_poisson < 1) W.pz_poisson = 1;
+
+    // tridiagonal plans: 0 x, 1 y, 2 z centres, 3 z faces
+    const int nl_x = 3 * W.ry;
+    int Ps[4];
+    int ns[4] = {g.nx, g.ny, g.nz, g.walls ? g.nz - 1 : g.nz};
+    Ps[0] = 256 / nl_x;
+    Ps[1] = Ps[2] = Ps[3] = 256 / W.tx;
+    for (int q = 0; q < 4; ++q) {
+        if (Ps[q] > ns[q] / 3) Ps[q] = ns[q] / 3;
+        if (Ps[q] < 1) Ps[q] = 1;
+        TriPlanStore<T> &s = W.store[q];
+        const int n = ns[q], m = 2 * Ps[q];
+        s.a = M.get<T>(n); s.c = M.get<T>(n); s.inv = M.get<T>(n);
+        s.at = M.get<T>(n); s.ct = M.get<T>(n);
+        s.rlo = M.get<T>(m); s.rinv = M.get<T>(m); s.rcp = M.get<T>(m);
+        s.rz = M.get<T>(m); s.rsc = M.get<T>(2);
+        TriPlan<T> &p = W.plan[q];
+        p.n = n;
+        p.P = Ps[q];
+        p.cyclic = (q < 2) ? 1 : (g.walls ? 0 : 1);
+        p.off = (q == 3 && g.walls) ? 1 : 0;
+        p.a = s.a; p.c = s.c; p.inv = s.inv; p.at = s.at; p.ct = s.ct;
+        p.rlo = s.rlo; p.rinv = s.rinv; p.rcp = s.rcp; p.rz = s.rz; p.rsc = s.rsc;
+    }
+    if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "plan allocation failed");
+
+    // FFT plans and twiddles
+    W.fpx = make_fft_plan(g.mx);
+    W.fpy = make_fft_plan(g.ny);
+    auto up_tw = [&](int n, int count, const cplx<T> **dst) {
+        std::vector<double> re, im;
+        twiddles(n, count, re, im);
+        std::vector<cplx<T>> h(count);
+        for (int m = 0; m < count; ++m) h[m] = cplx<T>{T(re[m]), T(im[m])};
+        cplx<T> *d = M.get<cplx<T>>(count);
+        if (d) upload(d, h);
+        *dst = d;
+    };
+    up_tw(g.mx, g.mx, &W.twx);
+    up_tw(g.ny, g.ny, &W.twy);
+    up_tw(g.nx, g.mx + 1, &W.twpost);
+    // modified wavenumbers
+    {
+        std::vector<T> lx(lamx.size()), ly(lamy.size());
+        for (size_t i = 0; i < lamx.size(); ++i) lx[i] = T(lamx[i]);
+        for (size_t i = 0; i < lamy.size(); ++i) ly[i] = T(lamy[i]);
+        T *dlx = M.get<T>(lx.size());
+        T *dly = M.get<T>(ly.size());
+        double *dlxd = M.get<double>(lamx.size());
+        double *dlyd = M.get<double>(lamy.size());
+        int *dm = M.get<int>(nzm.size());
+        W.nz_scratch = M.get<double>(4 * (size_t)g.nz * (nzm.size() ? nzm.size() : 1));
+        if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "table allocation failed");
+        upload(dlx, lx);
+        upload(dly, ly);
+        upload(dlxd, lamx);
+        upload(dlyd, lamy);
+        upload(dm, nzm);
+        W.lamx = dlx; W.lamy = dly; W.lamx_d = dlxd; W.lamy_d = dlyd;
+        W.nzm = dm;
+        W.n_nzm = (int)nzm.size();
+    }
+    if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "table allocation failed");
+    set_smem_limits_sweep<T>(g, W);
+    set_smem_limits_poisson<T>(g, W);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FSEI_E_CUDA, "grid setup: %s", cudaGetErrorString(e));
+    return FSEI_OK;
+}
+
+template <typename T>
+fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx, const void *fy,
+                      const void *fz, const StepArgs &a, int nsteps, cudaStream_t st) {
+    Fields<T> F;
+    F.u = (T *)s->u; F.v = (T *)s->v; F.w = (T *)s->w; F.p = (T *)s->p;
+    F.hu = (T *)s->hu; F.hv = (T *)s->hv; F.hw = (T *)s->hw;
+    F.fx = (const T *)fx; F.fy = (const T *)fy; F.fz = (const T *)fz;
+    const GridDev &g = G->g;
+    KernelTimer &tm = G->timer;
+    if (a.cfl > 0.0) {
+        cudaMemsetAsync(&G->sc->speed_next, 0, sizeof(unsigned long long), st);
+        tm.run(KK_SPEED, st, [&] { launch_speed<T>(g, F.u, F.v, F.w, G->sc, st); });
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        const int euler = (n == 0 && !s->have_prev_h) ? 1 : 0;
+        tm.run(KK_BEGIN, st, [&] { launch_step_begin<T>(g, W, G->sc, a, euler, st); });
+        tm.run(KK_RHS_X, st, [&] { launch_rhs_x<T>(g, F, W, G->sc, a, st); });
+        tm.run(KK_SWEEP_Y, st, [&] { launch_sweep_y<T>(g, W, st); });
+        tm.run(KK_SWEEP_Z, st, [&] { launch_sweep_z<T>(g, F, W, st); });
+        tm.run(KK_RFFT_X, st, [&] { launch_rfft_x<T>(g, W, G->sc, nullptr, 0, st); });
+        tm.run(KK_FFT_Y, st, [&] { launch_fft_y<T>(g, W, 0, st); });
+        tm.run(KK_POISSON_Z, st, [&] { launch_poisson_z<T>(g, W, st); });
+        tm.run(KK_IFFT_Y, st, [&] { launch_fft_y<T>(g, W, 1, st); });
+        tm.run(KK_IRFFT_X, st, [&] { launch_irfft_x<T>(g, W, W.phi, st); });
+        tm.run(KK_PROJECT, st, [&] { launch_project<T>(g, F, W, G->sc, st); });
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FSEI_E_CUDA, "step launch: %s", cudaGetErrorString(e));
+    return FSEI_OK;
+}
+
+template <typename T>
+fsei_status run_poisson(fsei_grid_s *G, Work<T> &W, const void *rhs, void *phi, cudaStream_t st) {
+    const GridDev &g = G->g;
+    KernelTimer &tm = G->timer;
+    tm.run(KK_RFFT_X, st, [&] { launch_rfft_x<T>(g, W, G->sc, (const T *)rhs, 1, st); });
+    tm.run(KK_FFT_Y, st, [&] { launch_fft_y<T>(g, W, 0, st); });
+    tm.run(KK_POISSON_Z, st, [&] { launch_poisson_z<T>(g, W, st); });
+    tm.run(KK_IFFT_Y, st, [&] { launch_fft_y<T>(g, W, 1, st); });
+    tm.run(KK_IRFFT_X, st, [&] { launch_irfft_x<T>(g, W, (T *)phi, st); });
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FSEI_E_CUDA, "poisson launch: %s", cudaGetErrorString(e));
+    return FSEI_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *fsei_last_error(void) { return g_err.c_str(); }
+
+const char *fsei_version(void) { return "fsei-gb300 0.1 (sm_103a)"; }
+
+fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
+    g_err.clear();
+    if (!d || !out) return fail(FSEI_E_ARG, "fsei_grid_create: NULL argument");
+    *out = nullptr;
+    const int nx = d->nx, ny = d->ny, nz = d->nz;
+    if (nx < 8 || nx % 2 || !is_2a3b(nx / 2) || nx / 2 > 1024)
+        return fail(FSEI_E_SHAPE, "nx = %d: need nx even, nx/2 = 2^a 3^b in [4, 1024]", nx);
+    if (ny < 4 || ny % 2 || !is_2a3b(ny) || ny > 1024)
+        return fail(FSEI_E_SHAPE, "ny = %d: need ny even, 2^a 3^b in [4, 1024]", ny);
+    if (nz < 8 || nz > 2048) return fail(FSEI_E_SHAPE, "nz = %d: need 8 <= nz <= 2048", nz);
+    if (!(d->lx > 0) || !(d->ly > 0)) return fail(FSEI_E_ARG, "lx, ly must be > 0");
+    if (d->zbc != FSEI_Z_PERIODIC && d->zbc != FSEI_Z_WALLS) return fail(FSEI_E_ARG, "bad zbc %d", d->zbc);
+    if (d->prec != FSEI_FP64 && d->prec != FSEI_MIXED) return fail(FSEI_E_ARG, "bad prec %d", d->prec);
+    if (d->zbc == FSEI_Z_PERIODIC && !(d->lz > 0)) return fail(FSEI_E_ARG, "periodic z needs lz > 0");
+    if (d->zbc == FSEI_Z_PERIODIC && d->zfaces) return fail(FSEI_E_ARG, "zfaces are for walls only");
+    if (!(d->stretch >= 0)) return fail(FSEI_E_ARG, "stretch must be >= 0");
+
+    // z faces (walls: tanh clustering on [-1, 1] or given faces)
+    std::vector<double> zf(nz + 1);
+    if (d->zbc == FSEI_Z_PERIODIC) {
+        for (int k = 0; k <= nz; ++k) zf[k] = k * (d->lz / nz);
+    } else if (d->zfaces) {
+        for (int k = 0; k <= nz; ++k) zf[k] = d->zfaces[k];
+        for (int k = 0; k < nz; ++k)
+            if (!(zf[k + 1] > zf[k])) return fail(FSEI_E_ARG, "zfaces must increase strictly");
+    } else if (d->stretch > 0) {
+        const double s = d->stretch;
+        for (int k = 0; k <= nz; ++k) zf[k] = tanh(s * (2.0 * k / nz - 1.0)) / tanh(s);
+    } else {
+        for (int k = 0; k <= nz; ++k) zf[k] = -1.0 + 2.0 * k / nz;
+    }
+    std::vector<double> dz(nz), idz(nz), hc(nz + 1), ihc(nz + 1);
+    for (int k = 0; k < nz; ++k) dz[k] = zf[k + 1] - zf[k];
+    for (int k = 1; k < nz; ++k) hc[k] = 0.5 * (zf[k + 1] + zf[k]) - 0.5 * (zf[k] + zf[k - 1]);
+    if (d->zbc == FSEI_Z_WALLS) {
+        hc[0] = 0.5 * dz[0];
+        hc[nz] = 0.5 * dz[nz - 1];
+    } else {
+        hc[0] = hc[nz] = 0.5 * (dz[nz - 1] + dz[0]);
+    }
+    for (int k = 0; k < nz; ++k) idz[k] = 1.0 / dz[k];
+    for (int k = 0; k <= nz; ++k) ihc[k] = 1.0 / hc[k];
+
+    fsei_grid_s *G = new fsei_grid_s();
+    G->desc = *d;
+    G->desc.zfaces = nullptr;
+    G->prec = d->prec;
+    cudaGetDevice(&G->device);
+    GridDev &g = G->g;
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    g.walls = d->zbc == FSEI_Z_WALLS;
+    g.mx = nx / 2;
+    g.sk = ((g.mx + 1 + 15) / 16) * 16;
+    g.dx = d->lx / nx; g.dy = d->ly / ny;
+    g.idx = 1.0 / g.dx; g.idy = 1.0 / g.dy;
+    g.idx2 = g.idx * g.idx; g.idy2 = g.idy * g.idy;
+    DevAllocs &M = G->mem;
+    double *ddz = M.get<double>(nz), *didz = M.get<double>(nz), *dihc = M.get<double>(nz + 1);
+    float *fdz = M.get<float>(nz), *fidz = M.get<float>(nz), *fihc = M.get<float>(nz + 1);
+    G->sc = M.get<StepScalars>(1);
+    if (M.err != cudaSuccess) {
+        M.release();
+        delete G;
+        return fail(FSEI_E_NOMEM, "metric allocation failed: %s", cudaGetErrorString(M.err));
+    }
+    auto tof = [](const std::vector<double> &v) {
+        std::vector<float> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+        return o;
+    };
+    upload(ddz, dz); upload(didz, idz); upload(dihc, ihc);
+    upload(fdz, tof(dz)); upload(fidz, tof(idz)); upload(fihc, tof(ihc));
+    g.dz = ddz; g.idz = didz; g.ihc = dihc;
+    g.dzf = fdz; g.idzf = fidz; g.ihcf = fihc;
+    cudaMemset(G->sc, 0, sizeof(StepScalars));
+    if (cudaMallocHost((void **)&G->sc_host, sizeof(StepScalars)) != cudaSuccess) {
+        M.release();
+        delete G;
+        return fail(FSEI_E_NOMEM, "pinned host allocation failed");
+    }
+
+    // modified wavenumbers and the modes solved exactly in double
+    std::vector<double> lamx(g.sk), lamy(ny);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int kx = 0; kx < g.sk; ++kx)
+        lamx[kx] = (double)((2.0L - 2.0L * cosl(2.0L * pi * kx / nx)) / ((long double)g.dx * g.dx));
+    for (int ky = 0; ky < ny; ++ky)
+        lamy[ky] = (double)((2.0L - 2.0L * cosl(2.0L * pi * ky / ny)) / ((long double)g.dy * g.dy));
+    std::vector<int> nzm;
+    nzm.push_back(0);
+    if (d->prec == FSEI_MIXED) {
+        const double tau = d->near_zero_tau > 0 ? d->near_zero_tau : 64.0;
+        const double lz = zf[nz] - zf[0];
+        for (int ky = 0; ky < ny; ++ky)
+            for (int kx = 0; kx <= g.mx; ++kx) {
+                if (kx == 0 && ky == 0) continue;
+                if ((lamx[kx] + lamy[ky]) * lz * lz < tau) nzm.push_back(kx + g.sk * ky);
+            }
+    }
+    fsei_status st = d->prec == FSEI_FP64 ? setup_work<double>(G, G->wd, lamx, lamy, nzm)
+                                          : setup_work<float>(G, G->wf, lamx, lamy, nzm);
+    if (st != FSEI_OK) {
+        cudaFreeHost(G->sc_host);
+        M.release();
+        delete G;
+        return st;
+    }
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFreeHost(G->sc_host);
+        M.release();
+        delete G;
+        return fail(FSEI_E_CUDA, "grid setup: %s", cudaGetErrorString(e));
+    }
+    *out = G;
+    return FSEI_OK;
+}
+
+void fsei_grid_destroy(fsei_grid G) {
+    if (!G) return;
+    DeviceGuard dg(G->device);
+    cudaDeviceSynchronize();
+    if (G->sc_host) cudaFreeHost(G->sc_host);
+    G->mem.release();
+    delete G;
+}
+
+int64_t fsei_grid_workspace_bytes(fsei_grid G) { return G ? (int64_t)G->mem.bytes : 0; }
+
+fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy, const void *fz,
+                      const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,
+                      fsei_step_stats *out) {
+    g_err.clear();
+    if (!G || !s || !prm) return fail(FSEI_E_ARG, "fsei_step: NULL argument");
+    if (nsteps < 0) return fail(FSEI_E_ARG, "nsteps < 0");
+    const void *req[7] = {s->u, s->v, s->w, s->p, s->hu, s->hv, s->hw};
+    for (int i = 0; i < 7; ++i) {
+        if (!req[i]) return fail(FSEI_E_ARG, "state field %d is NULL", i);
+        if (!aligned16(req[i])) return fail(FSEI_E_ARG, "state field %d not 16-byte aligned", i);
+    }
+    const void *fo[3] = {fx, fy, fz};
+    for (int i = 0; i < 3; ++i)
+        if (fo[i] && !aligned16(fo[i])) return fail(FSEI_E_ARG, "force %d not 16-byte aligned", i);
+    if (!(prm->re > 0)) return fail(FSEI_E_ARG, "re must be > 0");
+    if (!(prm->cfl > 0) && !(prm->dt > 0)) return fail(FSEI_E_ARG, "need dt > 0 or cfl > 0");
+    StepArgs a;
+    a.re = prm->re; a.dt = prm->dt; a.cfl = prm->cfl; a.gamma = prm->gamma; a.rho = prm->rho;
+    for (int i = 0; i < 3; ++i) a.fconst[i] = prm->fconst[i];
+    DeviceGuard dg(G->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    fsei_status r = FSEI_OK;
+    if (nsteps > 0) {
+        r = G->prec == FSEI_FP64 ? run_steps<double>(G, G->wd, s, fx, fy, fz, a, nsteps, st)
+                                 : run_steps<float>(G, G->wf, s, fx, fy, fz, a, nsteps, st);
+        if (r != FSEI_OK) return r;
+        s->have_prev_h = 1;
+    }
+    if (out) {
+        cudaMemcpyAsync(G->sc_host, G->sc, sizeof(StepScalars), cudaMemcpyDeviceToHost, st);
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(FSEI_E_CUDA, "fsei_step: %s", cudaGetErrorString(e));
+        const StepScalars &h = *G->sc_host;
+        out->dt_used = h.dt;
+        const double spd = __builtin_bit_cast(double, h.speed_next);
+        out->cfl = h.dt * spd;
+        out->max_div = __builtin_bit_cast(double, h.maxdiv);
+        out->kinetic_energy = h.ke;
+        out->flags = h.flags;
+        if (out->cfl > 1.0) out->flags |= FSEI_FLAG_CFL;
+        if (out->flags & FSEI_FLAG_NONFINITE) return fail(FSEI_E_NONFINITE, "non-finite value in the new state");
+        if (out->flags & FSEI_FLAG_CFL) return fail(FSEI_E_CFL, "CFL number %g above 1", out->cfl);
+    }
+    return FSEI_OK;
+}
+
+fsei_status fsei_poisson_solve(fsei_grid G, const void *rhs, void *phi, void *cuda_stream) {
+    g_err.clear();
+    if (!G || !rhs || !phi) return fail(FSEI_E_ARG, "fsei_poisson_solve: NULL argument");
+    if (!aligned16(rhs) || !aligned16(phi)) return fail(FSEI_E_ARG, "rhs/phi not 16-byte aligned");
+    DeviceGuard dg(G->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    return G->prec == FSEI_FP64 ? run_poisson<double>(G, G->wd, rhs, phi, st)
+                                : run_poisson<float>(G, G->wf, rhs, phi, st);
+}
+
+fsei_status fsei_set_kernel_timing(fsei_grid G, int32_t enable) {
+    g_err.clear();
+    if (!G) return fail(FSEI_E_ARG, "fsei_set_kernel_timing: NULL grid");
+    DeviceGuard dg(G->device);
+    if (!enable) G->timer.collect();
+    G->timer.on = enable != 0;
+    return FSEI_OK;
+}
+
+int32_t fsei_kernel_times(fsei_grid G, double *total_ms, int64_t *launches, int32_t cap) {
+    if (!G) return 0;
+    DeviceGuard dg(G->device);
+    G->timer.collect();
+    for (int k = 0; k < KK_COUNT && k < cap; ++k) {
+        if (total_ms) total_ms[k] = G->timer.ms[k];
+        if (launches) launches[k] = G->timer.n[k];
+    }
+    for (int k = 0; k < KK_COUNT; ++k) {
+        G->timer.ms[k] = 0;
+        G->timer.n[k] = 0;
+    }
+    return KK_COUNT;
+}
+
+const char *fsei_kernel_name(int32_t kind) {
+    return (kind >= 0 && kind < KK_COUNT) ? kKernelNames[kind] : nullptr;
+}
+
+}  // extern "C"

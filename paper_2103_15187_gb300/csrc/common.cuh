@@ -1,0 +1,100 @@
+// Internal definitions shared by the kernels and the host library of
+// libfsei.so (fractional-step Navier-Stokes step, arXiv 2103.15187 Sec. 2.1,
+// Sec. 3.1).  Nothing here is part of the public ABI (include/fsei.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FSEI_HD __host__ __device__ __forceinline__
+#define FSEI_D __device__ __forceinline__
+
+namespace fsei {
+
+// ----------------------------------------------------------- complex -------
+template <typename T> struct cplx { T re, im; };
+template <typename T> struct alignas(2 * sizeof(T)) cplxa { T re, im; };
+
+template <typename T> FSEI_HD cplx<T> cmk(T a, T b) { return {a, b}; }
+template <typename T> FSEI_HD cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> FSEI_HD cplx<T> operator-(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> FSEI_HD cplx<T> operator*(cplx<T> a, cplx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T> FSEI_HD cplx<T> operator*(T s, cplx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> FSEI_HD cplx<T> conj(cplx<T> a) { return {a.re, -a.im}; }
+// multiply by -i (sign < 0) or +i (sign > 0)
+template <typename T, int SIGN> FSEI_HD cplx<T> mul_i(cplx<T> a) {
+    return SIGN < 0 ? cplx<T>{a.im, -a.re} : cplx<T>{-a.im, a.re};
+}
+
+// -------------------------------------------------------------- grid -------
+// Mesh description on the device.  z metrics are kept in double and float;
+// kernels pick the copy matching their arithmetic type.
+struct GridDev {
+    int nx, ny, nz;
+    int walls;          // 1: no-slip walls in z, 0: periodic z
+    int mx;             // nx / 2 (length of the half-size complex x FFT)
+    int sk;             // row stride (complex elements) of the spectrum
+    double dx, dy, idx, idy, idx2, idy2;
+    const double *dz, *idz, *ihc;   // dz[nz], 1/dz[nz], 1/hc[nz+1]
+    const float *dzf, *idzf, *ihcf;
+};
+
+template <typename T> struct Metric;
+template <> struct Metric<double> {
+    static FSEI_D const double *idz(const GridDev &g) { return g.idz; }
+    static FSEI_D const double *ihc(const GridDev &g) { return g.ihc; }
+    static FSEI_D const double *dz(const GridDev &g) { return g.dz; }
+};
+template <> struct Metric<float> {
+    static FSEI_D const float *idz(const GridDev &g) { return g.idzf; }
+    static FSEI_D const float *ihc(const GridDev &g) { return g.ihcf; }
+    static FSEI_D const float *dz(const GridDev &g) { return g.dzf; }
+};
+
+// ---------------------------------------------------- per-step scalars -----
+// Device-resident scalars of the running step (written by k_step_begin and
+// the reductions; read by every kernel so that dt computed from the CFL
+// condition never visits the host).
+struct StepScalars {
+    double dt;            // this step's dt
+    double beta;          // dt / (2 Re)
+    double gamma, rho;    // Adams-Bashforth weights of this step
+    unsigned long long speed_cur;   // bits of max(|u_c|/dx+...) of u^n
+    unsigned long long speed_next;  // same, accumulated for u^{n+1}
+    unsigned long long maxdiv;      // bits of max |D u^{n+1}|
+    double ke;            // kinetic energy of u^{n+1}
+    int flags;            // FSEI_FLAG_*
+    int pad;
+};
+
+// --------------------------------------------- partitioned tridiagonal -----
+// A line of n unknowns is cut into P chunks [s_p, e_p], s_p = p n / P.
+// Chunk interiors are eliminated independently (each interior unknown is
+// expressed through the two chunk ends), the 2P chunk ends form a reduced
+// tridiagonal system (cyclic when the line is periodic), solved per line,
+// and the interiors are recovered by one backward pass.  The matrix-only
+// factors are the same for every line of a sweep; they are built once per
+// step on the device (k_step_begin) into a TriPlan.
+template <typename T> struct TriPlan {
+    int n, P, cyclic, off;   // off: first unknown's index in the stored line
+    const T *a, *c;          // sub- and super-diagonal (n)
+    const T *inv;            // interior forward pivots 1/den_i (n)
+    const T *at, *ct;        // interior forward factors a~_i, c~_i (n)
+    const T *rlo, *rinv, *rcp, *rz; // reduced system (2P): couplings and LU
+    const T *rsc;            // [0] = a_0/g (cyclic), [1] = 1/(1+v.z)
+};
+
+// Raw (mutable) storage of one plan inside the workspace.
+template <typename T> struct TriPlanStore {
+    T *a, *c, *inv, *at, *ct, *rlo, *rinv, *rcp, *rz, *rsc;
+};
+
+FSEI_HD int chunk_start(int p, int n, int P) { return (int)(((long long)p * n) / P); }
+
+// bit pattern of a non-negative double, monotone in its value
+FSEI_D unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+FSEI_D double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+}  // namespace fsei

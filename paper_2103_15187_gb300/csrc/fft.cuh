@@ -1,0 +1,103 @@
+// Batched complex FFTs in shared memory for the pressure Poisson solve
+// (Fourier transform in the two periodic directions, Sec. 3.1 / Sec. 4; the
+// paper uses FFTW3 on the CPU, here every transform is hand-written).
+//
+// Self-sorting mixed-radix Stockham transform of length N = 2^a 3^b.  A pass
+// of radix R with p = product of the radices already applied takes, for
+// each butterfly index i < N/R (k = i mod p), the inputs x_r = in[i + r N/R],
+// multiplies x_r by w^(r k N / (p R)) with w = exp(-2 pi i / N) (conjugated
+// for the inverse), applies the length-R DFT, and stores output r at
+// out[(i - k) R + k + r p].  After the last pass the result is in natural
+// order.  Forward transforms are unnormalised sums with exp(-...); inverse
+// ones unnormalised sums with exp(+...).
+#pragma once
+#include "common.cuh"
+
+namespace fsei {
+
+struct FftPlanDev {
+    int n;        // transform length
+    int nr;       // number of passes
+    int rad[16];  // radix of each pass (2, 3 or 4)
+};
+
+template <typename T, int SIGN>
+FSEI_D void dft2(cplx<T> &x0, cplx<T> &x1) {
+    const cplx<T> a = x0 + x1, b = x0 - x1;
+    x0 = a;
+    x1 = b;
+}
+
+template <typename T, int SIGN>
+FSEI_D void dft3(cplx<T> &x0, cplx<T> &x1, cplx<T> &x2) {
+    const T h = T(0.86602540378443864676);   // sqrt(3)/2
+    const cplx<T> t = x1 + x2;
+    const cplx<T> m = x0 - T(0.5) * t;
+    const cplx<T> dd = mul_i<T, SIGN>(h * (x1 - x2));
+    x0 = x0 + t;
+    x1 = m + dd;
+    x2 = m - dd;
+}
+
+template <typename T, int SIGN>
+FSEI_D void dft4(cplx<T> &x0, cplx<T> &x1, cplx<T> &x2, cplx<T> &x3) {
+    const cplx<T> a = x0 + x2, b = x0 - x2, c = x1 + x3;
+    const cplx<T> d = mul_i<T, SIGN>(x1 - x3);
+    x0 = a + c;
+    x2 = a - c;
+    x1 = b + d;
+    x3 = b - d;
+}
+
+// Transform nl lines.  Element i of line l: buf[i * es + l * ls].  Data
+// starts in a; b is scratch of the same size.  Returns the buffer holding
+// the result.  tw: table of w^m, m < N (forward sign).  Must be called by
+// every thread of the block; ends with a barrier.
+template <typename T, int SIGN>
+__device__ cplx<T> *fft_lines(cplx<T> *a, cplx<T> *b, int es, int ls, int nl,
+                              const FftPlanDev &fp, const cplx<T> *__restrict__ tw,
+                              bool line_fastest) {
+    const int N = fp.n;
+    int p = 1;
+    cplx<T> *src = a, *dst = b;
+    for (int s = 0; s < fp.nr; ++s) {
+        const int R = fp.rad[s];
+        const int TN = N / R;
+        const int tstep = N / (p * R);
+        const int total = nl * TN;
+        for (int w = threadIdx.x; w < total; w += blockDim.x) {
+            int l, i;
+            if (line_fastest) { l = w % nl; i = w / nl; }
+            else { i = w % TN; l = w / TN; }
+            const int k = i % p;
+            const int j = (i - k) * R + k;
+            cplx<T> x[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r < R) {
+                    cplx<T> v = src[(i + r * TN) * es + l * ls];
+                    if (r > 0 && k > 0) {
+                        cplx<T> wv = tw[r * k * tstep];
+                        if (SIGN > 0) wv = conj(wv);
+                        v = v * wv;
+                    }
+                    x[r] = v;
+                }
+            }
+            if (R == 4) dft4<T, SIGN>(x[0], x[1], x[2], x[3]);
+            else if (R == 2) dft2<T, SIGN>(x[0], x[1]);
+            else dft3<T, SIGN>(x[0], x[1], x[2]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (r < R) dst[(j + r * p) * es + l * ls] = x[r];
+        }
+        __syncthreads();
+        cplx<T> *tmp = src;
+        src = dst;
+        dst = tmp;
+        p *= R;
+    }
+    return src;
+}
+
+}  // namespace fsei

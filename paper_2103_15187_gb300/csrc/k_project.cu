@@ -1,0 +1,123 @@
+// Projection and pressure update of the fractional step (Sec. 2.1): with the
+// pressure increment phi from the Poisson solve,
+//     u^{n+1} = u* - dt G phi,   p^{n+1} = p^n + phi - beta (D G) phi,
+// beta = dt / (2 Re).  Fused double-precision reductions of the new state:
+// max |D u^{n+1}|, kinetic energy, and max |u_c|/dx + |v_c|/dy + |w_c|/dz_k
+// (the CFL speed that sets the next step's dt).
+#include "kernels.cuh"
+
+namespace fsei {
+
+namespace {
+
+FSEI_D size_t fid(int i, int j, int k, int nx, int ny) {
+    return ((size_t)k * ny + j) * nx + i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_project(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict__ q1,
+          const T *__restrict__ q2, const T *__restrict__ phi, StepScalars *sc) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const size_t ncell = (size_t)nx * ny * nz;
+    const T dt = T(sc->dt), beta = T(sc->beta);
+    const T idx = T(g.idx), idy = T(g.idy), idx2 = T(g.idx2), idy2 = T(g.idy2);
+    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
+    const double vxy = g.dx * g.dy;
+    double mdiv = 0.0, mspd = 0.0, ke = 0.0;
+    int flags = 0;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < ncell;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c % nx);
+        const int j = (int)((c / nx) % ny);
+        const int k = (int)(c / ((size_t)nx * ny));
+        const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+        const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
+        const bool hasdn = !g.walls || k > 0, hasup = !g.walls || k < nz - 1;
+        const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
+        const T f0 = phi[c];
+        const T fim = phi[fid(im, j, k, nx, ny)], fip = phi[fid(ip, j, k, nx, ny)];
+        const T fjm = phi[fid(i, jm, k, nx, ny)], fjp = phi[fid(i, jp, k, nx, ny)];
+        const T fkd = hasdn ? phi[fid(i, j, kd, nx, ny)] : T(0);
+        const T fku = hasup ? phi[fid(i, j, ku, nx, ny)] : T(0);
+        const T ihck = ihc[k], ihcu = ihc[k + 1], idzk = idz[k];
+        const T un = q0[c] - dt * (f0 - fim) * idx;
+        const T vn = q1[c] - dt * (f0 - fjm) * idy;
+        const T wn = hasdn ? q2[c] - dt * (f0 - fkd) * ihck : T(0);
+        const T fup = hasup ? (fku - f0) * ihcu : T(0);
+        const T fdn = hasdn ? (f0 - fkd) * ihck : T(0);
+        const T lphi = (fip - T(2) * f0 + fim) * idx2 + (fjp - T(2) * f0 + fjm) * idy2 +
+                       (fup - fdn) * idzk;
+        const T pn = F.p[c] + f0 - beta * lphi;
+        F.u[c] = un;
+        F.v[c] = vn;
+        F.w[c] = wn;
+        F.p[c] = pn;
+        // neighbours of the new state needed by the cell-centre statistics
+        const T uip = q0[fid(ip, j, k, nx, ny)] - dt * (fip - f0) * idx;
+        const T vjp = q1[fid(i, jp, k, nx, ny)] - dt * (fjp - f0) * idy;
+        const T wku = hasup ? q2[fid(i, j, ku, nx, ny)] - dt * (fku - f0) * ihcu : T(0);
+        const double di = ((double)uip - (double)un) * g.idx + ((double)vjp - (double)vn) * g.idy +
+                          ((double)wku - (double)wn) * g.idz[k];
+        mdiv = fmax(mdiv, fabs(di));
+        const double sp = fabs(0.5 * ((double)un + (double)uip)) * g.idx +
+                          fabs(0.5 * ((double)vn + (double)vjp)) * g.idy +
+                          fabs(0.5 * ((double)wn + (double)wku)) * g.idz[k];
+        mspd = fmax(mspd, sp);
+        const double hck = hasdn ? 1.0 / g.ihc[k] : 0.0;
+        ke += 0.5 * vxy * (((double)un * un + (double)vn * vn) * g.dz[k] + (double)wn * wn * hck);
+        if (!isfinite(un) || !isfinite(vn) || !isfinite(wn) || !isfinite(pn)) flags |= 1;
+    }
+    __shared__ double sdiv[32], sspd[32], ske[32];
+    __shared__ int sfl[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        mdiv = fmax(mdiv, __shfl_down_sync(0xffffffffu, mdiv, o));
+        mspd = fmax(mspd, __shfl_down_sync(0xffffffffu, mspd, o));
+        ke += __shfl_down_sync(0xffffffffu, ke, o);
+        flags |= __shfl_down_sync(0xffffffffu, flags, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sdiv[wid] = mdiv;
+        sspd[wid] = mspd;
+        ske[wid] = ke;
+        sfl[wid] = flags;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        mdiv = lane < nw ? sdiv[lane] : 0.0;
+        mspd = lane < nw ? sspd[lane] : 0.0;
+        ke = lane < nw ? ske[lane] : 0.0;
+        flags = lane < nw ? sfl[lane] : 0;
+        for (int o = 16; o > 0; o >>= 1) {
+            mdiv = fmax(mdiv, __shfl_down_sync(0xffffffffu, mdiv, o));
+            mspd = fmax(mspd, __shfl_down_sync(0xffffffffu, mspd, o));
+            ke += __shfl_down_sync(0xffffffffu, ke, o);
+            flags |= __shfl_down_sync(0xffffffffu, flags, o);
+        }
+        if (lane == 0) {
+            atomicMax(&sc->maxdiv, dbits(mdiv));
+            atomicMax(&sc->speed_next, dbits(mspd));
+            atomicAdd(&sc->ke, ke);
+            if (flags) atomicOr(&sc->flags, flags);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,
+                                          StepScalars *sc, cudaStream_t st) {
+    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
+    int blocks = (int)((ncell + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_project<T><<<blocks, 256, 0, st>>>(g, F, W.q0, W.q1, W.q2, W.phi, sc);
+}
+
+template void launch_project<float>(const GridDev &, const Fields<float> &, Work<float> &,
+                                    StepScalars *, cudaStream_t);
+template void launch_project<double>(const GridDev &, const Fields<double> &, Work<double> &,
+                                     StepScalars *, cudaStream_t);
+
+}  // namespace fsei

@@ -1,0 +1,458 @@
+// Explicit right-hand side and implicit viscous sweeps of one fractional
+// step (Sec. 2.1, Eq. 3; Sec. 3.1 approximate factorisation with one
+// tridiagonal system per direction, cyclic in x and y).
+//
+//   k_speed       max over cells of |u_c|/dx + |v_c|/dy + |w_c|/dz_k (for the
+//                 CFL time step), double reduction
+//   k_scalars     dt, beta = dt/(2 Re), gamma, rho of the step; resets the
+//                 step's reductions
+//   k_plans       matrix-only factors of the four sweep matrices (x, y, z at
+//                 centres, z at faces) for this step's beta
+//   k_rhs_x       H^n = -div(uu)^n, RHS = dt[gamma H^n + rho H^{n-1}
+//                 + Re^-1 L u^n - G p^n + f], stores H^n, solves
+//                 (I - beta L_x) q = RHS along x
+//   k_sweep_y     (I - beta L_y) r = q along y
+//   k_sweep_z     (I - beta L_z) du = r along z; u* = u^n + du
+#include "kernels.cuh"
+#include "tri.cuh"
+
+namespace fsei {
+
+namespace {
+
+FSEI_D size_t fid(int i, int j, int k, int nx, int ny) {
+    return ((size_t)k * ny + j) * nx + i;
+}
+
+template <typename T>
+__device__ double block_max(double v) {
+    __shared__ double wmax[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wmax[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? wmax[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+template <typename T>
+__global__ void k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
+                        const T *__restrict__ w, StepScalars *sc) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const size_t ncell = (size_t)nx * ny * nz;
+    double m = 0.0;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < ncell;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c % nx);
+        const int j = (int)((c / nx) % ny);
+        const int k = (int)(c / ((size_t)nx * ny));
+        const int ip = i == nx - 1 ? 0 : i + 1, jp = j == ny - 1 ? 0 : j + 1;
+        const bool hasup = !g.walls || k < nz - 1;
+        const int ku = k == nz - 1 ? 0 : k + 1;
+        const double uc = 0.5 * ((double)u[c] + (double)u[fid(ip, j, k, nx, ny)]);
+        const double vc = 0.5 * ((double)v[c] + (double)v[fid(i, jp, k, nx, ny)]);
+        const double wku = hasup ? (double)w[fid(i, j, ku, nx, ny)] : 0.0;
+        const double wc = 0.5 * ((double)w[c] + wku);
+        const double s = fabs(uc) * g.idx + fabs(vc) * g.idy + fabs(wc) * g.idz[k];
+        m = fmax(m, s);
+    }
+    m = block_max<T>(m);
+    if (threadIdx.x == 0) atomicMax(&sc->speed_next, dbits(m));
+}
+
+__global__ void k_scalars(StepScalars *sc, StepArgs a, int euler) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double dt = a.dt;
+    if (a.cfl > 0.0) {
+        const double s = bitsd(sc->speed_next);
+        dt = s > 0.0 ? a.cfl / s : a.dt;
+    }
+    sc->speed_cur = sc->speed_next;
+    sc->speed_next = 0ull;
+    sc->maxdiv = 0ull;
+    sc->ke = 0.0;
+    sc->flags = 0;
+    sc->dt = dt;
+    sc->beta = dt / (2.0 * a.re);
+    sc->gamma = euler ? 1.0 : a.gamma;
+    sc->rho = euler ? 0.0 : a.rho;
+}
+
+// Coefficients of the four sweep matrices, in double.  Row i of a line:
+// a(i) x_{i-1} + b(i) x_i + c(i) x_{i+1}; a(0), c(n-1) are the periodic
+// couplings of cyclic lines and 0 otherwise.
+struct SweepCoef {
+    int kind, n, nz, walls;
+    double beta, r;
+    const double *idz, *ihc;
+    FSEI_D double araw(int i) const {
+        if (kind < 2) return -r;
+        if (kind == 2) return -beta * ihc[i] * idz[i];
+        if (walls) { const int k = i + 1; return -beta * idz[k - 1] * ihc[k]; }
+        const int kd = i == 0 ? nz - 1 : i - 1;
+        return -beta * idz[kd] * ihc[i];
+    }
+    FSEI_D double craw(int i) const {
+        if (kind < 2) return -r;
+        if (kind == 2) return -beta * ihc[i + 1] * idz[i];
+        const int k = walls ? i + 1 : i;
+        return -beta * idz[k] * ihc[k];
+    }
+    FSEI_D double b(int i) const { return 1.0 - araw(i) - craw(i); }
+    FSEI_D double a(int i) const { return (kind >= 2 && walls && i == 0) ? 0.0 : araw(i); }
+    FSEI_D double c(int i) const { return (kind >= 2 && walls && i == n - 1) ? 0.0 : craw(i); }
+};
+
+// one block per plan; thread p < P builds chunk p; thread 0 the reduced LU
+template <typename T>
+__global__ void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int kind = blockIdx.x;
+    const TriPlan<T> &pl = W.plan[kind];
+    const TriPlanStore<T> &st = W.store[kind];
+    const int n = pl.n, P = pl.P;
+    double *sat = reinterpret_cast<double *>(smraw);
+    double *sct = sat + n;
+    double *lo = sct + n, *di = lo + 2 * P, *up = di + 2 * P;
+    SweepCoef cf;
+    cf.kind = kind;
+    cf.n = n;
+    cf.nz = g.nz;
+    cf.walls = g.walls;
+    cf.beta = sc->beta;
+    cf.r = kind == 0 ? sc->beta * g.idx2 : sc->beta * g.idy2;
+    cf.idz = g.idz;
+    cf.ihc = g.ihc;
+    const int p = threadIdx.x;
+    if (p < P) {
+        const int s0 = chunk_start(p, n, P), e0 = chunk_start(p + 1, n, P) - 1;
+        for (int i = s0; i <= e0; ++i) {
+            st.a[i] = T(cf.a(i));
+            st.c[i] = T(cf.c(i));
+        }
+        int i = s0 + 1;
+        double inv = 1.0 / cf.b(i);
+        double at = cf.a(i) * inv, ct = cf.c(i) * inv;
+        sat[i] = at; sct[i] = ct;
+        st.inv[i] = T(inv); st.at[i] = T(at); st.ct[i] = T(ct);
+        for (i = s0 + 2; i < e0; ++i) {
+            const double ai = cf.a(i);
+            inv = 1.0 / (cf.b(i) - ai * ct);
+            at = -ai * at * inv;
+            ct = cf.c(i) * inv;
+            sat[i] = at; sct[i] = ct;
+            st.inv[i] = T(inv); st.at[i] = T(at); st.ct[i] = T(ct);
+        }
+        double ah = sat[e0 - 1], ch = sct[e0 - 1];
+        const double ahe = ah, che = ch;
+        for (i = e0 - 2; i > s0; --i) {
+            ah = sat[i] - sct[i] * ah;
+            ch = -sct[i] * ch;
+        }
+        lo[2 * p] = cf.a(s0);
+        di[2 * p] = cf.b(s0) - cf.c(s0) * ah;
+        up[2 * p] = -cf.c(s0) * ch;
+        lo[2 * p + 1] = -cf.a(e0) * ahe;
+        di[2 * p + 1] = cf.b(e0) - cf.a(e0) * che;
+        up[2 * p + 1] = cf.c(e0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int m = 2 * P;
+        const double g0 = -di[0];
+        const double lo0 = lo[0], upm = up[m - 1];
+        if (pl.cyclic) {
+            di[0] -= g0;
+            di[m - 1] -= upm * lo0 / g0;
+        }
+        double inv = 1.0 / di[0];
+        double cp = up[0] * inv;
+        st.rlo[0] = T(lo[0]); st.rinv[0] = T(inv); st.rcp[0] = T(cp);
+        di[0] = inv; up[0] = cp;
+        for (int j = 1; j < m; ++j) {
+            inv = 1.0 / (di[j] - lo[j] * cp);
+            cp = up[j] * inv;
+            st.rlo[j] = T(lo[j]); st.rinv[j] = T(inv); st.rcp[j] = T(cp);
+            di[j] = inv; up[j] = cp;
+        }
+        if (pl.cyclic) {
+            // z = T^-1 (g0, 0, ..., 0, upm); stored in lo[] after use
+            double z = g0 * di[0];
+            lo[0] = z;
+            for (int j = 1; j < m; ++j) {
+                const double uj = (j == m - 1) ? upm : 0.0;
+                z = di[j] * (uj - lo[j] * z);
+                lo[j] = z;
+            }
+            for (int j = m - 2; j >= 0; --j) {
+                z = lo[j] - up[j] * z;
+                lo[j] = z;
+            }
+            const double vl = lo0 / g0;
+            for (int j = 0; j < m; ++j) st.rz[j] = T(lo[j]);
+            st.rsc[0] = T(vl);
+            st.rsc[1] = T(1.0 / (1.0 + lo[0] + vl * lo[m - 1]));
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
+        const StepScalars *sc, TriPlan<T> px, int ry, T fc0, T fc1, T fc2, T inv_re) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sd = reinterpret_cast<T *>(smraw);
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int nl = 3 * ry, es = nl | 1;
+    T *red = sd + (size_t)nx * es;
+    const int rs = 2 * px.P + 1;
+    const int nby = ny / ry;
+    const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * ry;
+    const T dt = T(sc->dt), gam = T(sc->gamma), rho = T(sc->rho);
+    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
+    const T idx = T(g.idx), idy = T(g.idy), idx2 = T(g.idx2), idy2 = T(g.idy2);
+    const bool walls = g.walls != 0;
+    const bool hasdn = !walls || k > 0, hasup = !walls || k < nz - 1;
+    const bool wall_face = walls && k == 0;
+    const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
+    const T idzk = idz[k], idzd = idz[kd], ihck = ihc[k], ihcu = ihc[k + 1];
+    const T h = T(0.5), z0 = T(0);
+    const T *__restrict__ u = F.u;
+    const T *__restrict__ v = F.v;
+    const T *__restrict__ w = F.w;
+    const T *__restrict__ p = F.p;
+
+    for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
+        const int r = e / nx, i = e - r * nx, j = j0 + r;
+        const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+        const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
+        const size_t c0 = fid(i, j, k, nx, ny);
+        // u neighbourhood
+        const T u0 = u[c0], uip = u[fid(ip, j, k, nx, ny)], uim = u[fid(im, j, k, nx, ny)];
+        const T ujp = u[fid(i, jp, k, nx, ny)], ujm = u[fid(i, jm, k, nx, ny)];
+        const T ukp = hasup ? u[fid(i, j, ku, nx, ny)] : z0;
+        const T ukm = hasdn ? u[fid(i, j, kd, nx, ny)] : z0;
+        const T u_ip_jm = u[fid(ip, jm, k, nx, ny)];
+        const T u_ip_kd = hasdn ? u[fid(ip, j, kd, nx, ny)] : z0;
+        // v neighbourhood
+        const T v0 = v[c0], vip = v[fid(ip, j, k, nx, ny)], vim = v[fid(im, j, k, nx, ny)];
+        const T vjp = v[fid(i, jp, k, nx, ny)], vjm = v[fid(i, jm, k, nx, ny)];
+        const T vkp = hasup ? v[fid(i, j, ku, nx, ny)] : z0;
+        const T vkm = hasdn ? v[fid(i, j, kd, nx, ny)] : z0;
+        const T v_im_jp = v[fid(im, jp, k, nx, ny)];
+        const T v_jp_kd = hasdn ? v[fid(i, jp, kd, nx, ny)] : z0;
+        // w neighbourhood (w at the bottom wall face is stored as 0)
+        const T w0 = w[c0], wip = w[fid(ip, j, k, nx, ny)], wim = w[fid(im, j, k, nx, ny)];
+        const T wjp = w[fid(i, jp, k, nx, ny)], wjm = w[fid(i, jm, k, nx, ny)];
+        const T wku = hasup ? w[fid(i, j, ku, nx, ny)] : z0;
+        const T wkd = hasdn ? w[fid(i, j, kd, nx, ny)] : z0;
+        const T w_im_ku = hasup ? w[fid(im, j, ku, nx, ny)] : z0;
+        const T w_jm_ku = hasup ? w[fid(i, jm, ku, nx, ny)] : z0;
+        // p
+        const T p0 = p[c0], pim = p[fid(im, j, k, nx, ny)], pjm = p[fid(i, jm, k, nx, ny)];
+        const T pkd = hasdn ? p[fid(i, j, kd, nx, ny)] : z0;
+
+        // cross fluxes at the cell edges
+        const T e_xy = (h * (v0 + vim)) * (h * (u0 + ujm));          // (x_i, y_j)
+        const T e_xy_jp = (h * (vjp + v_im_jp)) * (h * (ujp + u0));  // (x_i, y_j+1)
+        const T e_xy_ip = (h * (vip + v0)) * (h * (uip + u_ip_jm));  // (x_i+1, y_j)
+        const T e_xz = hasdn ? (h * (w0 + wim)) * (h * (u0 + ukm)) : z0;          // (x_i, z_k)
+        const T e_xz_kp = hasup ? (h * (wku + w_im_ku)) * (h * (ukp + u0)) : z0;  // (x_i, z_k+1)
+        const T e_xz_ip = hasdn ? (h * (wip + w0)) * (h * (uip + u_ip_kd)) : z0;  // (x_i+1, z_k)
+        const T e_yz = hasdn ? (h * (w0 + wjm)) * (h * (v0 + vkm)) : z0;
+        const T e_yz_kp = hasup ? (h * (wku + w_jm_ku)) * (h * (vkp + v0)) : z0;
+        const T e_yz_jp = hasdn ? (h * (wjp + w0)) * (h * (vjp + v_jp_kd)) : z0;
+
+        const T ucp = h * (u0 + uip), ucm = h * (uim + u0);
+        const T Hu = -((ucp * ucp - ucm * ucm) * idx + (e_xy_jp - e_xy) * idy +
+                       (e_xz_kp - e_xz) * idzk);
+        const T vcp = h * (v0 + vjp), vcm = h * (vjm + v0);
+        const T Hv = -((e_xy_ip - e_xy) * idx + (vcp * vcp - vcm * vcm) * idy +
+                       (e_yz_kp - e_yz) * idzk);
+        T Hw = z0;
+        if (!wall_face) {
+            const T wcp = h * (w0 + wku), wcm = h * (wkd + w0);
+            Hw = -((e_xz_ip - e_xz) * idx + (e_yz_jp - e_yz) * idy + (wcp * wcp - wcm * wcm) * ihck);
+        }
+        const T Lu = (uip - T(2) * u0 + uim) * idx2 + (ujp - T(2) * u0 + ujm) * idy2 +
+                     ((ukp - u0) * ihcu - (u0 - ukm) * ihck) * idzk;
+        const T Lv = (vip - T(2) * v0 + vim) * idx2 + (vjp - T(2) * v0 + vjm) * idy2 +
+                     ((vkp - v0) * ihcu - (v0 - vkm) * ihck) * idzk;
+        const T fx = F.fx ? F.fx[c0] : z0, fy = F.fy ? F.fy[c0] : z0;
+        const T ru = dt * (gam * Hu + rho * F.hu[c0] + inv_re * Lu - (p0 - pim) * idx + fx + fc0);
+        const T rv = dt * (gam * Hv + rho * F.hv[c0] + inv_re * Lv - (p0 - pjm) * idy + fy + fc1);
+        T rw = z0;
+        if (!wall_face) {
+            const T Lw = (wip - T(2) * w0 + wim) * idx2 + (wjp - T(2) * w0 + wjm) * idy2 +
+                         ((wku - w0) * idzk - (w0 - wkd) * idzd) * ihck;
+            const T fz = F.fz ? F.fz[c0] : z0;
+            rw = dt * (gam * Hw + rho * F.hw[c0] + inv_re * Lw - (p0 - pkd) * ihck + fz + fc2);
+        }
+        F.hu[c0] = Hu;
+        F.hv[c0] = Hv;
+        F.hw[c0] = Hw;
+        sd[i * es + r] = ru;
+        sd[i * es + ry + r] = rv;
+        sd[i * es + 2 * ry + r] = rw;
+    }
+    __syncthreads();
+    tri_plan_solve<T, T>(sd, es, 1, nl, px, red, rs);
+    for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
+        const int r = e / nx, i = e - r * nx;
+        const size_t c0 = fid(i, j0 + r, k, nx, ny);
+        q0[c0] = sd[i * es + r];
+        q1[c0] = sd[i * es + ry + r];
+        q2[c0] = sd[i * es + 2 * ry + r];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_sweep_y(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2, TriPlan<T> py,
+          int tx) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sd = reinterpret_cast<T *>(smraw);
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    T *red = sd + (size_t)ny * tx;
+    const int rs = 2 * py.P + 1;
+    const int nxt = (nx + tx - 1) / tx;
+    int b = blockIdx.x;
+    const int xt = b % nxt; b /= nxt;
+    const int k = b % nz;
+    const int comp = b / nz;
+    T *q = comp == 0 ? q0 : (comp == 1 ? q1 : q2);
+    const int x0 = xt * tx;
+    for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
+        const int j = e / tx, l = e - j * tx;
+        sd[e] = (x0 + l < nx) ? q[fid(x0 + l, j, k, nx, ny)] : T(0);
+    }
+    __syncthreads();
+    tri_plan_solve<T, T>(sd, tx, 1, tx, py, red, rs);
+    for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
+        const int j = e / tx, l = e - j * tx;
+        if (x0 + l < nx) q[fid(x0 + l, j, k, nx, ny)] = sd[e];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_sweep_z(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
+          TriPlan<T> pzc, TriPlan<T> pzf, int tx) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sd = reinterpret_cast<T *>(smraw);
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    T *red = sd + (size_t)nz * tx;
+    const int nxt = (nx + tx - 1) / tx;
+    int b = blockIdx.x;
+    const int xt = b % nxt; b /= nxt;
+    const int j = b % ny;
+    const int comp = b / ny;
+    T *q = comp == 0 ? q0 : (comp == 1 ? q1 : q2);
+    const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
+    const TriPlan<T> &pl = comp < 2 ? pzc : pzf;
+    const int rs = 2 * pl.P + 1;
+    const int x0 = xt * tx;
+    for (int e = threadIdx.x; e < nz * tx; e += blockDim.x) {
+        const int k = e / tx, l = e - k * tx;
+        sd[e] = (x0 + l < nx) ? q[fid(x0 + l, j, k, nx, ny)] : T(0);
+    }
+    __syncthreads();
+    tri_plan_solve<T, T>(sd, tx, 1, tx, pl, red, rs);
+    for (int e = threadIdx.x; e < nz * tx; e += blockDim.x) {
+        const int k = e / tx, l = e - k * tx;
+        if (x0 + l < nx) {
+            const size_t c = fid(x0 + l, j, k, nx, ny);
+            q[c] = un[c] + sd[e];
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+template <typename T> size_t smem_rhs_x(const GridDev &g, const Work<T> &W) {
+    const int nl = 3 * W.ry, es = nl | 1;
+    return sizeof(T) * ((size_t)g.nx * es + (size_t)nl * (2 * W.plan[0].P + 1));
+}
+template <typename T> size_t smem_sweep(int n, const Work<T> &W, int P) {
+    return sizeof(T) * ((size_t)n * W.tx + (size_t)W.tx * (2 * P + 1));
+}
+
+template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v, const T *w,
+                                        StepScalars *sc, cudaStream_t st) {
+    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
+    int blocks = (int)((ncell + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_speed<T><<<blocks, 256, 0, st>>>(g, u, v, w, sc);
+}
+
+template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepScalars *sc,
+                                             const StepArgs &a, int euler, cudaStream_t st) {
+    k_scalars<<<1, 32, 0, st>>>(sc, a, euler);
+    int maxn = 0, maxp = 0;
+    for (int q = 0; q < 4; ++q) {
+        if (W.plan[q].n > maxn) maxn = W.plan[q].n;
+        if (W.plan[q].P > maxp) maxp = W.plan[q].P;
+    }
+    const size_t sm = sizeof(double) * (2 * (size_t)maxn + 6 * (size_t)maxp);
+    k_plans<T><<<4, ((maxp + 31) / 32) * 32, sm, st>>>(g, W, sc);
+}
+
+template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
+                                        const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
+    const int nl = 3 * W.ry;
+    const int threads = ((nl * W.plan[0].P + 31) / 32) * 32;
+    const int blocks = g.nz * (g.ny / W.ry);
+    k_rhs_x<T><<<blocks, threads, smem_rhs_x(g, W), st>>>(
+        g, F, W.q0, W.q1, W.q2, sc, W.plan[0], W.ry, T(a.fconst[0]), T(a.fconst[1]),
+        T(a.fconst[2]), T(1.0 / a.re));
+}
+
+template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, cudaStream_t st) {
+    const int threads = ((W.tx * W.plan[1].P + 31) / 32) * 32;
+    const int nxt = (g.nx + W.tx - 1) / W.tx;
+    k_sweep_y<T><<<3 * g.nz * nxt, threads, smem_sweep<T>(g.ny, W, W.plan[1].P), st>>>(
+        g, W.q0, W.q1, W.q2, W.plan[1], W.tx);
+}
+
+template <typename T> void launch_sweep_z(const GridDev &g, const Fields<T> &F, Work<T> &W,
+                                          cudaStream_t st) {
+    const int P = W.plan[2].P > W.plan[3].P ? W.plan[2].P : W.plan[3].P;
+    const int threads = ((W.tx * P + 31) / 32) * 32;
+    const int nxt = (g.nx + W.tx - 1) / W.tx;
+    k_sweep_z<T><<<3 * g.ny * nxt, threads, smem_sweep<T>(g.nz, W, P), st>>>(
+        g, F, W.q0, W.q1, W.q2, W.plan[2], W.plan[3], W.tx);
+}
+
+template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T> &W) {
+    const int P = W.plan[2].P > W.plan[3].P ? W.plan[2].P : W.plan[3].P;
+    cudaFuncSetAttribute(k_rhs_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_rhs_x(g, W));
+    cudaFuncSetAttribute(k_sweep_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_sweep<T>(g.ny, W, W.plan[1].P));
+    cudaFuncSetAttribute(k_sweep_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_sweep<T>(g.nz, W, P));
+}
+
+#define FSEI_INST(T)                                                                           \
+    template size_t smem_rhs_x<T>(const GridDev &, const Work<T> &);                          \
+    template size_t smem_sweep<T>(int, const Work<T> &, int);                                 \
+    template void launch_speed<T>(const GridDev &, const T *, const T *, const T *,            \
+                                  StepScalars *, cudaStream_t);                               \
+    template void launch_step_begin<T>(const GridDev &, Work<T> &, StepScalars *,              \
+                                       const StepArgs &, int, cudaStream_t);                  \
+    template void launch_rhs_x<T>(const GridDev &, const Fields<T> &, Work<T> &,               \
+                                  const StepScalars *, const StepArgs &, cudaStream_t);       \
+    template void launch_sweep_y<T>(const GridDev &, Work<T> &, cudaStream_t);                 \
+    template void launch_sweep_z<T>(const GridDev &, const Fields<T> &, Work<T> &,             \
+                                    cudaStream_t);                                            \
+    template void set_smem_limits_sweep<T>(const GridDev &, const Work<T> &);
+FSEI_INST(float)
+FSEI_INST(double)
+#undef FSEI_INST
+
+}  // namespace fsei

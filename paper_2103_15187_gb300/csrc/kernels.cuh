@@ -1,0 +1,68 @@
+// Launch interface between the host library (api.cu) and the kernels of one
+// fractional step.  Internal to libfsei.so.
+#pragma once
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace fsei {
+
+// Body force and state fields of one step (device pointers, caller-owned).
+template <typename T> struct Fields {
+    T *u, *v, *w, *p, *hu, *hv, *hw;
+    const T *fx, *fy, *fz;   // may be NULL
+};
+
+// Library-owned workspace and launch configuration of one grid.
+template <typename T> struct Work {
+    T *q0, *q1, *q2;         // sweep intermediates, then u* (3 fields)
+    T *phi;                  // pressure increment (1 field)
+    cplx<T> *spec;           // spectrum [nz][ny][sk]
+    TriPlanStore<T> store[4];
+    TriPlan<T> plan[4];      // 0: x, 1: y, 2: z at centres, 3: z at faces
+    FftPlanDev fpx, fpy;     // x: length nx/2, y: length ny
+    const cplx<T> *twx, *twy, *twpost;   // w^m tables; twpost[k] =
+                                          // exp(-2 pi i k / nx), k <= nx/2
+    const T *lamx, *lamy;    // modified wavenumbers (sk and ny entries)
+    const double *lamx_d, *lamy_d;
+    const int *nzm;          // near-zero modes to solve in double: kx + sk*ky
+    int n_nzm;
+    double *nz_scratch;      // 2 * nz doubles per near-zero mode
+    int ry;                  // rows per block of the x-line kernels
+    int tx;                  // x columns per block of the y/z sweeps
+    int tkx;                 // kx columns per block of the y FFT / z Poisson
+    int pz_poisson;          // chunks per z line in the Poisson solve
+};
+
+struct StepArgs {
+    double re, dt, cfl, gamma, rho;
+    double fconst[3];
+};
+
+template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v, const T *w,
+                                        StepScalars *sc, cudaStream_t st);
+template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepScalars *sc,
+                                             const StepArgs &a, int euler, cudaStream_t st);
+template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
+                                        const StepScalars *sc, const StepArgs &a, cudaStream_t st);
+template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, cudaStream_t st);
+template <typename T> void launch_sweep_z(const GridDev &g, const Fields<T> &F, Work<T> &W,
+                                          cudaStream_t st);
+// mode 0: s = D(q0,q1,q2) / dt ; mode 1: s = the given field src (scaled 1)
+template <typename T> void launch_rfft_x(const GridDev &g, Work<T> &W, const StepScalars *sc,
+                                         const T *src, int mode, cudaStream_t st);
+template <typename T> void launch_fft_y(const GridDev &g, Work<T> &W, int inverse, cudaStream_t st);
+template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaStream_t st);
+template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st);
+template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,
+                                          StepScalars *sc, cudaStream_t st);
+
+// dynamic shared memory bytes of each kernel (host-side sizing helpers)
+template <typename T> size_t smem_rhs_x(const GridDev &g, const Work<T> &W);
+template <typename T> size_t smem_sweep(int n, const Work<T> &W, int P);
+template <typename T> size_t smem_fft_x(const GridDev &g, const Work<T> &W);
+template <typename T> size_t smem_fft_y(const GridDev &g, const Work<T> &W);
+template <typename T> size_t smem_poisson(const GridDev &g, const Work<T> &W);
+template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T> &W);
+template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<T> &W);
+
+}  // namespace fsei

@@ -1,0 +1,219 @@
+// Batched tridiagonal solves in shared memory for the approximately
+// factorised viscous step (Sec. 3.1: one tridiagonal system per direction,
+// cyclic in the two periodic directions) and for the z systems of the
+// pressure Poisson equation.
+//
+// Partitioned elimination.  Each line of n unknowns is cut into P chunks
+// [s, e].  In a chunk the interior rows s+1..e-1 are eliminated downwards,
+// which writes every interior unknown as
+//     x_i = d~_i - a~_i x_s - c~_i x_{i+1},
+// and an upward pass then gives x_{s+1} and x_{e-1} through the two chunk
+// ends x_s, x_e alone.  Substituting those into the original rows s and e
+// leaves a tridiagonal system in the 2P chunk ends (cyclic when the line is
+// periodic: the periodic coupling of the original line becomes the corner
+// coupling of the reduced one).  It is solved by one thread per line with
+// Thomas' algorithm, plus a Sherman-Morrison correction when cyclic.  A last
+// upward pass per chunk recovers the interior.  This is Gaussian
+// elimination in another order; for the diagonally dominant matrices here
+// it needs no pivoting, like the Thomas algorithm it replaces.
+#pragma once
+#include "common.cuh"
+
+namespace fsei {
+
+// y - a x for real or complex x, y and real a
+template <typename T> FSEI_D T nmad(T a, T x, T y) { return y - a * x; }
+template <typename T> FSEI_D cplx<T> nmad(T a, cplx<T> x, cplx<T> y) {
+    return {y.re - a * x.re, y.im - a * x.im};
+}
+template <typename T> FSEI_D T scl(T a, T x) { return a * x; }
+template <typename T> FSEI_D cplx<T> scl(T a, cplx<T> x) { return {a * x.re, a * x.im}; }
+template <typename T> FSEI_D T addv(T a, T b) { return a + b; }
+template <typename T> FSEI_D cplx<T> addv(cplx<T> a, cplx<T> b) { return a + b; }
+
+// Solve nl lines held in shared memory with the matrix-only factors of a
+// TriPlan (same matrix for every line).  Element i of line l lives at
+// s[(i + plan.off) * es + l * ls].  Threads t < nl * P own chunk t / nl of
+// line t % nl.  red: shared scratch of nl * rs values (rs >= 2P).
+// Must be called by every thread of the block.
+template <typename T, typename V>
+__device__ void tri_plan_solve(V *s, int es, int ls, int nl, const TriPlan<T> &pl,
+                               V *red, int rs) {
+    const int t = threadIdx.x;
+    const int n = pl.n, P = pl.P, off = pl.off;
+    const bool active = t < nl * P;
+    const int l = t % nl, p = t / nl;
+    int s0 = 0, e0 = 0;
+    V *d = s + l * ls;
+    if (active) {
+        s0 = chunk_start(p, n, P);
+        e0 = chunk_start(p + 1, n, P) - 1;
+        // downward elimination of the interior
+        V prev = scl(pl.inv[s0 + 1], d[(s0 + 1 + off) * es]);
+        d[(s0 + 1 + off) * es] = prev;
+        for (int i = s0 + 2; i < e0; ++i) {
+            prev = scl(pl.inv[i], nmad(pl.a[i], prev, d[(i + off) * es]));
+            d[(i + off) * es] = prev;
+        }
+        // upward pass: right-hand side part of x_{s+1} (through x_s, x_e)
+        V dh = d[(e0 - 1 + off) * es];
+        const V dhe = dh;
+        for (int i = e0 - 2; i > s0; --i) dh = nmad(pl.ct[i], dh, d[(i + off) * es]);
+        red[l * rs + 2 * p] = nmad(pl.c[s0], dh, d[(s0 + off) * es]);
+        red[l * rs + 2 * p + 1] = nmad(pl.a[e0], dhe, d[(e0 + off) * es]);
+    }
+    __syncthreads();
+    if (t < nl) {
+        V *r = red + t * rs;
+        const int m = 2 * P;
+        V y = scl(pl.rinv[0], r[0]);
+        r[0] = y;
+        for (int j = 1; j < m; ++j) {
+            y = scl(pl.rinv[j], nmad(pl.rlo[j], y, r[j]));
+            r[j] = y;
+        }
+        for (int j = m - 2; j >= 0; --j) {
+            y = nmad(pl.rcp[j], y, r[j]);
+            r[j] = y;
+        }
+        if (pl.cyclic) {
+            const V f = scl(pl.rsc[1], addv(r[0], scl(pl.rsc[0], r[m - 1])));
+            for (int j = 0; j < m; ++j) r[j] = nmad(pl.rz[j], f, r[j]);
+        }
+    }
+    __syncthreads();
+    if (active) {
+        const V F = red[l * rs + 2 * p], E = red[l * rs + 2 * p + 1];
+        d[(s0 + off) * es] = F;
+        d[(e0 + off) * es] = E;
+        V x = E;
+        for (int i = e0 - 1; i > s0; --i) {
+            x = nmad(pl.ct[i], x, nmad(pl.at[i], F, d[(i + off) * es]));
+            d[(i + off) * es] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// Same elimination with a matrix that differs per line (the Poisson z
+// systems, one per Fourier mode: real matrix, complex right-hand side).
+// The factors are computed on the fly: fa, fc hold a~, c~ (layout of the
+// data with strides fes, fls); rlo, rdi, rup, rr hold the reduced rows.
+// Mat provides a(i), c(i) (real, line-independent) and b(l, i).
+template <typename T, typename Mat>
+__device__ void tri_fly_solve(cplx<T> *s, int es, int ls, T *fa, T *fc, int fes, int fls,
+                              int nl, int n, int P, int cyclic, const Mat &M,
+                              cplx<T> *rr, T *rlo, T *rdi, T *rup, int rs) {
+    const int t = threadIdx.x;
+    const bool active = t < nl * P;
+    const int l = t % nl, p = t / nl;
+    int s0 = 0, e0 = 0;
+    cplx<T> *d = s + l * ls;
+    T *A = fa + l * fls, *C = fc + l * fls;
+    if (active) {
+        s0 = chunk_start(p, n, P);
+        e0 = chunk_start(p + 1, n, P) - 1;
+        int i = s0 + 1;
+        T inv = T(1) / M.b(l, i);
+        T at = M.a(i) * inv, ct = M.c(i) * inv;
+        A[i * fes] = at;
+        C[i * fes] = ct;
+        cplx<T> prev = scl(inv, d[i * es]);
+        d[i * es] = prev;
+        for (i = s0 + 2; i < e0; ++i) {
+            const T ai = M.a(i);
+            inv = T(1) / (M.b(l, i) - ai * ct);
+            at = -ai * at * inv;
+            ct = M.c(i) * inv;
+            A[i * fes] = at;
+            C[i * fes] = ct;
+            prev = scl(inv, nmad(ai, prev, d[i * es]));
+            d[i * es] = prev;
+        }
+        cplx<T> dh = d[(e0 - 1) * es];
+        T ah = A[(e0 - 1) * fes], ch = C[(e0 - 1) * fes];
+        const cplx<T> dhe = dh;
+        const T ahe = ah, che = ch;
+        for (i = e0 - 2; i > s0; --i) {
+            const T cti = C[i * fes];
+            dh = nmad(cti, dh, d[i * es]);
+            ah = A[i * fes] - cti * ah;
+            ch = -cti * ch;
+        }
+        const T as = M.a(s0), cs = M.c(s0), ae = M.a(e0), ce = M.c(e0);
+        const int jF = l * rs + 2 * p, jE = jF + 1;
+        rlo[jF] = as;
+        rdi[jF] = M.b(l, s0) - cs * ah;
+        rup[jF] = -cs * ch;
+        rr[jF] = nmad(cs, dh, d[s0 * es]);
+        rlo[jE] = -ae * ahe;
+        rdi[jE] = M.b(l, e0) - ae * che;
+        rup[jE] = ce;
+        rr[jE] = nmad(ae, dhe, d[e0 * es]);
+    }
+    __syncthreads();
+    if (t < nl) {
+        const int m = 2 * P, o = t * rs;
+        T *lo = rlo + o, *di = rdi + o, *up = rup + o;
+        cplx<T> *r = rr + o;
+        T g = T(0), lo0 = lo[0];
+        if (cyclic) {
+            g = -di[0];
+            di[0] -= g;
+            di[m - 1] -= up[m - 1] * lo0 / g;
+        }
+        // forward: overwrite up[] with c', di[] with 1/den
+        T inv = T(1) / di[0];
+        di[0] = inv;
+        up[0] *= inv;
+        cplx<T> y = scl(inv, r[0]);
+        r[0] = y;
+        for (int j = 1; j < m; ++j) {
+            inv = T(1) / (di[j] - lo[j] * up[j - 1]);
+            di[j] = inv;
+            up[j] *= inv;
+            y = scl(inv, nmad(lo[j], y, r[j]));
+            r[j] = y;
+        }
+        for (int j = m - 2; j >= 0; --j) {
+            y = nmad(up[j], y, r[j]);
+            r[j] = y;
+        }
+        if (cyclic) {
+            // Sherman-Morrison: z = T^-1 u with u = (g, 0, ..., 0, c_{n-1}),
+            // the last entry being the original corner coupling of the line.
+            // z overwrites lo[] (each lo[j] is read before it is replaced).
+            const T cl = M.c(n - 1);
+            T z = g * di[0];
+            lo[0] = z;
+            for (int j = 1; j < m; ++j) {
+                const T uj = (j == m - 1) ? cl : T(0);
+                z = di[j] * (uj - lo[j] * z);
+                lo[j] = z;
+            }
+            for (int j = m - 2; j >= 0; --j) {
+                z = lo[j] - up[j] * z;
+                lo[j] = z;
+            }
+            const T vl = lo0 / g;
+            const T fac = T(1) / (T(1) + lo[0] + vl * lo[m - 1]);
+            const cplx<T> f = scl(fac, addv(r[0], scl(vl, r[m - 1])));
+            for (int j = 0; j < m; ++j) r[j] = nmad(lo[j], f, r[j]);
+        }
+    }
+    __syncthreads();
+    if (active) {
+        const int jF = l * rs + 2 * p;
+        const cplx<T> F = rr[jF], E = rr[jF + 1];
+        d[s0 * es] = F;
+        d[e0 * es] = E;
+        cplx<T> x = E;
+        for (int i = e0 - 1; i > s0; --i) {
+            x = nmad(C[i * fes], x, nmad(A[i * fes], F, d[i * es]));
+            d[i * es] = x;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace fsei

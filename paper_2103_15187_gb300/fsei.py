@@ -1,0 +1,218 @@
+"""ctypes binding of libfsei.so (include/fsei.h): argument marshalling only.
+
+Every step of the fractional-step integrator runs in the library's CUDA
+kernels; torch tensors only supply device memory and the CUDA stream.  The
+library is loaded on first use and a missing or unloadable library raises
+``FseiUnavailable`` -- there is no fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfsei.so")
+
+FSEI_OK = 0
+STATUS_NAMES = {0: "FSEI_OK", 1: "FSEI_E_ARG", 2: "FSEI_E_SHAPE",
+                3: "FSEI_E_UNSUPPORTED", 4: "FSEI_E_NOMEM", 5: "FSEI_E_CUDA",
+                6: "FSEI_E_NONFINITE", 7: "FSEI_E_CFL", 8: "FSEI_E_TIMEOUT"}
+FSEI_FP64, FSEI_MIXED = 0, 1
+FSEI_Z_PERIODIC, FSEI_Z_WALLS = 0, 1
+FLAG_NONFINITE, FLAG_CFL = 1, 2
+
+# exported symbols and their C signatures (kept in step with include/fsei.h)
+EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
+           "fsei_step", "fsei_poisson_solve", "fsei_set_kernel_timing",
+           "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version")
+
+
+class FseiUnavailable(RuntimeError):
+    pass
+
+
+class FseiError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("zbc", ctypes.c_int32), ("lz", ctypes.c_double),
+                ("stretch", ctypes.c_double),
+                ("zfaces", ctypes.POINTER(ctypes.c_double)),
+                ("prec", ctypes.c_int32), ("near_zero_tau", ctypes.c_double)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("p", ctypes.c_void_p), ("hu", ctypes.c_void_p), ("hv", ctypes.c_void_p),
+                ("hw", ctypes.c_void_p), ("have_prev_h", ctypes.c_int32)]
+
+
+class StepParams(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("dt", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("rho", ctypes.c_double),
+                ("fconst", ctypes.c_double * 3)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("dt_used", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("max_div", ctypes.c_double), ("kinetic_energy", ctypes.c_double),
+                ("flags", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libfsei.so (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FseiUnavailable("libfsei.so not built at %s (run __graft_entry__.build())" % path)
+    try:
+        lib = ctypes.CDLL(path)
+    except OSError as exc:
+        raise FseiUnavailable("cannot load %s: %s" % (path, exc)) from exc
+    vp = ctypes.c_void_p
+    lib.fsei_grid_create.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(vp)]
+    lib.fsei_grid_create.restype = ctypes.c_int
+    lib.fsei_grid_destroy.argtypes = [vp]
+    lib.fsei_grid_destroy.restype = None
+    lib.fsei_grid_workspace_bytes.argtypes = [vp]
+    lib.fsei_grid_workspace_bytes.restype = ctypes.c_int64
+    lib.fsei_step.argtypes = [vp, ctypes.POINTER(State), vp, vp, vp,
+                              ctypes.POINTER(StepParams), ctypes.c_int32, vp,
+                              ctypes.POINTER(StepStats)]
+    lib.fsei_step.restype = ctypes.c_int
+    lib.fsei_poisson_solve.argtypes = [vp, vp, vp, vp]
+    lib.fsei_poisson_solve.restype = ctypes.c_int
+    lib.fsei_set_kernel_timing.argtypes = [vp, ctypes.c_int32]
+    lib.fsei_set_kernel_timing.restype = ctypes.c_int
+    lib.fsei_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
+    lib.fsei_kernel_times.restype = ctypes.c_int32
+    lib.fsei_kernel_name.argtypes = [ctypes.c_int32]
+    lib.fsei_kernel_name.restype = ctypes.c_char_p
+    lib.fsei_last_error.argtypes = []
+    lib.fsei_last_error.restype = ctypes.c_char_p
+    lib.fsei_version.argtypes = []
+    lib.fsei_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != FSEI_OK:
+        raise FseiError(status, load().fsei_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+class Grid:
+    """Owning wrapper of an fsei_grid handle (fsei_grid_create /
+    fsei_grid_destroy)."""
+
+    def __init__(self, nx, ny, nz, lx, ly, zbc=FSEI_Z_WALLS, lz=2.0, stretch=0.0,
+                 prec=FSEI_FP64, zfaces=None, near_zero_tau=0.0):
+        lib = load()
+        d = GridDesc()
+        d.nx, d.ny, d.nz = nx, ny, nz
+        d.lx, d.ly, d.zbc, d.lz, d.stretch = lx, ly, zbc, lz, stretch
+        d.prec = prec
+        d.near_zero_tau = near_zero_tau
+        self._zf = None
+        if zfaces is not None:
+            self._zf = np.ascontiguousarray(zfaces, dtype=np.float64)
+            d.zfaces = self._zf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        _check(lib.fsei_grid_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.prec = prec
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def workspace_bytes(self):
+        return load().fsei_grid_workspace_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().fsei_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grid_create(**kw):
+    return Grid(**kw)
+
+
+def step(grid, state, f=None, re=100.0, dt=1e-3, cfl=0.0, gamma=1.5, rho=-0.5,
+         fconst=(0.0, 0.0, 0.0), nsteps=1, stream=None, stats=True):
+    """fsei_step on a dict of torch tensors u, v, w, p, hu, hv, hw and the
+    key have_prev_h (updated in place).  f: None or (fx, fy, fz) tensors.
+    Returns the statistics dict of the last step when stats=True (the call
+    then synchronises the stream), else None."""
+    lib = load()
+    st = State(_ptr(state["u"]), _ptr(state["v"]), _ptr(state["w"]), _ptr(state["p"]),
+               _ptr(state["hu"]), _ptr(state["hv"]), _ptr(state["hw"]),
+               int(state.get("have_prev_h", 0)))
+    prm = StepParams(re, dt, cfl, gamma, rho, (ctypes.c_double * 3)(*fconst))
+    fx, fy, fz = (None, None, None) if f is None else f
+    out = StepStats() if stats else None
+    status = lib.fsei_step(grid.handle, ctypes.byref(st), _ptr(fx), _ptr(fy), _ptr(fz),
+                           ctypes.byref(prm), int(nsteps), _stream_handle(stream),
+                           ctypes.byref(out) if out is not None else None)
+    state["have_prev_h"] = st.have_prev_h
+    _check(status)
+    return out.as_dict() if out is not None else None
+
+
+def poisson_solve(grid, rhs, phi, stream=None):
+    """fsei_poisson_solve: phi with D G phi = rhs (device tensors)."""
+    _check(load().fsei_poisson_solve(grid.handle, _ptr(rhs), _ptr(phi),
+                                     _stream_handle(stream)))
+
+
+def set_kernel_timing(grid, enable):
+    """fsei_set_kernel_timing: event pairs around every kernel launch."""
+    _check(load().fsei_set_kernel_timing(grid.handle, int(bool(enable))))
+
+
+def kernel_times(grid):
+    """fsei_kernel_times: {kernel name: (total ms, launches)} since the last
+    call (synchronises the device)."""
+    lib = load()
+    cap = 32
+    ms = (ctypes.c_double * cap)()
+    n = (ctypes.c_int64 * cap)()
+    count = lib.fsei_kernel_times(grid.handle, ms, n, cap)
+    return {lib.fsei_kernel_name(k).decode(): (ms[k], n[k]) for k in range(count)}
+
+
+def version():
+    return load().fsei_version().decode()

@@ -1,0 +1,139 @@
+"""GPU parity of the CUDA fractional step (through the C ABI) against the FP64
+oracle on the same seeded inputs (Sec. 2.1, Eq. 3; Sec. 3.1).
+
+FP64 gate: relative L2 <= 1e-12 per field.  Mixed precision: velocity
+relative L2 <= 1e-5 against the FP64 oracle after 100 steps.  Grids include
+ragged tiles (extents that are not multiples of the kernels' tile widths),
+periodic and wall-bounded z, stretched meshes, body forces and CFL-driven dt.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2103_15187_gb300 import inputs
+from oracle.grid import Grid as OGrid, Z_PERIODIC, Z_WALLS
+from oracle.poisson import oracle_poisson
+
+import parity_util as pu
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def fsei():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_15187_gb300 import fsei as mod
+    mod.load()
+    return mod
+
+
+def _compatible_rhs(g, seed):
+    rng = np.random.default_rng(seed)
+    s = rng.standard_normal(g.shape)
+    vol = g.cell_volume_uvp()
+    return s - (s * vol).sum() / (vol.sum() * g.nx * g.ny)
+
+
+POISSON_GRIDS = [
+    (12, 24, 9, Z_WALLS, 2.0),      # ragged: 12/2 = 6 modes, odd nz
+    (32, 32, 32, Z_PERIODIC, 0.0),
+    (48, 36, 20, Z_WALLS, 2.0),
+    (64, 16, 24, Z_PERIODIC, 0.0),
+    (96, 96, 40, Z_WALLS, 1.5),     # radix-3 FFT lengths
+    (256, 64, 48, Z_WALLS, 2.0),
+]
+
+
+@pytest.mark.parametrize("nx,ny,nz,zbc,stretch", POISSON_GRIDS)
+def test_poisson_fp64_matches_oracle(fsei, nx, ny, nz, zbc, stretch):
+    import torch
+    g = OGrid(nx, ny, nz, 2 * np.pi, np.pi, zbc, lz=2.0, stretch=stretch)
+    s = _compatible_rhs(g, nx + ny + nz)
+    ref = oracle_poisson(g, s)
+    grid = fsei.Grid(nx, ny, nz, 2 * np.pi, np.pi, zbc=zbc, lz=2.0, stretch=stretch,
+                     prec=fsei.FSEI_FP64)
+    rhs = torch.tensor(s, dtype=torch.float64, device="cuda")
+    phi = torch.empty_like(rhs)
+    fsei.poisson_solve(grid, rhs, phi)
+    torch.cuda.synchronize()
+    err = pu.rel_l2(phi.cpu().numpy(), ref)
+    assert err <= FP64_TOL, err
+
+
+@pytest.mark.parametrize("nx,ny,nz,zbc,stretch", POISSON_GRIDS[:4])
+def test_poisson_mixed_error_stated(fsei, nx, ny, nz, zbc, stretch):
+    import torch
+    g = OGrid(nx, ny, nz, 2 * np.pi, np.pi, zbc, lz=2.0, stretch=stretch)
+    s = _compatible_rhs(g, 7 + nx)
+    ref = oracle_poisson(g, s)
+    grid = fsei.Grid(nx, ny, nz, 2 * np.pi, np.pi, zbc=zbc, lz=2.0, stretch=stretch,
+                     prec=fsei.FSEI_MIXED)
+    rhs = torch.tensor(s, dtype=torch.float32, device="cuda")
+    phi = torch.empty_like(rhs)
+    fsei.poisson_solve(grid, rhs, phi)
+    torch.cuda.synchronize()
+    err = pu.rel_l2(phi.double().cpu().numpy(), ref)
+    assert err <= 1e-5, err
+
+
+def _assert_fp64(gpu, ref, tol=FP64_TOL):
+    errs = pu.compare(gpu, ref)
+    bad = {k: e for k, e in errs.items() if not e <= tol}
+    assert not bad, errs
+
+
+def test_taylor_green_fp64_10_steps(fsei):
+    """32^3 triply periodic Taylor-Green, Re 100, dt 1e-3, 10 steps."""
+    case = inputs.case_taylor_green(32, steps=10)
+    gpu, st = pu.run_gpu(case, 10, fsei.FSEI_FP64)
+    ref, rst = pu.run_oracle(case, 10)
+    _assert_fp64(gpu, ref)
+    assert abs(st["kinetic_energy"] / rst[-1]["kinetic_energy"] - 1) < 1e-12
+    assert st["max_div"] < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(48, 24, 36), (48, 36, 17)])
+def test_channel_fp64_10_steps(fsei, shape):
+    """Stretched channel with random solenoidal perturbation, Gaussian-blob
+    body force, Poiseuille drive and CFL 0.5 time step; ragged extents."""
+    nx, ny, nz = shape
+    case = inputs.case_channel(nx, ny, nz, steps=10, kmax=4.0, rms=0.3, seed=nx,
+                               blobs=dict(nblobs=3, sigma=3.0, amp=10.0))
+    gpu, st = pu.run_gpu(case, 10, fsei.FSEI_FP64, per_call=4)
+    ref, rst = pu.run_oracle(case, 10)
+    _assert_fp64(gpu, ref)
+    assert abs(st["dt_used"] / rst[-1]["dt_used"] - 1) < 1e-12
+    assert abs(st["cfl"] / rst[-1]["cfl"] - 1) < 1e-12
+
+
+def test_periodic_random_fp64_10_steps(fsei):
+    case = inputs.case_periodic_random(24, seed=3, steps=10)
+    gpu, _ = pu.run_gpu(case, 10, fsei.FSEI_FP64)
+    ref, _ = pu.run_oracle(case, 10)
+    _assert_fp64(gpu, ref)
+
+
+def test_mixed_channel_100_steps_against_fp64_oracle(fsei):
+    """Mixed precision (FP32 fields, FP64 near-zero Poisson modes and
+    reductions) stays within 1e-5 of the FP64 oracle in velocity after 100
+    steps of a 64^3 stretched channel."""
+    case = inputs.case_channel(64, 64, 64, steps=100, seed=2)
+    gpu, _ = pu.run_gpu(case, 100, fsei.FSEI_MIXED)
+    ref, _ = pu.run_oracle(case, 100)
+    vel = np.sqrt(sum(np.linalg.norm(gpu[k] - ref[k]) ** 2 for k in "uvw")
+                  / sum(np.linalg.norm(ref[k]) ** 2 for k in "uvw"))
+    assert vel <= 1e-5, (vel, pu.compare(gpu, ref))
+
+
+def test_full_size_channel_fp64_two_steps(fsei):
+    """256^3 stretched channel (the mixed-vs-FP64 workload) at full size:
+    two FP64 steps against the oracle."""
+    case = inputs.case_channel(256, 256, 256, steps=2)
+    gpu, st = pu.run_gpu(case, 2, fsei.FSEI_FP64)
+    ref, rst = pu.run_oracle(case, 2)
+    _assert_fp64(gpu, ref)
+    assert st["max_div"] < 1e-9
