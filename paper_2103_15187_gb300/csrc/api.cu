@@ -240,6 +240,12 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
         upload(dlxd, lamx);
         upload(dlyd, lamy);
         upload(dm, nzm);
+        std::vector<unsigned char> flag((size_t)g.sk * g.ny, 0);
+        for (int code : nzm) flag[code] = 1;
+        unsigned char *dflag = M.get<unsigned char>(flag.size());
+        if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "table allocation failed");
+        upload(dflag, flag);
+        W.exact = dflag;
         W.lamx = dlx; W.lamy = dly; W.lamx_d = dlxd; W.lamy_d = dlyd;
         W.nzm = dm;
         W.n_nzm = (int)nzm.size();

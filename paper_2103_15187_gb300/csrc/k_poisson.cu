@@ -105,7 +105,8 @@ template <typename T> struct PoissonMat {
 template <typename T>
 __global__ void __launch_bounds__(512)
 k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
-            const T *__restrict__ lamy, int tkx, int P, T scale) {
+            const T *__restrict__ lamy, const unsigned char *__restrict__ exact, int tkx, int P,
+            T scale) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int ny = g.ny, nz = g.nz, sk = g.sk;
     const int rs = 2 * P + 1;
@@ -121,8 +122,8 @@ k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
     const int ky = blockIdx.x / nkt, x0 = (blockIdx.x % nkt) * tkx;
     if (threadIdx.x < tkx) {
         T lv = lamx[x0 + threadIdx.x] + lamy[ky];
-        // the singular (0, 0) mode is solved exactly afterwards; keep this
-        // copy of its system regular
+        // the singular (0, 0) mode is solved by k_poisson_exact; keep this
+        // (discarded) copy of its system regular
         if (x0 + threadIdx.x == 0 && ky == 0) lv = T(1);
         lam[threadIdx.x] = lv;
     }
@@ -135,9 +136,12 @@ k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
     __syncthreads();
     PoissonMat<T> M{Metric<T>::idz(g), Metric<T>::ihc(g), lam, nz, g.walls};
     tri_fly_solve<T>(D, tkx, 1, fa, fc, tkx, 1, tkx, nz, P, !g.walls, M, rr, rlo, rdi, rup, rs);
+    // modes solved exactly in double (k_poisson_exact, launched before this
+    // kernel) keep their values
+    const unsigned char *ex = exact + (size_t)ky * sk + x0;
     for (int e = threadIdx.x; e < nz * tkx; e += blockDim.x) {
         const int k = e / tkx, l = e - k * tkx;
-        base[(size_t)k * plane + l] = scale * D[e];
+        if (!ex[l]) base[(size_t)k * plane + l] = scale * D[e];
     }
 }
 
@@ -297,10 +301,11 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
     const int blocks = g.ny * (g.sk / W.tkx);
     const int threads = ((W.tkx * W.pz_poisson + 31) / 32) * 32;
     const double scale = 1.0 / ((double)g.nx * g.ny);
-    k_poisson_z<T><<<blocks, threads, smem_poisson(g, W), st>>>(g, W.spec, W.lamx, W.lamy, W.tkx,
-                                                                W.pz_poisson, T(scale));
+    // exact modes first: they read the untouched right-hand side
     k_poisson_exact<T><<<(W.n_nzm + 31) / 32, 32, 0, st>>>(g, W.spec, W.nzm, W.n_nzm, W.lamx_d,
                                                            W.lamy_d, W.nz_scratch, scale);
+    k_poisson_z<T><<<blocks, threads, smem_poisson(g, W), st>>>(
+        g, W.spec, W.lamx, W.lamy, W.exact, W.tkx, W.pz_poisson, T(scale));
 }
 
 template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {

@@ -26,6 +26,7 @@ template <typename T> struct Work {
     const double *lamx_d, *lamy_d;
     const int *nzm;          // near-zero modes to solve in double: kx + sk*ky
     int n_nzm;
+    const unsigned char *exact;   // [ny][sk]: 1 for the modes in nzm
     double *nz_scratch;      // 2 * nz doubles per near-zero mode
     int ry;                  // rows per block of the x-line kernels
     int tx;                  // x columns per block of the y/z sweeps

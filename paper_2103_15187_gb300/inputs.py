@@ -192,6 +192,8 @@ def gaussian_blobs(rng, nx, ny, nz, nblobs=20, sigma=8.0, amp=10.0,
     fz = np.zeros((nz, ny, nx))
     lo = 3.0 * sigma if zbc == Z_WALLS else 0.0
     hi = nz - 3.0 * sigma if zbc == Z_WALLS else float(nz)
+    if hi < lo:                      # box thinner than 6 sigma: centre plane
+        lo = hi = 0.5 * nz
     r = int(np.ceil(cut * sigma))
     for _ in range(nblobs):
         c = np.array([rng.uniform(0, nx), rng.uniform(0, ny),

@@ -86,6 +86,24 @@ def _assert_fp64(gpu, ref, tol=FP64_TOL):
     assert not bad, errs
 
 
+@pytest.mark.parametrize("zbc", [Z_WALLS, Z_PERIODIC])
+def test_forced_rest_state_fp64_one_step(fsei, zbc):
+    """Fluid at rest driven by a random body force: no advection, so one step
+    exercises the sweeps, the Poisson solve and the projection alone."""
+    from paper_2103_15187_gb300.inputs import Case
+    nx, ny, nz = 24, 12, 18
+    rng = np.random.default_rng(11)
+    z = np.zeros((nz, ny, nx))
+    f = tuple(rng.standard_normal((nz, ny, nx)) for _ in range(3))
+    if zbc == Z_WALLS:
+        f[2][0] = 0.0
+    case = Case("rest", nx, ny, nz, 2.0, 1.0, zbc, 1.5, 2.0, 50.0, 1e-2, 0.0, 1,
+                z, z.copy(), z.copy(), z.copy(), f)
+    gpu, _ = pu.run_gpu(case, 1, fsei.FSEI_FP64)
+    ref, _ = pu.run_oracle(case, 1)
+    _assert_fp64(gpu, ref)
+
+
 def test_taylor_green_fp64_10_steps(fsei):
     """32^3 triply periodic Taylor-Green, Re 100, dt 1e-3, 10 steps."""
     case = inputs.case_taylor_green(32, steps=10)
