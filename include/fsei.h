@@ -160,6 +160,38 @@ fsei_status fsei_step(fsei_grid grid, fsei_state *state, const void *fx,
 fsei_status fsei_poisson_solve(fsei_grid grid, const void *rhs, void *phi,
                                void *cuda_stream);
 
+/* Size in bytes of the device array that backs fsei_poisson_solve_noalloc. */
+#define FSEI_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Allocation-free Poisson solve.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * a solve -- a host application that owns every allocation and hands the
+ * library raw pointers only, code whose device memory is already fully
+ * reserved by a caching allocator, or loops that must not pay the implicit
+ * synchronisation of cudaMalloc/cudaFree.  It computes the same phi as
+ * fsei_poisson_solve for a grid described by desc, without a grid handle:
+ * all scratch (metrics, twiddles, wavenumber tables, spectrum) lives in one
+ * file-scope device array of FSEI_NOALLOC_SCRATCH_BYTES (32 MiB) that every
+ * GPU loading the library holds until the process exits.  It calls no
+ * cudaMalloc/cudaFree and no allocating routine, on the device or the host.
+ *   desc: as for fsei_grid_create (zfaces read during the call only);
+ *   rhs, phi: device fields [nz][ny][nx] of the precision's element type,
+ *   16-byte aligned, caller-owned; rhs with zero volume-weighted mean.
+ * Returns FSEI_E_SHAPE when the extents are unsupported or the grid needs
+ * more scratch than the array holds (e.g. FP64 up to about 128^3 cells),
+ * FSEI_E_ARG for bad arguments, FSEI_E_CUDA if a CUDA call fails.  It does
+ * not set fsei_last_error().  The first call on a device (made with that
+ * device current) looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the array, which keeps the
+ * last call's contents (the spectrum is cleared on every call); calls whose
+ * GPU work overlaps -- on different streams or from different host
+ * threads -- race on it and must be serialised by the caller.  The tables
+ * are copied from host memory on the given stream, which makes the call wait
+ * for work already queued on that stream. */
+fsei_status fsei_poisson_solve_noalloc(const fsei_grid_desc *desc,
+                                       const void *rhs, void *phi,
+                                       void *cuda_stream);
+
 /* Per-kernel timing, for measurement tools.  While enabled, fsei_step and
  * fsei_poisson_solve record a CUDA event pair on the call's stream around
  * every kernel they launch.  fsei_kernel_times synchronises the device,
