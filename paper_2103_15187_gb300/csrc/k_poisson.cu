@@ -145,43 +145,37 @@ k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
     }
 }
 
-// Thomas' algorithm in double on one z line of the spectrum (one thread).
-// Rows lo..nz-1 are solved; with pin0 the unknown at k = 0 is fixed to 0.
-// cyc: periodic line solved with Sherman-Morrison.  cp, yr, yi, zz: scratch
-// of nz doubles.
-template <typename T>
-__device__ void exact_line(const GridDev &g, cplx<T> *line, size_t stride, double lam,
-                           bool pin0, double scale, double *cp, double *yr, double *yi,
-                           double *zz) {
+// Thomas' algorithm in double on one z line held in shared memory (one
+// thread).  With pin0 the unknown at k = 0 is fixed to 0 and rows 1..nz-1
+// are solved; a periodic line without pin0 is solved with Sherman-Morrison.
+// yr, yi: the right-hand side on entry, the solution on exit; cp, zz:
+// scratch of nz doubles.
+FSEI_D void exact_line(const GridDev &g, double lam, bool pin0, double *yr, double *yi,
+                       double *cp, double *zz) {
     const int nz = g.nz;
     const bool walls = g.walls != 0;
     const int k0 = pin0 ? 1 : 0;
     const bool cyc = !walls && !pin0;
     auto A = [&](int k) { return (walls && k == 0) ? 0.0 : g.ihc[k] * g.idz[k]; };
     auto C = [&](int k) { return (walls && k == nz - 1) ? 0.0 : g.ihc[k + 1] * g.idz[k]; };
-    const double gsm = cyc ? -(-(A(0) + C(0)) - lam) : 0.0;   // -b_0
+    const double gsm = cyc ? (A(0) + C(0)) + lam : 0.0;   // -b_0
     auto Bm = [&](int k) {
         double b = -(A(k) + C(k)) - lam;
         if (cyc && k == 0) b -= gsm;
         if (cyc && k == nz - 1) b -= C(nz - 1) * A(0) / gsm;
         return b;
     };
-    // forward elimination: cp = c', (yr, yi) = d', zz = Sherman-Morrison rhs
     double inv = 1.0 / Bm(k0);
     cp[k0] = C(k0) * inv;
-    {
-        const cplx<T> v = line[(size_t)k0 * stride];
-        yr[k0] = (double)v.re * inv;
-        yi[k0] = (double)v.im * inv;
-        zz[k0] = cyc ? gsm * inv : 0.0;
-    }
+    yr[k0] *= inv;
+    yi[k0] *= inv;
+    zz[k0] = cyc ? gsm * inv : 0.0;
     for (int k = k0 + 1; k < nz; ++k) {
         const double a = A(k);
         inv = 1.0 / (Bm(k) - a * cp[k - 1]);
         cp[k] = C(k) * inv;
-        const cplx<T> v = line[(size_t)k * stride];
-        yr[k] = ((double)v.re - a * yr[k - 1]) * inv;
-        yi[k] = ((double)v.im - a * yi[k - 1]) * inv;
+        yr[k] = (yr[k] - a * yr[k - 1]) * inv;
+        yi[k] = (yi[k] - a * yi[k - 1]) * inv;
         if (cyc) zz[k] = ((k == nz - 1 ? C(nz - 1) : 0.0) - a * zz[k - 1]) * inv;
     }
     for (int k = nz - 2; k >= k0; --k) {
@@ -202,36 +196,68 @@ __device__ void exact_line(const GridDev &g, cplx<T> *line, size_t stride, doubl
     if (pin0) {
         yr[0] = 0.0;
         yi[0] = 0.0;
-        // volume-weighted mean of the mode removed (gauge)
-        double sr = 0.0, si = 0.0, sw = 0.0;
-        for (int k = 0; k < nz; ++k) {
-            sr += yr[k] * g.dz[k];
-            si += yi[k] * g.dz[k];
-            sw += g.dz[k];
-        }
-        sr /= sw;
-        si /= sw;
-        for (int k = 0; k < nz; ++k) {
-            yr[k] -= sr;
-            yi[k] -= si;
-        }
     }
-    for (int k = 0; k < nz; ++k)
-        line[(size_t)k * stride] = cplx<T>{T(yr[k] * scale), T(yi[k] * scale)};
 }
 
+// One block per exactly solved mode: the z line is staged in shared memory
+// (double), solved by one thread, written back scaled by 1/(nx ny).  For the
+// (0, 0) mode the volume-weighted mean is removed afterwards (gauge); with
+// compat the right-hand side of that mode first loses its own dz-weighted
+// mean (makes an arbitrary right-hand side compatible).
 template <typename T>
-__global__ void k_poisson_exact(GridDev g, cplx<T> *spec, const int *modes, int nmodes,
-                                const double *lamx, const double *lamy, double *scratch,
-                                double scale) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= nmodes) return;
-    const int code = modes[m];
+__global__ void __launch_bounds__(128)
+k_poisson_exact(GridDev g, cplx<T> *spec, const int *modes, const double *lamx,
+                const double *lamy, double scale, int compat) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nz = g.nz;
+    double *yr = reinterpret_cast<double *>(smraw);
+    double *yi = yr + nz, *cp = yi + nz, *zz = cp + nz;
+    __shared__ double red[2][128];
+    const int code = modes[blockIdx.x];
     const int kx = code % g.sk, ky = code / g.sk;
+    const bool zero_mode = kx == 0 && ky == 0;
     const size_t stride = (size_t)g.ny * g.sk;
-    double *s = scratch + (size_t)m * 4 * g.nz;
-    exact_line<T>(g, spec + (size_t)ky * g.sk + kx, stride, lamx[kx] + lamy[ky],
-                  kx == 0 && ky == 0, scale, s, s + g.nz, s + 2 * g.nz, s + 3 * g.nz);
+    cplx<T> *line = spec + (size_t)ky * g.sk + kx;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        const cplx<T> v = line[(size_t)k * stride];
+        yr[k] = (double)v.re;
+        yi[k] = (double)v.im;
+    }
+    __syncthreads();
+    // dz-weighted means of the line (before: compat; after: gauge)
+    auto wmean = [&](double &mr, double &mi) {
+        double sr = 0.0, si = 0.0;
+        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+            sr += yr[k] * g.dz[k];
+            si += yi[k] * g.dz[k];
+        }
+        red[0][threadIdx.x] = sr;
+        red[1][threadIdx.x] = si;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0, w = 0.0;
+            for (int t = 0; t < (int)blockDim.x; ++t) { a += red[0][t]; b += red[1][t]; }
+            for (int k = 0; k < nz; ++k) w += g.dz[k];
+            red[0][0] = a / w;
+            red[1][0] = b / w;
+        }
+        __syncthreads();
+        mr = red[0][0];
+        mi = red[1][0];
+        __syncthreads();
+    };
+    if (zero_mode && compat) {
+        double mr, mi;
+        wmean(mr, mi);
+        for (int k = threadIdx.x; k < nz; k += blockDim.x) { yr[k] -= mr; yi[k] -= mi; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) exact_line(g, lamx[kx] + lamy[ky], zero_mode, yr, yi, cp, zz);
+    __syncthreads();
+    double mr = 0.0, mi = 0.0;
+    if (zero_mode) wmean(mr, mi);
+    for (int k = threadIdx.x; k < nz; k += blockDim.x)
+        line[(size_t)k * stride] = cplx<T>{T((yr[k] - mr) * scale), T((yi[k] - mi) * scale)};
 }
 
 template <typename T>
@@ -302,8 +328,8 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
     const int threads = ((W.tkx * W.pz_poisson + 31) / 32) * 32;
     const double scale = 1.0 / ((double)g.nx * g.ny);
     // exact modes first: they read the untouched right-hand side
-    k_poisson_exact<T><<<(W.n_nzm + 31) / 32, 32, 0, st>>>(g, W.spec, W.nzm, W.n_nzm, W.lamx_d,
-                                                           W.lamy_d, W.nz_scratch, scale);
+    k_poisson_exact<T><<<W.n_nzm, 128, 4 * sizeof(double) * g.nz, st>>>(
+        g, W.spec, W.nzm, W.lamx_d, W.lamy_d, scale, 0);
     k_poisson_z<T><<<blocks, threads, smem_poisson(g, W), st>>>(
         g, W.spec, W.lamx, W.lamy, W.exact, W.tkx, W.pz_poisson, T(scale));
 }
@@ -327,6 +353,8 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
                          (int)smem_fft_y(g, W));
     cudaFuncSetAttribute(k_poisson_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_poisson(g, W));
+    cudaFuncSetAttribute(k_poisson_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(4 * sizeof(double) * g.nz));
 }
 
 #define FSEI_INST(T)                                                                           \

@@ -1,9 +1,11 @@
 // Projection and pressure update of the fractional step (Sec. 2.1): with the
 // pressure increment phi from the Poisson solve,
 //     u^{n+1} = u* - dt G phi,   p^{n+1} = p^n + phi - beta (D G) phi,
-// beta = dt / (2 Re).  Fused double-precision reductions of the new state:
-// max |D u^{n+1}|, kinetic energy, and max |u_c|/dx + |v_c|/dy + |w_c|/dz_k
-// (the CFL speed that sets the next step's dt).
+// beta = dt / (2 Re).  Fused reductions of the new state: max |D u^{n+1}|,
+// kinetic energy, and max |u_c|/dx + |v_c|/dy + |w_c|/dz_k (the CFL speed
+// that sets the next step's dt).  Per-cell statistics are evaluated in the
+// field precision; the grid-wide accumulation (per-warp partials onwards)
+// is in double.
 #include "kernels.cuh"
 
 namespace fsei {
@@ -14,91 +16,95 @@ FSEI_D size_t fid(int i, int j, int k, int nx, int ny) {
     return ((size_t)k * ny + j) * nx + i;
 }
 
+// One block per (j, k) row group: blockIdx.x = k * (ny / rows) + row tile,
+// threads stride over x.  No integer division per element.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_project(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict__ q1,
-          const T *__restrict__ q2, const T *__restrict__ phi, StepScalars *sc) {
+          const T *__restrict__ q2, const T *__restrict__ phi, StepScalars *sc, int rows) {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const size_t ncell = (size_t)nx * ny * nz;
+    const int nbj = ny / rows;
+    const int k = blockIdx.x / nbj, j0 = (blockIdx.x % nbj) * rows;
     const T dt = T(sc->dt), beta = T(sc->beta);
     const T idx = T(g.idx), idy = T(g.idy), idx2 = T(g.idx2), idy2 = T(g.idy2);
     const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
-    const double vxy = g.dx * g.dy;
-    double mdiv = 0.0, mspd = 0.0, ke = 0.0;
+    const bool hasdn = !g.walls || k > 0, hasup = !g.walls || k < nz - 1;
+    const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
+    const T ihck = ihc[k], ihcu = ihc[k + 1], idzk = idz[k];
+    const T vxy = T(g.dx * g.dy);
+    const T vu = vxy * Metric<T>::dz(g)[k];
+    const T vw = hasdn ? vxy / ihck : T(0);
+    T mdiv = T(0), mspd = T(0);
+    double ke = 0.0;
     int flags = 0;
-    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < ncell;
-         c += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c % nx);
-        const int j = (int)((c / nx) % ny);
-        const int k = (int)(c / ((size_t)nx * ny));
-        const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+    for (int r = 0; r < rows; ++r) {
+        const int j = j0 + r;
         const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
-        const bool hasdn = !g.walls || k > 0, hasup = !g.walls || k < nz - 1;
-        const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
-        const T f0 = phi[c];
-        const T fim = phi[fid(im, j, k, nx, ny)], fip = phi[fid(ip, j, k, nx, ny)];
-        const T fjm = phi[fid(i, jm, k, nx, ny)], fjp = phi[fid(i, jp, k, nx, ny)];
-        const T fkd = hasdn ? phi[fid(i, j, kd, nx, ny)] : T(0);
-        const T fku = hasup ? phi[fid(i, j, ku, nx, ny)] : T(0);
-        const T ihck = ihc[k], ihcu = ihc[k + 1], idzk = idz[k];
-        const T un = q0[c] - dt * (f0 - fim) * idx;
-        const T vn = q1[c] - dt * (f0 - fjm) * idy;
-        const T wn = hasdn ? q2[c] - dt * (f0 - fkd) * ihck : T(0);
-        const T fup = hasup ? (fku - f0) * ihcu : T(0);
-        const T fdn = hasdn ? (f0 - fkd) * ihck : T(0);
-        const T lphi = (fip - T(2) * f0 + fim) * idx2 + (fjp - T(2) * f0 + fjm) * idy2 +
-                       (fup - fdn) * idzk;
-        const T pn = F.p[c] + f0 - beta * lphi;
-        F.u[c] = un;
-        F.v[c] = vn;
-        F.w[c] = wn;
-        F.p[c] = pn;
-        // neighbours of the new state needed by the cell-centre statistics
-        const T uip = q0[fid(ip, j, k, nx, ny)] - dt * (fip - f0) * idx;
-        const T vjp = q1[fid(i, jp, k, nx, ny)] - dt * (fjp - f0) * idy;
-        const T wku = hasup ? q2[fid(i, j, ku, nx, ny)] - dt * (fku - f0) * ihcu : T(0);
-        const double di = ((double)uip - (double)un) * g.idx + ((double)vjp - (double)vn) * g.idy +
-                          ((double)wku - (double)wn) * g.idz[k];
-        mdiv = fmax(mdiv, fabs(di));
-        const double sp = fabs(0.5 * ((double)un + (double)uip)) * g.idx +
-                          fabs(0.5 * ((double)vn + (double)vjp)) * g.idy +
-                          fabs(0.5 * ((double)wn + (double)wku)) * g.idz[k];
-        mspd = fmax(mspd, sp);
-        const double hck = hasdn ? 1.0 / g.ihc[k] : 0.0;
-        ke += 0.5 * vxy * (((double)un * un + (double)vn * vn) * g.dz[k] + (double)wn * wn * hck);
-        if (!isfinite(un) || !isfinite(vn) || !isfinite(wn) || !isfinite(pn)) flags |= 1;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+            const size_t c = fid(i, j, k, nx, ny);
+            const T f0 = phi[c];
+            const T fim = phi[fid(im, j, k, nx, ny)], fip = phi[fid(ip, j, k, nx, ny)];
+            const T fjm = phi[fid(i, jm, k, nx, ny)], fjp = phi[fid(i, jp, k, nx, ny)];
+            const T fkd = hasdn ? phi[fid(i, j, kd, nx, ny)] : T(0);
+            const T fku = hasup ? phi[fid(i, j, ku, nx, ny)] : T(0);
+            const T un = q0[c] - dt * (f0 - fim) * idx;
+            const T vn = q1[c] - dt * (f0 - fjm) * idy;
+            const T wn = hasdn ? q2[c] - dt * (f0 - fkd) * ihck : T(0);
+            const T fup = hasup ? (fku - f0) * ihcu : T(0);
+            const T fdn = hasdn ? (f0 - fkd) * ihck : T(0);
+            const T lphi = (fip - T(2) * f0 + fim) * idx2 + (fjp - T(2) * f0 + fjm) * idy2 +
+                           (fup - fdn) * idzk;
+            const T pn = F.p[c] + f0 - beta * lphi;
+            F.u[c] = un;
+            F.v[c] = vn;
+            F.w[c] = wn;
+            F.p[c] = pn;
+            // neighbours of the new state needed by the cell-centre statistics
+            const T uip = q0[fid(ip, j, k, nx, ny)] - dt * (fip - f0) * idx;
+            const T vjp = q1[fid(i, jp, k, nx, ny)] - dt * (fjp - f0) * idy;
+            const T wku = hasup ? q2[fid(i, j, ku, nx, ny)] - dt * (fku - f0) * ihcu : T(0);
+            const T di = (uip - un) * idx + (vjp - vn) * idy + (wku - wn) * idzk;
+            mdiv = fmax(mdiv, fabs(di));
+            const T sp = fabs(T(0.5) * (un + uip)) * idx + fabs(T(0.5) * (vn + vjp)) * idy +
+                         fabs(T(0.5) * (wn + wku)) * idzk;
+            mspd = fmax(mspd, sp);
+            ke += (double)(T(0.5) * ((un * un + vn * vn) * vu + wn * wn * vw));
+            if (!isfinite(un) || !isfinite(vn) || !isfinite(wn) || !isfinite(pn)) flags |= 1;
+        }
     }
+    double dmdiv = (double)mdiv, dmspd = (double)mspd;
     __shared__ double sdiv[32], sspd[32], ske[32];
     __shared__ int sfl[32];
     for (int o = 16; o > 0; o >>= 1) {
-        mdiv = fmax(mdiv, __shfl_down_sync(0xffffffffu, mdiv, o));
-        mspd = fmax(mspd, __shfl_down_sync(0xffffffffu, mspd, o));
+        dmdiv = fmax(dmdiv, __shfl_down_sync(0xffffffffu, dmdiv, o));
+        dmspd = fmax(dmspd, __shfl_down_sync(0xffffffffu, dmspd, o));
         ke += __shfl_down_sync(0xffffffffu, ke, o);
         flags |= __shfl_down_sync(0xffffffffu, flags, o);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-        sdiv[wid] = mdiv;
-        sspd[wid] = mspd;
+        sdiv[wid] = dmdiv;
+        sspd[wid] = dmspd;
         ske[wid] = ke;
         sfl[wid] = flags;
     }
     __syncthreads();
     if (wid == 0) {
         const int nw = (blockDim.x + 31) >> 5;
-        mdiv = lane < nw ? sdiv[lane] : 0.0;
-        mspd = lane < nw ? sspd[lane] : 0.0;
+        dmdiv = lane < nw ? sdiv[lane] : 0.0;
+        dmspd = lane < nw ? sspd[lane] : 0.0;
         ke = lane < nw ? ske[lane] : 0.0;
         flags = lane < nw ? sfl[lane] : 0;
         for (int o = 16; o > 0; o >>= 1) {
-            mdiv = fmax(mdiv, __shfl_down_sync(0xffffffffu, mdiv, o));
-            mspd = fmax(mspd, __shfl_down_sync(0xffffffffu, mspd, o));
+            dmdiv = fmax(dmdiv, __shfl_down_sync(0xffffffffu, dmdiv, o));
+            dmspd = fmax(dmspd, __shfl_down_sync(0xffffffffu, dmspd, o));
             ke += __shfl_down_sync(0xffffffffu, ke, o);
             flags |= __shfl_down_sync(0xffffffffu, flags, o);
         }
         if (lane == 0) {
-            atomicMax(&sc->maxdiv, dbits(mdiv));
-            atomicMax(&sc->speed_next, dbits(mspd));
+            atomicMax(&sc->maxdiv, dbits(dmdiv));
+            atomicMax(&sc->speed_next, dbits(dmspd));
             atomicAdd(&sc->ke, ke);
             if (flags) atomicOr(&sc->flags, flags);
         }
@@ -107,12 +113,18 @@ k_project(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict_
 
 }  // namespace
 
+int project_rows(const GridDev &g) {
+    for (int r = 8; r >= 1; r /= 2)
+        if (g.ny % r == 0) return r;
+    return 1;
+}
+
 template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                           StepScalars *sc, cudaStream_t st) {
-    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
-    int blocks = (int)((ncell + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_project<T><<<blocks, 256, 0, st>>>(g, F, W.q0, W.q1, W.q2, W.phi, sc);
+    const int rows = project_rows(g);
+    const int threads = g.nx >= 256 ? 256 : ((g.nx + 31) / 32) * 32;
+    k_project<T><<<g.nz * (g.ny / rows), threads, 0, st>>>(g, F, W.q0, W.q1, W.q2, W.phi, sc,
+                                                           rows);
 }
 
 template void launch_project<float>(const GridDev &, const Fields<float> &, Work<float> &,

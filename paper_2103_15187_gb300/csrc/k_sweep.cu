@@ -39,29 +39,33 @@ __device__ double block_max(double v) {
     return v;
 }
 
+// one block per group of rows (no integer division per element); per-cell
+// speed in the field precision, the grid-wide maximum in double
 template <typename T>
-__global__ void k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
-                        const T *__restrict__ w, StepScalars *sc) {
+__global__ void __launch_bounds__(256)
+k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v, const T *__restrict__ w,
+        StepScalars *sc, int rows) {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const size_t ncell = (size_t)nx * ny * nz;
-    double m = 0.0;
-    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < ncell;
-         c += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c % nx);
-        const int j = (int)((c / nx) % ny);
-        const int k = (int)(c / ((size_t)nx * ny));
-        const int ip = i == nx - 1 ? 0 : i + 1, jp = j == ny - 1 ? 0 : j + 1;
-        const bool hasup = !g.walls || k < nz - 1;
-        const int ku = k == nz - 1 ? 0 : k + 1;
-        const double uc = 0.5 * ((double)u[c] + (double)u[fid(ip, j, k, nx, ny)]);
-        const double vc = 0.5 * ((double)v[c] + (double)v[fid(i, jp, k, nx, ny)]);
-        const double wku = hasup ? (double)w[fid(i, j, ku, nx, ny)] : 0.0;
-        const double wc = 0.5 * ((double)w[c] + wku);
-        const double s = fabs(uc) * g.idx + fabs(vc) * g.idy + fabs(wc) * g.idz[k];
-        m = fmax(m, s);
+    const int nbj = ny / rows;
+    const int k = blockIdx.x / nbj, j0 = (blockIdx.x % nbj) * rows;
+    const bool hasup = !g.walls || k < nz - 1;
+    const int ku = k == nz - 1 ? 0 : k + 1;
+    const T idx = T(g.idx), idy = T(g.idy), idzk = Metric<T>::idz(g)[k];
+    T m = T(0);
+    for (int r = 0; r < rows; ++r) {
+        const int j = j0 + r, jp = j == ny - 1 ? 0 : j + 1;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int ip = i == nx - 1 ? 0 : i + 1;
+            const size_t c = fid(i, j, k, nx, ny);
+            const T uc = T(0.5) * (u[c] + u[fid(ip, j, k, nx, ny)]);
+            const T vc = T(0.5) * (v[c] + v[fid(i, jp, k, nx, ny)]);
+            const T wku = hasup ? w[fid(i, j, ku, nx, ny)] : T(0);
+            const T wc = T(0.5) * (w[c] + wku);
+            m = fmax(m, fabs(uc) * idx + fabs(vc) * idy + fabs(wc) * idzk);
+        }
     }
-    m = block_max<T>(m);
-    if (threadIdx.x == 0) atomicMax(&sc->speed_next, dbits(m));
+    const double mm = block_max<T>((double)m);
+    if (threadIdx.x == 0) atomicMax(&sc->speed_next, dbits(mm));
 }
 
 __global__ void k_scalars(StepScalars *sc, StepArgs a, int euler) {
@@ -210,6 +214,7 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
     const int nl = 3 * ry, es = nl | 1;
     T *red = sd + (size_t)nx * es;
     const int rs = 2 * px.P + 1;
+    const TriPlan<T> pxs = stage_plan(px, red + (size_t)nl * rs);
     const int nby = ny / ry;
     const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * ry;
     const T dt = T(sc->dt), gam = T(sc->gamma), rho = T(sc->rho);
@@ -300,7 +305,7 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
         sd[i * es + 2 * ry + r] = rw;
     }
     __syncthreads();
-    tri_plan_solve<T, T>(sd, es, 1, nl, px, red, rs);
+    tri_plan_solve<T, T>(sd, es, 1, nl, pxs, red, rs);
     for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
         const int r = e / nx, i = e - r * nx;
         const size_t c0 = fid(i, j0 + r, k, nx, ny);
@@ -319,6 +324,7 @@ k_sweep_y(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     T *red = sd + (size_t)ny * tx;
     const int rs = 2 * py.P + 1;
+    const TriPlan<T> pys = stage_plan(py, red + (size_t)tx * rs);
     const int nxt = (nx + tx - 1) / tx;
     int b = blockIdx.x;
     const int xt = b % nxt; b /= nxt;
@@ -331,7 +337,7 @@ k_sweep_y(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
         sd[e] = (x0 + l < nx) ? q[fid(x0 + l, j, k, nx, ny)] : T(0);
     }
     __syncthreads();
-    tri_plan_solve<T, T>(sd, tx, 1, tx, py, red, rs);
+    tri_plan_solve<T, T>(sd, tx, 1, tx, pys, red, rs);
     for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
         const int j = e / tx, l = e - j * tx;
         if (x0 + l < nx) q[fid(x0 + l, j, k, nx, ny)] = sd[e];
@@ -353,7 +359,8 @@ k_sweep_z(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__r
     const int comp = b / ny;
     T *q = comp == 0 ? q0 : (comp == 1 ? q1 : q2);
     const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
-    const TriPlan<T> &pl = comp < 2 ? pzc : pzf;
+    const int Pmax = pzc.P > pzf.P ? pzc.P : pzf.P;
+    const TriPlan<T> pl = stage_plan(comp < 2 ? pzc : pzf, red + (size_t)tx * (2 * Pmax + 1));
     const int rs = 2 * pl.P + 1;
     const int x0 = xt * tx;
     for (int e = threadIdx.x; e < nz * tx; e += blockDim.x) {
@@ -376,18 +383,20 @@ k_sweep_z(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__r
 // ------------------------------------------------------------- launchers --
 template <typename T> size_t smem_rhs_x(const GridDev &g, const Work<T> &W) {
     const int nl = 3 * W.ry, es = nl | 1;
-    return sizeof(T) * ((size_t)g.nx * es + (size_t)nl * (2 * W.plan[0].P + 1));
+    return sizeof(T) * ((size_t)g.nx * es + (size_t)nl * (2 * W.plan[0].P + 1) +
+                        plan_stage_words(W.plan[0].n, W.plan[0].P));
 }
 template <typename T> size_t smem_sweep(int n, const Work<T> &W, int P) {
-    return sizeof(T) * ((size_t)n * W.tx + (size_t)W.tx * (2 * P + 1));
+    return sizeof(T) * ((size_t)n * W.tx + (size_t)W.tx * (2 * P + 1) + plan_stage_words(n, P));
 }
 
 template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v, const T *w,
                                         StepScalars *sc, cudaStream_t st) {
-    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
-    int blocks = (int)((ncell + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_speed<T><<<blocks, 256, 0, st>>>(g, u, v, w, sc);
+    int rows = 1;
+    for (int r = 8; r >= 1; r /= 2)
+        if (g.ny % r == 0) { rows = r; break; }
+    const int threads = g.nx >= 256 ? 256 : ((g.nx + 31) / 32) * 32;
+    k_speed<T><<<g.nz * (g.ny / rows), threads, 0, st>>>(g, u, v, w, sc, rows);
 }
 
 template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepScalars *sc,

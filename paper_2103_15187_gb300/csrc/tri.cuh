@@ -31,6 +31,38 @@ template <typename T> FSEI_D cplx<T> scl(T a, cplx<T> x) { return {a * x.re, a *
 template <typename T> FSEI_D T addv(T a, T b) { return a + b; }
 template <typename T> FSEI_D cplx<T> addv(cplx<T> a, cplx<T> b) { return a + b; }
 
+// Shared-memory words needed by stage_plan for a plan of n unknowns and P
+// chunks.
+FSEI_HD int plan_stage_words(int n, int P) { return 5 * n + 8 * P + 2; }
+
+// Copy a plan's factors into shared memory (every thread of the block calls
+// it; ends with a barrier) and return a plan that points there.
+template <typename T>
+__device__ TriPlan<T> stage_plan(const TriPlan<T> &in, T *sm) {
+    const int n = in.n, m = 2 * in.P;
+    TriPlan<T> out = in;
+    T *a = sm, *c = a + n, *inv = c + n, *at = inv + n, *ct = at + n;
+    T *rlo = ct + n, *rinv = rlo + m, *rcp = rinv + m, *rz = rcp + m, *rsc = rz + m;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a[i] = in.a[i];
+        c[i] = in.c[i];
+        inv[i] = in.inv[i];
+        at[i] = in.at[i];
+        ct[i] = in.ct[i];
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        rlo[i] = in.rlo[i];
+        rinv[i] = in.rinv[i];
+        rcp[i] = in.rcp[i];
+        rz[i] = in.cyclic ? in.rz[i] : T(0);
+    }
+    if (threadIdx.x < 2) rsc[threadIdx.x] = in.cyclic ? in.rsc[threadIdx.x] : T(0);
+    __syncthreads();
+    out.a = a; out.c = c; out.inv = inv; out.at = at; out.ct = ct;
+    out.rlo = rlo; out.rinv = rinv; out.rcp = rcp; out.rz = rz; out.rsc = rsc;
+    return out;
+}
+
 // Solve nl lines held in shared memory with the matrix-only factors of a
 // TriPlan (same matrix for every line).  Element i of line l lives at
 // s[(i + plan.off) * es + l * ls].  Threads t < nl * P own chunk t / nl of
