@@ -67,7 +67,7 @@ def measured_peaks():
 
 # --------------------------------------------------------------- clocks ----
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 100 ms) during the timed region."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -85,6 +85,12 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # wait for nvidia-smi's first sample, then keep only samples taken
+            # from here on (the timed region starts right after)
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:
+                time.sleep(0.02)
+            self.lines.clear()
         except Exception:
             self.proc = None
         return self
@@ -350,7 +356,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=None, help="profiling override of the extents")
+    ap.add_argument("--ny", type=int, default=None)
+    ap.add_argument("--nz", type=int, default=None)
     args = ap.parse_args()
+    for key in ("nx", "ny", "nz"):
+        if getattr(args, key):
+            WORKLOAD[key] = getattr(args, key)
     args.warmup = max(args.warmup, 3) if args.impl == "fsei" else args.warmup
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -383,8 +395,9 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "channel 256x256x256, tanh-stretched walls (2.0), Re 2000, "
-                               "CFL 0.5, Poiseuille + solenoidal perturbation (RMS 0.1, k 1-8)",
+        "config": {"workload": "channel %dx%dx%d, tanh-stretched walls (2.0), Re 2000, "
+                               "CFL 0.5, Poiseuille + solenoidal perturbation (RMS 0.1, k 1-8)"
+                               % (nx, ny, nz),
                    "cells": nx * ny * nz, "precision": "mixed (FP32 fields; FP64 near-zero "
                    "Poisson modes and reductions)", "parallelism": "replicas only",
                    "l2": "inputs larger than L2 (state 470 MB + workspace 420 MB per step)"},
