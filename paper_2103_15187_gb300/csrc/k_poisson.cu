@@ -145,74 +145,39 @@ k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
     }
 }
 
-// Thomas' algorithm in double on one z line held in shared memory (one
-// thread).  With pin0 the unknown at k = 0 is fixed to 0 and rows 1..nz-1
-// are solved; a periodic line without pin0 is solved with Sherman-Morrison.
-// yr, yi: the right-hand side on entry, the solution on exit; cp, zz:
-// scratch of nz doubles.
-FSEI_D void exact_line(const GridDev &g, double lam, bool pin0, double *yr, double *yi,
-                       double *cp, double *zz) {
-    const int nz = g.nz;
-    const bool walls = g.walls != 0;
-    const int k0 = pin0 ? 1 : 0;
-    const bool cyc = !walls && !pin0;
-    auto A = [&](int k) { return (walls && k == 0) ? 0.0 : g.ihc[k] * g.idz[k]; };
-    auto C = [&](int k) { return (walls && k == nz - 1) ? 0.0 : g.ihc[k + 1] * g.idz[k]; };
-    const double gsm = cyc ? (A(0) + C(0)) + lam : 0.0;   // -b_0
-    auto Bm = [&](int k) {
-        double b = -(A(k) + C(k)) - lam;
-        if (cyc && k == 0) b -= gsm;
-        if (cyc && k == nz - 1) b -= C(nz - 1) * A(0) / gsm;
-        return b;
-    };
-    double inv = 1.0 / Bm(k0);
-    cp[k0] = C(k0) * inv;
-    yr[k0] *= inv;
-    yi[k0] *= inv;
-    zz[k0] = cyc ? gsm * inv : 0.0;
-    for (int k = k0 + 1; k < nz; ++k) {
-        const double a = A(k);
-        inv = 1.0 / (Bm(k) - a * cp[k - 1]);
-        cp[k] = C(k) * inv;
-        yr[k] = (yr[k] - a * yr[k - 1]) * inv;
-        yi[k] = (yi[k] - a * yi[k - 1]) * inv;
-        if (cyc) zz[k] = ((k == nz - 1 ? C(nz - 1) : 0.0) - a * zz[k - 1]) * inv;
-    }
-    for (int k = nz - 2; k >= k0; --k) {
-        yr[k] -= cp[k] * yr[k + 1];
-        yi[k] -= cp[k] * yi[k + 1];
-        if (cyc) zz[k] -= cp[k] * zz[k + 1];
-    }
-    if (cyc) {
-        const double vl = A(0) / gsm;
-        const double fac = 1.0 / (1.0 + zz[0] + vl * zz[nz - 1]);
-        const double fr = (yr[0] + vl * yr[nz - 1]) * fac;
-        const double fi = (yi[0] + vl * yi[nz - 1]) * fac;
-        for (int k = 0; k < nz; ++k) {
-            yr[k] -= fr * zz[k];
-            yi[k] -= fi * zz[k];
-        }
-    }
-    if (pin0) {
-        yr[0] = 0.0;
-        yi[0] = 0.0;
-    }
-}
+// z operator of one exactly solved mode in double: rows k = i + shift of the
+// line (shift 1 for the pinned (0, 0) mode, whose unknown at k = 0 is fixed
+// to 0; its neighbours at k = 0 and, with periodic z, k = nz are then
+// Dirichlet zeros and drop out of the first and last rows).
+struct ExactMat {
+    const double *idz, *ihc;
+    double lam;
+    int nz, walls, shift;
+    FSEI_D double acut(int k) const { return (walls && k == 0) ? 0.0 : ihc[k] * idz[k]; }
+    FSEI_D double ccut(int k) const { return (walls && k == nz - 1) ? 0.0 : ihc[k + 1] * idz[k]; }
+    FSEI_D double a(int i) const { return acut(i + shift); }
+    FSEI_D double c(int i) const { return ccut(i + shift); }
+    FSEI_D double b(int, int i) const { return -(acut(i + shift) + ccut(i + shift)) - lam; }
+};
 
 // One block per exactly solved mode: the z line is staged in shared memory
-// (double), solved by one thread, written back scaled by 1/(nx ny).  For the
-// (0, 0) mode the volume-weighted mean is removed afterwards (gauge); with
-// compat the right-hand side of that mode first loses its own dz-weighted
-// mean (makes an arbitrary right-hand side compatible).
+// in double and solved with the partitioned elimination of tri.cuh (chunks
+// in parallel, reduced system on one thread), then written back scaled by
+// 1/(nx ny).  For the (0, 0) mode the volume-weighted mean is removed
+// afterwards (gauge); with compat its right-hand side first loses its own
+// dz-weighted mean (makes an arbitrary right-hand side compatible).
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(64)
 k_poisson_exact(GridDev g, cplx<T> *spec, const int *modes, const double *lamx,
-                const double *lamy, double scale, int compat) {
+                const double *lamy, double scale, int compat, int P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nz = g.nz;
-    double *yr = reinterpret_cast<double *>(smraw);
-    double *yi = yr + nz, *cp = yi + nz, *zz = cp + nz;
-    __shared__ double red[2][128];
+    const int rs = 2 * P + 1;
+    cplx<double> *D = reinterpret_cast<cplx<double> *>(smraw);
+    cplx<double> *rr = D + nz;
+    double *fa = reinterpret_cast<double *>(rr + rs);
+    double *fc = fa + nz, *rlo = fc + nz, *rdi = rlo + rs, *rup = rdi + rs;
+    __shared__ double red[2][64];
     const int code = modes[blockIdx.x];
     const int kx = code % g.sk, ky = code / g.sk;
     const bool zero_mode = kx == 0 && ky == 0;
@@ -220,16 +185,14 @@ k_poisson_exact(GridDev g, cplx<T> *spec, const int *modes, const double *lamx,
     cplx<T> *line = spec + (size_t)ky * g.sk + kx;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
         const cplx<T> v = line[(size_t)k * stride];
-        yr[k] = (double)v.re;
-        yi[k] = (double)v.im;
+        D[k] = cplx<double>{(double)v.re, (double)v.im};
     }
     __syncthreads();
-    // dz-weighted means of the line (before: compat; after: gauge)
     auto wmean = [&](double &mr, double &mi) {
         double sr = 0.0, si = 0.0;
         for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-            sr += yr[k] * g.dz[k];
-            si += yi[k] * g.dz[k];
+            sr += D[k].re * g.dz[k];
+            si += D[k].im * g.dz[k];
         }
         red[0][threadIdx.x] = sr;
         red[1][threadIdx.x] = si;
@@ -249,15 +212,33 @@ k_poisson_exact(GridDev g, cplx<T> *spec, const int *modes, const double *lamx,
     if (zero_mode && compat) {
         double mr, mi;
         wmean(mr, mi);
-        for (int k = threadIdx.x; k < nz; k += blockDim.x) { yr[k] -= mr; yi[k] -= mi; }
+        for (int k = threadIdx.x; k < nz; k += blockDim.x) { D[k].re -= mr; D[k].im -= mi; }
         __syncthreads();
     }
-    if (threadIdx.x == 0) exact_line(g, lamx[kx] + lamy[ky], zero_mode, yr, yi, cp, zz);
+    ExactMat M{g.idz, g.ihc, lamx[kx] + lamy[ky], nz, g.walls, zero_mode ? 1 : 0};
+    const int n = zero_mode ? nz - 1 : nz;
+    int Pl = P;
+    if (Pl > n / 3) Pl = n / 3;
+    if (Pl < 1) Pl = 1;
+    tri_fly_solve<double>(D + M.shift, 1, 0, fa, fc, 1, 0, 1, n, Pl, (!g.walls && !zero_mode), M,
+                          rr, rlo, rdi, rup, rs);
+    if (zero_mode && threadIdx.x == 0) D[0] = cplx<double>{0.0, 0.0};
     __syncthreads();
     double mr = 0.0, mi = 0.0;
     if (zero_mode) wmean(mr, mi);
     for (int k = threadIdx.x; k < nz; k += blockDim.x)
-        line[(size_t)k * stride] = cplx<T>{T((yr[k] - mr) * scale), T((yi[k] - mi) * scale)};
+        line[(size_t)k * stride] = cplx<T>{T((D[k].re - mr) * scale), T((D[k].im - mi) * scale)};
+}
+
+size_t smem_exact(int nz, int P) {
+    const size_t rs = 2 * P + 1;
+    return sizeof(cplx<double>) * (nz + rs) + sizeof(double) * (2 * (size_t)nz + 3 * rs);
+}
+
+int exact_chunks(int nz) {
+    int P = 64;
+    if (P > (nz - 1) / 3) P = (nz - 1) / 3;
+    return P < 1 ? 1 : P;
 }
 
 template <typename T>
@@ -328,8 +309,9 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
     const int threads = ((W.tkx * W.pz_poisson + 31) / 32) * 32;
     const double scale = 1.0 / ((double)g.nx * g.ny);
     // exact modes first: they read the untouched right-hand side
-    k_poisson_exact<T><<<W.n_nzm, 128, 4 * sizeof(double) * g.nz, st>>>(
-        g, W.spec, W.nzm, W.lamx_d, W.lamy_d, scale, 0);
+    const int Pe = exact_chunks(g.nz);
+    k_poisson_exact<T><<<W.n_nzm, 64, smem_exact(g.nz, Pe), st>>>(
+        g, W.spec, W.nzm, W.lamx_d, W.lamy_d, scale, 0, Pe);
     k_poisson_z<T><<<blocks, threads, smem_poisson(g, W), st>>>(
         g, W.spec, W.lamx, W.lamy, W.exact, W.tkx, W.pz_poisson, T(scale));
 }
@@ -354,7 +336,7 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     cudaFuncSetAttribute(k_poisson_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_poisson(g, W));
     cudaFuncSetAttribute(k_poisson_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(4 * sizeof(double) * g.nz));
+                         (int)smem_exact(g.nz, exact_chunks(g.nz)));
 }
 
 #define FSEI_INST(T)                                                                           \

@@ -5,7 +5,7 @@
 // kinetic energy, and max |u_c|/dx + |v_c|/dy + |w_c|/dz_k (the CFL speed
 // that sets the next step's dt).  Per-cell statistics are evaluated in the
 // field precision; the grid-wide accumulation (per-warp partials onwards)
-// is in double.
+// is in double (each thread sums its own few cells in the field precision).
 #include "kernels.cuh"
 
 namespace fsei {
@@ -34,8 +34,7 @@ k_project(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict_
     const T vxy = T(g.dx * g.dy);
     const T vu = vxy * Metric<T>::dz(g)[k];
     const T vw = hasdn ? vxy / ihck : T(0);
-    T mdiv = T(0), mspd = T(0);
-    double ke = 0.0;
+    T mdiv = T(0), mspd = T(0), kel = T(0);
     int flags = 0;
     for (int r = 0; r < rows; ++r) {
         const int j = j0 + r;
@@ -69,11 +68,11 @@ k_project(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict_
             const T sp = fabs(T(0.5) * (un + uip)) * idx + fabs(T(0.5) * (vn + vjp)) * idy +
                          fabs(T(0.5) * (wn + wku)) * idzk;
             mspd = fmax(mspd, sp);
-            ke += (double)(T(0.5) * ((un * un + vn * vn) * vu + wn * wn * vw));
+            kel += T(0.5) * ((un * un + vn * vn) * vu + wn * wn * vw);
             if (!isfinite(un) || !isfinite(vn) || !isfinite(wn) || !isfinite(pn)) flags |= 1;
         }
     }
-    double dmdiv = (double)mdiv, dmspd = (double)mspd;
+    double dmdiv = (double)mdiv, dmspd = (double)mspd, ke = (double)kel;
     __shared__ double sdiv[32], sspd[32], ske[32];
     __shared__ int sfl[32];
     for (int o = 16; o > 0; o >>= 1) {

@@ -72,27 +72,37 @@ template <typename T, typename V>
 __device__ void tri_plan_solve(V *s, int es, int ls, int nl, const TriPlan<T> &pl,
                                V *red, int rs) {
     const int t = threadIdx.x;
-    const int n = pl.n, P = pl.P, off = pl.off;
+    const int n = pl.n, P = pl.P;
     const bool active = t < nl * P;
     const int l = t % nl, p = t / nl;
     int s0 = 0, e0 = 0;
-    V *d = s + l * ls;
+    V *d = s + l * ls + pl.off * es;
     if (active) {
         s0 = chunk_start(p, n, P);
         e0 = chunk_start(p + 1, n, P) - 1;
         // downward elimination of the interior
-        V prev = scl(pl.inv[s0 + 1], d[(s0 + 1 + off) * es]);
-        d[(s0 + 1 + off) * es] = prev;
+        V *dp = d + (s0 + 1) * es;
+        const T *pa = pl.a + s0 + 1, *pinv = pl.inv + s0 + 1;
+        V prev = scl(*pinv, *dp);
+        *dp = prev;
         for (int i = s0 + 2; i < e0; ++i) {
-            prev = scl(pl.inv[i], nmad(pl.a[i], prev, d[(i + off) * es]));
-            d[(i + off) * es] = prev;
+            dp += es;
+            ++pa;
+            ++pinv;
+            prev = scl(*pinv, nmad(*pa, prev, *dp));
+            *dp = prev;
         }
         // upward pass: right-hand side part of x_{s+1} (through x_s, x_e)
-        V dh = d[(e0 - 1 + off) * es];
+        V dh = *dp;
         const V dhe = dh;
-        for (int i = e0 - 2; i > s0; --i) dh = nmad(pl.ct[i], dh, d[(i + off) * es]);
-        red[l * rs + 2 * p] = nmad(pl.c[s0], dh, d[(s0 + off) * es]);
-        red[l * rs + 2 * p + 1] = nmad(pl.a[e0], dhe, d[(e0 + off) * es]);
+        const T *pct = pl.ct + e0 - 2;
+        for (int i = e0 - 2; i > s0; --i) {
+            dp -= es;
+            dh = nmad(*pct, dh, *dp);
+            --pct;
+        }
+        red[l * rs + 2 * p] = nmad(pl.c[s0], dh, d[s0 * es]);
+        red[l * rs + 2 * p + 1] = nmad(pl.a[e0], dhe, d[e0 * es]);
     }
     __syncthreads();
     if (t < nl) {
@@ -116,12 +126,17 @@ __device__ void tri_plan_solve(V *s, int es, int ls, int nl, const TriPlan<T> &p
     __syncthreads();
     if (active) {
         const V F = red[l * rs + 2 * p], E = red[l * rs + 2 * p + 1];
-        d[(s0 + off) * es] = F;
-        d[(e0 + off) * es] = E;
+        d[s0 * es] = F;
+        V *dp = d + e0 * es;
+        *dp = E;
         V x = E;
+        const T *pat = pl.at + e0 - 1, *pct = pl.ct + e0 - 1;
         for (int i = e0 - 1; i > s0; --i) {
-            x = nmad(pl.ct[i], x, nmad(pl.at[i], F, d[(i + off) * es]));
-            d[(i + off) * es] = x;
+            dp -= es;
+            x = nmad(*pct, x, nmad(*pat, F, *dp));
+            *dp = x;
+            --pat;
+            --pct;
         }
     }
     __syncthreads();
