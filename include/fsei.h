@@ -160,6 +160,24 @@ fsei_status fsei_step(fsei_grid grid, fsei_state *state, const void *fx,
 fsei_status fsei_poisson_solve(fsei_grid grid, const void *rhs, void *phi,
                                void *cuda_stream);
 
+/* Discrete adjoint of one step: the exact transpose (Euclidean inner product
+ * of the stored arrays) of the step's map (u^n, p^n, H^{n-1}, f) ->
+ * (u^{n+1}, p^{n+1}, H^n) at a frozen dt (Eq. 3 with the factorisation of
+ * Sec. 3.1; the CFL maximum is not differentiable, so params->cfl must be
+ * <= 0 and params->dt the step's dt).
+ *   fwd:  the step's inputs; u, v, w read (p and H are not needed: the step
+ *         is linear in them), have_prev_h selects gamma, rho as in fsei_step.
+ *   adj:  in: cotangents of the outputs u, v, w, p (step n+1) and hu, hv, hw
+ *         (the stored H^n); out, in place: cotangents of the inputs u, v, w,
+ *         p (step n) and hu, hv, hw (H^{n-1}).
+ *   fbar_x/y/z: if not NULL, the cotangent of the body force is added.
+ * With walls the wall face w[0] is not an input: its cotangent is 0.  The
+ * first call allocates three fields of adjoint workspace.  Asynchronous. */
+fsei_status fsei_adjoint_step(fsei_grid grid, const fsei_state *fwd,
+                              const fsei_step_params *params, fsei_state *adj,
+                              void *fbar_x, void *fbar_y, void *fbar_z,
+                              void *cuda_stream);
+
 /* Size in bytes of the device array that backs fsei_poisson_solve_noalloc. */
 #define FSEI_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -253,6 +253,7 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "table allocation failed");
     set_smem_limits_sweep<T>(g, W);
     set_smem_limits_poisson<T>(g, W);
+    set_smem_limits_adjoint<T>(g, W);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FSEI_E_CUDA, "grid setup: %s", cudaGetErrorString(e));
     return FSEI_OK;
@@ -497,6 +498,55 @@ fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy
         if (out->flags & FSEI_FLAG_CFL) return fail(FSEI_E_CFL, "CFL number %g above 1", out->cfl);
     }
     return FSEI_OK;
+}
+
+fsei_status fsei_adjoint_step(fsei_grid G, const fsei_state *fwd, const fsei_step_params *prm,
+                              fsei_state *adj, void *fbar_x, void *fbar_y, void *fbar_z,
+                              void *cuda_stream) {
+    g_err.clear();
+    if (!G || !fwd || !prm || !adj) return fail(FSEI_E_ARG, "fsei_adjoint_step: NULL argument");
+    const void *fw[3] = {fwd->u, fwd->v, fwd->w};
+    for (int i = 0; i < 3; ++i)
+        if (!fw[i] || !aligned16(fw[i])) return fail(FSEI_E_ARG, "forward field %d NULL or misaligned", i);
+    const void *ad[7] = {adj->u, adj->v, adj->w, adj->p, adj->hu, adj->hv, adj->hw};
+    for (int i = 0; i < 7; ++i)
+        if (!ad[i] || !aligned16(ad[i])) return fail(FSEI_E_ARG, "cotangent field %d NULL or misaligned", i);
+    const void *fb[3] = {fbar_x, fbar_y, fbar_z};
+    for (int i = 0; i < 3; ++i)
+        if (fb[i] && !aligned16(fb[i])) return fail(FSEI_E_ARG, "fbar %d not 16-byte aligned", i);
+    if (!(prm->re > 0)) return fail(FSEI_E_ARG, "re must be > 0");
+    if (prm->cfl > 0) return fail(FSEI_E_ARG, "the adjoint needs a frozen dt: pass cfl = 0 and the dt of the forward step");
+    if (!(prm->dt > 0)) return fail(FSEI_E_ARG, "dt must be > 0");
+    StepArgs a;
+    a.re = prm->re; a.dt = prm->dt; a.cfl = 0.0; a.gamma = prm->gamma; a.rho = prm->rho;
+    for (int i = 0; i < 3; ++i) a.fconst[i] = prm->fconst[i];
+    DeviceGuard dg(G->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    auto run = [&](auto &W, auto tag) -> fsei_status {
+        using T = decltype(tag);
+        const size_t ncell = (size_t)G->g.nx * G->g.ny * G->g.nz;
+        if (!W.adj0) {
+            W.adj0 = G->mem.get<T>(ncell);
+            W.adj1 = G->mem.get<T>(ncell);
+            W.adj2 = G->mem.get<T>(ncell);
+            if (G->mem.err != cudaSuccess) {
+                W.adj0 = W.adj1 = W.adj2 = nullptr;
+                G->mem.err = cudaSuccess;
+                return fail(FSEI_E_NOMEM, "adjoint workspace allocation failed");
+            }
+        }
+        const int euler = fwd->have_prev_h ? 0 : 1;
+        KernelTimer &tm = G->timer;
+        tm.run(KK_BEGIN, st, [&] { launch_step_begin<T>(G->g, W, G->sc, a, euler, st); });
+        launch_adjoint_step<T>(G->g, W, G->sc, (const T *)fwd->u, (const T *)fwd->v,
+                               (const T *)fwd->w, (T *)adj->u, (T *)adj->v, (T *)adj->w,
+                               (T *)adj->p, (T *)adj->hu, (T *)adj->hv, (T *)adj->hw,
+                               (T *)fbar_x, (T *)fbar_y, (T *)fbar_z, prm->re, st);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(FSEI_E_CUDA, "adjoint launch: %s", cudaGetErrorString(e));
+        return FSEI_OK;
+    };
+    return G->prec == FSEI_FP64 ? run(G->wd, double(0)) : run(G->wf, float(0));
 }
 
 fsei_status fsei_poisson_solve(fsei_grid G, const void *rhs, void *phi, void *cuda_stream) {

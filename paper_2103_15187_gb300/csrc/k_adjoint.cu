@@ -1,0 +1,335 @@
+// Discrete adjoint of one fractional step (Sec. 2.1, Eq. 3; Sec. 3.1): the
+// exact transpose, in the Euclidean inner product of the stored arrays, of
+//   (u^n, p^n, H^{n-1}, f) -> (u^{n+1}, p^{n+1}, H^n)
+// at a frozen dt.  With V the cell volumes and W the z weights (dz_k at
+// z-centre points, hc_k at z-faces) the linear pieces transpose as
+//   G^T = -V D W_f^-1-form stencils written out below,
+//   (I - beta L_z)^-T = W (I - beta L_z)^-1 W^-1,  L_z^T = W L_z W^-1,
+//   (D G)^+T = V (D G)^+ V^-1 on compatible right-hand sides,
+// x and y operators being symmetric.  Kernels, in call order:
+//   k_adj_phibar   x = V^-1 phi-bar, phi-bar = -dt G^T u-bar + p-bar
+//                  - beta (DG)^T p-bar          (then the Poisson chain)
+//   k_adj_ustar    u*-bar = u-bar - (W_f / dt) G psi;  q = u*-bar / W
+//   k_sweep_z<1>   q = W (I - beta L_z)^-1 q    (the forward z kernel)
+//   k_sweep_y      q = (I - beta L_y)^-1 q
+//   k_sweep_x      q = (I - beta L_x)^-1 q      (= RHS-bar)
+//   k_adj_hist     Hb = dt gamma q + H-bar;  H-bar_out = dt rho q;
+//                  f-bar += dt q
+//   k_adj_gather   u-bar = u*-bar + dt/Re L^T q + J_A(u^n)^T Hb;
+//                  p-bar -= dt G^T q
+#include "kernels.cuh"
+#include "tri.cuh"
+
+namespace fsei {
+
+namespace {
+
+// neighbour access with periodic x, y and periodic or walled z (out-of-range
+// z reads give 0 with walls)
+struct Nb {
+    int nx, ny, nz, walls;
+    FSEI_D int wxi(int i) const { return i < 0 ? i + nx : (i >= nx ? i - nx : i); }
+    FSEI_D int wyi(int j) const { return j < 0 ? j + ny : (j >= ny ? j - ny : j); }
+    FSEI_D int wzi(int k) const { return k < 0 ? k + nz : (k >= nz ? k - nz : k); }
+    FSEI_D bool zin(int k) const { return !walls || (k >= 0 && k < nz); }
+    template <typename T> FSEI_D T at(const T *f, int i, int j, int k) const {
+        if (!zin(k)) return T(0);
+        return f[((size_t)wzi(k) * ny + wyi(j)) * nx + wxi(i)];
+    }
+};
+
+FSEI_D size_t fid(int i, int j, int k, int nx, int ny) {
+    return ((size_t)k * ny + j) * nx + i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_phibar(GridDev g, const T *__restrict__ ub, const T *__restrict__ vb,
+             const T *__restrict__ wb, const T *__restrict__ pb, T *__restrict__ x,
+             const StepScalars *sc) {
+    const Nb N{g.nx, g.ny, g.nz, g.walls};
+    const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
+    const T dt = T(sc->dt), beta = T(sc->beta);
+    const T idx = T(g.idx), idy = T(g.idy), idx2 = T(g.idx2), idy2 = T(g.idy2);
+    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
+    const int nz = g.nz;
+    const bool walls = g.walls != 0;
+    const int kd = N.wzi(k - 1), ku = N.wzi(k + 1);
+    const T inv_vol = T(g.idx * g.idy) * idz[k];
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        // G^T u-bar
+        const T cz0 = (walls && k == 0) ? T(0) : N.at(wb, i, j, k) * ihc[k];
+        const T cz1 = (walls && k == nz - 1) ? T(0) : N.at(wb, i, j, k + 1) * ihc[k + 1];
+        const T gtu = (N.at(ub, i, j, k) - N.at(ub, i + 1, j, k)) * idx +
+                      (N.at(vb, i, j, k) - N.at(vb, i, j + 1, k)) * idy + (cz0 - cz1);
+        // (DG)^T p-bar = lap_xy(p-bar) + dz_k lapz((p-bar) / dz)
+        const T p0 = N.at(pb, i, j, k);
+        const T lxy = (N.at(pb, i + 1, j, k) - T(2) * p0 + N.at(pb, i - 1, j, k)) * idx2 +
+                      (N.at(pb, i, j + 1, k) - T(2) * p0 + N.at(pb, i, j - 1, k)) * idy2;
+        const T q0 = p0 * idz[k];
+        const T fup = (walls && k == nz - 1) ? T(0) : (N.at(pb, i, j, k + 1) * idz[ku] - q0) * ihc[k + 1];
+        const T fdn = (walls && k == 0) ? T(0) : (q0 - N.at(pb, i, j, k - 1) * idz[kd]) * ihc[k];
+        const T lp = lxy + dz[k] * (fup - fdn) * idz[k];
+        const T phib = -dt * gtu + p0 - beta * lp;
+        x[fid(i, j, k, g.nx, g.ny)] = phib * inv_vol;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_ustar(GridDev g, T *__restrict__ ub, T *__restrict__ vb, T *__restrict__ wb,
+            const T *__restrict__ psi, T *__restrict__ q0, T *__restrict__ q1,
+            T *__restrict__ q2, const StepScalars *sc) {
+    const Nb N{g.nx, g.ny, g.nz, g.walls};
+    const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
+    const T idt = T(1.0 / sc->dt);
+    const T *dz = Metric<T>::dz(g), *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
+    const T dxv = T(g.dx), dyv = T(g.dy);
+    const bool wall_face = g.walls && k == 0;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        const size_t c = fid(i, j, k, g.nx, g.ny);
+        const T s0 = psi[c];
+        const T us = ub[c] - dyv * dz[k] * (s0 - N.at(psi, i - 1, j, k)) * idt;
+        const T vs = vb[c] - dxv * dz[k] * (s0 - N.at(psi, i, j - 1, k)) * idt;
+        const T ws = wall_face ? T(0) : wb[c] - dxv * dyv * (s0 - N.at(psi, i, j, k - 1)) * idt;
+        ub[c] = us;
+        vb[c] = vs;
+        wb[c] = ws;
+        q0[c] = us * idz[k];
+        q1[c] = vs * idz[k];
+        q2[c] = ws * ihc[k];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_sweep_x(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2, TriPlan<T> px,
+          int ry) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sd = reinterpret_cast<T *>(smraw);
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int es = ry | 1;
+    T *red = sd + (size_t)nx * es;
+    const int rs = 2 * px.P + 1;
+    const TriPlan<T> pl = stage_plan(px, red + (size_t)ry * rs);
+    const int nby = ny / ry;
+    int b = blockIdx.x;
+    const int jb = b % nby; b /= nby;
+    const int k = b % nz;
+    const int comp = b / nz;
+    T *q = comp == 0 ? q0 : (comp == 1 ? q1 : q2);
+    const int j0 = jb * ry;
+    for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
+        const int r = e / nx, i = e - r * nx;
+        sd[i * es + r] = q[fid(i, j0 + r, k, nx, ny)];
+    }
+    __syncthreads();
+    tri_plan_solve<T, T>(sd, es, 1, ry, pl, red, rs);
+    for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
+        const int r = e / nx, i = e - r * nx;
+        q[fid(i, j0 + r, k, nx, ny)] = sd[i * es + r];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_hist(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
+           const T *__restrict__ q2, T *__restrict__ hbu, T *__restrict__ hbv,
+           T *__restrict__ hbw, T *__restrict__ h0, T *__restrict__ h1, T *__restrict__ h2,
+           T *fbx, T *fby, T *fbz, const StepScalars *sc) {
+    const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
+    const T dt = T(sc->dt), gam = T(sc->gamma), rho = T(sc->rho);
+    const bool wall_face = g.walls && k == 0;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        const size_t c = fid(i, j, k, g.nx, g.ny);
+        const T a = q0[c], b = q1[c], cc = wall_face ? T(0) : q2[c];
+        h0[c] = dt * gam * a + hbu[c];
+        h1[c] = dt * gam * b + hbv[c];
+        h2[c] = wall_face ? T(0) : dt * gam * cc + hbw[c];
+        hbu[c] = dt * rho * a;
+        hbv[c] = dt * rho * b;
+        hbw[c] = dt * rho * cc;
+        if (fbx) fbx[c] += dt * a;
+        if (fby) fby[c] += dt * b;
+        if (fbz) fbz[c] += dt * cc;
+    }
+}
+
+// u-bar += dt/Re L^T q + J_A(u^n)^T Hb (one component per call of the
+// helpers below); p-bar -= dt G^T q.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
+             const T *__restrict__ w, const T *__restrict__ q0, const T *__restrict__ q1,
+             const T *__restrict__ q2, const T *__restrict__ H0, const T *__restrict__ H1,
+             const T *__restrict__ H2, T *__restrict__ ub, T *__restrict__ vb,
+             T *__restrict__ wb, T *__restrict__ pb, const StepScalars *sc, T inv_re) {
+    const Nb N{g.nx, g.ny, g.nz, g.walls};
+    const int nz = g.nz;
+    const bool walls = g.walls != 0;
+    const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
+    const T dt = T(sc->dt);
+    const T idx = T(g.idx), idy = T(g.idy), idx2 = T(g.idx2), idy2 = T(g.idy2);
+    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
+    const T h = T(0.5);
+    auto IDZ = [&](int kk) { return idz[N.wzi(kk)]; };
+    auto IHC = [&](int kk) { return ihc[kk < 0 ? kk + nz : (kk > nz ? kk - nz : kk)]; };
+    // cotangents of the advection term, with the sign of -div(uu) folded in
+    auto A = [&](int i, int jj, int kk) { return -N.at(H0, i, jj, kk); };
+    auto B = [&](int i, int jj, int kk) { return -N.at(H1, i, jj, kk); };
+    auto C = [&](int i, int jj, int kk) {
+        if (walls && (kk <= 0 || kk >= nz)) return T(0);
+        return -N.at(H2, i, jj, kk);
+    };
+    // flux cotangents at centres and edges
+    auto Qb = [&](int i, int jj, int kk) { return (A(i, jj, kk) - A(i + 1, jj, kk)) * idx; };
+    auto Rb = [&](int i, int jj, int kk) { return (B(i, jj, kk) - B(i, jj + 1, kk)) * idy; };
+    auto Sb = [&](int i, int jj, int kk) {
+        return C(i, jj, kk) * IHC(kk) - C(i, jj, kk + 1) * IHC(kk + 1);
+    };
+    auto Euv = [&](int i, int jj, int kk) {
+        return (A(i, jj - 1, kk) - A(i, jj, kk)) * idy + (B(i - 1, jj, kk) - B(i, jj, kk)) * idx;
+    };
+    auto Euw = [&](int i, int jj, int kk) {
+        if (walls && (kk <= 0 || kk >= nz)) return T(0);
+        return (A(i, jj, kk - 1) * IDZ(kk - 1) - A(i, jj, kk) * IDZ(kk)) +
+               (C(i - 1, jj, kk) - C(i, jj, kk)) * idx;
+    };
+    auto Evw = [&](int i, int jj, int kk) {
+        if (walls && (kk <= 0 || kk >= nz)) return T(0);
+        return (B(i, jj, kk - 1) * IDZ(kk - 1) - B(i, jj, kk) * IDZ(kk)) +
+               (C(i, jj - 1, kk) - C(i, jj, kk)) * idy;
+    };
+    // forward averages
+    auto U = [&](int i, int jj, int kk) { return N.at(u, i, jj, kk); };
+    auto V = [&](int i, int jj, int kk) { return N.at(v, i, jj, kk); };
+    auto Wf = [&](int i, int jj, int kk) {
+        if (walls && (kk <= 0 || kk >= nz)) return T(0);
+        return N.at(w, i, jj, kk);
+    };
+    const int kd = N.wzi(k - 1), ku = N.wzi(k + 1);
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        const size_t c = fid(i, j, k, g.nx, g.ny);
+        // ---- u
+        {
+            const T uc0 = h * (U(i, j, k) + U(i + 1, j, k));
+            const T ucm = h * (U(i - 1, j, k) + U(i, j, k));
+            T a = h * (T(2) * uc0 * Qb(i, j, k) + T(2) * ucm * Qb(i - 1, j, k));
+            a += h * (Euv(i, j, k) * h * (V(i, j, k) + V(i - 1, j, k)) +
+                      Euv(i, j + 1, k) * h * (V(i, j + 1, k) + V(i - 1, j + 1, k)));
+            a += h * (Euw(i, j, k) * h * (Wf(i, j, k) + Wf(i - 1, j, k)) +
+                      Euw(i, j, k + 1) * h * (Wf(i, j, k + 1) + Wf(i - 1, j, k + 1)));
+            // viscous: lap_xy(q) + dz_k lapz_centre(q / dz)
+            const T qc = N.at(q0, i, j, k);
+            const T lxy = (N.at(q0, i + 1, j, k) - T(2) * qc + N.at(q0, i - 1, j, k)) * idx2 +
+                          (N.at(q0, i, j + 1, k) - T(2) * qc + N.at(q0, i, j - 1, k)) * idy2;
+            const T sq = qc * idz[k];
+            const T sup = N.zin(k + 1) ? N.at(q0, i, j, k + 1) * idz[ku] : T(0);
+            const T sdn = N.zin(k - 1) ? N.at(q0, i, j, k - 1) * idz[kd] : T(0);
+            const T lz = ((sup - sq) * ihc[k + 1] - (sq - sdn) * ihc[k]) * idz[k];
+            ub[c] = ub[c] + dt * inv_re * (lxy + dz[k] * lz) + a;
+        }
+        // ---- v
+        {
+            const T vc0 = h * (V(i, j, k) + V(i, j + 1, k));
+            const T vcm = h * (V(i, j - 1, k) + V(i, j, k));
+            T a = h * (T(2) * vc0 * Rb(i, j, k) + T(2) * vcm * Rb(i, j - 1, k));
+            a += h * (Euv(i, j, k) * h * (U(i, j, k) + U(i, j - 1, k)) +
+                      Euv(i + 1, j, k) * h * (U(i + 1, j, k) + U(i + 1, j - 1, k)));
+            a += h * (Evw(i, j, k) * h * (Wf(i, j, k) + Wf(i, j - 1, k)) +
+                      Evw(i, j, k + 1) * h * (Wf(i, j, k + 1) + Wf(i, j - 1, k + 1)));
+            const T qc = N.at(q1, i, j, k);
+            const T lxy = (N.at(q1, i + 1, j, k) - T(2) * qc + N.at(q1, i - 1, j, k)) * idx2 +
+                          (N.at(q1, i, j + 1, k) - T(2) * qc + N.at(q1, i, j - 1, k)) * idy2;
+            const T sq = qc * idz[k];
+            const T sup = N.zin(k + 1) ? N.at(q1, i, j, k + 1) * idz[ku] : T(0);
+            const T sdn = N.zin(k - 1) ? N.at(q1, i, j, k - 1) * idz[kd] : T(0);
+            const T lz = ((sup - sq) * ihc[k + 1] - (sq - sdn) * ihc[k]) * idz[k];
+            vb[c] = vb[c] + dt * inv_re * (lxy + dz[k] * lz) + a;
+        }
+        // ---- w
+        if (walls && k == 0) {
+            wb[c] = T(0);
+        } else {
+            const T wc0 = h * (Wf(i, j, k) + Wf(i, j, k + 1));
+            const T wcm = h * (Wf(i, j, k - 1) + Wf(i, j, k));
+            T a = h * (T(2) * wc0 * Sb(i, j, k) + T(2) * wcm * Sb(i, j, k - 1));
+            a += h * (Euw(i, j, k) * h * (U(i, j, k) + U(i, j, k - 1)) +
+                      Euw(i + 1, j, k) * h * (U(i + 1, j, k) + U(i + 1, j, k - 1)));
+            a += h * (Evw(i, j, k) * h * (V(i, j, k) + V(i, j, k - 1)) +
+                      Evw(i, j + 1, k) * h * (V(i, j + 1, k) + V(i, j + 1, k - 1)));
+            // viscous: lap_xy(q) + hc_k lapz_face(q / hc), q = 0 on the walls
+            auto QW = [&](int ii, int jj, int kk) {
+                if (walls && (kk <= 0 || kk >= nz)) return T(0);
+                return N.at(q2, ii, jj, kk);
+            };
+            const T qc = QW(i, j, k);
+            const T lxy = (QW(i + 1, j, k) - T(2) * qc + QW(i - 1, j, k)) * idx2 +
+                          (QW(i, j + 1, k) - T(2) * qc + QW(i, j - 1, k)) * idy2;
+            const T sq = qc * ihc[k];
+            const T sup = QW(i, j, k + 1) * IHC(k + 1 == nz ? (walls ? nz : 0) : k + 1);
+            const T sdn = QW(i, j, k - 1) * IHC(k - 1 < 0 ? nz - 1 : k - 1);
+            const T lz = ((sup - sq) * idz[k] - (sq - sdn) * idz[kd]) * ihc[k];
+            wb[c] = wb[c] + dt * inv_re * (lxy + lz / ihc[k]) + a;
+        }
+        // ---- p: p-bar -= dt G^T q
+        {
+            const T cz0 = (walls && k == 0) ? T(0) : N.at(q2, i, j, k) * ihc[k];
+            const T cz1 = (walls && k == nz - 1) ? T(0) : N.at(q2, i, j, k + 1) * ihc[k + 1];
+            const T gtq = (N.at(q0, i, j, k) - N.at(q0, i + 1, j, k)) * idx +
+                          (N.at(q1, i, j, k) - N.at(q1, i, j + 1, k)) * idy + (cz0 - cz1);
+            pb[c] = pb[c] - dt * gtq;
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T> size_t smem_sweep_x(const GridDev &g, const Work<T> &W) {
+    const int es = W.ry | 1;
+    return sizeof(T) * ((size_t)g.nx * es + (size_t)W.ry * (2 * W.plan[0].P + 1) +
+                        plan_stage_words(W.plan[0].n, W.plan[0].P));
+}
+
+template <typename T>
+void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T *u, const T *v,
+                         const T *w, T *ub, T *vb, T *wb, T *pb, T *hbu, T *hbv, T *hbw, T *fbx,
+                         T *fby, T *fbz, double re, cudaStream_t st) {
+    const int rows = g.ny * g.nz;
+    const int thr = g.nx >= 256 ? 256 : ((g.nx + 31) / 32) * 32;
+    k_adj_phibar<T><<<rows, thr, 0, st>>>(g, ub, vb, wb, pb, W.phi, sc);
+    launch_rfft_x<T>(g, W, sc, W.phi, 1, st);
+    launch_fft_y<T>(g, W, 0, st);
+    launch_poisson_z<T>(g, W, st, 1);
+    launch_fft_y<T>(g, W, 1, st);
+    launch_irfft_x<T>(g, W, W.phi, st);
+    k_adj_ustar<T><<<rows, thr, 0, st>>>(g, ub, vb, wb, W.phi, W.q0, W.q1, W.q2, sc);
+    launch_sweep_z_adjoint<T>(g, W, st);
+    launch_sweep_y<T>(g, W, st);
+    {
+        const int ry = W.ry;
+        const int threads = ((ry * W.plan[0].P + 31) / 32) * 32;
+        k_sweep_x<T><<<3 * g.nz * (g.ny / ry), threads < 64 ? 64 : threads, smem_sweep_x(g, W),
+                       st>>>(g, W.q0, W.q1, W.q2, W.plan[0], ry);
+    }
+    k_adj_hist<T><<<rows, thr, 0, st>>>(g, W.q0, W.q1, W.q2, hbu, hbv, hbw, W.adj0, W.adj1,
+                                        W.adj2, fbx, fby, fbz, sc);
+    k_adj_gather<T><<<rows, thr, 0, st>>>(g, u, v, w, W.q0, W.q1, W.q2, W.adj0, W.adj1, W.adj2, ub,
+                                          vb, wb, pb, sc, T(1.0 / re));
+}
+
+template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<T> &W) {
+    cudaFuncSetAttribute(k_sweep_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_sweep_x(g, W));
+}
+
+#define FSEI_INST(T)                                                                           \
+    template void launch_adjoint_step<T>(const GridDev &, Work<T> &, StepScalars *, const T *,  \
+                                         const T *, const T *, T *, T *, T *, T *, T *, T *,    \
+                                         T *, T *, T *, T *, double, cudaStream_t);             \
+    template void set_smem_limits_adjoint<T>(const GridDev &, const Work<T> &);
+FSEI_INST(float)
+FSEI_INST(double)
+#undef FSEI_INST
+
+}  // namespace fsei

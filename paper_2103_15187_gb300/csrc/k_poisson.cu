@@ -304,14 +304,15 @@ template <typename T> void launch_fft_y(const GridDev &g, Work<T> &W, int invers
         k_fft_y<T, -1><<<blocks, 256, smem_fft_y(g, W), st>>>(g, W.spec, W.twy, W.fpy, W.tkx);
 }
 
-template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaStream_t st) {
+template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaStream_t st,
+                                            int compat) {
     const int blocks = g.ny * (g.sk / W.tkx);
     const int threads = ((W.tkx * W.pz_poisson + 31) / 32) * 32;
     const double scale = 1.0 / ((double)g.nx * g.ny);
     // exact modes first: they read the untouched right-hand side
     const int Pe = exact_chunks(g.nz);
     k_poisson_exact<T><<<W.n_nzm, 64, smem_exact(g.nz, Pe), st>>>(
-        g, W.spec, W.nzm, W.lamx_d, W.lamy_d, scale, 0, Pe);
+        g, W.spec, W.nzm, W.lamx_d, W.lamy_d, scale, compat, Pe);
     k_poisson_z<T><<<blocks, threads, smem_poisson(g, W), st>>>(
         g, W.spec, W.lamx, W.lamy, W.exact, W.tkx, W.pz_poisson, T(scale));
 }
@@ -346,7 +347,7 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     template void launch_rfft_x<T>(const GridDev &, Work<T> &, const StepScalars *, const T *, \
                                    int, cudaStream_t);                                        \
     template void launch_fft_y<T>(const GridDev &, Work<T> &, int, cudaStream_t);              \
-    template void launch_poisson_z<T>(const GridDev &, Work<T> &, cudaStream_t);               \
+    template void launch_poisson_z<T>(const GridDev &, Work<T> &, cudaStream_t, int);          \
     template void launch_irfft_x<T>(const GridDev &, Work<T> &, T *, cudaStream_t);            \
     template void set_smem_limits_poisson<T>(const GridDev &, const Work<T> &);
 FSEI_INST(float)

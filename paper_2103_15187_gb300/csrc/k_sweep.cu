@@ -13,6 +13,8 @@
 //                 (I - beta L_x) q = RHS along x
 //   k_sweep_y     (I - beta L_y) r = q along y
 //   k_sweep_z     (I - beta L_z) du = r along z; u* = u^n + du
+#include <string.h>
+
 #include "kernels.cuh"
 #include "tri.cuh"
 
@@ -344,7 +346,10 @@ k_sweep_y(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
     }
 }
 
-template <typename T>
+// MODE 0 (step): q = u^n + (I - beta L_z)^-1 q.
+// MODE 1 (adjoint): q = W (I - beta L_z)^-1 q with W = dz_k (u, v) or hc_k
+// (w; 0 on the wall face).
+template <typename T, int MODE>
 __global__ void __launch_bounds__(512)
 k_sweep_z(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
           TriPlan<T> pzc, TriPlan<T> pzf, int tx) {
@@ -373,7 +378,13 @@ k_sweep_z(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__r
         const int k = e / tx, l = e - k * tx;
         if (x0 + l < nx) {
             const size_t c = fid(x0 + l, j, k, nx, ny);
-            q[c] = un[c] + sd[e];
+            if (MODE == 0) {
+                q[c] = un[c] + sd[e];
+            } else {
+                const T wk = comp < 2 ? Metric<T>::dz(g)[k]
+                                      : ((g.walls && k == 0) ? T(0) : T(1) / Metric<T>::ihc(g)[k]);
+                q[c] = wk * sd[e];
+            }
         }
     }
 }
@@ -433,8 +444,18 @@ template <typename T> void launch_sweep_z(const GridDev &g, const Fields<T> &F, 
     const int P = W.plan[2].P > W.plan[3].P ? W.plan[2].P : W.plan[3].P;
     const int threads = ((W.tx * P + 31) / 32) * 32;
     const int nxt = (g.nx + W.tx - 1) / W.tx;
-    k_sweep_z<T><<<3 * g.ny * nxt, threads, smem_sweep<T>(g.nz, W, P), st>>>(
+    k_sweep_z<T, 0><<<3 * g.ny * nxt, threads, smem_sweep<T>(g.nz, W, P), st>>>(
         g, F, W.q0, W.q1, W.q2, W.plan[2], W.plan[3], W.tx);
+}
+
+template <typename T> void launch_sweep_z_adjoint(const GridDev &g, Work<T> &W, cudaStream_t st) {
+    const int P = W.plan[2].P > W.plan[3].P ? W.plan[2].P : W.plan[3].P;
+    const int threads = ((W.tx * P + 31) / 32) * 32;
+    const int nxt = (g.nx + W.tx - 1) / W.tx;
+    Fields<T> none;
+    memset(&none, 0, sizeof none);
+    k_sweep_z<T, 1><<<3 * g.ny * nxt, threads, smem_sweep<T>(g.nz, W, P), st>>>(
+        g, none, W.q0, W.q1, W.q2, W.plan[2], W.plan[3], W.tx);
 }
 
 template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T> &W) {
@@ -443,7 +464,9 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
                          (int)smem_rhs_x(g, W));
     cudaFuncSetAttribute(k_sweep_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_sweep<T>(g.ny, W, W.plan[1].P));
-    cudaFuncSetAttribute(k_sweep_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_sweep_z<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_sweep<T>(g.nz, W, P));
+    cudaFuncSetAttribute(k_sweep_z<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_sweep<T>(g.nz, W, P));
 }
 
@@ -459,6 +482,7 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     template void launch_sweep_y<T>(const GridDev &, Work<T> &, cudaStream_t);                 \
     template void launch_sweep_z<T>(const GridDev &, const Fields<T> &, Work<T> &,             \
                                     cudaStream_t);                                            \
+    template void launch_sweep_z_adjoint<T>(const GridDev &, Work<T> &, cudaStream_t);         \
     template void set_smem_limits_sweep<T>(const GridDev &, const Work<T> &);
 FSEI_INST(float)
 FSEI_INST(double)

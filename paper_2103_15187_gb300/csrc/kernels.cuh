@@ -27,7 +27,8 @@ template <typename T> struct Work {
     const int *nzm;          // near-zero modes to solve in double: kx + sk*ky
     int n_nzm;
     const unsigned char *exact;   // [ny][sk]: 1 for the modes in nzm
-    double *nz_scratch;      // 2 * nz doubles per near-zero mode
+    double *nz_scratch;      // unused scratch kept for layout compatibility
+    T *adj0, *adj1, *adj2;   // adjoint workspace (allocated on first use)
     int ry;                  // rows per block of the x-line kernels
     int tx;                  // x columns per block of the y/z sweeps
     int tkx;                 // kx columns per block of the y FFT / z Poisson
@@ -52,8 +53,19 @@ template <typename T> void launch_sweep_z(const GridDev &g, const Fields<T> &F, 
 template <typename T> void launch_rfft_x(const GridDev &g, Work<T> &W, const StepScalars *sc,
                                          const T *src, int mode, cudaStream_t st);
 template <typename T> void launch_fft_y(const GridDev &g, Work<T> &W, int inverse, cudaStream_t st);
-template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaStream_t st);
+// compat = 1: the (0, 0) mode's right-hand side first loses its dz-weighted
+// mean (an arbitrary right-hand side made compatible; used by the adjoint)
+template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaStream_t st,
+                                            int compat = 0);
 template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st);
+// z sweep of the adjoint: q = W (I - beta L_z)^-1 q, W = dz_k (u, v) or
+// hc_k (w)
+template <typename T> void launch_sweep_z_adjoint(const GridDev &g, Work<T> &W, cudaStream_t st);
+template <typename T>
+void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T *u, const T *v,
+                         const T *w, T *ub, T *vb, T *wb, T *pb, T *hbu, T *hbv, T *hbw, T *fbx,
+                         T *fby, T *fbz, double re, cudaStream_t st);
+template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<T> &W);
 template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                           StepScalars *sc, cudaStream_t st);
 

@@ -24,7 +24,7 @@ FLAG_NONFINITE, FLAG_CFL = 1, 2
 
 # exported symbols and their C signatures (kept in step with include/fsei.h)
 EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
-           "fsei_step", "fsei_poisson_solve", "fsei_set_kernel_timing",
+           "fsei_step", "fsei_poisson_solve", "fsei_adjoint_step", "fsei_set_kernel_timing",
            "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version")
 
 
@@ -95,6 +95,9 @@ def load(path=LIB_PATH):
     lib.fsei_step.restype = ctypes.c_int
     lib.fsei_poisson_solve.argtypes = [vp, vp, vp, vp]
     lib.fsei_poisson_solve.restype = ctypes.c_int
+    lib.fsei_adjoint_step.argtypes = [vp, ctypes.POINTER(State), ctypes.POINTER(StepParams),
+                                      ctypes.POINTER(State), vp, vp, vp, vp]
+    lib.fsei_adjoint_step.restype = ctypes.c_int
     lib.fsei_set_kernel_timing.argtypes = [vp, ctypes.c_int32]
     lib.fsei_set_kernel_timing.restype = ctypes.c_int
     lib.fsei_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -196,6 +199,24 @@ def poisson_solve(grid, rhs, phi, stream=None):
     """fsei_poisson_solve: phi with D G phi = rhs (device tensors)."""
     _check(load().fsei_poisson_solve(grid.handle, _ptr(rhs), _ptr(phi),
                                      _stream_handle(stream)))
+
+
+def adjoint_step(grid, fwd, adj, fbar=None, re=100.0, dt=1e-3, gamma=1.5, rho=-0.5,
+                 fconst=(0.0, 0.0, 0.0), stream=None):
+    """fsei_adjoint_step.  fwd: dict with the step's input u, v, w (and
+    have_prev_h); adj: dict of cotangent tensors u, v, w, p, hu, hv, hw,
+    updated in place from output to input cotangents; fbar: None or
+    (fbx, fby, fbz) accumulated in place."""
+    lib = load()
+    f = State(_ptr(fwd["u"]), _ptr(fwd["v"]), _ptr(fwd["w"]), None, None, None, None,
+              int(fwd.get("have_prev_h", 0)))
+    a = State(_ptr(adj["u"]), _ptr(adj["v"]), _ptr(adj["w"]), _ptr(adj["p"]),
+              _ptr(adj["hu"]), _ptr(adj["hv"]), _ptr(adj["hw"]), 0)
+    prm = StepParams(re, dt, 0.0, gamma, rho, (ctypes.c_double * 3)(*fconst))
+    fb = (None, None, None) if fbar is None else fbar
+    _check(lib.fsei_adjoint_step(grid.handle, ctypes.byref(f), ctypes.byref(prm),
+                                 ctypes.byref(a), _ptr(fb[0]), _ptr(fb[1]), _ptr(fb[2]),
+                                 _stream_handle(stream)))
 
 
 def set_kernel_timing(grid, enable):
