@@ -85,8 +85,11 @@ def _window_case(shape):
 @pytest.mark.parametrize("shape", [(64, 48, 40), (128, 128, 192)])
 def test_window_gradient_matches_finite_differences(fsei, shape):
     """FP64, 20 steps, checkpoint every 5, dt frozen from CFL 0.5 at step 0;
-    16 seeded Gaussian unit directions over (u0, v0, w0, fx, fy, fz);
-    central differences with step 1e-4 agree with the adjoint to 1e-6."""
+    16 seeded Gaussian directions over (u0, v0, w0, fx, fy, fz), each scaled
+    to the norm of the initial velocity so that the step 1e-4 is relative;
+    central differences agree with the adjoint to 1e-6.  (With unit-norm
+    directions over ~1e7 values each point moves by ~1e-8 and round-off in
+    J dominates the difference quotient.)"""
     import torch
     from paper_2103_15187_gb300 import autograd as fad
     case = _window_case(shape)
@@ -113,7 +116,8 @@ def test_window_gradient_matches_finite_differences(fsei, shape):
         d[2][0] = 0.0
         d[5][0] = 0.0
         nrm = np.sqrt(sum((a * a).sum() for a in d))
-        d = [dev(a / nrm) for a in d]
+        scale = np.sqrt((case.u ** 2).sum() + (case.v ** 2).sum() + (case.w ** 2).sum()) / nrm
+        d = [dev(a * scale) for a in d]
         eps = 1e-4
         with torch.no_grad():
             jp = float(J([a + eps * b for a, b in zip(x0, d)]))
