@@ -178,6 +178,31 @@ fsei_status fsei_adjoint_step(fsei_grid grid, const fsei_state *fwd,
                               void *fbar_x, void *fbar_y, void *fbar_z,
                               void *cuda_stream);
 
+/* Batched ensemble of independent boxes of uneven sizes (each with its own
+ * grid description, Reynolds number, dt or CFL, body force and state).
+ * fsei_batch_create creates one grid per box (as fsei_grid_create) plus the
+ * streams and events of a CUDA graph.  fsei_batch_step advances every box by
+ * nsteps fractional steps: one step of all boxes is captured into a CUDA
+ * graph whose per-box kernel chains run on parallel branches, and the graph
+ * is replayed once per step on cuda_stream.  The graph is re-captured when
+ * the state pointers, forces, parameters or history flags differ from the
+ * last capture (the first call, and the call after it, capture).
+ *   states: nboxes fsei_state (device pointers per box, have_prev_h updated);
+ *   forces: NULL, or 3*nboxes pointers (fx, fy, fz per box, each nullable);
+ *   params: nboxes fsei_step_params;
+ *   out: NULL or nboxes fsei_step_stats (the call then synchronises; the
+ *        status reports the first box with a device flag).
+ * Each box's results equal those of fsei_step on that box alone. */
+typedef struct fsei_batch_s *fsei_batch;
+fsei_status fsei_batch_create(const fsei_grid_desc *descs, int32_t nboxes,
+                              fsei_batch *out);
+void fsei_batch_destroy(fsei_batch batch);
+int32_t fsei_batch_size(fsei_batch batch);
+fsei_status fsei_batch_step(fsei_batch batch, fsei_state *states,
+                            const void *const *forces,
+                            const fsei_step_params *params, int32_t nsteps,
+                            void *cuda_stream, fsei_step_stats *out);
+
 /* Size in bytes of the device array that backs fsei_poisson_solve_noalloc. */
 #define FSEI_NOALLOC_SCRATCH_BYTES (32u << 20)
 

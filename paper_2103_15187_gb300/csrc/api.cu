@@ -261,14 +261,15 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
 
 template <typename T>
 fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx, const void *fy,
-                      const void *fz, const StepArgs &a, int nsteps, cudaStream_t st) {
+                      const void *fz, const StepArgs &a, int nsteps, cudaStream_t st,
+                      bool with_speed = true) {
     Fields<T> F;
     F.u = (T *)s->u; F.v = (T *)s->v; F.w = (T *)s->w; F.p = (T *)s->p;
     F.hu = (T *)s->hu; F.hv = (T *)s->hv; F.hw = (T *)s->hw;
     F.fx = (const T *)fx; F.fy = (const T *)fy; F.fz = (const T *)fz;
     const GridDev &g = G->g;
     KernelTimer &tm = G->timer;
-    if (a.cfl > 0.0) {
+    if (a.cfl > 0.0 && with_speed) {
         cudaMemsetAsync(&G->sc->speed_next, 0, sizeof(unsigned long long), st);
         tm.run(KK_SPEED, st, [&] { launch_speed<T>(g, F.u, F.v, F.w, G->sc, st); });
     }
@@ -585,6 +586,205 @@ int32_t fsei_kernel_times(fsei_grid G, double *total_ms, int64_t *launches, int3
 
 const char *fsei_kernel_name(int32_t kind) {
     return (kind >= 0 && kind < KK_COUNT) ? kKernelNames[kind] : nullptr;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- batches ----
+// An ensemble of independent grids advanced together.  One step of every
+// box is captured into a CUDA graph whose per-box kernel chains sit on
+// parallel branches (the capture forks over library-owned streams), so the
+// boxes' kernels overlap on the GPU; the graph is replayed once per step on
+// the caller's stream.  Two graphs are kept: the first step of a call (CFL
+// pre-pass, Euler start for boxes without history) and the following steps.
+// They are re-captured when the state pointers, forces or parameters of a
+// call differ from the captured ones.
+struct fsei_batch_s {
+    std::vector<fsei_grid> grids;
+    int device = 0;
+    std::vector<cudaStream_t> branches;
+    cudaStream_t capture = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraphExec_t first = nullptr, rest = nullptr;
+    std::vector<unsigned char> key;   // bytes of the captured call's arguments
+};
+
+namespace {
+
+void batch_clear_graphs(fsei_batch_s *B) {
+    if (B->first) cudaGraphExecDestroy(B->first);
+    if (B->rest) cudaGraphExecDestroy(B->rest);
+    B->first = B->rest = nullptr;
+    B->key.clear();
+}
+
+fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const *forces,
+                          const fsei_step_params *prm, bool first, cudaGraphExec_t *out) {
+    cudaStream_t cs = B->capture;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(FSEI_E_CUDA, "batch: cannot begin graph capture");
+    cudaEventRecord(B->fork, cs);
+    for (cudaStream_t b : B->branches) cudaStreamWaitEvent(b, B->fork, 0);
+    fsei_status r = FSEI_OK;
+    for (size_t i = 0; i < B->grids.size() && r == FSEI_OK; ++i) {
+        fsei_grid_s *G = B->grids[i];
+        cudaStream_t st = B->branches[i % B->branches.size()];
+        StepArgs a;
+        a.re = prm[i].re; a.dt = prm[i].dt; a.cfl = prm[i].cfl;
+        a.gamma = prm[i].gamma; a.rho = prm[i].rho;
+        for (int c = 0; c < 3; ++c) a.fconst[c] = prm[i].fconst[c];
+        fsei_state s = states[i];
+        if (!first) s.have_prev_h = 1;
+        const void *f0 = forces ? forces[3 * i] : nullptr;
+        const void *f1 = forces ? forces[3 * i + 1] : nullptr;
+        const void *f2 = forces ? forces[3 * i + 2] : nullptr;
+        r = G->prec == FSEI_FP64 ? run_steps<double>(G, G->wd, &s, f0, f1, f2, a, 1, st, first)
+                                 : run_steps<float>(G, G->wf, &s, f0, f1, f2, a, 1, st, first);
+    }
+    for (size_t b = 0; b < B->branches.size(); ++b) {
+        cudaEventRecord(B->joins[b], B->branches[b]);
+        cudaStreamWaitEvent(cs, B->joins[b], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (r != FSEI_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return r;
+    }
+    if (e != cudaSuccess || !graph) return fail(FSEI_E_CUDA, "batch: capture failed: %s", cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(FSEI_E_CUDA, "batch: graph instantiation failed: %s", cudaGetErrorString(ei));
+    return FSEI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fsei_status fsei_batch_create(const fsei_grid_desc *descs, int32_t nboxes, fsei_batch *out) {
+    g_err.clear();
+    if (!descs || !out || nboxes < 1) return fail(FSEI_E_ARG, "fsei_batch_create: bad arguments");
+    *out = nullptr;
+    fsei_batch_s *B = new fsei_batch_s();
+    cudaGetDevice(&B->device);
+    for (int i = 0; i < nboxes; ++i) {
+        fsei_grid g = nullptr;
+        const fsei_status st = fsei_grid_create(&descs[i], &g);
+        if (st != FSEI_OK) {
+            const std::string msg = g_err;
+            fsei_batch_destroy(B);
+            return fail(st, "box %d: %s", i, msg.c_str());
+        }
+        B->grids.push_back(g);
+    }
+    const int nb = nboxes < 8 ? nboxes : 8;
+    B->branches.resize(nb);
+    B->joins.resize(nb);
+    bool ok = cudaStreamCreateWithFlags(&B->capture, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < nb && ok; ++b)
+        ok = cudaStreamCreateWithFlags(&B->branches[b], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&B->joins[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        fsei_batch_destroy(B);
+        return fail(FSEI_E_CUDA, "fsei_batch_create: stream/event creation failed");
+    }
+    *out = B;
+    return FSEI_OK;
+}
+
+void fsei_batch_destroy(fsei_batch B) {
+    if (!B) return;
+    DeviceGuard dg(B->device);
+    cudaDeviceSynchronize();
+    batch_clear_graphs(B);
+    for (cudaStream_t s : B->branches)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : B->joins)
+        if (e) cudaEventDestroy(e);
+    if (B->capture) cudaStreamDestroy(B->capture);
+    if (B->fork) cudaEventDestroy(B->fork);
+    for (fsei_grid g : B->grids) fsei_grid_destroy(g);
+    delete B;
+}
+
+int32_t fsei_batch_size(fsei_batch B) { return B ? (int32_t)B->grids.size() : 0; }
+
+fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const *forces,
+                            const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,
+                            fsei_step_stats *out) {
+    g_err.clear();
+    if (!B || !states || !prm) return fail(FSEI_E_ARG, "fsei_batch_step: NULL argument");
+    if (nsteps < 0) return fail(FSEI_E_ARG, "nsteps < 0");
+    const size_t nb = B->grids.size();
+    for (size_t i = 0; i < nb; ++i) {
+        const fsei_state &s = states[i];
+        const void *req[7] = {s.u, s.v, s.w, s.p, s.hu, s.hv, s.hw};
+        for (int c = 0; c < 7; ++c)
+            if (!req[c] || !aligned16(req[c])) return fail(FSEI_E_ARG, "box %zu: state field %d NULL or misaligned", i, c);
+        for (int c = 0; c < 3 && forces; ++c)
+            if (forces[3 * i + c] && !aligned16(forces[3 * i + c])) return fail(FSEI_E_ARG, "box %zu: force %d misaligned", i, c);
+        if (!(prm[i].re > 0)) return fail(FSEI_E_ARG, "box %zu: re must be > 0", i);
+        if (!(prm[i].cfl > 0) && !(prm[i].dt > 0)) return fail(FSEI_E_ARG, "box %zu: need dt > 0 or cfl > 0", i);
+    }
+    DeviceGuard dg(B->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (nsteps > 0) {
+        // the captured graphs bake in pointers, forces, parameters and the
+        // history flags: compare their bytes with the last capture
+        std::vector<unsigned char> key;
+        auto put = [&](const void *p, size_t n) {
+            const unsigned char *c = static_cast<const unsigned char *>(p);
+            key.insert(key.end(), c, c + n);
+        };
+        for (size_t i = 0; i < nb; ++i) {
+            put(&states[i], sizeof(fsei_state));
+            put(&prm[i], sizeof(fsei_step_params));
+            for (int c = 0; c < 3; ++c) {
+                const void *f = forces ? forces[3 * i + c] : nullptr;
+                put(&f, sizeof f);
+            }
+        }
+        if (key != B->key || !B->first) {
+            batch_clear_graphs(B);
+            fsei_status r = batch_capture(B, states, forces, prm, true, &B->first);
+            if (r == FSEI_OK) r = batch_capture(B, states, forces, prm, false, &B->rest);
+            if (r != FSEI_OK) {
+                batch_clear_graphs(B);
+                return r;
+            }
+            B->key = key;
+        }
+        if (cudaGraphLaunch(B->first, st) != cudaSuccess) return fail(FSEI_E_CUDA, "batch: graph launch failed");
+        for (int n = 1; n < nsteps; ++n)
+            if (cudaGraphLaunch(B->rest, st) != cudaSuccess) return fail(FSEI_E_CUDA, "batch: graph launch failed");
+        // the history flags become 1; a following call therefore differs from
+        // this capture (its key holds the flags) and is captured once more
+        for (size_t i = 0; i < nb; ++i) states[i].have_prev_h = 1;
+    }
+    if (out) {
+        for (size_t i = 0; i < nb; ++i)
+            cudaMemcpyAsync(B->grids[i]->sc_host, B->grids[i]->sc, sizeof(StepScalars),
+                            cudaMemcpyDeviceToHost, st);
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(FSEI_E_CUDA, "fsei_batch_step: %s", cudaGetErrorString(e));
+        fsei_status worst = FSEI_OK;
+        for (size_t i = 0; i < nb; ++i) {
+            const StepScalars &h = *B->grids[i]->sc_host;
+            out[i].dt_used = h.dt;
+            out[i].cfl = h.dt * __builtin_bit_cast(double, h.speed_next);
+            out[i].max_div = __builtin_bit_cast(double, h.maxdiv);
+            out[i].kinetic_energy = h.ke;
+            out[i].flags = h.flags;
+            if (out[i].cfl > 1.0) out[i].flags |= FSEI_FLAG_CFL;
+            if ((out[i].flags & FSEI_FLAG_NONFINITE) && worst == FSEI_OK) worst = fail(FSEI_E_NONFINITE, "box %zu: non-finite state", i);
+            else if ((out[i].flags & FSEI_FLAG_CFL) && worst == FSEI_OK) worst = fail(FSEI_E_CFL, "box %zu: CFL %g above 1", i, out[i].cfl);
+        }
+        return worst;
+    }
+    return FSEI_OK;
 }
 
 }  // extern "C"

@@ -24,7 +24,8 @@ FLAG_NONFINITE, FLAG_CFL = 1, 2
 
 # exported symbols and their C signatures (kept in step with include/fsei.h)
 EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
-           "fsei_step", "fsei_poisson_solve", "fsei_adjoint_step", "fsei_set_kernel_timing",
+           "fsei_step", "fsei_poisson_solve", "fsei_adjoint_step", "fsei_batch_create",
+           "fsei_batch_destroy", "fsei_batch_size", "fsei_batch_step", "fsei_set_kernel_timing",
            "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version")
 
 
@@ -98,6 +99,16 @@ def load(path=LIB_PATH):
     lib.fsei_adjoint_step.argtypes = [vp, ctypes.POINTER(State), ctypes.POINTER(StepParams),
                                       ctypes.POINTER(State), vp, vp, vp, vp]
     lib.fsei_adjoint_step.restype = ctypes.c_int
+    lib.fsei_batch_create.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int32, ctypes.POINTER(vp)]
+    lib.fsei_batch_create.restype = ctypes.c_int
+    lib.fsei_batch_destroy.argtypes = [vp]
+    lib.fsei_batch_destroy.restype = None
+    lib.fsei_batch_size.argtypes = [vp]
+    lib.fsei_batch_size.restype = ctypes.c_int32
+    lib.fsei_batch_step.argtypes = [vp, ctypes.POINTER(State), ctypes.POINTER(vp),
+                                    ctypes.POINTER(StepParams), ctypes.c_int32, vp,
+                                    ctypes.POINTER(StepStats)]
+    lib.fsei_batch_step.restype = ctypes.c_int
     lib.fsei_set_kernel_timing.argtypes = [vp, ctypes.c_int32]
     lib.fsei_set_kernel_timing.restype = ctypes.c_int
     lib.fsei_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -217,6 +228,70 @@ def adjoint_step(grid, fwd, adj, fbar=None, re=100.0, dt=1e-3, gamma=1.5, rho=-0
     _check(lib.fsei_adjoint_step(grid.handle, ctypes.byref(f), ctypes.byref(prm),
                                  ctypes.byref(a), _ptr(fb[0]), _ptr(fb[1]), _ptr(fb[2]),
                                  _stream_handle(stream)))
+
+
+def _desc(nx, ny, nz, lx, ly, zbc=FSEI_Z_WALLS, lz=2.0, stretch=0.0, prec=FSEI_FP64,
+          near_zero_tau=0.0):
+    d = GridDesc()
+    d.nx, d.ny, d.nz = nx, ny, nz
+    d.lx, d.ly, d.zbc, d.lz, d.stretch = lx, ly, zbc, lz, stretch
+    d.prec = prec
+    d.near_zero_tau = near_zero_tau
+    return d
+
+
+class Batch:
+    """Owning wrapper of an fsei_batch (fsei_batch_create / destroy).
+    boxes: list of dicts with the fsei.Grid keyword arguments."""
+
+    def __init__(self, boxes):
+        lib = load()
+        arr = (GridDesc * len(boxes))(*[_desc(**b) for b in boxes])
+        h = ctypes.c_void_p()
+        _check(lib.fsei_batch_create(arr, len(boxes), ctypes.byref(h)))
+        self.handle = h
+        self.n = len(boxes)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().fsei_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_step(batch, states, forces, params, nsteps=1, stream=None, stats=True):
+    """fsei_batch_step.  states: list of state dicts (as for step); forces:
+    None or list of None / (fx, fy, fz); params: list of dicts with re, dt,
+    cfl, gamma, rho, fconst.  Returns the per-box statistics when stats."""
+    lib = load()
+    n = batch.n
+    st = (State * n)()
+    for i, s in enumerate(states):
+        st[i] = State(_ptr(s["u"]), _ptr(s["v"]), _ptr(s["w"]), _ptr(s["p"]), _ptr(s["hu"]),
+                      _ptr(s["hv"]), _ptr(s["hw"]), int(s.get("have_prev_h", 0)))
+    fp = None
+    if forces is not None:
+        fp = (ctypes.c_void_p * (3 * n))()
+        for i, f in enumerate(forces):
+            for c in range(3):
+                fp[3 * i + c] = None if f is None else f[c].data_ptr()
+    prm = (StepParams * n)()
+    for i, p in enumerate(params):
+        prm[i] = StepParams(p.get("re", 100.0), p.get("dt", 0.0), p.get("cfl", 0.0),
+                            p.get("gamma", 1.5), p.get("rho", -0.5),
+                            (ctypes.c_double * 3)(*p.get("fconst", (0.0, 0.0, 0.0))))
+    out = (StepStats * n)() if stats else None
+    status = lib.fsei_batch_step(batch.handle, st, fp, prm, int(nsteps), _stream_handle(stream),
+                                 out)
+    for i, s in enumerate(states):
+        s["have_prev_h"] = st[i].have_prev_h
+    _check(status)
+    return [o.as_dict() for o in out] if out is not None else None
 
 
 def set_kernel_timing(grid, enable):

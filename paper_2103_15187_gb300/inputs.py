@@ -278,3 +278,34 @@ def case_periodic_random(n=32, seed=0, re=1000.0, cfl=0.5, steps=100,
     return Case("periodic_random_%d" % n, n, n, n, 2 * np.pi, 2 * np.pi,
                 Z_PERIODIC, 2 * np.pi, 0.0, re, 0.0, cfl, steps, u * s, v * s,
                 w * s, np.zeros_like(u))
+
+
+ENSEMBLE_SIZES = ((32, 32, 32), (64, 64, 64), (96, 96, 128), (128, 128, 192))
+
+
+def case_ensemble(nboxes=64, seed=5, steps=100, sizes=ENSEMBLE_SIZES):
+    """Ensemble of independent boxes of uneven sizes: sizes drawn uniformly
+    from `sizes` (box-mix seed), box b seeded with 5000 + b.  Cubes of side
+    32 or 64 are triply periodic 2 pi boxes with a Taylor-Green or a random
+    solenoidal field (coin flip; the random one scaled to the Taylor-Green
+    kinetic energy); the others are stretched channels (Poiseuille plus
+    perturbation, RMS 0.1, |k| in [1, 8]).  Re log-uniform in [500, 4000],
+    CFL 0.5."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    picks = rng.integers(0, len(sizes), nboxes)
+    cases = []
+    for b in range(nboxes):
+        nx, ny, nz = sizes[int(picks[b])]
+        brng = np.random.Generator(np.random.PCG64(5000 + b))
+        re = float(np.exp(brng.uniform(np.log(500.0), np.log(4000.0))))
+        if nx == ny == nz and nx <= 64:
+            if brng.uniform() < 0.5:
+                c = case_taylor_green(nx, steps=steps, re=re)
+                c.cfl, c.dt = 0.5, 0.0
+            else:
+                c = case_periodic_random(nx, seed=5000 + b, re=re, steps=steps)
+        else:
+            c = case_channel(nx, ny, nz, re=re, steps=steps, seed=5000 + b)
+        c.name = "box%02d_%s" % (b, c.name)
+        cases.append(c)
+    return cases
