@@ -254,6 +254,7 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     set_smem_limits_sweep<T>(g, W);
     set_smem_limits_poisson<T>(g, W);
     set_smem_limits_adjoint<T>(g, W);
+    preload_project<T>();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FSEI_E_CUDA, "grid setup: %s", cudaGetErrorString(e));
     return FSEI_OK;
@@ -622,7 +623,8 @@ void batch_clear_graphs(fsei_batch_s *B) {
 fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const *forces,
                           const fsei_step_params *prm, bool first, cudaGraphExec_t *out) {
     cudaStream_t cs = B->capture;
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    cudaGetLastError();
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
         return fail(FSEI_E_CUDA, "batch: cannot begin graph capture");
     cudaEventRecord(B->fork, cs);
     for (cudaStream_t b : B->branches) cudaStreamWaitEvent(b, B->fork, 0);
@@ -641,6 +643,11 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
         const void *f2 = forces ? forces[3 * i + 2] : nullptr;
         r = G->prec == FSEI_FP64 ? run_steps<double>(G, G->wd, &s, f0, f1, f2, a, 1, st, first)
                                  : run_steps<float>(G, G->wf, &s, f0, f1, f2, a, 1, st, first);
+        if (r != FSEI_OK) {
+            const std::string msg = g_err;
+            r = fail(r, "batch capture, box %zu (%s graph): %s", i, first ? "first" : "rest",
+                     msg.c_str());
+        }
     }
     for (size_t b = 0; b < B->branches.size(); ++b) {
         cudaEventRecord(B->joins[b], B->branches[b]);

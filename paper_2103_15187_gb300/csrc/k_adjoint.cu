@@ -319,6 +319,11 @@ void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T 
 }
 
 template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<T> &W) {
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_adj_phibar<T>);
+    cudaFuncGetAttributes(&fa, k_adj_ustar<T>);
+    cudaFuncGetAttributes(&fa, k_adj_hist<T>);
+    cudaFuncGetAttributes(&fa, k_adj_gather<T>);
     cudaFuncSetAttribute(k_sweep_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_sweep_x(g, W));
 }

@@ -126,6 +126,13 @@ template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, 
                                                            rows);
 }
 
+template <typename T> void preload_project() {
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_project<T>);
+}
+template void preload_project<float>();
+template void preload_project<double>();
+
 template void launch_project<float>(const GridDev &, const Fields<float> &, Work<float> &,
                                     StepScalars *, cudaStream_t);
 template void launch_project<double>(const GridDev &, const Fields<double> &, Work<double> &,

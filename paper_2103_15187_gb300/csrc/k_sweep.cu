@@ -459,6 +459,12 @@ template <typename T> void launch_sweep_z_adjoint(const GridDev &g, Work<T> &W, 
 }
 
 template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T> &W) {
+    // load every kernel of this file now: a kernel loaded lazily at its first
+    // launch cannot be loaded inside a stream capture
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_speed<T>);
+    cudaFuncGetAttributes(&fa, k_scalars);
+    cudaFuncGetAttributes(&fa, k_plans<T>);
     const int P = W.plan[2].P > W.plan[3].P ? W.plan[2].P : W.plan[3].P;
     cudaFuncSetAttribute(k_rhs_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_rhs_x(g, W));

@@ -66,6 +66,7 @@ void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T 
                          const T *w, T *ub, T *vb, T *wb, T *pb, T *hbu, T *hbv, T *hbw, T *fbx,
                          T *fby, T *fbz, double re, cudaStream_t st);
 template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<T> &W);
+template <typename T> void preload_project();
 template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                           StepScalars *sc, cudaStream_t st);
 
