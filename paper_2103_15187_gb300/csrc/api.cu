@@ -105,7 +105,20 @@ struct KernelTimer {
         }
         return pool[i];
     }
+    // while capturing a graph: the first launch group that raised an error
+    bool check = false;
+    int fail_kind = -1;
+    cudaError_t fail_err = cudaSuccess;
     template <class F> void run(int kind, cudaStream_t st, F &&f) {
+        if (check) {
+            f();
+            const cudaError_t e = cudaPeekAtLastError();
+            if (e != cudaSuccess && fail_kind < 0) {
+                fail_kind = kind;
+                fail_err = e;
+            }
+            return;
+        }
         if (!on) { f(); return; }
         const size_t i = kinds.size();
         cudaEventRecord(ev(2 * i), st);
@@ -624,10 +637,25 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
                           const fsei_step_params *prm, bool first, cudaGraphExec_t *out) {
     cudaStream_t cs = B->capture;
     cudaGetLastError();
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
-        return fail(FSEI_E_CUDA, "batch: cannot begin graph capture");
-    cudaEventRecord(B->fork, cs);
-    for (cudaStream_t b : B->branches) cudaStreamWaitEvent(b, B->fork, 0);
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess)
+        return fail(FSEI_E_CUDA, "batch: cannot begin graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaEventRecord(B->fork, cs);
+    if (ce != cudaSuccess) {
+        cudaGraph_t gdead = nullptr;
+        cudaStreamEndCapture(cs, &gdead);
+        if (gdead) cudaGraphDestroy(gdead);
+        return fail(FSEI_E_CUDA, "batch: fork record: %s", cudaGetErrorString(ce));
+    }
+    for (cudaStream_t b : B->branches) {
+        ce = cudaStreamWaitEvent(b, B->fork, 0);
+        if (ce != cudaSuccess) {
+            cudaGraph_t gdead = nullptr;
+            cudaStreamEndCapture(cs, &gdead);
+            if (gdead) cudaGraphDestroy(gdead);
+            return fail(FSEI_E_CUDA, "batch: fork wait: %s", cudaGetErrorString(ce));
+        }
+    }
     fsei_status r = FSEI_OK;
     for (size_t i = 0; i < B->grids.size() && r == FSEI_OK; ++i) {
         fsei_grid_s *G = B->grids[i];
@@ -641,12 +669,17 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
         const void *f0 = forces ? forces[3 * i] : nullptr;
         const void *f1 = forces ? forces[3 * i + 1] : nullptr;
         const void *f2 = forces ? forces[3 * i + 2] : nullptr;
+        G->timer.check = true;
+        G->timer.fail_kind = -1;
         r = G->prec == FSEI_FP64 ? run_steps<double>(G, G->wd, &s, f0, f1, f2, a, 1, st, first)
                                  : run_steps<float>(G, G->wf, &s, f0, f1, f2, a, 1, st, first);
+        G->timer.check = false;
         if (r != FSEI_OK) {
             const std::string msg = g_err;
-            r = fail(r, "batch capture, box %zu (%s graph): %s", i, first ? "first" : "rest",
-                     msg.c_str());
+            r = fail(r, "batch capture, box %zu (%s graph), first failing launch: %s (%s); %s", i,
+                     first ? "first" : "rest",
+                     G->timer.fail_kind >= 0 ? kKernelNames[G->timer.fail_kind] : "-",
+                     cudaGetErrorString(G->timer.fail_err), msg.c_str());
         }
     }
     for (size_t b = 0; b < B->branches.size(); ++b) {
