@@ -324,8 +324,7 @@ template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<
     cudaFuncGetAttributes(&fa, k_adj_ustar<T>);
     cudaFuncGetAttributes(&fa, k_adj_hist<T>);
     cudaFuncGetAttributes(&fa, k_adj_gather<T>);
-    cudaFuncSetAttribute(k_sweep_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_sweep_x(g, W));
+    cudaFuncSetAttribute(k_sweep_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
 }
 
 #define FSEI_INST(T)                                                                           \

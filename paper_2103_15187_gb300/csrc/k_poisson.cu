@@ -325,20 +325,13 @@ template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, 
 
 template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<T> &W) {
     (void)0;  // every kernel of this file gets an attribute below, which loads it
-    cudaFuncSetAttribute(k_rfft_x<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_fft_x(g, W));
-    cudaFuncSetAttribute(k_rfft_x<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_fft_x(g, W));
-    cudaFuncSetAttribute(k_irfft_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_fft_x(g, W));
-    cudaFuncSetAttribute(k_fft_y<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_fft_y(g, W));
-    cudaFuncSetAttribute(k_fft_y<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_fft_y(g, W));
-    cudaFuncSetAttribute(k_poisson_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_poisson(g, W));
-    cudaFuncSetAttribute(k_poisson_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_exact(g.nz, exact_chunks(g.nz)));
+    cudaFuncSetAttribute(k_rfft_x<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    cudaFuncSetAttribute(k_rfft_x<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    cudaFuncSetAttribute(k_irfft_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    cudaFuncSetAttribute(k_fft_y<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    cudaFuncSetAttribute(k_fft_y<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    cudaFuncSetAttribute(k_poisson_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    cudaFuncSetAttribute(k_poisson_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
 }
 
 #define FSEI_INST(T)                                                                           \

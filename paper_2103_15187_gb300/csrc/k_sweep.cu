@@ -465,15 +465,12 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     cudaFuncGetAttributes(&fa, k_speed<T>);
     cudaFuncGetAttributes(&fa, k_scalars);
     cudaFuncGetAttributes(&fa, k_plans<T>);
-    const int P = W.plan[2].P > W.plan[3].P ? W.plan[2].P : W.plan[3].P;
-    cudaFuncSetAttribute(k_rhs_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_rhs_x(g, W));
-    cudaFuncSetAttribute(k_sweep_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_sweep<T>(g.ny, W, W.plan[1].P));
-    cudaFuncSetAttribute(k_sweep_z<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_sweep<T>(g.nz, W, P));
-    cudaFuncSetAttribute(k_sweep_z<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_sweep<T>(g.nz, W, P));
+    (void)g;
+    (void)W;
+    cudaFuncSetAttribute(k_rhs_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    cudaFuncSetAttribute(k_sweep_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    cudaFuncSetAttribute(k_sweep_z<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    cudaFuncSetAttribute(k_sweep_z<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
 }
 
 #define FSEI_INST(T)                                                                           \

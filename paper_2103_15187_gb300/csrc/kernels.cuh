@@ -70,6 +70,17 @@ template <typename T> void preload_project();
 template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                           StepScalars *sc, cudaStream_t st);
 
+// Largest dynamic shared memory a block may opt into on the current device.
+// Every kernel's MaxDynamicSharedMemorySize attribute is raised to it: the
+// attribute is per kernel and process-wide, so a value sized for one grid
+// would cap the launches of another grid of the same kernel.
+inline int smem_optin() {
+    int dev = 0, v = 48 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
 // dynamic shared memory bytes of each kernel (host-side sizing helpers)
 template <typename T> size_t smem_rhs_x(const GridDev &g, const Work<T> &W);
 template <typename T> size_t smem_sweep(int n, const Work<T> &W, int P);
