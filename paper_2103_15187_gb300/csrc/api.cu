@@ -465,6 +465,7 @@ void fsei_grid_destroy(fsei_grid G) {
     if (G->sc_host) cudaFreeHost(G->sc_host);
     G->mem.release();
     delete G;
+    cudaGetLastError();   // teardown leaves no error behind for later calls
 }
 
 int64_t fsei_grid_workspace_bytes(fsei_grid G) { return G ? (int64_t)G->mem.bytes : 0; }
@@ -473,6 +474,7 @@ fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy
                       const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,
                       fsei_step_stats *out) {
     g_err.clear();
+    cudaGetLastError();   // an error left by an unrelated earlier call is not ours
     if (!G || !s || !prm) return fail(FSEI_E_ARG, "fsei_step: NULL argument");
     if (nsteps < 0) return fail(FSEI_E_ARG, "nsteps < 0");
     const void *req[7] = {s->u, s->v, s->w, s->p, s->hu, s->hv, s->hw};
@@ -519,6 +521,7 @@ fsei_status fsei_adjoint_step(fsei_grid G, const fsei_state *fwd, const fsei_ste
                               fsei_state *adj, void *fbar_x, void *fbar_y, void *fbar_z,
                               void *cuda_stream) {
     g_err.clear();
+    cudaGetLastError();   // an error left by an unrelated earlier call is not ours
     if (!G || !fwd || !prm || !adj) return fail(FSEI_E_ARG, "fsei_adjoint_step: NULL argument");
     const void *fw[3] = {fwd->u, fwd->v, fwd->w};
     for (int i = 0; i < 3; ++i)
@@ -566,6 +569,7 @@ fsei_status fsei_adjoint_step(fsei_grid G, const fsei_state *fwd, const fsei_ste
 
 fsei_status fsei_poisson_solve(fsei_grid G, const void *rhs, void *phi, void *cuda_stream) {
     g_err.clear();
+    cudaGetLastError();   // an error left by an unrelated earlier call is not ours
     if (!G || !rhs || !phi) return fail(FSEI_E_ARG, "fsei_poisson_solve: NULL argument");
     if (!aligned16(rhs) || !aligned16(phi)) return fail(FSEI_E_ARG, "rhs/phi not 16-byte aligned");
     DeviceGuard dg(G->device);
@@ -748,6 +752,7 @@ void fsei_batch_destroy(fsei_batch B) {
     if (B->fork) cudaEventDestroy(B->fork);
     for (fsei_grid g : B->grids) fsei_grid_destroy(g);
     delete B;
+    cudaGetLastError();
 }
 
 int32_t fsei_batch_size(fsei_batch B) { return B ? (int32_t)B->grids.size() : 0; }
@@ -756,6 +761,7 @@ fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const 
                             const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,
                             fsei_step_stats *out) {
     g_err.clear();
+    cudaGetLastError();   // an error left by an unrelated earlier call is not ours
     if (!B || !states || !prm) return fail(FSEI_E_ARG, "fsei_batch_step: NULL argument");
     if (nsteps < 0) return fail(FSEI_E_ARG, "nsteps < 0");
     const size_t nb = B->grids.size();

@@ -324,7 +324,7 @@ template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<
     cudaFuncGetAttributes(&fa, k_adj_ustar<T>);
     cudaFuncGetAttributes(&fa, k_adj_hist<T>);
     cudaFuncGetAttributes(&fa, k_adj_gather<T>);
-    cudaFuncSetAttribute(k_sweep_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    raise_smem_limit(k_sweep_x<T>);
 }
 
 #define FSEI_INST(T)                                                                           \

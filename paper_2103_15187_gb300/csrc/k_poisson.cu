@@ -325,13 +325,13 @@ template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, 
 
 template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<T> &W) {
     (void)0;  // every kernel of this file gets an attribute below, which loads it
-    cudaFuncSetAttribute(k_rfft_x<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-    cudaFuncSetAttribute(k_rfft_x<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-    cudaFuncSetAttribute(k_irfft_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-    cudaFuncSetAttribute(k_fft_y<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-    cudaFuncSetAttribute(k_fft_y<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-    cudaFuncSetAttribute(k_poisson_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-    cudaFuncSetAttribute(k_poisson_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    raise_smem_limit(k_rfft_x<T, 0>);
+    raise_smem_limit(k_rfft_x<T, 1>);
+    raise_smem_limit(k_irfft_x<T>);
+    raise_smem_limit(k_fft_y<T, 1>);
+    raise_smem_limit(k_fft_y<T, -1>);
+    raise_smem_limit(k_poisson_z<T>);
+    raise_smem_limit(k_poisson_exact<T>);
 }
 
 #define FSEI_INST(T)                                                                           \

@@ -467,10 +467,10 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     cudaFuncGetAttributes(&fa, k_plans<T>);
     (void)g;
     (void)W;
-    cudaFuncSetAttribute(k_rhs_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-    cudaFuncSetAttribute(k_sweep_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-    cudaFuncSetAttribute(k_sweep_z<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-    cudaFuncSetAttribute(k_sweep_z<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+    raise_smem_limit(k_rhs_x<T>);
+    raise_smem_limit(k_sweep_y<T>);
+    raise_smem_limit(k_sweep_z<T, 0>);
+    raise_smem_limit(k_sweep_z<T, 1>);
 }
 
 #define FSEI_INST(T)                                                                           \

@@ -81,6 +81,15 @@ inline int smem_optin() {
     return v;
 }
 
+// Raise a kernel's dynamic shared memory limit to what the device allows
+// next to the kernel's static shared memory.
+template <typename F> inline void raise_smem_limit(F *kernel) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_optin() - (int)a.sharedSizeBytes);
+}
+
 // dynamic shared memory bytes of each kernel (host-side sizing helpers)
 template <typename T> size_t smem_rhs_x(const GridDev &g, const Work<T> &W);
 template <typename T> size_t smem_sweep(int n, const Work<T> &W, int P);

@@ -288,6 +288,7 @@ extern "C" fsei_status fsei_poisson_solve_noalloc(const fsei_grid_desc *d, const
         g_dev_scratch[dev] = static_cast<unsigned char *>(p);
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaGetLastError();   // an error left by an unrelated earlier call is not ours
     return d->prec == FSEI_FP64
                ? solve_noalloc<double>(d, rhs, phi, st, g_dev_scratch[dev])
                : solve_noalloc<float>(d, rhs, phi, st, g_dev_scratch[dev]);
