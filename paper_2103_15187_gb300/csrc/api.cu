@@ -201,7 +201,19 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     int Ps[4];
     int ns[4] = {g.nx, g.ny, g.nz, g.walls ? g.nz - 1 : g.nz};
     Ps[0] = 256 / nl_x;
-    Ps[1] = Ps[2] = Ps[3] = 256 / W.tx;
+    {
+        int cy, py, ty, cz, pz, tz, cf, pf, tf;
+        sweep_geometry(ns[1], cy, py, ty);
+        sweep_geometry(ns[2], cz, pz, tz);
+        sweep_geometry(ns[3], cf, pf, tf);
+        Ps[1] = py;
+        Ps[2] = pz;
+        Ps[3] = pf;
+        W.chunk_y = cy;
+        W.tx_y = ty;
+        W.chunk_z = cz > cf ? cz : cf;
+        W.tx_z = tz < tf ? tz : tf;
+    }
     for (int q = 0; q < 4; ++q) {
         if (Ps[q] > ns[q] / 3) Ps[q] = ns[q] / 3;
         if (Ps[q] < 1) Ps[q] = 1;
@@ -265,6 +277,7 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     }
     if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "table allocation failed");
     set_smem_limits_sweep<T>(g, W);
+    set_smem_limits_lines<T>(g, W);
     set_smem_limits_poisson<T>(g, W);
     set_smem_limits_adjoint<T>(g, W);
     preload_project<T>();

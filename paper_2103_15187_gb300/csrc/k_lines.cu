@@ -1,0 +1,237 @@
+// Implicit viscous sweeps along y and z (Sec. 3.1: one tridiagonal system
+// per direction; cyclic in y; Dirichlet walls or cyclic in z) with the
+// partitioned elimination of tri.cuh held in registers.
+//
+// A block owns tx consecutive x columns of one component and one plane (y
+// lines) or one y row (z lines).  Thread (lane, p) owns chunk p of line lane:
+// it loads the chunk straight from global memory (a warp reads tx
+// consecutive x values per row: coalesced), eliminates the chunk interior in
+// registers, writes its two reduced-row right-hand sides to shared memory,
+// and after one thread per line has solved the reduced system recovers the
+// interior in registers and stores it.  Shared memory holds only the plan
+// factors and the reduced systems.
+#include <string.h>
+
+#include "kernels.cuh"
+#include "tri.cuh"
+
+namespace fsei {
+
+namespace {
+
+template <typename T, int L>
+__device__ __forceinline__ void chunk_forward(T (&d)[L], int len, const TriPlan<T> &pl, int s0,
+                                              T &rF, T &rE) {
+    // interior rows 1 .. len-2 of the chunk (positions s0+1 .. s0+len-2)
+    d[1] = pl.inv[s0 + 1] * d[1];
+#pragma unroll
+    for (int i = 2; i < L - 1; ++i)
+        if (i < len - 1) d[i] = pl.inv[s0 + i] * (d[i] - pl.a[s0 + i] * d[i - 1]);
+    // upward pass for the right-hand side part of x_{s0+1}
+    T dh = T(0), dhe = T(0);
+#pragma unroll
+    for (int i = L - 2; i >= 1; --i) {
+        if (i == len - 2) {
+            dh = d[i];
+            dhe = d[i];
+        } else if (i < len - 2) {
+            dh = d[i] - pl.ct[s0 + i] * dh;
+        }
+    }
+    rF = d[0] - pl.c[s0] * dh;
+    T last = d[0];
+#pragma unroll
+    for (int i = 1; i < L; ++i)
+        if (i == len - 1) last = d[i];
+    rE = last - pl.a[s0 + len - 1] * dhe;
+}
+
+template <typename T, int L>
+__device__ __forceinline__ void chunk_backward(T (&d)[L], int len, const TriPlan<T> &pl, int s0,
+                                               T F, T E) {
+    d[0] = F;
+    T x = E;
+#pragma unroll
+    for (int i = L - 1; i >= 1; --i) {
+        if (i == len - 1) {
+            d[i] = E;
+        } else if (i < len - 1) {
+            x = d[i] - pl.at[s0 + i] * F - pl.ct[s0 + i] * x;
+            d[i] = x;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void reduced_solve(T *r, const TriPlan<T> &pl) {
+    const int m = 2 * pl.P;
+    T y = pl.rinv[0] * r[0];
+    r[0] = y;
+    for (int j = 1; j < m; ++j) {
+        y = pl.rinv[j] * (r[j] - pl.rlo[j] * y);
+        r[j] = y;
+    }
+    for (int j = m - 2; j >= 0; --j) {
+        y = r[j] - pl.rcp[j] * y;
+        r[j] = y;
+    }
+    if (pl.cyclic) {
+        const T f = pl.rsc[1] * (r[0] + pl.rsc[0] * r[m - 1]);
+        for (int j = 0; j < m; ++j) r[j] -= pl.rz[j] * f;
+    }
+}
+
+// DIR 1: y lines of plane k.  DIR 2: z lines of row j.
+// MODE (z only): 0 -> q = u^n + solution (step); 1 -> q = W solution
+// (adjoint, W = dz_k for u, v and hc_k for w).
+template <typename T, int L, int DIR, int MODE>
+__global__ void __launch_bounds__(L <= 16 ? 1024 : 512)
+k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
+            T *__restrict__ q2, TriPlan<T> pa, TriPlan<T> pb, int tx) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    const int nx = g.nx, ny = g.ny;
+    const int nxt = (nx + tx - 1) / tx;
+    int b = blockIdx.x;
+    const int xt = b % nxt;
+    b /= nxt;
+    const int outer = DIR == 1 ? g.nz : g.ny;
+    const int row = b % outer;          // k for y lines, j for z lines
+    const int comp = b / outer;
+    const TriPlan<T> &src = (DIR == 2 && comp == 2) ? pb : pa;
+    const int Pmax = pa.P > pb.P ? pa.P : pb.P;
+    const int rs = 2 * Pmax + 1;
+    T *red = sm;
+    const TriPlan<T> pl = stage_plan(src, red + (size_t)tx * rs);
+    T *q = comp == 0 ? q0 : (comp == 1 ? q1 : q2);
+    const size_t stride = DIR == 1 ? (size_t)nx : (size_t)nx * ny;
+    const int t = threadIdx.x;
+    const int l = t % tx, p = t / tx;
+    const int x = xt * tx + l;
+    const bool active = p < pl.P && x < nx;
+    const size_t base = (DIR == 1 ? (size_t)row * ny * nx : (size_t)row * nx) + x +
+                        (size_t)pl.off * stride;
+    int s0 = 0, len = 0;
+    T d[L];
+    if (active) {
+        s0 = chunk_start(p, pl.n, pl.P);
+        len = chunk_start(p + 1, pl.n, pl.P) - s0;
+        const T *qp = q + base + (size_t)s0 * stride;
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < len) d[i] = qp[(size_t)i * stride];
+        T rF, rE;
+        chunk_forward<T, L>(d, len, pl, s0, rF, rE);
+        red[l * rs + 2 * p] = rF;
+        red[l * rs + 2 * p + 1] = rE;
+    }
+    __syncthreads();
+    if (t < tx && xt * tx + t < nx) reduced_solve<T>(red + t * rs, pl);
+    __syncthreads();
+    if (active) {
+        chunk_backward<T, L>(d, len, pl, s0, red[l * rs + 2 * p], red[l * rs + 2 * p + 1]);
+        T *qp = q + base + (size_t)s0 * stride;
+        if (DIR == 1) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < len) qp[(size_t)i * stride] = d[i];
+        } else if (MODE == 0) {
+            const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
+            const T *up = un + base + (size_t)s0 * stride;
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < len) qp[(size_t)i * stride] = up[(size_t)i * stride] + d[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < len) {
+                    const int k = s0 + i + pl.off;
+                    const T wk = comp < 2 ? Metric<T>::dz(g)[k] : T(1) / Metric<T>::ihc(g)[k];
+                    qp[(size_t)i * stride] = wk * d[i];
+                }
+        }
+    }
+}
+
+template <typename T, int L, int DIR, int MODE>
+void launch_reg(const GridDev &g, const Fields<T> &F, Work<T> &W, const TriPlan<T> &pa,
+                const TriPlan<T> &pb, int tx, cudaStream_t st) {
+    const int Pmax = pa.P > pb.P ? pa.P : pb.P;
+    const int nmax = pa.n > pb.n ? pa.n : pb.n;
+    const int threads = ((tx * Pmax + 31) / 32) * 32;
+    const size_t smem = sizeof(T) * ((size_t)tx * (2 * Pmax + 1) + plan_stage_words(nmax, Pmax));
+    const int nxt = (g.nx + tx - 1) / tx;
+    const int outer = DIR == 1 ? g.nz : g.ny;
+    k_sweep_reg<T, L, DIR, MODE><<<3 * outer * nxt, threads, smem, st>>>(
+        g, F, W.q0, W.q1, W.q2, pa, pb, tx);
+}
+
+template <typename T, int DIR, int MODE>
+void dispatch(const GridDev &g, const Fields<T> &F, Work<T> &W, cudaStream_t st) {
+    const TriPlan<T> &pa = DIR == 1 ? W.plan[1] : W.plan[2];
+    const TriPlan<T> &pb = DIR == 1 ? W.plan[1] : W.plan[3];
+    const int chunk = DIR == 1 ? W.chunk_y : W.chunk_z;
+    const int tx = DIR == 1 ? W.tx_y : W.tx_z;
+    if (chunk <= 8) launch_reg<T, 8, DIR, MODE>(g, F, W, pa, pb, tx, st);
+    else if (chunk <= 16) launch_reg<T, 16, DIR, MODE>(g, F, W, pa, pb, tx, st);
+    else launch_reg<T, 32, DIR, MODE>(g, F, W, pa, pb, tx, st);
+}
+
+}  // namespace
+
+// Chunk length and x-tile width of the register sweeps for a line of n
+// unknowns: chunks of at most 16 with up to 1024 threads per block, or of at
+// most 32 (long lines) with up to 512 threads per block.
+void sweep_geometry(int n, int &chunk, int &P, int &tx) {
+    chunk = n <= 512 ? 16 : 32;
+    P = (n + chunk - 1) / chunk;
+    if (P > n / 3) P = n / 3;
+    if (P < 1) P = 1;
+    chunk = (n + P - 1) / P;
+    const int maxthr = chunk <= 16 ? 1024 : 512;
+    tx = 32;
+    while (tx > 1 && tx * P > maxthr) tx /= 2;
+}
+
+template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, cudaStream_t st) {
+    Fields<T> none;
+    memset(&none, 0, sizeof none);
+    dispatch<T, 1, 0>(g, none, W, st);
+}
+
+template <typename T> void launch_sweep_z(const GridDev &g, const Fields<T> &F, Work<T> &W,
+                                          cudaStream_t st) {
+    dispatch<T, 2, 0>(g, F, W, st);
+}
+
+template <typename T> void launch_sweep_z_adjoint(const GridDev &g, Work<T> &W, cudaStream_t st) {
+    Fields<T> none;
+    memset(&none, 0, sizeof none);
+    dispatch<T, 2, 1>(g, none, W, st);
+}
+
+template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T> &W) {
+    (void)g;
+    (void)W;
+    raise_smem_limit(k_sweep_reg<T, 8, 1, 0>);
+    raise_smem_limit(k_sweep_reg<T, 16, 1, 0>);
+    raise_smem_limit(k_sweep_reg<T, 32, 1, 0>);
+    raise_smem_limit(k_sweep_reg<T, 8, 2, 0>);
+    raise_smem_limit(k_sweep_reg<T, 16, 2, 0>);
+    raise_smem_limit(k_sweep_reg<T, 32, 2, 0>);
+    raise_smem_limit(k_sweep_reg<T, 8, 2, 1>);
+    raise_smem_limit(k_sweep_reg<T, 16, 2, 1>);
+    raise_smem_limit(k_sweep_reg<T, 32, 2, 1>);
+}
+
+#define FSEI_INST(T)                                                                           \
+    template void launch_sweep_y<T>(const GridDev &, Work<T> &, cudaStream_t);                 \
+    template void launch_sweep_z<T>(const GridDev &, const Fields<T> &, Work<T> &,             \
+                                    cudaStream_t);                                            \
+    template void launch_sweep_z_adjoint<T>(const GridDev &, Work<T> &, cudaStream_t);         \
+    template void set_smem_limits_lines<T>(const GridDev &, const Work<T> &);
+FSEI_INST(float)
+FSEI_INST(double)
+#undef FSEI_INST
+
+}  // namespace fsei

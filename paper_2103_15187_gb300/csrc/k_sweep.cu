@@ -11,8 +11,7 @@
 //   k_rhs_x       H^n = -div(uu)^n, RHS = dt[gamma H^n + rho H^{n-1}
 //                 + Re^-1 L u^n - G p^n + f], stores H^n, solves
 //                 (I - beta L_x) q = RHS along x
-//   k_sweep_y     (I - beta L_y) r = q along y
-//   k_sweep_z     (I - beta L_z) du = r along z; u* = u^n + du
+// (the y and z sweeps are in k_lines.cu)
 #include <string.h>
 
 #include "kernels.cuh"
@@ -317,78 +316,6 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512)
-k_sweep_y(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2, TriPlan<T> py,
-          int tx) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *sd = reinterpret_cast<T *>(smraw);
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    T *red = sd + (size_t)ny * tx;
-    const int rs = 2 * py.P + 1;
-    const TriPlan<T> pys = stage_plan(py, red + (size_t)tx * rs);
-    const int nxt = (nx + tx - 1) / tx;
-    int b = blockIdx.x;
-    const int xt = b % nxt; b /= nxt;
-    const int k = b % nz;
-    const int comp = b / nz;
-    T *q = comp == 0 ? q0 : (comp == 1 ? q1 : q2);
-    const int x0 = xt * tx;
-    for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
-        const int j = e / tx, l = e - j * tx;
-        sd[e] = (x0 + l < nx) ? q[fid(x0 + l, j, k, nx, ny)] : T(0);
-    }
-    __syncthreads();
-    tri_plan_solve<T, T>(sd, tx, 1, tx, pys, red, rs);
-    for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
-        const int j = e / tx, l = e - j * tx;
-        if (x0 + l < nx) q[fid(x0 + l, j, k, nx, ny)] = sd[e];
-    }
-}
-
-// MODE 0 (step): q = u^n + (I - beta L_z)^-1 q.
-// MODE 1 (adjoint): q = W (I - beta L_z)^-1 q with W = dz_k (u, v) or hc_k
-// (w; 0 on the wall face).
-template <typename T, int MODE>
-__global__ void __launch_bounds__(512)
-k_sweep_z(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
-          TriPlan<T> pzc, TriPlan<T> pzf, int tx) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *sd = reinterpret_cast<T *>(smraw);
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    T *red = sd + (size_t)nz * tx;
-    const int nxt = (nx + tx - 1) / tx;
-    int b = blockIdx.x;
-    const int xt = b % nxt; b /= nxt;
-    const int j = b % ny;
-    const int comp = b / ny;
-    T *q = comp == 0 ? q0 : (comp == 1 ? q1 : q2);
-    const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
-    const int Pmax = pzc.P > pzf.P ? pzc.P : pzf.P;
-    const TriPlan<T> pl = stage_plan(comp < 2 ? pzc : pzf, red + (size_t)tx * (2 * Pmax + 1));
-    const int rs = 2 * pl.P + 1;
-    const int x0 = xt * tx;
-    for (int e = threadIdx.x; e < nz * tx; e += blockDim.x) {
-        const int k = e / tx, l = e - k * tx;
-        sd[e] = (x0 + l < nx) ? q[fid(x0 + l, j, k, nx, ny)] : T(0);
-    }
-    __syncthreads();
-    tri_plan_solve<T, T>(sd, tx, 1, tx, pl, red, rs);
-    for (int e = threadIdx.x; e < nz * tx; e += blockDim.x) {
-        const int k = e / tx, l = e - k * tx;
-        if (x0 + l < nx) {
-            const size_t c = fid(x0 + l, j, k, nx, ny);
-            if (MODE == 0) {
-                q[c] = un[c] + sd[e];
-            } else {
-                const T wk = comp < 2 ? Metric<T>::dz(g)[k]
-                                      : ((g.walls && k == 0) ? T(0) : T(1) / Metric<T>::ihc(g)[k]);
-                q[c] = wk * sd[e];
-            }
-        }
-    }
-}
-
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
@@ -432,32 +359,6 @@ template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Wo
         T(a.fconst[2]), T(1.0 / a.re));
 }
 
-template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, cudaStream_t st) {
-    const int threads = ((W.tx * W.plan[1].P + 31) / 32) * 32;
-    const int nxt = (g.nx + W.tx - 1) / W.tx;
-    k_sweep_y<T><<<3 * g.nz * nxt, threads, smem_sweep<T>(g.ny, W, W.plan[1].P), st>>>(
-        g, W.q0, W.q1, W.q2, W.plan[1], W.tx);
-}
-
-template <typename T> void launch_sweep_z(const GridDev &g, const Fields<T> &F, Work<T> &W,
-                                          cudaStream_t st) {
-    const int P = W.plan[2].P > W.plan[3].P ? W.plan[2].P : W.plan[3].P;
-    const int threads = ((W.tx * P + 31) / 32) * 32;
-    const int nxt = (g.nx + W.tx - 1) / W.tx;
-    k_sweep_z<T, 0><<<3 * g.ny * nxt, threads, smem_sweep<T>(g.nz, W, P), st>>>(
-        g, F, W.q0, W.q1, W.q2, W.plan[2], W.plan[3], W.tx);
-}
-
-template <typename T> void launch_sweep_z_adjoint(const GridDev &g, Work<T> &W, cudaStream_t st) {
-    const int P = W.plan[2].P > W.plan[3].P ? W.plan[2].P : W.plan[3].P;
-    const int threads = ((W.tx * P + 31) / 32) * 32;
-    const int nxt = (g.nx + W.tx - 1) / W.tx;
-    Fields<T> none;
-    memset(&none, 0, sizeof none);
-    k_sweep_z<T, 1><<<3 * g.ny * nxt, threads, smem_sweep<T>(g.nz, W, P), st>>>(
-        g, none, W.q0, W.q1, W.q2, W.plan[2], W.plan[3], W.tx);
-}
-
 template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T> &W) {
     // load every kernel of this file now: a kernel loaded lazily at its first
     // launch cannot be loaded inside a stream capture
@@ -468,9 +369,6 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     (void)g;
     (void)W;
     raise_smem_limit(k_rhs_x<T>);
-    raise_smem_limit(k_sweep_y<T>);
-    raise_smem_limit(k_sweep_z<T, 0>);
-    raise_smem_limit(k_sweep_z<T, 1>);
 }
 
 #define FSEI_INST(T)                                                                           \
@@ -482,10 +380,6 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
                                        const StepArgs &, int, cudaStream_t);                  \
     template void launch_rhs_x<T>(const GridDev &, const Fields<T> &, Work<T> &,               \
                                   const StepScalars *, const StepArgs &, cudaStream_t);       \
-    template void launch_sweep_y<T>(const GridDev &, Work<T> &, cudaStream_t);                 \
-    template void launch_sweep_z<T>(const GridDev &, const Fields<T> &, Work<T> &,             \
-                                    cudaStream_t);                                            \
-    template void launch_sweep_z_adjoint<T>(const GridDev &, Work<T> &, cudaStream_t);         \
     template void set_smem_limits_sweep<T>(const GridDev &, const Work<T> &);
 FSEI_INST(float)
 FSEI_INST(double)

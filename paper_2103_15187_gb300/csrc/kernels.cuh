@@ -30,7 +30,9 @@ template <typename T> struct Work {
     double *nz_scratch;      // unused scratch kept for layout compatibility
     T *adj0, *adj1, *adj2;   // adjoint workspace (allocated on first use)
     int ry;                  // rows per block of the x-line kernels
-    int tx;                  // x columns per block of the y/z sweeps
+    int tx;                  // (unused) x columns of the former shared-memory sweeps
+    int chunk_y, chunk_z;    // register chunk length of the y / z sweeps
+    int tx_y, tx_z;          // x columns per block of the y / z sweeps
     int tkx;                 // kx columns per block of the y FFT / z Poisson
     int pz_poisson;          // chunks per z line in the Poisson solve
 };
@@ -97,6 +99,10 @@ template <typename T> size_t smem_fft_x(const GridDev &g, const Work<T> &W);
 template <typename T> size_t smem_fft_y(const GridDev &g, const Work<T> &W);
 template <typename T> size_t smem_poisson(const GridDev &g, const Work<T> &W);
 template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T> &W);
+template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T> &W);
+// chunk length, chunks per line and x columns per block of the register
+// sweeps for lines of n unknowns
+void sweep_geometry(int n, int &chunk, int &P, int &tx);
 template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<T> &W);
 
 }  // namespace fsei
