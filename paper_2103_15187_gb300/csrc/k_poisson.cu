@@ -21,10 +21,6 @@ namespace fsei {
 
 namespace {
 
-FSEI_D size_t fid(int i, int j, int k, int nx, int ny) {
-    return ((size_t)k * ny + j) * nx + i;
-}
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(512)
 k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
@@ -44,19 +40,23 @@ k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
     const int ku = k == nz - 1 ? 0 : k + 1;
     const T idx = T(g.idx), idy = T(g.idy);
     const T idzk = Metric<T>::idz(g)[k];
-    for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
-        const int r = e / nx, i = e - r * nx, j = j0 + r;
-        const size_t c = fid(i, j, k, nx, ny);
-        T s;
+    for (int r = 0; r < ry; ++r) {
+        const int j = j0 + r, jp = j == ny - 1 ? 0 : j + 1;
+        const size_t oc = ((size_t)k * ny + j) * nx;
+        T *arow = reinterpret_cast<T *>(A + (size_t)r * ls);
         if (MODE == 0) {
-            const int ip = i == nx - 1 ? 0 : i + 1, jp = j == ny - 1 ? 0 : j + 1;
-            const T wku = hasup ? q2[fid(i, j, ku, nx, ny)] : T(0);
-            s = ((q0[fid(ip, j, k, nx, ny)] - q0[c]) * idx + (q1[fid(i, jp, k, nx, ny)] - q1[c]) * idy +
-                 (wku - q2[c]) * idzk) * invdt;
+            const T *a0 = q0 + oc, *a1 = q1 + oc, *a1jp = q1 + ((size_t)k * ny + jp) * nx;
+            const T *a2 = q2 + oc, *a2ku = q2 + ((size_t)ku * ny + j) * nx;
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+                const int ip = i == nx - 1 ? 0 : i + 1;
+                const T wku = hasup ? a2ku[i] : T(0);
+                arow[i] = ((a0[ip] - a0[i]) * idx + (a1jp[i] - a1[i]) * idy + (wku - a2[i]) * idzk) *
+                          invdt;
+            }
         } else {
-            s = src[c];
+            const T *sr = src + oc;
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) arow[i] = sr[i];
         }
-        reinterpret_cast<T *>(A + (size_t)r * ls)[i] = s;
     }
     __syncthreads();
     const cplx<T> *R = fft_lines<T, -1>(A, B, 1, ls, ry, fp, twx, false);
@@ -264,9 +264,10 @@ k_irfft_x(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
     }
     __syncthreads();
     const cplx<T> *R = fft_lines<T, 1>(A, B, 1, ls, ry, fp, twx, false);
-    for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
-        const int r = e / nx, i = e - r * nx;
-        dst[fid(i, j0 + r, k, nx, ny)] = reinterpret_cast<const T *>(R + (size_t)r * ls)[i];
+    for (int r = 0; r < ry; ++r) {
+        T *drow = dst + ((size_t)k * ny + j0 + r) * nx;
+        const T *srow = reinterpret_cast<const T *>(R + (size_t)r * ls);
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) drow[i] = srow[i];
     }
 }
 

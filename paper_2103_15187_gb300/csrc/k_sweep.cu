@@ -21,10 +21,6 @@ namespace fsei {
 
 namespace {
 
-FSEI_D size_t fid(int i, int j, int k, int nx, int ny) {
-    return ((size_t)k * ny + j) * nx + i;
-}
-
 template <typename T>
 __device__ double block_max(double v) {
     __shared__ double wmax[32];
@@ -55,13 +51,15 @@ k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v, const T *__
     T m = T(0);
     for (int r = 0; r < rows; ++r) {
         const int j = j0 + r, jp = j == ny - 1 ? 0 : j + 1;
+        const size_t oc = ((size_t)k * ny + j) * nx;
+        const T *ur = u + oc, *vr = v + oc, *vjp = v + ((size_t)k * ny + jp) * nx, *wr = w + oc,
+                *wkur = w + ((size_t)ku * ny + j) * nx;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const int ip = i == nx - 1 ? 0 : i + 1;
-            const size_t c = fid(i, j, k, nx, ny);
-            const T uc = T(0.5) * (u[c] + u[fid(ip, j, k, nx, ny)]);
-            const T vc = T(0.5) * (v[c] + v[fid(i, jp, k, nx, ny)]);
-            const T wku = hasup ? w[fid(i, j, ku, nx, ny)] : T(0);
-            const T wc = T(0.5) * (w[c] + wku);
+            const T uc = T(0.5) * (ur[i] + ur[ip]);
+            const T vc = T(0.5) * (vr[i] + vjp[i]);
+            const T wku = hasup ? wkur[i] : T(0);
+            const T wc = T(0.5) * (wr[i] + wku);
             m = fmax(m, fabs(uc) * idx + fabs(vc) * idy + fabs(wc) * idzk);
         }
     }
@@ -232,35 +230,51 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
     const T *__restrict__ w = F.w;
     const T *__restrict__ p = F.p;
 
-    for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
-        const int r = e / nx, i = e - r * nx, j = j0 + r;
+    // row base offsets are formed once per row; the inner loop adds only the
+    // 32-bit x offset (wide integer multiplies share GB300's reduced FP64
+    // pipe)
+    for (int r = 0; r < ry; ++r) {
+      const int j = j0 + r;
+      const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
+      const size_t oc = ((size_t)k * ny + j) * nx, ojp = ((size_t)k * ny + jp) * nx,
+                   ojm = ((size_t)k * ny + jm) * nx, oku = ((size_t)ku * ny + j) * nx,
+                   okd = ((size_t)kd * ny + j) * nx, ojpkd = ((size_t)kd * ny + jp) * nx,
+                   ojmku = ((size_t)ku * ny + jm) * nx;
+      const T *uc = u + oc, *ujp_r = u + ojp, *ujm_r = u + ojm, *uku_r = u + oku, *ukd_r = u + okd;
+      const T *vc = v + oc, *vjp_r = v + ojp, *vjm_r = v + ojm, *vku_r = v + oku, *vkd_r = v + okd;
+      const T *vjpkd_r = v + ojpkd;
+      const T *wc = w + oc, *wjp_r = w + ojp, *wjm_r = w + ojm, *wku_r = w + oku, *wkd_r = w + okd;
+      const T *wjmku_r = w + ojmku;
+      const T *pc = p + oc, *pjm_r = p + ojm, *pkd_r = p + okd;
+      T *huc = F.hu + oc, *hvc = F.hv + oc, *hwc = F.hw + oc;
+      const T *fxc = F.fx ? F.fx + oc : nullptr, *fyc = F.fy ? F.fy + oc : nullptr,
+              *fzc = F.fz ? F.fz + oc : nullptr;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
-        const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
-        const size_t c0 = fid(i, j, k, nx, ny);
         // u neighbourhood
-        const T u0 = u[c0], uip = u[fid(ip, j, k, nx, ny)], uim = u[fid(im, j, k, nx, ny)];
-        const T ujp = u[fid(i, jp, k, nx, ny)], ujm = u[fid(i, jm, k, nx, ny)];
-        const T ukp = hasup ? u[fid(i, j, ku, nx, ny)] : z0;
-        const T ukm = hasdn ? u[fid(i, j, kd, nx, ny)] : z0;
-        const T u_ip_jm = u[fid(ip, jm, k, nx, ny)];
-        const T u_ip_kd = hasdn ? u[fid(ip, j, kd, nx, ny)] : z0;
+        const T u0 = uc[i], uip = uc[ip], uim = uc[im];
+        const T ujp = ujp_r[i], ujm = ujm_r[i];
+        const T ukp = hasup ? uku_r[i] : z0;
+        const T ukm = hasdn ? ukd_r[i] : z0;
+        const T u_ip_jm = ujm_r[ip];
+        const T u_ip_kd = hasdn ? ukd_r[ip] : z0;
         // v neighbourhood
-        const T v0 = v[c0], vip = v[fid(ip, j, k, nx, ny)], vim = v[fid(im, j, k, nx, ny)];
-        const T vjp = v[fid(i, jp, k, nx, ny)], vjm = v[fid(i, jm, k, nx, ny)];
-        const T vkp = hasup ? v[fid(i, j, ku, nx, ny)] : z0;
-        const T vkm = hasdn ? v[fid(i, j, kd, nx, ny)] : z0;
-        const T v_im_jp = v[fid(im, jp, k, nx, ny)];
-        const T v_jp_kd = hasdn ? v[fid(i, jp, kd, nx, ny)] : z0;
+        const T v0 = vc[i], vip = vc[ip], vim = vc[im];
+        const T vjp = vjp_r[i], vjm = vjm_r[i];
+        const T vkp = hasup ? vku_r[i] : z0;
+        const T vkm = hasdn ? vkd_r[i] : z0;
+        const T v_im_jp = vjp_r[im];
+        const T v_jp_kd = hasdn ? vjpkd_r[i] : z0;
         // w neighbourhood (w at the bottom wall face is stored as 0)
-        const T w0 = w[c0], wip = w[fid(ip, j, k, nx, ny)], wim = w[fid(im, j, k, nx, ny)];
-        const T wjp = w[fid(i, jp, k, nx, ny)], wjm = w[fid(i, jm, k, nx, ny)];
-        const T wku = hasup ? w[fid(i, j, ku, nx, ny)] : z0;
-        const T wkd = hasdn ? w[fid(i, j, kd, nx, ny)] : z0;
-        const T w_im_ku = hasup ? w[fid(im, j, ku, nx, ny)] : z0;
-        const T w_jm_ku = hasup ? w[fid(i, jm, ku, nx, ny)] : z0;
+        const T w0 = wc[i], wip = wc[ip], wim = wc[im];
+        const T wjp = wjp_r[i], wjm = wjm_r[i];
+        const T wku = hasup ? wku_r[i] : z0;
+        const T wkd = hasdn ? wkd_r[i] : z0;
+        const T w_im_ku = hasup ? wku_r[im] : z0;
+        const T w_jm_ku = hasup ? wjmku_r[i] : z0;
         // p
-        const T p0 = p[c0], pim = p[fid(im, j, k, nx, ny)], pjm = p[fid(i, jm, k, nx, ny)];
-        const T pkd = hasdn ? p[fid(i, j, kd, nx, ny)] : z0;
+        const T p0 = pc[i], pim = pc[im], pjm = pjm_r[i];
+        const T pkd = hasdn ? pkd_r[i] : z0;
 
         // cross fluxes at the cell edges
         const T e_xy = (h * (v0 + vim)) * (h * (u0 + ujm));          // (x_i, y_j)
@@ -288,31 +302,34 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
                      ((ukp - u0) * ihcu - (u0 - ukm) * ihck) * idzk;
         const T Lv = (vip - T(2) * v0 + vim) * idx2 + (vjp - T(2) * v0 + vjm) * idy2 +
                      ((vkp - v0) * ihcu - (v0 - vkm) * ihck) * idzk;
-        const T fx = F.fx ? F.fx[c0] : z0, fy = F.fy ? F.fy[c0] : z0;
-        const T ru = dt * (gam * Hu + rho * F.hu[c0] + inv_re * Lu - (p0 - pim) * idx + fx + fc0);
-        const T rv = dt * (gam * Hv + rho * F.hv[c0] + inv_re * Lv - (p0 - pjm) * idy + fy + fc1);
+        const T fx = fxc ? fxc[i] : z0, fy = fyc ? fyc[i] : z0;
+        const T ru = dt * (gam * Hu + rho * huc[i] + inv_re * Lu - (p0 - pim) * idx + fx + fc0);
+        const T rv = dt * (gam * Hv + rho * hvc[i] + inv_re * Lv - (p0 - pjm) * idy + fy + fc1);
         T rw = z0;
         if (!wall_face) {
             const T Lw = (wip - T(2) * w0 + wim) * idx2 + (wjp - T(2) * w0 + wjm) * idy2 +
                          ((wku - w0) * idzk - (w0 - wkd) * idzd) * ihck;
-            const T fz = F.fz ? F.fz[c0] : z0;
-            rw = dt * (gam * Hw + rho * F.hw[c0] + inv_re * Lw - (p0 - pkd) * ihck + fz + fc2);
+            const T fz = fzc ? fzc[i] : z0;
+            rw = dt * (gam * Hw + rho * hwc[i] + inv_re * Lw - (p0 - pkd) * ihck + fz + fc2);
         }
-        F.hu[c0] = Hu;
-        F.hv[c0] = Hv;
-        F.hw[c0] = Hw;
+        huc[i] = Hu;
+        hvc[i] = Hv;
+        hwc[i] = Hw;
         sd[i * es + r] = ru;
         sd[i * es + ry + r] = rv;
         sd[i * es + 2 * ry + r] = rw;
+      }
     }
     __syncthreads();
     tri_plan_solve<T, T>(sd, es, 1, nl, pxs, red, rs);
-    for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
-        const int r = e / nx, i = e - r * nx;
-        const size_t c0 = fid(i, j0 + r, k, nx, ny);
-        q0[c0] = sd[i * es + r];
-        q1[c0] = sd[i * es + ry + r];
-        q2[c0] = sd[i * es + 2 * ry + r];
+    for (int r = 0; r < ry; ++r) {
+        const size_t o = ((size_t)k * ny + j0 + r) * nx;
+        T *a0 = q0 + o, *a1 = q1 + o, *a2 = q2 + o;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            a0[i] = sd[i * es + r];
+            a1[i] = sd[i * es + ry + r];
+            a2[i] = sd[i * es + 2 * ry + r];
+        }
     }
 }
 
