@@ -200,7 +200,9 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     const int nl_x = 3 * W.ry;
     int Ps[4];
     int ns[4] = {g.nx, g.ny, g.nz, g.walls ? g.nz - 1 : g.nz};
-    Ps[0] = 256 / nl_x;
+    // x chunks: a power of two (warp PCR for the reduced systems)
+    Ps[0] = 1;
+    while (2 * Ps[0] * nl_x <= 256 && 2 * Ps[0] <= 16) Ps[0] *= 2;
     {
         int cy, py, ty, cz, pz, tz, cf, pf, tf;
         sweep_geometry(ns[1], cy, py, ty);
@@ -223,6 +225,7 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
         s.at = M.get<T>(n); s.ct = M.get<T>(n);
         s.rlo = M.get<T>(m); s.rinv = M.get<T>(m); s.rcp = M.get<T>(m);
         s.rz = M.get<T>(m); s.rsc = M.get<T>(2);
+        s.pk1 = M.get<T>(5 * m); s.pk2 = M.get<T>(5 * m); s.pdinv = M.get<T>(m);
         TriPlan<T> &p = W.plan[q];
         p.n = n;
         p.P = Ps[q];
@@ -230,6 +233,10 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
         p.off = (q == 3 && g.walls) ? 1 : 0;
         p.a = s.a; p.c = s.c; p.inv = s.inv; p.at = s.at; p.ct = s.ct;
         p.rlo = s.rlo; p.rinv = s.rinv; p.rcp = s.rcp; p.rz = s.rz; p.rsc = s.rsc;
+        p.pk1 = s.pk1; p.pk2 = s.pk2; p.pdinv = s.pdinv;
+        p.levels = 0;
+        if (m <= 32 && (m & (m - 1)) == 0)
+            while ((1 << p.levels) < m) ++p.levels;
     }
     if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "plan allocation failed");
 

@@ -62,25 +62,6 @@ __device__ __forceinline__ void chunk_backward(T (&d)[L], int len, const TriPlan
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void reduced_solve(T *r, const TriPlan<T> &pl) {
-    const int m = 2 * pl.P;
-    T y = pl.rinv[0] * r[0];
-    r[0] = y;
-    for (int j = 1; j < m; ++j) {
-        y = pl.rinv[j] * (r[j] - pl.rlo[j] * y);
-        r[j] = y;
-    }
-    for (int j = m - 2; j >= 0; --j) {
-        y = r[j] - pl.rcp[j] * y;
-        r[j] = y;
-    }
-    if (pl.cyclic) {
-        const T f = pl.rsc[1] * (r[0] + pl.rsc[0] * r[m - 1]);
-        for (int j = 0; j < m; ++j) r[j] -= pl.rz[j] * f;
-    }
-}
-
 // DIR 1: y lines of plane k.  DIR 2: z lines of row j.
 // MODE (z only): 0 -> q = u^n + solution (step); 1 -> q = W solution
 // (adjoint, W = dz_k for u, v and hc_k for w).
@@ -126,7 +107,7 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
         red[l * rs + 2 * p + 1] = rE;
     }
     __syncthreads();
-    if (t < tx && xt * tx + t < nx) reduced_solve<T>(red + t * rs, pl);
+    reduced_lines<T>(red, rs, tx, pl);
     __syncthreads();
     if (active) {
         chunk_backward<T, L>(d, len, pl, s0, red[l * rs + 2 * p], red[l * rs + 2 * p + 1]);
@@ -180,13 +161,15 @@ void dispatch(const GridDev &g, const Fields<T> &F, Work<T> &W, cudaStream_t st)
 }  // namespace
 
 // Chunk length and x-tile width of the register sweeps for a line of n
-// unknowns: chunks of at most 16 with up to 1024 threads per block, or of at
-// most 32 (long lines) with up to 512 threads per block.
+// unknowns.  P is a power of two (2P <= 32 lets the reduced systems use warp
+// PCR): the smallest with chunks of at most 16, else 16 chunks while they
+// stay <= 32, else 32 chunks (reduced systems by Thomas); at most 1024
+// threads per block for chunks <= 16, 512 above.
 void sweep_geometry(int n, int &chunk, int &P, int &tx) {
-    chunk = n <= 512 ? 16 : 32;
-    P = (n + chunk - 1) / chunk;
-    if (P > n / 3) P = n / 3;
-    if (P < 1) P = 1;
+    P = 1;
+    while (P < 16 && (n + P - 1) / P > 16) P *= 2;
+    if ((n + P - 1) / P > 32) P = 32;
+    while (P > 1 && n / P < 3) P /= 2;
     chunk = (n + P - 1) / P;
     const int maxthr = chunk <= 16 ? 1024 : 512;
     tx = 32;

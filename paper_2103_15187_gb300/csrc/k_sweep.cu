@@ -164,6 +164,32 @@ __global__ void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
         up[2 * p + 1] = cf.c(e0);
     }
     __syncthreads();
+    if (threadIdx.x == 0 && pl.levels > 0) {
+        // parallel cyclic reduction multipliers of the reduced system
+        const int m = 2 * P;
+        double L[32], D[32], U[32], nL[32], nD[32], nU[32];
+        for (int i = 0; i < m; ++i) { L[i] = lo[i]; D[i] = di[i]; U[i] = up[i]; }
+        for (int lev = 0; lev < pl.levels; ++lev) {
+            const int sft = 1 << lev;
+            for (int i = 0; i < m; ++i) {
+                const int im = i - sft, ip = i + sft;
+                const bool hm = pl.cyclic || im >= 0, hp = pl.cyclic || ip < m;
+                const int jm = (im + m) & (m - 1), jp = ip & (m - 1);
+                const double k1 = hm ? -L[i] / D[jm] : 0.0;
+                const double k2 = hp ? -U[i] / D[jp] : 0.0;
+                nD[i] = D[i] + (hm ? k1 * U[jm] : 0.0) + (hp ? k2 * L[jp] : 0.0);
+                nL[i] = hm ? k1 * L[jm] : 0.0;
+                nU[i] = hp ? k2 * U[jp] : 0.0;
+                st.pk1[lev * m + i] = T(k1);
+                st.pk2[lev * m + i] = T(k2);
+            }
+            for (int i = 0; i < m; ++i) { L[i] = nL[i]; D[i] = nD[i]; U[i] = nU[i]; }
+        }
+        // after the last level a cyclic equation couples only to itself
+        for (int i = 0; i < m; ++i)
+            st.pdinv[i] = T(1.0 / (D[i] + (pl.cyclic ? L[i] + U[i] : 0.0)));
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         const int m = 2 * P;
         const double g0 = -di[0];

@@ -32,8 +32,56 @@ template <typename T> FSEI_D T addv(T a, T b) { return a + b; }
 template <typename T> FSEI_D cplx<T> addv(cplx<T> a, cplx<T> b) { return a + b; }
 
 // Shared-memory words needed by stage_plan for a plan of n unknowns and P
-// chunks.
-FSEI_HD int plan_stage_words(int n, int P) { return 5 * n + 8 * P + 2; }
+// chunks (factors, reduced LU, PCR multipliers of up to 5 levels).
+FSEI_HD int plan_stage_words(int n, int P) { return 5 * n + 8 * P + 2 + 22 * P; }
+
+// Reduced system of one line solved by one warp with parallel cyclic
+// reduction (lane i holds unknown i; 2P <= 32, a power of two).  Every lane
+// of the warp must call it.
+template <typename T>
+__device__ __forceinline__ void pcr_warp_solve(T *r, const TriPlan<T> &pl, int lane) {
+    const int m = 2 * pl.P;
+    T x = lane < m ? r[lane] : T(0);
+    for (int lev = 0; lev < pl.levels; ++lev) {
+        const int s = 1 << lev;
+        const T xm = __shfl_sync(0xffffffffu, x, (lane - s) & (m - 1));
+        const T xp = __shfl_sync(0xffffffffu, x, (lane + s) & (m - 1));
+        if (lane < m) x = x + pl.pk1[lev * m + lane] * xm + pl.pk2[lev * m + lane] * xp;
+    }
+    if (lane < m) r[lane] = x * pl.pdinv[lane];
+}
+
+// Solve the reduced systems of lines 0..nl-1 (line l at red + l * rs): one
+// warp per line in turn when the plan has PCR multipliers, else one thread
+// per line with Thomas' algorithm (plus Sherman-Morrison when cyclic).
+template <typename T>
+__device__ __forceinline__ void reduced_lines(T *red, int rs, int nl, const TriPlan<T> &pl) {
+    if (pl.levels > 0) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int l = wid; l < nl; l += nw) pcr_warp_solve(red + l * rs, pl, lane);
+        return;
+    }
+    const int t = threadIdx.x;
+    if (t < nl) {
+        T *r = red + t * rs;
+        const int m = 2 * pl.P;
+        T y = pl.rinv[0] * r[0];
+        r[0] = y;
+        for (int j = 1; j < m; ++j) {
+            y = pl.rinv[j] * (r[j] - pl.rlo[j] * y);
+            r[j] = y;
+        }
+        for (int j = m - 2; j >= 0; --j) {
+            y = r[j] - pl.rcp[j] * y;
+            r[j] = y;
+        }
+        if (pl.cyclic) {
+            const T f = pl.rsc[1] * (r[0] + pl.rsc[0] * r[m - 1]);
+            for (int j = 0; j < m; ++j) r[j] -= pl.rz[j] * f;
+        }
+    }
+}
 
 // Copy a plan's factors into shared memory (every thread of the block calls
 // it; ends with a barrier) and return a plan that points there.
@@ -43,6 +91,7 @@ __device__ TriPlan<T> stage_plan(const TriPlan<T> &in, T *sm) {
     TriPlan<T> out = in;
     T *a = sm, *c = a + n, *inv = c + n, *at = inv + n, *ct = at + n;
     T *rlo = ct + n, *rinv = rlo + m, *rcp = rinv + m, *rz = rcp + m, *rsc = rz + m;
+    T *pk1 = rsc + 2, *pk2 = pk1 + 5 * m, *pdinv = pk2 + 5 * m;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         a[i] = in.a[i];
         c[i] = in.c[i];
@@ -57,9 +106,17 @@ __device__ TriPlan<T> stage_plan(const TriPlan<T> &in, T *sm) {
         rz[i] = in.cyclic ? in.rz[i] : T(0);
     }
     if (threadIdx.x < 2) rsc[threadIdx.x] = in.cyclic ? in.rsc[threadIdx.x] : T(0);
+    if (in.levels > 0) {
+        for (int i = threadIdx.x; i < in.levels * m; i += blockDim.x) {
+            pk1[i] = in.pk1[i];
+            pk2[i] = in.pk2[i];
+        }
+        for (int i = threadIdx.x; i < m; i += blockDim.x) pdinv[i] = in.pdinv[i];
+    }
     __syncthreads();
     out.a = a; out.c = c; out.inv = inv; out.at = at; out.ct = ct;
     out.rlo = rlo; out.rinv = rinv; out.rcp = rcp; out.rz = rz; out.rsc = rsc;
+    out.pk1 = pk1; out.pk2 = pk2; out.pdinv = pdinv;
     return out;
 }
 
@@ -105,24 +162,7 @@ __device__ void tri_plan_solve(V *s, int es, int ls, int nl, const TriPlan<T> &p
         red[l * rs + 2 * p + 1] = nmad(pl.a[e0], dhe, d[e0 * es]);
     }
     __syncthreads();
-    if (t < nl) {
-        V *r = red + t * rs;
-        const int m = 2 * P;
-        V y = scl(pl.rinv[0], r[0]);
-        r[0] = y;
-        for (int j = 1; j < m; ++j) {
-            y = scl(pl.rinv[j], nmad(pl.rlo[j], y, r[j]));
-            r[j] = y;
-        }
-        for (int j = m - 2; j >= 0; --j) {
-            y = nmad(pl.rcp[j], y, r[j]);
-            r[j] = y;
-        }
-        if (pl.cyclic) {
-            const V f = scl(pl.rsc[1], addv(r[0], scl(pl.rsc[0], r[m - 1])));
-            for (int j = 0; j < m; ++j) r[j] = nmad(pl.rz[j], f, r[j]);
-        }
-    }
+    reduced_lines<T>(red, rs, nl, pl);
     __syncthreads();
     if (active) {
         const V F = red[l * rs + 2 * p], E = red[l * rs + 2 * p + 1];
