@@ -370,6 +370,8 @@ fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
     if (ny < 4 || ny % 2 || !is_2a3b(ny) || ny > 1024)
         return fail(FSEI_E_SHAPE, "ny = %d: need ny even, 2^a 3^b in [4, 1024]", ny);
     if (nz < 8 || nz > 2048) return fail(FSEI_E_SHAPE, "nz = %d: need 8 <= nz <= 2048", nz);
+    if ((long long)nx * ny * nz > 0x7fffffffLL)
+        return fail(FSEI_E_SHAPE, "%d x %d x %d cells: a field must hold fewer than 2^31 values", nx, ny, nz);
     if (!(d->lx > 0) || !(d->ly > 0)) return fail(FSEI_E_ARG, "lx, ly must be > 0");
     if (d->zbc != FSEI_Z_PERIODIC && d->zbc != FSEI_Z_WALLS) return fail(FSEI_E_ARG, "bad zbc %d", d->zbc);
     if (d->prec != FSEI_FP64 && d->prec != FSEI_MIXED) return fail(FSEI_E_ARG, "bad prec %d", d->prec);

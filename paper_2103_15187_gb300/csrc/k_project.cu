@@ -35,37 +35,33 @@ k_project(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict_
     for (int r = 0; r < rows; ++r) {
         const int j = j0 + r;
         const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
-        // row base offsets once per row (no wide multiplies in the x loop)
-        const size_t oc = ((size_t)k * ny + j) * nx, ojm = ((size_t)k * ny + jm) * nx,
-                     ojp = ((size_t)k * ny + jp) * nx, okd = ((size_t)kd * ny + j) * nx,
-                     oku = ((size_t)ku * ny + j) * nx;
-        const T *fc = phi + oc, *fjm_r = phi + ojm, *fjp_r = phi + ojp, *fkd_r = phi + okd,
-                *fku_r = phi + oku;
-        const T *q0c = q0 + oc, *q1c = q1 + oc, *q2c = q2 + oc, *q1jp = q1 + ojp, *q2ku = q2 + oku;
-        T *uc = F.u + oc, *vc = F.v + oc, *wc = F.w + oc, *pc = F.p + oc;
+        // 32-bit row offsets once per row (no wide multiplies in the x loop)
+        const int oc = (k * ny + j) * nx, ojm = (k * ny + jm) * nx, ojp = (k * ny + jp) * nx,
+                  okd = (kd * ny + j) * nx, oku = (ku * ny + j) * nx;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
-            const T f0 = fc[i];
-            const T fim = fc[im], fip = fc[ip];
-            const T fjm = fjm_r[i], fjp = fjp_r[i];
-            const T fkd = hasdn ? fkd_r[i] : T(0);
-            const T fku = hasup ? fku_r[i] : T(0);
-            const T un = q0c[i] - dt * (f0 - fim) * idx;
-            const T vn = q1c[i] - dt * (f0 - fjm) * idy;
-            const T wn = hasdn ? q2c[i] - dt * (f0 - fkd) * ihck : T(0);
+            const int c = oc + i;
+            const T f0 = phi[c];
+            const T fim = phi[oc + im], fip = phi[oc + ip];
+            const T fjm = phi[ojm + i], fjp = phi[ojp + i];
+            const T fkd = hasdn ? phi[okd + i] : T(0);
+            const T fku = hasup ? phi[oku + i] : T(0);
+            const T un = q0[c] - dt * (f0 - fim) * idx;
+            const T vn = q1[c] - dt * (f0 - fjm) * idy;
+            const T wn = hasdn ? q2[c] - dt * (f0 - fkd) * ihck : T(0);
             const T fup = hasup ? (fku - f0) * ihcu : T(0);
             const T fdn = hasdn ? (f0 - fkd) * ihck : T(0);
             const T lphi = (fip - T(2) * f0 + fim) * idx2 + (fjp - T(2) * f0 + fjm) * idy2 +
                            (fup - fdn) * idzk;
-            const T pn = pc[i] + f0 - beta * lphi;
-            uc[i] = un;
-            vc[i] = vn;
-            wc[i] = wn;
-            pc[i] = pn;
+            const T pn = F.p[c] + f0 - beta * lphi;
+            F.u[c] = un;
+            F.v[c] = vn;
+            F.w[c] = wn;
+            F.p[c] = pn;
             // neighbours of the new state needed by the cell-centre statistics
-            const T uip = q0c[ip] - dt * (fip - f0) * idx;
-            const T vjp = q1jp[i] - dt * (fjp - f0) * idy;
-            const T wku = hasup ? q2ku[i] - dt * (fku - f0) * ihcu : T(0);
+            const T uip = q0[oc + ip] - dt * (fip - f0) * idx;
+            const T vjp = q1[ojp + i] - dt * (fjp - f0) * idy;
+            const T wku = hasup ? q2[oku + i] - dt * (fku - f0) * ihcu : T(0);
             const T di = (uip - un) * idx + (vjp - vn) * idy + (wku - wn) * idzk;
             mdiv = fmax(mdiv, fabs(di));
             const T sp = fabs(T(0.5) * (un + uip)) * idx + fabs(T(0.5) * (vn + vjp)) * idy +

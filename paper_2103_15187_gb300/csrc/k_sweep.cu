@@ -164,33 +164,40 @@ __global__ void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
         up[2 * p + 1] = cf.c(e0);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && pl.levels > 0) {
-        // parallel cyclic reduction multipliers of the reduced system
+    if (pl.levels > 0) {
+        // parallel cyclic reduction multipliers of the reduced system: one
+        // thread per equation, levels separated by barriers (in place over
+        // copies of lo, di, up kept after the LU arrays)
         const int m = 2 * P;
-        double L[32], D[32], U[32], nL[32], nD[32], nU[32];
-        for (int i = 0; i < m; ++i) { L[i] = lo[i]; D[i] = di[i]; U[i] = up[i]; }
+        double *L = up + 2 * P, *D = L + m, *U = D + m;
+        const int i = threadIdx.x;
+        if (i < m) { L[i] = lo[i]; D[i] = di[i]; U[i] = up[i]; }
+        __syncthreads();
         for (int lev = 0; lev < pl.levels; ++lev) {
             const int sft = 1 << lev;
-            for (int i = 0; i < m; ++i) {
+            double nL = 0.0, nD = 0.0, nU = 0.0;
+            if (i < m) {
                 const int im = i - sft, ip = i + sft;
                 const bool hm = pl.cyclic || im >= 0, hp = pl.cyclic || ip < m;
                 const int jm = (im + m) & (m - 1), jp = ip & (m - 1);
                 const double k1 = hm ? -L[i] / D[jm] : 0.0;
                 const double k2 = hp ? -U[i] / D[jp] : 0.0;
-                nD[i] = D[i] + (hm ? k1 * U[jm] : 0.0) + (hp ? k2 * L[jp] : 0.0);
-                nL[i] = hm ? k1 * L[jm] : 0.0;
-                nU[i] = hp ? k2 * U[jp] : 0.0;
+                nD = D[i] + (hm ? k1 * U[jm] : 0.0) + (hp ? k2 * L[jp] : 0.0);
+                nL = hm ? k1 * L[jm] : 0.0;
+                nU = hp ? k2 * U[jp] : 0.0;
                 st.pk1[lev * m + i] = T(k1);
                 st.pk2[lev * m + i] = T(k2);
             }
-            for (int i = 0; i < m; ++i) { L[i] = nL[i]; D[i] = nD[i]; U[i] = nU[i]; }
+            __syncthreads();
+            if (i < m) { L[i] = nL; D[i] = nD; U[i] = nU; }
+            __syncthreads();
         }
         // after the last level a cyclic equation couples only to itself
-        for (int i = 0; i < m; ++i)
-            st.pdinv[i] = T(1.0 / (D[i] + (pl.cyclic ? L[i] + U[i] : 0.0)));
+        if (i < m) st.pdinv[i] = T(1.0 / (D[i] + (pl.cyclic ? L[i] + U[i] : 0.0)));
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // Thomas factors of the reduced system: only needed without PCR
+    if (threadIdx.x == 0 && pl.levels == 0) {
         const int m = 2 * P;
         const double g0 = -di[0];
         const double lo0 = lo[0], upm = up[m - 1];
@@ -256,51 +263,41 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
     const T *__restrict__ w = F.w;
     const T *__restrict__ p = F.p;
 
-    // row base offsets are formed once per row; the inner loop adds only the
-    // 32-bit x offset (wide integer multiplies share GB300's reduced FP64
-    // pipe)
+    // 32-bit row offsets formed once per row (a field holds < 2^31 values);
+    // the loads add them to the field base pointers (no wide multiplies)
     for (int r = 0; r < ry; ++r) {
       const int j = j0 + r;
       const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
-      const size_t oc = ((size_t)k * ny + j) * nx, ojp = ((size_t)k * ny + jp) * nx,
-                   ojm = ((size_t)k * ny + jm) * nx, oku = ((size_t)ku * ny + j) * nx,
-                   okd = ((size_t)kd * ny + j) * nx, ojpkd = ((size_t)kd * ny + jp) * nx,
-                   ojmku = ((size_t)ku * ny + jm) * nx;
-      const T *uc = u + oc, *ujp_r = u + ojp, *ujm_r = u + ojm, *uku_r = u + oku, *ukd_r = u + okd;
-      const T *vc = v + oc, *vjp_r = v + ojp, *vjm_r = v + ojm, *vku_r = v + oku, *vkd_r = v + okd;
-      const T *vjpkd_r = v + ojpkd;
-      const T *wc = w + oc, *wjp_r = w + ojp, *wjm_r = w + ojm, *wku_r = w + oku, *wkd_r = w + okd;
-      const T *wjmku_r = w + ojmku;
-      const T *pc = p + oc, *pjm_r = p + ojm, *pkd_r = p + okd;
-      T *huc = F.hu + oc, *hvc = F.hv + oc, *hwc = F.hw + oc;
-      const T *fxc = F.fx ? F.fx + oc : nullptr, *fyc = F.fy ? F.fy + oc : nullptr,
-              *fzc = F.fz ? F.fz + oc : nullptr;
+      const int oc = (k * ny + j) * nx, ojp = (k * ny + jp) * nx, ojm = (k * ny + jm) * nx,
+                oku = (ku * ny + j) * nx, okd = (kd * ny + j) * nx, ojpkd = (kd * ny + jp) * nx,
+                ojmku = (ku * ny + jm) * nx;
       for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+        const int c0 = oc + i;
         // u neighbourhood
-        const T u0 = uc[i], uip = uc[ip], uim = uc[im];
-        const T ujp = ujp_r[i], ujm = ujm_r[i];
-        const T ukp = hasup ? uku_r[i] : z0;
-        const T ukm = hasdn ? ukd_r[i] : z0;
-        const T u_ip_jm = ujm_r[ip];
-        const T u_ip_kd = hasdn ? ukd_r[ip] : z0;
+        const T u0 = u[c0], uip = u[oc + ip], uim = u[oc + im];
+        const T ujp = u[ojp + i], ujm = u[ojm + i];
+        const T ukp = hasup ? u[oku + i] : z0;
+        const T ukm = hasdn ? u[okd + i] : z0;
+        const T u_ip_jm = u[ojm + ip];
+        const T u_ip_kd = hasdn ? u[okd + ip] : z0;
         // v neighbourhood
-        const T v0 = vc[i], vip = vc[ip], vim = vc[im];
-        const T vjp = vjp_r[i], vjm = vjm_r[i];
-        const T vkp = hasup ? vku_r[i] : z0;
-        const T vkm = hasdn ? vkd_r[i] : z0;
-        const T v_im_jp = vjp_r[im];
-        const T v_jp_kd = hasdn ? vjpkd_r[i] : z0;
+        const T v0 = v[c0], vip = v[oc + ip], vim = v[oc + im];
+        const T vjp = v[ojp + i], vjm = v[ojm + i];
+        const T vkp = hasup ? v[oku + i] : z0;
+        const T vkm = hasdn ? v[okd + i] : z0;
+        const T v_im_jp = v[ojp + im];
+        const T v_jp_kd = hasdn ? v[ojpkd + i] : z0;
         // w neighbourhood (w at the bottom wall face is stored as 0)
-        const T w0 = wc[i], wip = wc[ip], wim = wc[im];
-        const T wjp = wjp_r[i], wjm = wjm_r[i];
-        const T wku = hasup ? wku_r[i] : z0;
-        const T wkd = hasdn ? wkd_r[i] : z0;
-        const T w_im_ku = hasup ? wku_r[im] : z0;
-        const T w_jm_ku = hasup ? wjmku_r[i] : z0;
+        const T w0 = w[c0], wip = w[oc + ip], wim = w[oc + im];
+        const T wjp = w[ojp + i], wjm = w[ojm + i];
+        const T wku = hasup ? w[oku + i] : z0;
+        const T wkd = hasdn ? w[okd + i] : z0;
+        const T w_im_ku = hasup ? w[oku + im] : z0;
+        const T w_jm_ku = hasup ? w[ojmku + i] : z0;
         // p
-        const T p0 = pc[i], pim = pc[im], pjm = pjm_r[i];
-        const T pkd = hasdn ? pkd_r[i] : z0;
+        const T p0 = p[c0], pim = p[oc + im], pjm = p[ojm + i];
+        const T pkd = hasdn ? p[okd + i] : z0;
 
         // cross fluxes at the cell edges
         const T e_xy = (h * (v0 + vim)) * (h * (u0 + ujm));          // (x_i, y_j)
@@ -328,19 +325,19 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
                      ((ukp - u0) * ihcu - (u0 - ukm) * ihck) * idzk;
         const T Lv = (vip - T(2) * v0 + vim) * idx2 + (vjp - T(2) * v0 + vjm) * idy2 +
                      ((vkp - v0) * ihcu - (v0 - vkm) * ihck) * idzk;
-        const T fx = fxc ? fxc[i] : z0, fy = fyc ? fyc[i] : z0;
-        const T ru = dt * (gam * Hu + rho * huc[i] + inv_re * Lu - (p0 - pim) * idx + fx + fc0);
-        const T rv = dt * (gam * Hv + rho * hvc[i] + inv_re * Lv - (p0 - pjm) * idy + fy + fc1);
+        const T fx = F.fx ? F.fx[c0] : z0, fy = F.fy ? F.fy[c0] : z0;
+        const T ru = dt * (gam * Hu + rho * F.hu[c0] + inv_re * Lu - (p0 - pim) * idx + fx + fc0);
+        const T rv = dt * (gam * Hv + rho * F.hv[c0] + inv_re * Lv - (p0 - pjm) * idy + fy + fc1);
         T rw = z0;
         if (!wall_face) {
             const T Lw = (wip - T(2) * w0 + wim) * idx2 + (wjp - T(2) * w0 + wjm) * idy2 +
                          ((wku - w0) * idzk - (w0 - wkd) * idzd) * ihck;
-            const T fz = fzc ? fzc[i] : z0;
-            rw = dt * (gam * Hw + rho * hwc[i] + inv_re * Lw - (p0 - pkd) * ihck + fz + fc2);
+            const T fz = F.fz ? F.fz[c0] : z0;
+            rw = dt * (gam * Hw + rho * F.hw[c0] + inv_re * Lw - (p0 - pkd) * ihck + fz + fc2);
         }
-        huc[i] = Hu;
-        hvc[i] = Hv;
-        hwc[i] = Hw;
+        F.hu[c0] = Hu;
+        F.hv[c0] = Hv;
+        F.hw[c0] = Hw;
         sd[i * es + r] = ru;
         sd[i * es + ry + r] = rv;
         sd[i * es + 2 * ry + r] = rw;
@@ -349,12 +346,11 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
     __syncthreads();
     tri_plan_solve<T, T>(sd, es, 1, nl, pxs, red, rs);
     for (int r = 0; r < ry; ++r) {
-        const size_t o = ((size_t)k * ny + j0 + r) * nx;
-        T *a0 = q0 + o, *a1 = q1 + o, *a2 = q2 + o;
+        const int o = (k * ny + j0 + r) * nx;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            a0[i] = sd[i * es + r];
-            a1[i] = sd[i * es + ry + r];
-            a2[i] = sd[i * es + 2 * ry + r];
+            q0[o + i] = sd[i * es + r];
+            q1[o + i] = sd[i * es + ry + r];
+            q2[o + i] = sd[i * es + 2 * ry + r];
         }
     }
 }
@@ -388,8 +384,9 @@ template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepS
         if (W.plan[q].n > maxn) maxn = W.plan[q].n;
         if (W.plan[q].P > maxp) maxp = W.plan[q].P;
     }
-    const size_t sm = sizeof(double) * (2 * (size_t)maxn + 6 * (size_t)maxp);
-    k_plans<T><<<4, ((maxp + 31) / 32) * 32, sm, st>>>(g, W, sc);
+    const size_t sm = sizeof(double) * (2 * (size_t)maxn + 12 * (size_t)maxp);
+    int thr = ((2 * maxp + 31) / 32) * 32;
+    k_plans<T><<<4, thr, sm, st>>>(g, W, sc);
 }
 
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
