@@ -181,7 +181,7 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     // launch geometry
     const int tsz = (int)sizeof(T);
     W.ry = 1;
-    const int rymax = tsz == 8 ? 4 : 8;
+    const int rymax = 4;
     for (int r = rymax; r >= 1; r /= 2)
         if (g.ny % r == 0) { W.ry = r; break; }
     W.tx = 128 / tsz;

@@ -83,24 +83,38 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     const int Pmax = pa.P > pb.P ? pa.P : pb.P;
     const int rs = 2 * Pmax + 1;
     T *red = sm;
-    const TriPlan<T> pl = stage_plan(src, red + (size_t)tx * rs);
     T *q = comp == 0 ? q0 : (comp == 1 ? q1 : q2);
     const size_t stride = DIR == 1 ? (size_t)nx : (size_t)nx * ny;
     const int t = threadIdx.x;
     const int l = t % tx, p = t / tx;
     const int x = xt * tx + l;
-    const bool active = p < pl.P && x < nx;
+    const bool active = p < src.P && x < nx;
     const size_t base = (DIR == 1 ? (size_t)row * ny * nx : (size_t)row * nx) + x +
-                        (size_t)pl.off * stride;
+                        (size_t)src.off * stride;
     int s0 = 0, len = 0;
     T d[L];
+    // u^n of the step's z sweep is prefetched with the chunk in single
+    // precision (in double it would cost the registers of a second chunk)
+    constexpr bool kPrefetch = DIR == 2 && MODE == 0 && sizeof(T) == 4;
+    T un_pre[kPrefetch ? L : 1];
+    // issue the chunk's loads first; staging the plan below overlaps them
     if (active) {
-        s0 = chunk_start(p, pl.n, pl.P);
-        len = chunk_start(p + 1, pl.n, pl.P) - s0;
+        s0 = chunk_start(p, src.n, src.P);
+        len = chunk_start(p + 1, src.n, src.P) - s0;
         const T *qp = q + base + (size_t)s0 * stride;
 #pragma unroll
         for (int i = 0; i < L; ++i)
             if (i < len) d[i] = qp[(size_t)i * stride];
+        if constexpr (kPrefetch) {
+            const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
+            const T *up = un + base + (size_t)s0 * stride;
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < len) un_pre[i] = up[(size_t)i * stride];
+        }
+    }
+    const TriPlan<T> pl = stage_plan(src, red + (size_t)tx * rs);
+    if (active) {
         T rF, rE;
         chunk_forward<T, L>(d, len, pl, s0, rF, rE);
         red[l * rs + 2 * p] = rF;
@@ -117,11 +131,17 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
             for (int i = 0; i < L; ++i)
                 if (i < len) qp[(size_t)i * stride] = d[i];
         } else if (MODE == 0) {
-            const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
-            const T *up = un + base + (size_t)s0 * stride;
+            if constexpr (kPrefetch) {
 #pragma unroll
-            for (int i = 0; i < L; ++i)
-                if (i < len) qp[(size_t)i * stride] = up[(size_t)i * stride] + d[i];
+                for (int i = 0; i < L; ++i)
+                    if (i < len) qp[(size_t)i * stride] = un_pre[i] + d[i];
+            } else {
+                const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
+                const T *up = un + base + (size_t)s0 * stride;
+#pragma unroll
+                for (int i = 0; i < L; ++i)
+                    if (i < len) qp[(size_t)i * stride] = up[(size_t)i * stride] + d[i];
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < L; ++i)

@@ -246,7 +246,6 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
     const int nl = 3 * ry, es = nl | 1;
     T *red = sd + (size_t)nx * es;
     const int rs = 2 * px.P + 1;
-    const TriPlan<T> pxs = stage_plan(px, red + (size_t)nl * rs);
     const int nby = ny / ry;
     const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * ry;
     const T dt = T(sc->dt), gam = T(sc->gamma), rho = T(sc->rho);
@@ -343,7 +342,9 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
         sd[i * es + 2 * ry + r] = rw;
       }
     }
-    __syncthreads();
+    // staged after the right-hand side so its loads start at once; its
+    // closing barrier also publishes the right-hand side in sd
+    const TriPlan<T> pxs = stage_plan(px, red + (size_t)nl * rs);
     tri_plan_solve<T, T>(sd, es, 1, nl, pxs, red, rs);
     for (int r = 0; r < ry; ++r) {
         const int o = (k * ny + j0 + r) * nx;
