@@ -181,9 +181,11 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     // launch geometry
     const int tsz = (int)sizeof(T);
     W.ry = 1;
-    const int rymax = 4;
-    for (int r = rymax; r >= 1; r /= 2)
+    for (int r = 4; r >= 1; r /= 2)
         if (g.ny % r == 0) { W.ry = r; break; }
+    W.ry_fft = 1;
+    for (int r = tsz == 8 ? 4 : 8; r >= 1; r /= 2)
+        if (g.ny % r == 0) { W.ry_fft = r; break; }
     W.tx = 128 / tsz;
     while (W.tx > 4 && (size_t)g.nz * W.tx * tsz > 200 * 1024) W.tx /= 2;
     while (W.tx > 4 && (size_t)g.ny * W.tx * tsz > 200 * 1024) W.tx /= 2;

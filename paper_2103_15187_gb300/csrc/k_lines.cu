@@ -191,7 +191,7 @@ void sweep_geometry(int n, int &chunk, int &P, int &tx) {
     if ((n + P - 1) / P > 32) P = 32;
     while (P > 1 && n / P < 3) P /= 2;
     chunk = (n + P - 1) / P;
-    const int maxthr = chunk <= 16 ? 1024 : 512;
+    const int maxthr = chunk <= 16 ? 256 : 512;
     tx = 32;
     while (tx > 1 && tx * P > maxthr) tx /= 2;
 }

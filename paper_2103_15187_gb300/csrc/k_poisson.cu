@@ -274,7 +274,7 @@ k_irfft_x(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
 }  // namespace
 
 template <typename T> size_t smem_fft_x(const GridDev &g, const Work<T> &W) {
-    return 2 * sizeof(cplx<T>) * (size_t)W.ry * (g.mx | 1);
+    return 2 * sizeof(cplx<T>) * (size_t)W.ry_fft * (g.mx | 1);
 }
 template <typename T> size_t smem_fft_y(const GridDev &g, const Work<T> &W) {
     return 2 * sizeof(cplx<T>) * (size_t)W.tkx * g.ny;
@@ -287,14 +287,14 @@ template <typename T> size_t smem_poisson(const GridDev &g, const Work<T> &W) {
 
 template <typename T> void launch_rfft_x(const GridDev &g, Work<T> &W, const StepScalars *sc,
                                          const T *src, int mode, cudaStream_t st) {
-    const int blocks = g.nz * (g.ny / W.ry);
+    const int blocks = g.nz * (g.ny / W.ry_fft);
     const int threads = 256;
     if (mode == 0)
         k_rfft_x<T, 0><<<blocks, threads, smem_fft_x(g, W), st>>>(
-            g, W.q0, W.q1, W.q2, nullptr, W.spec, W.twx, W.twpost, W.fpx, sc, W.ry);
+            g, W.q0, W.q1, W.q2, nullptr, W.spec, W.twx, W.twpost, W.fpx, sc, W.ry_fft);
     else
         k_rfft_x<T, 1><<<blocks, threads, smem_fft_x(g, W), st>>>(
-            g, nullptr, nullptr, nullptr, src, W.spec, W.twx, W.twpost, W.fpx, sc, W.ry);
+            g, nullptr, nullptr, nullptr, src, W.spec, W.twx, W.twpost, W.fpx, sc, W.ry_fft);
 }
 
 template <typename T> void launch_fft_y(const GridDev &g, Work<T> &W, int inverse, cudaStream_t st) {
@@ -319,9 +319,9 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
 }
 
 template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
-    const int blocks = g.nz * (g.ny / W.ry);
+    const int blocks = g.nz * (g.ny / W.ry_fft);
     k_irfft_x<T><<<blocks, 256, smem_fft_x(g, W), st>>>(g, W.spec, dst, W.twx, W.twpost, W.fpx,
-                                                        W.ry);
+                                                        W.ry_fft);
 }
 
 template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<T> &W) {

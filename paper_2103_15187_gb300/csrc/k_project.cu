@@ -32,6 +32,7 @@ k_project(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict_
     const T vw = hasdn ? vxy / ihck : T(0);
     T mdiv = T(0), mspd = T(0), kel = T(0);
     int flags = 0;
+#pragma unroll 2
     for (int r = 0; r < rows; ++r) {
         const int j = j0 + r;
         const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;

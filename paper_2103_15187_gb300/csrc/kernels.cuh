@@ -29,7 +29,8 @@ template <typename T> struct Work {
     const unsigned char *exact;   // [ny][sk]: 1 for the modes in nzm
     double *nz_scratch;      // unused scratch kept for layout compatibility
     T *adj0, *adj1, *adj2;   // adjoint workspace (allocated on first use)
-    int ry;                  // rows per block of the x-line kernels
+    int ry;                  // rows per block of the x-line solves
+    int ry_fft;              // rows per block of the x transforms
     int tx;                  // (unused) x columns of the former shared-memory sweeps
     int chunk_y, chunk_z;    // register chunk length of the y / z sweeps
     int tx_y, tx_z;          // x columns per block of the y / z sweeps

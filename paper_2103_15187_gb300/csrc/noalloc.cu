@@ -225,6 +225,7 @@ fsei_status solve_noalloc(const fsei_grid_desc *d, const void *rhs, void *phi, c
     W.ry = 1;
     for (int r = (tsz == 8 ? 4 : 8); r >= 1; r /= 2)
         if (ny % r == 0) { W.ry = r; break; }
+    W.ry_fft = W.ry;
     W.tkx = 128 / (2 * tsz);
     while (W.tkx > 2 && ((size_t)nz * W.tkx * 4 * tsz > 200 * 1024 ||
                          (size_t)2 * ny * W.tkx * 2 * tsz > 200 * 1024))
