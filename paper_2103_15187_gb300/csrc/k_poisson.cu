@@ -235,8 +235,10 @@ size_t smem_exact(int nz, int P) {
     return sizeof(cplx<double>) * (nz + rs) + sizeof(double) * (2 * (size_t)nz + 3 * rs);
 }
 
+// about sqrt(nz) chunks: the chunk sweeps and the serial reduced system
+// (FP64 divisions on its critical path) then have similar lengths
 int exact_chunks(int nz) {
-    int P = 64;
+    int P = 16;
     if (P > (nz - 1) / 3) P = (nz - 1) / 3;
     return P < 1 ? 1 : P;
 }

@@ -4,8 +4,8 @@
 // beta = dt / (2 Re).  Fused reductions of the new state: max |D u^{n+1}|,
 // kinetic energy, and max |u_c|/dx + |v_c|/dy + |w_c|/dz_k (the CFL speed
 // that sets the next step's dt).  Per-cell statistics are evaluated in the
-// field precision; the grid-wide accumulation (per-warp partials onwards)
-// is in double (each thread sums its own few cells in the field precision).
+// field precision and reduced within each warp in it; the block and
+// grid-wide accumulation is in double.
 #include "kernels.cuh"
 
 namespace fsei {
@@ -72,41 +72,39 @@ k_project(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict_
             if (!isfinite(un) || !isfinite(vn) || !isfinite(wn) || !isfinite(pn)) flags |= 1;
         }
     }
-    double dmdiv = (double)mdiv, dmspd = (double)mspd, ke = (double)kel;
-    __shared__ double sdiv[32], sspd[32], ske[32];
-    __shared__ int sfl[32];
+    // warp level in the field precision (the maxima are exact in it; the
+    // energy partials are sums of at most a few hundred cells), block and
+    // grid level in double
     for (int o = 16; o > 0; o >>= 1) {
-        dmdiv = fmax(dmdiv, __shfl_down_sync(0xffffffffu, dmdiv, o));
-        dmspd = fmax(dmspd, __shfl_down_sync(0xffffffffu, dmspd, o));
-        ke += __shfl_down_sync(0xffffffffu, ke, o);
+        mdiv = fmax(mdiv, __shfl_down_sync(0xffffffffu, mdiv, o));
+        mspd = fmax(mspd, __shfl_down_sync(0xffffffffu, mspd, o));
+        kel += __shfl_down_sync(0xffffffffu, kel, o);
         flags |= __shfl_down_sync(0xffffffffu, flags, o);
     }
+    __shared__ double sdiv[32], sspd[32], ske[32];
+    __shared__ int sfl[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-        sdiv[wid] = dmdiv;
-        sspd[wid] = dmspd;
-        ske[wid] = ke;
+        sdiv[wid] = (double)mdiv;
+        sspd[wid] = (double)mspd;
+        ske[wid] = (double)kel;
         sfl[wid] = flags;
     }
     __syncthreads();
-    if (wid == 0) {
+    if (threadIdx.x == 0) {
         const int nw = (blockDim.x + 31) >> 5;
-        dmdiv = lane < nw ? sdiv[lane] : 0.0;
-        dmspd = lane < nw ? sspd[lane] : 0.0;
-        ke = lane < nw ? ske[lane] : 0.0;
-        flags = lane < nw ? sfl[lane] : 0;
-        for (int o = 16; o > 0; o >>= 1) {
-            dmdiv = fmax(dmdiv, __shfl_down_sync(0xffffffffu, dmdiv, o));
-            dmspd = fmax(dmspd, __shfl_down_sync(0xffffffffu, dmspd, o));
-            ke += __shfl_down_sync(0xffffffffu, ke, o);
-            flags |= __shfl_down_sync(0xffffffffu, flags, o);
+        double dd = 0.0, ds = 0.0, ke = 0.0;
+        int fl = 0;
+        for (int w = 0; w < nw; ++w) {
+            dd = fmax(dd, sdiv[w]);
+            ds = fmax(ds, sspd[w]);
+            ke += ske[w];
+            fl |= sfl[w];
         }
-        if (lane == 0) {
-            atomicMax(&sc->maxdiv, dbits(dmdiv));
-            atomicMax(&sc->speed_next, dbits(dmspd));
-            atomicAdd(&sc->ke, ke);
-            if (flags) atomicOr(&sc->flags, flags);
-        }
+        atomicMax(&sc->maxdiv, dbits(dd));
+        atomicMax(&sc->speed_next, dbits(ds));
+        atomicAdd(&sc->ke, ke);
+        if (fl) atomicOr(&sc->flags, fl);
     }
 }
 

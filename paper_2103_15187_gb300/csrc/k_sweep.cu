@@ -21,21 +21,6 @@ namespace fsei {
 
 namespace {
 
-template <typename T>
-__device__ double block_max(double v) {
-    __shared__ double wmax[32];
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) wmax[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        v = lane < nw ? wmax[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    }
-    return v;
-}
-
 // one block per group of rows (no integer division per element); per-cell
 // speed in the field precision, the grid-wide maximum in double
 template <typename T>
@@ -63,8 +48,15 @@ k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v, const T *__
             m = fmax(m, fabs(uc) * idx + fabs(vc) * idy + fabs(wc) * idzk);
         }
     }
-    const double mm = block_max<T>((double)m);
-    if (threadIdx.x == 0) atomicMax(&sc->speed_next, dbits(mm));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double wmax[32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = (double)m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0.0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) mm = fmax(mm, wmax[w]);
+        atomicMax(&sc->speed_next, dbits(mm));
+    }
 }
 
 __global__ void k_scalars(StepScalars *sc, StepArgs a, int euler) {
