@@ -385,7 +385,11 @@ template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepS
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
     const int nl = 3 * W.ry;
-    const int threads = ((nl * W.plan[0].P + 31) / 32) * 32;
+    int threads = ((nl * W.plan[0].P + 31) / 32) * 32;
+    // the right-hand-side phase strides over x: a block as wide as a row (up
+    // to the 256-thread bound) avoids a mostly idle second pass per row
+    const int row_threads = g.nx < 256 ? ((g.nx + 31) / 32) * 32 : 256;
+    if (threads < row_threads) threads = row_threads;
     const int blocks = g.nz * (g.ny / W.ry);
     k_rhs_x<T><<<blocks, threads, smem_rhs_x(g, W), st>>>(
         g, F, W.q0, W.q1, W.q2, sc, W.plan[0], W.ry, T(a.fconst[0]), T(a.fconst[1]),
