@@ -229,7 +229,7 @@ __global__ void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
         const StepScalars *sc, TriPlan<T> px, int ry, T fc0, T fc1, T fc2, T inv_re) {
     extern __shared__ __align__(16) unsigned char smraw[];
