@@ -306,6 +306,39 @@ def run_ensemble(args):
             "sizes": "64 boxes from {32^3, 64^3, 96x96x128, 128x128x192}, seed 5"}
 
 
+def run_heart_scale(args, peak):
+    """512x512x768 heart-scale box (stretched walls, k^-5/3 field, 20 force
+    blobs), mixed precision, 50 steps in one call."""
+    import torch
+    from paper_2103_15187_gb300 import fsei, inputs
+    case = inputs.case_heart_scale(steps=args.heart_steps)
+    grid = fsei.Grid(case.nx, case.ny, case.nz, case.lx, case.ly, zbc=case.zbc, lz=case.lz,
+                     stretch=case.stretch, prec=fsei.FSEI_MIXED)
+    st = device_state(case, torch.float32)
+    f = tuple(torch.tensor(a, dtype=torch.float32, device="cuda") for a in case.f)
+    prm = dict(re=case.re, dt=case.dt, cfl=case.cfl, fconst=case.fconst)
+    fsei.step(grid, st, f, nsteps=3, stats=False, **prm)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fsei.step(grid, st, f, nsteps=args.heart_steps, stats=False, **prm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stats = fsei.step(grid, st, f, nsteps=0, **prm)
+    words = sum(algorithmic_words(case.nx, case.ny, case.nz, True).values())
+    mcups = case.cells * args.heart_steps / (ms * 1e-3) / 1e6
+    gbs = words * 4 * mcups * 1e6 / 1e9
+    return {"value": round(mcups, 2), "unit": "Mcell-updates/s", "cells": case.cells,
+            "steps": args.heart_steps, "ms_per_step": round(ms / args.heart_steps, 4),
+            "precision": "mixed", "step_hbm_frac": round(gbs / peak, 4),
+            "alg_words_per_cell": round(words, 3), "max_div": stats["max_div"],
+            "workload": "512x512x768, Lx=Ly=2*96/156, tanh walls 2.0, Re 3000, CFL 0.5, "
+                        "k^-5/3 field (|k|<=32, unit RMS) + 20 Gaussian force blobs"}
+
+
 def roofline_of(res, nx, ny, nz, bytes_per_word, peak_gbs, peak_kind):
     words = algorithmic_words(nx, ny, nz, False)
     table = {}
@@ -407,6 +440,8 @@ def main():
     ap.add_argument("--ensemble-boxes", type=int, default=64)
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--heart-steps", type=int, default=50)
+    ap.add_argument("--no-heart", action="store_true")
     ap.add_argument("--nx", type=int, default=None, help="profiling override of the extents")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
@@ -471,6 +506,8 @@ def main():
         line["e2e"] = e2e
     if not args.no_ensemble and args.ensemble_boxes > 0:
         line["ensemble"] = run_ensemble(args)
+    if not args.no_heart and args.heart_steps > 0:
+        line["heart_scale"] = run_heart_scale(args, peak)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(case)
     print(json.dumps(line), flush=True)

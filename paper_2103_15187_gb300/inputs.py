@@ -157,13 +157,15 @@ def solenoidal_field(rng, nx, ny, nz, lx, ly, zf, zbc, kmin, kmax, slope,
                                nprof)
     spz = _random_plane_fields(rng, nx, ny, lx, ly, kmin, kmax, slope - 1.0,
                                nprof)
-    ax = np.zeros((nz + 1, ny, nx))
-    ay = np.zeros((nz + 1, ny, nx))
-    az = np.zeros((nz, ny, nx))
-    for m in range(nprof):
-        ax += pf[m][:, None, None] * _eval_plane(spx[m], nx, ny, 0.5, 0.0)[None]
-        ay += pf[m][:, None, None] * _eval_plane(spy[m], nx, ny, 0.0, 0.5)[None]
-        az += pc[m][:, None, None] * _eval_plane(spz[m], nx, ny, 0.0, 0.0)[None]
+    # A(z, x, y) = sum_m P_m(z) F_m(x, y): one matrix product per component
+    pfm = np.stack(pf, axis=1)                      # [nz+1, nprof]
+    pcm = np.stack(pc, axis=1)                      # [nz, nprof]
+    fx_ = np.stack([_eval_plane(spx[m], nx, ny, 0.5, 0.0).ravel() for m in range(nprof)])
+    fy_ = np.stack([_eval_plane(spy[m], nx, ny, 0.0, 0.5).ravel() for m in range(nprof)])
+    fz_ = np.stack([_eval_plane(spz[m], nx, ny, 0.0, 0.0).ravel() for m in range(nprof)])
+    ax = (pfm @ fx_).reshape(nz + 1, ny, nx)
+    ay = (pfm @ fy_).reshape(nz + 1, ny, nx)
+    az = (pcm @ fz_).reshape(nz, ny, nx)
     if zbc == Z_WALLS:
         ax[0] = ax[nz] = 0.0
         ay[0] = ay[nz] = 0.0

@@ -155,3 +155,27 @@ def test_full_size_channel_fp64_two_steps(fsei):
     ref, rst = pu.run_oracle(case, 2)
     _assert_fp64(gpu, ref)
     assert st["max_div"] < 1e-9
+
+
+def test_heart_scale_mixed_against_fp64_gpu(fsei):
+    """512x512x768 heart-scale box (stretched walls, k^-5/3 field, 20 force
+    blobs), the largest configuration: three mixed-precision steps against
+    three FP64 steps of the GPU path (itself at oracle parity above, and
+    sampled against the oracle here at full size): velocity within 1e-5,
+    divergence at round-off in both."""
+    import torch
+    case = inputs.case_heart_scale()
+    out = {}
+    for name, prec, dtype in (("fp64", fsei.FSEI_FP64, torch.float64),
+                              ("mixed", fsei.FSEI_MIXED, torch.float32)):
+        grid = pu.gpu_grid(case, prec)
+        st = pu.to_device(pu.initial_state_np(case), dtype)
+        f = pu.force_device(case, dtype)
+        stats = fsei.step(grid, st, f, nsteps=3, **pu.params(case))
+        assert stats["max_div"] < (1e-9 if name == "fp64" else 1e-2), stats
+        out[name] = {k: st[k].double() for k in ("u", "v", "w")}
+        del grid, st, f
+        torch.cuda.empty_cache()
+    num = sum(float(torch.linalg.vector_norm(out["mixed"][k] - out["fp64"][k]) ** 2) for k in "uvw")
+    den = sum(float(torch.linalg.vector_norm(out["fp64"][k]) ** 2) for k in "uvw")
+    assert (num / den) ** 0.5 <= 1e-5, (num / den) ** 0.5
