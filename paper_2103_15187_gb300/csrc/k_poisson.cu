@@ -94,12 +94,13 @@ k_fft_y(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ twy, 
     }
 }
 
+// z operator of the modes in a block; a, c and -(a + c) staged in shared
+// memory (a(0) and c(nz-1) are the periodic couplings, 0 with walls)
 template <typename T> struct PoissonMat {
-    const T *idz, *ihc, *lam;
-    int nz, walls;
-    FSEI_D T a(int i) const { return (walls && i == 0) ? T(0) : ihc[i] * idz[i]; }
-    FSEI_D T c(int i) const { return (walls && i == nz - 1) ? T(0) : ihc[i + 1] * idz[i]; }
-    FSEI_D T b(int l, int i) const { return -(a(i) + c(i)) - lam[l]; }
+    const T *sa, *sc, *sb0, *lam;
+    FSEI_D T a(int i) const { return sa[i]; }
+    FSEI_D T c(int i) const { return sc[i]; }
+    FSEI_D T b(int l, int i) const { return sb0[i] - lam[l]; }
 };
 
 template <typename T>
@@ -118,6 +119,7 @@ k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
     T *rdi = rlo + (size_t)tkx * rs;
     T *rup = rdi + (size_t)tkx * rs;
     T *lam = rup + (size_t)tkx * rs;
+    T *sa = lam + tkx, *scc = sa + nz, *sb0 = scc + nz;
     const int nkt = sk / tkx;
     const int ky = blockIdx.x / nkt, x0 = (blockIdx.x % nkt) * tkx;
     if (threadIdx.x < tkx) {
@@ -133,8 +135,18 @@ k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
         const int k = e / tkx, l = e - k * tkx;
         D[e] = base[(size_t)k * plane + l];
     }
+    {
+        const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
+        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+            const T a = (g.walls && k == 0) ? T(0) : ihc[k] * idz[k];
+            const T c = (g.walls && k == nz - 1) ? T(0) : ihc[k + 1] * idz[k];
+            sa[k] = a;
+            scc[k] = c;
+            sb0[k] = -(a + c);
+        }
+    }
     __syncthreads();
-    PoissonMat<T> M{Metric<T>::idz(g), Metric<T>::ihc(g), lam, nz, g.walls};
+    PoissonMat<T> M{sa, scc, sb0, lam};
     tri_fly_solve<T>(D, tkx, 1, fa, fc, tkx, 1, tkx, nz, P, !g.walls, M, rr, rlo, rdi, rup, rs);
     // modes solved exactly in double (k_poisson_exact, launched before this
     // kernel) keep their values
@@ -284,7 +296,7 @@ template <typename T> size_t smem_fft_y(const GridDev &g, const Work<T> &W) {
 template <typename T> size_t smem_poisson(const GridDev &g, const Work<T> &W) {
     const size_t rs = 2 * W.pz_poisson + 1;
     return sizeof(cplx<T>) * ((size_t)g.nz * W.tkx + W.tkx * rs) +
-           sizeof(T) * (2 * (size_t)g.nz * W.tkx + 3 * W.tkx * rs + W.tkx);
+           sizeof(T) * (2 * (size_t)g.nz * W.tkx + 3 * W.tkx * rs + W.tkx + 3 * (size_t)g.nz);
 }
 
 template <typename T> void launch_rfft_x(const GridDev &g, Work<T> &W, const StepScalars *sc,

@@ -21,6 +21,11 @@
 
 namespace fsei {
 
+// 1/x: the correctly rounded reciprocal instruction sequence in single
+// precision (cheaper than a division), a plain division in double
+FSEI_D float rcp(float x) { return __frcp_rn(x); }
+FSEI_D double rcp(double x) { return 1.0 / x; }
+
 // y - a x for real or complex x, y and real a
 template <typename T> FSEI_D T nmad(T a, T x, T y) { return y - a * x; }
 template <typename T> FSEI_D cplx<T> nmad(T a, cplx<T> x, cplx<T> y) {
@@ -201,7 +206,7 @@ __device__ void tri_fly_solve(cplx<T> *s, int es, int ls, T *fa, T *fc, int fes,
         s0 = chunk_start(p, n, P);
         e0 = chunk_start(p + 1, n, P) - 1;
         int i = s0 + 1;
-        T inv = T(1) / M.b(l, i);
+        T inv = rcp(M.b(l, i));
         T at = M.a(i) * inv, ct = M.c(i) * inv;
         A[i * fes] = at;
         C[i * fes] = ct;
@@ -209,7 +214,7 @@ __device__ void tri_fly_solve(cplx<T> *s, int es, int ls, T *fa, T *fc, int fes,
         d[i * es] = prev;
         for (i = s0 + 2; i < e0; ++i) {
             const T ai = M.a(i);
-            inv = T(1) / (M.b(l, i) - ai * ct);
+            inv = rcp(M.b(l, i) - ai * ct);
             at = -ai * at * inv;
             ct = M.c(i) * inv;
             A[i * fes] = at;
@@ -250,13 +255,13 @@ __device__ void tri_fly_solve(cplx<T> *s, int es, int ls, T *fa, T *fc, int fes,
             di[m - 1] -= up[m - 1] * lo0 / g;
         }
         // forward: overwrite up[] with c', di[] with 1/den
-        T inv = T(1) / di[0];
+        T inv = rcp(di[0]);
         di[0] = inv;
         up[0] *= inv;
         cplx<T> y = scl(inv, r[0]);
         r[0] = y;
         for (int j = 1; j < m; ++j) {
-            inv = T(1) / (di[j] - lo[j] * up[j - 1]);
+            inv = rcp(di[j] - lo[j] * up[j - 1]);
             di[j] = inv;
             up[j] *= inv;
             y = scl(inv, nmad(lo[j], y, r[j]));
@@ -283,7 +288,7 @@ __device__ void tri_fly_solve(cplx<T> *s, int es, int ls, T *fa, T *fc, int fes,
                 lo[j] = z;
             }
             const T vl = lo0 / g;
-            const T fac = T(1) / (T(1) + lo[0] + vl * lo[m - 1]);
+            const T fac = rcp(T(1) + lo[0] + vl * lo[m - 1]);
             const cplx<T> f = scl(fac, addv(r[0], scl(vl, r[m - 1])));
             for (int j = 0; j < m; ++j) r[j] = nmad(lo[j], f, r[j]);
         }
