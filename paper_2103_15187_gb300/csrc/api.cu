@@ -189,15 +189,17 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     W.tx = 128 / tsz;
     while (W.tx > 4 && (size_t)g.nz * W.tx * tsz > 200 * 1024) W.tx /= 2;
     while (W.tx > 4 && (size_t)g.ny * W.tx * tsz > 200 * 1024) W.tx /= 2;
+    // Poisson / y-FFT tile width: the largest (<= 128 bytes of complex per
+    // row) whose shared memory, computed exactly, fits the device limit
     W.tkx = 128 / (2 * tsz);
-    auto poisson_bytes = [&](int tk) { return (size_t)g.nz * tk * (2 * tsz + 2 * tsz); };
-    while (W.tkx > 2 && (poisson_bytes(W.tkx) > 200 * 1024 ||
-                         (size_t)2 * g.ny * W.tkx * 2 * tsz > 200 * 1024))
+    for (;;) {
+        W.pz_poisson = 256 / W.tkx;
+        if (W.pz_poisson > g.nz / 3) W.pz_poisson = g.nz / 3;
+        if (W.pz_poisson < 1) W.pz_poisson = 1;
+        const size_t lim = (size_t)smem_optin() - 2048;
+        if (W.tkx <= 2 || (smem_poisson<T>(g, W) <= lim && smem_fft_y<T>(g, W) <= lim)) break;
         W.tkx /= 2;
-    W.pz_poisson = 256 / W.tkx;
-    if (W.pz_poisson > g.nz / 3) W.pz_poisson = g.nz / 3;
-    if (W.pz_poisson < 1) W.pz_poisson = 1;
-
+    }
     // tridiagonal plans: 0 x, 1 y, 2 z centres, 3 z faces
     const int nl_x = 3 * W.ry;
     int Ps[4];

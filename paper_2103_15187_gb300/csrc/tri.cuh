@@ -21,9 +21,10 @@
 
 namespace fsei {
 
-// 1/x: the correctly rounded reciprocal instruction sequence in single
-// precision (cheaper than a division), a plain division in double
-FSEI_D float rcp(float x) { return __frcp_rn(x); }
+// 1/x: the hardware reciprocal approximation (a few ulp) in single
+// precision, where it sits on the serial critical path of the eliminations;
+// a plain division in double
+FSEI_D float rcp(float x) { return __fdividef(1.0f, x); }
 FSEI_D double rcp(double x) { return 1.0 / x; }
 
 // y - a x for real or complex x, y and real a
