@@ -100,4 +100,42 @@ __device__ cplx<T> *fft_lines(cplx<T> *a, cplx<T> *b, int es, int ls, int nl,
     return src;
 }
 
+// In-register DFT of length B (a power of two, B <= 32): iterative radix-2
+// with bit-reversed input order, every index a compile-time constant once
+// unrolled.  tw: table of w^m = exp(-2 pi i m / N), m < N, for a transform
+// length N that B divides (stage twiddles are tw[k N / (2h)]).
+template <int B> struct Log2 { static constexpr int v = 1 + Log2<B / 2>::v; };
+template <> struct Log2<1> { static constexpr int v = 0; };
+
+template <typename T, int B, int SIGN>
+FSEI_D void dft_reg(cplx<T> (&x)[B], const cplx<T> *tw, int N) {
+    constexpr int LB = Log2<B>::v;
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int b = 0; b < LB; ++b) r |= ((i >> b) & 1) << (LB - 1 - b);
+        if (r > i) {
+            const cplx<T> t = x[i];
+            x[i] = x[r];
+            x[r] = t;
+        }
+    }
+#pragma unroll
+    for (int h = 1; h < B; h *= 2) {
+#pragma unroll
+        for (int g0 = 0; g0 < B; g0 += 2 * h) {
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                cplx<T> w = tw[k * (N / (2 * h))];
+                if (SIGN > 0) w = conj(w);
+                const cplx<T> a = x[g0 + k];
+                const cplx<T> b = (k == 0) ? x[g0 + k + h] : x[g0 + k + h] * w;
+                x[g0 + k] = a + b;
+                x[g0 + k + h] = a - b;
+            }
+        }
+    }
+}
+
 }  // namespace fsei

@@ -19,6 +19,10 @@ namespace fsei {
 
 namespace {
 
+// The chunk's last rows are picked out with "i >= len - 1" style tests, never
+// "i == len - 1": the compiler folds an equality chain over an unrolled loop
+// into an array access at a run-time index, which moves d[] to local memory.
+// Chunks hold at least three unknowns.
 template <typename T, int L>
 __device__ __forceinline__ void chunk_forward(T (&d)[L], int len, const TriPlan<T> &pl, int s0,
                                               T &rF, T &rE) {
@@ -27,22 +31,18 @@ __device__ __forceinline__ void chunk_forward(T (&d)[L], int len, const TriPlan<
 #pragma unroll
     for (int i = 2; i < L - 1; ++i)
         if (i < len - 1) d[i] = pl.inv[s0 + i] * (d[i] - pl.a[s0 + i] * d[i - 1]);
-    // upward pass for the right-hand side part of x_{s0+1}
-    T dh = T(0), dhe = T(0);
+    // upward pass for the right-hand side part of x_{s0+1}; dh starts at 0,
+    // so at i = len-2 it takes d[len-2]
+    T dh = T(0), dhe = T(0), last = T(0);
 #pragma unroll
     for (int i = L - 2; i >= 1; --i) {
-        if (i == len - 2) {
-            dh = d[i];
-            dhe = d[i];
-        } else if (i < len - 2) {
-            dh = d[i] - pl.ct[s0 + i] * dh;
-        }
+        if (i >= len - 2) dhe = d[i];
+        if (i <= len - 2) dh = d[i] - pl.ct[s0 + i] * dh;
     }
-    rF = d[0] - pl.c[s0] * dh;
-    T last = d[0];
 #pragma unroll
-    for (int i = 1; i < L; ++i)
-        if (i == len - 1) last = d[i];
+    for (int i = 0; i < L; ++i)
+        if (i <= len - 1) last = d[i];
+    rF = d[0] - pl.c[s0] * dh;
     rE = last - pl.a[s0 + len - 1] * dhe;
 }
 
@@ -53,9 +53,9 @@ __device__ __forceinline__ void chunk_backward(T (&d)[L], int len, const TriPlan
     T x = E;
 #pragma unroll
     for (int i = L - 1; i >= 1; --i) {
-        if (i == len - 1) {
-            d[i] = E;
-        } else if (i < len - 1) {
+        if (i >= len - 1) {
+            d[i] = E;    // rows past the chunk are not stored
+        } else {
             x = d[i] - pl.at[s0 + i] * F - pl.ct[s0 + i] * x;
             d[i] = x;
         }
@@ -65,8 +65,11 @@ __device__ __forceinline__ void chunk_backward(T (&d)[L], int len, const TriPlan
 // DIR 1: y lines of plane k.  DIR 2: z lines of row j.
 // MODE (z only): 0 -> q = u^n + solution (step); 1 -> q = W solution
 // (adjoint, W = dz_k for u, v and hc_k for w).
+// Blocks hold at most 256 threads for chunks of <= 16 unknowns, 512 above
+// (sweep_geometry); the minimum-blocks hint leaves room for the chunk, and in
+// single precision for the prefetched u^n, in registers.
 template <typename T, int L, int DIR, int MODE>
-__global__ void __launch_bounds__(L <= 16 ? 1024 : 512)
+__global__ void __launch_bounds__(L <= 16 ? 256 : 512, L <= 16 ? (sizeof(T) == 4 ? 3 : 2) : 1)
 k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
             T *__restrict__ q2, TriPlan<T> pa, TriPlan<T> pb, int tx) {
     extern __shared__ __align__(16) unsigned char smraw[];
