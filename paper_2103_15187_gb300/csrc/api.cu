@@ -183,44 +183,29 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     W.ry = 1;
     for (int r = 4; r >= 1; r /= 2)
         if (g.ny % r == 0) { W.ry = r; break; }
-    W.ry_fft = 1;
-    for (int r = tsz == 8 ? 4 : 8; r >= 1; r /= 2)
-        if (g.ny % r == 0) { W.ry_fft = r; break; }
-    W.tx = 128 / tsz;
-    while (W.tx > 4 && (size_t)g.nz * W.tx * tsz > 200 * 1024) W.tx /= 2;
-    while (W.tx > 4 && (size_t)g.ny * W.tx * tsz > 200 * 1024) W.tx /= 2;
-    // Poisson / y-FFT tile width: the largest (<= 128 bytes of complex per
-    // row) whose shared memory, computed exactly, fits the device limit
-    W.tkx = 128 / (2 * tsz);
-    for (;;) {
-        W.pz_poisson = 256 / W.tkx;
-        if (W.pz_poisson > g.nz / 3) W.pz_poisson = g.nz / 3;
-        if (W.pz_poisson < 1) W.pz_poisson = 1;
-        const size_t lim = (size_t)smem_optin() - 2048;
-        if (W.tkx <= 2 || (smem_poisson<T>(g, W) <= lim && smem_fft_y<T>(g, W) <= lim)) break;
-        W.tkx /= 2;
+    poisson_geometry<T>(g, W);
+    // x lines (uniform, periodic): 3 ry lines of a block, chunks of at most
+    // 64 unknowns (fewer rows per block for the widest meshes)
+    uni_geometry(g.nx, 3 * W.ry, 256, W.px, W.chunk_x);
+    while (W.chunk_x > 64 && W.ry > 1) {
+        W.ry /= 2;
+        uni_geometry(g.nx, 3 * W.ry, 256, W.px, W.chunk_x);
     }
-    // tridiagonal plans: 0 x, 1 y, 2 z centres, 3 z faces
-    const int nl_x = 3 * W.ry;
-    int Ps[4];
+    sweep_y_geometry(g.ny, W.chunk_y, W.py, W.tx_y);
+    // tridiagonal plans of the z lines: 2 centres, 3 faces (entries 0 and 1
+    // are unused: the x and y lines need no plan)
+    int Ps[4] = {1, 1, 1, 1};
     int ns[4] = {g.nx, g.ny, g.nz, g.walls ? g.nz - 1 : g.nz};
-    // x chunks: a power of two (warp PCR for the reduced systems)
-    Ps[0] = 1;
-    while (2 * Ps[0] * nl_x <= 256 && 2 * Ps[0] <= 16) Ps[0] *= 2;
     {
-        int cy, py, ty, cz, pz, tz, cf, pf, tf;
-        sweep_geometry(ns[1], cy, py, ty);
+        int cz, pz, tz, cf, pf, tf;
         sweep_geometry(ns[2], cz, pz, tz);
         sweep_geometry(ns[3], cf, pf, tf);
-        Ps[1] = py;
         Ps[2] = pz;
         Ps[3] = pf;
-        W.chunk_y = cy;
-        W.tx_y = ty;
         W.chunk_z = cz > cf ? cz : cf;
         W.tx_z = tz < tf ? tz : tf;
     }
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 2; q < 4; ++q) {
         if (Ps[q] > ns[q] / 3) Ps[q] = ns[q] / 3;
         if (Ps[q] < 1) Ps[q] = 1;
         TriPlanStore<T> &s = W.store[q];
@@ -269,7 +254,6 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
         double *dlxd = M.get<double>(lamx.size());
         double *dlyd = M.get<double>(lamy.size());
         int *dm = M.get<int>(nzm.size());
-        W.nz_scratch = M.get<double>(4 * (size_t)g.nz * (nzm.size() ? nzm.size() : 1));
         if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "table allocation failed");
         upload(dlx, lx);
         upload(dly, ly);
@@ -315,7 +299,7 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
         const int euler = (n == 0 && !s->have_prev_h) ? 1 : 0;
         tm.run(KK_BEGIN, st, [&] { launch_step_begin<T>(g, W, G->sc, a, euler, st); });
         tm.run(KK_RHS_X, st, [&] { launch_rhs_x<T>(g, F, W, G->sc, a, st); });
-        tm.run(KK_SWEEP_Y, st, [&] { launch_sweep_y<T>(g, W, st); });
+        tm.run(KK_SWEEP_Y, st, [&] { launch_sweep_y<T>(g, W, G->sc, st); });
         tm.run(KK_SWEEP_Z, st, [&] { launch_sweep_z<T>(g, F, W, st); });
         tm.run(KK_RFFT_X, st, [&] { launch_rfft_x<T>(g, W, G->sc, nullptr, 0, st); });
         tm.run(KK_FFT_Y, st, [&] { launch_fft_y<T>(g, W, 0, st); });

@@ -67,6 +67,9 @@ struct StepScalars {
     double ke;            // kinetic energy of u^{n+1}
     int flags;            // FSEI_FLAG_*
     int pad;
+    // factors of the uniform periodic x and y sweep matrices (tri.cuh,
+    // uni_solve): alpha and 1/c for r = beta/dx^2 and beta/dy^2
+    double ax, cix, ay, ciy;
 };
 
 // --------------------------------------------- partitioned tridiagonal -----
@@ -99,6 +102,54 @@ template <typename T> struct TriPlanStore {
 };
 
 FSEI_HD int chunk_start(int p, int n, int P) { return (int)(((long long)p * n) / P); }
+
+// An opaque copy of a pointer: addresses formed from it are recomputed
+// rather than kept live in registers from an earlier use of the original.
+template <typename P> FSEI_D P *fresh(P *p) {
+    asm volatile("" : "+l"(p));
+    return p;
+}
+
+// x mod d and x / d for x >= 0, d > 0: shifts when d is a power of two (the
+// usual transform and tile sizes), the integer division otherwise
+FSEI_D int dmod(int x, int d) { return (d & (d - 1)) == 0 ? (x & (d - 1)) : x % d; }
+FSEI_D int ddiv(int x, int d) { return (d & (d - 1)) == 0 ? (x >> (31 - __clz(d))) : x / d; }
+
+// ------------------------------------------------ asynchronous copies ------
+// cp.async: global -> shared copies that complete in the background (no
+// register staging, so a thread can have all of its copies in flight).
+// 16 bytes: both addresses 16-byte aligned; 4 bytes: both 4-byte aligned.
+FSEI_D void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+FSEI_D void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// wait for every copy this thread has issued (a barrier must follow before
+// other threads read them)
+FSEI_D void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy rows of row_bytes bytes (row r: gsrc + r gstride -> sdst + r sstride)
+// with every thread of the block issuing copies.  16-byte copies when the
+// row length, both strides and both bases are multiples of 16 bytes, 4-byte
+// copies otherwise (then all of them must be multiples of 4).
+FSEI_D void copy_rows_async(void *sdst, size_t sstride, const void *gsrc, size_t gstride,
+                            int rows, int row_bytes) {
+    unsigned char *sd = static_cast<unsigned char *>(sdst);
+    const unsigned char *gs = static_cast<const unsigned char *>(gsrc);
+    const bool v16 = ((row_bytes | sstride | gstride) & 15) == 0 &&
+                     (((uintptr_t)sd | (uintptr_t)gs) & 15) == 0;
+    const int w = v16 ? 16 : 4;
+    const int per = row_bytes / w;
+    const int total = rows * per;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int r = ddiv(e, per), c = (e - r * per) * w;
+        if (v16) cp_async16(sd + r * sstride + c, gs + r * gstride + c);
+        else cp_async4(sd + r * sstride + c, gs + r * gstride + c);
+    }
+}
 
 // bit pattern of a non-negative double, monotone in its value
 FSEI_D unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }

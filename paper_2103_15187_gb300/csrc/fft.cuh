@@ -51,25 +51,32 @@ FSEI_D void dft4(cplx<T> &x0, cplx<T> &x1, cplx<T> &x2, cplx<T> &x3) {
 
 // Transform nl lines.  Element i of line l: buf[i * es + l * ls].  Data
 // starts in a; b is scratch of the same size.  Returns the buffer holding
-// the result.  tw: table of w^m, m < N (forward sign).  Must be called by
-// every thread of the block; ends with a barrier.
+// the result.  tw: table of w^m, m < N (forward sign), normally staged in
+// shared memory by the caller.  Must be called by every thread of the block;
+// ends with a barrier.
 template <typename T, int SIGN>
 __device__ cplx<T> *fft_lines(cplx<T> *a, cplx<T> *b, int es, int ls, int nl,
                               const FftPlanDev &fp, const cplx<T> *__restrict__ tw,
                               bool line_fastest) {
     const int N = fp.n;
+    // the radices packed two bits each (radix - 2): a run-time index into
+    // fp.rad would place the plan in local memory
+    unsigned code = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        if (q < fp.nr) code |= (unsigned)(fp.rad[q] - 2) << (2 * q);
     int p = 1;
     cplx<T> *src = a, *dst = b;
     for (int s = 0; s < fp.nr; ++s) {
-        const int R = fp.rad[s];
+        const int R = (int)((code >> (2 * s)) & 3u) + 2;
         const int TN = N / R;
         const int tstep = N / (p * R);
         const int total = nl * TN;
         for (int w = threadIdx.x; w < total; w += blockDim.x) {
             int l, i;
-            if (line_fastest) { l = w % nl; i = w / nl; }
-            else { i = w % TN; l = w / TN; }
-            const int k = i % p;
+            if (line_fastest) { i = ddiv(w, nl); l = w - i * nl; }
+            else { l = ddiv(w, TN); i = w - l * TN; }
+            const int k = dmod(i, p);
             const int j = (i - k) * R + k;
             cplx<T> x[4];
 #pragma unroll

@@ -101,17 +101,18 @@ k_adj_ustar(GridDev g, T *__restrict__ ub, T *__restrict__ vb, T *__restrict__ w
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512)
-k_sweep_x(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2, TriPlan<T> px,
-          int ry) {
+// x sweep of the adjoint: q = (I - beta L_x)^-T q = (I - beta L_x)^-1 q (the
+// uniform periodic matrix is symmetric).  A block owns ry rows of one
+// component in plane k; thread t < ry P owns chunk t / ry of row t % ry.
+template <typename T, int L>
+__global__ void __launch_bounds__(256)
+k_sweep_x(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
+          const StepScalars *sc, int ry, int P) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sd = reinterpret_cast<T *>(smraw);
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int es = ry | 1;
-    T *red = sd + (size_t)nx * es;
-    const int rs = 2 * px.P + 1;
-    const TriPlan<T> pl = stage_plan(px, red + (size_t)ry * rs);
+    T *car = sd + (size_t)nx * es;
     const int nby = ny / ry;
     int b = blockIdx.x;
     const int jb = b % nby; b /= nby;
@@ -124,7 +125,22 @@ k_sweep_x(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
         sd[i * es + r] = q[fid(i, j0 + r, k, nx, ny)];
     }
     __syncthreads();
-    tri_plan_solve<T, T>(sd, es, 1, ry, pl, red, rs);
+    {
+        const int t = threadIdx.x;
+        const bool active = t < ry * P;
+        const int p = active ? t / ry : 0, l = active ? t - p * ry : 0;
+        const int s0 = chunk_start(p, nx, P);
+        const int len = active ? chunk_start(p + 1, nx, P) - s0 : 0;
+        T d[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < len) d[i] = sd[(s0 + i) * es + l];
+        uni_solve<T, L>(d, len, active, l, p, ry, nx, P, T(sc->ax), T(sc->cix), car);
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < len) sd[(s0 + i) * es + l] = d[i];
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < ry * nx; e += blockDim.x) {
         const int r = e / nx, i = e - r * nx;
         q[fid(i, j0 + r, k, nx, ny)] = sd[i * es + r];
@@ -285,10 +301,28 @@ k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
 
 }  // namespace
 
-template <typename T> size_t smem_sweep_x(const GridDev &g, const Work<T> &W) {
-    const int es = W.ry | 1;
-    return sizeof(T) * ((size_t)g.nx * es + (size_t)W.ry * (2 * W.plan[0].P + 1) +
-                        plan_stage_words(W.plan[0].n, W.plan[0].P));
+// chunks per line of the adjoint x sweep (ry lines per block, 256 threads)
+template <typename T> void sweep_x_geometry(const GridDev &g, const Work<T> &W, int &P, int &chunk) {
+    uni_geometry(g.nx, W.ry, 256, P, chunk);
+}
+
+template <typename T, int L>
+void sweep_x_L(const GridDev &g, Work<T> &W, const StepScalars *sc, int P, cudaStream_t st) {
+    const int ry = W.ry;
+    const int threads = ((ry * P + 31) / 32) * 32;
+    const size_t smem = sizeof(T) * ((size_t)g.nx * (ry | 1) + 2 * (size_t)ry * P);
+    k_sweep_x<T, L><<<3 * g.nz * (g.ny / ry), threads < 64 ? 64 : threads, smem, st>>>(
+        g, W.q0, W.q1, W.q2, sc, ry, P);
+}
+
+template <typename T>
+void launch_sweep_x_adjoint(const GridDev &g, Work<T> &W, const StepScalars *sc, cudaStream_t st) {
+    int P, chunk;
+    sweep_x_geometry(g, W, P, chunk);
+    if (chunk <= 8) sweep_x_L<T, 8>(g, W, sc, P, st);
+    else if (chunk <= 16) sweep_x_L<T, 16>(g, W, sc, P, st);
+    else if (chunk <= 32) sweep_x_L<T, 32>(g, W, sc, P, st);
+    else sweep_x_L<T, 64>(g, W, sc, P, st);
 }
 
 template <typename T>
@@ -305,13 +339,8 @@ void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T 
     launch_irfft_x<T>(g, W, W.phi, st);
     k_adj_ustar<T><<<rows, thr, 0, st>>>(g, ub, vb, wb, W.phi, W.q0, W.q1, W.q2, sc);
     launch_sweep_z_adjoint<T>(g, W, st);
-    launch_sweep_y<T>(g, W, st);
-    {
-        const int ry = W.ry;
-        const int threads = ((ry * W.plan[0].P + 31) / 32) * 32;
-        k_sweep_x<T><<<3 * g.nz * (g.ny / ry), threads < 64 ? 64 : threads, smem_sweep_x(g, W),
-                       st>>>(g, W.q0, W.q1, W.q2, W.plan[0], ry);
-    }
+    launch_sweep_y<T>(g, W, sc, st);
+    launch_sweep_x_adjoint<T>(g, W, sc, st);
     k_adj_hist<T><<<rows, thr, 0, st>>>(g, W.q0, W.q1, W.q2, hbu, hbv, hbw, W.adj0, W.adj1,
                                         W.adj2, fbx, fby, fbz, sc);
     k_adj_gather<T><<<rows, thr, 0, st>>>(g, u, v, w, W.q0, W.q1, W.q2, W.adj0, W.adj1, W.adj2, ub,
@@ -324,7 +353,10 @@ template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<
     cudaFuncGetAttributes(&fa, k_adj_ustar<T>);
     cudaFuncGetAttributes(&fa, k_adj_hist<T>);
     cudaFuncGetAttributes(&fa, k_adj_gather<T>);
-    raise_smem_limit(k_sweep_x<T>);
+    raise_smem_limit(k_sweep_x<T, 8>);
+    raise_smem_limit(k_sweep_x<T, 16>);
+    raise_smem_limit(k_sweep_x<T, 32>);
+    raise_smem_limit(k_sweep_x<T, 64>);
 }
 
 #define FSEI_INST(T)                                                                           \

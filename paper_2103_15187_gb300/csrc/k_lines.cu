@@ -1,15 +1,19 @@
 // Implicit viscous sweeps along y and z (Sec. 3.1: one tridiagonal system
-// per direction; cyclic in y; Dirichlet walls or cyclic in z) with the
-// partitioned elimination of tri.cuh held in registers.
+// per direction; cyclic in y; Dirichlet walls or cyclic in z).
 //
-// A block owns tx consecutive x columns of one component and one plane (y
-// lines) or one y row (z lines).  Thread (lane, p) owns chunk p of line lane:
-// it loads the chunk straight from global memory (a warp reads tx
-// consecutive x values per row: coalesced), eliminates the chunk interior in
-// registers, writes its two reduced-row right-hand sides to shared memory,
-// and after one thread per line has solved the reduced system recovers the
+// z lines (stretched mesh: the coefficients vary along the line) use the
+// partitioned elimination of tri.cuh held in registers.  A block owns tx
+// consecutive x columns of one component and one y row.  Thread (lane, p)
+// owns chunk p of line lane: it loads the chunk straight from global memory
+// (a warp reads tx consecutive x values per row: coalesced), eliminates the
+// chunk interior in registers, writes its two reduced-row right-hand sides
+// to shared memory, and after the reduced systems are solved recovers the
 // interior in registers and stores it.  Shared memory holds only the plan
 // factors and the reduced systems.
+//
+// y lines (uniform and periodic: one cyclic Toeplitz matrix for every line)
+// use the factorised solve uni_solve of tri.cuh with the same block shape:
+// chunks in registers, only the chunk carries pass through shared memory.
 #include <string.h>
 
 #include "kernels.cuh"
@@ -128,7 +132,7 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     __syncthreads();
     if (active) {
         chunk_backward<T, L>(d, len, pl, s0, red[l * rs + 2 * p], red[l * rs + 2 * p + 1]);
-        T *qp = q + base + (size_t)s0 * stride;
+        T *qp = fresh(q) + base + (size_t)s0 * stride;
         if (DIR == 1) {
 #pragma unroll
             for (int i = 0; i < L; ++i)
@@ -157,6 +161,38 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     }
 }
 
+// y sweep of plane k: q = (I - beta L_y)^-1 q for the three components.
+template <typename T, int L>
+__global__ void __launch_bounds__(256, L <= 16 ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? 2 : 1))
+k_sweep_y_uni(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
+              const StepScalars *sc, int P, int tx) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *car = reinterpret_cast<T *>(smraw);
+    const int nx = g.nx, ny = g.ny;
+    const int nxt = (nx + tx - 1) / tx;
+    int b = blockIdx.x;
+    const int xt = b % nxt;
+    b /= nxt;
+    const int k = b % g.nz, comp = b / g.nz;
+    T *q = comp == 0 ? q0 : (comp == 1 ? q1 : q2);
+    const int t = threadIdx.x;
+    const int p = ddiv(t, tx), l = t - p * tx;
+    const int x = xt * tx + l;
+    const bool active = p < P && x < nx;
+    const int s0 = active ? chunk_start(p, ny, P) : 0;
+    const int len = active ? chunk_start(p + 1, ny, P) - s0 : 0;
+    T *qp = q + (k * ny + s0) * nx + x;    // a field holds < 2^31 values
+    T d[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i)
+        if (i < len) d[i] = qp[i * nx];
+    uni_solve<T, L>(d, len, active, l, p, tx, ny, P, T(sc->ay), T(sc->ciy), car);
+    T *qs = fresh(qp);
+#pragma unroll
+    for (int i = 0; i < L; ++i)
+        if (i < len) qs[i * nx] = d[i];
+}
+
 template <typename T, int L, int DIR, int MODE>
 void launch_reg(const GridDev &g, const Fields<T> &F, Work<T> &W, const TriPlan<T> &pa,
                 const TriPlan<T> &pb, int tx, cudaStream_t st) {
@@ -172,10 +208,11 @@ void launch_reg(const GridDev &g, const Fields<T> &F, Work<T> &W, const TriPlan<
 
 template <typename T, int DIR, int MODE>
 void dispatch(const GridDev &g, const Fields<T> &F, Work<T> &W, cudaStream_t st) {
-    const TriPlan<T> &pa = DIR == 1 ? W.plan[1] : W.plan[2];
-    const TriPlan<T> &pb = DIR == 1 ? W.plan[1] : W.plan[3];
-    const int chunk = DIR == 1 ? W.chunk_y : W.chunk_z;
-    const int tx = DIR == 1 ? W.tx_y : W.tx_z;
+    static_assert(DIR == 2, "y lines use k_sweep_y_uni");
+    const TriPlan<T> &pa = W.plan[2];
+    const TriPlan<T> &pb = W.plan[3];
+    const int chunk = W.chunk_z;
+    const int tx = W.tx_z;
     if (chunk <= 8) launch_reg<T, 8, DIR, MODE>(g, F, W, pa, pb, tx, st);
     else if (chunk <= 16) launch_reg<T, 16, DIR, MODE>(g, F, W, pa, pb, tx, st);
     else launch_reg<T, 32, DIR, MODE>(g, F, W, pa, pb, tx, st);
@@ -199,10 +236,31 @@ void sweep_geometry(int n, int &chunk, int &P, int &tx) {
     while (tx > 1 && tx * P > maxthr) tx /= 2;
 }
 
-template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, cudaStream_t st) {
-    Fields<T> none;
-    memset(&none, 0, sizeof none);
-    dispatch<T, 1, 0>(g, none, W, st);
+// Chunks per line and x columns per block of the uniform y sweep: P the
+// smallest power of two giving chunks of at most 16 (at most 32 chunks, so a
+// line's carries fit one warp); up to 32 columns in a block of at most 256
+// threads.
+void sweep_y_geometry(int n, int &chunk, int &P, int &tx) {
+    P = 1;
+    while (P < 32 && (n + P - 1) / P > 16) P *= 2;
+    chunk = (n + P - 1) / P;
+    tx = 256 / P < 32 ? 256 / P : 32;
+}
+
+template <typename T, int L>
+void launch_y_uni(const GridDev &g, Work<T> &W, const StepScalars *sc, cudaStream_t st) {
+    const int tx = W.tx_y, P = W.py;
+    const int nxt = (g.nx + tx - 1) / tx;
+    const int threads = ((tx * P + 31) / 32) * 32;
+    k_sweep_y_uni<T, L><<<3 * g.nz * nxt, threads, 2 * sizeof(T) * tx * P, st>>>(
+        g, W.q0, W.q1, W.q2, sc, P, tx);
+}
+
+template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, const StepScalars *sc,
+                                          cudaStream_t st) {
+    if (W.chunk_y <= 8) launch_y_uni<T, 8>(g, W, sc, st);
+    else if (W.chunk_y <= 16) launch_y_uni<T, 16>(g, W, sc, st);
+    else launch_y_uni<T, 32>(g, W, sc, st);
 }
 
 template <typename T> void launch_sweep_z(const GridDev &g, const Fields<T> &F, Work<T> &W,
@@ -219,9 +277,9 @@ template <typename T> void launch_sweep_z_adjoint(const GridDev &g, Work<T> &W, 
 template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T> &W) {
     (void)g;
     (void)W;
-    raise_smem_limit(k_sweep_reg<T, 8, 1, 0>);
-    raise_smem_limit(k_sweep_reg<T, 16, 1, 0>);
-    raise_smem_limit(k_sweep_reg<T, 32, 1, 0>);
+    raise_smem_limit(k_sweep_y_uni<T, 8>);
+    raise_smem_limit(k_sweep_y_uni<T, 16>);
+    raise_smem_limit(k_sweep_y_uni<T, 32>);
     raise_smem_limit(k_sweep_reg<T, 8, 2, 0>);
     raise_smem_limit(k_sweep_reg<T, 16, 2, 0>);
     raise_smem_limit(k_sweep_reg<T, 32, 2, 0>);
@@ -231,7 +289,8 @@ template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T>
 }
 
 #define FSEI_INST(T)                                                                           \
-    template void launch_sweep_y<T>(const GridDev &, Work<T> &, cudaStream_t);                 \
+    template void launch_sweep_y<T>(const GridDev &, Work<T> &, const StepScalars *,           \
+                                    cudaStream_t);                                            \
     template void launch_sweep_z<T>(const GridDev &, const Fields<T> &, Work<T> &,             \
                                     cudaStream_t);                                            \
     template void launch_sweep_z_adjoint<T>(const GridDev &, Work<T> &, cudaStream_t);         \

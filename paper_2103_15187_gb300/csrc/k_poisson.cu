@@ -21,76 +21,121 @@ namespace fsei {
 
 namespace {
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(512)
+// Row length (complex elements) of the x-transform lines in shared memory:
+// mx rounded up to even, so that every line starts on a 16-byte boundary.
+FSEI_HD int fft_x_ls(int mx) { return mx + (mx & 1); }
+// complex values per staged spectrum row of the inverse x transform: kx <=
+// mx, rounded up to whole 16-byte copies (within the row stride sk, a
+// multiple of 16)
+FSEI_HD int irfft_stage_row(int mx) { return (mx + 1 + 1) & ~1; }
+
+// Stage the x twiddles w^m (m < mx) and the post-processing factors
+// exp(-2 pi i kx / nx) (kx <= mx) in shared memory.
+template <typename T>
+FSEI_D void stage_x_twiddles(cplx<T> *TW, cplx<T> *TP, const cplx<T> *twx,
+                             const cplx<T> *twpost, int mx) {
+    for (int m = threadIdx.x; m < mx; m += blockDim.x) TW[m] = twx[m];
+    for (int m = threadIdx.x; m <= mx; m += blockDim.x) TP[m] = twpost[m];
+}
+
+// Real-to-complex transform along x of RY rows (j0 .. j0+RY-1 of plane k):
+// the real row of nx values is read as mx = nx/2 complex values (even
+// entries real parts, odd entries imaginary parts), transformed with a
+// half-length complex FFT, and split into the nx/2 + 1 coefficients
+//   X_kx = (Z_kx + conj Z_{mx-kx}) / 2 - i w^kx (Z_kx - conj Z_{mx-kx}) / 2,
+// w = exp(-2 pi i / nx).  MODE 0: the rows are s = D u* / dt, formed from
+// the three velocity fields with every load of a thread in flight at once;
+// MODE 1: the rows of a given field, copied asynchronously.
+template <typename T, int MODE, int RY>
+__global__ void __launch_bounds__(256)
 k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
          const T *__restrict__ q2, const T *__restrict__ src, cplx<T> *__restrict__ spec,
          const cplx<T> *__restrict__ twx, const cplx<T> *__restrict__ twpost, FftPlanDev fp,
-         const StepScalars *sc, int ry) {
+         const StepScalars *sc) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx, ny = g.ny, nz = g.nz, mx = g.mx, sk = g.sk;
-    const int ls = mx | 1;
+    const int ls = fft_x_ls(mx);
     cplx<T> *A = reinterpret_cast<cplx<T> *>(smraw);
-    cplx<T> *B = A + (size_t)ry * ls;
-    const int nby = ny / ry;
-    const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * ry;
-    T invdt = T(1);
-    if (MODE == 0) invdt = T(1.0 / sc->dt);
-    const bool hasup = !g.walls || k < nz - 1;
-    const int ku = k == nz - 1 ? 0 : k + 1;
-    const T idx = T(g.idx), idy = T(g.idy);
-    const T idzk = Metric<T>::idz(g)[k];
-    for (int r = 0; r < ry; ++r) {
-        const int j = j0 + r, jp = j == ny - 1 ? 0 : j + 1;
-        const size_t oc = ((size_t)k * ny + j) * nx;
-        T *arow = reinterpret_cast<T *>(A + (size_t)r * ls);
-        if (MODE == 0) {
-            const T *a0 = q0 + oc, *a1 = q1 + oc, *a1jp = q1 + ((size_t)k * ny + jp) * nx;
-            const T *a2 = q2 + oc, *a2ku = q2 + ((size_t)ku * ny + j) * nx;
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-                const int ip = i == nx - 1 ? 0 : i + 1;
-                const T wku = hasup ? a2ku[i] : T(0);
-                arow[i] = ((a0[ip] - a0[i]) * idx + (a1jp[i] - a1[i]) * idy + (wku - a2[i]) * idzk) *
-                          invdt;
+    cplx<T> *B = A + (size_t)RY * ls;
+    cplx<T> *TW = B + (size_t)RY * ls;
+    cplx<T> *TP = TW + fft_x_ls(mx);
+    const int nby = ny / RY;
+    const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * RY;
+    if (MODE == 1) {
+        copy_rows_async(A, ls * sizeof(cplx<T>), src + ((size_t)k * ny + j0) * nx,
+                        (size_t)nx * sizeof(T), RY, nx * (int)sizeof(T));
+        stage_x_twiddles(TW, TP, twx, twpost, mx);
+        cp_async_wait_all();
+    } else {
+        const T invdt = T(1.0 / sc->dt);
+        const bool hasup = !g.walls || k < nz - 1;
+        const int ku = k == nz - 1 ? 0 : k + 1;
+        const T idx = T(g.idx), idy = T(g.idy);
+        const T idzk = Metric<T>::idz(g)[k];
+        const int oc0 = (k * ny + j0) * nx, ou0 = (ku * ny + j0) * nx;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int ip = i == nx - 1 ? 0 : i + 1;
+            T a0[RY], a0p[RY], a1[RY], a1p[RY], a2[RY], a2u[RY];
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const int o = oc0 + r * nx;
+                const int ojp = (j0 + r == ny - 1) ? (k * ny) * nx : o + nx;
+                a0[r] = q0[o + i];
+                a0p[r] = q0[o + ip];
+                a1[r] = q1[o + i];
+                a1p[r] = q1[ojp + i];
+                a2[r] = q2[o + i];
+                a2u[r] = hasup ? q2[ou0 + r * nx + i] : T(0);
             }
-        } else {
-            const T *sr = src + oc;
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) arow[i] = sr[i];
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                T *arow = reinterpret_cast<T *>(A + (size_t)r * ls);
+                arow[i] = ((a0p[r] - a0[r]) * idx + (a1p[r] - a1[r]) * idy +
+                           (a2u[r] - a2[r]) * idzk) * invdt;
+            }
         }
+        stage_x_twiddles(TW, TP, twx, twpost, mx);
     }
     __syncthreads();
-    const cplx<T> *R = fft_lines<T, -1>(A, B, 1, ls, ry, fp, twx, false);
+    const cplx<T> *R = fft_lines<T, -1>(A, B, 1, ls, RY, fp, TW, false);
     const T hf = T(0.5);
-    for (int e = threadIdx.x; e < ry * (mx + 1); e += blockDim.x) {
+    for (int e = threadIdx.x; e < RY * (mx + 1); e += blockDim.x) {
         const int r = e / (mx + 1), kx = e - r * (mx + 1);
         const cplx<T> zk = R[r * ls + (kx == mx ? 0 : kx)];
         const cplx<T> zc = conj(R[r * ls + (kx == 0 ? 0 : mx - kx)]);
         const cplx<T> ev = hf * (zk + zc);
-        const cplx<T> od = mul_i<T, -1>(hf * (twpost[kx] * (zk - zc)));
+        const cplx<T> od = mul_i<T, -1>(hf * (TP[kx] * (zk - zc)));
         spec[((size_t)k * ny + j0 + r) * sk + kx] = ev + od;
     }
 }
 
+// Complex DFT along y of tkx spectrum columns of plane k: the tile is
+// copied asynchronously into shared memory (rows of tkx values), transformed
+// with the line index fastest, and written back with 16-byte stores.
 template <typename T, int SIGN>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(256)
 k_fft_y(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ twy, FftPlanDev fp,
         int tkx) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int ny = g.ny, sk = g.sk;
     cplx<T> *A = reinterpret_cast<cplx<T> *>(smraw);
     cplx<T> *B = A + (size_t)ny * tkx;
+    cplx<T> *TW = B + (size_t)ny * tkx;
     const int nkt = sk / tkx;
     const int k = blockIdx.x / nkt, x0 = (blockIdx.x % nkt) * tkx;
     cplx<T> *base = spec + (size_t)k * ny * sk + x0;
-    for (int e = threadIdx.x; e < ny * tkx; e += blockDim.x) {
-        const int j = e / tkx, l = e - j * tkx;
-        A[e] = base[(size_t)j * sk + l];
-    }
+    const int rb = tkx * (int)sizeof(cplx<T>);
+    copy_rows_async(A, rb, base, (size_t)sk * sizeof(cplx<T>), ny, rb);
+    for (int m = threadIdx.x; m < ny; m += blockDim.x) TW[m] = twy[m];
+    cp_async_wait_all();
     __syncthreads();
-    const cplx<T> *R = fft_lines<T, SIGN>(A, B, tkx, 1, tkx, fp, twy, true);
-    for (int e = threadIdx.x; e < ny * tkx; e += blockDim.x) {
-        const int j = e / tkx, l = e - j * tkx;
-        base[(size_t)j * sk + l] = R[e];
+    const cplx<T> *R = fft_lines<T, SIGN>(A, B, tkx, 1, tkx, fp, TW, true);
+    // 16-byte stores: rb is a multiple of 16 (tkx even in single precision)
+    const int per = rb / 16;
+    for (int e = threadIdx.x; e < ny * per; e += blockDim.x) {
+        const int j = ddiv(e, per), c = e - j * per;
+        const uint4 v = reinterpret_cast<const uint4 *>(R + (size_t)j * tkx)[c];
+        reinterpret_cast<uint4 *>(base + (size_t)j * sk)[c] = v;
     }
 }
 
@@ -131,10 +176,8 @@ k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
     }
     const size_t plane = (size_t)ny * sk;
     cplx<T> *base = spec + (size_t)ky * sk + x0;
-    for (int e = threadIdx.x; e < nz * tkx; e += blockDim.x) {
-        const int k = e / tkx, l = e - k * tkx;
-        D[e] = base[(size_t)k * plane + l];
-    }
+    copy_rows_async(D, tkx * sizeof(cplx<T>), base, plane * sizeof(cplx<T>), nz,
+                    tkx * (int)sizeof(cplx<T>));
     {
         const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
         for (int k = threadIdx.x; k < nz; k += blockDim.x) {
@@ -145,6 +188,7 @@ k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
             sb0[k] = -(a + c);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     PoissonMat<T> M{sa, scc, sb0, lam};
     tri_fly_solve<T>(D, tkx, 1, fa, fc, tkx, 1, tkx, nz, P, !g.walls, M, rr, rlo, rdi, rup, rs);
@@ -255,43 +299,71 @@ int exact_chunks(int nz) {
     return P < 1 ? 1 : P;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512)
+// Complex-to-real inverse DFT along x of RY spectrum rows into dst: the
+// rows (kx <= mx) are copied asynchronously, recombined into the half-length
+// complex sequence Z_kx = (X_kx + conj X_{mx-kx}) + i conj(w^kx) (X_kx -
+// conj X_{mx-kx}), inverse transformed, and the complex result stored as the
+// interleaved real row.
+template <typename T, int RY>
+__global__ void __launch_bounds__(256)
 k_irfft_x(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
-          const cplx<T> *__restrict__ twx, const cplx<T> *__restrict__ twpost, FftPlanDev fp,
-          int ry) {
+          const cplx<T> *__restrict__ twx, const cplx<T> *__restrict__ twpost, FftPlanDev fp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx, ny = g.ny, mx = g.mx, sk = g.sk;
-    const int ls = mx | 1;
+    const int ls = fft_x_ls(mx);
+    const int ss = irfft_stage_row(mx);
     cplx<T> *A = reinterpret_cast<cplx<T> *>(smraw);
-    cplx<T> *B = A + (size_t)ry * ls;
-    const int nby = ny / ry;
-    const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * ry;
-    for (int e = threadIdx.x; e < ry * mx; e += blockDim.x) {
-        const int r = e / mx, kx = e - r * mx;
-        const cplx<T> *row = spec + ((size_t)k * ny + j0 + r) * sk;
+    cplx<T> *B = A + (size_t)RY * ls;
+    cplx<T> *TW = B + (size_t)RY * ls;
+    cplx<T> *TP = TW + fft_x_ls(mx);
+    cplx<T> *S = TP + fft_x_ls(mx + 1);
+    const int nby = ny / RY;
+    const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * RY;
+    copy_rows_async(S, ss * sizeof(cplx<T>), spec + ((size_t)k * ny + j0) * sk,
+                    (size_t)sk * sizeof(cplx<T>), RY, ss * (int)sizeof(cplx<T>));
+    stage_x_twiddles(TW, TP, twx, twpost, mx);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int e = threadIdx.x; e < RY * mx; e += blockDim.x) {
+        const int r = ddiv(e, mx), kx = e - r * mx;
+        const cplx<T> *row = S + (size_t)r * ss;
         const cplx<T> xk = row[kx];
         const cplx<T> xm = conj(row[mx - kx]);
         const cplx<T> ev = xk + xm;
-        const cplx<T> od = (xk - xm) * conj(twpost[kx]);
+        const cplx<T> od = (xk - xm) * conj(TP[kx]);
         A[r * ls + kx] = ev + mul_i<T, 1>(od);
     }
     __syncthreads();
-    const cplx<T> *R = fft_lines<T, 1>(A, B, 1, ls, ry, fp, twx, false);
-    for (int r = 0; r < ry; ++r) {
+    const cplx<T> *R = fft_lines<T, 1>(A, B, 1, ls, RY, fp, TW, false);
+    const bool v16 = ((nx * sizeof(T)) & 15) == 0;
+    for (int r = 0; r < RY; ++r) {
         T *drow = dst + ((size_t)k * ny + j0 + r) * nx;
         const T *srow = reinterpret_cast<const T *>(R + (size_t)r * ls);
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) drow[i] = srow[i];
+        if (v16) {
+            const int per = nx * (int)sizeof(T) / 16;
+            for (int c = threadIdx.x; c < per; c += blockDim.x)
+                reinterpret_cast<uint4 *>(drow)[c] = reinterpret_cast<const uint4 *>(srow)[c];
+        } else {
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) drow[i] = srow[i];
+        }
     }
 }
 
 }  // namespace
 
+// x transforms: two line buffers, the twiddle tables and (inverse only) the
+// staged spectrum rows; ry rows per block
+template <typename T> size_t smem_rfft_x(const GridDev &g, int ry) {
+    return sizeof(cplx<T>) * (2 * (size_t)ry * fft_x_ls(g.mx) + fft_x_ls(g.mx) + fft_x_ls(g.mx + 1));
+}
+template <typename T> size_t smem_irfft_x(const GridDev &g, int ry) {
+    return smem_rfft_x<T>(g, ry) + sizeof(cplx<T>) * (size_t)ry * irfft_stage_row(g.mx);
+}
 template <typename T> size_t smem_fft_x(const GridDev &g, const Work<T> &W) {
-    return 2 * sizeof(cplx<T>) * (size_t)W.ry_fft * (g.mx | 1);
+    return smem_irfft_x<T>(g, W.ry_fft);
 }
 template <typename T> size_t smem_fft_y(const GridDev &g, const Work<T> &W) {
-    return 2 * sizeof(cplx<T>) * (size_t)W.tkx * g.ny;
+    return sizeof(cplx<T>) * (2 * (size_t)W.tkx * g.ny + g.ny);
 }
 template <typename T> size_t smem_poisson(const GridDev &g, const Work<T> &W) {
     const size_t rs = 2 * W.pz_poisson + 1;
@@ -299,16 +371,50 @@ template <typename T> size_t smem_poisson(const GridDev &g, const Work<T> &W) {
            sizeof(T) * (2 * (size_t)g.nz * W.tkx + 3 * W.tkx * rs + W.tkx + 3 * (size_t)g.nz);
 }
 
+// Launch geometry of the transforms and the z solve: rows per block of the x
+// transforms (up to 8 in single, 4 in double precision, dividing ny) and kx
+// columns per block of the y transform and z solve (up to 128 bytes of
+// complex values per row), each the largest whose shared memory, computed
+// exactly, fits the device limit.
+template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W) {
+    const size_t lim = (size_t)smem_optin() - 2048;
+    const int tsz = (int)sizeof(T);
+    W.ry_fft = 1;
+    for (int r = tsz == 8 ? 4 : 8; r >= 1; r /= 2)
+        if (g.ny % r == 0) { W.ry_fft = r; break; }
+    while (W.ry_fft > 1 && smem_fft_x<T>(g, W) > lim) W.ry_fft /= 2;
+    W.tkx = 128 / (2 * tsz);
+    for (;;) {
+        W.pz_poisson = 256 / W.tkx;
+        if (W.pz_poisson > g.nz / 3) W.pz_poisson = g.nz / 3;
+        if (W.pz_poisson < 1) W.pz_poisson = 1;
+        if (W.tkx <= 2 || (smem_poisson<T>(g, W) <= lim && smem_fft_y<T>(g, W) <= lim)) break;
+        W.tkx /= 2;
+    }
+}
+
+template <typename T, int MODE, int RY>
+void rfft_x_ry(const GridDev &g, Work<T> &W, const StepScalars *sc, const T *src, cudaStream_t st) {
+    const int blocks = g.nz * (g.ny / RY);
+    k_rfft_x<T, MODE, RY><<<blocks, 256, smem_rfft_x<T>(g, RY), st>>>(
+        g, W.q0, W.q1, W.q2, src, W.spec, W.twx, W.twpost, W.fpx, sc);
+}
+
+template <typename T, int MODE>
+void rfft_x_mode(const GridDev &g, Work<T> &W, const StepScalars *sc, const T *src,
+                 cudaStream_t st) {
+    switch (W.ry_fft) {
+    case 8: rfft_x_ry<T, MODE, 8>(g, W, sc, src, st); break;
+    case 4: rfft_x_ry<T, MODE, 4>(g, W, sc, src, st); break;
+    case 2: rfft_x_ry<T, MODE, 2>(g, W, sc, src, st); break;
+    default: rfft_x_ry<T, MODE, 1>(g, W, sc, src, st); break;
+    }
+}
+
 template <typename T> void launch_rfft_x(const GridDev &g, Work<T> &W, const StepScalars *sc,
                                          const T *src, int mode, cudaStream_t st) {
-    const int blocks = g.nz * (g.ny / W.ry_fft);
-    const int threads = 256;
-    if (mode == 0)
-        k_rfft_x<T, 0><<<blocks, threads, smem_fft_x(g, W), st>>>(
-            g, W.q0, W.q1, W.q2, nullptr, W.spec, W.twx, W.twpost, W.fpx, sc, W.ry_fft);
-    else
-        k_rfft_x<T, 1><<<blocks, threads, smem_fft_x(g, W), st>>>(
-            g, nullptr, nullptr, nullptr, src, W.spec, W.twx, W.twpost, W.fpx, sc, W.ry_fft);
+    if (mode == 0) rfft_x_mode<T, 0>(g, W, sc, nullptr, st);
+    else rfft_x_mode<T, 1>(g, W, sc, src, st);
 }
 
 template <typename T> void launch_fft_y(const GridDev &g, Work<T> &W, int inverse, cudaStream_t st) {
@@ -332,17 +438,36 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
         g, W.spec, W.lamx, W.lamy, W.exact, W.tkx, W.pz_poisson, T(scale));
 }
 
+template <typename T, int RY>
+void irfft_x_ry(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
+    const int blocks = g.nz * (g.ny / RY);
+    k_irfft_x<T, RY><<<blocks, 256, smem_irfft_x<T>(g, RY), st>>>(g, W.spec, dst, W.twx,
+                                                                  W.twpost, W.fpx);
+}
+
 template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
-    const int blocks = g.nz * (g.ny / W.ry_fft);
-    k_irfft_x<T><<<blocks, 256, smem_fft_x(g, W), st>>>(g, W.spec, dst, W.twx, W.twpost, W.fpx,
-                                                        W.ry_fft);
+    switch (W.ry_fft) {
+    case 8: irfft_x_ry<T, 8>(g, W, dst, st); break;
+    case 4: irfft_x_ry<T, 4>(g, W, dst, st); break;
+    case 2: irfft_x_ry<T, 2>(g, W, dst, st); break;
+    default: irfft_x_ry<T, 1>(g, W, dst, st); break;
+    }
 }
 
 template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<T> &W) {
     (void)0;  // every kernel of this file gets an attribute below, which loads it
-    raise_smem_limit(k_rfft_x<T, 0>);
-    raise_smem_limit(k_rfft_x<T, 1>);
-    raise_smem_limit(k_irfft_x<T>);
+    raise_smem_limit(k_rfft_x<T, 0, 1>);
+    raise_smem_limit(k_rfft_x<T, 0, 2>);
+    raise_smem_limit(k_rfft_x<T, 0, 4>);
+    raise_smem_limit(k_rfft_x<T, 0, 8>);
+    raise_smem_limit(k_rfft_x<T, 1, 1>);
+    raise_smem_limit(k_rfft_x<T, 1, 2>);
+    raise_smem_limit(k_rfft_x<T, 1, 4>);
+    raise_smem_limit(k_rfft_x<T, 1, 8>);
+    raise_smem_limit(k_irfft_x<T, 1>);
+    raise_smem_limit(k_irfft_x<T, 2>);
+    raise_smem_limit(k_irfft_x<T, 4>);
+    raise_smem_limit(k_irfft_x<T, 8>);
     raise_smem_limit(k_fft_y<T, 1>);
     raise_smem_limit(k_fft_y<T, -1>);
     raise_smem_limit(k_poisson_z<T>);
@@ -353,6 +478,7 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     template size_t smem_fft_x<T>(const GridDev &, const Work<T> &);                          \
     template size_t smem_fft_y<T>(const GridDev &, const Work<T> &);                          \
     template size_t smem_poisson<T>(const GridDev &, const Work<T> &);                        \
+    template void poisson_geometry<T>(const GridDev &, Work<T> &);                             \
     template void launch_rfft_x<T>(const GridDev &, Work<T> &, const StepScalars *, const T *, \
                                    int, cudaStream_t);                                        \
     template void launch_fft_y<T>(const GridDev &, Work<T> &, int, cudaStream_t);              \

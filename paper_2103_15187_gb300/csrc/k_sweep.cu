@@ -6,11 +6,13 @@
 //                 CFL time step), double reduction
 //   k_scalars     dt, beta = dt/(2 Re), gamma, rho of the step; resets the
 //                 step's reductions
-//   k_plans       matrix-only factors of the four sweep matrices (x, y, z at
-//                 centres, z at faces) for this step's beta
+//   k_plans       matrix-only factors of the two z sweep matrices (centres,
+//                 faces) for this step's beta; the uniform x and y lines need
+//                 only alpha and 1/c of their cyclic Toeplitz factorisation,
+//                 set by k_scalars
 //   k_rhs_x       H^n = -div(uu)^n, RHS = dt[gamma H^n + rho H^{n-1}
 //                 + Re^-1 L u^n - G p^n + f], stores H^n, solves
-//                 (I - beta L_x) q = RHS along x
+//                 (I - beta L_x) q = RHS along x (uni_solve)
 // (the y and z sweeps are in k_lines.cu)
 #include <string.h>
 
@@ -59,7 +61,15 @@ k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v, const T *__
     }
 }
 
-__global__ void k_scalars(StepScalars *sc, StepArgs a, int euler) {
+// alpha and 1/c of the cyclic Toeplitz factorisation (tri.cuh, uni_solve)
+// of (1 + 2r) I - r (E + E^-1)
+__device__ void uni_factors(double r, double &alpha, double &cinv) {
+    const double c = 0.5 * ((1.0 + 2.0 * r) + sqrt(1.0 + 4.0 * r));
+    alpha = r / c;
+    cinv = 1.0 / c;
+}
+
+__global__ void k_scalars(StepScalars *sc, StepArgs a, int euler, double idx2, double idy2) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double dt = a.dt;
     if (a.cfl > 0.0) {
@@ -73,6 +83,8 @@ __global__ void k_scalars(StepScalars *sc, StepArgs a, int euler) {
     sc->flags = 0;
     sc->dt = dt;
     sc->beta = dt / (2.0 * a.re);
+    uni_factors(sc->beta * idx2, sc->ax, sc->cix);
+    uni_factors(sc->beta * idy2, sc->ay, sc->ciy);
     sc->gamma = euler ? 1.0 : a.gamma;
     sc->rho = euler ? 0.0 : a.rho;
 }
@@ -106,7 +118,7 @@ struct SweepCoef {
 template <typename T>
 __global__ void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int kind = blockIdx.x;
+    const int kind = 2 + blockIdx.x;   // the z plans (x and y lines use uni_solve)
     const TriPlan<T> &pl = W.plan[kind];
     const TriPlanStore<T> &st = W.store[kind];
     const int n = pl.n, P = pl.P;
@@ -228,16 +240,18 @@ __global__ void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 4)
+// L: register chunk length of the x solve (>= nx / P).  Single precision
+// keeps four blocks per SM for chunks of up to 16; longer chunks (nx > 256)
+// take more registers.
+template <typename T, int L>
+__global__ void __launch_bounds__(256, L <= 16 ? (sizeof(T) == 4 ? 4 : 2) : (L <= 32 ? 2 : 1))
 k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
-        const StepScalars *sc, TriPlan<T> px, int ry, T fc0, T fc1, T fc2, T inv_re) {
+        const StepScalars *sc, int ry, int P, T fc0, T fc1, T fc2, T inv_re) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sd = reinterpret_cast<T *>(smraw);
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int nl = 3 * ry, es = nl | 1;
-    T *red = sd + (size_t)nx * es;
-    const int rs = 2 * px.P + 1;
+    T *car = sd + (size_t)nx * es;
     const int nby = ny / ry;
     const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * ry;
     const T dt = T(sc->dt), gam = T(sc->gamma), rho = T(sc->rho);
@@ -334,10 +348,25 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
         sd[i * es + 2 * ry + r] = rw;
       }
     }
-    // staged after the right-hand side so its loads start at once; its
-    // closing barrier also publishes the right-hand side in sd
-    const TriPlan<T> pxs = stage_plan(px, red + (size_t)nl * rs);
-    tri_plan_solve<T, T>(sd, es, 1, nl, pxs, red, rs);
+    __syncthreads();
+    // (I - beta L_x)^-1 along the nl lines: thread t < nl P owns chunk
+    // t / nl of line t % nl in registers
+    {
+        const int t = threadIdx.x;
+        const bool active = t < nl * P;
+        const int p = active ? t / nl : 0, l = active ? t - p * nl : 0;
+        const int s0 = chunk_start(p, nx, P);
+        const int len = active ? chunk_start(p + 1, nx, P) - s0 : 0;
+        T d[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < len) d[i] = sd[(s0 + i) * es + l];
+        uni_solve<T, L>(d, len, active, l, p, nl, nx, P, T(sc->ax), T(sc->cix), car);
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < len) sd[(s0 + i) * es + l] = d[i];
+    }
+    __syncthreads();
     for (int r = 0; r < ry; ++r) {
         const int o = (k * ny + j0 + r) * nx;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -351,13 +380,15 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
+void uni_geometry(int n, int nl, int maxthr, int &P, int &chunk) {
+    P = 1;
+    while (P < 32 && nl * 2 * P <= maxthr) P *= 2;
+    chunk = (n + P - 1) / P;
+}
+
 template <typename T> size_t smem_rhs_x(const GridDev &g, const Work<T> &W) {
     const int nl = 3 * W.ry, es = nl | 1;
-    return sizeof(T) * ((size_t)g.nx * es + (size_t)nl * (2 * W.plan[0].P + 1) +
-                        plan_stage_words(W.plan[0].n, W.plan[0].P));
-}
-template <typename T> size_t smem_sweep(int n, const Work<T> &W, int P) {
-    return sizeof(T) * ((size_t)n * W.tx + (size_t)W.tx * (2 * P + 1) + plan_stage_words(n, P));
+    return sizeof(T) * ((size_t)g.nx * es + 2 * (size_t)nl * W.px);
 }
 
 template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v, const T *w,
@@ -371,29 +402,38 @@ template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v
 
 template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepScalars *sc,
                                              const StepArgs &a, int euler, cudaStream_t st) {
-    k_scalars<<<1, 32, 0, st>>>(sc, a, euler);
+    k_scalars<<<1, 32, 0, st>>>(sc, a, euler, g.idx2, g.idy2);
     int maxn = 0, maxp = 0;
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 2; q < 4; ++q) {
         if (W.plan[q].n > maxn) maxn = W.plan[q].n;
         if (W.plan[q].P > maxp) maxp = W.plan[q].P;
     }
     const size_t sm = sizeof(double) * (2 * (size_t)maxn + 12 * (size_t)maxp);
     int thr = ((2 * maxp + 31) / 32) * 32;
-    k_plans<T><<<4, thr, sm, st>>>(g, W, sc);
+    k_plans<T><<<2, thr, sm, st>>>(g, W, sc);
 }
 
-template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
-                                        const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
+template <typename T, int L>
+void rhs_x_L(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
+             const StepArgs &a, cudaStream_t st) {
     const int nl = 3 * W.ry;
-    int threads = ((nl * W.plan[0].P + 31) / 32) * 32;
+    int threads = ((nl * W.px + 31) / 32) * 32;
     // the right-hand-side phase strides over x: a block as wide as a row (up
     // to the 256-thread bound) avoids a mostly idle second pass per row
     const int row_threads = g.nx < 256 ? ((g.nx + 31) / 32) * 32 : 256;
     if (threads < row_threads) threads = row_threads;
     const int blocks = g.nz * (g.ny / W.ry);
-    k_rhs_x<T><<<blocks, threads, smem_rhs_x(g, W), st>>>(
-        g, F, W.q0, W.q1, W.q2, sc, W.plan[0], W.ry, T(a.fconst[0]), T(a.fconst[1]),
-        T(a.fconst[2]), T(1.0 / a.re));
+    k_rhs_x<T, L><<<blocks, threads, smem_rhs_x(g, W), st>>>(
+        g, F, W.q0, W.q1, W.q2, sc, W.ry, W.px, T(a.fconst[0]), T(a.fconst[1]), T(a.fconst[2]),
+        T(1.0 / a.re));
+}
+
+template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
+                                        const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
+    if (W.chunk_x <= 8) rhs_x_L<T, 8>(g, F, W, sc, a, st);
+    else if (W.chunk_x <= 16) rhs_x_L<T, 16>(g, F, W, sc, a, st);
+    else if (W.chunk_x <= 32) rhs_x_L<T, 32>(g, F, W, sc, a, st);
+    else rhs_x_L<T, 64>(g, F, W, sc, a, st);
 }
 
 template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T> &W) {
@@ -405,12 +445,14 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     cudaFuncGetAttributes(&fa, k_plans<T>);
     (void)g;
     (void)W;
-    raise_smem_limit(k_rhs_x<T>);
+    raise_smem_limit(k_rhs_x<T, 8>);
+    raise_smem_limit(k_rhs_x<T, 16>);
+    raise_smem_limit(k_rhs_x<T, 32>);
+    raise_smem_limit(k_rhs_x<T, 64>);
 }
 
 #define FSEI_INST(T)                                                                           \
     template size_t smem_rhs_x<T>(const GridDev &, const Work<T> &);                          \
-    template size_t smem_sweep<T>(int, const Work<T> &, int);                                 \
     template void launch_speed<T>(const GridDev &, const T *, const T *, const T *,            \
                                   StepScalars *, cudaStream_t);                               \
     template void launch_step_begin<T>(const GridDev &, Work<T> &, StepScalars *,              \

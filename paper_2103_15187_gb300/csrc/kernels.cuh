@@ -27,13 +27,13 @@ template <typename T> struct Work {
     const int *nzm;          // near-zero modes to solve in double: kx + sk*ky
     int n_nzm;
     const unsigned char *exact;   // [ny][sk]: 1 for the modes in nzm
-    double *nz_scratch;      // unused scratch kept for layout compatibility
     T *adj0, *adj1, *adj2;   // adjoint workspace (allocated on first use)
     int ry;                  // rows per block of the x-line solves
     int ry_fft;              // rows per block of the x transforms
-    int tx;                  // (unused) x columns of the former shared-memory sweeps
     int chunk_y, chunk_z;    // register chunk length of the y / z sweeps
     int tx_y, tx_z;          // x columns per block of the y / z sweeps
+    int py;                  // chunks per y line
+    int px, chunk_x;         // chunks per x line and their length (x solves)
     int tkx;                 // kx columns per block of the y FFT / z Poisson
     int pz_poisson;          // chunks per z line in the Poisson solve
 };
@@ -49,7 +49,8 @@ template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepS
                                              const StepArgs &a, int euler, cudaStream_t st);
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st);
-template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, cudaStream_t st);
+template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, const StepScalars *sc,
+                                          cudaStream_t st);
 template <typename T> void launch_sweep_z(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                           cudaStream_t st);
 // mode 0: s = D(q0,q1,q2) / dt ; mode 1: s = the given field src (scaled 1)
@@ -95,7 +96,6 @@ template <typename F> inline void raise_smem_limit(F *kernel) {
 
 // dynamic shared memory bytes of each kernel (host-side sizing helpers)
 template <typename T> size_t smem_rhs_x(const GridDev &g, const Work<T> &W);
-template <typename T> size_t smem_sweep(int n, const Work<T> &W, int P);
 template <typename T> size_t smem_fft_x(const GridDev &g, const Work<T> &W);
 template <typename T> size_t smem_fft_y(const GridDev &g, const Work<T> &W);
 template <typename T> size_t smem_poisson(const GridDev &g, const Work<T> &W);
@@ -104,6 +104,15 @@ template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T>
 // chunk length, chunks per line and x columns per block of the register
 // sweeps for lines of n unknowns
 void sweep_geometry(int n, int &chunk, int &P, int &tx);
+// the same for the uniform periodic y sweep (uni_solve)
+void sweep_y_geometry(int n, int &chunk, int &P, int &tx);
+// chunks per line P (a power of two <= 32 with nl P <= maxthr) and chunk
+// length for nl uniform periodic lines of n unknowns solved by one block
+void uni_geometry(int n, int nl, int maxthr, int &P, int &chunk);
 template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<T> &W);
+// rows per block of the x transforms, kx columns per block of the y
+// transform and z solve, chunks per z line of the z solve (sets ry_fft, tkx,
+// pz_poisson)
+template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W);
 
 }  // namespace fsei

@@ -67,7 +67,7 @@ __host__ void unit_root(int m, int n, double *re, double *im) {
 // Byte offsets of the regions inside the scratch array.
 struct Layout {
     size_t sc, dz, idz, ihc, dzf, idzf, ihcf, twx, twy, twpost, lamx, lamy, lamxd, lamyd,
-        exact, nzm, tables_end, nzs, spec, total;
+        exact, nzm, tables_end, spec, total;
 };
 
 template <typename T>
@@ -93,7 +93,6 @@ Layout layout_for(int nx, int ny, int nz, int sk, int nmodes) {
     L.exact = take((size_t)sk * ny);
     L.nzm = take(sizeof(int) * nmodes);
     L.tables_end = o;
-    L.nzs = take(sizeof(double) * 4 * (size_t)nz * nmodes);
     L.spec = take(sizeof(cplx<T>) * (size_t)sk * ny * nz);
     L.total = o;
     return L;
@@ -219,20 +218,12 @@ fsei_status solve_noalloc(const fsei_grid_desc *d, const void *rhs, void *phi, c
     W.exact = (const unsigned char *)(dev + L.exact);
     W.nzm = (const int *)(dev + L.nzm);
     W.n_nzm = nm;
-    W.nz_scratch = (double *)(dev + L.nzs);
     // launch geometry (same rules as a grid handle of this shape)
     const int tsz = (int)sizeof(T);
     W.ry = 1;
     for (int r = (tsz == 8 ? 4 : 8); r >= 1; r /= 2)
         if (ny % r == 0) { W.ry = r; break; }
-    W.ry_fft = W.ry;
-    W.tkx = 128 / (2 * tsz);
-    while (W.tkx > 2 && ((size_t)nz * W.tkx * 4 * tsz > 200 * 1024 ||
-                         (size_t)2 * ny * W.tkx * 2 * tsz > 200 * 1024))
-        W.tkx /= 2;
-    W.pz_poisson = 256 / W.tkx;
-    if (W.pz_poisson > nz / 3) W.pz_poisson = nz / 3;
-    if (W.pz_poisson < 1) W.pz_poisson = 1;
+    poisson_geometry<T>(g, W);
     W.fpx.n = mx;
     W.fpy.n = ny;
     for (FftPlanDev *fp : {&W.fpx, &W.fpy}) {

@@ -126,68 +126,6 @@ __device__ TriPlan<T> stage_plan(const TriPlan<T> &in, T *sm) {
     return out;
 }
 
-// Solve nl lines held in shared memory with the matrix-only factors of a
-// TriPlan (same matrix for every line).  Element i of line l lives at
-// s[(i + plan.off) * es + l * ls].  Threads t < nl * P own chunk t / nl of
-// line t % nl.  red: shared scratch of nl * rs values (rs >= 2P).
-// Must be called by every thread of the block.
-template <typename T, typename V>
-__device__ void tri_plan_solve(V *s, int es, int ls, int nl, const TriPlan<T> &pl,
-                               V *red, int rs) {
-    const int t = threadIdx.x;
-    const int n = pl.n, P = pl.P;
-    const bool active = t < nl * P;
-    const int l = t % nl, p = t / nl;
-    int s0 = 0, e0 = 0;
-    V *d = s + l * ls + pl.off * es;
-    if (active) {
-        s0 = chunk_start(p, n, P);
-        e0 = chunk_start(p + 1, n, P) - 1;
-        // downward elimination of the interior
-        V *dp = d + (s0 + 1) * es;
-        const T *pa = pl.a + s0 + 1, *pinv = pl.inv + s0 + 1;
-        V prev = scl(*pinv, *dp);
-        *dp = prev;
-        for (int i = s0 + 2; i < e0; ++i) {
-            dp += es;
-            ++pa;
-            ++pinv;
-            prev = scl(*pinv, nmad(*pa, prev, *dp));
-            *dp = prev;
-        }
-        // upward pass: right-hand side part of x_{s+1} (through x_s, x_e)
-        V dh = *dp;
-        const V dhe = dh;
-        const T *pct = pl.ct + e0 - 2;
-        for (int i = e0 - 2; i > s0; --i) {
-            dp -= es;
-            dh = nmad(*pct, dh, *dp);
-            --pct;
-        }
-        red[l * rs + 2 * p] = nmad(pl.c[s0], dh, d[s0 * es]);
-        red[l * rs + 2 * p + 1] = nmad(pl.a[e0], dhe, d[e0 * es]);
-    }
-    __syncthreads();
-    reduced_lines<T>(red, rs, nl, pl);
-    __syncthreads();
-    if (active) {
-        const V F = red[l * rs + 2 * p], E = red[l * rs + 2 * p + 1];
-        d[s0 * es] = F;
-        V *dp = d + e0 * es;
-        *dp = E;
-        V x = E;
-        const T *pat = pl.at + e0 - 1, *pct = pl.ct + e0 - 1;
-        for (int i = e0 - 1; i > s0; --i) {
-            dp -= es;
-            x = nmad(*pct, x, nmad(*pat, F, *dp));
-            *dp = x;
-            --pat;
-            --pct;
-        }
-    }
-    __syncthreads();
-}
-
 // Same elimination with a matrix that differs per line (the Poisson z
 // systems, one per Fourier mode: real matrix, complex right-hand side).
 // The factors are computed on the fly: fa, fc hold a~, c~ (layout of the
@@ -307,6 +245,127 @@ __device__ void tri_fly_solve(cplx<T> *s, int es, int ls, T *fa, T *fc, int fes,
         }
     }
     __syncthreads();
+}
+
+// ------------------------------------- constant-coefficient periodic lines --
+// In the two uniform periodic directions every line has the same cyclic
+// Toeplitz matrix  A = (1 + 2r) I - r (E + E^-1),  r = beta / h^2,
+// E x_i = x_{i+1} (indices mod n).  It factors exactly as
+//     A = c (I - alpha E)(I - alpha E^-1),
+// c alpha = r, c (1 + alpha^2) = 1 + 2r, i.e.
+//     c = ((1 + 2r) + sqrt(1 + 4r)) / 2,  alpha = r / c  (0 <= alpha < 1),
+// so A^-1 y is two periodic first-order recurrences and a scaling:
+//     z_i = y_i + alpha z_{i+1},   x'_i = z_i + alpha x'_{i-1},   x = x' / c.
+// A line is cut into P chunks of consecutive unknowns (chunk p starts at
+// chunk_start(p, n, P)).  Each recurrence runs inside every chunk from a zero
+// carry; the true carries then follow from a cyclic recurrence over the
+// chunks, e.g. for the first one Z_p = zf_p + alpha^len_p Z_{p+1} (Z_p the
+// true value at the chunk's first unknown, zf_p the zero-carry one), and
+// each element gets alpha^distance times its chunk's carry added.  This is
+// the same inverse as the cyclic Thomas / Sherman-Morrison solve of the
+// paper's scheme, evaluated in another order.
+
+// Cyclic recurrences over the chunks of nl lines, one warp per group of
+// 32 / P lines (chunk p of a line in lane p of a width-P segment, P a power
+// of two <= 32).  v[l * P + p] holds the zero-carry end value of chunk p of
+// line l and is replaced by the carry that chunk p needs:
+//   BACK = 1:  Z_p = v_p + g_p Z_{p+1},  chunk p needs Z_{p+1}
+//   BACK = 0:  X_p = v_p + g_p X_{p-1},  chunk p needs X_{p-1}
+// with g_p = alpha^len_p and indices mod P.  Every thread of the block calls
+// it (the shuffles need whole warps); a barrier must separate it from the
+// writes of v and from the reads of the carries.
+template <typename T, int BACK>
+__device__ __forceinline__ void uni_carries(T *v, int nl, int n, int P, T alpha) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (int)((blockDim.x + 31) >> 5);
+    const int per = 32 / P;             // lines per warp
+    const int p = lane & (P - 1), seg = lane / P;
+    for (int l0 = wid * per; l0 < nl; l0 += nw * per) {
+        const int l = l0 + seg;
+        const bool on = l < nl;
+        const int len = chunk_start(p + 1, n, P) - chunk_start(p, n, P);
+        T g = T(1), a = alpha;
+        for (int e = len; e > 0; e >>= 1) {      // alpha^len by squaring
+            if (e & 1) g *= a;
+            a *= a;
+        }
+        T A = on ? v[l * P + p] : T(0), B = g;
+        // scan of the affine maps Z -> A + B Z along the segment
+        for (int s = 1; s < P; s <<= 1) {
+            const T A2 = BACK ? __shfl_down_sync(0xffffffffu, A, s, P)
+                              : __shfl_up_sync(0xffffffffu, A, s, P);
+            const T B2 = BACK ? __shfl_down_sync(0xffffffffu, B, s, P)
+                              : __shfl_up_sync(0xffffffffu, B, s, P);
+            if (BACK ? (p + s < P) : (p >= s)) {
+                A = A + B * A2;
+                B = B * B2;
+            }
+        }
+        // the composition over the whole cycle closes it: V = A / (1 - B)
+        // at lane 0 (BACK) or lane P-1; then V_p = A_p + B_p V
+        const int root = BACK ? 0 : P - 1;
+        const T Ar = __shfl_sync(0xffffffffu, A, root, P);
+        const T Br = __shfl_sync(0xffffffffu, B, root, P);
+        const T V = Ar * rcp(T(1) - Br);
+        const T mine = A + B * V;
+        // carry of chunk p: value of the next (BACK) or previous chunk
+        const T nb = BACK ? __shfl_down_sync(0xffffffffu, mine, 1, P)
+                          : __shfl_up_sync(0xffffffffu, mine, 1, P);
+        const T carry = BACK ? (p == P - 1 ? V : nb) : (p == 0 ? V : nb);
+        if (on) v[l * P + p] = carry;
+    }
+}
+
+// Solve the chunks of nl constant-coefficient periodic lines, chunk p of
+// line l held by one thread in d[0 .. len-1] (active threads only).  car:
+// shared scratch of 2 nl P values.  Every thread of the block calls it; it
+// contains barriers.
+template <typename T, int L>
+__device__ __forceinline__ void uni_solve(T (&d)[L], int len, bool active, int l, int p, int nl,
+                                          int n, int P, T alpha, T cinv, T *car) {
+    T *zc = car, *xc = car + nl * P;
+    if (active) {
+        T z = T(0);
+#pragma unroll
+        for (int i = L - 1; i >= 0; --i)
+            if (i < len) {
+                z = d[i] + alpha * z;
+                d[i] = z;
+            }
+        zc[l * P + p] = z;          // zero-carry value at the chunk's first unknown
+    }
+    __syncthreads();
+    uni_carries<T, 1>(zc, nl, n, P, alpha);
+    __syncthreads();
+    if (active) {
+        T pw = zc[l * P + p];       // Z of the next chunk
+#pragma unroll
+        for (int i = L - 1; i >= 0; --i)
+            if (i < len) {
+                pw *= alpha;
+                d[i] += pw;
+            }
+        T x = T(0);
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < len) {
+                x = d[i] + alpha * x;
+                d[i] = x;
+            }
+        xc[l * P + p] = x;          // zero-carry value at the chunk's last unknown
+    }
+    __syncthreads();
+    uni_carries<T, 0>(xc, nl, n, P, alpha);
+    __syncthreads();
+    if (active) {
+        T pw = xc[l * P + p];       // X of the previous chunk
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < len) {
+                pw *= alpha;
+                d[i] = (d[i] + pw) * cinv;
+            }
+    }
 }
 
 }  // namespace fsei
