@@ -82,13 +82,13 @@ struct DevAllocs {
 
 enum KernelKind {
     KK_SPEED, KK_BEGIN, KK_RHS_X, KK_SWEEP_Y, KK_SWEEP_Z, KK_RFFT_X, KK_FFT_Y, KK_POISSON_Z,
-    KK_IFFT_Y, KK_IRFFT_X, KK_PROJECT, KK_COUNT
+    KK_IFFT_Y, KK_IRFFT_X, KK_PROJECT, KK_PLANS, KK_COUNT
 };
 const char *const kKernelNames[KK_COUNT] = {
-    "speed (CFL reduction)", "step_begin (scalars + sweep plans)", "rhs_x (RHS + x sweep)",
+    "speed (CFL reduction)", "step_begin (scalars)", "rhs_x (RHS + x sweep)",
     "sweep_y", "sweep_z (+ u*)", "rfft_x (div + x R2C)", "fft_y (forward)",
     "poisson_z (+ exact modes)", "fft_y (inverse)", "irfft_x (x C2R)",
-    "project (+ p update, stats)"};
+    "project (+ p update, stats)", "z-sweep plans (side stream)"};
 
 // Event pairs recorded around kernel launches while timing is enabled.
 struct KernelTimer {
@@ -158,13 +158,113 @@ struct fsei_grid_s {
     StepScalars *sc = nullptr;      // device
     StepScalars *sc_host = nullptr; // pinned
     KernelTimer timer;
+    // side stream and fork/join events: the z-sweep plans run beside the
+    // RHS and y sweep
+    Overlap ov_plans{};
 };
 
 namespace {
 
+fsei_status create_overlap(fsei_grid_s *G) {
+    cudaStream_t side = nullptr;
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(FSEI_E_CUDA, "side stream creation failed");
+    G->ov_plans.side = side;
+    cudaEvent_t *evs[2] = {&G->ov_plans.fork, &G->ov_plans.join};
+    for (cudaEvent_t *e : evs)
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
+            return fail(FSEI_E_CUDA, "event creation failed");
+    return FSEI_OK;
+}
+
+void destroy_overlap(fsei_grid_s *G) {
+    cudaEvent_t evs[2] = {G->ov_plans.fork, G->ov_plans.join};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (G->ov_plans.side) cudaStreamDestroy(G->ov_plans.side);
+    G->ov_plans = Overlap{};
+}
+
+}  // namespace
+
+namespace {
+
+// Thomas factors of the z systems of the exactly solved Poisson modes
+// (grid constants), in extended precision: per mode the rows i < n of
+// (L_z - lambda) phi = s (the (0, 0) mode: rows k = 1 .. nz-1 with phi_0 = 0)
+// and, for cyclic lines, the Sherman-Morrison data; layout as Work::xa.
+struct ExactFactors {
+    std::vector<double> xa, xm, xc, xz, xs;
+};
+
+ExactFactors exact_factors(int nz, bool walls, const std::vector<double> &idz,
+                           const std::vector<double> &ihc, const std::vector<double> &lamx,
+                           const std::vector<double> &lamy, int sk, const std::vector<int> &nzm) {
+    typedef long double R;
+    ExactFactors f;
+    const size_t nm = nzm.size();
+    f.xa.assign(nm * nz, 0.0);
+    f.xm.assign(nm * nz, 0.0);
+    f.xc.assign(nm * nz, 0.0);
+    f.xz.assign(nm * nz, 0.0);
+    f.xs.assign(2 * nm, 0.0);
+    auto acut = [&](int k) -> R { return (walls && k == 0) ? 0.0L : (R)ihc[k] * (R)idz[k]; };
+    auto ccut = [&](int k) -> R {
+        return (walls && k == nz - 1) ? 0.0L : (R)ihc[k + 1] * (R)idz[k];
+    };
+    for (size_t m = 0; m < nm; ++m) {
+        const int kx = nzm[m] % sk, ky = nzm[m] / sk;
+        const bool zero = kx == 0 && ky == 0;
+        const bool cyclic = !walls && !zero;
+        const int shift = zero ? 1 : 0, n = nz - shift;
+        const R lam = (R)lamx[kx] + (R)lamy[ky];
+        std::vector<R> a(n), b(n), c(n), xa(n), xm(n), xc(n);
+        for (int i = 0; i < n; ++i) {
+            const int k = i + shift;
+            a[i] = acut(k);
+            c[i] = ccut(k);
+            b[i] = -(acut(k) + ccut(k)) - lam;
+        }
+        R gam = 0.0L;
+        if (cyclic) {
+            gam = -b[0];
+            b[0] -= gam;
+            b[n - 1] -= a[0] * c[n - 1] / gam;
+        }
+        for (int i = 0; i < n; ++i) {
+            const R den = i == 0 ? b[0] : b[i] - a[i] * xc[i - 1];
+            xm[i] = 1.0L / den;
+            xa[i] = i == 0 ? 0.0L : -a[i] * xm[i];
+            xc[i] = i == n - 1 ? 0.0L : c[i] * xm[i];
+        }
+        const size_t o = m * (size_t)nz;
+        for (int i = 0; i < n; ++i) {
+            f.xa[o + i] = (double)xa[i];
+            f.xm[o + i] = (double)xm[i];
+            f.xc[o + i] = (double)xc[i];
+        }
+        if (cyclic) {
+            // z = T^-1 u, u = (gamma, 0, ..., 0, c_{n-1})
+            std::vector<R> z(n);
+            for (int i = 0; i < n; ++i) {
+                const R ui = i == 0 ? gam : (i == n - 1 ? c[n - 1] : 0.0L);
+                z[i] = (i == 0 ? 0.0L : xa[i] * z[i - 1]) + xm[i] * ui;
+            }
+            for (int i = n - 2; i >= 0; --i) z[i] -= xc[i] * z[i + 1];
+            const R vl = a[0] / gam;
+            for (int i = 0; i < n; ++i) f.xz[o + i] = (double)z[i];
+            f.xs[2 * m] = (double)vl;
+            f.xs[2 * m + 1] = (double)(1.0L / (1.0L + z[0] + vl * z[n - 1]));
+        }
+    }
+    return f;
+}
+
 template <typename T>
 fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &lamx,
-                       const std::vector<double> &lamy, const std::vector<int> &nzm) {
+                       const std::vector<double> &lamy, const std::vector<int> &nzm,
+                       const std::vector<double> &dz, const std::vector<double> &idz,
+                       const std::vector<double> &ihc) {
     GridDev &g = G->g;
     DevAllocs &M = G->mem;
     const size_t ncell = (size_t)g.nx * g.ny * g.nz;
@@ -270,6 +370,22 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
         W.nzm = dm;
         W.n_nzm = (int)nzm.size();
     }
+    {
+        const ExactFactors ef = exact_factors(g.nz, g.walls != 0, idz, ihc, lamx, lamy, g.sk, nzm);
+        double *xa = M.get<double>(ef.xa.size()), *xm = M.get<double>(ef.xm.size());
+        double *xc = M.get<double>(ef.xc.size()), *xz = M.get<double>(ef.xz.size());
+        double *xs = M.get<double>(ef.xs.size());
+        if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "table allocation failed");
+        upload(xa, ef.xa);
+        upload(xm, ef.xm);
+        upload(xc, ef.xc);
+        upload(xz, ef.xz);
+        upload(xs, ef.xs);
+        W.xa = xa; W.xm = xm; W.xc = xc; W.xz = xz; W.xs = xs;
+        double zl = 0.0;
+        for (double d : dz) zl += d;
+        W.zlen = zl;
+    }
     if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "table allocation failed");
     set_smem_limits_sweep<T>(g, W);
     set_smem_limits_lines<T>(g, W);
@@ -297,9 +413,17 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
     }
     for (int n = 0; n < nsteps; ++n) {
         const int euler = (n == 0 && !s->have_prev_h) ? 1 : 0;
-        tm.run(KK_BEGIN, st, [&] { launch_step_begin<T>(g, W, G->sc, a, euler, st); });
+        tm.run(KK_BEGIN, st, [&] { launch_step_scalars(g, G->sc, a, euler, st); });
+        // the z-sweep plans depend on this step's beta and are first read by
+        // the z sweep: they run on the side stream beside rhs_x and sweep_y
+        const Overlap &op = G->ov_plans;
+        cudaEventRecord(op.fork, st);
+        cudaStreamWaitEvent(op.side, op.fork, 0);
+        tm.run(KK_PLANS, op.side, [&] { launch_step_plans<T>(g, W, G->sc, op.side); });
+        cudaEventRecord(op.join, op.side);
         tm.run(KK_RHS_X, st, [&] { launch_rhs_x<T>(g, F, W, G->sc, a, st); });
         tm.run(KK_SWEEP_Y, st, [&] { launch_sweep_y<T>(g, W, G->sc, st); });
+        cudaStreamWaitEvent(st, op.join, 0);
         tm.run(KK_SWEEP_Z, st, [&] { launch_sweep_z<T>(g, F, W, st); });
         tm.run(KK_RFFT_X, st, [&] { launch_rfft_x<T>(g, W, G->sc, nullptr, 0, st); });
         tm.run(KK_FFT_Y, st, [&] { launch_fft_y<T>(g, W, 0, st); });
@@ -406,6 +530,7 @@ fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
     g.dx = d->lx / nx; g.dy = d->ly / ny;
     g.idx = 1.0 / g.dx; g.idy = 1.0 / g.dy;
     g.idx2 = g.idx * g.idx; g.idy2 = g.idy * g.idy;
+    grid_float_copies(g);
     DevAllocs &M = G->mem;
     double *ddz = M.get<double>(nz), *didz = M.get<double>(nz), *dihc = M.get<double>(nz + 1);
     float *fdz = M.get<float>(nz), *fidz = M.get<float>(nz), *fihc = M.get<float>(nz + 1);
@@ -449,9 +574,12 @@ fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
                 if ((lamx[kx] + lamy[ky]) * lz * lz < tau) nzm.push_back(kx + g.sk * ky);
             }
     }
-    fsei_status st = d->prec == FSEI_FP64 ? setup_work<double>(G, G->wd, lamx, lamy, nzm)
-                                          : setup_work<float>(G, G->wf, lamx, lamy, nzm);
+    fsei_status st = d->prec == FSEI_FP64
+                         ? setup_work<double>(G, G->wd, lamx, lamy, nzm, dz, idz, ihc)
+                         : setup_work<float>(G, G->wf, lamx, lamy, nzm, dz, idz, ihc);
+    if (st == FSEI_OK) st = create_overlap(G);
     if (st != FSEI_OK) {
+        destroy_overlap(G);
         cudaFreeHost(G->sc_host);
         M.release();
         delete G;
@@ -459,6 +587,7 @@ fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
     }
     const cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
+        destroy_overlap(G);
         cudaFreeHost(G->sc_host);
         M.release();
         delete G;
@@ -472,6 +601,7 @@ void fsei_grid_destroy(fsei_grid G) {
     if (!G) return;
     DeviceGuard dg(G->device);
     cudaDeviceSynchronize();
+    destroy_overlap(G);
     if (G->sc_host) cudaFreeHost(G->sc_host);
     G->mem.release();
     delete G;

@@ -39,7 +39,25 @@ struct GridDev {
     double dx, dy, idx, idy, idx2, idy2;
     const double *dz, *idz, *ihc;   // dz[nz], 1/dz[nz], 1/hc[nz+1]
     const float *dzf, *idzf, *ihcf;
+    // float roundings of dx, dy, idx, idy, idx2, idy2 and dx dy (the
+    // single-precision kernels read these rather than convert per thread:
+    // GB300's double-precision pipe is narrow)
+    float fdx, fdy, fidx, fidy, fidx2, fidy2, fvxy;
 };
+
+// Set the float copies of a GridDev's double x/y spacings.
+inline void grid_float_copies(GridDev &g) {
+    g.fdx = (float)g.dx; g.fdy = (float)g.dy;
+    g.fidx = (float)g.idx; g.fidy = (float)g.idy;
+    g.fidx2 = (float)g.idx2; g.fidy2 = (float)g.idy2;
+    g.fvxy = (float)(g.dx * g.dy);
+}
+
+// The double (T = double) or float (T = float) copy of a scalar kept in
+// both precisions.
+template <typename T> FSEI_HD T fpick(double d, float f);
+template <> FSEI_HD double fpick<double>(double d, float) { return d; }
+template <> FSEI_HD float fpick<float>(double, float f) { return f; }
 
 template <typename T> struct Metric;
 template <> struct Metric<double> {
@@ -70,6 +88,10 @@ struct StepScalars {
     // factors of the uniform periodic x and y sweep matrices (tri.cuh,
     // uni_solve): alpha and 1/c for r = beta/dx^2 and beta/dy^2
     double ax, cix, ay, ciy;
+    double invdt;         // 1 / dt
+    // float roundings of dt, beta, gamma, rho, 1/dt and the four factors
+    // above, for the single-precision kernels
+    float fdt, fbeta, fgamma, frho, finvdt, fax, fcix, fay, fciy;
 };
 
 // --------------------------------------------- partitioned tridiagonal -----
@@ -101,7 +123,15 @@ template <typename T> struct TriPlanStore {
     T *pk1, *pk2, *pdinv;
 };
 
-FSEI_HD int chunk_start(int p, int n, int P) { return (int)(((long long)p * n) / P); }
+// p n < 2^31 for the line lengths and chunk counts used here (n <= 2048,
+// P <= 64); P is usually a power of two (a shift)
+FSEI_HD int chunk_start(int p, int n, int P) {
+#ifdef __CUDA_ARCH__
+    return (P & (P - 1)) == 0 ? (p * n) >> (31 - __clz(P)) : (p * n) / P;
+#else
+    return (p * n) / P;
+#endif
+}
 
 // An opaque copy of a pointer: addresses formed from it are recomputed
 // rather than kept live in registers from an earlier use of the original.

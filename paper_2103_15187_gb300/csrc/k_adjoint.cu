@@ -49,8 +49,9 @@ k_adj_phibar(GridDev g, const T *__restrict__ ub, const T *__restrict__ vb,
              const StepScalars *sc) {
     const Nb N{g.nx, g.ny, g.nz, g.walls};
     const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
-    const T dt = T(sc->dt), beta = T(sc->beta);
-    const T idx = T(g.idx), idy = T(g.idy), idx2 = T(g.idx2), idy2 = T(g.idy2);
+    const T dt = fpick<T>(sc->dt, sc->fdt), beta = fpick<T>(sc->beta, sc->fbeta);
+    const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
+    const T idx2 = fpick<T>(g.idx2, g.fidx2), idy2 = fpick<T>(g.idy2, g.fidy2);
     const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
     const int nz = g.nz;
     const bool walls = g.walls != 0;
@@ -82,9 +83,9 @@ k_adj_ustar(GridDev g, T *__restrict__ ub, T *__restrict__ vb, T *__restrict__ w
             T *__restrict__ q2, const StepScalars *sc) {
     const Nb N{g.nx, g.ny, g.nz, g.walls};
     const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
-    const T idt = T(1.0 / sc->dt);
+    const T idt = fpick<T>(sc->invdt, sc->finvdt);
     const T *dz = Metric<T>::dz(g), *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
-    const T dxv = T(g.dx), dyv = T(g.dy);
+    const T dxv = fpick<T>(g.dx, g.fdx), dyv = fpick<T>(g.dy, g.fdy);
     const bool wall_face = g.walls && k == 0;
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
         const size_t c = fid(i, j, k, g.nx, g.ny);
@@ -135,7 +136,8 @@ k_sweep_x(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
 #pragma unroll
         for (int i = 0; i < L; ++i)
             if (i < len) d[i] = sd[(s0 + i) * es + l];
-        uni_solve<T, L>(d, len, active, l, p, ry, nx, P, T(sc->ax), T(sc->cix), car);
+        uni_solve<T, L>(d, len, active, l, p, ry, nx, P, fpick<T>(sc->ax, sc->fax),
+                        fpick<T>(sc->cix, sc->fcix), car);
 #pragma unroll
         for (int i = 0; i < L; ++i)
             if (i < len) sd[(s0 + i) * es + l] = d[i];
@@ -154,7 +156,8 @@ k_adj_hist(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
            T *__restrict__ hbw, T *__restrict__ h0, T *__restrict__ h1, T *__restrict__ h2,
            T *fbx, T *fby, T *fbz, const StepScalars *sc) {
     const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
-    const T dt = T(sc->dt), gam = T(sc->gamma), rho = T(sc->rho);
+    const T dt = fpick<T>(sc->dt, sc->fdt), gam = fpick<T>(sc->gamma, sc->fgamma);
+    const T rho = fpick<T>(sc->rho, sc->frho);
     const bool wall_face = g.walls && k == 0;
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
         const size_t c = fid(i, j, k, g.nx, g.ny);
@@ -184,8 +187,9 @@ k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
     const int nz = g.nz;
     const bool walls = g.walls != 0;
     const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
-    const T dt = T(sc->dt);
-    const T idx = T(g.idx), idy = T(g.idy), idx2 = T(g.idx2), idy2 = T(g.idy2);
+    const T dt = fpick<T>(sc->dt, sc->fdt);
+    const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
+    const T idx2 = fpick<T>(g.idx2, g.fidx2), idy2 = fpick<T>(g.idy2, g.fidy2);
     const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
     const T h = T(0.5);
     auto IDZ = [&](int kk) { return idz[N.wzi(kk)]; };

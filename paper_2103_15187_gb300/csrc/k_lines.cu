@@ -186,7 +186,8 @@ k_sweep_y_uni(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__
 #pragma unroll
     for (int i = 0; i < L; ++i)
         if (i < len) d[i] = qp[i * nx];
-    uni_solve<T, L>(d, len, active, l, p, tx, ny, P, T(sc->ay), T(sc->ciy), car);
+    uni_solve<T, L>(d, len, active, l, p, tx, ny, P, fpick<T>(sc->ay, sc->fay),
+                    fpick<T>(sc->ciy, sc->fciy), car);
     T *qs = fresh(qp);
 #pragma unroll
     for (int i = 0; i < L; ++i)

@@ -67,10 +67,10 @@ k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
         stage_x_twiddles(TW, TP, twx, twpost, mx);
         cp_async_wait_all();
     } else {
-        const T invdt = T(1.0 / sc->dt);
+        const T invdt = fpick<T>(sc->invdt, sc->finvdt);
         const bool hasup = !g.walls || k < nz - 1;
         const int ku = k == nz - 1 ? 0 : k + 1;
-        const T idx = T(g.idx), idy = T(g.idy);
+        const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
         const T idzk = Metric<T>::idz(g)[k];
         const int oc0 = (k * ny + j0) * nx, ou0 = (ku * ny + j0) * nx;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -286,6 +286,138 @@ k_poisson_exact(GridDev g, cplx<T> *spec, const int *modes, const double *lamx,
         line[(size_t)k * stride] = cplx<T>{T((D[k].re - mr) * scale), T((D[k].im - mi) * scale)};
 }
 
+// Exactly solved modes with factors computed at grid creation: one warp
+// per mode solves, in double, the forward recurrence y_i = xa_i y_{i-1} +
+// xm_i s_i and the backward one phi_i = y_i - xc_i phi_{i+1} (Thomas'
+// algorithm) as parallel scans of affine maps: lane l composes the maps of
+// its E consecutive rows, a shuffle scan over the lanes gives each lane its
+// incoming value, and the lane re-runs its rows from it.  Cyclic lines (a
+// non-zero mode with periodic z) add the Sherman-Morrison correction phi -=
+// xz (v . y) / (1 + v . z), v . y = y_0 + v_last y_{n-1}.  The (0, 0) mode
+// pins phi_0 = 0 (rows 1 .. nz-1) and removes the volume-weighted mean, as
+// k_poisson_exact does.
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_poisson_exact_f(GridDev g, cplx<T> *spec, const int *modes, const double *xa,
+                  const double *xm, const double *xc, const double *xz, const double *xs,
+                  double scale, int compat, double zlen) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<double> *D = reinterpret_cast<cplx<double> *>(smraw);
+    const int nz = g.nz, lane = threadIdx.x;
+    const int mode = blockIdx.x, code = modes[mode];
+    const int kx = code % g.sk, ky = code / g.sk;
+    const bool zero_mode = kx == 0 && ky == 0;
+    const bool cyclic = !g.walls && !zero_mode;
+    const size_t stride = (size_t)g.ny * g.sk;
+    cplx<T> *line = spec + (size_t)ky * g.sk + kx;
+    for (int k = lane; k < nz; k += 32) {
+        const cplx<T> v = line[(size_t)k * stride];
+        D[k] = cplx<double>{(double)v.re, (double)v.im};
+    }
+    __syncwarp();
+    // dz-weighted mean of the line (warp reduction)
+    auto wmean = [&](double &mr, double &mi) {
+        double sr = 0.0, si = 0.0;
+        for (int k = lane; k < nz; k += 32) {
+            sr += D[k].re * g.dz[k];
+            si += D[k].im * g.dz[k];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        mr = sr / zlen;
+        mi = si / zlen;
+    };
+    if (zero_mode && compat) {
+        double mr, mi;
+        wmean(mr, mi);
+        __syncwarp();
+        for (int k = lane; k < nz; k += 32) { D[k].re -= mr; D[k].im -= mi; }
+        __syncwarp();
+    }
+    const int shift = zero_mode ? 1 : 0, n = nz - shift;
+    cplx<double> *d = D + shift;
+    const size_t o = (size_t)mode * nz;
+    const double *A = xa + o, *M = xm + o, *C = xc + o;
+    const int E = (n + 31) / 32;
+    const int i0 = lane * E < n ? lane * E : n, i1 = i0 + E < n ? i0 + E : n;
+    // forward: y_i = A_i y_{i-1} + M_i s_i
+    {
+        double ga = 1.0, gr = 0.0, gi = 0.0;
+        for (int i = i0; i < i1; ++i) {
+            ga = A[i] * ga;
+            gr = A[i] * gr + M[i] * d[i].re;
+            gi = A[i] * gi + M[i] * d[i].im;
+        }
+        for (int s = 1; s < 32; s <<= 1) {
+            const double pa = __shfl_up_sync(0xffffffffu, ga, s);
+            const double pr = __shfl_up_sync(0xffffffffu, gr, s);
+            const double pi = __shfl_up_sync(0xffffffffu, gi, s);
+            if (lane >= s) {
+                gr = ga * pr + gr;
+                gi = ga * pi + gi;
+                ga = ga * pa;
+            }
+        }
+        double yr = __shfl_up_sync(0xffffffffu, gr, 1), yi = __shfl_up_sync(0xffffffffu, gi, 1);
+        if (lane == 0) yr = yi = 0.0;
+        for (int i = i0; i < i1; ++i) {
+            yr = A[i] * yr + M[i] * d[i].re;
+            yi = A[i] * yi + M[i] * d[i].im;
+            d[i] = cplx<double>{yr, yi};
+        }
+    }
+    __syncwarp();
+    // backward: phi_i = y_i - C_i phi_{i+1}
+    {
+        double ga = 1.0, gr = 0.0, gi = 0.0;
+        for (int i = i1 - 1; i >= i0; --i) {
+            ga = -C[i] * ga;
+            gr = d[i].re - C[i] * gr;
+            gi = d[i].im - C[i] * gi;
+        }
+        for (int s = 1; s < 32; s <<= 1) {
+            const double pa = __shfl_down_sync(0xffffffffu, ga, s);
+            const double pr = __shfl_down_sync(0xffffffffu, gr, s);
+            const double pi = __shfl_down_sync(0xffffffffu, gi, s);
+            if (lane + s < 32) {
+                gr = ga * pr + gr;
+                gi = ga * pi + gi;
+                ga = ga * pa;
+            }
+        }
+        double xr = __shfl_down_sync(0xffffffffu, gr, 1), xi = __shfl_down_sync(0xffffffffu, gi, 1);
+        if (lane == 31) xr = xi = 0.0;
+        for (int i = i1 - 1; i >= i0; --i) {
+            xr = d[i].re - C[i] * xr;
+            xi = d[i].im - C[i] * xi;
+            d[i] = cplx<double>{xr, xi};
+        }
+    }
+    __syncwarp();
+    if (cyclic) {
+        const double vl = xs[2 * mode], fac = xs[2 * mode + 1];
+        const double sr = fac * (d[0].re + vl * d[n - 1].re);
+        const double si = fac * (d[0].im + vl * d[n - 1].im);
+        __syncwarp();
+        const double *Z = xz + o;
+        for (int i = lane; i < n; i += 32) {
+            d[i].re -= Z[i] * sr;
+            d[i].im -= Z[i] * si;
+        }
+        __syncwarp();
+    }
+    double mr = 0.0, mi = 0.0;
+    if (zero_mode) {
+        if (lane == 0) D[0] = cplx<double>{0.0, 0.0};
+        __syncwarp();
+        wmean(mr, mi);
+    }
+    for (int k = lane; k < nz; k += 32)
+        line[(size_t)k * stride] = cplx<T>{T((D[k].re - mr) * scale), T((D[k].im - mi) * scale)};
+}
+
 size_t smem_exact(int nz, int P) {
     const size_t rs = 2 * P + 1;
     return sizeof(cplx<double>) * (nz + rs) + sizeof(double) * (2 * (size_t)nz + 3 * rs);
@@ -430,10 +562,16 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
     const int blocks = g.ny * (g.sk / W.tkx);
     const int threads = ((W.tkx * W.pz_poisson + 31) / 32) * 32;
     const double scale = 1.0 / ((double)g.nx * g.ny);
-    // exact modes first: they read the untouched right-hand side
-    const int Pe = exact_chunks(g.nz);
-    k_poisson_exact<T><<<W.n_nzm, 64, smem_exact(g.nz, Pe), st>>>(
-        g, W.spec, W.nzm, W.lamx_d, W.lamy_d, scale, compat, Pe);
+    // exact modes first: they read the untouched right-hand side, and
+    // k_poisson_z leaves them alone
+    if (W.xa) {
+        k_poisson_exact_f<T><<<W.n_nzm, 32, sizeof(cplx<double>) * g.nz, st>>>(
+            g, W.spec, W.nzm, W.xa, W.xm, W.xc, W.xz, W.xs, scale, compat, W.zlen);
+    } else {
+        const int Pe = exact_chunks(g.nz);
+        k_poisson_exact<T><<<W.n_nzm, 64, smem_exact(g.nz, Pe), st>>>(
+            g, W.spec, W.nzm, W.lamx_d, W.lamy_d, scale, compat, Pe);
+    }
     k_poisson_z<T><<<blocks, threads, smem_poisson(g, W), st>>>(
         g, W.spec, W.lamx, W.lamy, W.exact, W.tkx, W.pz_poisson, T(scale));
 }
@@ -472,6 +610,7 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     raise_smem_limit(k_fft_y<T, -1>);
     raise_smem_limit(k_poisson_z<T>);
     raise_smem_limit(k_poisson_exact<T>);
+    raise_smem_limit(k_poisson_exact_f<T>);
 }
 
 #define FSEI_INST(T)                                                                           \

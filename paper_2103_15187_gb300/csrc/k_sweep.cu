@@ -34,7 +34,8 @@ k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v, const T *__
     const int k = blockIdx.x / nbj, j0 = (blockIdx.x % nbj) * rows;
     const bool hasup = !g.walls || k < nz - 1;
     const int ku = k == nz - 1 ? 0 : k + 1;
-    const T idx = T(g.idx), idy = T(g.idy), idzk = Metric<T>::idz(g)[k];
+    const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
+    const T idzk = Metric<T>::idz(g)[k];
     T m = T(0);
     for (int r = 0; r < rows; ++r) {
         const int j = j0 + r, jp = j == ny - 1 ? 0 : j + 1;
@@ -87,6 +88,16 @@ __global__ void k_scalars(StepScalars *sc, StepArgs a, int euler, double idx2, d
     uni_factors(sc->beta * idy2, sc->ay, sc->ciy);
     sc->gamma = euler ? 1.0 : a.gamma;
     sc->rho = euler ? 0.0 : a.rho;
+    sc->invdt = 1.0 / dt;
+    sc->fdt = (float)dt;
+    sc->fbeta = (float)sc->beta;
+    sc->fgamma = (float)sc->gamma;
+    sc->frho = (float)sc->rho;
+    sc->finvdt = (float)sc->invdt;
+    sc->fax = (float)sc->ax;
+    sc->fcix = (float)sc->cix;
+    sc->fay = (float)sc->ay;
+    sc->fciy = (float)sc->ciy;
 }
 
 // Coefficients of the four sweep matrices, in double.  Row i of a line:
@@ -240,9 +251,138 @@ __global__ void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
     }
 }
 
+// Stencil values around one point (i, j, k) read by the divergence-form
+// advection, the Laplacian and the pressure gradient: u, v, w, p at the
+// point and at its neighbours (ip/im: i +- 1, jp/jm: j +- 1, kp/km and
+// ku/kd: k +- 1; a neighbour beyond a wall is 0).
+template <typename T> struct Stencil {
+    T u0, uip, uim, ujp, ujm, ukp, ukm, u_ip_jm, u_ip_kd;
+    T v0, vip, vim, vjp, vjm, vkp, vkm, v_im_jp, v_jp_kd;
+    T w0, wip, wim, wjp, wjm, wku, wkd, w_im_ku, w_jm_ku;
+    T p0, pim, pjm, pkd;
+};
+
+// Step and plane-k coefficients of the point formula.
+template <typename T> struct RhsCoef {
+    T dt, gam, rho, inv_re, idx, idy, idx2, idy2, idzk, idzd, ihck, ihcu, fc0, fc1, fc2;
+    bool hasdn, hasup, wall_face;
+};
+
+// H^n = -div(uu)^n at the u, v and w points of cell (i, j, k) (products of
+// two-point averages at the cell centres and edges, differenced) and RHS =
+// dt [gamma H^n + rho H^{n-1} + Re^-1 L u^n - G p^n + f] (Eq. 3).  On the
+// bottom wall face (wall_face) H_w and RHS_w are 0.
+template <typename T>
+FSEI_D void rhs_point(const Stencil<T> &s, const RhsCoef<T> &c, T hu1, T hv1, T hw1, T fx, T fy,
+                      T fz, T &Hu, T &Hv, T &Hw, T &ru, T &rv, T &rw) {
+    const T h = T(0.5), z0 = T(0);
+    // cross fluxes at the cell edges
+    const T e_xy = (h * (s.v0 + s.vim)) * (h * (s.u0 + s.ujm));              // (x_i, y_j)
+    const T e_xy_jp = (h * (s.vjp + s.v_im_jp)) * (h * (s.ujp + s.u0));      // (x_i, y_j+1)
+    const T e_xy_ip = (h * (s.vip + s.v0)) * (h * (s.uip + s.u_ip_jm));      // (x_i+1, y_j)
+    const T e_xz = c.hasdn ? (h * (s.w0 + s.wim)) * (h * (s.u0 + s.ukm)) : z0;
+    const T e_xz_kp = c.hasup ? (h * (s.wku + s.w_im_ku)) * (h * (s.ukp + s.u0)) : z0;
+    const T e_xz_ip = c.hasdn ? (h * (s.wip + s.w0)) * (h * (s.uip + s.u_ip_kd)) : z0;
+    const T e_yz = c.hasdn ? (h * (s.w0 + s.wjm)) * (h * (s.v0 + s.vkm)) : z0;
+    const T e_yz_kp = c.hasup ? (h * (s.wku + s.w_jm_ku)) * (h * (s.vkp + s.v0)) : z0;
+    const T e_yz_jp = c.hasdn ? (h * (s.wjp + s.w0)) * (h * (s.vjp + s.v_jp_kd)) : z0;
+
+    const T ucp = h * (s.u0 + s.uip), ucm = h * (s.uim + s.u0);
+    Hu = -((ucp * ucp - ucm * ucm) * c.idx + (e_xy_jp - e_xy) * c.idy +
+           (e_xz_kp - e_xz) * c.idzk);
+    const T vcp = h * (s.v0 + s.vjp), vcm = h * (s.vjm + s.v0);
+    Hv = -((e_xy_ip - e_xy) * c.idx + (vcp * vcp - vcm * vcm) * c.idy +
+           (e_yz_kp - e_yz) * c.idzk);
+    Hw = z0;
+    if (!c.wall_face) {
+        const T wcp = h * (s.w0 + s.wku), wcm = h * (s.wkd + s.w0);
+        Hw = -((e_xz_ip - e_xz) * c.idx + (e_yz_jp - e_yz) * c.idy +
+               (wcp * wcp - wcm * wcm) * c.ihck);
+    }
+    const T Lu = (s.uip - T(2) * s.u0 + s.uim) * c.idx2 + (s.ujp - T(2) * s.u0 + s.ujm) * c.idy2 +
+                 ((s.ukp - s.u0) * c.ihcu - (s.u0 - s.ukm) * c.ihck) * c.idzk;
+    const T Lv = (s.vip - T(2) * s.v0 + s.vim) * c.idx2 + (s.vjp - T(2) * s.v0 + s.vjm) * c.idy2 +
+                 ((s.vkp - s.v0) * c.ihcu - (s.v0 - s.vkm) * c.ihck) * c.idzk;
+    ru = c.dt * (c.gam * Hu + c.rho * hu1 + c.inv_re * Lu - (s.p0 - s.pim) * c.idx + fx + c.fc0);
+    rv = c.dt * (c.gam * Hv + c.rho * hv1 + c.inv_re * Lv - (s.p0 - s.pjm) * c.idy + fy + c.fc1);
+    rw = z0;
+    if (!c.wall_face) {
+        const T Lw = (s.wip - T(2) * s.w0 + s.wim) * c.idx2 +
+                     (s.wjp - T(2) * s.w0 + s.wjm) * c.idy2 +
+                     ((s.wku - s.w0) * c.idzk - (s.w0 - s.wkd) * c.idzd) * c.ihck;
+        rw = c.dt * (c.gam * Hw + c.rho * hw1 + c.inv_re * Lw - (s.p0 - s.pkd) * c.ihck + fz +
+                     c.fc2);
+    }
+}
+
+template <typename T>
+FSEI_D RhsCoef<T> rhs_coef(const GridDev &g, const StepScalars *sc, int k, T fc0, T fc1, T fc2,
+                           T inv_re) {
+    RhsCoef<T> c;
+    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
+    const int nz = g.nz;
+    const bool walls = g.walls != 0;
+    const int kd = k == 0 ? nz - 1 : k - 1;
+    c.dt = fpick<T>(sc->dt, sc->fdt);
+    c.gam = fpick<T>(sc->gamma, sc->fgamma);
+    c.rho = fpick<T>(sc->rho, sc->frho);
+    c.inv_re = inv_re;
+    c.idx = fpick<T>(g.idx, g.fidx);
+    c.idy = fpick<T>(g.idy, g.fidy);
+    c.idx2 = fpick<T>(g.idx2, g.fidx2);
+    c.idy2 = fpick<T>(g.idy2, g.fidy2);
+    c.idzk = idz[k];
+    c.idzd = idz[kd];
+    c.ihck = ihc[k];
+    c.ihcu = ihc[k + 1];
+    c.fc0 = fc0;
+    c.fc1 = fc1;
+    c.fc2 = fc2;
+    c.hasdn = !walls || k > 0;
+    c.hasup = !walls || k < nz - 1;
+    c.wall_face = walls && k == 0;
+    return c;
+}
+
+// (I - beta L_x)^-1 along the nl = 3 ry right-hand-side lines of a block,
+// held in sd[i * es + line] (line = component * ry + row), then stored as
+// q0, q1, q2 rows j0 .. j0+ry-1 of plane k.  Thread t < nl P owns chunk
+// t / nl of line t % nl in registers (uni_solve).  Every thread calls it.
+template <typename T, int L>
+FSEI_D void x_solve_store(T *sd, int es, int ry, int P, int nx, int ny, int k, int j0,
+                          const StepScalars *sc, T *car, T *q0, T *q1, T *q2) {
+    const int nl = 3 * ry;
+    {
+        const int t = threadIdx.x;
+        const bool active = t < nl * P;
+        const int p = active ? t / nl : 0, l = active ? t - p * nl : 0;
+        const int s0 = chunk_start(p, nx, P);
+        const int len = active ? chunk_start(p + 1, nx, P) - s0 : 0;
+        T d[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < len) d[i] = sd[(s0 + i) * es + l];
+        uni_solve<T, L>(d, len, active, l, p, nl, nx, P, fpick<T>(sc->ax, sc->fax),
+                        fpick<T>(sc->cix, sc->fcix), car);
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < len) sd[(s0 + i) * es + l] = d[i];
+    }
+    __syncthreads();
+    for (int r = 0; r < ry; ++r) {
+        const int o = (k * ny + j0 + r) * nx;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            q0[o + i] = sd[i * es + r];
+            q1[o + i] = sd[i * es + ry + r];
+            q2[o + i] = sd[i * es + 2 * ry + r];
+        }
+    }
+}
+
 // L: register chunk length of the x solve (>= nx / P).  Single precision
 // keeps four blocks per SM for chunks of up to 16; longer chunks (nx > 256)
-// take more registers.
+// take more registers.  General kernel (any nx): stencil values read from
+// global memory; the tiled kernel below is used where it applies.
 template <typename T, int L>
 __global__ void __launch_bounds__(256, L <= 16 ? (sizeof(T) == 4 ? 4 : 2) : (L <= 32 ? 2 : 1))
 k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
@@ -254,15 +394,10 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
     T *car = sd + (size_t)nx * es;
     const int nby = ny / ry;
     const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * ry;
-    const T dt = T(sc->dt), gam = T(sc->gamma), rho = T(sc->rho);
-    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
-    const T idx = T(g.idx), idy = T(g.idy), idx2 = T(g.idx2), idy2 = T(g.idy2);
-    const bool walls = g.walls != 0;
-    const bool hasdn = !walls || k > 0, hasup = !walls || k < nz - 1;
-    const bool wall_face = walls && k == 0;
+    const RhsCoef<T> cf = rhs_coef<T>(g, sc, k, fc0, fc1, fc2, inv_re);
+    const bool hasdn = cf.hasdn, hasup = cf.hasup;
     const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
-    const T idzk = idz[k], idzd = idz[kd], ihck = ihc[k], ihcu = ihc[k + 1];
-    const T h = T(0.5), z0 = T(0);
+    const T z0 = T(0);
     const T *__restrict__ u = F.u;
     const T *__restrict__ v = F.v;
     const T *__restrict__ w = F.w;
@@ -279,67 +414,32 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
       for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
         const int c0 = oc + i;
-        // u neighbourhood
-        const T u0 = u[c0], uip = u[oc + ip], uim = u[oc + im];
-        const T ujp = u[ojp + i], ujm = u[ojm + i];
-        const T ukp = hasup ? u[oku + i] : z0;
-        const T ukm = hasdn ? u[okd + i] : z0;
-        const T u_ip_jm = u[ojm + ip];
-        const T u_ip_kd = hasdn ? u[okd + ip] : z0;
-        // v neighbourhood
-        const T v0 = v[c0], vip = v[oc + ip], vim = v[oc + im];
-        const T vjp = v[ojp + i], vjm = v[ojm + i];
-        const T vkp = hasup ? v[oku + i] : z0;
-        const T vkm = hasdn ? v[okd + i] : z0;
-        const T v_im_jp = v[ojp + im];
-        const T v_jp_kd = hasdn ? v[ojpkd + i] : z0;
-        // w neighbourhood (w at the bottom wall face is stored as 0)
-        const T w0 = w[c0], wip = w[oc + ip], wim = w[oc + im];
-        const T wjp = w[ojp + i], wjm = w[ojm + i];
-        const T wku = hasup ? w[oku + i] : z0;
-        const T wkd = hasdn ? w[okd + i] : z0;
-        const T w_im_ku = hasup ? w[oku + im] : z0;
-        const T w_jm_ku = hasup ? w[ojmku + i] : z0;
-        // p
-        const T p0 = p[c0], pim = p[oc + im], pjm = p[ojm + i];
-        const T pkd = hasdn ? p[okd + i] : z0;
-
-        // cross fluxes at the cell edges
-        const T e_xy = (h * (v0 + vim)) * (h * (u0 + ujm));          // (x_i, y_j)
-        const T e_xy_jp = (h * (vjp + v_im_jp)) * (h * (ujp + u0));  // (x_i, y_j+1)
-        const T e_xy_ip = (h * (vip + v0)) * (h * (uip + u_ip_jm));  // (x_i+1, y_j)
-        const T e_xz = hasdn ? (h * (w0 + wim)) * (h * (u0 + ukm)) : z0;          // (x_i, z_k)
-        const T e_xz_kp = hasup ? (h * (wku + w_im_ku)) * (h * (ukp + u0)) : z0;  // (x_i, z_k+1)
-        const T e_xz_ip = hasdn ? (h * (wip + w0)) * (h * (uip + u_ip_kd)) : z0;  // (x_i+1, z_k)
-        const T e_yz = hasdn ? (h * (w0 + wjm)) * (h * (v0 + vkm)) : z0;
-        const T e_yz_kp = hasup ? (h * (wku + w_jm_ku)) * (h * (vkp + v0)) : z0;
-        const T e_yz_jp = hasdn ? (h * (wjp + w0)) * (h * (vjp + v_jp_kd)) : z0;
-
-        const T ucp = h * (u0 + uip), ucm = h * (uim + u0);
-        const T Hu = -((ucp * ucp - ucm * ucm) * idx + (e_xy_jp - e_xy) * idy +
-                       (e_xz_kp - e_xz) * idzk);
-        const T vcp = h * (v0 + vjp), vcm = h * (vjm + v0);
-        const T Hv = -((e_xy_ip - e_xy) * idx + (vcp * vcp - vcm * vcm) * idy +
-                       (e_yz_kp - e_yz) * idzk);
-        T Hw = z0;
-        if (!wall_face) {
-            const T wcp = h * (w0 + wku), wcm = h * (wkd + w0);
-            Hw = -((e_xz_ip - e_xz) * idx + (e_yz_jp - e_yz) * idy + (wcp * wcp - wcm * wcm) * ihck);
-        }
-        const T Lu = (uip - T(2) * u0 + uim) * idx2 + (ujp - T(2) * u0 + ujm) * idy2 +
-                     ((ukp - u0) * ihcu - (u0 - ukm) * ihck) * idzk;
-        const T Lv = (vip - T(2) * v0 + vim) * idx2 + (vjp - T(2) * v0 + vjm) * idy2 +
-                     ((vkp - v0) * ihcu - (v0 - vkm) * ihck) * idzk;
+        Stencil<T> s;
+        s.u0 = u[c0]; s.uip = u[oc + ip]; s.uim = u[oc + im];
+        s.ujp = u[ojp + i]; s.ujm = u[ojm + i];
+        s.ukp = hasup ? u[oku + i] : z0;
+        s.ukm = hasdn ? u[okd + i] : z0;
+        s.u_ip_jm = u[ojm + ip];
+        s.u_ip_kd = hasdn ? u[okd + ip] : z0;
+        s.v0 = v[c0]; s.vip = v[oc + ip]; s.vim = v[oc + im];
+        s.vjp = v[ojp + i]; s.vjm = v[ojm + i];
+        s.vkp = hasup ? v[oku + i] : z0;
+        s.vkm = hasdn ? v[okd + i] : z0;
+        s.v_im_jp = v[ojp + im];
+        s.v_jp_kd = hasdn ? v[ojpkd + i] : z0;
+        // w at the bottom wall face is stored as 0
+        s.w0 = w[c0]; s.wip = w[oc + ip]; s.wim = w[oc + im];
+        s.wjp = w[ojp + i]; s.wjm = w[ojm + i];
+        s.wku = hasup ? w[oku + i] : z0;
+        s.wkd = hasdn ? w[okd + i] : z0;
+        s.w_im_ku = hasup ? w[oku + im] : z0;
+        s.w_jm_ku = hasup ? w[ojmku + i] : z0;
+        s.p0 = p[c0]; s.pim = p[oc + im]; s.pjm = p[ojm + i];
+        s.pkd = hasdn ? p[okd + i] : z0;
         const T fx = F.fx ? F.fx[c0] : z0, fy = F.fy ? F.fy[c0] : z0;
-        const T ru = dt * (gam * Hu + rho * F.hu[c0] + inv_re * Lu - (p0 - pim) * idx + fx + fc0);
-        const T rv = dt * (gam * Hv + rho * F.hv[c0] + inv_re * Lv - (p0 - pjm) * idy + fy + fc1);
-        T rw = z0;
-        if (!wall_face) {
-            const T Lw = (wip - T(2) * w0 + wim) * idx2 + (wjp - T(2) * w0 + wjm) * idy2 +
-                         ((wku - w0) * idzk - (w0 - wkd) * idzd) * ihck;
-            const T fz = F.fz ? F.fz[c0] : z0;
-            rw = dt * (gam * Hw + rho * F.hw[c0] + inv_re * Lw - (p0 - pkd) * ihck + fz + fc2);
-        }
+        const T fz = (F.fz && !cf.wall_face) ? F.fz[c0] : z0;
+        T Hu, Hv, Hw, ru, rv, rw;
+        rhs_point(s, cf, F.hu[c0], F.hv[c0], F.hw[c0], fx, fy, fz, Hu, Hv, Hw, ru, rv, rw);
         F.hu[c0] = Hu;
         F.hv[c0] = Hv;
         F.hw[c0] = Hw;
@@ -349,32 +449,176 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
       }
     }
     __syncthreads();
-    // (I - beta L_x)^-1 along the nl lines: thread t < nl P owns chunk
-    // t / nl of line t % nl in registers
+    x_solve_store<T, L>(sd, es, ry, P, nx, ny, k, j0, sc, car, q0, q1, q2);
+}
+
+// Shared-memory rows of the tiled right-hand side for a block of RY rows
+// j0 .. j0+RY-1 of plane k, by group (first row index; rows in y order):
+//   plane k:   u, v, w rows j0-1 .. j0+RY; p rows j0-1 .. j0+RY-1;
+//              H^{n-1} (hu, hv, hw) rows j0 .. j0+RY-1
+//   plane k+1: u, v rows j0 .. j0+RY-1; w rows j0-1 .. j0+RY-1
+//   plane k-1: u, w, p rows j0 .. j0+RY-1; v rows j0 .. j0+RY
+// j wraps periodically; k +- 1 wraps when z is periodic and is absent (not
+// copied, read as 0) beyond a wall.  14 RY + 9 rows in all.
+struct TileRows {
+    int u, v, w, p, hu, hv, hw, uu, vu, wu, ud, wd, pd, vd, total;
+    FSEI_HD explicit TileRows(int RY) {
+        int r = 0;
+        u = r; r += RY + 2;
+        v = r; r += RY + 2;
+        w = r; r += RY + 2;
+        p = r; r += RY + 1;
+        hu = r; r += RY;
+        hv = r; r += RY;
+        hw = r; r += RY;
+        uu = r; r += RY;
+        vu = r; r += RY;
+        wu = r; r += RY + 1;
+        ud = r; r += RY;
+        wd = r; r += RY;
+        pd = r; r += RY;
+        vd = r; r += RY + 1;
+        total = r;
+    }
+};
+constexpr int kTileRowsMax = 14 * 4 + 9;
+
+// Element offset of a staged row's first value (16 bytes: the left x halo
+// sits just before it) and the row stride: nx values plus one 16-byte slot
+// on each side.
+template <typename T> FSEI_HD int tile_xo() { return 16 / (int)sizeof(T); }
+template <typename T> FSEI_HD int tile_rsz(int nx) { return nx + 2 * tile_xo<T>(); }
+
+// Global row (field, plane kk, row jj) feeding staged row r, or NULL for a
+// plane beyond a wall.
+template <typename T>
+FSEI_D const T *tile_source(const TileRows &tr, int RY, int r, const Fields<T> &F, int nx, int ny,
+                            int k, int ku, int kd, bool hasup, bool hasdn, int j0) {
+    const T *f;
+    int kk, jrel;
+    if (r < tr.v) { f = F.u; kk = k; jrel = r - tr.u - 1; }
+    else if (r < tr.w) { f = F.v; kk = k; jrel = r - tr.v - 1; }
+    else if (r < tr.p) { f = F.w; kk = k; jrel = r - tr.w - 1; }
+    else if (r < tr.hu) { f = F.p; kk = k; jrel = r - tr.p - 1; }
+    else if (r < tr.hv) { f = F.hu; kk = k; jrel = r - tr.hu; }
+    else if (r < tr.hw) { f = F.hv; kk = k; jrel = r - tr.hv; }
+    else if (r < tr.uu) { f = F.hw; kk = k; jrel = r - tr.hw; }
+    else if (r < tr.vu) { f = hasup ? F.u : nullptr; kk = ku; jrel = r - tr.uu; }
+    else if (r < tr.wu) { f = hasup ? F.v : nullptr; kk = ku; jrel = r - tr.vu; }
+    else if (r < tr.ud) { f = hasup ? F.w : nullptr; kk = ku; jrel = r - tr.wu - 1; }
+    else if (r < tr.wd) { f = hasdn ? F.u : nullptr; kk = kd; jrel = r - tr.ud; }
+    else if (r < tr.pd) { f = hasdn ? F.w : nullptr; kk = kd; jrel = r - tr.wd; }
+    else if (r < tr.vd) { f = hasdn ? F.p : nullptr; kk = kd; jrel = r - tr.pd; }
+    else { f = hasdn ? F.v : nullptr; kk = kd; jrel = r - tr.vd; }
+    if (!f) return nullptr;
+    int j = j0 + jrel;
+    if (j < 0) j += ny;
+    if (j >= ny) j -= ny;
+    return f + (kk * ny + j) * nx;
+}
+
+// Tiled right-hand side + x sweep: every stencil row of the block is
+// staged in shared memory with 16-byte asynchronous copies (all in flight
+// together), each staged row padded with its periodic x neighbours, so the
+// point formula reads shared memory only.  Needs nx * sizeof(T) % 16 == 0.
+// Same arithmetic, in the same order, as k_rhs_x.
+template <typename T, int L, int RY>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (L <= 16 ? 4 : (L <= 32 ? 3 : 2))
+                                                      : (L <= 16 ? 2 : 1))
+k_rhs_x_tile(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
+             T *__restrict__ q2, const StepScalars *sc, int P, T fc0, T fc1, T fc2, T inv_re) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ const T *rowsrc[kTileRowsMax];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const TileRows tr(RY);
+    const int xo = tile_xo<T>(), rsz = tile_rsz<T>(nx);
+    T *S = reinterpret_cast<T *>(smraw);
+    const int nl = 3 * RY, es = nl | 1;
+    T *sd = S + (size_t)tr.total * rsz;
+    T *car = sd + (size_t)nx * es;
+    const int nby = ny / RY;
+    const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * RY;
+    const RhsCoef<T> cf = rhs_coef<T>(g, sc, k, fc0, fc1, fc2, inv_re);
+    const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
+    const int t = threadIdx.x;
+    if (t < tr.total)
+        rowsrc[t] = tile_source<T>(tr, RY, t, F, nx, ny, k, ku, kd, cf.hasup, cf.hasdn, j0);
+    __syncthreads();
     {
-        const int t = threadIdx.x;
-        const bool active = t < nl * P;
-        const int p = active ? t / nl : 0, l = active ? t - p * nl : 0;
-        const int s0 = chunk_start(p, nx, P);
-        const int len = active ? chunk_start(p + 1, nx, P) - s0 : 0;
-        T d[L];
-#pragma unroll
-        for (int i = 0; i < L; ++i)
-            if (i < len) d[i] = sd[(s0 + i) * es + l];
-        uni_solve<T, L>(d, len, active, l, p, nl, nx, P, T(sc->ax), T(sc->cix), car);
-#pragma unroll
-        for (int i = 0; i < L; ++i)
-            if (i < len) sd[(s0 + i) * es + l] = d[i];
+        constexpr int VW = 16 / (int)sizeof(T);
+        const int cpr = nx / VW;
+        const int total = tr.total * cpr;
+        for (int e = t; e < total; e += blockDim.x) {
+            const int r = ddiv(e, cpr), c = e - r * cpr;
+            const T *src = rowsrc[r];
+            if (src) cp_async16(S + r * rsz + xo + c * VW, src + c * VW);
+        }
+        // periodic x neighbours of every row (plain loads, issued after the
+        // asynchronous copies)
+        for (int e = t; e < 2 * tr.total; e += blockDim.x) {
+            const int r = e >> 1;
+            const T *src = rowsrc[r];
+            if (src) {
+                if (e & 1) S[r * rsz + xo + nx] = src[0];
+                else S[r * rsz + xo - 1] = src[nx - 1];
+            }
+        }
+        cp_async_wait_all();
     }
     __syncthreads();
-    for (int r = 0; r < ry; ++r) {
-        const int o = (k * ny + j0 + r) * nx;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            q0[o + i] = sd[i * es + r];
-            q1[o + i] = sd[i * es + ry + r];
-            q2[o + i] = sd[i * es + 2 * ry + r];
+    const T z0 = T(0);
+    const bool hasdn = cf.hasdn, hasup = cf.hasup;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        const T *Uk = S + (tr.u + 1 + r) * rsz + xo, *Ujm = Uk - rsz, *Ujp = Uk + rsz;
+        const T *Vk = S + (tr.v + 1 + r) * rsz + xo, *Vjm = Vk - rsz, *Vjp = Vk + rsz;
+        const T *Wk = S + (tr.w + 1 + r) * rsz + xo, *Wjm = Wk - rsz, *Wjp = Wk + rsz;
+        const T *Pk = S + (tr.p + 1 + r) * rsz + xo, *Pjm = Pk - rsz;
+        const T *Hu1 = S + (tr.hu + r) * rsz + xo, *Hv1 = S + (tr.hv + r) * rsz + xo,
+                *Hw1 = S + (tr.hw + r) * rsz + xo;
+        const T *Uu = S + (tr.uu + r) * rsz + xo, *Vu = S + (tr.vu + r) * rsz + xo;
+        const T *Wu = S + (tr.wu + 1 + r) * rsz + xo, *Wujm = Wu - rsz;
+        const T *Ud = S + (tr.ud + r) * rsz + xo, *Wd = S + (tr.wd + r) * rsz + xo,
+                *Pd = S + (tr.pd + r) * rsz + xo, *Vd = S + (tr.vd + r) * rsz + xo,
+                *Vdjp = Vd + rsz;
+        const int oc = (k * ny + j0 + r) * nx;
+        for (int i = t; i < nx; i += blockDim.x) {
+            const int c0 = oc + i;
+            Stencil<T> s;
+            s.u0 = Uk[i]; s.uip = Uk[i + 1]; s.uim = Uk[i - 1];
+            s.ujp = Ujp[i]; s.ujm = Ujm[i];
+            s.ukp = hasup ? Uu[i] : z0;
+            s.ukm = hasdn ? Ud[i] : z0;
+            s.u_ip_jm = Ujm[i + 1];
+            s.u_ip_kd = hasdn ? Ud[i + 1] : z0;
+            s.v0 = Vk[i]; s.vip = Vk[i + 1]; s.vim = Vk[i - 1];
+            s.vjp = Vjp[i]; s.vjm = Vjm[i];
+            s.vkp = hasup ? Vu[i] : z0;
+            s.vkm = hasdn ? Vd[i] : z0;
+            s.v_im_jp = Vjp[i - 1];
+            s.v_jp_kd = hasdn ? Vdjp[i] : z0;
+            s.w0 = Wk[i]; s.wip = Wk[i + 1]; s.wim = Wk[i - 1];
+            s.wjp = Wjp[i]; s.wjm = Wjm[i];
+            s.wku = hasup ? Wu[i] : z0;
+            s.wkd = hasdn ? Wd[i] : z0;
+            s.w_im_ku = hasup ? Wu[i - 1] : z0;
+            s.w_jm_ku = hasup ? Wujm[i] : z0;
+            s.p0 = Pk[i]; s.pim = Pk[i - 1]; s.pjm = Pjm[i];
+            s.pkd = hasdn ? Pd[i] : z0;
+            const T fx = F.fx ? F.fx[c0] : z0, fy = F.fy ? F.fy[c0] : z0;
+            const T fz = (F.fz && !cf.wall_face) ? F.fz[c0] : z0;
+            T Hu, Hv, Hw, ru, rv, rw;
+            rhs_point(s, cf, Hu1[i], Hv1[i], Hw1[i], fx, fy, fz, Hu, Hv, Hw, ru, rv, rw);
+            F.hu[c0] = Hu;
+            F.hv[c0] = Hv;
+            F.hw[c0] = Hw;
+            sd[i * es + r] = ru;
+            sd[i * es + RY + r] = rv;
+            sd[i * es + 2 * RY + r] = rw;
         }
     }
+    __syncthreads();
+    x_solve_store<T, L>(sd, es, RY, P, nx, ny, k, j0, sc, car, q0, q1, q2);
 }
 
 }  // namespace
@@ -400,9 +644,13 @@ template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v
     k_speed<T><<<g.nz * (g.ny / rows), threads, 0, st>>>(g, u, v, w, sc, rows);
 }
 
-template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepScalars *sc,
-                                             const StepArgs &a, int euler, cudaStream_t st) {
+void launch_step_scalars(const GridDev &g, StepScalars *sc, const StepArgs &a, int euler,
+                         cudaStream_t st) {
     k_scalars<<<1, 32, 0, st>>>(sc, a, euler, g.idx2, g.idy2);
+}
+
+template <typename T> void launch_step_plans(const GridDev &g, Work<T> &W, const StepScalars *sc,
+                                             cudaStream_t st) {
     int maxn = 0, maxp = 0;
     for (int q = 2; q < 4; ++q) {
         if (W.plan[q].n > maxn) maxn = W.plan[q].n;
@@ -411,6 +659,12 @@ template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepS
     const size_t sm = sizeof(double) * (2 * (size_t)maxn + 12 * (size_t)maxp);
     int thr = ((2 * maxp + 31) / 32) * 32;
     k_plans<T><<<2, thr, sm, st>>>(g, W, sc);
+}
+
+template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepScalars *sc,
+                                             const StepArgs &a, int euler, cudaStream_t st) {
+    launch_step_scalars(g, sc, a, euler, st);
+    launch_step_plans<T>(g, W, sc, st);
 }
 
 template <typename T, int L>
@@ -428,8 +682,54 @@ void rhs_x_L(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars
         T(1.0 / a.re));
 }
 
+// Geometry of the tiled right-hand side: RY rows per block (2, else 1),
+// P chunks per x line (the largest power of two <= 32 with 3 RY P <= 256
+// threads and chunks of at least two unknowns), its shared memory; false
+// where it does not apply (rows not 16-byte multiples, or too large for
+// shared memory).
+template <typename T> bool rhs_tile_geometry(const GridDev &g, int &RY, int &P, size_t &smem) {
+    if ((g.nx * (int)sizeof(T)) % 16 != 0) return false;
+    const size_t lim = (size_t)smem_optin() - 1024;
+    for (RY = 2; RY >= 1; --RY) {
+        if (g.ny % RY) continue;
+        const int nl = 3 * RY, es = nl | 1;
+        P = 1;
+        while (P < 32 && nl * (2 * P) <= 256 && g.nx / (2 * P) >= 2) P *= 2;
+        const TileRows tr(RY);
+        smem = sizeof(T) * ((size_t)tr.total * tile_rsz<T>(g.nx) + (size_t)g.nx * es +
+                            2 * (size_t)nl * P);
+        if (smem <= lim) return true;
+    }
+    return false;
+}
+
+template <typename T, int L, int RY>
+void rhs_tile_L(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
+                const StepArgs &a, int P, size_t smem, cudaStream_t st) {
+    k_rhs_x_tile<T, L, RY><<<g.nz * (g.ny / RY), 256, smem, st>>>(
+        g, F, W.q0, W.q1, W.q2, sc, P, T(a.fconst[0]), T(a.fconst[1]), T(a.fconst[2]),
+        T(1.0 / a.re));
+}
+
+template <typename T, int RY>
+void rhs_tile_ry(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
+                 const StepArgs &a, int P, size_t smem, cudaStream_t st) {
+    const int chunk = (g.nx + P - 1) / P;
+    if (chunk <= 8) rhs_tile_L<T, 8, RY>(g, F, W, sc, a, P, smem, st);
+    else if (chunk <= 16) rhs_tile_L<T, 16, RY>(g, F, W, sc, a, P, smem, st);
+    else if (chunk <= 32) rhs_tile_L<T, 32, RY>(g, F, W, sc, a, P, smem, st);
+    else rhs_tile_L<T, 64, RY>(g, F, W, sc, a, P, smem, st);
+}
+
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
+    int RY = 0, P = 0;
+    size_t smem = 0;
+    if (rhs_tile_geometry<T>(g, RY, P, smem)) {
+        if (RY == 2) rhs_tile_ry<T, 2>(g, F, W, sc, a, P, smem, st);
+        else rhs_tile_ry<T, 1>(g, F, W, sc, a, P, smem, st);
+        return;
+    }
     if (W.chunk_x <= 8) rhs_x_L<T, 8>(g, F, W, sc, a, st);
     else if (W.chunk_x <= 16) rhs_x_L<T, 16>(g, F, W, sc, a, st);
     else if (W.chunk_x <= 32) rhs_x_L<T, 32>(g, F, W, sc, a, st);
@@ -449,6 +749,14 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     raise_smem_limit(k_rhs_x<T, 16>);
     raise_smem_limit(k_rhs_x<T, 32>);
     raise_smem_limit(k_rhs_x<T, 64>);
+    raise_smem_limit(k_rhs_x_tile<T, 8, 1>);
+    raise_smem_limit(k_rhs_x_tile<T, 16, 1>);
+    raise_smem_limit(k_rhs_x_tile<T, 32, 1>);
+    raise_smem_limit(k_rhs_x_tile<T, 64, 1>);
+    raise_smem_limit(k_rhs_x_tile<T, 8, 2>);
+    raise_smem_limit(k_rhs_x_tile<T, 16, 2>);
+    raise_smem_limit(k_rhs_x_tile<T, 32, 2>);
+    raise_smem_limit(k_rhs_x_tile<T, 64, 2>);
 }
 
 #define FSEI_INST(T)                                                                           \
@@ -457,6 +765,8 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
                                   StepScalars *, cudaStream_t);                               \
     template void launch_step_begin<T>(const GridDev &, Work<T> &, StepScalars *,              \
                                        const StepArgs &, int, cudaStream_t);                  \
+    template void launch_step_plans<T>(const GridDev &, Work<T> &, const StepScalars *,        \
+                                       cudaStream_t);                                         \
     template void launch_rhs_x<T>(const GridDev &, const Fields<T> &, Work<T> &,               \
                                   const StepScalars *, const StepArgs &, cudaStream_t);       \
     template void set_smem_limits_sweep<T>(const GridDev &, const Work<T> &);

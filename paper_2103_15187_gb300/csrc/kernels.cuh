@@ -26,6 +26,14 @@ template <typename T> struct Work {
     const double *lamx_d, *lamy_d;
     const int *nzm;          // near-zero modes to solve in double: kx + sk*ky
     int n_nzm;
+    // Factors of the exactly solved modes' z systems (grid constants, set at
+    // grid creation; NULL selects the on-the-fly k_poisson_exact): per mode
+    // m and rows i < nz, xa[m nz + i] = -a_i / den_i, xm = 1 / den_i,
+    // xc = c_i / den_i of Thomas' algorithm (cyclic lines: of the
+    // Sherman-Morrison modified matrix, with xz its solution for the
+    // correction vector and xs[2 m], xs[2 m + 1] = v_last, 1 / (1 + v.z)).
+    const double *xa, *xm, *xc, *xz, *xs;
+    double zlen;             // z extent (sum of dz)
     const unsigned char *exact;   // [ny][sk]: 1 for the modes in nzm
     T *adj0, *adj1, *adj2;   // adjoint workspace (allocated on first use)
     int ry;                  // rows per block of the x-line solves
@@ -47,6 +55,21 @@ template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v
                                         StepScalars *sc, cudaStream_t st);
 template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepScalars *sc,
                                              const StepArgs &a, int euler, cudaStream_t st);
+// the two halves of launch_step_begin: this step's scalars (dt, beta, AB2
+// weights, reset reductions), then the z-sweep plans that depend on beta
+// (needed from the z sweep on, so they may run beside the RHS and y sweep)
+void launch_step_scalars(const GridDev &g, StepScalars *sc, const StepArgs &a, int euler,
+                         cudaStream_t st);
+template <typename T> void launch_step_plans(const GridDev &g, Work<T> &W, const StepScalars *sc,
+                                             cudaStream_t st);
+
+// A second stream of a grid and two events for a fork-join around work that
+// may run beside the main chain (its launches stay stream-ordered, also
+// inside a graph capture).
+struct Overlap {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st);
 template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, const StepScalars *sc,

@@ -199,6 +199,7 @@ fsei_status solve_noalloc(const fsei_grid_desc *d, const void *rhs, void *phi, c
     g.dx = dx; g.dy = dy;
     g.idx = 1.0 / dx; g.idy = 1.0 / dy;
     g.idx2 = g.idx * g.idx; g.idy2 = g.idy * g.idy;
+    grid_float_copies(g);
     g.dz = (const double *)(dev + L.dz);
     g.idz = (const double *)(dev + L.idz);
     g.ihc = (const double *)(dev + L.ihc);
