@@ -23,6 +23,12 @@ namespace fsei {
 
 namespace {
 
+// 16 bytes of consecutive values (4 floats or 2 doubles)
+template <typename T> struct alignas(16) Vec16 {
+    static constexpr int W = 16 / (int)sizeof(T);
+    T v[W];
+};
+
 // one block per group of rows (no integer division per element); per-cell
 // speed in the field precision, the grid-wide maximum in double
 template <typename T>
@@ -621,6 +627,212 @@ k_rhs_x_tile(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     x_solve_store<T, L>(sd, es, RY, P, nx, ny, k, j0, sc, car, q0, q1, q2);
 }
 
+// Row-resident right-hand side + x sweep: the LPR lanes of a warp segment
+// (or of LPR / 32 warps) own one x row (j, k); lane r holds cells CPL r ..
+// CPL r + CPL - 1 and reads every stencil row it needs as 16-byte vectors
+// straight from global memory (neighbour rows are served by the caches).
+// The x neighbours beyond its cells come from the neighbouring lanes (the
+// row is periodic, so they rotate around the line); edge fluxes shared by
+// two cells of a lane are formed once (the same products, so the same
+// values as k_rhs_x).  The x solve runs on the registers (line_solve_uni),
+// with no shared-memory staging; only lines wider than a warp exchange
+// their carries through shared memory.  Needs nx = LPR CPL, CPL a multiple
+// of the 16-byte vector, ny a multiple of the rows per block.
+template <typename T, int CPL>
+FSEI_D void ldrow(T (&a)[CPL], const T *p) {
+    constexpr int VW = 16 / (int)sizeof(T);
+#pragma unroll
+    for (int c = 0; c < CPL / VW; ++c) {
+        const Vec16<T> v = *reinterpret_cast<const Vec16<T> *>(p + c * VW);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) a[c * VW + e] = v.v[e];
+    }
+}
+template <typename T, int CPL>
+FSEI_D void strow(T *p, const T (&a)[CPL]) {
+    constexpr int VW = 16 / (int)sizeof(T);
+#pragma unroll
+    for (int c = 0; c < CPL / VW; ++c) {
+        Vec16<T> v;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) v.v[e] = a[c * VW + e];
+        *reinterpret_cast<Vec16<T> *>(p + c * VW) = v;
+    }
+}
+// value of the periodic x neighbour left (LEFT = 1) of this lane's first
+// cell, or right of its last one: from the neighbouring lane of the line
+// (mine: this lane's last / first value), or, where the line crosses a warp
+// boundary, from the row in memory
+template <typename T, int LPR, int LEFT>
+FSEI_D T xnb(T mine, const T *row, int i0, int nx, int CPL) {
+    constexpr int W = LPR < 32 ? LPR : 32;
+    const int p = threadIdx.x & (W - 1);
+    T v = __shfl_sync(0xffffffffu, mine, LEFT ? ((p - 1) & (W - 1)) : ((p + 1) & (W - 1)), W);
+    if (LPR > 32) {
+        if (LEFT && p == 0) v = row[i0 == 0 ? nx - 1 : i0 - 1];
+        if (!LEFT && p == W - 1) v = row[i0 + CPL == nx ? 0 : i0 + CPL];
+    }
+    return v;
+}
+
+template <typename T, int CPL, int LPR>
+__global__ void __launch_bounds__(LPR > 128 ? LPR : 128)
+k_rhs_x_row(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
+            T *__restrict__ q2, const StepScalars *sc, int rpb, T fc0, T fc1, T fc2, T inv_re) {
+    __shared__ T xs[2 * 3 * (LPR > 128 ? LPR : 128) / 32];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int nby = ny / rpb;
+    const int k = blockIdx.x / nby;
+    const int j = (blockIdx.x % nby) * rpb + (int)threadIdx.x / LPR;
+    const int lr = (int)threadIdx.x & (LPR - 1);
+    const int i0 = lr * CPL;
+    const RhsCoef<T> cf = rhs_coef<T>(g, sc, k, fc0, fc1, fc2, inv_re);
+    const bool hasdn = cf.hasdn, hasup = cf.hasup;
+    const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
+    const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
+    const int oc = (k * ny + j) * nx, ojm = (k * ny + jm) * nx, ojp = (k * ny + jp) * nx,
+              oku = (ku * ny + j) * nx, okd = (kd * ny + j) * nx, ojmku = (ku * ny + jm) * nx,
+              ojpkd = (kd * ny + jp) * nx;
+    const T h = T(0.5), z0 = T(0);
+    // stencil rows (cells i0 .. i0+CPL-1); planes beyond a wall are 0
+    T U[CPL], Ujm[CPL], Ujp[CPL], Uu[CPL], Ud[CPL];
+    T V[CPL], Vjm[CPL], Vjp[CPL], Vu[CPL], Vd[CPL], Vdjp[CPL];
+    T W[CPL], Wjm[CPL], Wjp[CPL], Wu[CPL], Wujm[CPL], Wd[CPL];
+    T P[CPL], Pjm[CPL], Pd[CPL];
+    ldrow(U, F.u + oc + i0); ldrow(Ujm, F.u + ojm + i0); ldrow(Ujp, F.u + ojp + i0);
+    ldrow(V, F.v + oc + i0); ldrow(Vjm, F.v + ojm + i0); ldrow(Vjp, F.v + ojp + i0);
+    ldrow(W, F.w + oc + i0); ldrow(Wjm, F.w + ojm + i0); ldrow(Wjp, F.w + ojp + i0);
+    ldrow(P, F.p + oc + i0); ldrow(Pjm, F.p + ojm + i0);
+    if (hasup) {
+        ldrow(Uu, F.u + oku + i0); ldrow(Vu, F.v + oku + i0);
+        ldrow(Wu, F.w + oku + i0); ldrow(Wujm, F.w + ojmku + i0);
+    } else {
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) Uu[e] = Vu[e] = Wu[e] = Wujm[e] = z0;
+    }
+    if (hasdn) {
+        ldrow(Ud, F.u + okd + i0); ldrow(Vd, F.v + okd + i0); ldrow(Vdjp, F.v + ojpkd + i0);
+        ldrow(Wd, F.w + okd + i0); ldrow(Pd, F.p + okd + i0);
+    } else {
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) Ud[e] = Vd[e] = Vdjp[e] = Wd[e] = Pd[e] = z0;
+    }
+    // x neighbours outside the lane's cells
+    const T Ul = xnb<T, LPR, 1>(U[CPL - 1], F.u + oc, i0, nx, CPL);
+    const T Ur = xnb<T, LPR, 0>(U[0], F.u + oc, i0, nx, CPL);
+    const T Ujmr = xnb<T, LPR, 0>(Ujm[0], F.u + ojm, i0, nx, CPL);
+    const T Udr = hasdn ? xnb<T, LPR, 0>(Ud[0], F.u + okd, i0, nx, CPL) : z0;
+    const T Vl = xnb<T, LPR, 1>(V[CPL - 1], F.v + oc, i0, nx, CPL);
+    const T Vr = xnb<T, LPR, 0>(V[0], F.v + oc, i0, nx, CPL);
+    const T Vjpl = xnb<T, LPR, 1>(Vjp[CPL - 1], F.v + ojp, i0, nx, CPL);
+    const T Wl = xnb<T, LPR, 1>(W[CPL - 1], F.w + oc, i0, nx, CPL);
+    const T Wr = xnb<T, LPR, 0>(W[0], F.w + oc, i0, nx, CPL);
+    const T Wul = hasup ? xnb<T, LPR, 1>(Wu[CPL - 1], F.w + oku, i0, nx, CPL) : z0;
+    const T Pl = xnb<T, LPR, 1>(P[CPL - 1], F.p + oc, i0, nx, CPL);
+    // quantities at the CPL + 1 x faces / edges i0 .. i0+CPL of the lane
+    T ucc[CPL + 1], exy[CPL + 1], exz[CPL + 1];
+#pragma unroll
+    for (int e = 0; e <= CPL; ++e) {
+        const T um = e == 0 ? Ul : U[e - 1], u0 = e == CPL ? Ur : U[e];
+        const T vm = e == 0 ? Vl : V[e - 1], v0 = e == CPL ? Vr : V[e];
+        const T wm = e == 0 ? Wl : W[e - 1], w0 = e == CPL ? Wr : W[e];
+        const T ujm = e == CPL ? Ujmr : Ujm[e], ud = e == CPL ? Udr : Ud[e];
+        ucc[e] = h * (um + u0);
+        exy[e] = (h * (v0 + vm)) * (h * (u0 + ujm));
+        exz[e] = hasdn ? (h * (w0 + wm)) * (h * (u0 + ud)) : z0;
+    }
+    T R[3][CPL];
+    T Hn[3][CPL];
+    {
+        T H1[CPL];
+        ldrow(H1, F.hu + oc + i0);
+        T fx[CPL];
+        if (F.fx) ldrow(fx, F.fx + oc + i0);
+        else {
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) fx[e] = z0;
+        }
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+            const T uim = e == 0 ? Ul : U[e - 1], uip = e == CPL - 1 ? Ur : U[e + 1];
+            const T vim = e == 0 ? Vjpl : Vjp[e - 1];
+            const T wuim = e == 0 ? Wul : Wu[e - 1];
+            const T e_xy_jp = (h * (Vjp[e] + vim)) * (h * (Ujp[e] + U[e]));
+            const T e_xz_kp = hasup ? (h * (Wu[e] + wuim)) * (h * (Uu[e] + U[e])) : z0;
+            const T Hu = -((ucc[e + 1] * ucc[e + 1] - ucc[e] * ucc[e]) * cf.idx +
+                           (e_xy_jp - exy[e]) * cf.idy + (e_xz_kp - exz[e]) * cf.idzk);
+            const T Lu = (uip - T(2) * U[e] + uim) * cf.idx2 +
+                         (Ujp[e] - T(2) * U[e] + Ujm[e]) * cf.idy2 +
+                         ((Uu[e] - U[e]) * cf.ihcu - (U[e] - Ud[e]) * cf.ihck) * cf.idzk;
+            const T pim = e == 0 ? Pl : P[e - 1];
+            Hn[0][e] = Hu;
+            R[0][e] = cf.dt * (cf.gam * Hu + cf.rho * H1[e] + cf.inv_re * Lu -
+                               (P[e] - pim) * cf.idx + fx[e] + cf.fc0);
+        }
+    }
+    {
+        T H1[CPL];
+        ldrow(H1, F.hv + oc + i0);
+        T fy[CPL];
+        if (F.fy) ldrow(fy, F.fy + oc + i0);
+        else {
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) fy[e] = z0;
+        }
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+            const T vim = e == 0 ? Vl : V[e - 1], vip = e == CPL - 1 ? Vr : V[e + 1];
+            const T e_yz = hasdn ? (h * (W[e] + Wjm[e])) * (h * (V[e] + Vd[e])) : z0;
+            const T e_yz_kp = hasup ? (h * (Wu[e] + Wujm[e])) * (h * (Vu[e] + V[e])) : z0;
+            const T vcp = h * (V[e] + Vjp[e]), vcm = h * (Vjm[e] + V[e]);
+            const T Hv = -((exy[e + 1] - exy[e]) * cf.idx + (vcp * vcp - vcm * vcm) * cf.idy +
+                           (e_yz_kp - e_yz) * cf.idzk);
+            const T Lv = (vip - T(2) * V[e] + vim) * cf.idx2 +
+                         (Vjp[e] - T(2) * V[e] + Vjm[e]) * cf.idy2 +
+                         ((Vu[e] - V[e]) * cf.ihcu - (V[e] - Vd[e]) * cf.ihck) * cf.idzk;
+            Hn[1][e] = Hv;
+            R[1][e] = cf.dt * (cf.gam * Hv + cf.rho * H1[e] + cf.inv_re * Lv -
+                               (P[e] - Pjm[e]) * cf.idy + fy[e] + cf.fc1);
+        }
+    }
+    {
+        T H1[CPL];
+        ldrow(H1, F.hw + oc + i0);
+        T fz[CPL];
+        if (F.fz && !cf.wall_face) ldrow(fz, F.fz + oc + i0);
+        else {
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) fz[e] = z0;
+        }
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+            T Hw = z0, rw = z0;
+            if (!cf.wall_face) {
+                const T wim = e == 0 ? Wl : W[e - 1], wip = e == CPL - 1 ? Wr : W[e + 1];
+                const T e_yz = hasdn ? (h * (W[e] + Wjm[e])) * (h * (V[e] + Vd[e])) : z0;
+                const T e_yz_jp = hasdn ? (h * (Wjp[e] + W[e])) * (h * (Vjp[e] + Vdjp[e])) : z0;
+                const T wcp = h * (W[e] + Wu[e]), wcm = h * (Wd[e] + W[e]);
+                Hw = -((exz[e + 1] - exz[e]) * cf.idx + (e_yz_jp - e_yz) * cf.idy +
+                       (wcp * wcp - wcm * wcm) * cf.ihck);
+                const T Lw = (wip - T(2) * W[e] + wim) * cf.idx2 +
+                             (Wjp[e] - T(2) * W[e] + Wjm[e]) * cf.idy2 +
+                             ((Wu[e] - W[e]) * cf.idzk - (W[e] - Wd[e]) * cf.idzd) * cf.ihck;
+                rw = cf.dt * (cf.gam * Hw + cf.rho * H1[e] + cf.inv_re * Lw -
+                              (P[e] - Pd[e]) * cf.ihck + fz[e] + cf.fc2);
+            }
+            Hn[2][e] = Hw;
+            R[2][e] = rw;
+        }
+    }
+    strow(F.hu + oc + i0, Hn[0]);
+    strow(F.hv + oc + i0, Hn[1]);
+    strow(F.hw + oc + i0, Hn[2]);
+    line_solve_uni<T, CPL, LPR, 3>(R, fpick<T>(sc->ax, sc->fax), fpick<T>(sc->cix, sc->fcix), xs);
+    strow(q0 + oc + i0, R[0]);
+    strow(q1 + oc + i0, R[1]);
+    strow(q2 + oc + i0, R[2]);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launchers --
@@ -721,8 +933,51 @@ void rhs_tile_ry(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepSca
     else rhs_tile_L<T, 64, RY>(g, F, W, sc, a, P, smem, st);
 }
 
+// Geometry of the row-resident right-hand side: CPL cells per lane (8 in
+// single, 4 in double precision), LPR = nx / CPL lanes per row (a power of
+// two, 4 .. 256), rows per block rpb (a power of two dividing ny, the block
+// of rpb LPR >= 32 threads at most max(128, LPR)); false where it does not
+// apply.
+template <typename T> bool rhs_row_geometry(const GridDev &g, int &cpl, int &lpr, int &rpb) {
+    cpl = sizeof(T) == 4 ? 8 : 4;
+    if (g.nx % cpl) return false;
+    lpr = g.nx / cpl;
+    if (lpr < 4 || lpr > 256 || (lpr & (lpr - 1))) return false;
+    const int bmax = lpr > 128 ? lpr : 128;
+    for (rpb = bmax / lpr; rpb >= 1; rpb /= 2)
+        if (g.ny % rpb == 0 && rpb * lpr >= 32) return true;
+    return false;
+}
+
+template <typename T, int CPL, int LPR>
+void rhs_row_launch(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
+                    const StepArgs &a, int rpb, cudaStream_t st) {
+    k_rhs_x_row<T, CPL, LPR><<<g.nz * (g.ny / rpb), rpb * LPR, 0, st>>>(
+        g, F, W.q0, W.q1, W.q2, sc, rpb, T(a.fconst[0]), T(a.fconst[1]), T(a.fconst[2]),
+        T(1.0 / a.re));
+}
+
+template <typename T, int CPL>
+bool rhs_row_dispatch(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
+                      const StepArgs &a, int lpr, int rpb, cudaStream_t st) {
+    switch (lpr) {
+    case 4: rhs_row_launch<T, CPL, 4>(g, F, W, sc, a, rpb, st); return true;
+    case 8: rhs_row_launch<T, CPL, 8>(g, F, W, sc, a, rpb, st); return true;
+    case 16: rhs_row_launch<T, CPL, 16>(g, F, W, sc, a, rpb, st); return true;
+    case 32: rhs_row_launch<T, CPL, 32>(g, F, W, sc, a, rpb, st); return true;
+    case 64: rhs_row_launch<T, CPL, 64>(g, F, W, sc, a, rpb, st); return true;
+    case 128: rhs_row_launch<T, CPL, 128>(g, F, W, sc, a, rpb, st); return true;
+    case 256: rhs_row_launch<T, CPL, 256>(g, F, W, sc, a, rpb, st); return true;
+    default: return false;
+    }
+}
+
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
+    int cpl = 0, lpr = 0, rpb = 0;
+    if (rhs_row_geometry<T>(g, cpl, lpr, rpb) &&
+        rhs_row_dispatch<T, sizeof(T) == 4 ? 8 : 4>(g, F, W, sc, a, lpr, rpb, st))
+        return;
     int RY = 0, P = 0;
     size_t smem = 0;
     if (rhs_tile_geometry<T>(g, RY, P, smem)) {
@@ -757,6 +1012,14 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     raise_smem_limit(k_rhs_x_tile<T, 16, 2>);
     raise_smem_limit(k_rhs_x_tile<T, 32, 2>);
     raise_smem_limit(k_rhs_x_tile<T, 64, 2>);
+    constexpr int C = sizeof(T) == 4 ? 8 : 4;
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 4>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 8>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 16>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 32>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 64>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 128>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 256>);
 }
 
 #define FSEI_INST(T)                                                                           \

@@ -368,4 +368,157 @@ __device__ __forceinline__ void uni_solve(T (&d)[L], int len, bool active, int l
     }
 }
 
+// ------------------------------------------ lane-resident periodic lines --
+// A periodic line of n = LPR CPL unknowns held in registers by LPR
+// consecutive threads (lane r of the line holds unknowns CPL r .. CPL r +
+// CPL - 1); LPR a power of two.  A line of more than 32 lanes spans LPR / 32
+// whole warps of the block.
+
+// Carries of NV independent cyclic first-order recurrences with a common
+// slope over the lanes of a line.  Lane p holds the zero-carry end values
+// v[m] of its unknowns and g = alpha^CPL:
+//   BACK = 1:  Z_p = v_p + g Z_{p+1}   (Z_p: value at lane p's first
+//              unknown); on return v[m] = Z_{p+1}, the carry lane p needs
+//   BACK = 0:  X_p = v_p + g X_{p-1}   (X_p: value at its last unknown);
+//              on return v[m] = X_{p-1}
+// with lane indices mod LPR.  Within a warp a scan of the affine maps Z ->
+// v + g Z gives each lane the composition of its segment's maps; lines
+// longer than a warp combine the warps' compositions through xs (2 NV
+// values per warp of the block) between two barriers.  Every thread of the
+// block calls it.
+template <typename T, int LPR, int BACK, int NV>
+FSEI_D void line_carries(T (&v)[NV], T g, T *xs) {
+    constexpr int W = LPR < 32 ? LPR : 32;
+    const int lane = threadIdx.x & 31;
+    const int p = lane & (W - 1);
+    T A[NV], B = g;
+#pragma unroll
+    for (int m = 0; m < NV; ++m) A[m] = v[m];
+#pragma unroll
+    for (int s = 1; s < W; s <<= 1) {
+        const T B2 = BACK ? __shfl_down_sync(0xffffffffu, B, s, W)
+                          : __shfl_up_sync(0xffffffffu, B, s, W);
+        const bool take = BACK ? (p + s < W) : (p >= s);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            const T A2 = BACK ? __shfl_down_sync(0xffffffffu, A[m], s, W)
+                              : __shfl_up_sync(0xffffffffu, A[m], s, W);
+            if (take) A[m] = A[m] + B * A2;
+        }
+        if (take) B = B * B2;
+    }
+    // (A, B) at lane p: composition of the maps p .. W-1 (BACK) or 0 .. p
+    // of its segment; the segment's own composition sits at its root lane
+    const int root = BACK ? 0 : W - 1;
+    T Vin[NV];   // value entering the segment from beyond its far end
+    if (LPR <= 32) {
+        const T Br = __shfl_sync(0xffffffffu, B, root, W);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            const T Ar = __shfl_sync(0xffffffffu, A[m], root, W);
+            Vin[m] = Ar * rcp(T(1) - Br);   // the cycle closes: V = Ar + Br V
+        }
+    } else {
+        constexpr int NW = LPR / 32;
+        const int wid = threadIdx.x >> 5;
+        const int w = wid & (NW - 1), w0 = wid - w;
+        if (lane == root) {
+#pragma unroll
+            for (int m = 0; m < NV; ++m) xs[(2 * NV) * wid + m] = A[m];
+            xs[(2 * NV) * wid + NV] = B;
+        }
+        __syncthreads();
+        // compositions of the line's warps: around the whole cycle (TA, TB)
+        // and over the warps beyond this one (RA, RB), BACK: w+1 .. NW-1,
+        // forward: w-1 .. 0, each applied first-to-last away from the root
+        T TA[NV], RA[NV], TB = T(1), RB = T(1);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) { TA[m] = T(0); RA[m] = T(0); }
+#pragma unroll
+        for (int t = 0; t < NW; ++t) {
+            // BACK composes from the last warp down to the first; forward
+            // from the first up to the last
+            const int u = BACK ? NW - 1 - t : t;
+            const T *a = xs + (2 * NV) * (w0 + u);
+            const T ub = a[NV];
+#pragma unroll
+            for (int m = 0; m < NV; ++m) TA[m] = a[m] + ub * TA[m];
+            TB = ub * TB;
+            if (BACK ? (u > w) : (u < w)) {
+#pragma unroll
+                for (int m = 0; m < NV; ++m) RA[m] = a[m] + ub * RA[m];
+                RB = ub * RB;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < NV; ++m) {
+            const T V = TA[m] * rcp(T(1) - TB);   // Z_0 (BACK) or X_{n-1}
+            Vin[m] = RA[m] + RB * V;
+        }
+    }
+    // value at this lane's own end, then the carry from its neighbour
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+        const T mine = A[m] + B * Vin[m];
+        const T nb = BACK ? __shfl_down_sync(0xffffffffu, mine, 1, W)
+                          : __shfl_up_sync(0xffffffffu, mine, 1, W);
+        v[m] = (BACK ? p == W - 1 : p == 0) ? Vin[m] : nb;
+    }
+}
+
+// Solve NV constant-coefficient periodic lines (I - beta L) x = y with the
+// factorised inverse of uni_solve: z_i = y_i + alpha z_{i+1}, x'_i = z_i +
+// alpha x'_{i-1}, x = x' / c, each recurrence evaluated lane by lane from a
+// zero carry and corrected with the carries of line_carries.  d[m][e]:
+// unknown CPL r + e of line m at lane r of the line.  Every thread of the
+// block calls it.
+template <typename T, int CPL, int LPR, int NV>
+FSEI_D void line_solve_uni(T (&d)[NV][CPL], T alpha, T cinv, T *xs) {
+    T g = T(1), a = alpha;
+#pragma unroll
+    for (int e = CPL; e > 0; e >>= 1) {    // alpha^CPL by squaring
+        if (e & 1) g *= a;
+        a *= a;
+    }
+    T c[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+        T z = T(0);
+#pragma unroll
+        for (int i = CPL - 1; i >= 0; --i) {
+            z = d[m][i] + alpha * z;
+            d[m][i] = z;
+        }
+        c[m] = z;
+    }
+    line_carries<T, LPR, 1, NV>(c, g, xs);
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+        T pw = c[m];
+#pragma unroll
+        for (int i = CPL - 1; i >= 0; --i) {
+            pw *= alpha;
+            d[m][i] += pw;
+        }
+        T x = T(0);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            x = d[m][i] + alpha * x;
+            d[m][i] = x;
+        }
+        c[m] = x;
+    }
+    line_carries<T, LPR, 0, NV>(c, g, xs);
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+        T pw = c[m];
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            pw *= alpha;
+            d[m][i] = (d[m][i] + pw) * cinv;
+        }
+    }
+}
+
 }  // namespace fsei
