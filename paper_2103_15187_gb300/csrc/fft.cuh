@@ -145,4 +145,94 @@ FSEI_D void dft_reg(cplx<T> (&x)[B], const cplx<T> *tw, int N) {
     }
 }
 
+// Split N = N1 N2 of the two-pass transforms below (N1 >= N2, both powers of
+// two <= 16: the register arrays stay small), 0 for lengths that take the
+// Stockham passes of fft_lines.
+FSEI_HD int fft_split_n1(int n) {
+    switch (n) {
+    case 16: return 4;
+    case 32: return 8;
+    case 64: return 8;
+    case 128: return 16;
+    case 256: return 16;
+    default: return 0;
+    }
+}
+// Complex values of scratch per line that the two-pass transform of a line
+// stored whole (element stride 1) needs: N2 blocks of N1 + 1 (the padding
+// staggers the banks of the transposed accesses); n otherwise.
+FSEI_HD int fft_scratch_len(int n) {
+    const int n1 = fft_split_n1(n);
+    return n1 ? (n / n1) * (n1 + 1) : n;
+}
+
+// Two-pass transform of nl lines of length N = N1 N2, with n = N2 n1 + n2
+// and k = k1 + N1 k2:
+//   X[k] = sum_n2 w_N2^(n2 k2) w_N^(n2 k1) sum_n1 w_N1^(n1 k1) x[N2 n1 + n2].
+// Pass 1, item (l, n2): the N1 values x[N2 n1 + n2] of line l, an in-register
+// DFT of length N1, the twiddles w_N^(n2 k1), stored to b.  Pass 2, item
+// (l, k1): the N2 values of k1 from b, an in-register DFT of length N2,
+// X[k1 + N1 k2] to a.  LF (lines fastest, the layout of a with element
+// stride es, line stride ls): b has a's layout, value (n2, k1) at position
+// n2 N1 + k1; otherwise (lines stored whole) line l's values sit in b at
+// l bls + n2 (N1 + 1) + k1.  tw: w^m = exp(-2 pi i m / N), m < N (conjugated
+// for SIGN > 0).  Every thread of the block calls it; returns a (natural
+// order) after a barrier.
+template <typename T, int SIGN, int N1, int N2, bool LF>
+__device__ cplx<T> *fft_lines_2p(cplx<T> *a, cplx<T> *b, int es, int ls, int bls, int nl,
+                                 const cplx<T> *__restrict__ tw) {
+    constexpr int N = N1 * N2;
+    for (int w = threadIdx.x; w < nl * N2; w += blockDim.x) {
+        int l, n2;
+        if (LF) { n2 = ddiv(w, nl); l = w - n2 * nl; }
+        else { l = w / N2; n2 = w - l * N2; }
+        cplx<T> x[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = a[(n1 * N2 + n2) * es + l * ls];
+        dft_reg<T, N1, SIGN>(x, tw, N);
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) {
+            cplx<T> t = tw[n2 * k1];
+            if (SIGN > 0) t = conj(t);
+            x[k1] = x[k1] * t;
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            if (LF) b[(n2 * N1 + k1) * es + l * ls] = x[k1];
+            else b[l * bls + n2 * (N1 + 1) + k1] = x[k1];
+        }
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < nl * N1; w += blockDim.x) {
+        int l, k1;
+        if (LF) { k1 = ddiv(w, nl); l = w - k1 * nl; }
+        else { l = w / N1; k1 = w - l * N1; }
+        cplx<T> y[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2)
+            y[n2] = LF ? b[(n2 * N1 + k1) * es + l * ls] : b[l * bls + n2 * (N1 + 1) + k1];
+        dft_reg<T, N2, SIGN>(y, tw, N);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) a[(k1 + N1 * k2) * es + l * ls] = y[k2];
+    }
+    __syncthreads();
+    return a;
+}
+
+// fft_lines with the two-pass transform for the lengths fft_split_n1 lists;
+// b then holds at least nl fft_scratch_len(N) values (lines stored whole,
+// line stride bls in b) or a's layout (LF).
+template <typename T, int SIGN, bool LF>
+__device__ cplx<T> *fft_lines_fast(cplx<T> *a, cplx<T> *b, int es, int ls, int bls, int nl,
+                                   const FftPlanDev &fp, const cplx<T> *__restrict__ tw) {
+    switch (fp.n) {
+    case 16: return fft_lines_2p<T, SIGN, 4, 4, LF>(a, b, es, ls, bls, nl, tw);
+    case 32: return fft_lines_2p<T, SIGN, 8, 4, LF>(a, b, es, ls, bls, nl, tw);
+    case 64: return fft_lines_2p<T, SIGN, 8, 8, LF>(a, b, es, ls, bls, nl, tw);
+    case 128: return fft_lines_2p<T, SIGN, 16, 8, LF>(a, b, es, ls, bls, nl, tw);
+    case 256: return fft_lines_2p<T, SIGN, 16, 16, LF>(a, b, es, ls, bls, nl, tw);
+    default: return fft_lines<T, SIGN>(a, b, es, ls, nl, fp, tw, LF);
+    }
+}
+
 }  // namespace fsei

@@ -72,12 +72,12 @@ __device__ __forceinline__ void chunk_backward(T (&d)[L], int len, const TriPlan
 // Blocks hold at most 256 threads for chunks of <= 16 unknowns, 512 above
 // (sweep_geometry); the minimum-blocks hint leaves room for the chunk, and in
 // single precision for the prefetched u^n, in registers.
-template <typename T, int L, int DIR, int MODE>
-__global__ void __launch_bounds__(L <= 16 ? 256 : 512, L <= 16 ? (sizeof(T) == 4 ? 3 : 2) : 1)
-k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
-            T *__restrict__ q2, TriPlan<T> pa, TriPlan<T> pb, int tx) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);
+// EXACT: every chunk of the line holds L unknowns (n = L P).
+template <typename T, int L, int DIR, int MODE, bool EXACT>
+__device__ __forceinline__ void sweep_reg_body(const GridDev &g, const Fields<T> &F,
+                                               T *__restrict__ q0, T *__restrict__ q1,
+                                               T *__restrict__ q2, const TriPlan<T> &pa,
+                                               const TriPlan<T> &pb, int tx, T *sm) {
     const int nx = g.nx, ny = g.ny;
     const int nxt = (nx + tx - 1) / tx;
     int b = blockIdx.x;
@@ -106,24 +106,24 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     T un_pre[kPrefetch ? L : 1];
     // issue the chunk's loads first; staging the plan below overlaps them
     if (active) {
-        s0 = chunk_start(p, src.n, src.P);
-        len = chunk_start(p + 1, src.n, src.P) - s0;
+        s0 = EXACT ? p * L : chunk_start(p, src.n, src.P);
+        len = EXACT ? L : chunk_start(p + 1, src.n, src.P) - s0;
         const T *qp = q + base + (size_t)s0 * stride;
 #pragma unroll
         for (int i = 0; i < L; ++i)
-            if (i < len) d[i] = qp[(size_t)i * stride];
+            if (EXACT || i < len) d[i] = qp[(size_t)i * stride];
         if constexpr (kPrefetch) {
             const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
             const T *up = un + base + (size_t)s0 * stride;
 #pragma unroll
             for (int i = 0; i < L; ++i)
-                if (i < len) un_pre[i] = up[(size_t)i * stride];
+                if (EXACT || i < len) un_pre[i] = up[(size_t)i * stride];
         }
     }
     const TriPlan<T> pl = stage_plan(src, red + (size_t)tx * rs);
     if (active) {
         T rF, rE;
-        chunk_forward<T, L>(d, len, pl, s0, rF, rE);
+        chunk_forward<T, L>(d, EXACT ? L : len, pl, s0, rF, rE);
         red[l * rs + 2 * p] = rF;
         red[l * rs + 2 * p + 1] = rE;
     }
@@ -131,28 +131,29 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     reduced_lines<T>(red, rs, tx, pl);
     __syncthreads();
     if (active) {
-        chunk_backward<T, L>(d, len, pl, s0, red[l * rs + 2 * p], red[l * rs + 2 * p + 1]);
+        chunk_backward<T, L>(d, EXACT ? L : len, pl, s0, red[l * rs + 2 * p],
+                             red[l * rs + 2 * p + 1]);
         T *qp = fresh(q) + base + (size_t)s0 * stride;
         if (DIR == 1) {
 #pragma unroll
             for (int i = 0; i < L; ++i)
-                if (i < len) qp[(size_t)i * stride] = d[i];
+                if (EXACT || i < len) qp[(size_t)i * stride] = d[i];
         } else if (MODE == 0) {
             if constexpr (kPrefetch) {
 #pragma unroll
                 for (int i = 0; i < L; ++i)
-                    if (i < len) qp[(size_t)i * stride] = un_pre[i] + d[i];
+                    if (EXACT || i < len) qp[(size_t)i * stride] = un_pre[i] + d[i];
             } else {
                 const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
                 const T *up = un + base + (size_t)s0 * stride;
 #pragma unroll
                 for (int i = 0; i < L; ++i)
-                    if (i < len) qp[(size_t)i * stride] = up[(size_t)i * stride] + d[i];
+                    if (EXACT || i < len) qp[(size_t)i * stride] = up[(size_t)i * stride] + d[i];
             }
         } else {
 #pragma unroll
             for (int i = 0; i < L; ++i)
-                if (i < len) {
+                if (EXACT || i < len) {
                     const int k = s0 + i + pl.off;
                     const T wk = comp < 2 ? Metric<T>::dz(g)[k] : T(1) / Metric<T>::ihc(g)[k];
                     qp[(size_t)i * stride] = wk * d[i];
@@ -161,8 +162,26 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     }
 }
 
+template <typename T, int L, int DIR, int MODE>
+__global__ void __launch_bounds__(L <= 16 ? 256 : 512, L <= 16 ? (sizeof(T) == 4 ? 3 : 2) : 1)
+k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
+            T *__restrict__ q2, TriPlan<T> pa, TriPlan<T> pb, int tx) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    // the component of this block picks its plan; lines of L P unknowns take
+    // the guard-free path
+    const int outer = DIR == 1 ? g.nz : g.ny;
+    const int comp = (int)blockIdx.x / ((g.nx + tx - 1) / tx) / outer;
+    const TriPlan<T> &src = (DIR == 2 && comp == 2) ? pb : pa;
+    if (src.n == L * src.P)
+        sweep_reg_body<T, L, DIR, MODE, true>(g, F, q0, q1, q2, pa, pb, tx, sm);
+    else
+        sweep_reg_body<T, L, DIR, MODE, false>(g, F, q0, q1, q2, pa, pb, tx, sm);
+}
+
 // y sweep of plane k: q = (I - beta L_y)^-1 q for the three components.
-template <typename T, int L>
+// EXACT: every chunk holds L unknowns (ny = L P), no per-unknown guards.
+template <typename T, int L, bool EXACT>
 __global__ void __launch_bounds__(256, L <= 16 ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? 2 : 1))
 k_sweep_y_uni(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
               const StepScalars *sc, int P, int tx) {
@@ -179,19 +198,19 @@ k_sweep_y_uni(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__
     const int p = ddiv(t, tx), l = t - p * tx;
     const int x = xt * tx + l;
     const bool active = p < P && x < nx;
-    const int s0 = active ? chunk_start(p, ny, P) : 0;
-    const int len = active ? chunk_start(p + 1, ny, P) - s0 : 0;
+    const int s0 = active ? (EXACT ? p * L : chunk_start(p, ny, P)) : 0;
+    const int len = EXACT ? L : (active ? chunk_start(p + 1, ny, P) - s0 : 0);
     T *qp = q + (k * ny + s0) * nx + x;    // a field holds < 2^31 values
     T d[L];
 #pragma unroll
     for (int i = 0; i < L; ++i)
-        if (i < len) d[i] = qp[i * nx];
-    uni_solve<T, L>(d, len, active, l, p, tx, ny, P, fpick<T>(sc->ay, sc->fay),
-                    fpick<T>(sc->ciy, sc->fciy), car);
+        if (active && i < len) d[i] = qp[i * nx];
+    uni_solve<T, L, EXACT>(d, len, active, l, p, tx, ny, P, fpick<T>(sc->ay, sc->fay),
+                           fpick<T>(sc->ciy, sc->fciy), car);
     T *qs = fresh(qp);
 #pragma unroll
     for (int i = 0; i < L; ++i)
-        if (i < len) qs[i * nx] = d[i];
+        if (active && i < len) qs[i * nx] = d[i];
 }
 
 template <typename T, int L, int DIR, int MODE>
@@ -253,8 +272,13 @@ void launch_y_uni(const GridDev &g, Work<T> &W, const StepScalars *sc, cudaStrea
     const int tx = W.tx_y, P = W.py;
     const int nxt = (g.nx + tx - 1) / tx;
     const int threads = ((tx * P + 31) / 32) * 32;
-    k_sweep_y_uni<T, L><<<3 * g.nz * nxt, threads, 2 * sizeof(T) * tx * P, st>>>(
-        g, W.q0, W.q1, W.q2, sc, P, tx);
+    const size_t sm = 2 * sizeof(T) * tx * P;
+    if (g.ny == L * P)
+        k_sweep_y_uni<T, L, true><<<3 * g.nz * nxt, threads, sm, st>>>(g, W.q0, W.q1, W.q2, sc,
+                                                                       P, tx);
+    else
+        k_sweep_y_uni<T, L, false><<<3 * g.nz * nxt, threads, sm, st>>>(g, W.q0, W.q1, W.q2, sc,
+                                                                        P, tx);
 }
 
 template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, const StepScalars *sc,
@@ -278,9 +302,12 @@ template <typename T> void launch_sweep_z_adjoint(const GridDev &g, Work<T> &W, 
 template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T> &W) {
     (void)g;
     (void)W;
-    raise_smem_limit(k_sweep_y_uni<T, 8>);
-    raise_smem_limit(k_sweep_y_uni<T, 16>);
-    raise_smem_limit(k_sweep_y_uni<T, 32>);
+    raise_smem_limit(k_sweep_y_uni<T, 8, false>);
+    raise_smem_limit(k_sweep_y_uni<T, 8, true>);
+    raise_smem_limit(k_sweep_y_uni<T, 16, false>);
+    raise_smem_limit(k_sweep_y_uni<T, 16, true>);
+    raise_smem_limit(k_sweep_y_uni<T, 32, false>);
+    raise_smem_limit(k_sweep_y_uni<T, 32, true>);
     raise_smem_limit(k_sweep_reg<T, 8, 2, 0>);
     raise_smem_limit(k_sweep_reg<T, 16, 2, 0>);
     raise_smem_limit(k_sweep_reg<T, 32, 2, 0>);

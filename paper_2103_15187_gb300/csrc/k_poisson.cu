@@ -24,6 +24,12 @@ namespace {
 // Row length (complex elements) of the x-transform lines in shared memory:
 // mx rounded up to even, so that every line starts on a 16-byte boundary.
 FSEI_HD int fft_x_ls(int mx) { return mx + (mx & 1); }
+// Scratch row length of the x transforms (the two-pass transform's padded
+// layout where it applies), even.
+FSEI_HD int fft_x_bls(int mx) {
+    const int b = fft_scratch_len(mx) > mx ? fft_scratch_len(mx) : mx;
+    return b + (b & 1);
+}
 // complex values per staged spectrum row of the inverse x transform: kx <=
 // mx, rounded up to whole 16-byte copies (within the row stride sk, a
 // multiple of 16)
@@ -55,9 +61,10 @@ k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx, ny = g.ny, nz = g.nz, mx = g.mx, sk = g.sk;
     const int ls = fft_x_ls(mx);
+    const int bls = fft_x_bls(mx);
     cplx<T> *A = reinterpret_cast<cplx<T> *>(smraw);
     cplx<T> *B = A + (size_t)RY * ls;
-    cplx<T> *TW = B + (size_t)RY * ls;
+    cplx<T> *TW = B + (size_t)RY * bls;
     cplx<T> *TP = TW + fft_x_ls(mx);
     const int nby = ny / RY;
     const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * RY;
@@ -97,7 +104,7 @@ k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
         stage_x_twiddles(TW, TP, twx, twpost, mx);
     }
     __syncthreads();
-    const cplx<T> *R = fft_lines<T, -1>(A, B, 1, ls, RY, fp, TW, false);
+    const cplx<T> *R = fft_lines_fast<T, -1, false>(A, B, 1, ls, bls, RY, fp, TW);
     const T hf = T(0.5);
     for (int e = threadIdx.x; e < RY * (mx + 1); e += blockDim.x) {
         const int r = e / (mx + 1), kx = e - r * (mx + 1);
@@ -129,7 +136,7 @@ k_fft_y(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ twy, 
     for (int m = threadIdx.x; m < ny; m += blockDim.x) TW[m] = twy[m];
     cp_async_wait_all();
     __syncthreads();
-    const cplx<T> *R = fft_lines<T, SIGN>(A, B, tkx, 1, tkx, fp, TW, true);
+    const cplx<T> *R = fft_lines_fast<T, SIGN, true>(A, B, tkx, 1, 0, tkx, fp, TW);
     // 16-byte stores: rb is a multiple of 16 (tkx even in single precision)
     const int per = rb / 16;
     for (int e = threadIdx.x; e < ny * per; e += blockDim.x) {
@@ -444,9 +451,10 @@ k_irfft_x(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
     const int nx = g.nx, ny = g.ny, mx = g.mx, sk = g.sk;
     const int ls = fft_x_ls(mx);
     const int ss = irfft_stage_row(mx);
+    const int bls = fft_x_bls(mx);
     cplx<T> *A = reinterpret_cast<cplx<T> *>(smraw);
     cplx<T> *B = A + (size_t)RY * ls;
-    cplx<T> *TW = B + (size_t)RY * ls;
+    cplx<T> *TW = B + (size_t)RY * bls;
     cplx<T> *TP = TW + fft_x_ls(mx);
     cplx<T> *S = TP + fft_x_ls(mx + 1);
     const int nby = ny / RY;
@@ -466,7 +474,7 @@ k_irfft_x(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
         A[r * ls + kx] = ev + mul_i<T, 1>(od);
     }
     __syncthreads();
-    const cplx<T> *R = fft_lines<T, 1>(A, B, 1, ls, RY, fp, TW, false);
+    const cplx<T> *R = fft_lines_fast<T, 1, false>(A, B, 1, ls, bls, RY, fp, TW);
     const bool v16 = ((nx * sizeof(T)) & 15) == 0;
     for (int r = 0; r < RY; ++r) {
         T *drow = dst + ((size_t)k * ny + j0 + r) * nx;
@@ -486,7 +494,8 @@ k_irfft_x(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
 // x transforms: two line buffers, the twiddle tables and (inverse only) the
 // staged spectrum rows; ry rows per block
 template <typename T> size_t smem_rfft_x(const GridDev &g, int ry) {
-    return sizeof(cplx<T>) * (2 * (size_t)ry * fft_x_ls(g.mx) + fft_x_ls(g.mx) + fft_x_ls(g.mx + 1));
+    return sizeof(cplx<T>) * ((size_t)ry * (fft_x_ls(g.mx) + fft_x_bls(g.mx)) + fft_x_ls(g.mx) +
+                              fft_x_ls(g.mx + 1));
 }
 template <typename T> size_t smem_irfft_x(const GridDev &g, int ry) {
     return smem_rfft_x<T>(g, ry) + sizeof(cplx<T>) * (size_t)ry * irfft_stage_row(g.mx);

@@ -274,7 +274,7 @@ __device__ void tri_fly_solve(cplx<T> *s, int es, int ls, T *fa, T *fc, int fes,
 // with g_p = alpha^len_p and indices mod P.  Every thread of the block calls
 // it (the shuffles need whole warps); a barrier must separate it from the
 // writes of v and from the reads of the carries.
-template <typename T, int BACK>
+template <typename T, int BACK, int FIXED = 0>
 __device__ __forceinline__ void uni_carries(T *v, int nl, int n, int P, T alpha) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (int)((blockDim.x + 31) >> 5);
@@ -283,7 +283,7 @@ __device__ __forceinline__ void uni_carries(T *v, int nl, int n, int P, T alpha)
     for (int l0 = wid * per; l0 < nl; l0 += nw * per) {
         const int l = l0 + seg;
         const bool on = l < nl;
-        const int len = chunk_start(p + 1, n, P) - chunk_start(p, n, P);
+        const int len = FIXED ? FIXED : chunk_start(p + 1, n, P) - chunk_start(p, n, P);
         T g = T(1), a = alpha;
         for (int e = len; e > 0; e >>= 1) {      // alpha^len by squaring
             if (e & 1) g *= a;
@@ -318,11 +318,13 @@ __device__ __forceinline__ void uni_carries(T *v, int nl, int n, int P, T alpha)
 
 // Solve the chunks of nl constant-coefficient periodic lines, chunk p of
 // line l held by one thread in d[0 .. len-1] (active threads only).  car:
-// shared scratch of 2 nl P values.  Every thread of the block calls it; it
-// contains barriers.
-template <typename T, int L>
-__device__ __forceinline__ void uni_solve(T (&d)[L], int len, bool active, int l, int p, int nl,
+// shared scratch of 2 nl P values.  EXACT: every chunk has L unknowns (len
+// is then L; no per-unknown guards).  Every thread of the block calls it;
+// it contains barriers.
+template <typename T, int L, bool EXACT = false>
+__device__ __forceinline__ void uni_solve(T (&d)[L], int len_, bool active, int l, int p, int nl,
                                           int n, int P, T alpha, T cinv, T *car) {
+    const int len = EXACT ? L : len_;
     T *zc = car, *xc = car + nl * P;
     if (active) {
         T z = T(0);
@@ -335,7 +337,7 @@ __device__ __forceinline__ void uni_solve(T (&d)[L], int len, bool active, int l
         zc[l * P + p] = z;          // zero-carry value at the chunk's first unknown
     }
     __syncthreads();
-    uni_carries<T, 1>(zc, nl, n, P, alpha);
+    uni_carries<T, 1, EXACT ? L : 0>(zc, nl, n, P, alpha);
     __syncthreads();
     if (active) {
         T pw = zc[l * P + p];       // Z of the next chunk
@@ -355,7 +357,7 @@ __device__ __forceinline__ void uni_solve(T (&d)[L], int len, bool active, int l
         xc[l * P + p] = x;          // zero-carry value at the chunk's last unknown
     }
     __syncthreads();
-    uni_carries<T, 0>(xc, nl, n, P, alpha);
+    uni_carries<T, 0, EXACT ? L : 0>(xc, nl, n, P, alpha);
     __syncthreads();
     if (active) {
         T pw = xc[l * P + p];       // X of the previous chunk
