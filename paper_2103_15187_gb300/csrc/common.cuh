@@ -148,10 +148,14 @@ FSEI_D int ddiv(int x, int d) { return (d & (d - 1)) == 0 ? (x >> (31 - __clz(d)
 // ------------------------------------------------ asynchronous copies ------
 // cp.async: global -> shared copies that complete in the background (no
 // register staging, so a thread can have all of its copies in flight).
-// 16 bytes: both addresses 16-byte aligned; 4 bytes: both 4-byte aligned.
+// 16 (8, 4) bytes: both addresses 16 (8, 4)-byte aligned.
 FSEI_D void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+FSEI_D void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 FSEI_D void cp_async4(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);

@@ -303,15 +303,17 @@ k_poisson_exact(GridDev g, cplx<T> *spec, const int *modes, const double *lamx,
 // xz (v . y) / (1 + v . z), v . y = y_0 + v_last y_{n-1}.  The (0, 0) mode
 // pins phi_0 = 0 (rows 1 .. nz-1) and removes the volume-weighted mean, as
 // k_poisson_exact does.
+// One warp (lane = 0 .. 31) solves exactly solved mode number `mode`; D:
+// shared scratch of nz values.
 template <typename T>
-__global__ void __launch_bounds__(32)
-k_poisson_exact_f(GridDev g, cplx<T> *spec, const int *modes, const double *xa,
-                  const double *xm, const double *xc, const double *xz, const double *xs,
-                  double scale, int compat, double zlen) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<double> *D = reinterpret_cast<cplx<double> *>(smraw);
-    const int nz = g.nz, lane = threadIdx.x;
-    const int mode = blockIdx.x, code = modes[mode];
+__device__ __forceinline__ void exact_mode_solve(const GridDev &g, cplx<T> *spec, int mode,
+                                                 const int *modes, const double *xa,
+                                                 const double *xm, const double *xc,
+                                                 const double *xz, const double *xs,
+                                                 double scale, int compat, double zlen,
+                                                 cplx<double> *D, int lane) {
+    const int nz = g.nz;
+    const int code = modes[mode];
     const int kx = code % g.sk, ky = code / g.sk;
     const bool zero_mode = kx == 0 && ky == 0;
     const bool cyclic = !g.walls && !zero_mode;
@@ -425,6 +427,215 @@ k_poisson_exact_f(GridDev g, cplx<T> *spec, const int *modes, const double *xa,
         line[(size_t)k * stride] = cplx<T>{T((D[k].re - mr) * scale), T((D[k].im - mi) * scale)};
 }
 
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_poisson_exact_f(GridDev g, cplx<T> *spec, const int *modes, const double *xa,
+                  const double *xm, const double *xc, const double *xz, const double *xs,
+                  double scale, int compat, double zlen) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    exact_mode_solve<T>(g, spec, blockIdx.x, modes, xa, xm, xc, xz, xs, scale, compat, zlen,
+                        reinterpret_cast<cplx<double> *>(smraw), threadIdx.x);
+}
+
+// Lane-resident z solve: one warp segment of LPL lanes per Fourier mode
+// line (kx, ky), lane r holding rows r E .. r E + E - 1 (nz = LPL E) of
+// (L_z - lambda_x - lambda_y) phi = s in registers.  The block owns NL =
+// 256 / LPL consecutive kx columns of one ky row; the tile is staged in
+// shared memory by asynchronous copies, XOR-swizzled so that the lanes'
+// strided rows fall in different banks.  Each lane eliminates its chunk
+// interior with factors formed on the fly (as tri_fly_solve), which leaves
+// two unknowns per lane (its first and last row) in a tridiagonal system of
+// 2 LPL unknowns coupled cyclically across the lanes (with walls the end
+// couplings are zero, so the cyclic indexing changes nothing); parallel
+// cyclic reduction over lane shuffles solves it in log2(2 LPL) levels, and
+// each lane substitutes back into its chunk.  Blocks 0 .. n_exact-1 instead
+// solve the exactly handled modes in double (exact_mode_solve), starting
+// before the others; the other blocks read those modes but do not store
+// them.  Results scaled by 1/(nx ny).
+template <typename T> struct alignas(4 * sizeof(T)) ZCoef { T a, c, b0, pad; };
+
+template <typename T, int E, int LPL>
+__global__ void __launch_bounds__(256, 2)
+k_poisson_zl(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
+             const T *__restrict__ lamy, const unsigned char *__restrict__ exact, T scale,
+             int n_exact, const int *modes, const double *xa, const double *xm,
+             const double *xc, const double *xz, const double *xs, double dscale, int compat,
+             double zlen) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if ((int)blockIdx.x < n_exact) {
+        if (threadIdx.x < 32)
+            exact_mode_solve<T>(g, spec, blockIdx.x, modes, xa, xm, xc, xz, xs, dscale, compat,
+                                zlen, reinterpret_cast<cplx<double> *>(smraw), threadIdx.x);
+        return;
+    }
+    constexpr int NL = 256 / LPL;                                // lines per block
+    constexpr int SLOTS = 128 / (2 * (int)sizeof(T));            // values per 128 bytes
+    constexpr int GR = SLOTS > NL ? SLOTS / NL : 1;              // tile rows per group
+    constexpr int GW = GR * NL;
+    static_assert(E % GR == 0 && E >= 4, "chunk rows");
+    const int nz = g.nz, ny = g.ny, sk = g.sk;
+    cplx<T> *S = reinterpret_cast<cplx<T> *>(smraw);
+    ZCoef<T> *C = reinterpret_cast<ZCoef<T> *>(S + (size_t)nz * NL);
+    // tile position of value (z, line w): groups of GR rows, the values of a
+    // group permuted by the lane index z / E of the reading lane
+    auto pos = [](int z, int w) {
+        return (z / GR) * GW + (((z % GR) * NL + w) ^ ((z / E) & (GW - 1)));
+    };
+    const int bl = blockIdx.x - n_exact;
+    const int nkt = sk / NL;
+    const int ky = bl / nkt, x0 = (bl - ky * nkt) * NL;
+    const size_t plane = (size_t)ny * sk;
+    const int t = threadIdx.x;
+    cplx<T> *col = spec + (size_t)ky * sk + x0;
+    for (int e = t; e < nz * NL; e += 256) {
+        const int z = e / NL, w = e - z * NL;
+        if (sizeof(T) == 4) cp_async8(S + pos(z, w), col + (size_t)z * plane + w);
+        else cp_async16(S + pos(z, w), col + (size_t)z * plane + w);
+    }
+    {
+        const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
+        for (int k = t; k < nz; k += 256) {
+            const T a = (g.walls && k == 0) ? T(0) : ihc[k] * idz[k];
+            const T c = (g.walls && k == nz - 1) ? T(0) : ihc[k + 1] * idz[k];
+            ZCoef<T> zc;
+            zc.a = a;
+            zc.c = c;
+            zc.b0 = -(a + c);
+            zc.pad = T(0);
+            C[k + k / E] = zc;
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int lane = t & 31;
+    const int r = lane & (LPL - 1);
+    const int w = (t >> 5) * (32 / LPL) + lane / LPL;
+    T lam = lamx[x0 + w] + lamy[ky];
+    // the singular (0, 0) mode is solved in double; keep this (discarded)
+    // copy of its system regular
+    if (x0 + w == 0 && ky == 0) lam = T(1);
+    const int s0 = r * E;
+    const ZCoef<T> *cr = C + s0 + r;       // row s0 + i at cr[i]
+    cplx<T> d[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) d[i] = S[pos(s0 + i, w)];
+    // chunk interior: x_i = d~_i - a~_i x_s0 - c~_i x_{i+1}
+    T at[E], ct[E];
+    {
+        const ZCoef<T> q = cr[1];
+        const T inv = rcp(q.b0 - lam);
+        at[1] = q.a * inv;
+        ct[1] = q.c * inv;
+        d[1] = cplx<T>{d[1].re * inv, d[1].im * inv};
+    }
+#pragma unroll
+    for (int i = 2; i < E - 1; ++i) {
+        const ZCoef<T> q = cr[i];
+        const T inv = rcp((q.b0 - lam) - q.a * ct[i - 1]);
+        at[i] = -q.a * at[i - 1] * inv;
+        ct[i] = q.c * inv;
+        d[i] = cplx<T>{(d[i].re - q.a * d[i - 1].re) * inv, (d[i].im - q.a * d[i - 1].im) * inv};
+    }
+    // x_{s0+1} through the chunk ends
+    cplx<T> dh = d[E - 2];
+    T ah = at[E - 2], ch = ct[E - 2];
+#pragma unroll
+    for (int i = E - 3; i >= 1; --i) {
+        dh = cplx<T>{d[i].re - ct[i] * dh.re, d[i].im - ct[i] * dh.im};
+        ah = at[i] - ct[i] * ah;
+        ch = -ct[i] * ch;
+    }
+    // reduced rows: F (row s0) and E (row s0 + E - 1); L couples to the
+    // unknown before, U to the one after in the order F_0 E_0 F_1 E_1 ...
+    T Lf, Df, Uf, Le, De, Ue;
+    cplx<T> Rf, Re;
+    {
+        const ZCoef<T> q = cr[0];
+        Lf = q.a;
+        Df = (q.b0 - lam) - q.c * ah;
+        Uf = -q.c * ch;
+        Rf = cplx<T>{d[0].re - q.c * dh.re, d[0].im - q.c * dh.im};
+        const ZCoef<T> u = cr[E - 1];
+        Le = -u.a * at[E - 2];
+        De = (u.b0 - lam) - u.a * ct[E - 2];
+        Ue = u.c;
+        Re = cplx<T>{d[E - 1].re - u.a * d[E - 2].re, d[E - 1].im - u.a * d[E - 2].im};
+    }
+    // parallel cyclic reduction; stride 1 couples F_r with E_{r-1} and E_r,
+    // E_r with F_r and F_{r+1}
+    {
+        const int rm = (r - 1) & (LPL - 1), rp = (r + 1) & (LPL - 1);
+        const T pLe = __shfl_sync(0xffffffffu, Le, rm, LPL);
+        const T pDe = __shfl_sync(0xffffffffu, De, rm, LPL);
+        const T pUe = __shfl_sync(0xffffffffu, Ue, rm, LPL);
+        const T pRer = __shfl_sync(0xffffffffu, Re.re, rm, LPL);
+        const T pRei = __shfl_sync(0xffffffffu, Re.im, rm, LPL);
+        const T nLf = __shfl_sync(0xffffffffu, Lf, rp, LPL);
+        const T nDf = __shfl_sync(0xffffffffu, Df, rp, LPL);
+        const T nUf = __shfl_sync(0xffffffffu, Uf, rp, LPL);
+        const T nRfr = __shfl_sync(0xffffffffu, Rf.re, rp, LPL);
+        const T nRfi = __shfl_sync(0xffffffffu, Rf.im, rp, LPL);
+        const T f1 = -Lf * rcp(pDe), f2 = -Uf * rcp(De);
+        const T e1 = -Le * rcp(Df), e2 = -Ue * rcp(nDf);
+        const T Lf2 = f1 * pLe, Uf2 = f2 * Ue, Df2 = Df + f1 * pUe + f2 * Le;
+        const cplx<T> Rf2{Rf.re + f1 * pRer + f2 * Re.re, Rf.im + f1 * pRei + f2 * Re.im};
+        const T Le2 = e1 * Lf, Ue2 = e2 * nUf, De2 = De + e1 * Uf + e2 * nLf;
+        const cplx<T> Re2{Re.re + e1 * Rf.re + e2 * nRfr, Re.im + e1 * Rf.im + e2 * nRfi};
+        Lf = Lf2; Uf = Uf2; Df = Df2; Rf = Rf2;
+        Le = Le2; Ue = Ue2; De = De2; Re = Re2;
+    }
+    // strides 2, 4, .., 2 LPL / 2: unknowns of the same kind, lanes r -/+ q
+#pragma unroll
+    for (int q = 1; q < LPL; q <<= 1) {
+        const int rm = (r - q) & (LPL - 1), rp = (r + q) & (LPL - 1);
+        T *Ls[2] = {&Lf, &Le}, *Ds[2] = {&Df, &De}, *Us[2] = {&Uf, &Ue};
+        cplx<T> *Rs[2] = {&Rf, &Re};
+#pragma unroll
+        for (int kind = 0; kind < 2; ++kind) {
+            T &L = *Ls[kind], &D = *Ds[kind], &U = *Us[kind];
+            cplx<T> &R = *Rs[kind];
+            const T mL = __shfl_sync(0xffffffffu, L, rm, LPL);
+            const T mD = __shfl_sync(0xffffffffu, D, rm, LPL);
+            const T mU = __shfl_sync(0xffffffffu, U, rm, LPL);
+            const T mRr = __shfl_sync(0xffffffffu, R.re, rm, LPL);
+            const T mRi = __shfl_sync(0xffffffffu, R.im, rm, LPL);
+            const T pL = __shfl_sync(0xffffffffu, L, rp, LPL);
+            const T pD = __shfl_sync(0xffffffffu, D, rp, LPL);
+            const T pU = __shfl_sync(0xffffffffu, U, rp, LPL);
+            const T pRr = __shfl_sync(0xffffffffu, R.re, rp, LPL);
+            const T pRi = __shfl_sync(0xffffffffu, R.im, rp, LPL);
+            const T k1 = -L * rcp(mD), k2 = -U * rcp(pD);
+            const T D2 = D + k1 * mU + k2 * pL;
+            R = cplx<T>{R.re + k1 * mRr + k2 * pRr, R.im + k1 * mRi + k2 * pRi};
+            L = k1 * mL;
+            U = k2 * pU;
+            D = D2;
+        }
+    }
+    // every equation now couples only to itself (cyclic) or to nothing
+    const T fi = rcp(Df + Lf + Uf), ei = rcp(De + Le + Ue);
+    const cplx<T> xF{Rf.re * fi, Rf.im * fi}, xE{Re.re * ei, Re.im * ei};
+    d[0] = xF;
+    d[E - 1] = xE;
+    {
+        cplx<T> x = xE;
+#pragma unroll
+        for (int i = E - 2; i >= 1; --i) {
+            x = cplx<T>{d[i].re - at[i] * xF.re - ct[i] * x.re,
+                        d[i].im - at[i] * xF.im - ct[i] * x.im};
+            d[i] = x;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i) S[pos(s0 + i, w)] = d[i];
+    __syncthreads();
+    const unsigned char *ex = exact + (size_t)ky * sk + x0;
+    for (int e = t; e < nz * NL; e += 256) {
+        const int z = e / NL, w2 = e - z * NL;
+        if (!ex[w2]) col[(size_t)z * plane + w2] = scale * S[pos(z, w2)];
+    }
+}
+
 size_t smem_exact(int nz, int P) {
     const size_t rs = 2 * P + 1;
     return sizeof(cplx<double>) * (nz + rs) + sizeof(double) * (2 * (size_t)nz + 3 * rs);
@@ -524,6 +735,21 @@ template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W) {
     for (int r = tsz == 8 ? 4 : 8; r >= 1; r /= 2)
         if (g.ny % r == 0) { W.ry_fft = r; break; }
     while (W.ry_fft > 1 && smem_fft_x<T>(g, W) > lim) W.ry_fft /= 2;
+    // lane-resident z solve: the first instantiated (lanes per line, rows per
+    // lane) with nz = LPL E; in double at most 8 rows per lane (registers)
+    W.zl_lpl = W.zl_e = 0;
+    {
+        static const int cand[][2] = {{16, 4}, {16, 6}, {16, 8}, {32, 8}, {16, 12},
+                                      {16, 16}, {16, 24}, {32, 16}, {32, 24}};
+        for (const auto &c : cand) {
+            if (tsz == 8 && c[1] > 8) continue;
+            if (g.nz == c[0] * c[1] && g.sk % (256 / c[0]) == 0) {
+                W.zl_lpl = c[0];
+                W.zl_e = c[1];
+                break;
+            }
+        }
+    }
     W.tkx = 128 / (2 * tsz);
     for (;;) {
         W.pz_poisson = 256 / W.tkx;
@@ -571,6 +797,28 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
     const int blocks = g.ny * (g.sk / W.tkx);
     const int threads = ((W.tkx * W.pz_poisson + 31) / 32) * 32;
     const double scale = 1.0 / ((double)g.nx * g.ny);
+    if (W.xa && W.zl_lpl) {
+        // one launch: the exactly solved modes in its first blocks
+        const int nl = 256 / W.zl_lpl;
+        const size_t sm1 = sizeof(cplx<T>) * (size_t)g.nz * nl +
+                           sizeof(ZCoef<T>) * (size_t)(g.nz + g.nz / W.zl_e);
+        const size_t sm2 = sizeof(cplx<double>) * (size_t)g.nz;
+        const size_t sm = sm1 > sm2 ? sm1 : sm2;
+        const int grid = W.n_nzm + g.ny * (g.sk / nl);
+        const T tsc = T(scale);
+#define FSEI_ZL(E_, L_)                                                                        \
+    if (W.zl_e == E_ && W.zl_lpl == L_) {                                                      \
+        k_poisson_zl<T, E_, L_><<<grid, 256, sm, st>>>(g, W.spec, W.lamx, W.lamy, W.exact, tsc, \
+                                                       W.n_nzm, W.nzm, W.xa, W.xm, W.xc, W.xz,  \
+                                                       W.xs, scale, compat, W.zlen);            \
+        return;                                                                                \
+    }
+        FSEI_ZL(4, 16) FSEI_ZL(6, 16) FSEI_ZL(8, 16) FSEI_ZL(8, 32)
+        if constexpr (sizeof(T) == 4) {
+            FSEI_ZL(12, 16) FSEI_ZL(16, 16) FSEI_ZL(24, 16) FSEI_ZL(16, 32) FSEI_ZL(24, 32)
+        }
+#undef FSEI_ZL
+    }
     // exact modes first: they read the untouched right-hand side, and
     // k_poisson_z leaves them alone
     if (W.xa) {
@@ -620,6 +868,17 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     raise_smem_limit(k_poisson_z<T>);
     raise_smem_limit(k_poisson_exact<T>);
     raise_smem_limit(k_poisson_exact_f<T>);
+    raise_smem_limit(k_poisson_zl<T, 4, 16>);
+    raise_smem_limit(k_poisson_zl<T, 6, 16>);
+    raise_smem_limit(k_poisson_zl<T, 8, 16>);
+    raise_smem_limit(k_poisson_zl<T, 8, 32>);
+    if constexpr (sizeof(T) == 4) {
+        raise_smem_limit(k_poisson_zl<T, 12, 16>);
+        raise_smem_limit(k_poisson_zl<T, 16, 16>);
+        raise_smem_limit(k_poisson_zl<T, 24, 16>);
+        raise_smem_limit(k_poisson_zl<T, 16, 32>);
+        raise_smem_limit(k_poisson_zl<T, 24, 32>);
+    }
 }
 
 #define FSEI_INST(T)                                                                           \

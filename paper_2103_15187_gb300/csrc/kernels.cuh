@@ -44,6 +44,8 @@ template <typename T> struct Work {
     int px, chunk_x;         // chunks per x line and their length (x solves)
     int tkx;                 // kx columns per block of the y FFT / z Poisson
     int pz_poisson;          // chunks per z line in the Poisson solve
+    int zl_lpl, zl_e;        // lane-resident z solve: lanes per mode line and
+                             // rows per lane (0: not used)
 };
 
 struct StepArgs {
