@@ -80,6 +80,34 @@ k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
         const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
         const T idzk = Metric<T>::idz(g)[k];
         const int oc0 = (k * ny + j0) * nx, ou0 = (ku * ny + j0) * nx;
+        constexpr int VW = 16 / (int)sizeof(T);
+        struct alignas(16) V { T v[VW]; };
+        if (nx % VW == 0) {
+            // 16-byte vectors: VW consecutive cells of a row per item, the
+            // u neighbour beyond the vector as a scalar
+            const int nv = nx / VW;
+            for (int e = threadIdx.x; e < RY * nv; e += blockDim.x) {
+                const int r = ddiv(e, nv), i0 = (e - r * nv) * VW;
+                const int o = oc0 + r * nx;
+                const int ojp = (j0 + r == ny - 1) ? (k * ny) * nx : o + nx;
+                const V a0 = *reinterpret_cast<const V *>(q0 + o + i0);
+                const V a1 = *reinterpret_cast<const V *>(q1 + o + i0);
+                const V a1p = *reinterpret_cast<const V *>(q1 + ojp + i0);
+                const V a2 = *reinterpret_cast<const V *>(q2 + o + i0);
+                V a2u;
+                if (hasup) a2u = *reinterpret_cast<const V *>(q2 + ou0 + r * nx + i0);
+                const T a0n = q0[o + (i0 + VW == nx ? 0 : i0 + VW)];
+                V dv;
+#pragma unroll
+                for (int c = 0; c < VW; ++c) {
+                    const T up = c == VW - 1 ? a0n : a0.v[c + 1];
+                    const T wu = hasup ? a2u.v[c] : T(0);
+                    dv.v[c] = ((up - a0.v[c]) * idx + (a1p.v[c] - a1.v[c]) * idy +
+                               (wu - a2.v[c]) * idzk) * invdt;
+                }
+                *reinterpret_cast<V *>(reinterpret_cast<T *>(A + (size_t)r * ls) + i0) = dv;
+            }
+        } else
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const int ip = i == nx - 1 ? 0 : i + 1;
             T a0[RY], a0p[RY], a1[RY], a1p[RY], a2[RY], a2u[RY];
@@ -732,7 +760,7 @@ template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W) {
     const size_t lim = (size_t)smem_optin() - 2048;
     const int tsz = (int)sizeof(T);
     W.ry_fft = 1;
-    for (int r = tsz == 8 ? 4 : 8; r >= 1; r /= 2)
+    for (int r = tsz == 8 ? 4 : 16; r >= 1; r /= 2)
         if (g.ny % r == 0) { W.ry_fft = r; break; }
     while (W.ry_fft > 1 && smem_fft_x<T>(g, W) > lim) W.ry_fft /= 2;
     // lane-resident z solve: the first instantiated (lanes per line, rows per
@@ -771,6 +799,7 @@ template <typename T, int MODE>
 void rfft_x_mode(const GridDev &g, Work<T> &W, const StepScalars *sc, const T *src,
                  cudaStream_t st) {
     switch (W.ry_fft) {
+    case 16: rfft_x_ry<T, MODE, 16>(g, W, sc, src, st); break;
     case 8: rfft_x_ry<T, MODE, 8>(g, W, sc, src, st); break;
     case 4: rfft_x_ry<T, MODE, 4>(g, W, sc, src, st); break;
     case 2: rfft_x_ry<T, MODE, 2>(g, W, sc, src, st); break;
@@ -842,6 +871,7 @@ void irfft_x_ry(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
 
 template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
     switch (W.ry_fft) {
+    case 16: irfft_x_ry<T, 16>(g, W, dst, st); break;
     case 8: irfft_x_ry<T, 8>(g, W, dst, st); break;
     case 4: irfft_x_ry<T, 4>(g, W, dst, st); break;
     case 2: irfft_x_ry<T, 2>(g, W, dst, st); break;
@@ -855,6 +885,9 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     raise_smem_limit(k_rfft_x<T, 0, 2>);
     raise_smem_limit(k_rfft_x<T, 0, 4>);
     raise_smem_limit(k_rfft_x<T, 0, 8>);
+    raise_smem_limit(k_rfft_x<T, 0, 16>);
+    raise_smem_limit(k_rfft_x<T, 1, 16>);
+    raise_smem_limit(k_irfft_x<T, 16>);
     raise_smem_limit(k_rfft_x<T, 1, 1>);
     raise_smem_limit(k_rfft_x<T, 1, 2>);
     raise_smem_limit(k_rfft_x<T, 1, 4>);

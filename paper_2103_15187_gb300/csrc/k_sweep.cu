@@ -675,6 +675,171 @@ FSEI_D T xnb(T mine, const T *row, int i0, int nx, int CPL) {
     return v;
 }
 
+// The rows one x row (j, k) of the right-hand side reads: each pointer is
+// the start of a row of nx values (in global or shared memory); rows of a
+// plane beyond a wall are NULL.  Names: U = u(j, k), Ujm = u(j-1, k), Uu =
+// u(j, k+1), Ud = u(j, k-1), Vdjp = v(j+1, k-1), Wujm = w(j-1, k+1), H1u
+// = H_u^{n-1}(j, k), and so on.
+template <typename T> struct RowSet {
+    const T *U, *Ujm, *Ujp, *Uu, *Ud;
+    const T *V, *Vjm, *Vjp, *Vu, *Vd, *Vdjp;
+    const T *W, *Wjm, *Wjp, *Wu, *Wujm, *Wd;
+    const T *P, *Pjm, *Pd;
+    const T *H1u, *H1v, *H1w;
+};
+
+// H^n and the right-hand side of one x row at the lane's CPL cells (i0 ..),
+// H^n stored to F.hu/hv/hw, then (I - beta L_x) q = RHS solved on the
+// registers (line_solve_uni) and q stored to q0, q1, q2 (oc: offset of the
+// row in the fields).  The products of two two-point averages are formed
+// without their factors 1/2; the 1/4 is folded into the difference
+// coefficients (scaling by powers of two is exact, so the values are those
+// of rhs_point).  Edge products shared by two cells of a lane are formed
+// once.  Every thread of the block calls it (line solves wider than a warp
+// synchronise the block).
+template <typename T, int CPL, int LPR>
+FSEI_D void rhs_row_body(const GridDev &g, const Fields<T> &F, const RowSet<T> &rs,
+                         T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
+                         const StepScalars *sc, const RhsCoef<T> &cf, int oc, int i0, T *xs) {
+    const int nx = g.nx;
+    const bool hasdn = cf.hasdn, hasup = cf.hasup;
+    const T z0 = T(0), two = T(2);
+    const T qidx = T(0.25) * cf.idx, qidy = T(0.25) * cf.idy, qidz = T(0.25) * cf.idzk,
+            qihc = T(0.25) * cf.ihck;
+    T U[CPL], Ujm[CPL], Ujp[CPL], Uu[CPL], Ud[CPL];
+    T V[CPL], Vjm[CPL], Vjp[CPL], Vu[CPL], Vd[CPL], Vdjp[CPL];
+    T W[CPL], Wjm[CPL], Wjp[CPL], Wu[CPL], Wujm[CPL], Wd[CPL];
+    T P[CPL], Pjm[CPL], Pd[CPL];
+    ldrow(U, rs.U + i0); ldrow(Ujm, rs.Ujm + i0); ldrow(Ujp, rs.Ujp + i0);
+    ldrow(V, rs.V + i0); ldrow(Vjm, rs.Vjm + i0); ldrow(Vjp, rs.Vjp + i0);
+    ldrow(W, rs.W + i0); ldrow(Wjm, rs.Wjm + i0); ldrow(Wjp, rs.Wjp + i0);
+    ldrow(P, rs.P + i0); ldrow(Pjm, rs.Pjm + i0);
+    if (hasup) {
+        ldrow(Uu, rs.Uu + i0); ldrow(Vu, rs.Vu + i0);
+        ldrow(Wu, rs.Wu + i0); ldrow(Wujm, rs.Wujm + i0);
+    } else {
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) Uu[e] = Vu[e] = Wu[e] = Wujm[e] = z0;
+    }
+    if (hasdn) {
+        ldrow(Ud, rs.Ud + i0); ldrow(Vd, rs.Vd + i0); ldrow(Vdjp, rs.Vdjp + i0);
+        ldrow(Wd, rs.Wd + i0); ldrow(Pd, rs.Pd + i0);
+    } else {
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) Ud[e] = Vd[e] = Vdjp[e] = Wd[e] = Pd[e] = z0;
+    }
+    // x neighbours outside the lane's cells
+    const T Ul = xnb<T, LPR, 1>(U[CPL - 1], rs.U, i0, nx, CPL);
+    const T Ur = xnb<T, LPR, 0>(U[0], rs.U, i0, nx, CPL);
+    const T Ujmr = xnb<T, LPR, 0>(Ujm[0], rs.Ujm, i0, nx, CPL);
+    const T Udr = hasdn ? xnb<T, LPR, 0>(Ud[0], rs.Ud, i0, nx, CPL) : z0;
+    const T Vl = xnb<T, LPR, 1>(V[CPL - 1], rs.V, i0, nx, CPL);
+    const T Vr = xnb<T, LPR, 0>(V[0], rs.V, i0, nx, CPL);
+    const T Vjpl = xnb<T, LPR, 1>(Vjp[CPL - 1], rs.Vjp, i0, nx, CPL);
+    const T Wl = xnb<T, LPR, 1>(W[CPL - 1], rs.W, i0, nx, CPL);
+    const T Wr = xnb<T, LPR, 0>(W[0], rs.W, i0, nx, CPL);
+    const T Wul = hasup ? xnb<T, LPR, 1>(Wu[CPL - 1], rs.Wu, i0, nx, CPL) : z0;
+    const T Pl = xnb<T, LPR, 1>(P[CPL - 1], rs.P, i0, nx, CPL);
+    // at the CPL + 1 x faces / edges i0 .. i0+CPL of the lane: (u_{i-1} +
+    // u_i)^2 and the products behind the xy and xz edge fluxes
+    T usq[CPL + 1], pxy[CPL + 1], pxz[CPL + 1];
+#pragma unroll
+    for (int e = 0; e <= CPL; ++e) {
+        const T um = e == 0 ? Ul : U[e - 1], u0 = e == CPL ? Ur : U[e];
+        const T vm = e == 0 ? Vl : V[e - 1], v0 = e == CPL ? Vr : V[e];
+        const T wm = e == 0 ? Wl : W[e - 1], w0 = e == CPL ? Wr : W[e];
+        const T ujm = e == CPL ? Ujmr : Ujm[e], ud = e == CPL ? Udr : Ud[e];
+        const T us = um + u0;
+        usq[e] = us * us;
+        pxy[e] = (v0 + vm) * (u0 + ujm);
+        pxz[e] = hasdn ? (w0 + wm) * (u0 + ud) : z0;
+    }
+    T R[3][CPL];
+    T Hn[3][CPL];
+    const T *fx = F.fx ? F.fx + oc : nullptr, *fy = F.fy ? F.fy + oc : nullptr;
+    const T *fz = (F.fz && !cf.wall_face) ? F.fz + oc : nullptr;
+    {
+        T H1[CPL], f[CPL];
+        ldrow(H1, rs.H1u + i0);
+        if (fx) ldrow(f, fx + i0);
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+            const T uim = e == 0 ? Ul : U[e - 1], uip = e == CPL - 1 ? Ur : U[e + 1];
+            const T vjpim = e == 0 ? Vjpl : Vjp[e - 1];
+            const T wuim = e == 0 ? Wul : Wu[e - 1];
+            const T pxy_jp = (Vjp[e] + vjpim) * (Ujp[e] + U[e]);
+            const T pxz_kp = hasup ? (Wu[e] + wuim) * (Uu[e] + U[e]) : z0;
+            const T Hu = -((usq[e + 1] - usq[e]) * qidx + (pxy_jp - pxy[e]) * qidy +
+                           (pxz_kp - pxz[e]) * qidz);
+            const T Lu = (uip - two * U[e] + uim) * cf.idx2 +
+                         (Ujp[e] - two * U[e] + Ujm[e]) * cf.idy2 +
+                         ((Uu[e] - U[e]) * cf.ihcu - (U[e] - Ud[e]) * cf.ihck) * cf.idzk;
+            const T pim = e == 0 ? Pl : P[e - 1];
+            Hn[0][e] = Hu;
+            R[0][e] = cf.dt * (cf.gam * Hu + cf.rho * H1[e] + cf.inv_re * Lu -
+                               (P[e] - pim) * cf.idx + (fx ? f[e] : z0) + cf.fc0);
+        }
+    }
+    {
+        T H1[CPL], f[CPL];
+        ldrow(H1, rs.H1v + i0);
+        if (fy) ldrow(f, fy + i0);
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+            const T vim = e == 0 ? Vl : V[e - 1], vip = e == CPL - 1 ? Vr : V[e + 1];
+            const T pyz = hasdn ? (W[e] + Wjm[e]) * (V[e] + Vd[e]) : z0;
+            const T pyz_kp = hasup ? (Wu[e] + Wujm[e]) * (Vu[e] + V[e]) : z0;
+            const T sp = V[e] + Vjp[e], sm = Vjm[e] + V[e];
+            const T Hv = -((pxy[e + 1] - pxy[e]) * qidx + (sp * sp - sm * sm) * qidy +
+                           (pyz_kp - pyz) * qidz);
+            const T Lv = (vip - two * V[e] + vim) * cf.idx2 +
+                         (Vjp[e] - two * V[e] + Vjm[e]) * cf.idy2 +
+                         ((Vu[e] - V[e]) * cf.ihcu - (V[e] - Vd[e]) * cf.ihck) * cf.idzk;
+            Hn[1][e] = Hv;
+            R[1][e] = cf.dt * (cf.gam * Hv + cf.rho * H1[e] + cf.inv_re * Lv -
+                               (P[e] - Pjm[e]) * cf.idy + (fy ? f[e] : z0) + cf.fc1);
+        }
+    }
+    {
+        T H1[CPL], f[CPL];
+        ldrow(H1, rs.H1w + i0);
+        if (fz) ldrow(f, fz + i0);
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+            T Hw = z0, rw = z0;
+            if (!cf.wall_face) {
+                const T wim = e == 0 ? Wl : W[e - 1], wip = e == CPL - 1 ? Wr : W[e + 1];
+                const T pyz = hasdn ? (W[e] + Wjm[e]) * (V[e] + Vd[e]) : z0;
+                const T pyz_jp = hasdn ? (Wjp[e] + W[e]) * (Vjp[e] + Vdjp[e]) : z0;
+                const T sp = W[e] + Wu[e], sm = Wd[e] + W[e];
+                Hw = -((pxz[e + 1] - pxz[e]) * qidx + (pyz_jp - pyz) * qidy +
+                       (sp * sp - sm * sm) * qihc);
+                const T Lw = (wip - two * W[e] + wim) * cf.idx2 +
+                             (Wjp[e] - two * W[e] + Wjm[e]) * cf.idy2 +
+                             ((Wu[e] - W[e]) * cf.idzk - (W[e] - Wd[e]) * cf.idzd) * cf.ihck;
+                rw = cf.dt * (cf.gam * Hw + cf.rho * H1[e] + cf.inv_re * Lw -
+                              (P[e] - Pd[e]) * cf.ihck + (fz ? f[e] : z0) + cf.fc2);
+            }
+            Hn[2][e] = Hw;
+            R[2][e] = rw;
+        }
+    }
+    // every load above precedes the first store (the row pointers may alias
+    // the outputs as far as the compiler knows)
+    strow(F.hu + oc + i0, Hn[0]);
+    strow(F.hv + oc + i0, Hn[1]);
+    strow(F.hw + oc + i0, Hn[2]);
+    line_solve_uni<T, CPL, LPR, 3>(R, fpick<T>(sc->ax, sc->fax), fpick<T>(sc->cix, sc->fcix), xs);
+    strow(q0 + oc + i0, R[0]);
+    strow(q1 + oc + i0, R[1]);
+    strow(q2 + oc + i0, R[2]);
+}
+
+// Row-resident right-hand side + x sweep reading its stencil rows straight
+// from global memory: the LPR lanes of a warp segment (or of LPR / 32
+// warps) own one x row (j, k), lane r cells CPL r .. CPL r + CPL - 1, read
+// as 16-byte vectors (neighbour rows are served by the caches).  Needs nx =
+// LPR CPL, CPL a multiple of the 16-byte vector, ny a multiple of rpb.
 template <typename T, int CPL, int LPR>
 __global__ void __launch_bounds__(LPR > 128 ? LPR : 128)
 k_rhs_x_row(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
@@ -684,153 +849,22 @@ k_rhs_x_row(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     const int nby = ny / rpb;
     const int k = blockIdx.x / nby;
     const int j = (blockIdx.x % nby) * rpb + (int)threadIdx.x / LPR;
-    const int lr = (int)threadIdx.x & (LPR - 1);
-    const int i0 = lr * CPL;
+    const int i0 = ((int)threadIdx.x & (LPR - 1)) * CPL;
     const RhsCoef<T> cf = rhs_coef<T>(g, sc, k, fc0, fc1, fc2, inv_re);
-    const bool hasdn = cf.hasdn, hasup = cf.hasup;
     const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
     const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
-    const int oc = (k * ny + j) * nx, ojm = (k * ny + jm) * nx, ojp = (k * ny + jp) * nx,
-              oku = (ku * ny + j) * nx, okd = (kd * ny + j) * nx, ojmku = (ku * ny + jm) * nx,
-              ojpkd = (kd * ny + jp) * nx;
-    const T h = T(0.5), z0 = T(0);
-    // stencil rows (cells i0 .. i0+CPL-1); planes beyond a wall are 0
-    T U[CPL], Ujm[CPL], Ujp[CPL], Uu[CPL], Ud[CPL];
-    T V[CPL], Vjm[CPL], Vjp[CPL], Vu[CPL], Vd[CPL], Vdjp[CPL];
-    T W[CPL], Wjm[CPL], Wjp[CPL], Wu[CPL], Wujm[CPL], Wd[CPL];
-    T P[CPL], Pjm[CPL], Pd[CPL];
-    ldrow(U, F.u + oc + i0); ldrow(Ujm, F.u + ojm + i0); ldrow(Ujp, F.u + ojp + i0);
-    ldrow(V, F.v + oc + i0); ldrow(Vjm, F.v + ojm + i0); ldrow(Vjp, F.v + ojp + i0);
-    ldrow(W, F.w + oc + i0); ldrow(Wjm, F.w + ojm + i0); ldrow(Wjp, F.w + ojp + i0);
-    ldrow(P, F.p + oc + i0); ldrow(Pjm, F.p + ojm + i0);
-    if (hasup) {
-        ldrow(Uu, F.u + oku + i0); ldrow(Vu, F.v + oku + i0);
-        ldrow(Wu, F.w + oku + i0); ldrow(Wujm, F.w + ojmku + i0);
-    } else {
-#pragma unroll
-        for (int e = 0; e < CPL; ++e) Uu[e] = Vu[e] = Wu[e] = Wujm[e] = z0;
-    }
-    if (hasdn) {
-        ldrow(Ud, F.u + okd + i0); ldrow(Vd, F.v + okd + i0); ldrow(Vdjp, F.v + ojpkd + i0);
-        ldrow(Wd, F.w + okd + i0); ldrow(Pd, F.p + okd + i0);
-    } else {
-#pragma unroll
-        for (int e = 0; e < CPL; ++e) Ud[e] = Vd[e] = Vdjp[e] = Wd[e] = Pd[e] = z0;
-    }
-    // x neighbours outside the lane's cells
-    const T Ul = xnb<T, LPR, 1>(U[CPL - 1], F.u + oc, i0, nx, CPL);
-    const T Ur = xnb<T, LPR, 0>(U[0], F.u + oc, i0, nx, CPL);
-    const T Ujmr = xnb<T, LPR, 0>(Ujm[0], F.u + ojm, i0, nx, CPL);
-    const T Udr = hasdn ? xnb<T, LPR, 0>(Ud[0], F.u + okd, i0, nx, CPL) : z0;
-    const T Vl = xnb<T, LPR, 1>(V[CPL - 1], F.v + oc, i0, nx, CPL);
-    const T Vr = xnb<T, LPR, 0>(V[0], F.v + oc, i0, nx, CPL);
-    const T Vjpl = xnb<T, LPR, 1>(Vjp[CPL - 1], F.v + ojp, i0, nx, CPL);
-    const T Wl = xnb<T, LPR, 1>(W[CPL - 1], F.w + oc, i0, nx, CPL);
-    const T Wr = xnb<T, LPR, 0>(W[0], F.w + oc, i0, nx, CPL);
-    const T Wul = hasup ? xnb<T, LPR, 1>(Wu[CPL - 1], F.w + oku, i0, nx, CPL) : z0;
-    const T Pl = xnb<T, LPR, 1>(P[CPL - 1], F.p + oc, i0, nx, CPL);
-    // quantities at the CPL + 1 x faces / edges i0 .. i0+CPL of the lane
-    T ucc[CPL + 1], exy[CPL + 1], exz[CPL + 1];
-#pragma unroll
-    for (int e = 0; e <= CPL; ++e) {
-        const T um = e == 0 ? Ul : U[e - 1], u0 = e == CPL ? Ur : U[e];
-        const T vm = e == 0 ? Vl : V[e - 1], v0 = e == CPL ? Vr : V[e];
-        const T wm = e == 0 ? Wl : W[e - 1], w0 = e == CPL ? Wr : W[e];
-        const T ujm = e == CPL ? Ujmr : Ujm[e], ud = e == CPL ? Udr : Ud[e];
-        ucc[e] = h * (um + u0);
-        exy[e] = (h * (v0 + vm)) * (h * (u0 + ujm));
-        exz[e] = hasdn ? (h * (w0 + wm)) * (h * (u0 + ud)) : z0;
-    }
-    T R[3][CPL];
-    T Hn[3][CPL];
-    {
-        T H1[CPL];
-        ldrow(H1, F.hu + oc + i0);
-        T fx[CPL];
-        if (F.fx) ldrow(fx, F.fx + oc + i0);
-        else {
-#pragma unroll
-            for (int e = 0; e < CPL; ++e) fx[e] = z0;
-        }
-#pragma unroll
-        for (int e = 0; e < CPL; ++e) {
-            const T uim = e == 0 ? Ul : U[e - 1], uip = e == CPL - 1 ? Ur : U[e + 1];
-            const T vim = e == 0 ? Vjpl : Vjp[e - 1];
-            const T wuim = e == 0 ? Wul : Wu[e - 1];
-            const T e_xy_jp = (h * (Vjp[e] + vim)) * (h * (Ujp[e] + U[e]));
-            const T e_xz_kp = hasup ? (h * (Wu[e] + wuim)) * (h * (Uu[e] + U[e])) : z0;
-            const T Hu = -((ucc[e + 1] * ucc[e + 1] - ucc[e] * ucc[e]) * cf.idx +
-                           (e_xy_jp - exy[e]) * cf.idy + (e_xz_kp - exz[e]) * cf.idzk);
-            const T Lu = (uip - T(2) * U[e] + uim) * cf.idx2 +
-                         (Ujp[e] - T(2) * U[e] + Ujm[e]) * cf.idy2 +
-                         ((Uu[e] - U[e]) * cf.ihcu - (U[e] - Ud[e]) * cf.ihck) * cf.idzk;
-            const T pim = e == 0 ? Pl : P[e - 1];
-            Hn[0][e] = Hu;
-            R[0][e] = cf.dt * (cf.gam * Hu + cf.rho * H1[e] + cf.inv_re * Lu -
-                               (P[e] - pim) * cf.idx + fx[e] + cf.fc0);
-        }
-    }
-    {
-        T H1[CPL];
-        ldrow(H1, F.hv + oc + i0);
-        T fy[CPL];
-        if (F.fy) ldrow(fy, F.fy + oc + i0);
-        else {
-#pragma unroll
-            for (int e = 0; e < CPL; ++e) fy[e] = z0;
-        }
-#pragma unroll
-        for (int e = 0; e < CPL; ++e) {
-            const T vim = e == 0 ? Vl : V[e - 1], vip = e == CPL - 1 ? Vr : V[e + 1];
-            const T e_yz = hasdn ? (h * (W[e] + Wjm[e])) * (h * (V[e] + Vd[e])) : z0;
-            const T e_yz_kp = hasup ? (h * (Wu[e] + Wujm[e])) * (h * (Vu[e] + V[e])) : z0;
-            const T vcp = h * (V[e] + Vjp[e]), vcm = h * (Vjm[e] + V[e]);
-            const T Hv = -((exy[e + 1] - exy[e]) * cf.idx + (vcp * vcp - vcm * vcm) * cf.idy +
-                           (e_yz_kp - e_yz) * cf.idzk);
-            const T Lv = (vip - T(2) * V[e] + vim) * cf.idx2 +
-                         (Vjp[e] - T(2) * V[e] + Vjm[e]) * cf.idy2 +
-                         ((Vu[e] - V[e]) * cf.ihcu - (V[e] - Vd[e]) * cf.ihck) * cf.idzk;
-            Hn[1][e] = Hv;
-            R[1][e] = cf.dt * (cf.gam * Hv + cf.rho * H1[e] + cf.inv_re * Lv -
-                               (P[e] - Pjm[e]) * cf.idy + fy[e] + cf.fc1);
-        }
-    }
-    {
-        T H1[CPL];
-        ldrow(H1, F.hw + oc + i0);
-        T fz[CPL];
-        if (F.fz && !cf.wall_face) ldrow(fz, F.fz + oc + i0);
-        else {
-#pragma unroll
-            for (int e = 0; e < CPL; ++e) fz[e] = z0;
-        }
-#pragma unroll
-        for (int e = 0; e < CPL; ++e) {
-            T Hw = z0, rw = z0;
-            if (!cf.wall_face) {
-                const T wim = e == 0 ? Wl : W[e - 1], wip = e == CPL - 1 ? Wr : W[e + 1];
-                const T e_yz = hasdn ? (h * (W[e] + Wjm[e])) * (h * (V[e] + Vd[e])) : z0;
-                const T e_yz_jp = hasdn ? (h * (Wjp[e] + W[e])) * (h * (Vjp[e] + Vdjp[e])) : z0;
-                const T wcp = h * (W[e] + Wu[e]), wcm = h * (Wd[e] + W[e]);
-                Hw = -((exz[e + 1] - exz[e]) * cf.idx + (e_yz_jp - e_yz) * cf.idy +
-                       (wcp * wcp - wcm * wcm) * cf.ihck);
-                const T Lw = (wip - T(2) * W[e] + wim) * cf.idx2 +
-                             (Wjp[e] - T(2) * W[e] + Wjm[e]) * cf.idy2 +
-                             ((Wu[e] - W[e]) * cf.idzk - (W[e] - Wd[e]) * cf.idzd) * cf.ihck;
-                rw = cf.dt * (cf.gam * Hw + cf.rho * H1[e] + cf.inv_re * Lw -
-                              (P[e] - Pd[e]) * cf.ihck + fz[e] + cf.fc2);
-            }
-            Hn[2][e] = Hw;
-            R[2][e] = rw;
-        }
-    }
-    strow(F.hu + oc + i0, Hn[0]);
-    strow(F.hv + oc + i0, Hn[1]);
-    strow(F.hw + oc + i0, Hn[2]);
-    line_solve_uni<T, CPL, LPR, 3>(R, fpick<T>(sc->ax, sc->fax), fpick<T>(sc->cix, sc->fcix), xs);
-    strow(q0 + oc + i0, R[0]);
-    strow(q1 + oc + i0, R[1]);
-    strow(q2 + oc + i0, R[2]);
+    auto row = [&](const T *f, int kk, int jj) { return f + (kk * ny + jj) * nx; };
+    RowSet<T> rs;
+    rs.U = row(F.u, k, j); rs.Ujm = row(F.u, k, jm); rs.Ujp = row(F.u, k, jp);
+    rs.V = row(F.v, k, j); rs.Vjm = row(F.v, k, jm); rs.Vjp = row(F.v, k, jp);
+    rs.W = row(F.w, k, j); rs.Wjm = row(F.w, k, jm); rs.Wjp = row(F.w, k, jp);
+    rs.P = row(F.p, k, j); rs.Pjm = row(F.p, k, jm);
+    rs.Uu = row(F.u, ku, j); rs.Vu = row(F.v, ku, j); rs.Wu = row(F.w, ku, j);
+    rs.Wujm = row(F.w, ku, jm);
+    rs.Ud = row(F.u, kd, j); rs.Vd = row(F.v, kd, j); rs.Vdjp = row(F.v, kd, jp);
+    rs.Wd = row(F.w, kd, j); rs.Pd = row(F.p, kd, j);
+    rs.H1u = row(F.hu, k, j); rs.H1v = row(F.hv, k, j); rs.H1w = row(F.hw, k, j);
+    rhs_row_body<T, CPL, LPR>(g, F, rs, q0, q1, q2, sc, cf, (k * ny + j) * nx, i0, xs);
 }
 
 }  // namespace
@@ -939,7 +973,9 @@ void rhs_tile_ry(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepSca
 // of rpb LPR >= 32 threads at most max(128, LPR)); false where it does not
 // apply.
 template <typename T> bool rhs_row_geometry(const GridDev &g, int &cpl, int &lpr, int &rpb) {
-    cpl = sizeof(T) == 4 ? 8 : 4;
+    // 4 cells per lane (2 doubles or 4 floats: fewer registers, more warps);
+    // floats on rows wider than 256 cells take 8
+    cpl = (sizeof(T) == 4 && g.nx > 256) ? 8 : 4;
     if (g.nx % cpl) return false;
     lpr = g.nx / cpl;
     if (lpr < 4 || lpr > 256 || (lpr & (lpr - 1))) return false;
@@ -976,7 +1012,8 @@ template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Wo
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
     int cpl = 0, lpr = 0, rpb = 0;
     if (rhs_row_geometry<T>(g, cpl, lpr, rpb) &&
-        rhs_row_dispatch<T, sizeof(T) == 4 ? 8 : 4>(g, F, W, sc, a, lpr, rpb, st))
+        (cpl == 4 ? rhs_row_dispatch<T, 4>(g, F, W, sc, a, lpr, rpb, st)
+                  : rhs_row_dispatch<T, sizeof(T) == 4 ? 8 : 4>(g, F, W, sc, a, lpr, rpb, st)))
         return;
     int RY = 0, P = 0;
     size_t smem = 0;
@@ -1012,6 +1049,13 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     raise_smem_limit(k_rhs_x_tile<T, 16, 2>);
     raise_smem_limit(k_rhs_x_tile<T, 32, 2>);
     raise_smem_limit(k_rhs_x_tile<T, 64, 2>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 4>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 8>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 16>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 32>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 64>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 128>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 256>);
     constexpr int C = sizeof(T) == 4 ? 8 : 4;
     cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 4>);
     cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 8>);
