@@ -257,13 +257,15 @@ template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, 
                                           StepScalars *sc, cudaStream_t st) {
     constexpr int VW = 16 / (int)sizeof(T);
     if (g.nx % VW == 0) {
-        // vector path: 256 threads, rows side by side, two passes per block
+        // vector path: 128 threads, rows side by side, about four passes per
+        // thread (the per-thread set-up and the block's reduction are then
+        // spread over more cells)
         const int tpr = g.nx / VW;
-        const int rpp = tpr >= 256 ? 1 : 256 / tpr;
+        const int rpp = tpr >= 128 ? 1 : 128 / tpr;
         int rows = 1;
-        for (int r = 2 * rpp; r >= 1; --r)
+        for (int r = 4 * rpp; r >= 1; --r)
             if (g.ny % r == 0) { rows = r; break; }
-        k_project_vec<T><<<g.nz * (g.ny / rows), 256, 0, st>>>(g, F, W.q0, W.q1, W.q2, W.phi,
+        k_project_vec<T><<<g.nz * (g.ny / rows), 128, 0, st>>>(g, F, W.q0, W.q1, W.q2, W.phi,
                                                                sc, rows);
         return;
     }
