@@ -295,7 +295,9 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     // tridiagonal plans of the z lines: 2 centres, 3 faces (entries 0 and 1
     // are unused: the x and y lines need no plan)
     int Ps[4] = {1, 1, 1, 1};
-    int ns[4] = {g.nx, g.ny, g.nz, g.walls ? g.nz - 1 : g.nz};
+    // the wall-bounded face lines (w, faces 1 .. nz-1) get one padding
+    // unknown: nz like the centre lines, so both split into equal chunks
+    int ns[4] = {g.nx, g.ny, g.nz, g.nz};
     {
         int cz, pz, tz, cf, pf, tf;
         sweep_geometry(ns[2], cz, pz, tz);
@@ -320,6 +322,7 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
         p.P = Ps[q];
         p.cyclic = (q < 2) ? 1 : (g.walls ? 0 : 1);
         p.off = (q == 3 && g.walls) ? 1 : 0;
+        p.pad = (q == 3 && g.walls) ? 1 : 0;
         p.a = s.a; p.c = s.c; p.inv = s.inv; p.at = s.at; p.ct = s.ct;
         p.rlo = s.rlo; p.rinv = s.rinv; p.rcp = s.rcp; p.rz = s.rz; p.rsc = s.rsc;
         p.pk1 = s.pk1; p.pk2 = s.pk2; p.pdinv = s.pdinv;

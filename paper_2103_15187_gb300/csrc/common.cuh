@@ -104,6 +104,9 @@ struct StepScalars {
 // step on the device (k_step_begin) into a TriPlan.
 template <typename T> struct TriPlan {
     int n, P, cyclic, off;   // off: first unknown's index in the stored line
+    int pad;                 // 1: unknown n-1 is a decoupled identity row past
+                             // the stored line (never loaded or stored), which
+                             // makes n a multiple of the chunk length
     const T *a, *c;          // sub- and super-diagonal (n)
     const T *inv;            // interior forward pivots 1/den_i (n)
     const T *at, *ct;        // interior forward factors a~_i, c~_i (n)

@@ -105,19 +105,26 @@ __device__ __forceinline__ void sweep_reg_body(const GridDev &g, const Fields<T>
     constexpr bool kPrefetch = DIR == 2 && MODE == 0 && sizeof(T) == 4;
     T un_pre[kPrefetch ? L : 1];
     // issue the chunk's loads first; staging the plan below overlaps them
+    // lastpad: the chunk ends with the plan's padding unknown (0, not stored)
+    bool lastpad = false;
+    auto keep = [&](int i) {
+        return (EXACT || i < len) && !(lastpad && i == (EXACT ? L : len) - 1);
+    };
     if (active) {
         s0 = EXACT ? p * L : chunk_start(p, src.n, src.P);
         len = EXACT ? L : chunk_start(p + 1, src.n, src.P) - s0;
+        lastpad = src.pad && s0 + (EXACT ? L : len) == src.n;
         const T *qp = q + base + (size_t)s0 * stride;
 #pragma unroll
         for (int i = 0; i < L; ++i)
-            if (EXACT || i < len) d[i] = qp[(size_t)i * stride];
+            if (keep(i)) d[i] = qp[(size_t)i * stride];
+            else d[i] = T(0);
         if constexpr (kPrefetch) {
             const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
             const T *up = un + base + (size_t)s0 * stride;
 #pragma unroll
             for (int i = 0; i < L; ++i)
-                if (EXACT || i < len) un_pre[i] = up[(size_t)i * stride];
+                if (keep(i)) un_pre[i] = up[(size_t)i * stride];
         }
     }
     const TriPlan<T> pl = stage_plan(src, red + (size_t)tx * rs);
@@ -137,23 +144,23 @@ __device__ __forceinline__ void sweep_reg_body(const GridDev &g, const Fields<T>
         if (DIR == 1) {
 #pragma unroll
             for (int i = 0; i < L; ++i)
-                if (EXACT || i < len) qp[(size_t)i * stride] = d[i];
+                if (keep(i)) qp[(size_t)i * stride] = d[i];
         } else if (MODE == 0) {
             if constexpr (kPrefetch) {
 #pragma unroll
                 for (int i = 0; i < L; ++i)
-                    if (EXACT || i < len) qp[(size_t)i * stride] = un_pre[i] + d[i];
+                    if (keep(i)) qp[(size_t)i * stride] = un_pre[i] + d[i];
             } else {
                 const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
                 const T *up = un + base + (size_t)s0 * stride;
 #pragma unroll
                 for (int i = 0; i < L; ++i)
-                    if (EXACT || i < len) qp[(size_t)i * stride] = up[(size_t)i * stride] + d[i];
+                    if (keep(i)) qp[(size_t)i * stride] = up[(size_t)i * stride] + d[i];
             }
         } else {
 #pragma unroll
             for (int i = 0; i < L; ++i)
-                if (EXACT || i < len) {
+                if (keep(i)) {
                     const int k = s0 + i + pl.off;
                     const T wk = comp < 2 ? Metric<T>::dz(g)[k] : T(1) / Metric<T>::ihc(g)[k];
                     qp[(size_t)i * stride] = wk * d[i];

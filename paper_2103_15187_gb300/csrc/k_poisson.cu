@@ -767,8 +767,10 @@ template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W) {
     // lane) with nz = LPL E; in double at most 8 rows per lane (registers)
     W.zl_lpl = W.zl_e = 0;
     {
-        static const int cand[][2] = {{16, 4}, {16, 6}, {16, 8}, {32, 8}, {16, 12},
-                                      {16, 16}, {16, 24}, {32, 16}, {32, 24}};
+        // 16 lanes per line first: fewer reduction levels, measured faster
+        // than 32 lanes of half the rows (256^3: 41 against 59 us)
+        static const int cand[][2] = {{16, 4}, {16, 6}, {16, 8}, {16, 12}, {16, 16},
+                                      {16, 24}, {32, 8}, {32, 16}, {32, 24}};
         for (const auto &c : cand) {
             if (tsz == 8 && c[1] > 8) continue;
             if (g.nz == c[0] * c[1] && g.sk % (256 / c[0]) == 0) {

@@ -110,7 +110,7 @@ __global__ void k_scalars(StepScalars *sc, StepArgs a, int euler, double idx2, d
 // a(i) x_{i-1} + b(i) x_i + c(i) x_{i+1}; a(0), c(n-1) are the periodic
 // couplings of cyclic lines and 0 otherwise.
 struct SweepCoef {
-    int kind, n, nz, walls;
+    int kind, n, nz, walls, pad;
     double beta, r;
     const double *idz, *ihc;
     FSEI_D double araw(int i) const {
@@ -126,9 +126,13 @@ struct SweepCoef {
         const int k = walls ? i + 1 : i;
         return -beta * idz[k] * ihc[k];
     }
-    FSEI_D double b(int i) const { return 1.0 - araw(i) - craw(i); }
-    FSEI_D double a(int i) const { return (kind >= 2 && walls && i == 0) ? 0.0 : araw(i); }
-    FSEI_D double c(int i) const { return (kind >= 2 && walls && i == n - 1) ? 0.0 : craw(i); }
+    // rows past `last` are the padding identity rows
+    FSEI_D int last() const { return n - 1 - pad; }
+    FSEI_D double b(int i) const { return i > last() ? 1.0 : 1.0 - araw(i) - craw(i); }
+    FSEI_D double a(int i) const {
+        return (kind >= 2 && walls && (i == 0 || i > last())) ? 0.0 : araw(i);
+    }
+    FSEI_D double c(int i) const { return (kind >= 2 && walls && i >= last()) ? 0.0 : craw(i); }
 };
 
 // one block per plan; thread p < P builds chunk p; thread 0 the reduced LU
@@ -147,6 +151,7 @@ __global__ void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
     cf.n = n;
     cf.nz = g.nz;
     cf.walls = g.walls;
+    cf.pad = pl.pad;
     cf.beta = sc->beta;
     cf.r = kind == 0 ? sc->beta * g.idx2 : sc->beta * g.idy2;
     cf.idz = g.idz;
