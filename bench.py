@@ -55,6 +55,15 @@ def algorithmic_words(nx, ny, nz, with_force):
     }
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# of the dominant kernel, from an ncu --set full capture of the 256^3
+# channel workload; reported only for that workload and that kernel build
+MEASURED_TRAFFIC = {
+    "rhs_x (RHS + x sweep)": {"bytes": 826.361e6, "cells": 256 ** 3,
+                              "kernel": "k_rhs_x_row<float, 4, 64>"},
+}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -67,7 +76,7 @@ def measured_peaks():
 
 # --------------------------------------------------------------- clocks ----
 class ClockSampler:
-    """nvidia-smi samples (every 100 ms) during the timed region."""
+    """nvidia-smi samples (every 50 ms) during the timed region."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -81,7 +90,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -357,16 +366,22 @@ def roofline_of(res, nx, ny, nz, bytes_per_word, peak_gbs, peak_kind):
         if name in words and (best is None or tot_ms > res["kernels"][best][0]):
             best = name
     e = table[best]
+    tr = MEASURED_TRAFFIC.get(best)
+    traffic = tr["bytes"] if (tr and tr["cells"] == nx * ny * nz and bytes_per_word == 4) else None
     roof = {"bound": "hbm", "kernel": best, "achieved": round(e["gbs"], 1),
             "peak": peak_gbs, "unit": "GB/s", "frac": round(e["frac"], 4),
-            "traffic": None, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+            "traffic": traffic, "alg_bytes": e["alg_bytes"],
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else peak_kind}
+    if traffic is not None:
+        roof["traffic_kernel"] = tr["kernel"]
     step_words = sum(words.values())
     return roof, table, step_words
 
 
-def cpu_oracle_sample(case, seconds_hint=30.0):
-    """One oracle step of the full workload on the host (numpy, FP64)."""
+def cpu_oracle_sample(case, steps=2):
+    """The oracle (numpy, FP64) advancing the full workload by `steps` steps
+    on the host: the first (Euler start) and then Adams-Bashforth steps."""
     from oracle.grid import Grid as OGrid
     from oracle.step import oracle_step
     g = OGrid(case.nx, case.ny, case.nz, case.lx, case.ly, case.zbc, lz=case.lz,
@@ -375,12 +390,14 @@ def cpu_oracle_sample(case, seconds_hint=30.0):
     s = {"u": case.u, "v": case.v, "w": case.w, "p": case.p, "hu": z, "hv": z, "hw": z,
          "have_prev_h": 0}
     t0 = time.perf_counter()
-    oracle_step(g, s, None, re=case.re, dt=case.dt, cfl=case.cfl, fconst=case.fconst)
+    for _ in range(steps):
+        s, _ = oracle_step(g, s, None, re=case.re, dt=case.dt, cfl=case.cfl,
+                           fconst=case.fconst)
     dt = time.perf_counter() - t0
-    return {"value": case.cells / dt / 1e6, "unit": "Mcell-updates/s", "cores": 1,
+    return {"value": case.cells * steps / dt / 1e6, "unit": "Mcell-updates/s", "cores": 1,
             "kind": "oracle",
-            "sample": "1 step of the full %dx%dx%d workload, numpy FP64, single thread "
-                      "(%.1f s)" % (case.nx, case.ny, case.nz, dt)}
+            "sample": "%d steps of the full %dx%dx%d workload, numpy FP64, single thread "
+                      "(%.1f s)" % (steps, case.nx, case.ny, case.nz, dt)}
 
 
 # ------------------------------------------------------- reference arm -----
@@ -430,7 +447,7 @@ def run_reference_arm(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fsei", choices=["fsei", "reference"])
     ap.add_argument("--error-steps", type=int, default=100)
