@@ -86,6 +86,7 @@ k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
             // 16-byte vectors: VW consecutive cells of a row per item, the
             // u neighbour beyond the vector as a scalar
             const int nv = nx / VW;
+#pragma unroll 4
             for (int e = threadIdx.x; e < RY * nv; e += blockDim.x) {
                 const int r = ddiv(e, nv), i0 = (e - r * nv) * VW;
                 const int o = oc0 + r * nx;

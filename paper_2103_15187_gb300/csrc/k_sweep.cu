@@ -68,6 +68,62 @@ k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v, const T *__
     }
 }
 
+// k_speed with 16-byte vectors: a thread owns VW = 16 / sizeof(T)
+// consecutive cells of a row (the u neighbour beyond them as a scalar),
+// tpr = nx / VW threads span a row, rpp = blockDim / tpr rows side by side;
+// needs nx % VW == 0.  Same per-cell arithmetic as k_speed.
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_speed_vec(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
+            const T *__restrict__ w, StepScalars *sc, int rows) {
+    constexpr int VW = 16 / (int)sizeof(T);
+    struct alignas(16) V { T x[VW]; };
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int tpr = nx / VW, nthr = (int)blockDim.x;
+    const int rpp = tpr >= nthr ? 1 : nthr / tpr;
+    const int xt = tpr >= nthr ? (int)threadIdx.x : (int)threadIdx.x % tpr;
+    const int r0 = tpr >= nthr ? 0 : (int)threadIdx.x / tpr;
+    const int xstride = tpr >= nthr ? nthr : tpr;
+    const int nbj = ny / rows;
+    const int k = blockIdx.x / nbj, j0 = (blockIdx.x % nbj) * rows;
+    const bool hasup = !g.walls || k < nz - 1;
+    const int ku = k == nz - 1 ? 0 : k + 1;
+    const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
+    const T idzk = Metric<T>::idz(g)[k];
+    T m = T(0);
+    for (int r = r0; r0 < rpp && r < rows; r += rpp) {
+        const int j = j0 + r, jp = j == ny - 1 ? 0 : j + 1;
+        const int oc = (k * ny + j) * nx, ojp = (k * ny + jp) * nx, oku = (ku * ny + j) * nx;
+        for (int xv = xt; xv < tpr; xv += xstride) {
+            const int i0 = xv * VW;
+            const V a = *reinterpret_cast<const V *>(u + oc + i0);
+            const V b = *reinterpret_cast<const V *>(v + oc + i0);
+            const V bp = *reinterpret_cast<const V *>(v + ojp + i0);
+            const V c = *reinterpret_cast<const V *>(w + oc + i0);
+            V cu;
+            if (hasup) cu = *reinterpret_cast<const V *>(w + oku + i0);
+            const T an = u[oc + (i0 + VW == nx ? 0 : i0 + VW)];
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const T uc = T(0.5) * (a.x[e] + (e == VW - 1 ? an : a.x[e + 1]));
+                const T vc = T(0.5) * (b.x[e] + bp.x[e]);
+                const T wku = hasup ? cu.x[e] : T(0);
+                const T wc = T(0.5) * (c.x[e] + wku);
+                m = fmax(m, fabs(uc) * idx + fabs(vc) * idy + fabs(wc) * idzk);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double wmax[32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = (double)m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0.0;
+        for (int q = 0; q < (int)((blockDim.x + 31) >> 5); ++q) mm = fmax(mm, wmax[q]);
+        atomicMax(&sc->speed_next, dbits(mm));
+    }
+}
+
 // alpha and 1/c of the cyclic Toeplitz factorisation (tri.cuh, uni_solve)
 // of (1 + 2r) I - r (E + E^-1)
 __device__ void uni_factors(double r, double &alpha, double &cinv) {
@@ -888,6 +944,17 @@ template <typename T> size_t smem_rhs_x(const GridDev &g, const Work<T> &W) {
 
 template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v, const T *w,
                                         StepScalars *sc, cudaStream_t st) {
+    constexpr int VW = 16 / (int)sizeof(T);
+    if (g.nx % VW == 0) {
+        // 128 threads, about four row passes per thread
+        const int tpr = g.nx / VW;
+        const int rpp = tpr >= 128 ? 1 : 128 / tpr;
+        int rows = 1;
+        for (int r = 4 * rpp; r >= 1; --r)
+            if (g.ny % r == 0) { rows = r; break; }
+        k_speed_vec<T><<<g.nz * (g.ny / rows), 128, 0, st>>>(g, u, v, w, sc, rows);
+        return;
+    }
     int rows = 1;
     for (int r = 8; r >= 1; r /= 2)
         if (g.ny % r == 0) { rows = r; break; }
@@ -1038,6 +1105,7 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     // launch cannot be loaded inside a stream capture
     cudaFuncAttributes fa;
     cudaFuncGetAttributes(&fa, k_speed<T>);
+    cudaFuncGetAttributes(&fa, k_speed_vec<T>);
     cudaFuncGetAttributes(&fa, k_scalars);
     cudaFuncGetAttributes(&fa, k_plans<T>);
     (void)g;
