@@ -175,6 +175,57 @@ k_fft_y(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ twy, 
     }
 }
 
+// The y transform for power-of-two ny = N1 N2 <= 256 (fft_lines_2p's split)
+// without staging tiles: pass 1 reads its N1 inputs per (line, n2) straight
+// from the spectrum into registers (coalesced across the tkx kx columns of
+// the block), applies the in-register DFT and the twiddles and writes the
+// transposed values to shared memory; pass 2 reads them back, applies the
+// second DFT and writes the result straight to the spectrum.  The block owns
+// its tile, so reading and writing in place is safe.
+template <typename T, int SIGN, int N1, int N2>
+__global__ void __launch_bounds__(256)
+k_fft_y_2p(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ twy, int tkx) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int N = N1 * N2;
+    const int sk = g.sk;
+    cplx<T> *B = reinterpret_cast<cplx<T> *>(smraw);   // [N][tkx]
+    cplx<T> *TW = B + (size_t)N * tkx;
+    const int nkt = sk / tkx;
+    const int k = blockIdx.x / nkt, x0 = (blockIdx.x % nkt) * tkx;
+    cplx<T> *base = spec + (size_t)k * N * sk + x0;
+    const int t = threadIdx.x;
+    const bool on1 = t < tkx * N2;
+    const int n2 = ddiv(t, tkx), l1 = t - n2 * tkx;
+    cplx<T> x[N1];
+    if (on1) {
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = base[(size_t)(n1 * N2 + n2) * sk + l1];
+    }
+    for (int m = t; m < N; m += blockDim.x) TW[m] = twy[m];
+    __syncthreads();
+    if (on1) {
+        dft_reg<T, N1, SIGN>(x, TW, N);
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) {
+            cplx<T> w = TW[n2 * k1];
+            if (SIGN > 0) w = conj(w);
+            x[k1] = x[k1] * w;
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) B[(n2 * N1 + k1) * tkx + l1] = x[k1];
+    }
+    __syncthreads();
+    if (t < tkx * N1) {
+        const int k1 = ddiv(t, tkx), l2 = t - k1 * tkx;
+        cplx<T> y[N2];
+#pragma unroll
+        for (int q = 0; q < N2; ++q) y[q] = B[(q * N1 + k1) * tkx + l2];
+        dft_reg<T, N2, SIGN>(y, TW, N);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) base[(size_t)(k1 + N1 * k2) * sk + l2] = y[k2];
+    }
+}
+
 // z operator of the modes in a block; a, c and -(a + c) staged in shared
 // memory (a(0) and c(nz-1) are the periodic couplings, 0 with walls)
 template <typename T> struct PoissonMat {
@@ -816,7 +867,25 @@ template <typename T> void launch_rfft_x(const GridDev &g, Work<T> &W, const Ste
     else rfft_x_mode<T, 1>(g, W, sc, src, st);
 }
 
+template <typename T, int SIGN>
+bool fft_y_2p_launch(const GridDev &g, Work<T> &W, cudaStream_t st) {
+    const int blocks = g.nz * (g.sk / W.tkx);
+    const int n1 = fft_split_n1(g.ny);
+    if (!n1 || W.tkx * n1 > 256) return false;
+    const size_t sm = sizeof(cplx<T>) * ((size_t)g.ny * W.tkx + g.ny);
+    const int thr = W.tkx * n1;
+    switch (g.ny) {
+    case 16: k_fft_y_2p<T, SIGN, 4, 4><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
+    case 32: k_fft_y_2p<T, SIGN, 8, 4><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
+    case 64: k_fft_y_2p<T, SIGN, 8, 8><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
+    case 128: k_fft_y_2p<T, SIGN, 16, 8><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
+    case 256: k_fft_y_2p<T, SIGN, 16, 16><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
+    default: return false;
+    }
+}
+
 template <typename T> void launch_fft_y(const GridDev &g, Work<T> &W, int inverse, cudaStream_t st) {
+    if (inverse ? fft_y_2p_launch<T, 1>(g, W, st) : fft_y_2p_launch<T, -1>(g, W, st)) return;
     const int blocks = g.nz * (g.sk / W.tkx);
     if (inverse)
         k_fft_y<T, 1><<<blocks, 256, smem_fft_y(g, W), st>>>(g, W.spec, W.twy, W.fpy, W.tkx);
@@ -901,6 +970,16 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     raise_smem_limit(k_irfft_x<T, 8>);
     raise_smem_limit(k_fft_y<T, 1>);
     raise_smem_limit(k_fft_y<T, -1>);
+    raise_smem_limit(k_fft_y_2p<T, 1, 4, 4>);
+    raise_smem_limit(k_fft_y_2p<T, -1, 4, 4>);
+    raise_smem_limit(k_fft_y_2p<T, 1, 8, 4>);
+    raise_smem_limit(k_fft_y_2p<T, -1, 8, 4>);
+    raise_smem_limit(k_fft_y_2p<T, 1, 8, 8>);
+    raise_smem_limit(k_fft_y_2p<T, -1, 8, 8>);
+    raise_smem_limit(k_fft_y_2p<T, 1, 16, 8>);
+    raise_smem_limit(k_fft_y_2p<T, -1, 16, 8>);
+    raise_smem_limit(k_fft_y_2p<T, 1, 16, 16>);
+    raise_smem_limit(k_fft_y_2p<T, -1, 16, 16>);
     raise_smem_limit(k_poisson_z<T>);
     raise_smem_limit(k_poisson_exact<T>);
     raise_smem_limit(k_poisson_exact_f<T>);
