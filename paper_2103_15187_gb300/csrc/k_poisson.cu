@@ -780,6 +780,77 @@ k_irfft_x(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
     }
 }
 
+// The inverse x transform for power-of-two mx = N1 N2 <= 256 without
+// staging tiles: pass 1 (item: row r, n2) loads the spectrum values X_m and
+// X_{mx-m} of its N1 indices m = N1' N2 + n2 straight from global memory,
+// forms the half-length sequence Z_m = (X_m + conj X_{mx-m}) + i conj(w^m)
+// (X_m - conj X_{mx-m}) in registers (as k_irfft_x does), applies the
+// in-register DFT and the twiddles and writes the transposed values to
+// shared memory; pass 2 (item: r, k1) applies the second DFT and stores z_m
+// as the real pair (x_2m, x_2m+1) straight to the output row.
+template <typename T, int RY, int N1, int N2>
+__global__ void __launch_bounds__(256)
+k_irfft_x_2p(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
+             const cplx<T> *__restrict__ twx, const cplx<T> *__restrict__ twpost) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int MX = N1 * N2;
+    constexpr int BL = N2 * (N1 + 1);
+    const int nx = g.nx, ny = g.ny, sk = g.sk;
+    cplx<T> *B = reinterpret_cast<cplx<T> *>(smraw);   // RY rows of BL
+    cplx<T> *TW = B + (size_t)RY * BL;                 // w^m, m < MX
+    cplx<T> *TP = TW + MX;                             // w_nx^m, m <= MX
+    const int nby = ny / RY;
+    const int k = blockIdx.x / nby, j0 = (blockIdx.x % nby) * RY;
+    const cplx<T> *src = spec + ((size_t)k * ny + j0) * sk;
+    const int t = threadIdx.x;
+    const bool on1 = t < RY * N2;
+    const int r1 = t / N2, n2 = t - r1 * N2;
+    cplx<T> xa[N1], xb[N1];
+    if (on1) {
+        const cplx<T> *row = src + (size_t)r1 * sk;
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            const int m = a * N2 + n2;
+            xa[a] = row[m];
+            xb[a] = row[MX - m];
+        }
+    }
+    for (int m = t; m < MX; m += blockDim.x) TW[m] = twx[m];
+    for (int m = t; m <= MX; m += blockDim.x) TP[m] = twpost[m];
+    __syncthreads();
+    if (on1) {
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+            const int m = a * N2 + n2;
+            const cplx<T> xk = xa[a], xm = conj(xb[a]);
+            const cplx<T> ev = xk + xm;
+            const cplx<T> od = (xk - xm) * conj(TP[m]);
+            xa[a] = ev + mul_i<T, 1>(od);
+        }
+        dft_reg<T, N1, 1>(xa, TW, MX);
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) xa[k1] = xa[k1] * conj(TW[n2 * k1]);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) B[r1 * BL + n2 * (N1 + 1) + k1] = xa[k1];
+    }
+    __syncthreads();
+    if (t < RY * N1) {
+        const int r2 = t / N1, k1 = t - r2 * N1;
+        cplx<T> y[N2];
+#pragma unroll
+        for (int q = 0; q < N2; ++q) y[q] = B[r2 * BL + q * (N1 + 1) + k1];
+        dft_reg<T, N2, 1>(y, TW, MX);
+        cplxa<T> *drow = reinterpret_cast<cplxa<T> *>(dst + ((size_t)k * ny + j0 + r2) * nx);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            cplxa<T> v;
+            v.re = y[k2].re;
+            v.im = y[k2].im;
+            drow[k1 + N1 * k2] = v;
+        }
+    }
+}
+
 }  // namespace
 
 // x transforms: two line buffers, the twiddle tables and (inverse only) the
@@ -941,7 +1012,25 @@ void irfft_x_ry(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
                                                                   W.twpost, W.fpx);
 }
 
+template <typename T, int RY>
+bool irfft_x_2p_launch(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
+    const int n1 = fft_split_n1(g.mx);
+    if (!n1 || W.ry_fft != RY || RY * n1 > 256) return false;
+    const int blocks = g.nz * (g.ny / RY);
+    const size_t sm = sizeof(cplx<T>) * ((size_t)RY * (g.mx / n1) * (n1 + 1) + 2 * g.mx + 1);
+    const int thr = RY * n1;
+    switch (g.mx) {
+    case 16: k_irfft_x_2p<T, RY, 4, 4><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
+    case 32: k_irfft_x_2p<T, RY, 8, 4><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
+    case 64: k_irfft_x_2p<T, RY, 8, 8><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
+    case 128: k_irfft_x_2p<T, RY, 16, 8><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
+    case 256: k_irfft_x_2p<T, RY, 16, 16><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
+    default: return false;
+    }
+}
+
 template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
+    if (irfft_x_2p_launch<T, sizeof(T) == 4 ? 16 : 4>(g, W, dst, st)) return;
     switch (W.ry_fft) {
     case 16: irfft_x_ry<T, 16>(g, W, dst, st); break;
     case 8: irfft_x_ry<T, 8>(g, W, dst, st); break;
@@ -960,6 +1049,14 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     raise_smem_limit(k_rfft_x<T, 0, 16>);
     raise_smem_limit(k_rfft_x<T, 1, 16>);
     raise_smem_limit(k_irfft_x<T, 16>);
+    {
+        constexpr int R = sizeof(T) == 4 ? 16 : 4;
+        raise_smem_limit(k_irfft_x_2p<T, R, 4, 4>);
+        raise_smem_limit(k_irfft_x_2p<T, R, 8, 4>);
+        raise_smem_limit(k_irfft_x_2p<T, R, 8, 8>);
+        raise_smem_limit(k_irfft_x_2p<T, R, 16, 8>);
+        raise_smem_limit(k_irfft_x_2p<T, R, 16, 16>);
+    }
     raise_smem_limit(k_rfft_x<T, 1, 1>);
     raise_smem_limit(k_rfft_x<T, 1, 2>);
     raise_smem_limit(k_rfft_x<T, 1, 4>);
