@@ -688,17 +688,9 @@ k_rhs_x_tile(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     x_solve_store<T, L>(sd, es, RY, P, nx, ny, k, j0, sc, car, q0, q1, q2);
 }
 
-// Row-resident right-hand side + x sweep: the LPR lanes of a warp segment
-// (or of LPR / 32 warps) own one x row (j, k); lane r holds cells CPL r ..
-// CPL r + CPL - 1 and reads every stencil row it needs as 16-byte vectors
-// straight from global memory (neighbour rows are served by the caches).
-// The x neighbours beyond its cells come from the neighbouring lanes (the
-// row is periodic, so they rotate around the line); edge fluxes shared by
-// two cells of a lane are formed once (the same products, so the same
-// values as k_rhs_x).  The x solve runs on the registers (line_solve_uni),
-// with no shared-memory staging; only lines wider than a warp exchange
-// their carries through shared memory.  Needs nx = LPR CPL, CPL a multiple
-// of the 16-byte vector, ny a multiple of the rows per block.
+// Helpers of the row-resident right-hand side (k_rhs_x_row below): CPL
+// consecutive values of a row as 16-byte vectors, from and to global
+// memory (neighbour rows are served by the caches).
 template <typename T, int CPL>
 FSEI_D void ldrow(T (&a)[CPL], const T *p) {
     constexpr int VW = 16 / (int)sizeof(T);
