@@ -132,34 +132,59 @@ __device__ void uni_factors(double r, double &alpha, double &cinv) {
     cinv = 1.0 / c;
 }
 
-__global__ void k_scalars(StepScalars *sc, StepArgs a, int euler, double idx2, double idy2) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Three warps, so that the serial double-precision chains (each a division
+// or square root at a time on GB300's narrow FP64 pipe) run side by side:
+// every warp forms dt and beta; warp 0 the x factors, warp 1 the y factors,
+// warp 2 1/dt, the AB2 weights and the reset of the step's reductions.
+// Lane 0 of each warp stores.
+__global__ void __launch_bounds__(96) k_scalars(StepScalars *sc, StepArgs a, int euler,
+                                                double idx2, double idy2) {
+    const int wid = threadIdx.x >> 5;
+    const bool lead = (threadIdx.x & 31) == 0;
+    const unsigned long long spd = sc->speed_next;
     double dt = a.dt;
     if (a.cfl > 0.0) {
-        const double s = bitsd(sc->speed_next);
+        const double s = bitsd(spd);
         dt = s > 0.0 ? a.cfl / s : a.dt;
     }
-    sc->speed_cur = sc->speed_next;
-    sc->speed_next = 0ull;
-    sc->maxdiv = 0ull;
-    sc->ke = 0.0;
-    sc->flags = 0;
-    sc->dt = dt;
-    sc->beta = dt / (2.0 * a.re);
-    uni_factors(sc->beta * idx2, sc->ax, sc->cix);
-    uni_factors(sc->beta * idy2, sc->ay, sc->ciy);
-    sc->gamma = euler ? 1.0 : a.gamma;
-    sc->rho = euler ? 0.0 : a.rho;
-    sc->invdt = 1.0 / dt;
-    sc->fdt = (float)dt;
-    sc->fbeta = (float)sc->beta;
-    sc->fgamma = (float)sc->gamma;
-    sc->frho = (float)sc->rho;
-    sc->finvdt = (float)sc->invdt;
-    sc->fax = (float)sc->ax;
-    sc->fcix = (float)sc->cix;
-    sc->fay = (float)sc->ay;
-    sc->fciy = (float)sc->ciy;
+    const double beta = dt / (2.0 * a.re);
+    __syncthreads();   // every warp has read speed_next before warp 2 resets it
+    if (wid == 0) {
+        double al, ci;
+        uni_factors(beta * idx2, al, ci);
+        if (lead) {
+            sc->ax = al;
+            sc->cix = ci;
+            sc->fax = (float)al;
+            sc->fcix = (float)ci;
+        }
+    } else if (wid == 1) {
+        double al, ci;
+        uni_factors(beta * idy2, al, ci);
+        if (lead) {
+            sc->ay = al;
+            sc->ciy = ci;
+            sc->fay = (float)al;
+            sc->fciy = (float)ci;
+        }
+    } else if (lead) {
+        const double invdt = 1.0 / dt;
+        sc->speed_cur = spd;
+        sc->speed_next = 0ull;
+        sc->maxdiv = 0ull;
+        sc->ke = 0.0;
+        sc->flags = 0;
+        sc->dt = dt;
+        sc->beta = beta;
+        sc->gamma = euler ? 1.0 : a.gamma;
+        sc->rho = euler ? 0.0 : a.rho;
+        sc->invdt = invdt;
+        sc->fdt = (float)dt;
+        sc->fbeta = (float)beta;
+        sc->fgamma = (float)sc->gamma;
+        sc->frho = (float)sc->rho;
+        sc->finvdt = (float)invdt;
+    }
 }
 
 // Coefficients of the four sweep matrices, in double.  Row i of a line:
@@ -956,7 +981,7 @@ template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v
 
 void launch_step_scalars(const GridDev &g, StepScalars *sc, const StepArgs &a, int euler,
                          cudaStream_t st) {
-    k_scalars<<<1, 32, 0, st>>>(sc, a, euler, g.idx2, g.idy2);
+    k_scalars<<<1, 96, 0, st>>>(sc, a, euler, g.idx2, g.idy2);
 }
 
 template <typename T> void launch_step_plans(const GridDev &g, Work<T> &W, const StepScalars *sc,
