@@ -189,6 +189,11 @@ def run_gpu_arm(args, rank, world):
             continue
         grid = fsei.Grid(case.nx, case.ny, case.nz, case.lx, case.ly, zbc=case.zbc,
                          lz=case.lz, stretch=case.stretch, prec=prec)
+        if args.schedule and prec_name == "mixed":
+            grid.set_schedule(json.loads(args.schedule))
+            sched = grid.schedule
+        else:
+            sched = grid.autotune() if not args.no_autotune else grid.schedule
         st = device_state(case, dtype)
         stream = torch.cuda.current_stream()
         if W > 0:
@@ -213,6 +218,7 @@ def run_gpu_arm(args, rank, world):
         kt = fsei.kernel_times(grid)
         fsei.set_kernel_timing(grid, False)
         res["kernels"] = kt
+        res["schedule"] = sched
         results[prec_name] = (res, grid, st)
         log("%s: %.3f ms/step, %.1f Mcell/s" % (prec_name, res["ms_per_step"], res["mcups"]))
 
@@ -277,6 +283,8 @@ def run_ensemble(args):
     boxes = [dict(nx=c.nx, ny=c.ny, nz=c.nz, lx=c.lx, ly=c.ly, zbc=c.zbc, lz=c.lz,
                   stretch=c.stretch, prec=fsei.FSEI_MIXED) for c in cases]
     batch = fsei.Batch(boxes)
+    if not args.no_autotune:
+        batch.autotune()
     states = [device_state(c, torch.float32) for c in cases]
     params = [dict(re=c.re, dt=c.dt, cfl=c.cfl, fconst=c.fconst) for c in cases]
     cells = sum(c.cells for c in cases)
@@ -323,6 +331,8 @@ def run_heart_scale(args, peak):
     case = inputs.case_heart_scale(steps=args.heart_steps)
     grid = fsei.Grid(case.nx, case.ny, case.nz, case.lx, case.ly, zbc=case.zbc, lz=case.lz,
                      stretch=case.stretch, prec=fsei.FSEI_MIXED)
+    if not args.no_autotune:
+        grid.autotune()
     st = device_state(case, torch.float32)
     f = tuple(torch.tensor(a, dtype=torch.float32, device="cuda") for a in case.f)
     prm = dict(re=case.re, dt=case.dt, cfl=case.cfl, fconst=case.fconst)
@@ -459,6 +469,11 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--heart-steps", type=int, default=50)
     ap.add_argument("--no-heart", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="run the default launch schedule instead of a measured one")
+    ap.add_argument("--schedule", default=None,
+                    help="JSON dict of fsei_schedule fields for the mixed-precision grid "
+                         "(e.g. one a previous run printed), applied instead of autotuning")
     ap.add_argument("--nx", type=int, default=None, help="profiling override of the extents")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
@@ -508,6 +523,9 @@ def main():
         "step_hbm": {"alg_words_per_cell": round(step_words, 3),
                      "achieved_gbs": round(step_gbs, 1), "frac": round(step_gbs / peak, 4)},
         "clocks": mres["clocks"],
+        "schedule": {"mixed": mres["schedule"],
+                     "source": ("given" if args.schedule else
+                                "default" if args.no_autotune else "autotuned")},
         "gpu_launches": int(sum(n for _, n in mres["kernels"].values())),
         "kernels": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv)
                         for kk, vv in v.items()} for k, v in table.items()},

@@ -140,6 +140,63 @@ void fsei_grid_destroy(fsei_grid grid);
 /* Bytes of device workspace the handle owns. */
 int64_t fsei_grid_workspace_bytes(fsei_grid grid);
 
+/* Launch schedule of a grid: the tile shapes and solver splits its tunable
+ * kernels run with.  The paper fixes none of them (its Sec. 3 maps the same
+ * sweeps and transforms onto its own GPUs); every admissible value computes
+ * the same quantities with the same operations grouped differently, so
+ * results agree to rounding and only the time changes.  0 marks a field
+ * whose kernel does not apply to the grid's extents.
+ *   rhs_cells_per_lane: RHS + x sweep (Eq. 3, Sec. 3.1), cells of a grid row
+ *     per lane of the row-resident kernel (4, or 8 in FSEI_MIXED);
+ *   poisson_lanes_per_line, poisson_rows_per_lane: z tridiagonal solve of
+ *     each Fourier mode (Sec. 3.2): lanes that share a line (reduction
+ *     across lanes) and rows each lane eliminates on its own; their product
+ *     is nz;
+ *   rfft_rows_per_block: forward x transform, grid rows per thread block;
+ *   ffty_columns_per_block: y transforms, kx columns per thread block;
+ *   project_passes_per_thread: projection and pressure update (Eq. 3),
+ *     row passes per thread. */
+typedef struct {
+    int32_t rhs_cells_per_lane;
+    int32_t poisson_lanes_per_line;
+    int32_t poisson_rows_per_lane;
+    int32_t rfft_rows_per_block;
+    int32_t ffty_columns_per_block;
+    int32_t project_passes_per_thread;
+} fsei_schedule;
+
+/* fsei_grid_autotune flag: measure again although this process already
+ * holds a schedule for the grid's shape. */
+#define FSEI_TUNE_FORCE 1
+
+/* Pick the grid's schedule by measurement.  For each field in turn, the
+ * others held, every admissible value runs inside whole fractional steps
+ * (one untimed, eight timed) on stand-in fields of the grid's extents that
+ * the call allocates (7 fields) and frees; CUDA events around the kernel
+ * that the field shapes give its device time, and the value of least time
+ * is kept (a challenger must be 1% faster than the value in place).  The
+ * choice is applied to the grid and remembered for the process under the
+ * grid's (device, precision, nx, ny, nz, zbc): every grid created later
+ * with that key, and a later autotune call without FSEI_TUNE_FORCE, takes
+ * it without measuring, so grids of one shape run identical kernels.
+ * Synchronises the device; allocates; not allowed inside a stream capture.
+ * The grid's per-kernel timing sums and step scalars are left as they were;
+ * no caller field is touched.  out (optional) receives the schedule.
+ * Returns FSEI_E_NOMEM when the stand-in fields do not fit, FSEI_E_ARG for
+ * a NULL grid or unknown flags, FSEI_E_CUDA if a launch fails. */
+fsei_status fsei_grid_autotune(fsei_grid grid, int32_t flags, void *cuda_stream,
+                               fsei_schedule *out);
+
+/* The schedule the grid runs with now. */
+fsei_status fsei_grid_get_schedule(fsei_grid grid, fsei_schedule *out);
+
+/* Run the grid with the given schedule (e.g. one recorded by an earlier
+ * autotune, for runs that must repeat bit for bit).  FSEI_E_ARG if a field
+ * is not admissible for the grid (0 is admissible exactly where the kernel
+ * does not apply).  Takes effect at the next launch; not remembered for
+ * other grids. */
+fsei_status fsei_grid_set_schedule(fsei_grid grid, const fsei_schedule *in);
+
 /* Advance the state by nsteps fractional steps (Eq. 3 with the
  * approximate factorisation of Sec. 3.1).  fx, fy, fz: body force at the u,
  * v and w points, constant over the call, or NULL for zero.  out: if not
@@ -198,6 +255,10 @@ fsei_status fsei_batch_create(const fsei_grid_desc *descs, int32_t nboxes,
                               fsei_batch *out);
 void fsei_batch_destroy(fsei_batch batch);
 int32_t fsei_batch_size(fsei_batch batch);
+/* fsei_grid_autotune for every box (one measurement per distinct shape;
+ * flags as there).  Drops the captured graphs, which the next
+ * fsei_batch_step captures again with the new schedules. */
+fsei_status fsei_batch_autotune(fsei_batch batch, int32_t flags, void *cuda_stream);
 fsei_status fsei_batch_step(fsei_batch batch, fsei_state *states,
                             const void *const *forces,
                             const fsei_step_params *params, int32_t nsteps,

@@ -6,7 +6,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/fsei.h"
@@ -454,6 +457,171 @@ fsei_status run_poisson(fsei_grid_s *G, Work<T> &W, const void *rhs, void *phi, 
     return FSEI_OK;
 }
 
+// Launch-schedule autotuner.  The schedules measured in this process, by
+// grid shape: every grid created later with a tuned shape starts from its
+// schedule, so grids of one shape (a batch's boxes, solo runs beside it)
+// run the same kernels and give identical results.
+using ScheduleKey = std::tuple<int, int, int, int, int, int>;
+std::mutex g_sched_mu;
+std::map<ScheduleKey, Schedule> g_sched;
+
+ScheduleKey schedule_key(const fsei_grid_s *G) {
+    return ScheduleKey(G->device, G->prec, G->g.nx, G->g.ny, G->g.nz, G->g.walls);
+}
+
+bool cached_schedule(const fsei_grid_s *G, Schedule *out) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    auto it = g_sched.find(schedule_key(G));
+    if (it == g_sched.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+void store_schedule(const fsei_grid_s *G, const Schedule &s) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched[schedule_key(G)] = s;
+}
+
+// the kernel kinds whose device time decides knob k
+double knob_ms(const KernelTimer &tm, int knob) {
+    switch (knob) {
+    case SK_RHS: return tm.ms[KK_RHS_X];
+    case SK_ZL: return tm.ms[KK_POISSON_Z];
+    case SK_RFFT: return tm.ms[KK_RFFT_X];
+    case SK_FFTY: return tm.ms[KK_FFT_Y] + tm.ms[KK_IFFT_Y];
+    case SK_PROJ: return tm.ms[KK_PROJECT];
+    default: return 0.0;
+    }
+}
+
+void set_knob(Schedule &s, int knob, const int v[2]) {
+    switch (knob) {
+    case SK_RHS: s.rhs_cpl = v[0]; break;
+    case SK_ZL: s.zl_lpl = v[0]; s.zl_e = v[1]; break;
+    case SK_RFFT: s.ry_rfft = v[0]; break;
+    case SK_FFTY: s.tkx_fft = v[0]; break;
+    case SK_PROJ: s.proj_mult = v[0]; break;
+    default: break;
+    }
+}
+
+// Times every candidate of every knob in turn (the others held at their
+// current choice) inside whole steps on stand-in fields, with the grid's
+// kernel timer, and keeps for each knob the candidate of least summed
+// device time over `reps` steps (a challenger must beat the incumbent by
+// 1%).  The grid's step scalars and timer sums are put back afterwards.
+template <typename T>
+fsei_status tune_grid(fsei_grid_s *G, Work<T> &W, int reps, cudaStream_t st) {
+    const GridDev &g = G->g;
+    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
+    T *buf = nullptr;
+    if (cudaMalloc(&buf, 7 * ncell * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FSEI_E_NOMEM, "autotune: no room for the stand-in fields (%zu bytes)",
+                    7 * ncell * sizeof(T));
+    }
+    // constant fill (0x3c bytes: about 0.0115 in float, 1.6e-18 in double):
+    // finite values, the same memory traffic as any other
+    cudaMemsetAsync(buf, 0x3c, 7 * ncell * sizeof(T), st);
+    fsei_state s;
+    s.u = buf; s.v = buf + ncell; s.w = buf + 2 * ncell; s.p = buf + 3 * ncell;
+    s.hu = buf + 4 * ncell; s.hv = buf + 5 * ncell; s.hw = buf + 6 * ncell;
+    s.have_prev_h = 1;
+    StepArgs a;
+    a.re = 1000.0; a.dt = 1e-4; a.cfl = 0.0; a.gamma = 1.5; a.rho = -0.5;
+    a.fconst[0] = a.fconst[1] = a.fconst[2] = 0.0;
+
+    KernelTimer &tm = G->timer;
+    tm.collect();
+    double ms_keep[KK_COUNT];
+    long long n_keep[KK_COUNT];
+    memcpy(ms_keep, tm.ms, sizeof ms_keep);
+    memcpy(n_keep, tm.n, sizeof n_keep);
+    const bool on_keep = tm.on;
+    StepScalars sc_keep;
+    cudaStreamSynchronize(st);
+    cudaMemcpy(&sc_keep, G->sc, sizeof sc_keep, cudaMemcpyDeviceToHost);
+
+    fsei_status r = FSEI_OK;
+    Schedule cur = schedule_of<T>(g, W);
+    tm.on = true;
+    for (int knob = 0; knob < SK_COUNT && r == FSEI_OK; ++knob) {
+        int cand[16][2];
+        const int nc = schedule_candidates<T>(g, knob, cand, 16);
+        if (nc < 2) continue;
+        int best = -1;
+        double best_ms = 0.0;
+        for (int c = 0; c < nc && r == FSEI_OK; ++c) {
+            Schedule trial = cur;
+            set_knob(trial, knob, cand[c]);
+            apply_schedule<T>(W, trial);
+            r = run_steps<T>(G, W, &s, nullptr, nullptr, nullptr, a, 1, st, false);
+            tm.collect();
+            memset(tm.ms, 0, sizeof tm.ms);
+            if (r == FSEI_OK) r = run_steps<T>(G, W, &s, nullptr, nullptr, nullptr, a, reps, st, false);
+            tm.collect();
+            const double t = knob_ms(tm, knob);
+            if (best < 0 || t < 0.99 * best_ms) {
+                best = c;
+                best_ms = t;
+            }
+        }
+        if (best >= 0) set_knob(cur, knob, cand[best]);
+    }
+    apply_schedule<T>(W, cur);
+    tm.on = on_keep;
+    memcpy(tm.ms, ms_keep, sizeof ms_keep);
+    memcpy(tm.n, n_keep, sizeof n_keep);
+    cudaMemcpy(G->sc, &sc_keep, sizeof sc_keep, cudaMemcpyHostToDevice);
+    cudaFree(buf);
+    const cudaError_t e = cudaGetLastError();
+    if (r == FSEI_OK && e != cudaSuccess) r = fail(FSEI_E_CUDA, "autotune: %s", cudaGetErrorString(e));
+    if (r == FSEI_OK) store_schedule(G, cur);
+    return r;
+}
+
+void to_public(const Schedule &s, fsei_schedule *o) {
+    o->rhs_cells_per_lane = s.rhs_cpl;
+    o->poisson_lanes_per_line = s.zl_lpl;
+    o->poisson_rows_per_lane = s.zl_e;
+    o->rfft_rows_per_block = s.ry_rfft;
+    o->ffty_columns_per_block = s.tkx_fft;
+    o->project_passes_per_thread = s.proj_mult;
+}
+
+Schedule grid_schedule(const fsei_grid_s *G) {
+    return G->prec == FSEI_FP64 ? schedule_of<double>(G->g, G->wd) : schedule_of<float>(G->g, G->wf);
+}
+
+void grid_apply(fsei_grid_s *G, const Schedule &s) {
+    if (G->prec == FSEI_FP64) apply_schedule<double>(G->wd, s);
+    else apply_schedule<float>(G->wf, s);
+}
+
+// s holds, for every knob, one of the grid's candidates (0 where the knob has
+// none)
+bool schedule_valid(const fsei_grid_s *G, const Schedule &s) {
+    for (int knob = 0; knob < SK_COUNT; ++knob) {
+        int cand[16][2];
+        const int nc = G->prec == FSEI_FP64 ? schedule_candidates<double>(G->g, knob, cand, 16)
+                                            : schedule_candidates<float>(G->g, knob, cand, 16);
+        int v0 = 0, v1 = 0;
+        switch (knob) {
+        case SK_RHS: v0 = s.rhs_cpl; break;
+        case SK_ZL: v0 = s.zl_lpl; v1 = s.zl_e; break;
+        case SK_RFFT: v0 = s.ry_rfft; break;
+        case SK_FFTY: v0 = s.tkx_fft; break;
+        case SK_PROJ: v0 = s.proj_mult; break;
+        default: break;
+        }
+        bool ok = nc == 0 && v0 == 0 && v1 == 0;
+        for (int c = 0; c < nc && !ok; ++c)
+            ok = cand[c][0] == v0 && (knob != SK_ZL || cand[c][1] == v1);
+        if (!ok) return false;
+    }
+    return true;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -581,6 +749,10 @@ fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
                          ? setup_work<double>(G, G->wd, lamx, lamy, nzm, dz, idz, ihc)
                          : setup_work<float>(G, G->wf, lamx, lamy, nzm, dz, idz, ihc);
     if (st == FSEI_OK) st = create_overlap(G);
+    if (st == FSEI_OK) {
+        Schedule cs;
+        if (cached_schedule(G, &cs)) grid_apply(G, cs);
+    }
     if (st != FSEI_OK) {
         destroy_overlap(G);
         cudaFreeHost(G->sc_host);
@@ -612,6 +784,48 @@ void fsei_grid_destroy(fsei_grid G) {
 }
 
 int64_t fsei_grid_workspace_bytes(fsei_grid G) { return G ? (int64_t)G->mem.bytes : 0; }
+
+fsei_status fsei_grid_autotune(fsei_grid G, int32_t flags, void *cuda_stream, fsei_schedule *out) {
+    g_err.clear();
+    cudaGetLastError();
+    if (!G) return fail(FSEI_E_ARG, "fsei_grid_autotune: NULL grid");
+    if (flags & ~FSEI_TUNE_FORCE) return fail(FSEI_E_ARG, "fsei_grid_autotune: unknown flags %d", flags);
+    DeviceGuard dg(G->device);
+    Schedule cs;
+    fsei_status r = FSEI_OK;
+    if (!(flags & FSEI_TUNE_FORCE) && cached_schedule(G, &cs)) {
+        grid_apply(G, cs);
+    } else {
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        r = G->prec == FSEI_FP64 ? tune_grid<double>(G, G->wd, 8, st)
+                                 : tune_grid<float>(G, G->wf, 8, st);
+    }
+    if (r == FSEI_OK && out) to_public(grid_schedule(G), out);
+    return r;
+}
+
+fsei_status fsei_grid_get_schedule(fsei_grid G, fsei_schedule *out) {
+    g_err.clear();
+    if (!G || !out) return fail(FSEI_E_ARG, "fsei_grid_get_schedule: NULL argument");
+    to_public(grid_schedule(G), out);
+    return FSEI_OK;
+}
+
+fsei_status fsei_grid_set_schedule(fsei_grid G, const fsei_schedule *in) {
+    g_err.clear();
+    if (!G || !in) return fail(FSEI_E_ARG, "fsei_grid_set_schedule: NULL argument");
+    Schedule s;
+    s.rhs_cpl = in->rhs_cells_per_lane;
+    s.zl_lpl = in->poisson_lanes_per_line;
+    s.zl_e = in->poisson_rows_per_lane;
+    s.ry_rfft = in->rfft_rows_per_block;
+    s.tkx_fft = in->ffty_columns_per_block;
+    s.proj_mult = in->project_passes_per_thread;
+    if (!schedule_valid(G, s))
+        return fail(FSEI_E_ARG, "fsei_grid_set_schedule: a field is not a candidate of this grid");
+    grid_apply(G, s);
+    return FSEI_OK;
+}
 
 fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy, const void *fz,
                       const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,
@@ -899,6 +1113,29 @@ void fsei_batch_destroy(fsei_batch B) {
 }
 
 int32_t fsei_batch_size(fsei_batch B) { return B ? (int32_t)B->grids.size() : 0; }
+
+fsei_status fsei_batch_autotune(fsei_batch B, int32_t flags, void *cuda_stream) {
+    g_err.clear();
+    if (!B) return fail(FSEI_E_ARG, "fsei_batch_autotune: NULL batch");
+    DeviceGuard dg(B->device);
+    cudaDeviceSynchronize();
+    batch_clear_graphs(B);
+    // one measurement per shape: later boxes of a tuned shape take the
+    // cached schedule (FSEI_TUNE_FORCE applies to the first box of a shape)
+    std::vector<ScheduleKey> done;
+    for (size_t i = 0; i < B->grids.size(); ++i) {
+        const ScheduleKey k = schedule_key(B->grids[i]);
+        bool seen = false;
+        for (const ScheduleKey &d : done) seen = seen || d == k;
+        const fsei_status r = fsei_grid_autotune(B->grids[i], seen ? 0 : flags, cuda_stream, nullptr);
+        if (r != FSEI_OK) {
+            const std::string msg = g_err;
+            return fail(r, "box %zu: %s", i, msg.c_str());
+        }
+        done.push_back(k);
+    }
+    return FSEI_OK;
+}
 
 fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const *forces,
                             const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,

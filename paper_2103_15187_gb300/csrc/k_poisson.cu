@@ -14,6 +14,8 @@
 //                     weighted mean removed) and, in mixed precision, every
 //                     near-zero mode, in double with Thomas' algorithm
 //   k_irfft_x         complex-to-real inverse DFT along x into phi
+#include <string.h>
+
 #include "kernels.cuh"
 #include "tri.cuh"
 
@@ -879,6 +881,24 @@ template <typename T> size_t smem_poisson(const GridDev &g, const Work<T> &W) {
 // columns per block of the y transform and z solve (up to 128 bytes of
 // complex values per row), each the largest whose shared memory, computed
 // exactly, fits the device limit.
+int zl_candidates(const GridDev &g, int elem_size, int (*out)[2], int cap) {
+    // instantiated splits with nz = LPL E, 16 lanes per line first (fewer
+    // reduction levels; at 256^3 measured 41 against 59 us for 32 lanes of
+    // half the rows); in double at most 8 rows per lane (registers)
+    static const int cand[][2] = {{16, 4}, {16, 6}, {16, 8}, {16, 12}, {16, 16},
+                                  {16, 24}, {32, 8}, {32, 16}, {32, 24}};
+    int n = 0;
+    for (const auto &c : cand) {
+        if (elem_size == 8 && c[1] > 8) continue;
+        if (g.nz == c[0] * c[1] && g.sk % (256 / c[0]) == 0 && n < cap) {
+            out[n][0] = c[0];
+            out[n][1] = c[1];
+            ++n;
+        }
+    }
+    return n;
+}
+
 template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W) {
     const size_t lim = (size_t)smem_optin() - 2048;
     const int tsz = (int)sizeof(T);
@@ -886,21 +906,14 @@ template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W) {
     for (int r = tsz == 8 ? 4 : 16; r >= 1; r /= 2)
         if (g.ny % r == 0) { W.ry_fft = r; break; }
     while (W.ry_fft > 1 && smem_fft_x<T>(g, W) > lim) W.ry_fft /= 2;
-    // lane-resident z solve: the first instantiated (lanes per line, rows per
-    // lane) with nz = LPL E; in double at most 8 rows per lane (registers)
+    // lane-resident z solve: the first applicable (lanes per line, rows per
+    // lane) split; the grid's autotuner may pick another
     W.zl_lpl = W.zl_e = 0;
     {
-        // 16 lanes per line first: fewer reduction levels, measured faster
-        // than 32 lanes of half the rows (256^3: 41 against 59 us)
-        static const int cand[][2] = {{16, 4}, {16, 6}, {16, 8}, {16, 12}, {16, 16},
-                                      {16, 24}, {32, 8}, {32, 16}, {32, 24}};
-        for (const auto &c : cand) {
-            if (tsz == 8 && c[1] > 8) continue;
-            if (g.nz == c[0] * c[1] && g.sk % (256 / c[0]) == 0) {
-                W.zl_lpl = c[0];
-                W.zl_e = c[1];
-                break;
-            }
+        int c[4][2];
+        if (zl_candidates(g, tsz, c, 4) > 0) {
+            W.zl_lpl = c[0][0];
+            W.zl_e = c[0][1];
         }
     }
     W.tkx = 128 / (2 * tsz);
@@ -910,6 +923,12 @@ template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W) {
         if (W.pz_poisson < 1) W.pz_poisson = 1;
         if (W.tkx <= 2 || (smem_poisson<T>(g, W) <= lim && smem_fft_y<T>(g, W) <= lim)) break;
         W.tkx /= 2;
+    }
+    W.ry_rfft = W.ry_fft;
+    W.tkx_fft = W.tkx;
+    {
+        const int n1 = fft_split_n1(g.ny);
+        while (n1 && W.tkx_fft > 1 && W.tkx_fft * n1 > 256) W.tkx_fft /= 2;
     }
 }
 
@@ -923,7 +942,7 @@ void rfft_x_ry(const GridDev &g, Work<T> &W, const StepScalars *sc, const T *src
 template <typename T, int MODE>
 void rfft_x_mode(const GridDev &g, Work<T> &W, const StepScalars *sc, const T *src,
                  cudaStream_t st) {
-    switch (W.ry_fft) {
+    switch (W.ry_rfft) {
     case 16: rfft_x_ry<T, MODE, 16>(g, W, sc, src, st); break;
     case 8: rfft_x_ry<T, MODE, 8>(g, W, sc, src, st); break;
     case 4: rfft_x_ry<T, MODE, 4>(g, W, sc, src, st); break;
@@ -940,17 +959,18 @@ template <typename T> void launch_rfft_x(const GridDev &g, Work<T> &W, const Ste
 
 template <typename T, int SIGN>
 bool fft_y_2p_launch(const GridDev &g, Work<T> &W, cudaStream_t st) {
-    const int blocks = g.nz * (g.sk / W.tkx);
+    const int tk = W.tkx_fft;
     const int n1 = fft_split_n1(g.ny);
-    if (!n1 || W.tkx * n1 > 256) return false;
-    const size_t sm = sizeof(cplx<T>) * ((size_t)g.ny * W.tkx + g.ny);
-    const int thr = W.tkx * n1;
+    if (!n1 || tk < 1 || g.sk % tk || tk * n1 > 256) return false;
+    const int blocks = g.nz * (g.sk / tk);
+    const size_t sm = sizeof(cplx<T>) * ((size_t)g.ny * tk + g.ny);
+    const int thr = tk * n1;
     switch (g.ny) {
-    case 16: k_fft_y_2p<T, SIGN, 4, 4><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
-    case 32: k_fft_y_2p<T, SIGN, 8, 4><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
-    case 64: k_fft_y_2p<T, SIGN, 8, 8><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
-    case 128: k_fft_y_2p<T, SIGN, 16, 8><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
-    case 256: k_fft_y_2p<T, SIGN, 16, 16><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, W.tkx); return true;
+    case 16: k_fft_y_2p<T, SIGN, 4, 4><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
+    case 32: k_fft_y_2p<T, SIGN, 8, 4><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
+    case 64: k_fft_y_2p<T, SIGN, 8, 8><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
+    case 128: k_fft_y_2p<T, SIGN, 16, 8><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
+    case 256: k_fft_y_2p<T, SIGN, 16, 16><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
     default: return false;
     }
 }
@@ -1093,11 +1113,106 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     }
 }
 
+template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*out)[2], int cap) {
+    const size_t lim = (size_t)smem_optin() - 2048;
+    const int tsz = (int)sizeof(T);
+    int n = 0;
+    auto put = [&](int a, int b) {
+        if (n < cap) {
+            out[n][0] = a;
+            out[n][1] = b;
+            ++n;
+        }
+    };
+    switch (knob) {
+    case SK_RHS: {
+        // the default (8 cells per lane in single precision on rows wider
+        // than 256 cells, 4 otherwise) first
+        int c[2];
+        const int m = rhs_cpl_candidates(g, tsz, c, 2);
+        const int def = (tsz == 4 && g.nx > 256) ? 8 : 4;
+        for (int i = 0; i < m; ++i)
+            if (c[i] == def) put(c[i], 0);
+        for (int i = 0; i < m; ++i)
+            if (c[i] != def) put(c[i], 0);
+        break;
+    }
+    case SK_ZL: {
+        int c[9][2];
+        const int m = zl_candidates(g, tsz, c, 9);
+        for (int i = 0; i < m; ++i) put(c[i][0], c[i][1]);
+        break;
+    }
+    case SK_RFFT: {
+        // rows per block: powers of two dividing ny whose buffers fit; the
+        // default (the largest up to 16 in single, 4 in double precision)
+        // first
+        Work<T> W;
+        memset(&W, 0, sizeof W);
+        poisson_geometry<T>(g, W);
+        put(W.ry_rfft, 0);
+        for (int r = 16; r >= 2; r /= 2)
+            if (r != W.ry_rfft && g.ny % r == 0 && smem_rfft_x<T>(g, r) <= lim) put(r, 0);
+        break;
+    }
+    case SK_FFTY: {
+        // kx columns per block of the two-pass y transform (power-of-two ny
+        // up to 256): tkx N1 threads, 32 to 256
+        const int n1 = fft_split_n1(g.ny);
+        if (!n1) break;
+        Work<T> W;
+        memset(&W, 0, sizeof W);
+        poisson_geometry<T>(g, W);
+        put(W.tkx_fft, 0);
+        for (int t = 32; t >= 2; t /= 2)
+            if (t != W.tkx_fft && g.sk % t == 0 && t * n1 <= 256 && t * n1 >= 32 &&
+                sizeof(cplx<T>) * ((size_t)g.ny * t + g.ny) <= lim)
+                put(t, 0);
+        break;
+    }
+    case SK_PROJ: {
+        // row passes per thread of the 16-byte vector projection
+        if (g.nx % (16 / tsz)) break;
+        const int opts[4] = {4, 2, 8, 1};
+        for (int m : opts) put(m, 0);
+        break;
+    }
+    default: break;
+    }
+    return n;
+}
+
+template <typename T> Schedule schedule_of(const GridDev &g, const Work<T> &W) {
+    Schedule s;
+    memset(&s, 0, sizeof s);
+    int c[1][2];
+    if (schedule_candidates<T>(g, SK_RHS, c, 1))
+        s.rhs_cpl = W.rhs_cpl ? W.rhs_cpl : c[0][0];
+    s.zl_lpl = W.zl_lpl;
+    s.zl_e = W.zl_e;
+    s.ry_rfft = W.ry_rfft;
+    if (schedule_candidates<T>(g, SK_FFTY, c, 1)) s.tkx_fft = W.tkx_fft;
+    if (schedule_candidates<T>(g, SK_PROJ, c, 1)) s.proj_mult = W.proj_mult ? W.proj_mult : 4;
+    return s;
+}
+
+template <typename T> void apply_schedule(Work<T> &W, const Schedule &s) {
+    W.rhs_cpl = s.rhs_cpl;
+    W.zl_lpl = s.zl_lpl;
+    W.zl_e = s.zl_e;
+    if (s.ry_rfft) W.ry_rfft = s.ry_rfft;
+    if (s.tkx_fft) W.tkx_fft = s.tkx_fft;
+    W.proj_mult = s.proj_mult;
+}
+
 #define FSEI_INST(T)                                                                           \
     template size_t smem_fft_x<T>(const GridDev &, const Work<T> &);                          \
     template size_t smem_fft_y<T>(const GridDev &, const Work<T> &);                          \
     template size_t smem_poisson<T>(const GridDev &, const Work<T> &);                        \
     template void poisson_geometry<T>(const GridDev &, Work<T> &);                             \
+    template int schedule_candidates<T>(const GridDev &, int, int (*)[2], int);                 \
+    template Schedule schedule_of<T>(const GridDev &, const Work<T> &);                        \
+    template void apply_schedule<T>(Work<T> &, const Schedule &);                              \
     template void launch_rfft_x<T>(const GridDev &, Work<T> &, const StepScalars *, const T *, \
                                    int, cudaStream_t);                                        \
     template void launch_fft_y<T>(const GridDev &, Work<T> &, int, cudaStream_t);              \

@@ -258,12 +258,14 @@ template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, 
     constexpr int VW = 16 / (int)sizeof(T);
     if (g.nx % VW == 0) {
         // vector path: 128 threads, rows side by side, about four passes per
-        // thread (the per-thread set-up and the block's reduction are then
-        // spread over more cells)
+        // thread by default (the per-thread set-up and the block's reduction
+        // are then spread over more cells; the grid's autotuner may pick
+        // another count)
         const int tpr = g.nx / VW;
         const int rpp = tpr >= 128 ? 1 : 128 / tpr;
+        const int mult = W.proj_mult > 0 ? W.proj_mult : 4;
         int rows = 1;
-        for (int r = 4 * rpp; r >= 1; --r)
+        for (int r = mult * rpp; r >= 1; --r)
             if (g.ny % r == 0) { rows = r; break; }
         k_project_vec<T><<<g.nz * (g.ny / rows), 128, 0, st>>>(g, F, W.q0, W.q1, W.q2, W.phi,
                                                                sc, rows);

@@ -1061,10 +1061,13 @@ void rhs_tile_ry(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepSca
 // two, 4 .. 256), rows per block rpb (a power of two dividing ny, the block
 // of rpb LPR >= 32 threads at most max(128, LPR)); false where it does not
 // apply.
-template <typename T> bool rhs_row_geometry(const GridDev &g, int &cpl, int &lpr, int &rpb) {
+template <typename T>
+bool rhs_row_geometry(const GridDev &g, int &cpl, int &lpr, int &rpb, int prefer = 0) {
     // 4 cells per lane (2 doubles or 4 floats: fewer registers, more warps);
-    // floats on rows wider than 256 cells take 8
+    // floats on rows wider than 256 cells take 8; `prefer` (4, or 8 in
+    // single precision, from the grid's autotuner) overrides
     cpl = (sizeof(T) == 4 && g.nx > 256) ? 8 : 4;
+    if (prefer == 4 || (prefer == 8 && sizeof(T) == 4)) cpl = prefer;
     if (g.nx % cpl) return false;
     lpr = g.nx / cpl;
     if (lpr < 4 || lpr > 256 || (lpr & (lpr - 1))) return false;
@@ -1100,7 +1103,7 @@ bool rhs_row_dispatch(const GridDev &g, const Fields<T> &F, Work<T> &W, const St
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
     int cpl = 0, lpr = 0, rpb = 0;
-    if (rhs_row_geometry<T>(g, cpl, lpr, rpb) &&
+    if (rhs_row_geometry<T>(g, cpl, lpr, rpb, W.rhs_cpl) &&
         (cpl == 4 ? rhs_row_dispatch<T, 4>(g, F, W, sc, a, lpr, rpb, st)
                   : rhs_row_dispatch<T, sizeof(T) == 4 ? 8 : 4>(g, F, W, sc, a, lpr, rpb, st)))
         return;
@@ -1115,6 +1118,18 @@ template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Wo
     else if (W.chunk_x <= 16) rhs_x_L<T, 16>(g, F, W, sc, a, st);
     else if (W.chunk_x <= 32) rhs_x_L<T, 32>(g, F, W, sc, a, st);
     else rhs_x_L<T, 64>(g, F, W, sc, a, st);
+}
+
+int rhs_cpl_candidates(const GridDev &g, int elem_size, int *out, int cap) {
+    int n = 0;
+    const int opts[2] = {4, 8};
+    for (int c : opts) {
+        int cpl = 0, lpr = 0, rpb = 0;
+        const bool ok = elem_size == 4 ? rhs_row_geometry<float>(g, cpl, lpr, rpb, c)
+                                       : rhs_row_geometry<double>(g, cpl, lpr, rpb, c);
+        if (ok && cpl == c && n < cap) out[n++] = c;
+    }
+    return n;
 }
 
 template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T> &W) {

@@ -46,7 +46,34 @@ template <typename T> struct Work {
     int pz_poisson;          // chunks per z line in the Poisson solve
     int zl_lpl, zl_e;        // lane-resident z solve: lanes per mode line and
                              // rows per lane (0: not used)
+    int rhs_cpl;             // cells per lane of the row-resident RHS (0: by
+                             // row width)
+    int proj_mult;           // row passes per thread of the projection (0: 4)
+    int ry_rfft;             // rows per block of the forward x transform
+    int tkx_fft;             // kx columns per block of the two-pass y
+                             // transform
 };
+
+// Launch schedule of a grid: the tile shapes and solver splits that its
+// tunable kernels run with.  Every candidate value of a field computes the
+// same quantities with the same operations, grouped differently, so results
+// agree to rounding and the choice only moves time.  0 marks a field whose
+// kernel does not apply to the grid.
+struct Schedule {
+    int rhs_cpl;    // RHS + x sweep: cells per lane of the row-resident kernel
+    int zl_lpl;     // z Poisson: lanes per mode line (the reduction across
+                    // lanes); zl_e: rows per lane (the elimination in a lane)
+    int zl_e;
+    int ry_rfft;    // forward x transform: grid rows per block
+    int tkx_fft;    // y transforms: kx columns per block
+    int proj_mult;  // projection: row passes per thread
+};
+enum ScheduleKnob { SK_RHS, SK_ZL, SK_RFFT, SK_FFTY, SK_PROJ, SK_COUNT };
+// the values knob k may take on this grid (pairs (lanes, rows) for SK_ZL,
+// single values in out[i][0] otherwise), the default first; their count
+template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*out)[2], int cap);
+template <typename T> Schedule schedule_of(const GridDev &g, const Work<T> &W);
+template <typename T> void apply_schedule(Work<T> &W, const Schedule &s);
 
 struct StepArgs {
     double re, dt, cfl, gamma, rho;
@@ -139,5 +166,11 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
 // transform and z solve, chunks per z line of the z solve (sets ry_fft, tkx,
 // pz_poisson)
 template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W);
+// the (lanes per line, rows per lane) splits of the lane-resident z solve
+// that apply to this grid, in order of preference (at most cap); their count
+int zl_candidates(const GridDev &g, int elem_size, int (*out)[2], int cap);
+// cells per lane of the row-resident RHS that apply to this grid (at most
+// cap); their count
+int rhs_cpl_candidates(const GridDev &g, int elem_size, int *out, int cap);
 
 }  // namespace fsei

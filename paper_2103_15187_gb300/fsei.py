@@ -26,7 +26,10 @@ FLAG_NONFINITE, FLAG_CFL = 1, 2
 EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
            "fsei_step", "fsei_poisson_solve", "fsei_adjoint_step", "fsei_batch_create",
            "fsei_batch_destroy", "fsei_batch_size", "fsei_batch_step", "fsei_set_kernel_timing",
-           "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version")
+           "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version",
+           "fsei_grid_autotune", "fsei_grid_get_schedule", "fsei_grid_set_schedule",
+           "fsei_batch_autotune")
+FSEI_TUNE_FORCE = 1
 
 
 class FseiUnavailable(RuntimeError):
@@ -64,6 +67,18 @@ class StepStats(ctypes.Structure):
     _fields_ = [("dt_used", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("max_div", ctypes.c_double), ("kinetic_energy", ctypes.c_double),
                 ("flags", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("rhs_cells_per_lane", ctypes.c_int32),
+                ("poisson_lanes_per_line", ctypes.c_int32),
+                ("poisson_rows_per_lane", ctypes.c_int32),
+                ("rfft_rows_per_block", ctypes.c_int32),
+                ("ffty_columns_per_block", ctypes.c_int32),
+                ("project_passes_per_thread", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -116,6 +131,14 @@ def load(path=LIB_PATH):
     lib.fsei_kernel_times.restype = ctypes.c_int32
     lib.fsei_kernel_name.argtypes = [ctypes.c_int32]
     lib.fsei_kernel_name.restype = ctypes.c_char_p
+    lib.fsei_grid_autotune.argtypes = [vp, ctypes.c_int32, vp, ctypes.POINTER(Schedule)]
+    lib.fsei_grid_autotune.restype = ctypes.c_int
+    lib.fsei_grid_get_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
+    lib.fsei_grid_get_schedule.restype = ctypes.c_int
+    lib.fsei_grid_set_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
+    lib.fsei_grid_set_schedule.restype = ctypes.c_int
+    lib.fsei_batch_autotune.argtypes = [vp, ctypes.c_int32, vp]
+    lib.fsei_batch_autotune.restype = ctypes.c_int
     lib.fsei_last_error.argtypes = []
     lib.fsei_last_error.restype = ctypes.c_char_p
     lib.fsei_version.argtypes = []
@@ -168,6 +191,29 @@ class Grid:
 
     def workspace_bytes(self):
         return load().fsei_grid_workspace_bytes(self.handle)
+
+    def autotune(self, force=False, stream=None):
+        """fsei_grid_autotune: pick the launch schedule by measurement (or
+        take the one this process holds for the shape); returns it."""
+        out = Schedule()
+        _check(load().fsei_grid_autotune(self.handle, FSEI_TUNE_FORCE if force else 0,
+                                         _stream_handle(stream), ctypes.byref(out)))
+        return out.as_dict()
+
+    @property
+    def schedule(self):
+        """fsei_grid_get_schedule as a dict."""
+        out = Schedule()
+        _check(load().fsei_grid_get_schedule(self.handle, ctypes.byref(out)))
+        return out.as_dict()
+
+    def set_schedule(self, sched):
+        """fsei_grid_set_schedule from a dict (missing keys keep their
+        current values)."""
+        cur = self.schedule
+        cur.update(sched)
+        s = Schedule(**cur)
+        _check(load().fsei_grid_set_schedule(self.handle, ctypes.byref(s)))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -251,6 +297,11 @@ class Batch:
         _check(lib.fsei_batch_create(arr, len(boxes), ctypes.byref(h)))
         self.handle = h
         self.n = len(boxes)
+
+    def autotune(self, force=False, stream=None):
+        """fsei_batch_autotune: one measured schedule per distinct box shape."""
+        _check(load().fsei_batch_autotune(self.handle, FSEI_TUNE_FORCE if force else 0,
+                                          _stream_handle(stream)))
 
     def close(self):
         if getattr(self, "handle", None):
