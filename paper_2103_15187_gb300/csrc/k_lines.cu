@@ -188,8 +188,10 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
 
 // y sweep of plane k: q = (I - beta L_y)^-1 q for the three components.
 // EXACT: every chunk holds L unknowns (ny = L P), no per-unknown guards.
+// Single precision, L <= 16: 5 blocks per SM (48 registers, no spills;
+// 256^3: 84 -> 79 us against 4 blocks).
 template <typename T, int L, bool EXACT>
-__global__ void __launch_bounds__(256, L <= 16 ? (sizeof(T) == 4 ? 4 : 2) : (sizeof(T) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(256, L <= 16 ? (sizeof(T) == 4 ? 5 : 2) : (sizeof(T) == 4 ? 2 : 1))
 k_sweep_y_uni(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
               const StepScalars *sc, int P, int tx) {
     extern __shared__ __align__(16) unsigned char smraw[];
