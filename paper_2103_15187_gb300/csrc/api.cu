@@ -413,13 +413,16 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
     F.fx = (const T *)fx; F.fy = (const T *)fy; F.fz = (const T *)fz;
     const GridDev &g = G->g;
     KernelTimer &tm = G->timer;
+    // programmatic dependent launches between the step's kernels, except
+    // while event pairs time each kernel or a graph is being captured
+    W.pdl = (!tm.on && !tm.check) ? 1 : 0;
     if (a.cfl > 0.0 && with_speed) {
         cudaMemsetAsync(&G->sc->speed_next, 0, sizeof(unsigned long long), st);
         tm.run(KK_SPEED, st, [&] { launch_speed<T>(g, F.u, F.v, F.w, G->sc, st); });
     }
     for (int n = 0; n < nsteps; ++n) {
         const int euler = (n == 0 && !s->have_prev_h) ? 1 : 0;
-        tm.run(KK_BEGIN, st, [&] { launch_step_scalars(g, G->sc, a, euler, st); });
+        tm.run(KK_BEGIN, st, [&] { launch_step_scalars(g, G->sc, a, euler, st, W.pdl != 0); });
         // the z-sweep plans depend on this step's beta and are first read by
         // the z sweep: they run on the side stream beside rhs_x and sweep_y
         const Overlap &op = G->ov_plans;
@@ -438,6 +441,7 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
         tm.run(KK_IRFFT_X, st, [&] { launch_irfft_x<T>(g, W, W.phi, st); });
         tm.run(KK_PROJECT, st, [&] { launch_project<T>(g, F, W, G->sc, st); });
     }
+    W.pdl = 0;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FSEI_E_CUDA, "step launch: %s", cudaGetErrorString(e));
     return FSEI_OK;

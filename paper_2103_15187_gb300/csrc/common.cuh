@@ -9,6 +9,16 @@
 #define FSEI_HD __host__ __device__ __forceinline__
 #define FSEI_D __device__ __forceinline__
 
+// Programmatic dependent launch (griddepcontrol): a kernel launched with the
+// programmatic-serialisation attribute may be scheduled while the previous
+// kernel of its stream finishes.  pdl_wait() blocks until that kernel has
+// completed and its memory operations are visible (a no-op for an ordinary
+// launch); the hot kernels call it before any global memory access.
+// pdl_trigger() allows the next such kernel to be scheduled once every block
+// of this one has called it.
+FSEI_D void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+FSEI_D void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 namespace fsei {
 
 // ----------------------------------------------------------- complex -------

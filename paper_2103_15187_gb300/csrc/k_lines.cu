@@ -174,6 +174,8 @@ __global__ void __launch_bounds__(L <= 16 ? 256 : 512, L <= 16 ? (sizeof(T) == 4
 k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
             T *__restrict__ q2, TriPlan<T> pa, TriPlan<T> pb, int tx) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();
+    pdl_trigger();
     T *sm = reinterpret_cast<T *>(smraw);
     // the component of this block picks its plan; lines of L P unknowns take
     // the guard-free path
@@ -195,6 +197,8 @@ __global__ void __launch_bounds__(256, L <= 16 ? (sizeof(T) == 4 ? 5 : 2) : (siz
 k_sweep_y_uni(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
               const StepScalars *sc, int P, int tx) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();
+    pdl_trigger();
     T *car = reinterpret_cast<T *>(smraw);
     const int nx = g.nx, ny = g.ny;
     const int nxt = (nx + tx - 1) / tx;
@@ -231,8 +235,8 @@ void launch_reg(const GridDev &g, const Fields<T> &F, Work<T> &W, const TriPlan<
     const size_t smem = sizeof(T) * ((size_t)tx * (2 * Pmax + 1) + plan_stage_words(nmax, Pmax));
     const int nxt = (g.nx + tx - 1) / tx;
     const int outer = DIR == 1 ? g.nz : g.ny;
-    k_sweep_reg<T, L, DIR, MODE><<<3 * outer * nxt, threads, smem, st>>>(
-        g, F, W.q0, W.q1, W.q2, pa, pb, tx);
+    launch_k(W.pdl != 0, k_sweep_reg<T, L, DIR, MODE>, dim3(3 * outer * nxt), dim3(threads), smem,
+             st, g, F, W.q0, W.q1, W.q2, pa, pb, tx);
 }
 
 template <typename T, int DIR, int MODE>
@@ -283,11 +287,11 @@ void launch_y_uni(const GridDev &g, Work<T> &W, const StepScalars *sc, cudaStrea
     const int threads = ((tx * P + 31) / 32) * 32;
     const size_t sm = 2 * sizeof(T) * tx * P;
     if (g.ny == L * P)
-        k_sweep_y_uni<T, L, true><<<3 * g.nz * nxt, threads, sm, st>>>(g, W.q0, W.q1, W.q2, sc,
-                                                                       P, tx);
+        launch_k(W.pdl != 0, k_sweep_y_uni<T, L, true>, dim3(3 * g.nz * nxt), dim3(threads), sm, st,
+                 g, W.q0, W.q1, W.q2, sc, P, tx);
     else
-        k_sweep_y_uni<T, L, false><<<3 * g.nz * nxt, threads, sm, st>>>(g, W.q0, W.q1, W.q2, sc,
-                                                                        P, tx);
+        launch_k(W.pdl != 0, k_sweep_y_uni<T, L, false>, dim3(3 * g.nz * nxt), dim3(threads), sm,
+                 st, g, W.q0, W.q1, W.q2, sc, P, tx);
 }
 
 template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, const StepScalars *sc,

@@ -63,6 +63,8 @@ k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
          const cplx<T> *__restrict__ twx, const cplx<T> *__restrict__ twpost, FftPlanDev fp,
          const StepScalars *sc) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();
+    pdl_trigger();
     const int nx = g.nx, ny = g.ny, nz = g.nz, mx = g.mx, sk = g.sk;
     const int ls = fft_x_ls(mx);
     const int bls = fft_x_bls(mx);
@@ -190,6 +192,8 @@ template <typename T, int SIGN, int N1, int N2>
 __global__ void __launch_bounds__(256)
 k_fft_y_2p(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ twy, int tkx) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();
+    pdl_trigger();
     constexpr int N = N1 * N2;
     const int sk = g.sk;
     cplx<T> *B = reinterpret_cast<cplx<T> *>(smraw);   // [N][tkx]
@@ -548,6 +552,8 @@ k_poisson_zl(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
              const double *xc, const double *xz, const double *xs, double dscale, int compat,
              double zlen) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();
+    pdl_trigger();
     if ((int)blockIdx.x < n_exact) {
         if (threadIdx.x < 32)
             exact_mode_solve<T>(g, spec, blockIdx.x, modes, xa, xm, xc, xz, xs, dscale, compat,
@@ -801,6 +807,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 k_irfft_x_2p(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
              const cplx<T> *__restrict__ twx, const cplx<T> *__restrict__ twpost) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_wait();
+    pdl_trigger();
     constexpr int MX = N1 * N2;
     constexpr int BL = N2 * (N1 + 1);
     const int nx = g.nx, ny = g.ny, sk = g.sk;
@@ -941,8 +949,8 @@ template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W) {
 template <typename T, int MODE, int RY>
 void rfft_x_ry(const GridDev &g, Work<T> &W, const StepScalars *sc, const T *src, cudaStream_t st) {
     const int blocks = g.nz * (g.ny / RY);
-    k_rfft_x<T, MODE, RY><<<blocks, 256, smem_rfft_x<T>(g, RY), st>>>(
-        g, W.q0, W.q1, W.q2, src, W.spec, W.twx, W.twpost, W.fpx, sc);
+    launch_k(W.pdl != 0, k_rfft_x<T, MODE, RY>, dim3(blocks), dim3(256), smem_rfft_x<T>(g, RY), st,
+             g, W.q0, W.q1, W.q2, src, W.spec, W.twx, W.twpost, W.fpx, sc);
 }
 
 template <typename T, int MODE>
@@ -971,14 +979,17 @@ bool fft_y_2p_launch(const GridDev &g, Work<T> &W, cudaStream_t st) {
     const int blocks = g.nz * (g.sk / tk);
     const size_t sm = sizeof(cplx<T>) * ((size_t)g.ny * tk + g.ny);
     const int thr = tk * n1;
+    void (*k)(GridDev, cplx<T> *, const cplx<T> *, int) = nullptr;
     switch (g.ny) {
-    case 16: k_fft_y_2p<T, SIGN, 4, 4><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
-    case 32: k_fft_y_2p<T, SIGN, 8, 4><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
-    case 64: k_fft_y_2p<T, SIGN, 8, 8><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
-    case 128: k_fft_y_2p<T, SIGN, 16, 8><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
-    case 256: k_fft_y_2p<T, SIGN, 16, 16><<<blocks, thr, sm, st>>>(g, W.spec, W.twy, tk); return true;
+    case 16: k = k_fft_y_2p<T, SIGN, 4, 4>; break;
+    case 32: k = k_fft_y_2p<T, SIGN, 8, 4>; break;
+    case 64: k = k_fft_y_2p<T, SIGN, 8, 8>; break;
+    case 128: k = k_fft_y_2p<T, SIGN, 16, 8>; break;
+    case 256: k = k_fft_y_2p<T, SIGN, 16, 16>; break;
     default: return false;
     }
+    launch_k(W.pdl != 0, k, dim3(blocks), dim3(thr), sm, st, g, W.spec, W.twy, tk);
+    return true;
 }
 
 template <typename T> void launch_fft_y(const GridDev &g, Work<T> &W, int inverse, cudaStream_t st) {
@@ -1006,9 +1017,9 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
         const T tsc = T(scale);
 #define FSEI_ZL(E_, L_)                                                                        \
     if (W.zl_e == E_ && W.zl_lpl == L_) {                                                      \
-        k_poisson_zl<T, E_, L_><<<grid, 256, sm, st>>>(g, W.spec, W.lamx, W.lamy, W.exact, tsc, \
-                                                       W.n_nzm, W.nzm, W.xa, W.xm, W.xc, W.xz,  \
-                                                       W.xs, scale, compat, W.zlen);            \
+        launch_k(W.pdl != 0, k_poisson_zl<T, E_, L_>, dim3(grid), dim3(256), sm, st, g, W.spec,  \
+                 W.lamx, W.lamy, W.exact, tsc, W.n_nzm, W.nzm, W.xa, W.xm, W.xc, W.xz, W.xs,   \
+                 scale, compat, W.zlen);                                                      \
         return;                                                                                \
     }
         FSEI_ZL(4, 16) FSEI_ZL(6, 16) FSEI_ZL(8, 16) FSEI_ZL(8, 32)
@@ -1045,14 +1056,17 @@ bool irfft_x_2p_launch(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
     const int blocks = g.nz * (g.ny / RY);
     const size_t sm = sizeof(cplx<T>) * ((size_t)RY * (g.mx / n1) * (n1 + 1) + 2 * g.mx + 1);
     const int thr = RY * n1;
+    void (*k)(GridDev, const cplx<T> *, T *, const cplx<T> *, const cplx<T> *) = nullptr;
     switch (g.mx) {
-    case 16: k_irfft_x_2p<T, RY, 4, 4><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
-    case 32: k_irfft_x_2p<T, RY, 8, 4><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
-    case 64: k_irfft_x_2p<T, RY, 8, 8><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
-    case 128: k_irfft_x_2p<T, RY, 16, 8><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
-    case 256: k_irfft_x_2p<T, RY, 16, 16><<<blocks, thr, sm, st>>>(g, W.spec, dst, W.twx, W.twpost); return true;
+    case 16: k = k_irfft_x_2p<T, RY, 4, 4>; break;
+    case 32: k = k_irfft_x_2p<T, RY, 8, 4>; break;
+    case 64: k = k_irfft_x_2p<T, RY, 8, 8>; break;
+    case 128: k = k_irfft_x_2p<T, RY, 16, 8>; break;
+    case 256: k = k_irfft_x_2p<T, RY, 16, 16>; break;
     default: return false;
     }
+    launch_k(W.pdl != 0, k, dim3(blocks), dim3(thr), sm, st, g, W.spec, dst, W.twx, W.twpost);
+    return true;
 }
 
 template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {

@@ -126,6 +126,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_project_vec(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict__ q1,
               const T *__restrict__ q2, const T *__restrict__ phi, StepScalars *sc, int rows) {
+    pdl_wait();
+    pdl_trigger();
     using V = Vec16<T>;
     constexpr int W = V::W;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -267,8 +269,8 @@ template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, 
         int rows = 1;
         for (int r = mult * rpp; r >= 1; --r)
             if (g.ny % r == 0) { rows = r; break; }
-        k_project_vec<T><<<g.nz * (g.ny / rows), 128, 0, st>>>(g, F, W.q0, W.q1, W.q2, W.phi,
-                                                               sc, rows);
+        launch_k(W.pdl != 0, k_project_vec<T>, dim3(g.nz * (g.ny / rows)), dim3(128), 0, st, g, F,
+                 W.q0, W.q1, W.q2, W.phi, sc, rows);
         return;
     }
     const int rows = project_rows(g);

@@ -139,6 +139,8 @@ __device__ void uni_factors(double r, double &alpha, double &cinv) {
 // Lane 0 of each warp stores.
 __global__ void __launch_bounds__(96) k_scalars(StepScalars *sc, StepArgs a, int euler,
                                                 double idx2, double idy2) {
+    pdl_wait();
+    pdl_trigger();
     const int wid = threadIdx.x >> 5;
     const bool lead = (threadIdx.x & 31) == 0;
     const unsigned long long spd = sc->speed_next;
@@ -923,6 +925,8 @@ __global__ void __launch_bounds__(LPR > 128 ? LPR : 128)
 k_rhs_x_row(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
             T *__restrict__ q2, const StepScalars *sc, int rpb, T fc0, T fc1, T fc2, T inv_re) {
     __shared__ T xs[2 * 3 * (LPR > 128 ? LPR : 128) / 32];
+    pdl_wait();
+    pdl_trigger();
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int nby = ny / rpb;
     const int k = blockIdx.x / nby;
@@ -980,8 +984,8 @@ template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v
 }
 
 void launch_step_scalars(const GridDev &g, StepScalars *sc, const StepArgs &a, int euler,
-                         cudaStream_t st) {
-    k_scalars<<<1, 96, 0, st>>>(sc, a, euler, g.idx2, g.idy2);
+                         cudaStream_t st, bool pdl) {
+    launch_k(pdl, k_scalars, dim3(1), dim3(96), 0, st, sc, a, euler, g.idx2, g.idy2);
 }
 
 template <typename T> void launch_step_plans(const GridDev &g, Work<T> &W, const StepScalars *sc,
@@ -1080,9 +1084,9 @@ bool rhs_row_geometry(const GridDev &g, int &cpl, int &lpr, int &rpb, int prefer
 template <typename T, int CPL, int LPR>
 void rhs_row_launch(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
                     const StepArgs &a, int rpb, cudaStream_t st) {
-    k_rhs_x_row<T, CPL, LPR><<<g.nz * (g.ny / rpb), rpb * LPR, 0, st>>>(
-        g, F, W.q0, W.q1, W.q2, sc, rpb, T(a.fconst[0]), T(a.fconst[1]), T(a.fconst[2]),
-        T(1.0 / a.re));
+    launch_k(W.pdl != 0, k_rhs_x_row<T, CPL, LPR>, dim3(g.nz * (g.ny / rpb)), dim3(rpb * LPR), 0,
+             st, g, F, W.q0, W.q1, W.q2, sc, rpb, T(a.fconst[0]), T(a.fconst[1]),
+             T(a.fconst[2]), T(1.0 / a.re));
 }
 
 template <typename T, int CPL>

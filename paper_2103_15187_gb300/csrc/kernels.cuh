@@ -1,6 +1,8 @@
 // Launch interface between the host library (api.cu) and the kernels of one
 // fractional step.  Internal to libfsei.so.
 #pragma once
+#include <utility>
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -52,6 +54,8 @@ template <typename T> struct Work {
     int ry_rfft;             // rows per block of the forward x transform
     int tkx_fft;             // kx columns per block of the two-pass y
                              // transform
+    int pdl;                 // launch the step's kernels as programmatic
+                             // dependent launches (launch_k)
 };
 
 // Launch schedule of a grid: the tile shapes and solver splits that its
@@ -88,7 +92,7 @@ template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepS
 // weights, reset reductions), then the z-sweep plans that depend on beta
 // (needed from the z sweep on, so they may run beside the RHS and y sweep)
 void launch_step_scalars(const GridDev &g, StepScalars *sc, const StepArgs &a, int euler,
-                         cudaStream_t st);
+                         cudaStream_t st, bool pdl = false);
 template <typename T> void launch_step_plans(const GridDev &g, Work<T> &W, const StepScalars *sc,
                                              cudaStream_t st);
 
@@ -127,6 +131,31 @@ template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, 
                                           StepScalars *sc, cudaStream_t st);
 
 // Largest dynamic shared memory a block may opt into on the current device.
+// Launch of kernel k on st; with pdl, as a programmatic dependent launch:
+// the grid may be scheduled while the stream's previous kernel finishes (the
+// kernel's pdl_wait() holds its blocks until that kernel has completed), so
+// the launch latency and the block ramp-up overlap the predecessor's last
+// wave.  The launch error, if any, is left for cudaGetLastError.
+template <typename... KP, typename... A>
+inline void launch_k(bool pdl, void (*k)(KP...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, A &&...args) {
+    if (pdl) {
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...) == cudaSuccess) return;
+        cudaGetLastError();   // the ordinary launch below reports the error
+    }
+    k<<<grid, block, smem, st>>>(std::forward<A>(args)...);
+}
+
 // Every kernel's MaxDynamicSharedMemorySize attribute is raised to it: the
 // attribute is per kernel and process-wide, so a value sized for one grid
 // would cap the launches of another grid of the same kernel.
