@@ -147,7 +147,7 @@ int64_t fsei_grid_workspace_bytes(fsei_grid grid);
  * results agree to rounding and only the time changes.  0 marks a field
  * whose kernel does not apply to the grid's extents.
  *   rhs_cells_per_lane: RHS + x sweep (Eq. 3, Sec. 3.1), cells of a grid row
- *     per lane of the row-resident kernel (4, or 8 in FSEI_MIXED);
+ *     per lane of the row-resident kernel (4, or 2 or 8 in FSEI_MIXED);
  *   poisson_lanes_per_line, poisson_rows_per_lane: z tridiagonal solve of
  *     each Fourier mode (Sec. 3.2): lanes that share a line (reduction
  *     across lanes) and rows each lane eliminates on its own; their product

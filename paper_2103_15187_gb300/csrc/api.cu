@@ -413,9 +413,10 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
     F.fx = (const T *)fx; F.fy = (const T *)fy; F.fz = (const T *)fz;
     const GridDev &g = G->g;
     KernelTimer &tm = G->timer;
-    // programmatic dependent launches between the step's kernels, except
-    // while event pairs time each kernel or a graph is being captured
-    W.pdl = (!tm.on && !tm.check) ? 1 : 0;
+    // programmatic dependent launches between the step's kernels (in a
+    // captured graph they become programmatic edges), except while event
+    // pairs time each kernel
+    W.pdl = !tm.on ? 1 : 0;
     if (a.cfl > 0.0 && with_speed) {
         cudaMemsetAsync(&G->sc->speed_next, 0, sizeof(unsigned long long), st);
         tm.run(KK_SPEED, st, [&] { launch_speed<T>(g, F.u, F.v, F.w, G->sc, st); });

@@ -1148,8 +1148,8 @@ template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*
     case SK_RHS: {
         // the default (8 cells per lane in single precision on rows wider
         // than 256 cells, 4 otherwise) first
-        int c[2];
-        const int m = rhs_cpl_candidates(g, tsz, c, 2);
+        int c[3];
+        const int m = rhs_cpl_candidates(g, tsz, c, 3);
         const int def = (tsz == 4 && g.nx > 256) ? 8 : 4;
         for (int i = 0; i < m; ++i)
             if (c[i] == def) put(c[i], 0);

@@ -716,27 +716,42 @@ k_rhs_x_tile(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
 }
 
 // Helpers of the row-resident right-hand side (k_rhs_x_row below): CPL
-// consecutive values of a row as 16-byte vectors, from and to global
-// memory (neighbour rows are served by the caches).
+// consecutive values of a row as 16-byte vectors (one 8-byte vector when the
+// lane holds 8 bytes), from and to global memory (neighbour rows are served
+// by the caches).
+template <typename T> struct alignas(8) Vec8 { T v[8 / sizeof(T)]; };
 template <typename T, int CPL>
 FSEI_D void ldrow(T (&a)[CPL], const T *p) {
-    constexpr int VW = 16 / (int)sizeof(T);
+    if constexpr (CPL * sizeof(T) == 8) {
+        const Vec8<T> v = *reinterpret_cast<const Vec8<T> *>(p);
 #pragma unroll
-    for (int c = 0; c < CPL / VW; ++c) {
-        const Vec16<T> v = *reinterpret_cast<const Vec16<T> *>(p + c * VW);
+        for (int e = 0; e < CPL; ++e) a[e] = v.v[e];
+    } else {
+        constexpr int VW = 16 / (int)sizeof(T);
 #pragma unroll
-        for (int e = 0; e < VW; ++e) a[c * VW + e] = v.v[e];
+        for (int c = 0; c < CPL / VW; ++c) {
+            const Vec16<T> v = *reinterpret_cast<const Vec16<T> *>(p + c * VW);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) a[c * VW + e] = v.v[e];
+        }
     }
 }
 template <typename T, int CPL>
 FSEI_D void strow(T *p, const T (&a)[CPL]) {
-    constexpr int VW = 16 / (int)sizeof(T);
+    if constexpr (CPL * sizeof(T) == 8) {
+        Vec8<T> v;
 #pragma unroll
-    for (int c = 0; c < CPL / VW; ++c) {
-        Vec16<T> v;
+        for (int e = 0; e < CPL; ++e) v.v[e] = a[e];
+        *reinterpret_cast<Vec8<T> *>(p) = v;
+    } else {
+        constexpr int VW = 16 / (int)sizeof(T);
 #pragma unroll
-        for (int e = 0; e < VW; ++e) v.v[e] = a[c * VW + e];
-        *reinterpret_cast<Vec16<T> *>(p + c * VW) = v;
+        for (int c = 0; c < CPL / VW; ++c) {
+            Vec16<T> v;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) v.v[e] = a[c * VW + e];
+            *reinterpret_cast<Vec16<T> *>(p + c * VW) = v;
+        }
     }
 }
 // value of the periodic x neighbour left (LEFT = 1) of this lane's first
@@ -918,8 +933,9 @@ FSEI_D void rhs_row_body(const GridDev &g, const Fields<T> &F, const RowSet<T> &
 // Row-resident right-hand side + x sweep reading its stencil rows straight
 // from global memory: the LPR lanes of a warp segment (or of LPR / 32
 // warps) own one x row (j, k), lane r cells CPL r .. CPL r + CPL - 1, read
-// as 16-byte vectors (neighbour rows are served by the caches).  Needs nx =
-// LPR CPL, CPL a multiple of the 16-byte vector, ny a multiple of rpb.
+// as 16-byte vectors or one 8-byte vector (neighbour rows are served by the
+// caches).  Needs nx = LPR CPL, CPL values spanning 8 bytes or a multiple of
+// 16, ny a multiple of rpb.
 template <typename T, int CPL, int LPR>
 __global__ void __launch_bounds__(LPR > 128 ? LPR : 128)
 k_rhs_x_row(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
@@ -1060,18 +1076,17 @@ void rhs_tile_ry(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepSca
     else rhs_tile_L<T, 64, RY>(g, F, W, sc, a, P, smem, st);
 }
 
-// Geometry of the row-resident right-hand side: CPL cells per lane (8 in
-// single, 4 in double precision), LPR = nx / CPL lanes per row (a power of
-// two, 4 .. 256), rows per block rpb (a power of two dividing ny, the block
-// of rpb LPR >= 32 threads at most max(128, LPR)); false where it does not
-// apply.
+// Geometry of the row-resident right-hand side: CPL cells per lane, LPR =
+// nx / CPL lanes per row (a power of two, 4 .. 256), rows per block rpb (a
+// power of two dividing ny, the block of rpb LPR >= 32 threads at most
+// max(128, LPR)); false where it does not apply.
 template <typename T>
 bool rhs_row_geometry(const GridDev &g, int &cpl, int &lpr, int &rpb, int prefer = 0) {
     // 4 cells per lane (2 doubles or 4 floats: fewer registers, more warps);
-    // floats on rows wider than 256 cells take 8; `prefer` (4, or 8 in
+    // floats on rows wider than 256 cells take 8; `prefer` (4, or 2 or 8 in
     // single precision, from the grid's autotuner) overrides
     cpl = (sizeof(T) == 4 && g.nx > 256) ? 8 : 4;
-    if (prefer == 4 || (prefer == 8 && sizeof(T) == 4)) cpl = prefer;
+    if (prefer == 4 || ((prefer == 8 || prefer == 2) && sizeof(T) == 4)) cpl = prefer;
     if (g.nx % cpl) return false;
     lpr = g.nx / cpl;
     if (lpr < 4 || lpr > 256 || (lpr & (lpr - 1))) return false;
@@ -1108,8 +1123,9 @@ template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Wo
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
     int cpl = 0, lpr = 0, rpb = 0;
     if (rhs_row_geometry<T>(g, cpl, lpr, rpb, W.rhs_cpl) &&
-        (cpl == 4 ? rhs_row_dispatch<T, 4>(g, F, W, sc, a, lpr, rpb, st)
-                  : rhs_row_dispatch<T, sizeof(T) == 4 ? 8 : 4>(g, F, W, sc, a, lpr, rpb, st)))
+        (cpl == 4   ? rhs_row_dispatch<T, 4>(g, F, W, sc, a, lpr, rpb, st)
+         : cpl == 8 ? rhs_row_dispatch<T, sizeof(T) == 4 ? 8 : 4>(g, F, W, sc, a, lpr, rpb, st)
+                    : rhs_row_dispatch<T, sizeof(T) == 4 ? 2 : 4>(g, F, W, sc, a, lpr, rpb, st)))
         return;
     int RY = 0, P = 0;
     size_t smem = 0;
@@ -1126,7 +1142,7 @@ template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Wo
 
 int rhs_cpl_candidates(const GridDev &g, int elem_size, int *out, int cap) {
     int n = 0;
-    const int opts[2] = {4, 8};
+    const int opts[3] = {4, 8, 2};
     for (int c : opts) {
         int cpl = 0, lpr = 0, rpb = 0;
         const bool ok = elem_size == 4 ? rhs_row_geometry<float>(g, cpl, lpr, rpb, c)
@@ -1173,6 +1189,14 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 64>);
     cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 128>);
     cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 256>);
+    constexpr int C2 = sizeof(T) == 4 ? 2 : 4;
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 4>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 8>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 16>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 32>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 64>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 128>);
+    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 256>);
 }
 
 #define FSEI_INST(T)                                                                           \

@@ -48,8 +48,8 @@ template <typename T> struct Work {
     int pz_poisson;          // chunks per z line in the Poisson solve
     int zl_lpl, zl_e;        // lane-resident z solve: lanes per mode line and
                              // rows per lane (0: not used)
-    int rhs_cpl;             // cells per lane of the row-resident RHS (0: by
-                             // row width)
+    int rhs_cpl;             // cells per lane of the row-resident RHS (2, 4
+                             // or 8; 0: by row width)
     int proj_mult;           // row passes per thread of the projection (0: 4)
     int ry_rfft;             // rows per block of the forward x transform
     int tkx_fft;             // kx columns per block of the two-pass y

@@ -22,7 +22,7 @@ MIXED_VEL_TOL = 1e-5
 
 # values tried per field: the admissible ones and some that never are
 TRIALS = {
-    "rhs_cells_per_lane": [4, 8, 5, 16],
+    "rhs_cells_per_lane": [4, 8, 2, 5, 16],
     "poisson": [(16, 16), (32, 8), (16, 8), (8, 32), (64, 4)],
     "rfft_rows_per_block": [1, 2, 4, 8, 16, 3, 32],
     "ffty_columns_per_block": [2, 4, 8, 16, 32, 3, 64],
