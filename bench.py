@@ -59,9 +59,18 @@ def algorithmic_words(nx, ny, nz, with_force):
 # of the dominant kernel, from an ncu --set full capture of the 256^3
 # channel workload; reported only for that workload and that kernel build
 MEASURED_TRAFFIC = {
-    "rhs_x (RHS + x sweep)": {"bytes": 826.361e6, "cells": 256 ** 3,
+    "rhs_x (RHS + x sweep)": {"bytes": 826.5e6, "cells": 256 ** 3,
                               "kernel": "k_rhs_x_row<float, 4, 64>"},
 }
+
+# FP64 instructions of one FP64 step per cell (DFMA + DADD + DMUL thread
+# instructions, the CFL pre-pass excluded), from one ncu capture of the FP64
+# step on a 128^3 channel (the count per cell does not depend on the size).
+# The FP64 step is bound by the FP64 pipe: its peak is 2 FP64 thread
+# instructions per clock per SM (1.25 TFLOP/s of DFMA nominal), times 152
+# SMs at the 2070 MHz maximum clock.
+FP64_INSTR_PER_CELL = 342.6
+FP64_PEAK_GINST = 2 * 152 * 2.070
 
 
 def measured_peaks():
@@ -532,9 +541,17 @@ def main():
     }
     if "fp64" in results:
         fres = results["fp64"][0]
+        ginst = FP64_INSTR_PER_CELL * fres["mcups"] / max(1, args.gpus) / 1e3
         line["fp64"] = {"value": round(fres["mcups"], 2), "unit": "Mcell-updates/s",
                         "ms_per_step": round(fres["ms_per_step"], 4),
-                        "mixed_speedup": round(mres["mcups"] / fres["mcups"], 3)}
+                        "mixed_speedup": round(mres["mcups"] / fres["mcups"], 3),
+                        "alu": {"bound": "alu", "achieved": round(ginst, 1),
+                                "peak": round(FP64_PEAK_GINST, 1),
+                                "unit": "G FP64 thread-instructions/s",
+                                "frac": round(ginst / FP64_PEAK_GINST, 4),
+                                "instr_per_cell": FP64_INSTR_PER_CELL,
+                                "peak_source": "derived: 2 FP64 lanes/clk/SM x 152 SMs x "
+                                               "2070 MHz"}}
     if err is not None:
         line["mixed_error"] = {"rel_l2_velocity_vs_fp64": err, "steps": args.error_steps}
     if e2e is not None:
