@@ -74,3 +74,76 @@ def test_missing_library_fails_loudly(tmp_path):
             fsei.load(str(tmp_path / "libfsei.so"))
     finally:
         fsei._lib = saved
+
+
+def _header_structs():
+    """typedef struct { ... } name; blocks of include/fsei.h: name -> field
+    names in declaration order."""
+    text = open(os.path.join(ROOT, "include", "fsei.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", text, re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            # drop the type (first word(s) before the declarators)
+            m = re.match(r"(?:const\s+)?\w+\s*(.*)$", decl, re.S)
+            for d in m.group(1).split(","):
+                fields.append(re.sub(r"[\s*]|\[.*?\]", "", d))
+        out[name] = fields
+    return out
+
+
+CTYPES_OF = {"fsei_grid_desc": "GridDesc", "fsei_state": "State",
+             "fsei_step_params": "StepParams", "fsei_step_stats": "StepStats",
+             "fsei_schedule": "Schedule"}
+
+
+def test_binding_structs_match_header_fields():
+    structs = _header_structs()
+    assert set(CTYPES_OF) <= set(structs), structs.keys()
+    for cname, pyname in CTYPES_OF.items():
+        py = [f for f, _ in getattr(fsei, pyname)._fields_]
+        assert py == structs[cname], (cname, py, structs[cname])
+
+
+def test_binding_struct_layouts_match_c_compiler(tmp_path):
+    """sizeof and every field offset of the header's structs, as a C compiler
+    lays them out, against the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = _header_structs()
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "fsei.h"', "int main(void) {"]
+    for cname in CTYPES_OF:
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in structs[cname]:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True,
+                             text=True).stdout.splitlines():
+        a, b, v = ln.split()
+        got[(a, b)] = int(v)
+    for cname, pyname in CTYPES_OF.items():
+        cls = getattr(fsei, pyname)
+        assert ctypes.sizeof(cls) == got[(cname, "sizeof")], cname
+        for f, _ in cls._fields_:
+            assert getattr(cls, f).offset == got[(cname, f)], (cname, f)
+
+
+def test_schedule_calls_reject_null_handles(lib):
+    s = fsei.Schedule()
+    assert lib.fsei_grid_autotune(None, 0, None, ctypes.byref(s)) == 1
+    assert lib.fsei_grid_get_schedule(None, ctypes.byref(s)) == 1
+    assert lib.fsei_grid_set_schedule(None, ctypes.byref(s)) == 1
+    assert lib.fsei_batch_autotune(None, 0, None) == 1
