@@ -221,3 +221,116 @@ def test_manufactured_solution_second_order():
     errs = np.array(errs)
     orders = np.log2(errs[:-1] / errs[1:])
     assert np.all(orders[-1] >= 1.9), (errs, orders)
+
+
+# ------------------------------------------------ CFL time step and energy --
+def _tanh_faces(nz, s):
+    """Stretched wall faces written out from the tanh clustering law, apart
+    from the oracle's grid module."""
+    return np.array([np.tanh(s * (2.0 * k / nz - 1.0)) / np.tanh(s)
+                     for k in range(nz + 1)])
+
+
+def test_cfl_dt_uniform_flow_periodic_box():
+    """A uniform stream u = U on a periodic box: every cell sees |U|/dx, so
+    dt = CFL dx / |U| exactly."""
+    g = Grid(12, 10, 8, 3.0, 2.0, Z_PERIODIC, lz=1.6)
+    U = -1.7
+    u = np.full(g.shape, U)
+    z = np.zeros(g.shape)
+    dt = st.oracle_cfl_dt(g, u, z, z.copy(), 0.5)
+    assert abs(dt - 0.5 * (3.0 / 12) / abs(U)) <= 1e-15
+
+
+def test_cfl_dt_single_cell_sum_on_stretched_channel():
+    """One u face, one v face and one interior w face that all bound cell
+    (k0, j0, i0) of a stretched channel carry U, V, W; every other value is 0.
+    The centre speeds are two-face averages, so that cell's speed is
+    |U|/(2 dx) + |V|/(2 dy) + |W|/(2 dz_k0), larger than that of any of its
+    neighbours (each sees one of the three halves), and
+    dt = CFL / that sum.  Reading face values instead of averages doubles it;
+    weighting the w term by hc_k instead of dz_k changes it; dropping a
+    component lowers it."""
+    nx, ny, nz = 10, 8, 12
+    g = Grid(nx, ny, nz, 2.0, 1.5, Z_WALLS, stretch=2.0)
+    zf = _tanh_faces(nz, 2.0)
+    dz = zf[1:] - zf[:-1]
+    k0, j0, i0 = 5, 3, 4
+    U, V, W = 0.9, -1.3, 0.7
+    u = np.zeros(g.shape)
+    v = np.zeros(g.shape)
+    w = np.zeros(g.shape)
+    u[k0, j0, i0] = U          # x face i0 = the low-x face of cell i0
+    v[k0, j0, i0] = V          # y face j0 = the low-y face of cell j0
+    w[k0, j0, i0] = W          # z face k0 = the low-z face of cell k0
+    spd = abs(U) / (2 * 2.0 / nx) + abs(V) / (2 * 1.5 / ny) + abs(W) / (2 * dz[k0])
+    # the neighbours each see one half-term only
+    assert spd > max(abs(U) / (2 * 2.0 / nx), abs(V) / (2 * 1.5 / ny),
+                     abs(W) / (2 * min(dz[k0 - 1], dz[k0])))
+    dt = st.oracle_cfl_dt(g, u, v, w, 0.5)
+    assert abs(dt / (0.5 / spd) - 1) <= 1e-14
+
+
+def test_cfl_dt_w_only_asymmetric_faces():
+    """w on the stretched channel only, on two neighbouring interior faces k1
+    and k1+1 with unequal values A and B: the centre between them has
+    w_c = (A+B)/2, its neighbours A/2 and B/2; dt = CFL / max over those
+    three of |w_c| / dz_k, computed here from the tanh faces directly."""
+    nx, ny, nz = 8, 6, 16
+    g = Grid(nx, ny, nz, 1.0, 1.0, Z_WALLS, stretch=2.0)
+    zf = _tanh_faces(nz, 2.0)
+    dz = zf[1:] - zf[:-1]
+    k1 = 2                      # near the bottom wall: dz varies fast there
+    A, B = 1.0, -0.25
+    w = np.zeros(g.shape)
+    w[k1, 2, 3] = A
+    w[k1 + 1, 2, 3] = B
+    z = np.zeros(g.shape)
+    cand = [abs(A) / 2 / dz[k1 - 1], abs(A + B) / 2 / dz[k1], abs(B) / 2 / dz[k1 + 1]]
+    dt = st.oracle_cfl_dt(g, z, z.copy(), w, 0.8)
+    assert abs(dt / (0.8 / max(cand)) - 1) <= 1e-14
+    # the bottom wall face is not an unknown: a value stored there is ignored
+    w2 = w.copy()
+    w2[0, 1, 1] = 50.0
+    assert st.oracle_cfl_dt(g, z, z.copy(), w2, 0.8) == dt
+
+
+@pytest.mark.parametrize("comp", ["u", "v", "w"])
+def test_kinetic_energy_closed_form_walls(comp):
+    """Constant component C on a stretched channel, the others 0.  u and v
+    live at the centres (weights dx dy dz_k, summing to lx ly 2), so
+    KE = lx ly C^2.  w lives on the interior faces k = 1..nz-1 (weights
+    dx dy hc_k, which sum to the distance between the first and last centres,
+    2 - dz_0/2 - dz_{nz-1}/2); the bottom wall face is not counted even when
+    a value is stored there."""
+    nx, ny, nz = 6, 4, 10
+    lx, ly = 1.5, 0.75
+    g = Grid(nx, ny, nz, lx, ly, Z_WALLS, stretch=2.0)
+    zf = _tanh_faces(nz, 2.0)
+    dz = zf[1:] - zf[:-1]
+    C = 0.6
+    f = {k: np.zeros(g.shape) for k in "uvw"}
+    f[comp][...] = C
+    ke = st.oracle_stats(g, f["u"], f["v"], f["w"], 1e-3)["kinetic_energy"]
+    if comp == "w":
+        want = 0.5 * lx * ly * C * C * (2.0 - dz[0] / 2 - dz[-1] / 2)
+    else:
+        want = 0.5 * lx * ly * C * C * 2.0
+    assert abs(ke / want - 1) <= 1e-14
+
+
+def test_kinetic_energy_closed_form_periodic_modes():
+    """Periodic box: u = a cos(2 pi x / lx) at the u points, v = b sin(2 pi y
+    / ly) at the v points, w = c cos(2 pi z / lz) at the w faces.  Each
+    squared mode sums to half its point count, so sum(u^2 dV) = a^2 lx ly lz
+    / 2 and KE = (a^2 + b^2 + c^2) lx ly lz / 4."""
+    g = Grid(8, 12, 10, 2.0, 3.0, Z_PERIODIC, lz=1.25)
+    a, b, c = 0.5, -1.5, 2.0
+    x = np.arange(8) * (2.0 / 8)
+    y = np.arange(12) * (3.0 / 12)
+    zfw = np.arange(10) * (1.25 / 10)
+    u = a * np.cos(2 * np.pi * x / 2.0)[None, None, :] * np.ones(g.shape)
+    v = b * np.sin(2 * np.pi * y / 3.0)[None, :, None] * np.ones(g.shape)
+    w = c * np.cos(2 * np.pi * zfw / 1.25)[:, None, None] * np.ones(g.shape)
+    ke = st.oracle_stats(g, u, v, w, 1e-3)["kinetic_energy"]
+    assert abs(ke / ((a * a + b * b + c * c) * 2.0 * 3.0 * 1.25 / 4) - 1) <= 1e-14
