@@ -28,6 +28,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "fractional-step Mcell-updates/s"
 WORKLOAD = dict(nx=256, ny=256, nz=256, lx=2 * np.pi, ly=np.pi, stretch=2.0,
                 re=2000.0, cfl=0.5, kmin=1.0, kmax=8.0, rms=0.1, seed=2)
 FIELDS = ("u", "v", "w", "p", "hu", "hv", "hw")
@@ -55,6 +56,18 @@ def algorithmic_words(nx, ny, nz, with_force):
     }
 
 
+def step_words_model(with_force):
+    """Words per cell one whole step must move in the pass-minimal model:
+    one pass per global line dependency (x, y and z line solves; x and y
+    transforms; the z Poisson lines), each word read or written once per
+    pass, the spectrum counted as one word per pass and the inverse x
+    transform fused with the projection.  RHS + x sweep 13 (16 with a body
+    force field), y sweep 6, z sweep + u* 9, divergence + x transform 4,
+    y transforms and z Poisson 2 each, inverse x transform + projection 9:
+    47 words (50 with a force field)."""
+    return 50.0 if with_force else 47.0
+
+
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
 # of the dominant kernel, from an ncu --set full capture of the 256^3
 # channel workload; reported only for that workload and that kernel build
@@ -66,11 +79,10 @@ MEASURED_TRAFFIC = {
 # FP64 instructions of one FP64 step per cell (DFMA + DADD + DMUL thread
 # instructions, the CFL pre-pass excluded), from one ncu capture of the FP64
 # step on a 128^3 channel (the count per cell does not depend on the size).
-# The FP64 step is bound by the FP64 pipe: its peak is 2 FP64 thread
-# instructions per clock per SM (1.25 TFLOP/s of DFMA nominal), times 152
-# SMs at the 2070 MHz maximum clock.
+# The FP64 step is bound by the FP64 pipe; its peak is measured in the run
+# (fsei_fp64_fma_rate: DFMA thread instructions per second with every SM
+# busy), and each of DFMA, DADD and DMUL takes one slot of that pipe.
 FP64_INSTR_PER_CELL = 342.6
-FP64_PEAK_GINST = 2 * 152 * 2.070
 
 
 def measured_peaks():
@@ -210,17 +222,27 @@ def run_gpu_arm(args, rank, world):
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        # blocks of exactly K steps, each bracketed by a barrier and a device
+        # synchronisation, repeated until at least min_timed_s of device time
+        # (and 3 blocks) have run, so that the clock sampler sees the load;
+        # the median block is reported
+        blocks = []
         with ClockSampler(dev) as clk:
-            e0.record(stream)
-            fsei.step(grid, st, None, nsteps=K, stats=False, **prm)
-            e1.record(stream)
-            barrier()
-        ms = e0.elapsed_time(e1)
-        ms = max_over_ranks(ms)
+            while len(blocks) < 3 or sum(blocks) < args.min_timed_s * 1e3:
+                barrier()
+                e0.record(stream)
+                fsei.step(grid, st, None, nsteps=K, stats=False, **prm)
+                e1.record(stream)
+                barrier()
+                blocks.append(max_over_ranks(e0.elapsed_time(e1)))
+                if len(blocks) >= args.max_blocks:
+                    break
+        ms = float(np.median(blocks))
         stats = fsei.step(grid, st, None, nsteps=0, **prm)
         res = {"ms_total": ms, "ms_per_step": ms / K, "cells": cells,
                "mcups": cells * K * world / (ms * 1e-3) / 1e6, "clocks": clk.summary(),
-               "last_stats": stats}
+               "last_stats": stats, "blocks": len(blocks),
+               "block_ms": {"median": ms, "min": float(min(blocks)), "max": float(max(blocks))}}
         # per-kernel device time over K more steps (event pairs on the stream)
         fsei.set_kernel_timing(grid, True)
         fsei.step(grid, st, None, nsteps=K, stats=False, **prm)
@@ -356,7 +378,7 @@ def run_heart_scale(args, peak):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     stats = fsei.step(grid, st, f, nsteps=0, **prm)
-    words = sum(algorithmic_words(case.nx, case.ny, case.nz, True).values())
+    words = step_words_model(True)
     mcups = case.cells * args.heart_steps / (ms * 1e-3) / 1e6
     gbs = words * 4 * mcups * 1e6 / 1e9
     return {"value": round(mcups, 2), "unit": "Mcell-updates/s", "cells": case.cells,
@@ -365,6 +387,106 @@ def run_heart_scale(args, peak):
             "alg_words_per_cell": round(words, 3), "max_div": stats["max_div"],
             "workload": "512x512x768, Lx=Ly=2*96/156, tanh walls 2.0, Re 3000, CFL 0.5, "
                         "k^-5/3 field (|k|<=32, unit RMS) + 20 Gaussian force blobs"}
+
+
+def adjoint_words(nx, with_fbar=True):
+    """Words per cell each launch group of the adjoint step must move (read
+    + write once; spectrum at its true size)."""
+    spec = 2.0 * (nx // 2 + 1) / nx
+    return {
+        "adj_phibar": 4 + 1,                       # u,v,w,p cotangents -> x
+        "adj_poisson (5 launches)": 2 + 8 * spec,   # as the forward Poisson chain
+        "adj_ustar": 4 + 6,                        # cotangents, psi -> cotangents, q
+        "adj_sweep_z": 6,
+        "adj_sweep_y": 6,
+        "adj_sweep_x": 6,
+        "adj_hist": 12 + (6 if with_fbar else 0),  # q, H-bar -> H-bar, Hb (+ f-bar +=)
+        "adj_gather": 13 + 4,                      # u, q, Hb, cotangents -> cotangents
+    }
+
+
+def run_adjoint(args, peak):
+    """The 128x128x192 channel's gradient window (20 steps, checkpoint every
+    5, dt frozen from CFL 0.5 at step 0, loss = kinetic energy of the central
+    32^3 block): forward and backward device time per step in mixed precision
+    and FP64, the adjoint kernels' device times and HBM fractions (mixed),
+    and the mixed-vs-FP64 gradient error."""
+    import torch
+    from paper_2103_15187_gb300 import autograd as fad
+    from paper_2103_15187_gb300 import fsei, inputs
+    case = inputs.case_channel(128, 128, 192, steps=20, seed=4)
+    zf = inputs.z_faces(case.nz, case.zbc, case.lz, case.stretch)
+    nsteps, ck = 20, 5
+    g64 = fsei.Grid(case.nx, case.ny, case.nz, case.lx, case.ly, zbc=case.zbc, lz=case.lz,
+                    stretch=case.stretch, prec=fsei.FSEI_FP64)
+    dt = fad.frozen_dt(g64, *[torch.tensor(a, dtype=torch.float64, device="cuda")
+                              for a in (case.u, case.v, case.w)], case.cfl, case.re,
+                       fconst=case.fconst)
+    stream = torch.cuda.current_stream()
+    out, grads = {}, {}
+    for name, prec, dtype in (("mixed", fsei.FSEI_MIXED, torch.float32),
+                              ("fp64", fsei.FSEI_FP64, torch.float64)):
+        grid = g64 if prec == fsei.FSEI_FP64 else fsei.Grid(
+            case.nx, case.ny, case.nz, case.lx, case.ly, zbc=case.zbc, lz=case.lz,
+            stretch=case.stretch, prec=prec)
+
+        def once(timing=False):
+            xs = [torch.tensor(a, dtype=dtype, device="cuda").requires_grad_(True)
+                  for a in (case.u, case.v, case.w)]
+            fs = [torch.zeros_like(xs[0]).requires_grad_(True) for _ in range(3)]
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            torch.cuda.synchronize()
+            e[0].record(stream)
+            u, v, w = fad.window(grid, *xs, *fs, nsteps=nsteps, dt=dt, re=case.re,
+                                 checkpoint_every=ck, fconst=case.fconst)
+            e[1].record(stream)
+            J = fad.kinetic_energy_subbox(u, v, w, zf, case.lx, case.ly)
+            if timing:
+                fsei.set_kernel_timing(grid, True)
+            J.backward()
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            kt = None
+            if timing:
+                kt = fsei.kernel_times(grid)
+                fsei.set_kernel_timing(grid, False)
+            return (e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]),
+                    [t.grad.detach().double() for t in xs + fs], kt)
+
+        once()
+        fwd_ms, bwd_ms, gr, _ = once()
+        res = {"forward_ms_per_step": round(fwd_ms / nsteps, 4),
+               "backward_ms_per_step": round(bwd_ms / nsteps, 4),
+               "backward_note": "recompute of each checkpointed segment + adjoint steps"}
+        if name == "mixed":
+            _, _, _, kt = once(timing=True)
+            words = adjoint_words(case.nx)
+            table = {}
+            for kname, (tot, n) in kt.items():
+                if n == 0 or kname not in words:
+                    continue
+                avg = tot / n
+                b = words[kname] * 4 * case.cells
+                table[kname] = {"avg_ms": round(avg, 5), "launches": n,
+                                "alg_bytes": int(b),
+                                "gbs": round(b / (avg * 1e-3) / 1e9, 1),
+                                "frac": round(b / (avg * 1e-3) / 1e9 / peak, 4)}
+            res["kernels"] = table
+            tot_words = sum(words.values())
+            adj_ms = sum(v["avg_ms"] for v in table.values())
+            res["adjoint_step"] = {"ms": round(adj_ms, 4), "alg_words_per_cell": round(tot_words, 3),
+                                   "frac": round(tot_words * 4 * case.cells / (adj_ms * 1e-3)
+                                                 / 1e9 / peak, 4)}
+        out[name] = res
+        grads[name] = gr
+    num = sum(float(torch.linalg.vector_norm(a - b) ** 2)
+              for a, b in zip(grads["mixed"], grads["fp64"]))
+    den = sum(float(torch.linalg.vector_norm(b) ** 2) for b in grads["fp64"])
+    out["mixed_vs_fp64_gradient_rel_l2"] = (num / den) ** 0.5
+    out["workload"] = ("128x128x192 channel (as the 256^3 one), 20-step window, checkpoint "
+                       "every 5, dt frozen from CFL 0.5, J = KE of the central 32^3 block; "
+                       "gradients wrt u0, v0, w0, fx, fy, fz")
+    return out
 
 
 def roofline_of(res, nx, ny, nz, bytes_per_word, peak_gbs, peak_kind):
@@ -398,45 +520,125 @@ def roofline_of(res, nx, ny, nz, bytes_per_word, peak_gbs, peak_kind):
     return roof, table, step_words
 
 
-def cpu_oracle_sample(case, steps=2):
-    """The oracle (numpy, FP64) advancing the full workload by `steps` steps
-    on the host: the first (Euler start) and then Adams-Bashforth steps."""
+def host_cpu():
+    """Logical CPU count and the model name lscpu reports."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def _mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as fh:
+            for ln in fh:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except Exception:
+        pass
+    return None
+
+
+def _oracle_state(case):
+    z = np.zeros_like(case.u)
+    return {"u": case.u, "v": case.v, "w": case.w, "p": case.p, "hu": z, "hv": z, "hw": z,
+            "have_prev_h": 0}
+
+
+def _oracle_steps(case, steps):
+    """Seconds the oracle (numpy, FP64, one thread) takes for `steps` steps
+    of `case` from its initial state."""
     from oracle.grid import Grid as OGrid
     from oracle.step import oracle_step
     g = OGrid(case.nx, case.ny, case.nz, case.lx, case.ly, case.zbc, lz=case.lz,
               stretch=case.stretch)
-    z = np.zeros_like(case.u)
-    s = {"u": case.u, "v": case.v, "w": case.w, "p": case.p, "hu": z, "hv": z, "hw": z,
-         "have_prev_h": 0}
+    s = _oracle_state(case)
     t0 = time.perf_counter()
     for _ in range(steps):
         s, _ = oracle_step(g, s, None, re=case.re, dt=case.dt, cfl=case.cfl,
                            fconst=case.fconst)
-    dt = time.perf_counter() - t0
-    return {"value": case.cells * steps / dt / 1e6, "unit": "Mcell-updates/s", "cores": 1,
-            "kind": "oracle",
-            "sample": "%d steps of the full %dx%dx%d workload, numpy FP64, single thread "
-                      "(%.1f s)" % (steps, case.nx, case.ny, case.nz, dt)}
+    return time.perf_counter() - t0
+
+
+def _oracle_worker(q, start, steps, workload):
+    """One process of the all-cores leg: builds the workload, waits for the
+    common start, times its steps."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    WORKLOAD.update(workload)
+    case = make_case()
+    q.put(("ready", None))
+    start.wait()
+    q.put(("done", _oracle_steps(case, steps)))
+
+
+def cpu_oracle_sample(case, steps=2, all_cores=True):
+    """The oracle advancing the full workload on the host, as it stands (it
+    is single-threaded numpy): once in this process, and as one independent
+    copy per core run at the same time (as many copies as the free host
+    memory holds at about 6.5 GB each), whose aggregate is the all-cores
+    figure.  The processes are spawned (the parent already holds a CUDA
+    context)."""
+    ncpu, model = host_cpu()
+    dt1 = _oracle_steps(case, steps)
+    one = case.cells * steps / dt1 / 1e6
+    out = {"value": round(one, 3), "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle",
+           "sample": "%d steps of the full %dx%dx%d workload, numpy FP64, one thread "
+                     "(%.1f s)" % (steps, case.nx, case.ny, case.nz, dt1),
+           "host": {"nproc": ncpu, "model": model}}
+    if not all_cores or ncpu < 2:
+        return out
+    avail = _mem_available_bytes()
+    nproc = ncpu if avail is None else max(1, min(ncpu, int(0.6 * avail // 6.5e9)))
+    if nproc < 2:
+        return out
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    start = ctx.Event()
+    procs = [ctx.Process(target=_oracle_worker, args=(q, start, 1, dict(WORKLOAD)), daemon=True)
+             for _ in range(nproc)]
+    for p in procs:
+        p.start()
+    try:
+        ready = 0
+        while ready < nproc:
+            kind, _ = q.get(timeout=600)
+            ready += kind == "ready"
+        start.set()
+        times = [q.get(timeout=1200)[1] for _ in range(nproc)]
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.terminate()
+    agg = case.cells * nproc / max(times) / 1e6
+    out["all_cores"] = {"value": round(agg, 3), "unit": "Mcell-updates/s", "cores": nproc,
+                        "sample": "%d concurrent copies of the oracle, one per core, each "
+                                  "advancing its own copy of the full workload by one step "
+                                  "(slowest %.1f s)" % (nproc, max(times))}
+    return out
 
 
 # ------------------------------------------------------- reference arm -----
 def run_reference_arm(args, rank, world):
     """The oracle as the reference implementation, on the host cores: each
-    step advances the 128^3 version of the channel workload (same physics,
-    1/8 of the cells), so a --steps K --warmup W run stays within minutes."""
+    step advances the full 256^3 channel workload (numpy, FP64, one thread;
+    about 6 s per step on a Grace core, so a --steps 20 --warmup 5 run takes
+    a few minutes)."""
     if rank != 0:
         return 0
-    from paper_2103_15187_gb300 import inputs
     from oracle.grid import Grid as OGrid
     from oracle.step import oracle_step
-    w = WORKLOAD
-    n = 128
-    case = inputs.case_channel(n, n, n, w["lx"], w["ly"], w["stretch"], w["re"], w["cfl"],
-                               100, w["kmin"], w["kmax"], 0.0, w["rms"], w["seed"])
-    g = OGrid(n, n, n, case.lx, case.ly, case.zbc, lz=case.lz, stretch=case.stretch)
-    z = np.zeros_like(case.u)
-    s = {"u": case.u, "v": case.v, "w": case.w, "p": case.p, "hu": z, "hv": z, "hw": z,
-         "have_prev_h": 0}
+    case = make_case()
+    g = OGrid(case.nx, case.ny, case.nz, case.lx, case.ly, case.zbc, lz=case.lz,
+              stretch=case.stretch)
+    s = _oracle_state(case)
     prm = dict(re=case.re, dt=case.dt, cfl=case.cfl, fconst=case.fconst)
     for _ in range(args.warmup):
         s, _ = oracle_step(g, s, None, **prm)
@@ -445,22 +647,31 @@ def run_reference_arm(args, rank, world):
         s, _ = oracle_step(g, s, None, **prm)
     el = time.perf_counter() - t0
     v = case.cells * args.steps / el / 1e6
-    sample = ("oracle steps of the 128^3 version of the 256^3 channel workload (same "
-              "Re, CFL, stretching and spectrum; 1/8 of the cells per step), numpy FP64, "
-              "single thread")
-    line = {"impl": "reference", "metric": "fractional-step Mcell-updates/s", "value": v,
+    ncpu, model = host_cpu()
+    sample = ("%d oracle steps of the full %dx%dx%d channel workload after %d untimed ones, "
+              "numpy FP64, one thread (host: %d logical CPUs, %s)"
+              % (args.steps, case.nx, case.ny, case.nz, args.warmup, ncpu, model))
+    line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "channel 256x256x256 (reference sample 128^3)",
-                       "precision": "fp64 oracle"},
+            "config": workload_config(case),
             "cpu_baseline": {"value": v, "unit": "Mcell-updates/s", "cores": 1,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": sample,
+                             "host": {"nproc": ncpu, "model": model}},
             "e2e": {"value": v, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def workload_config(case):
+    return {"workload": "channel %dx%dx%d, tanh-stretched walls (2.0), Re 2000, CFL 0.5, "
+                        "Poiseuille + solenoidal perturbation (RMS 0.1, k 1-8)"
+                        % (case.nx, case.ny, case.nz),
+            "cells": case.cells, "parallelism": "replicas only",
+            "l2": "inputs larger than L2 (state 470 MB + workspace 420 MB per step)"}
 
 
 def main():
@@ -470,6 +681,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fsei", choices=["fsei", "reference"])
     ap.add_argument("--error-steps", type=int, default=100)
+    ap.add_argument("--min-timed-s", type=float, default=1.0,
+                    help="repeat the K-step timed block until this much device time has run")
+    ap.add_argument("--max-blocks", type=int, default=1000)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -478,6 +692,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--heart-steps", type=int, default=50)
     ap.add_argument("--no-heart", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="run the default launch schedule instead of a measured one")
     ap.add_argument("--schedule", default=None,
@@ -506,11 +721,12 @@ def main():
     peak, peak_kind = measured_peaks()
     nx, ny, nz = case.nx, case.ny, case.nz
     mres = results["mixed"][0]
-    roof, table, step_words = roofline_of(mres, nx, ny, nz, 4, peak, peak_kind)
-    step_gbs = step_words * 4 * nx * ny * nz * mres["mcups"] / max(1, args.gpus) * 1e6 / 1e9 \
-        / (nx * ny * nz)
+    roof, table, kernel_words = roofline_of(mres, nx, ny, nz, 4, peak, peak_kind)
+    step_words = step_words_model(False)
+    per_gpu_cells_s = mres["mcups"] / max(1, args.gpus) * 1e6
+    step_gbs = step_words * 4 * per_gpu_cells_s / 1e9
     line = {
-        "metric": "fractional-step Mcell-updates/s (mixed FP32/FP64 step)",
+        "metric": METRIC,
         "value": round(mres["mcups"], 2),
         "unit": "Mcell-updates/s",
         "n_gpus": args.gpus,
@@ -522,15 +738,16 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "channel %dx%dx%d, tanh-stretched walls (2.0), Re 2000, "
-                               "CFL 0.5, Poiseuille + solenoidal perturbation (RMS 0.1, k 1-8)"
-                               % (nx, ny, nz),
-                   "cells": nx * ny * nz, "precision": "mixed (FP32 fields; FP64 near-zero "
-                   "Poisson modes and reductions)", "parallelism": "replicas only",
-                   "l2": "inputs larger than L2 (state 470 MB + workspace 420 MB per step)"},
+        "config": dict(workload_config(case),
+                       precision="mixed (FP32 fields; FP64 near-zero Poisson modes and "
+                                 "reductions)"),
         "roofline": roof,
-        "step_hbm": {"alg_words_per_cell": round(step_words, 3),
-                     "achieved_gbs": round(step_gbs, 1), "frac": round(step_gbs / peak, 4)},
+        "step_hbm": {"alg_words_per_cell": step_words,
+                     "model": "pass-minimal: one pass per global line dependency, spectrum "
+                              "1 word per pass, inverse x transform fused with the projection",
+                     "achieved_gbs": round(step_gbs, 1), "frac": round(step_gbs / peak, 4),
+                     "kernel_words_per_cell": round(kernel_words, 3),
+                     "kernel_gbs": round(kernel_words * 4 * per_gpu_cells_s / 1e9, 1)},
         "clocks": mres["clocks"],
         "schedule": {"mixed": mres["schedule"],
                      "source": ("given" if args.schedule else
@@ -540,18 +757,24 @@ def main():
                         for kk, vv in v.items()} for k, v in table.items()},
     }
     if "fp64" in results:
+        import torch
+        from paper_2103_15187_gb300 import fsei
         fres = results["fp64"][0]
         ginst = FP64_INSTR_PER_CELL * fres["mcups"] / max(1, args.gpus) / 1e3
+        fpeak = fsei.fp64_fma_rate()
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
         line["fp64"] = {"value": round(fres["mcups"], 2), "unit": "Mcell-updates/s",
                         "ms_per_step": round(fres["ms_per_step"], 4),
                         "mixed_speedup": round(mres["mcups"] / fres["mcups"], 3),
+                        "clocks": fres["clocks"],
                         "alu": {"bound": "alu", "achieved": round(ginst, 1),
-                                "peak": round(FP64_PEAK_GINST, 1),
+                                "peak": round(fpeak, 1),
                                 "unit": "G FP64 thread-instructions/s",
-                                "frac": round(ginst / FP64_PEAK_GINST, 4),
+                                "frac": round(ginst / fpeak, 4),
                                 "instr_per_cell": FP64_INSTR_PER_CELL,
-                                "peak_source": "derived: 2 FP64 lanes/clk/SM x 152 SMs x "
-                                               "2070 MHz"}}
+                                "peak_source": "measured in this run: fsei_fp64_fma_rate "
+                                               "(independent DFMA chains on all %d SMs)"
+                                               % props.multi_processor_count}}
     if err is not None:
         line["mixed_error"] = {"rel_l2_velocity_vs_fp64": err, "steps": args.error_steps}
     if e2e is not None:
@@ -560,6 +783,8 @@ def main():
         line["ensemble"] = run_ensemble(args)
     if not args.no_heart and args.heart_steps > 0:
         line["heart_scale"] = run_heart_scale(args, peak)
+    if not args.no_adjoint:
+        line["adjoint"] = run_adjoint(args, peak)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(case)
     print(json.dumps(line), flush=True)

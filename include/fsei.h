@@ -6,7 +6,7 @@
  * Method (Sec. 2.1, Eq. 2-3; Sec. 3.1):
  *   * incompressible Navier-Stokes, non-dimensional, Newtonian stress
  *     tau = 2 Re^-1 E (Sec. 2.1), body force f given per step (the immersed
- *     boundary forcing "applied at the fractional step", Sec. 3.2);
+ *     boundary forcing enters the fractional step as this field, Sec. 3.2);
  *   * central second-order differences on a staggered mesh (Sec. 2.1);
  *   * Adams-Bashforth for advection, Crank-Nicolson for viscosity,
  *     gamma = 3/2, rho = -1/2 (Eq. 3); first step of a run: gamma = 1,
@@ -59,8 +59,7 @@ typedef enum {
     FSEI_E_NOMEM = 4,       /* device allocation failed                      */
     FSEI_E_CUDA = 5,        /* a CUDA runtime call failed                    */
     FSEI_E_NONFINITE = 6,   /* a NaN/Inf appeared in the new state           */
-    FSEI_E_CFL = 7,         /* CFL number of the new state above 1           */
-    FSEI_E_TIMEOUT = 8      /* a bounded device wait gave up                 */
+    FSEI_E_CFL = 7          /* CFL number of the new state above 1           */
 } fsei_status;
 
 typedef enum {
@@ -131,7 +130,11 @@ typedef struct {
 
 /* Create a grid handle: z metrics, plans and workspace on the current CUDA
  * device.  Returns FSEI_E_SHAPE for unsupported extents, FSEI_E_ARG for bad
- * lengths or faces, FSEI_E_NOMEM if the workspace does not fit. */
+ * lengths or faces, FSEI_E_NOMEM if the workspace does not fit.  When the
+ * environment variable FSEI_WORKSPACE_LIMIT_BYTES holds a decimal number at
+ * the call, the handle's device allocations may not exceed that many bytes
+ * in total; a grid that needs more fails with FSEI_E_NOMEM (a memory budget
+ * for a process that shares the GPU). */
 fsei_status fsei_grid_create(const fsei_grid_desc *desc, fsei_grid *out);
 
 /* Release a handle (NULL is a no-op).  Synchronises the device first. */
@@ -149,7 +152,8 @@ int64_t fsei_grid_workspace_bytes(fsei_grid grid);
  *   rhs_cells_per_lane: RHS + x sweep (Eq. 3, Sec. 3.1), cells of a grid row
  *     per lane of the row-resident kernel (4, or 2 or 8 in FSEI_MIXED);
  *   poisson_lanes_per_line, poisson_rows_per_lane: z tridiagonal solve of
- *     each Fourier mode (Sec. 3.2): lanes that share a line (reduction
+ *     each Fourier mode of the pressure equation (Sec. 2.1; Sec. 3.1 and
+ *     Sec. 4 on its parallel solve): lanes that share a line (reduction
  *     across lanes) and rows each lane eliminates on its own; their product
  *     is nz;
  *   rfft_rows_per_block: forward x transform, grid rows per thread block;
@@ -208,7 +212,9 @@ fsei_status fsei_step(fsei_grid grid, fsei_state *state, const void *fx,
                       const fsei_step_params *params, int32_t nsteps,
                       void *cuda_stream, fsei_step_stats *out);
 
-/* Pressure-increment Poisson solve of the fractional step: phi with
+/* Pressure-increment Poisson solve of the fractional step (Sec. 2.1: the
+ * elliptic equation whose solution makes u^{n+1} solenoidal; Sec. 4: solved
+ * with transforms in the two periodic directions): phi with
  * D G phi = rhs at the cell centres (D G: the compound staggered Laplacian,
  * Neumann at walls), phi of zero volume-weighted mean.  rhs must have zero
  * volume-weighted mean (sum rhs dz_k = 0) -- the solve pins phi at k = 0 of
@@ -290,8 +296,8 @@ fsei_status fsei_batch_step(fsei_batch batch, fsei_state *states,
  * last call's contents (the spectrum is cleared on every call); calls whose
  * GPU work overlaps -- on different streams or from different host
  * threads -- race on it and must be serialised by the caller.  The tables
- * are copied from host memory on the given stream, which makes the call wait
- * for work already queued on that stream. */
+ * are built in a static host buffer and copied from it on the given stream;
+ * the call returns once that buffer may be reused by the next call. */
 fsei_status fsei_poisson_solve_noalloc(const fsei_grid_desc *desc,
                                        const void *rhs, void *phi,
                                        void *cuda_stream);
@@ -307,6 +313,14 @@ fsei_status fsei_set_kernel_timing(fsei_grid grid, int32_t enable);
 int32_t fsei_kernel_times(fsei_grid grid, double *total_ms, int64_t *launches,
                           int32_t cap);
 const char *fsei_kernel_name(int32_t kind);
+
+/* Measurement helper (the paper has no counterpart): the current device's
+ * double-precision fused multiply-add throughput, in 10^9 thread
+ * instructions per second -- the best of three timed launches of a kernel
+ * that fills every SM with independent DFMA chains.  The FP64 step is bound
+ * by this pipe, so measurement tools use the figure as its arithmetic peak.
+ * Synchronises the stream; FSEI_E_CUDA if a launch fails. */
+fsei_status fsei_fp64_fma_rate(void *cuda_stream, double *ginst_per_s);
 
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char *fsei_last_error(void);

@@ -13,6 +13,7 @@ library's CUDA kernels; torch only provides memory, the stream and the
 autograd plumbing.
 """
 
+import numpy as np
 import torch
 
 from . import fsei
@@ -87,3 +88,24 @@ def window(grid, u0, v0, w0, fx, fy, fz, nsteps, dt, re, checkpoint_every=5,
     """(u, v, w) after nsteps steps; differentiable in u0, v0, w0, fx, fy, fz."""
     return StepWindow.apply(u0, v0, w0, fx, fy, fz, grid, nsteps, dt, re, checkpoint_every,
                             tuple(fconst))
+
+
+def kinetic_energy_subbox(u, v, w, zfaces, lx, ly, half=16):
+    """J = 1/2 sum of component^2 times the local volume over the staggered
+    points whose cell index lies in the central (2 half)^3 block (dx dy dz_k
+    for u and v, dx dy hc_k for w; hc_k the centre-to-centre spacing, half a
+    cell at the bottom wall).  A differentiable torch expression of the
+    window's output, for gradient runs."""
+    nz, ny, nx = u.shape
+    zf = np.asarray(zfaces, dtype=np.float64)
+    dz = zf[1:] - zf[:-1]
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    hc = np.empty(nz)
+    hc[1:] = zc[1:] - zc[:-1]
+    hc[0] = 0.5 * dz[0]
+    dx, dy = lx / nx, ly / ny
+    k0, j0, i0 = nz // 2 - half, ny // 2 - half, nx // 2 - half
+    sl = (slice(k0, k0 + 2 * half), slice(j0, j0 + 2 * half), slice(i0, i0 + 2 * half))
+    vu = torch.tensor(dx * dy * dz[sl[0]], dtype=u.dtype, device=u.device)[:, None, None]
+    vw = torch.tensor(dx * dy * hc[sl[0]], dtype=u.dtype, device=u.device)[:, None, None]
+    return 0.5 * ((u[sl] ** 2 * vu).sum() + (v[sl] ** 2 * vu).sum() + (w[sl] ** 2 * vw).sum())

@@ -2,6 +2,7 @@
 // metrics, FFT twiddle tables, Fourier-mode tables and workspace of a grid,
 // and sequences the kernels of a fractional step (Sec. 2.1, Eq. 3; Sec. 3.1).
 #include <math.h>
+#include <stdlib.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -61,13 +62,21 @@ void twiddles(int n, int count, std::vector<double> &re, std::vector<double> &im
     }
 }
 
+// Device allocations of one grid.  limit caps their sum: an allocation
+// that would pass it fails like a cudaMalloc without room (a grid created
+// under FSEI_WORKSPACE_LIMIT_BYTES, see fsei_grid_create).
 struct DevAllocs {
     std::vector<void *> ptrs;
     size_t bytes = 0;
+    size_t limit = ~size_t(0);
     cudaError_t err = cudaSuccess;
     template <typename X> X *get(size_t count) {
         void *p = nullptr;
         const size_t b = (count ? count : 1) * sizeof(X);
+        if (b > limit - bytes) {
+            err = cudaErrorMemoryAllocation;
+            return nullptr;
+        }
         cudaError_t e = cudaMalloc(&p, b);
         if (e != cudaSuccess) {
             err = e;
@@ -85,13 +94,17 @@ struct DevAllocs {
 
 enum KernelKind {
     KK_SPEED, KK_BEGIN, KK_RHS_X, KK_SWEEP_Y, KK_SWEEP_Z, KK_RFFT_X, KK_FFT_Y, KK_POISSON_Z,
-    KK_IFFT_Y, KK_IRFFT_X, KK_PROJECT, KK_PLANS, KK_COUNT
+    KK_IFFT_Y, KK_IRFFT_X, KK_PROJECT, KK_PLANS,
+    // the adjoint step's launch groups (AdjointKind order)
+    KK_ADJ_FIRST, KK_COUNT = KK_ADJ_FIRST + AK_COUNT
 };
 const char *const kKernelNames[KK_COUNT] = {
     "speed (CFL reduction)", "step_begin (scalars)", "rhs_x (RHS + x sweep)",
     "sweep_y", "sweep_z (+ u*)", "rfft_x (div + x R2C)", "fft_y (forward)",
     "poisson_z (+ exact modes)", "fft_y (inverse)", "irfft_x (x C2R)",
-    "project (+ p update, stats)", "z-sweep plans (side stream)"};
+    "project (+ p update, stats)", "z-sweep plans (side stream)",
+    "adj_phibar", "adj_poisson (5 launches)", "adj_ustar", "adj_sweep_z", "adj_sweep_y",
+    "adj_sweep_x", "adj_hist", "adj_gather"};
 
 // Event pairs recorded around kernel launches while timing is enabled.
 struct KernelTimer {
@@ -123,11 +136,20 @@ struct KernelTimer {
             return;
         }
         if (!on) { f(); return; }
+        begin(kind, st);
+        f();
+        end(st);
+    }
+    // the two halves of run(), for launchers in other files (LaunchHook)
+    void begin(int kind, cudaStream_t st) {
+        if (!on) return;
         const size_t i = kinds.size();
         cudaEventRecord(ev(2 * i), st);
-        f();
-        cudaEventRecord(ev(2 * i + 1), st);
         kinds.push_back(kind);
+    }
+    void end(cudaStream_t st) {
+        if (!on || kinds.empty()) return;
+        cudaEventRecord(ev(2 * kinds.size() - 1), st);
     }
     void collect() {
         cudaDeviceSynchronize();
@@ -708,6 +730,11 @@ fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
     g.idx2 = g.idx * g.idx; g.idy2 = g.idy * g.idy;
     grid_float_copies(g);
     DevAllocs &M = G->mem;
+    if (const char *cap = getenv("FSEI_WORKSPACE_LIMIT_BYTES")) {
+        char *end = nullptr;
+        const unsigned long long v = strtoull(cap, &end, 10);
+        if (end != cap && *end == '\0') M.limit = (size_t)v;
+    }
     double *ddz = M.get<double>(nz), *didz = M.get<double>(nz), *dihc = M.get<double>(nz + 1);
     float *fdz = M.get<float>(nz), *fidz = M.get<float>(nz), *fihc = M.get<float>(nz + 1);
     G->sc = M.get<StepScalars>(1);
@@ -918,10 +945,17 @@ fsei_status fsei_adjoint_step(fsei_grid G, const fsei_state *fwd, const fsei_ste
         const int euler = fwd->have_prev_h ? 0 : 1;
         KernelTimer &tm = G->timer;
         tm.run(KK_BEGIN, st, [&] { launch_step_begin<T>(G->g, W, G->sc, a, euler, st); });
+        LaunchHook hook;
+        hook.ctx = &tm;
+        hook.before = [](void *c, int kind, cudaStream_t s2) {
+            static_cast<KernelTimer *>(c)->begin(KK_ADJ_FIRST + kind, s2);
+        };
+        hook.after = [](void *c, int, cudaStream_t s2) { static_cast<KernelTimer *>(c)->end(s2); };
         launch_adjoint_step<T>(G->g, W, G->sc, (const T *)fwd->u, (const T *)fwd->v,
                                (const T *)fwd->w, (T *)adj->u, (T *)adj->v, (T *)adj->w,
                                (T *)adj->p, (T *)adj->hu, (T *)adj->hv, (T *)adj->hw,
-                               (T *)fbar_x, (T *)fbar_y, (T *)fbar_z, prm->re, st);
+                               (T *)fbar_x, (T *)fbar_y, (T *)fbar_z, prm->re, st,
+                               tm.on ? &hook : nullptr);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(FSEI_E_CUDA, "adjoint launch: %s", cudaGetErrorString(e));
         return FSEI_OK;

@@ -332,23 +332,36 @@ void launch_sweep_x_adjoint(const GridDev &g, Work<T> &W, const StepScalars *sc,
 template <typename T>
 void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T *u, const T *v,
                          const T *w, T *ub, T *vb, T *wb, T *pb, T *hbu, T *hbv, T *hbw, T *fbx,
-                         T *fby, T *fbz, double re, cudaStream_t st) {
+                         T *fby, T *fbz, double re, cudaStream_t st, const LaunchHook *hook) {
     const int rows = g.ny * g.nz;
     const int thr = g.nx >= 256 ? 256 : ((g.nx + 31) / 32) * 32;
-    k_adj_phibar<T><<<rows, thr, 0, st>>>(g, ub, vb, wb, pb, W.phi, sc);
-    launch_rfft_x<T>(g, W, sc, W.phi, 1, st);
-    launch_fft_y<T>(g, W, 0, st);
-    launch_poisson_z<T>(g, W, st, 1);
-    launch_fft_y<T>(g, W, 1, st);
-    launch_irfft_x<T>(g, W, W.phi, st);
-    k_adj_ustar<T><<<rows, thr, 0, st>>>(g, ub, vb, wb, W.phi, W.q0, W.q1, W.q2, sc);
-    launch_sweep_z_adjoint<T>(g, W, st);
-    launch_sweep_y<T>(g, W, sc, st);
-    launch_sweep_x_adjoint<T>(g, W, sc, st);
-    k_adj_hist<T><<<rows, thr, 0, st>>>(g, W.q0, W.q1, W.q2, hbu, hbv, hbw, W.adj0, W.adj1,
-                                        W.adj2, fbx, fby, fbz, sc);
-    k_adj_gather<T><<<rows, thr, 0, st>>>(g, u, v, w, W.q0, W.q1, W.q2, W.adj0, W.adj1, W.adj2, ub,
-                                          vb, wb, pb, sc, T(1.0 / re));
+    auto group = [&](int kind, auto &&launch) {
+        if (hook) hook->before(hook->ctx, kind, st);
+        launch();
+        if (hook) hook->after(hook->ctx, kind, st);
+    };
+    group(AK_PHIBAR, [&] { k_adj_phibar<T><<<rows, thr, 0, st>>>(g, ub, vb, wb, pb, W.phi, sc); });
+    group(AK_POISSON, [&] {
+        launch_rfft_x<T>(g, W, sc, W.phi, 1, st);
+        launch_fft_y<T>(g, W, 0, st);
+        launch_poisson_z<T>(g, W, st, 1);
+        launch_fft_y<T>(g, W, 1, st);
+        launch_irfft_x<T>(g, W, W.phi, st);
+    });
+    group(AK_USTAR, [&] {
+        k_adj_ustar<T><<<rows, thr, 0, st>>>(g, ub, vb, wb, W.phi, W.q0, W.q1, W.q2, sc);
+    });
+    group(AK_SWEEP_Z, [&] { launch_sweep_z_adjoint<T>(g, W, st); });
+    group(AK_SWEEP_Y, [&] { launch_sweep_y<T>(g, W, sc, st); });
+    group(AK_SWEEP_X, [&] { launch_sweep_x_adjoint<T>(g, W, sc, st); });
+    group(AK_HIST, [&] {
+        k_adj_hist<T><<<rows, thr, 0, st>>>(g, W.q0, W.q1, W.q2, hbu, hbv, hbw, W.adj0, W.adj1,
+                                            W.adj2, fbx, fby, fbz, sc);
+    });
+    group(AK_GATHER, [&] {
+        k_adj_gather<T><<<rows, thr, 0, st>>>(g, u, v, w, W.q0, W.q1, W.q2, W.adj0, W.adj1,
+                                              W.adj2, ub, vb, wb, pb, sc, T(1.0 / re));
+    });
 }
 
 template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<T> &W) {
@@ -366,7 +379,8 @@ template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<
 #define FSEI_INST(T)                                                                           \
     template void launch_adjoint_step<T>(const GridDev &, Work<T> &, StepScalars *, const T *,  \
                                          const T *, const T *, T *, T *, T *, T *, T *, T *,    \
-                                         T *, T *, T *, T *, double, cudaStream_t);             \
+                                         T *, T *, T *, T *, double, cudaStream_t,              \
+                                         const LaunchHook *);                                   \
     template void set_smem_limits_adjoint<T>(const GridDev &, const Work<T> &);
 FSEI_INST(float)
 FSEI_INST(double)

@@ -121,10 +121,24 @@ template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, 
 // z sweep of the adjoint: q = W (I - beta L_z)^-1 q, W = dz_k (u, v) or
 // hc_k (w)
 template <typename T> void launch_sweep_z_adjoint(const GridDev &g, Work<T> &W, cudaStream_t st);
+// Optional hook around the launch groups of a multi-kernel launcher (used
+// for per-kernel timing): before(ctx, kind, st) and after(ctx, kind, st)
+// bracket the launches of group `kind` on st.
+struct LaunchHook {
+    void *ctx;
+    void (*before)(void *ctx, int kind, cudaStream_t st);
+    void (*after)(void *ctx, int kind, cudaStream_t st);
+};
+// launch groups of the adjoint step, in call order
+enum AdjointKind {
+    AK_PHIBAR, AK_POISSON, AK_USTAR, AK_SWEEP_Z, AK_SWEEP_Y, AK_SWEEP_X, AK_HIST, AK_GATHER,
+    AK_COUNT
+};
 template <typename T>
 void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T *u, const T *v,
                          const T *w, T *ub, T *vb, T *wb, T *pb, T *hbu, T *hbv, T *hbw, T *fbx,
-                         T *fby, T *fbz, double re, cudaStream_t st);
+                         T *fby, T *fbz, double re, cudaStream_t st,
+                         const LaunchHook *hook = nullptr);
 template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<T> &W);
 template <typename T> void preload_project();
 template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,

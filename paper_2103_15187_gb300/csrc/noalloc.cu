@@ -241,7 +241,6 @@ fsei_status solve_noalloc(const fsei_grid_desc *d, const void *rhs, void *phi, c
         return FSEI_E_CUDA;
     if (cudaMemsetAsync(W.spec, 0, sizeof(cplx<T>) * (size_t)sk * ny * nz, st) != cudaSuccess)
         return FSEI_E_CUDA;
-    set_smem_limits_poisson<T>(g, W);
     StepScalars *sc = (StepScalars *)(dev + L.sc);
     launch_rfft_x<T>(g, W, sc, (const T *)rhs, 1, st);
     launch_fft_y<T>(g, W, 0, st);
@@ -279,6 +278,20 @@ extern "C" fsei_status fsei_poisson_solve_noalloc(const fsei_grid_desc *d, const
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FSEI_E_CUDA;
         g_dev_scratch[dev] = static_cast<unsigned char *>(p);
+        // the transform and z-solve kernels' shared-memory limits, also once
+        // per device (the attributes are per device and process-wide)
+        GridDev g0;
+        memset(&g0, 0, sizeof g0);
+        Work<double> wd;
+        memset(&wd, 0, sizeof wd);
+        Work<float> wf;
+        memset(&wf, 0, sizeof wf);
+        set_smem_limits_poisson<double>(g0, wd);
+        set_smem_limits_poisson<float>(g0, wf);
+        if (cudaGetLastError() != cudaSuccess) {
+            g_dev_scratch[dev] = nullptr;
+            return FSEI_E_CUDA;
+        }
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     cudaGetLastError();   // an error left by an unrelated earlier call is not ours

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libfsei.so")
 FSEI_OK = 0
 STATUS_NAMES = {0: "FSEI_OK", 1: "FSEI_E_ARG", 2: "FSEI_E_SHAPE",
                 3: "FSEI_E_UNSUPPORTED", 4: "FSEI_E_NOMEM", 5: "FSEI_E_CUDA",
-                6: "FSEI_E_NONFINITE", 7: "FSEI_E_CFL", 8: "FSEI_E_TIMEOUT"}
+                6: "FSEI_E_NONFINITE", 7: "FSEI_E_CFL"}
 FSEI_FP64, FSEI_MIXED = 0, 1
 FSEI_Z_PERIODIC, FSEI_Z_WALLS = 0, 1
 FLAG_NONFINITE, FLAG_CFL = 1, 2
@@ -28,7 +28,7 @@ EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
            "fsei_batch_destroy", "fsei_batch_size", "fsei_batch_step", "fsei_set_kernel_timing",
            "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version",
            "fsei_grid_autotune", "fsei_grid_get_schedule", "fsei_grid_set_schedule",
-           "fsei_batch_autotune")
+           "fsei_batch_autotune", "fsei_fp64_fma_rate")
 FSEI_TUNE_FORCE = 1
 
 
@@ -37,9 +37,13 @@ class FseiUnavailable(RuntimeError):
 
 
 class FseiError(RuntimeError):
-    def __init__(self, status, message):
+    """A non-OK status.  stats: the statistics the call filled (a dict, or a
+    list of dicts for a batch) when it reports a device flag, else None."""
+
+    def __init__(self, status, message, stats=None):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
         self.status = status
+        self.stats = stats
 
 
 class GridDesc(ctypes.Structure):
@@ -139,6 +143,8 @@ def load(path=LIB_PATH):
     lib.fsei_grid_set_schedule.restype = ctypes.c_int
     lib.fsei_batch_autotune.argtypes = [vp, ctypes.c_int32, vp]
     lib.fsei_batch_autotune.restype = ctypes.c_int
+    lib.fsei_fp64_fma_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.fsei_fp64_fma_rate.restype = ctypes.c_int
     lib.fsei_last_error.argtypes = []
     lib.fsei_last_error.restype = ctypes.c_char_p
     lib.fsei_version.argtypes = []
@@ -147,9 +153,9 @@ def load(path=LIB_PATH):
     return lib
 
 
-def _check(status):
+def _check(status, stats=None):
     if status != FSEI_OK:
-        raise FseiError(status, load().fsei_last_error().decode())
+        raise FseiError(status, load().fsei_last_error().decode(), stats)
 
 
 def _ptr(t):
@@ -248,8 +254,9 @@ def step(grid, state, f=None, re=100.0, dt=1e-3, cfl=0.0, gamma=1.5, rho=-0.5,
                            ctypes.byref(prm), int(nsteps), _stream_handle(stream),
                            ctypes.byref(out) if out is not None else None)
     state["have_prev_h"] = st.have_prev_h
-    _check(status)
-    return out.as_dict() if out is not None else None
+    res = out.as_dict() if out is not None else None
+    _check(status, res)
+    return res
 
 
 def poisson_solve(grid, rhs, phi, stream=None):
@@ -341,8 +348,9 @@ def batch_step(batch, states, forces, params, nsteps=1, stream=None, stats=True)
                                  out)
     for i, s in enumerate(states):
         s["have_prev_h"] = st[i].have_prev_h
-    _check(status)
-    return [o.as_dict() for o in out] if out is not None else None
+    res = [o.as_dict() for o in out] if out is not None else None
+    _check(status, res)
+    return res
 
 
 def set_kernel_timing(grid, enable):
@@ -359,6 +367,14 @@ def kernel_times(grid):
     n = (ctypes.c_int64 * cap)()
     count = lib.fsei_kernel_times(grid.handle, ms, n, cap)
     return {lib.fsei_kernel_name(k).decode(): (ms[k], n[k]) for k in range(count)}
+
+
+def fp64_fma_rate(stream=None):
+    """fsei_fp64_fma_rate: measured DFMA throughput of the current device,
+    in 10^9 thread instructions per second."""
+    out = ctypes.c_double()
+    _check(load().fsei_fp64_fma_rate(_stream_handle(stream), ctypes.byref(out)))
+    return out.value
 
 
 def version():

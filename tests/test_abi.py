@@ -147,3 +147,11 @@ def test_schedule_calls_reject_null_handles(lib):
     assert lib.fsei_grid_get_schedule(None, ctypes.byref(s)) == 1
     assert lib.fsei_grid_set_schedule(None, ctypes.byref(s)) == 1
     assert lib.fsei_batch_autotune(None, 0, None) == 1
+
+
+def test_status_names_match_header_enum():
+    """The binding's status table is the header's fsei_status enum."""
+    text = open(os.path.join(ROOT, "include", "fsei.h")).read()
+    body = re.search(r"typedef enum \{(.*?)\} fsei_status;", text, re.S).group(1)
+    enum = {int(v): n for n, v in re.findall(r"(FSEI_\w+)\s*=\s*(\d+)", body)}
+    assert enum == fsei.STATUS_NAMES

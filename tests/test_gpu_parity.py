@@ -153,6 +153,7 @@ def test_channel_fp64_10_steps(fsei, shape):
     _assert_fp64(gpu, ref)
     assert abs(st["dt_used"] / rst[-1]["dt_used"] - 1) < 1e-12
     assert abs(st["cfl"] / rst[-1]["cfl"] - 1) < 1e-12
+    assert abs(st["kinetic_energy"] / rst[-1]["kinetic_energy"] - 1) < 1e-12
 
 
 def test_periodic_random_fp64_10_steps(fsei):
@@ -169,27 +170,103 @@ def test_mixed_channel_100_steps_against_fp64_oracle(fsei):
     case = inputs.case_channel(64, 64, 64, steps=100, seed=2)
     gpu, _ = pu.run_gpu(case, 100, fsei.FSEI_MIXED)
     ref, _ = pu.run_oracle(case, 100)
-    vel = np.sqrt(sum(np.linalg.norm(gpu[k] - ref[k]) ** 2 for k in "uvw")
-                  / sum(np.linalg.norm(ref[k]) ** 2 for k in "uvw"))
+    vel = _vel_err(gpu, ref)
     assert vel <= 1e-5, (vel, pu.compare(gpu, ref))
 
 
-def test_full_size_channel_fp64_two_steps(fsei):
-    """256^3 stretched channel (the mixed-vs-FP64 workload) at full size:
-    two FP64 steps against the oracle."""
-    case = inputs.case_channel(256, 256, 256, steps=2)
-    gpu, st = pu.run_gpu(case, 2, fsei.FSEI_FP64)
-    ref, rst = pu.run_oracle(case, 2)
+def _vel_err(gpu, ref):
+    return np.sqrt(sum(np.linalg.norm(gpu[k] - ref[k]) ** 2 for k in "uvw")
+                   / sum(np.linalg.norm(ref[k]) ** 2 for k in "uvw"))
+
+
+def test_full_size_channel_fp64_10_steps(fsei):
+    """256^3 stretched channel (the mixed-vs-FP64 workload: Re 2000, CFL 0.5,
+    Poiseuille drive, RMS 0.1 perturbation) at full size: ten FP64 steps
+    against ten oracle steps, 1e-12 per field, with the CFL time step, the
+    CFL number and the kinetic energy of the last step."""
+    case = inputs.case_channel(256, 256, 256, steps=10)
+    gpu, st = pu.run_gpu(case, 10, fsei.FSEI_FP64)
+    ref, rst = pu.run_oracle(case, 10)
     _assert_fp64(gpu, ref)
     assert st["max_div"] < 1e-9
+    for key in ("dt_used", "cfl", "kinetic_energy"):
+        assert abs(st[key] / rst[-1][key] - 1) < 1e-12, (key, st[key], rst[-1][key])
+
+
+def test_mixed_channel_128_cubed_100_steps_against_fp64_oracle(fsei):
+    """The mixed-precision gate against the FP64 oracle itself: 100 steps of
+    the 128^3 version of the 256^3 channel (same Re, CFL, stretching and
+    perturbation spectrum), velocity within 1e-5."""
+    case = inputs.case_channel(128, 128, 128, steps=100, seed=2)
+    gpu, st = pu.run_gpu(case, 100, fsei.FSEI_MIXED)
+    ref, rst = pu.run_oracle(case, 100)
+    err = _vel_err(gpu, ref)
+    print("mixed vs oracle, 128^3 channel, 100 steps: velocity rel L2 %.3e" % err)
+    assert err <= 1e-5, (err, pu.compare(gpu, ref))
+    assert abs(st["dt_used"] / rst[-1]["dt_used"] - 1) < 1e-4
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+def test_heart_scale_rows_and_y_transforms_against_oracle(fsei, prec_name):
+    """The heart-scale box's x-y plane (512 x 512, its domain, Re, k^-5/3
+    field and force blobs) on 16 stretched z cells: the RHS kernel's 512-wide
+    rows (8 cells per lane in single precision) and the y transforms of
+    length 512.  Three steps against the oracle: 1e-12 per field in FP64,
+    1e-5 in velocity for mixed precision."""
+    case = inputs.case_heart_scale(512, 512, 16, steps=3)
+    prec = fsei.FSEI_FP64 if prec_name == "fp64" else fsei.FSEI_MIXED
+    grid = pu.gpu_grid(case, prec)
+    if prec_name == "mixed":
+        assert grid.schedule["rhs_cells_per_lane"] == 8
+    gpu, st = pu.run_gpu(case, 3, prec, grid=grid)
+    ref, _ = pu.run_oracle(case, 3)
+    if prec_name == "fp64":
+        _assert_fp64(gpu, ref)
+    else:
+        err = _vel_err(gpu, ref)
+        assert err <= 1e-5, (err, pu.compare(gpu, ref))
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+def test_heart_scale_z_lines_against_oracle(fsei, prec_name):
+    """768 stretched z cells (the heart-scale box's z extent, its domain
+    and field) under a 32 x 32 plane: in single precision the z Poisson solve
+    splits each mode line over 32 lanes of 24 rows (the heart-scale split),
+    in double it takes the chunked solver.  The Poisson solve alone and three
+    steps against the oracle: 1e-12 per field in FP64, 1e-5 for mixed."""
+    import torch
+    case = inputs.case_heart_scale(32, 32, 768, steps=3)
+    prec = fsei.FSEI_FP64 if prec_name == "fp64" else fsei.FSEI_MIXED
+    dtype = torch.float64 if prec_name == "fp64" else torch.float32
+    tol = FP64_TOL if prec_name == "fp64" else 1e-5
+    grid = pu.gpu_grid(case, prec)
+    sched = grid.schedule
+    if prec_name == "mixed":
+        assert (sched["poisson_lanes_per_line"], sched["poisson_rows_per_lane"]) == (32, 24)
+    g = pu.oracle_grid(case)
+    s = _compatible_rhs(g, 768)
+    ref = oracle_poisson(g, s)
+    rhs = torch.tensor(s, dtype=dtype, device="cuda")
+    phi = torch.empty_like(rhs)
+    fsei.poisson_solve(grid, rhs, phi)
+    torch.cuda.synchronize()
+    err = pu.rel_l2(phi.double().cpu().numpy(), ref)
+    assert err <= tol, err
+    gpu, _ = pu.run_gpu(case, 3, prec, grid=grid)
+    ref, _ = pu.run_oracle(case, 3)
+    if prec_name == "fp64":
+        _assert_fp64(gpu, ref)
+    else:
+        err = _vel_err(gpu, ref)
+        assert err <= 1e-5, (err, pu.compare(gpu, ref))
 
 
 def test_heart_scale_mixed_against_fp64_gpu(fsei):
     """512x512x768 heart-scale box (stretched walls, k^-5/3 field, 20 force
-    blobs), the largest configuration: three mixed-precision steps against
-    three FP64 steps of the GPU path (itself at oracle parity above, and
-    sampled against the oracle here at full size): velocity within 1e-5,
-    divergence at round-off in both."""
+    blobs), the largest configuration, at full size: three mixed-precision
+    steps against three FP64 steps of the GPU path (the kernel paths of this
+    size meet the oracle in the two tests above, on slices of this box):
+    velocity within 1e-5, divergence at round-off in both."""
     import torch
     case = inputs.case_heart_scale()
     out = {}
