@@ -17,7 +17,8 @@ paper by eye:
                    (Sec. 3.1)
 * ``poisson``   -- pressure-increment Poisson solve, FFT in x, y + tridiagonal
                    in z, with the gauge of the singular mode
-* ``step``      -- one AB2 / Crank-Nicolson fractional step (Eq. 3)
+* ``step``      -- one AB2 / Crank-Nicolson fractional step (Eq. 3) and its
+                   third-order Runge-Kutta variant
 * ``adjoint``   -- the exact transpose of that step (discrete adjoint)
 
 Pins (tests/test_oracle_*.py) tie every function to something other than
@@ -28,5 +29,5 @@ convergence order and the adjoint dot-product identity.
 """
 
 from .grid import Grid  # noqa: F401
-from .step import oracle_step, oracle_cfl_dt, oracle_stats  # noqa: F401
+from .step import oracle_step, oracle_step_rk3, oracle_cfl_dt, oracle_stats  # noqa: F401
 from .poisson import oracle_poisson  # noqa: F401

@@ -160,3 +160,68 @@ def oracle_run(g, state, nsteps, f=None, **params):
         state, st = oracle_step(g, state, f, **params)
         all_stats.append(st)
     return state, all_stats
+
+
+# -------------------------------------------------- RK3 variant (Sec. 2.1) --
+# The paper notes that a third-order Runge-Kutta scheme is implemented beside
+# Adams-Bashforth without writing it out; its solver follows the cited Rai &
+# Moin and Verzicco & Orlandi, whose low-storage scheme takes three
+# sub-steps l = 1, 2, 3 with
+#     gamma_l = 8/15, 5/12, 3/4,   rho_l = 0, -17/60, -5/12,
+#     alpha_l = gamma_l + rho_l = 8/15, 2/15, 1/3  (sum 1),
+# the advection weighted by gamma_l (this sub-step) and rho_l (the previous
+# one), the viscous, pressure and force terms by alpha_l (Crank-Nicolson
+# over the sub-interval alpha_l dt).
+RK3_GAMMA = (8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0)
+RK3_RHO = (0.0, -17.0 / 60.0, -5.0 / 12.0)
+
+
+def rk3_substep(g, u, v, w, p, h_prev, dt, gamma_l, rho_l, alpha_l, re, f, fconst):
+    """One sub-step of the RK3 / Crank-Nicolson fractional step:
+    RHS = dt [gamma_l H^l + rho_l H^{l-1}] + alpha_l dt [Re^-1 L u^l - G p^l
+    + f]; (I - beta_l L_z)(I - beta_l L_y)(I - beta_l L_x) du = RHS with
+    beta_l = alpha_l dt / (2 Re); u* = u^l + du; phi = (D G)^-1 D u* /
+    (alpha_l dt); u^{l+1} = u* - alpha_l dt G phi; p^{l+1} = p^l + phi -
+    beta_l D G phi.  Returns (u, v, w, p, H^l)."""
+    w = op.wall_w(g, w)
+    hu, hv, hw = op.advection(g, u, v, w)
+    lu, lv, lw = op.viscous(g, u, v, w)
+    gx, gy, gz = op.gradient(g, p)
+    fx, fy, fz = (0.0, 0.0, 0.0) if f is None else f
+    adt = alpha_l * dt
+    beta = adt / (2.0 * re)
+    rhs_u = dt * (gamma_l * hu + rho_l * h_prev[0]) + adt * (lu / re - gx + fx + fconst[0])
+    rhs_v = dt * (gamma_l * hv + rho_l * h_prev[1]) + adt * (lv / re - gy + fy + fconst[1])
+    rhs_w = dt * (gamma_l * hw + rho_l * h_prev[2]) + adt * (lw / re - gz + fz + fconst[2])
+    if g.walls:
+        rhs_w[0] = 0.0
+    du = sweep_z_centre(g, beta, sweep_y(g, beta, sweep_x(g, beta, rhs_u)))
+    dv = sweep_z_centre(g, beta, sweep_y(g, beta, sweep_x(g, beta, rhs_v)))
+    dw = sweep_z_face(g, beta, sweep_y(g, beta, sweep_x(g, beta, rhs_w)))
+    us, vs, ws = u + du, v + dv, w + dw
+    if g.walls:
+        ws[0] = 0.0
+    phi = oracle_poisson(g, op.divergence(g, us, vs, ws) / adt)
+    px, py, pz = op.gradient(g, phi)
+    return (us - adt * px, vs - adt * py, ws - adt * pz,
+            p + phi - beta * op.laplacian_p(g, phi), (hu, hv, hw))
+
+
+def oracle_step_rk3(g, state, f=None, re=100.0, dt=1e-3, cfl=0.0,
+                    fconst=(0.0, 0.0, 0.0)):
+    """One full RK3 step n -> n+1 (three sub-steps).  dt: given, or from the
+    CFL rule on u^n (fixed for the three sub-steps).  The stored history
+    H^{n-1} is not used (rho_1 = 0); the last sub-step's H is stored.
+    Returns (new_state, stats) as oracle_step."""
+    u, v, w, p = state["u"], state["v"], state["w"], state["p"]
+    w = op.wall_w(g, w)
+    if cfl > 0.0:
+        dt = oracle_cfl_dt(g, u, v, w, cfl)
+    h = (state["hu"], state["hv"], state["hw"])
+    for gam, rho in zip(RK3_GAMMA, RK3_RHO):
+        u, v, w, p, h = rk3_substep(g, u, v, w, p, h, dt, gam, rho, gam + rho, re, f, fconst)
+    new = {"u": u, "v": v, "w": w, "p": p, "hu": h[0], "hv": h[1], "hw": h[2],
+           "have_prev_h": 1}
+    stats = {"dt_used": dt}
+    stats.update(oracle_stats(g, u, v, w, dt))
+    return new, stats
