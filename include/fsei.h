@@ -108,6 +108,19 @@ typedef struct {
     int32_t have_prev_h;
 } fsei_state;
 
+/* Time-integration scheme of fsei_step_params.scheme (Sec. 2.1).
+ *   FSEI_AB2_CN: Eq. 3, Adams-Bashforth advection with weights gamma, rho,
+ *     Crank-Nicolson viscosity, one fractional step per time step;
+ *   FSEI_RK3_CN: the third-order Runge-Kutta variant the paper notes beside
+ *     it (low-storage scheme of its cited Rai & Moin / Verzicco & Orlandi):
+ *     three fractional sub-steps l = 1, 2, 3 with advection weights
+ *     gamma_l = 8/15, 5/12, 3/4 and rho_l = 0, -17/60, -5/12 (previous
+ *     sub-step), viscous, pressure and force terms over alpha_l dt with
+ *     alpha_l = gamma_l + rho_l, Crank-Nicolson within each sub-step.
+ *     params->gamma and ->rho are not used; dt (or the CFL rule on u^n) is
+ *     the full step's; H of the last sub-step is stored as the history. */
+typedef enum { FSEI_AB2_CN = 0, FSEI_RK3_CN = 1 } fsei_scheme;
+
 typedef struct {
     double re;          /* Reynolds number (> 0) */
     double dt;          /* time step when cfl <= 0 */
@@ -118,10 +131,11 @@ typedef struct {
     double gamma, rho;  /* Adams-Bashforth weights, normally 1.5, -0.5 */
     double fconst[3];   /* uniform body force added to f (e.g. a channel's
                            pressure-gradient drive 2/Re in x) */
+    int32_t scheme;     /* fsei_scheme (0: Adams-Bashforth, Eq. 3) */
 } fsei_step_params;
 
 typedef struct {
-    double dt_used;        /* dt of the last step */
+    double dt_used;        /* dt of the last step (the full step's dt) */
     double cfl;            /* dt_used * max_cells(...) of the new state */
     double max_div;        /* max over cells of |D u^{n+1}| */
     double kinetic_energy; /* 1/2 sum u^2 dV over all staggered points */

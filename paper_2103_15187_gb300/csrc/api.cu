@@ -425,6 +425,18 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     return FSEI_OK;
 }
 
+// StepArgs of a caller's parameters (one Adams-Bashforth step; run_steps
+// splits Runge-Kutta steps into their sub-steps)
+StepArgs step_args(const fsei_step_params &p) {
+    StepArgs a;
+    a.re = p.re; a.dt = p.dt; a.cfl = p.cfl; a.gamma = p.gamma; a.rho = p.rho;
+    for (int i = 0; i < 3; ++i) a.fconst[i] = p.fconst[i];
+    a.scheme = p.scheme;
+    a.alpha = 1.0;
+    a.substep = 0;
+    return a;
+}
+
 template <typename T>
 fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx, const void *fy,
                       const void *fz, const StepArgs &a, int nsteps, cudaStream_t st,
@@ -443,9 +455,23 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
         cudaMemsetAsync(&G->sc->speed_next, 0, sizeof(unsigned long long), st);
         tm.run(KK_SPEED, st, [&] { launch_speed<T>(g, F.u, F.v, F.w, G->sc, st); });
     }
-    for (int n = 0; n < nsteps; ++n) {
-        const int euler = (n == 0 && !s->have_prev_h) ? 1 : 0;
-        tm.run(KK_BEGIN, st, [&] { launch_step_scalars(g, G->sc, a, euler, st, W.pdl != 0); });
+    const bool rk3 = a.scheme == FSEI_RK3_CN;
+    const int subs = rk3 ? 3 : 1;
+    for (int n = 0; n < nsteps * subs; ++n) {
+        // Eq. 3 (one fractional step), or Runge-Kutta sub-step l = n % 3 as
+        // a fractional step over alpha_l dt with weights gamma_l / alpha_l,
+        // rho_l / alpha_l (rho_1 = 0: no history needed)
+        StepArgs b = a;
+        int euler = (n == 0 && !s->have_prev_h) ? 1 : 0;
+        if (rk3) {
+            const int l = n % 3;
+            b.alpha = kRk3Gamma[l] + kRk3Rho[l];
+            b.gamma = kRk3Gamma[l] / b.alpha;
+            b.rho = kRk3Rho[l] / b.alpha;
+            b.substep = l;
+            euler = 0;
+        }
+        tm.run(KK_BEGIN, st, [&] { launch_step_scalars(g, G->sc, b, euler, st, W.pdl != 0); });
         // the z-sweep plans depend on this step's beta and are first read by
         // the z sweep: they run on the side stream beside rhs_x and sweep_y
         const Overlap &op = G->ov_plans;
@@ -453,7 +479,7 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
         cudaStreamWaitEvent(op.side, op.fork, 0);
         tm.run(KK_PLANS, op.side, [&] { launch_step_plans<T>(g, W, G->sc, op.side); });
         cudaEventRecord(op.join, op.side);
-        tm.run(KK_RHS_X, st, [&] { launch_rhs_x<T>(g, F, W, G->sc, a, st); });
+        tm.run(KK_RHS_X, st, [&] { launch_rhs_x<T>(g, F, W, G->sc, b, st); });
         tm.run(KK_SWEEP_Y, st, [&] { launch_sweep_y<T>(g, W, G->sc, st); });
         cudaStreamWaitEvent(st, op.join, 0);
         tm.run(KK_SWEEP_Z, st, [&] { launch_sweep_z<T>(g, F, W, st); });
@@ -554,8 +580,9 @@ fsei_status tune_grid(fsei_grid_s *G, Work<T> &W, int reps, cudaStream_t st) {
     s.u = buf; s.v = buf + ncell; s.w = buf + 2 * ncell; s.p = buf + 3 * ncell;
     s.hu = buf + 4 * ncell; s.hv = buf + 5 * ncell; s.hw = buf + 6 * ncell;
     s.have_prev_h = 1;
-    StepArgs a;
-    a.re = 1000.0; a.dt = 1e-4; a.cfl = 0.0; a.gamma = 1.5; a.rho = -0.5;
+    fsei_step_params tp = {};
+    tp.re = 1000.0; tp.dt = 1e-4; tp.gamma = 1.5; tp.rho = -0.5;
+    StepArgs a = step_args(tp);
     a.fconst[0] = a.fconst[1] = a.fconst[2] = 0.0;
 
     KernelTimer &tm = G->timer;
@@ -876,9 +903,9 @@ fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy
         if (fo[i] && !aligned16(fo[i])) return fail(FSEI_E_ARG, "force %d not 16-byte aligned", i);
     if (!(prm->re > 0)) return fail(FSEI_E_ARG, "re must be > 0");
     if (!(prm->cfl > 0) && !(prm->dt > 0)) return fail(FSEI_E_ARG, "need dt > 0 or cfl > 0");
-    StepArgs a;
-    a.re = prm->re; a.dt = prm->dt; a.cfl = prm->cfl; a.gamma = prm->gamma; a.rho = prm->rho;
-    for (int i = 0; i < 3; ++i) a.fconst[i] = prm->fconst[i];
+    if (prm->scheme != FSEI_AB2_CN && prm->scheme != FSEI_RK3_CN)
+        return fail(FSEI_E_ARG, "unknown scheme %d", prm->scheme);
+    const StepArgs a = step_args(*prm);
     DeviceGuard dg(G->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     fsei_status r = FSEI_OK;
@@ -893,9 +920,9 @@ fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy
         const cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return fail(FSEI_E_CUDA, "fsei_step: %s", cudaGetErrorString(e));
         const StepScalars &h = *G->sc_host;
-        out->dt_used = h.dt;
+        out->dt_used = h.dt_step;
         const double spd = __builtin_bit_cast(double, h.speed_next);
-        out->cfl = h.dt * spd;
+        out->cfl = h.dt_step * spd;
         out->max_div = __builtin_bit_cast(double, h.maxdiv);
         out->kinetic_energy = h.ke;
         out->flags = h.flags;
@@ -924,9 +951,11 @@ fsei_status fsei_adjoint_step(fsei_grid G, const fsei_state *fwd, const fsei_ste
     if (!(prm->re > 0)) return fail(FSEI_E_ARG, "re must be > 0");
     if (prm->cfl > 0) return fail(FSEI_E_ARG, "the adjoint needs a frozen dt: pass cfl = 0 and the dt of the forward step");
     if (!(prm->dt > 0)) return fail(FSEI_E_ARG, "dt must be > 0");
-    StepArgs a;
-    a.re = prm->re; a.dt = prm->dt; a.cfl = 0.0; a.gamma = prm->gamma; a.rho = prm->rho;
-    for (int i = 0; i < 3; ++i) a.fconst[i] = prm->fconst[i];
+    if (prm->scheme != FSEI_AB2_CN)
+        return fail(prm->scheme == FSEI_RK3_CN ? FSEI_E_UNSUPPORTED : FSEI_E_ARG,
+                    "the adjoint step is implemented for the Adams-Bashforth scheme only");
+    StepArgs a = step_args(*prm);
+    a.cfl = 0.0;
     DeviceGuard dg(G->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     auto run = [&](auto &W, auto tag) -> fsei_status {
@@ -1060,10 +1089,7 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
     for (size_t i = 0; i < B->grids.size() && r == FSEI_OK; ++i) {
         fsei_grid_s *G = B->grids[i];
         cudaStream_t st = B->branches[i % B->branches.size()];
-        StepArgs a;
-        a.re = prm[i].re; a.dt = prm[i].dt; a.cfl = prm[i].cfl;
-        a.gamma = prm[i].gamma; a.rho = prm[i].rho;
-        for (int c = 0; c < 3; ++c) a.fconst[c] = prm[i].fconst[c];
+        const StepArgs a = step_args(prm[i]);
         fsei_state s = states[i];
         if (!first) s.have_prev_h = 1;
         const void *f0 = forces ? forces[3 * i] : nullptr;
@@ -1193,6 +1219,8 @@ fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const 
             if (forces[3 * i + c] && !aligned16(forces[3 * i + c])) return fail(FSEI_E_ARG, "box %zu: force %d misaligned", i, c);
         if (!(prm[i].re > 0)) return fail(FSEI_E_ARG, "box %zu: re must be > 0", i);
         if (!(prm[i].cfl > 0) && !(prm[i].dt > 0)) return fail(FSEI_E_ARG, "box %zu: need dt > 0 or cfl > 0", i);
+        if (prm[i].scheme != FSEI_AB2_CN && prm[i].scheme != FSEI_RK3_CN)
+            return fail(FSEI_E_ARG, "box %zu: unknown scheme %d", i, prm[i].scheme);
     }
     DeviceGuard dg(B->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -1238,8 +1266,8 @@ fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const 
         fsei_status worst = FSEI_OK;
         for (size_t i = 0; i < nb; ++i) {
             const StepScalars &h = *B->grids[i]->sc_host;
-            out[i].dt_used = h.dt;
-            out[i].cfl = h.dt * __builtin_bit_cast(double, h.speed_next);
+            out[i].dt_used = h.dt_step;
+            out[i].cfl = h.dt_step * __builtin_bit_cast(double, h.speed_next);
             out[i].max_div = __builtin_bit_cast(double, h.maxdiv);
             out[i].kinetic_energy = h.ke;
             out[i].flags = h.flags;

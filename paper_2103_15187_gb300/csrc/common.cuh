@@ -86,7 +86,9 @@ template <> struct Metric<float> {
 // the reductions; read by every kernel so that dt computed from the CFL
 // condition never visits the host).
 struct StepScalars {
-    double dt;            // this step's dt
+    double dt;            // this fractional step's dt (alpha dt_n)
+    double dt_step;       // dt_n of the full time step (equal to dt unless
+                          // the step is split into Runge-Kutta sub-steps)
     double beta;          // dt / (2 Re)
     double gamma, rho;    // Adams-Bashforth weights of this step
     unsigned long long speed_cur;   // bits of max(|u_c|/dx+...) of u^n

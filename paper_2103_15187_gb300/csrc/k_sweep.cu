@@ -134,8 +134,10 @@ __device__ void uni_factors(double r, double &alpha, double &cinv) {
 
 // Three warps, so that the serial double-precision chains (each a division
 // or square root at a time on GB300's narrow FP64 pipe) run side by side:
-// every warp forms dt and beta; warp 0 the x factors, warp 1 the y factors,
-// warp 2 1/dt, the AB2 weights and the reset of the step's reductions.
+// every warp forms dt and beta (alpha dt_n, dt_n from dt or the CFL rule at
+// substep 0, kept from substep 0 after it); warp 0 the x factors, warp 1 the
+// y factors, warp 2 1/dt, the advection weights and the reset of the step's
+// reductions.
 // Lane 0 of each warp stores.
 __global__ void __launch_bounds__(96) k_scalars(StepScalars *sc, StepArgs a, int euler,
                                                 double idx2, double idy2) {
@@ -144,11 +146,14 @@ __global__ void __launch_bounds__(96) k_scalars(StepScalars *sc, StepArgs a, int
     const int wid = threadIdx.x >> 5;
     const bool lead = (threadIdx.x & 31) == 0;
     const unsigned long long spd = sc->speed_next;
-    double dt = a.dt;
-    if (a.cfl > 0.0) {
+    double dt_step = a.dt;
+    if (a.substep > 0) {
+        dt_step = sc->dt_step;   // the full step's dt, formed at substep 0
+    } else if (a.cfl > 0.0) {
         const double s = bitsd(spd);
-        dt = s > 0.0 ? a.cfl / s : a.dt;
+        dt_step = s > 0.0 ? a.cfl / s : a.dt;
     }
+    const double dt = a.alpha * dt_step;
     const double beta = dt / (2.0 * a.re);
     __syncthreads();   // every warp has read speed_next before warp 2 resets it
     if (wid == 0) {
@@ -177,6 +182,7 @@ __global__ void __launch_bounds__(96) k_scalars(StepScalars *sc, StepArgs a, int
         sc->ke = 0.0;
         sc->flags = 0;
         sc->dt = dt;
+        sc->dt_step = dt_step;
         sc->beta = beta;
         sc->gamma = euler ? 1.0 : a.gamma;
         sc->rho = euler ? 0.0 : a.rho;

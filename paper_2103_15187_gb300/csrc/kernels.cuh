@@ -79,10 +79,25 @@ template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*
 template <typename T> Schedule schedule_of(const GridDev &g, const Work<T> &W);
 template <typename T> void apply_schedule(Work<T> &W, const Schedule &s);
 
+// Parameters of one fractional step or sub-step.  dt and cfl give the time
+// step dt_n of the full step (dt, or cfl / speed of u^n, formed at substep
+// 0); the fractional step itself advances by alpha dt_n with the
+// Adams-Bashforth-style weights gamma, rho: with alpha = 1 and substep = 0
+// that is Eq. 3, and the Runge-Kutta sub-steps pass alpha_l and
+// gamma_l / alpha_l, rho_l / alpha_l (their advection weights relative to
+// the sub-interval).
 struct StepArgs {
     double re, dt, cfl, gamma, rho;
     double fconst[3];
+    int scheme;      // fsei_scheme
+    double alpha;    // fraction of dt_n this fractional step covers
+    int substep;     // 0: forms dt_n; > 0: reuses it
 };
+// The three sub-steps of the third-order Runge-Kutta scheme: advection
+// weights gamma_l (this sub-step) and rho_l (previous one); the linear terms
+// over alpha_l = gamma_l + rho_l of the step.
+constexpr double kRk3Gamma[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+constexpr double kRk3Rho[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 
 template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v, const T *w,
                                         StepScalars *sc, cudaStream_t st);

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "FSEI_OK", 1: "FSEI_E_ARG", 2: "FSEI_E_SHAPE",
                 6: "FSEI_E_NONFINITE", 7: "FSEI_E_CFL"}
 FSEI_FP64, FSEI_MIXED = 0, 1
 FSEI_Z_PERIODIC, FSEI_Z_WALLS = 0, 1
+FSEI_AB2_CN, FSEI_RK3_CN = 0, 1
 FLAG_NONFINITE, FLAG_CFL = 1, 2
 
 # exported symbols and their C signatures (kept in step with include/fsei.h)
@@ -64,7 +65,7 @@ class State(ctypes.Structure):
 class StepParams(ctypes.Structure):
     _fields_ = [("re", ctypes.c_double), ("dt", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("rho", ctypes.c_double),
-                ("fconst", ctypes.c_double * 3)]
+                ("fconst", ctypes.c_double * 3), ("scheme", ctypes.c_int32)]
 
 
 class StepStats(ctypes.Structure):
@@ -238,16 +239,17 @@ def grid_create(**kw):
 
 
 def step(grid, state, f=None, re=100.0, dt=1e-3, cfl=0.0, gamma=1.5, rho=-0.5,
-         fconst=(0.0, 0.0, 0.0), nsteps=1, stream=None, stats=True):
+         fconst=(0.0, 0.0, 0.0), nsteps=1, stream=None, stats=True, scheme=FSEI_AB2_CN):
     """fsei_step on a dict of torch tensors u, v, w, p, hu, hv, hw and the
     key have_prev_h (updated in place).  f: None or (fx, fy, fz) tensors.
+    scheme: FSEI_AB2_CN (Eq. 3) or FSEI_RK3_CN (three sub-steps per step).
     Returns the statistics dict of the last step when stats=True (the call
     then synchronises the stream), else None."""
     lib = load()
     st = State(_ptr(state["u"]), _ptr(state["v"]), _ptr(state["w"]), _ptr(state["p"]),
                _ptr(state["hu"]), _ptr(state["hv"]), _ptr(state["hw"]),
                int(state.get("have_prev_h", 0)))
-    prm = StepParams(re, dt, cfl, gamma, rho, (ctypes.c_double * 3)(*fconst))
+    prm = StepParams(re, dt, cfl, gamma, rho, (ctypes.c_double * 3)(*fconst), int(scheme))
     fx, fy, fz = (None, None, None) if f is None else f
     out = StepStats() if stats else None
     status = lib.fsei_step(grid.handle, ctypes.byref(st), _ptr(fx), _ptr(fy), _ptr(fz),
@@ -325,7 +327,8 @@ class Batch:
 def batch_step(batch, states, forces, params, nsteps=1, stream=None, stats=True):
     """fsei_batch_step.  states: list of state dicts (as for step); forces:
     None or list of None / (fx, fy, fz); params: list of dicts with re, dt,
-    cfl, gamma, rho, fconst.  Returns the per-box statistics when stats."""
+    cfl, gamma, rho, fconst and optionally scheme.  Returns the per-box
+    statistics when stats."""
     lib = load()
     n = batch.n
     st = (State * n)()
@@ -342,7 +345,8 @@ def batch_step(batch, states, forces, params, nsteps=1, stream=None, stats=True)
     for i, p in enumerate(params):
         prm[i] = StepParams(p.get("re", 100.0), p.get("dt", 0.0), p.get("cfl", 0.0),
                             p.get("gamma", 1.5), p.get("rho", -0.5),
-                            (ctypes.c_double * 3)(*p.get("fconst", (0.0, 0.0, 0.0))))
+                            (ctypes.c_double * 3)(*p.get("fconst", (0.0, 0.0, 0.0))),
+                            int(p.get("scheme", FSEI_AB2_CN)))
     out = (StepStats * n)() if stats else None
     status = lib.fsei_batch_step(batch.handle, st, fp, prm, int(nsteps), _stream_handle(stream),
                                  out)

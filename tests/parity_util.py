@@ -5,7 +5,7 @@ same seeded inputs, and compare field by field."""
 import numpy as np
 
 from oracle.grid import Grid as OGrid
-from oracle.step import oracle_step
+from oracle.step import oracle_step, oracle_step_rk3
 
 FIELDS = ("u", "v", "w", "p", "hu", "hv", "hw")
 
@@ -26,12 +26,16 @@ def params(case):
     return dict(re=case.re, dt=case.dt, cfl=case.cfl, fconst=case.fconst)
 
 
-def run_oracle(case, nsteps, state=None):
+def run_oracle(case, nsteps, state=None, scheme=0):
+    """nsteps oracle steps: Eq. 3 (scheme 0) or the RK3 variant (scheme 1)."""
     g = oracle_grid(case)
     s = initial_state_np(case) if state is None else state
     stats = []
     for _ in range(nsteps):
-        s, st = oracle_step(g, s, case.f, **params(case))
+        if scheme == 1:
+            s, st = oracle_step_rk3(g, s, case.f, **params(case))
+        else:
+            s, st = oracle_step(g, s, case.f, **params(case))
         stats.append(st)
     return s, stats
 
@@ -57,9 +61,10 @@ def force_device(case, dtype):
     return tuple(torch.tensor(a, dtype=dtype, device="cuda").contiguous() for a in case.f)
 
 
-def run_gpu(case, nsteps, prec, grid=None, per_call=None):
+def run_gpu(case, nsteps, prec, grid=None, per_call=None, scheme=0):
     """Advance the case nsteps on the GPU; returns (numpy state, last stats).
-    per_call: steps per fsei_step call (default: all in one call)."""
+    per_call: steps per fsei_step call (default: all in one call); scheme:
+    0 Adams-Bashforth (Eq. 3), 1 the RK3 variant."""
     import torch
     from paper_2103_15187_gb300 import fsei
     dtype = torch.float64 if prec == fsei.FSEI_FP64 else torch.float32
@@ -71,7 +76,7 @@ def run_gpu(case, nsteps, prec, grid=None, per_call=None):
     done = 0
     while done < nsteps:
         n = min(per_call, nsteps - done)
-        stats = fsei.step(g, st, f, nsteps=n, **params(case))
+        stats = fsei.step(g, st, f, nsteps=n, scheme=scheme, **params(case))
         done += n
     torch.cuda.synchronize()
     out = {k: st[k].double().cpu().numpy() for k in FIELDS}
