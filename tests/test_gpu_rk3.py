@@ -43,10 +43,10 @@ def test_rk3_taylor_green_fp64(fsei):
 @pytest.mark.parametrize("shape", [(48, 24, 36), (48, 36, 17)])
 def test_rk3_forced_channel_cfl_fp64(fsei, shape):
     """Stretched channel with Gaussian-blob force, Poiseuille drive and CFL
-    1.0 (the full step's dt from u^n, shared by the sub-steps); two calls of
+    0.8 (the full step's dt from u^n, shared by the sub-steps); two calls of
     three steps (the second starts from the stored history flag)."""
     nx, ny, nz = shape
-    case = inputs.case_channel(nx, ny, nz, steps=6, kmax=4.0, rms=0.3, seed=nx + 1, cfl=1.0,
+    case = inputs.case_channel(nx, ny, nz, steps=6, kmax=4.0, rms=0.3, seed=nx + 1, cfl=0.8,
                                blobs=dict(nblobs=3, sigma=3.0, amp=10.0))
     gpu, st = pu.run_gpu(case, 6, fsei.FSEI_FP64, per_call=3, scheme=RK3)
     ref, rst = pu.run_oracle(case, 6, scheme=RK3)
@@ -57,7 +57,7 @@ def test_rk3_forced_channel_cfl_fp64(fsei, shape):
 
 
 def test_rk3_mixed_channel_50_steps(fsei):
-    case = inputs.case_channel(64, 64, 64, steps=50, seed=2, cfl=1.0)
+    case = inputs.case_channel(64, 64, 64, steps=50, seed=2, cfl=0.8)
     gpu, _ = pu.run_gpu(case, 50, fsei.FSEI_MIXED, scheme=RK3)
     ref, _ = pu.run_oracle(case, 50, scheme=RK3)
     err = _vel_err(gpu, ref)
@@ -67,7 +67,7 @@ def test_rk3_mixed_channel_50_steps(fsei):
 def test_rk3_batch_equals_solo(fsei):
     import torch
     cases = [inputs.case_taylor_green(16, steps=3, dt=5e-3),
-             inputs.case_channel(24, 12, 18, steps=3, seed=30, re=700.0, cfl=1.0)]
+             inputs.case_channel(24, 12, 18, steps=3, seed=30, re=700.0, cfl=0.8)]
     batch = fsei.Batch([dict(nx=c.nx, ny=c.ny, nz=c.nz, lx=c.lx, ly=c.ly, zbc=c.zbc, lz=c.lz,
                              stretch=c.stretch, prec=fsei.FSEI_FP64) for c in cases])
     states = [pu.to_device(pu.initial_state_np(c), torch.float64) for c in cases]
