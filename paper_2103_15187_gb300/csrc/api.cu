@@ -18,6 +18,13 @@
 
 using namespace fsei;
 
+namespace fsei {
+LaunchRecorder *&launch_recorder() {
+    static thread_local LaunchRecorder *rec = nullptr;
+    return rec;
+}
+}  // namespace fsei
+
 namespace {
 
 thread_local std::string g_err;
@@ -452,7 +459,7 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
     // pairs time each kernel
     W.pdl = !tm.on ? 1 : 0;
     if (a.cfl > 0.0 && with_speed) {
-        cudaMemsetAsync(&G->sc->speed_next, 0, sizeof(unsigned long long), st);
+        memset_async(&G->sc->speed_next, 0, sizeof(unsigned long long), st);
         tm.run(KK_SPEED, st, [&] { launch_speed<T>(g, F.u, F.v, F.w, G->sc, st); });
     }
     const bool rk3 = a.scheme == FSEI_RK3_CN;
@@ -475,13 +482,11 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
         // the z-sweep plans depend on this step's beta and are first read by
         // the z sweep: they run on the side stream beside rhs_x and sweep_y
         const Overlap &op = G->ov_plans;
-        cudaEventRecord(op.fork, st);
-        cudaStreamWaitEvent(op.side, op.fork, 0);
+        fork_side(op, st);
         tm.run(KK_PLANS, op.side, [&] { launch_step_plans<T>(g, W, G->sc, op.side); });
-        cudaEventRecord(op.join, op.side);
         tm.run(KK_RHS_X, st, [&] { launch_rhs_x<T>(g, F, W, G->sc, b, st); });
         tm.run(KK_SWEEP_Y, st, [&] { launch_sweep_y<T>(g, W, G->sc, st); });
-        cudaStreamWaitEvent(st, op.join, 0);
+        join_side(op, st);
         tm.run(KK_SWEEP_Z, st, [&] { launch_sweep_z<T>(g, F, W, st); });
         tm.run(KK_RFFT_X, st, [&] { launch_rfft_x<T>(g, W, G->sc, nullptr, 0, st); });
         tm.run(KK_FFT_Y, st, [&] { launch_fft_y<T>(g, W, 0, st); });
@@ -1034,78 +1039,202 @@ const char *fsei_kernel_name(int32_t kind) {
 }  // extern "C"
 
 // ------------------------------------------------------------- batches ----
-// An ensemble of independent grids advanced together.  One step of every
-// box is captured into a CUDA graph whose per-box kernel chains sit on
-// parallel branches (the capture forks over library-owned streams), so the
-// boxes' kernels overlap on the GPU; the graph is replayed once per step on
-// the caller's stream.  Two graphs are kept: the first step of a call (CFL
-// pre-pass, Euler start for boxes without history) and the following steps.
-// They are re-captured when the state pointers, forces or parameters of a
-// call differ from the captured ones.
+// An ensemble of independent grids advanced together.  Boxes with the same
+// grid description (extents, lengths, z mesh, precision) and launch schedule
+// form a group: every pass of the step (scalars, z-sweep plans, RHS + x
+// sweep, y and z sweeps, the transforms and z Poisson solve, the projection)
+// is one launch over all boxes of the group, box b in blockIdx.z with its own
+// arguments (fields, workspace, step parameters) from a device table.  One
+// step of every group is captured into a CUDA graph, the groups on parallel
+// branches, and the graph is replayed once per step on the caller's stream.
+// Two graphs are kept: the first step of a call (CFL pre-pass, Euler start
+// for boxes without history) and the following steps.  They are re-captured
+// when the state pointers, forces or parameters of a call differ from the
+// captured ones.
 struct fsei_batch_s {
     std::vector<fsei_grid> grids;
+    std::vector<std::vector<unsigned char>> desc_key;   // per box: its description
     int device = 0;
     std::vector<cudaStream_t> branches;
     cudaStream_t capture = nullptr;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> joins;
     cudaGraphExec_t first = nullptr, rest = nullptr;
+    void *tab_first = nullptr, *tab_rest = nullptr;    // argument tables of the graphs
     std::vector<unsigned char> key;   // bytes of the captured call's arguments
+    int ngroups = 0;                  // groups of the last capture
 };
 
 namespace {
 
 void batch_clear_graphs(fsei_batch_s *B) {
+    if (B->tab_first || B->tab_rest) cudaDeviceSynchronize();   // no replay still reads them
     if (B->first) cudaGraphExecDestroy(B->first);
     if (B->rest) cudaGraphExecDestroy(B->rest);
+    if (B->tab_first) cudaFree(B->tab_first);
+    if (B->tab_rest) cudaFree(B->tab_rest);
     B->first = B->rest = nullptr;
+    B->tab_first = B->tab_rest = nullptr;
     B->key.clear();
 }
 
+template <typename X> void put_bytes(std::vector<unsigned char> &v, const X &x) {
+    const unsigned char *c = reinterpret_cast<const unsigned char *>(&x);
+    v.insert(v.end(), c, c + sizeof(X));
+}
+
+// the description of a box as bytes (faces copied when given)
+std::vector<unsigned char> desc_bytes(const fsei_grid_desc &d) {
+    std::vector<unsigned char> k;
+    put_bytes(k, d.nx); put_bytes(k, d.ny); put_bytes(k, d.nz);
+    put_bytes(k, d.lx); put_bytes(k, d.ly); put_bytes(k, d.zbc); put_bytes(k, d.lz);
+    put_bytes(k, d.stretch); put_bytes(k, d.prec); put_bytes(k, d.near_zero_tau);
+    const int has = d.zfaces ? 1 : 0;
+    put_bytes(k, has);
+    if (has)
+        for (int i = 0; i <= d.nz; ++i) put_bytes(k, d.zfaces[i]);
+    return k;
+}
+
+// two recorded steps launch the same kernels with the same shapes
+bool same_launches(const std::vector<RecordedOp> &a, const std::vector<RecordedOp> &b,
+                   cudaStream_t side_a, cudaStream_t side_b) {
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const RecordedOp &x = a[i], &y = b[i];
+        if (x.kind != y.kind || (x.st == side_a) != (y.st == side_b)) return false;
+        if (x.kind == RecordedOp::KERNEL &&
+            (x.entry != y.entry || x.grid.x != y.grid.x || x.grid.y != y.grid.y ||
+             x.block.x != y.block.x || x.block.y != y.block.y || x.block.z != y.block.z ||
+             x.smem != y.smem || x.pdl != y.pdl || x.args.size() != y.args.size()))
+            return false;
+        if (x.kind == RecordedOp::MEMSET && x.mem_bytes != y.mem_bytes) return false;
+    }
+    return true;
+}
+
 fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const *forces,
-                          const fsei_step_params *prm, bool first, cudaGraphExec_t *out) {
-    cudaStream_t cs = B->capture;
-    cudaGetLastError();
-    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-    if (ce != cudaSuccess)
-        return fail(FSEI_E_CUDA, "batch: cannot begin graph capture: %s", cudaGetErrorString(ce));
-    ce = cudaEventRecord(B->fork, cs);
-    if (ce != cudaSuccess) {
-        cudaGraph_t gdead = nullptr;
-        cudaStreamEndCapture(cs, &gdead);
-        if (gdead) cudaGraphDestroy(gdead);
-        return fail(FSEI_E_CUDA, "batch: fork record: %s", cudaGetErrorString(ce));
-    }
-    for (cudaStream_t b : B->branches) {
-        ce = cudaStreamWaitEvent(b, B->fork, 0);
-        if (ce != cudaSuccess) {
-            cudaGraph_t gdead = nullptr;
-            cudaStreamEndCapture(cs, &gdead);
-            if (gdead) cudaGraphDestroy(gdead);
-            return fail(FSEI_E_CUDA, "batch: fork wait: %s", cudaGetErrorString(ce));
-        }
-    }
-    fsei_status r = FSEI_OK;
-    for (size_t i = 0; i < B->grids.size() && r == FSEI_OK; ++i) {
+                          const fsei_step_params *prm, bool first, cudaGraphExec_t *out,
+                          void **tab_out) {
+    const size_t nb = B->grids.size();
+    // 1. one recorded step per box (nothing is launched)
+    std::vector<std::vector<RecordedOp>> rec(nb);
+    const cudaStream_t main_tag = B->capture;   // stands for the box's main stream
+    for (size_t i = 0; i < nb; ++i) {
         fsei_grid_s *G = B->grids[i];
-        cudaStream_t st = B->branches[i % B->branches.size()];
         const StepArgs a = step_args(prm[i]);
         fsei_state s = states[i];
         if (!first) s.have_prev_h = 1;
         const void *f0 = forces ? forces[3 * i] : nullptr;
         const void *f1 = forces ? forces[3 * i + 1] : nullptr;
         const void *f2 = forces ? forces[3 * i + 2] : nullptr;
-        G->timer.check = true;
-        G->timer.fail_kind = -1;
-        r = G->prec == FSEI_FP64 ? run_steps<double>(G, G->wd, &s, f0, f1, f2, a, 1, st, first)
-                                 : run_steps<float>(G, G->wf, &s, f0, f1, f2, a, 1, st, first);
-        G->timer.check = false;
-        if (r != FSEI_OK) {
+        LaunchRecorder r;
+        launch_recorder() = &r;
+        const bool timing = G->timer.on;
+        G->timer.on = false;
+        const fsei_status st = G->prec == FSEI_FP64
+                                   ? run_steps<double>(G, G->wd, &s, f0, f1, f2, a, 1, main_tag, first)
+                                   : run_steps<float>(G, G->wf, &s, f0, f1, f2, a, 1, main_tag, first);
+        G->timer.on = timing;
+        launch_recorder() = nullptr;
+        if (st != FSEI_OK) {
             const std::string msg = g_err;
-            r = fail(r, "batch capture, box %zu (%s graph), first failing launch: %s (%s); %s", i,
-                     first ? "first" : "rest",
-                     G->timer.fail_kind >= 0 ? kKernelNames[G->timer.fail_kind] : "-",
-                     cudaGetErrorString(G->timer.fail_err), msg.c_str());
+            return fail(st, "batch: box %zu: %s", i, msg.c_str());
+        }
+        rec[i] = std::move(r.ops);
+    }
+    // 2. groups: same description, schedule and launch sequence
+    std::vector<std::vector<size_t>> groups;
+    std::vector<std::vector<unsigned char>> gkeys;
+    for (size_t i = 0; i < nb; ++i) {
+        std::vector<unsigned char> k = B->desc_key[i];
+        put_bytes(k, grid_schedule(B->grids[i]));
+        size_t gi = 0;
+        for (; gi < groups.size(); ++gi) {
+            const size_t b0 = groups[gi][0];
+            if (gkeys[gi] == k && same_launches(rec[b0], rec[i], B->grids[b0]->ov_plans.side,
+                                                B->grids[i]->ov_plans.side))
+                break;
+        }
+        if (gi == groups.size()) {
+            groups.emplace_back();
+            gkeys.push_back(k);
+        }
+        groups[gi].push_back(i);
+    }
+    // 3. argument tables: for every kernel of a group, one row per box
+    std::vector<std::vector<size_t>> tab_off(groups.size());
+    size_t tab_bytes = 0;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const std::vector<RecordedOp> &ops = rec[groups[gi][0]];
+        for (size_t o = 0; o < ops.size(); ++o) {
+            tab_off[gi].push_back(tab_bytes);
+            if (ops[o].kind == RecordedOp::KERNEL)
+                tab_bytes += (ops[o].args.size() * groups[gi].size() + 255) & ~size_t(255);
+        }
+    }
+    std::vector<unsigned char> host(tab_bytes ? tab_bytes : 1);
+    for (size_t gi = 0; gi < groups.size(); ++gi)
+        for (size_t o = 0; o < rec[groups[gi][0]].size(); ++o) {
+            if (rec[groups[gi][0]][o].kind != RecordedOp::KERNEL) continue;
+            size_t at = tab_off[gi][o];
+            for (size_t b : groups[gi]) {
+                const std::vector<unsigned char> &ab = rec[b][o].args;
+                memcpy(host.data() + at, ab.data(), ab.size());
+                at += ab.size();
+            }
+            rec[groups[gi][0]][o].prepare_group();   // load it outside the capture
+        }
+    void *tab = nullptr;
+    if (cudaMalloc(&tab, host.size()) != cudaSuccess)
+        return fail(FSEI_E_NOMEM, "batch: argument tables (%zu bytes)", host.size());
+    if (cudaMemcpy(tab, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(tab);
+        return fail(FSEI_E_CUDA, "batch: argument table upload failed");
+    }
+    // 4. capture: every group on a branch, its side stream for the plans
+    cudaStream_t cs = B->capture;
+    cudaGetLastError();
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) {
+        cudaFree(tab);
+        return fail(FSEI_E_CUDA, "batch: cannot begin graph capture: %s", cudaGetErrorString(ce));
+    }
+    ce = cudaEventRecord(B->fork, cs);
+    for (cudaStream_t b : B->branches)
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b, B->fork, 0);
+    fsei_status r = ce == cudaSuccess ? FSEI_OK
+                                      : fail(FSEI_E_CUDA, "batch: fork: %s", cudaGetErrorString(ce));
+    for (size_t gi = 0; gi < groups.size() && r == FSEI_OK; ++gi) {
+        const std::vector<size_t> &bx = groups[gi];
+        fsei_grid_s *G0 = B->grids[bx[0]];
+        const Overlap &ov = G0->ov_plans;
+        const cudaStream_t mst = B->branches[gi % B->branches.size()];
+        const std::vector<RecordedOp> &ops = rec[bx[0]];
+        for (size_t o = 0; o < ops.size() && r == FSEI_OK; ++o) {
+            const RecordedOp &op = ops[o];
+            const cudaStream_t st = op.st == ov.side ? ov.side : mst;
+            switch (op.kind) {
+            case RecordedOp::KERNEL:
+                op.launch_group(static_cast<unsigned char *>(tab) + tab_off[gi][o], (int)bx.size(),
+                                op.grid, op.block, op.smem, st, op.pdl);
+                break;
+            case RecordedOp::MEMSET:
+                for (size_t b : bx) cudaMemsetAsync(rec[b][o].mem, 0, rec[b][o].mem_bytes, st);
+                break;
+            case RecordedOp::FORK:
+                cudaEventRecord(ov.fork, mst);
+                cudaStreamWaitEvent(ov.side, ov.fork, 0);
+                break;
+            case RecordedOp::JOIN:
+                cudaEventRecord(ov.join, ov.side);
+                cudaStreamWaitEvent(mst, ov.join, 0);
+                break;
+            }
+            const cudaError_t e = cudaPeekAtLastError();
+            if (e != cudaSuccess)
+                r = fail(FSEI_E_CUDA, "batch capture, group %zu (%zu boxes from box %zu), launch %zu: %s",
+                         gi, bx.size(), bx[0], o, cudaGetErrorString(e));
         }
     }
     for (size_t b = 0; b < B->branches.size(); ++b) {
@@ -1114,14 +1243,21 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (r == FSEI_OK && (e != cudaSuccess || !graph))
+        r = fail(FSEI_E_CUDA, "batch: capture failed: %s", cudaGetErrorString(e));
+    if (r == FSEI_OK) {
+        const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+        if (ei != cudaSuccess)
+            r = fail(FSEI_E_CUDA, "batch: graph instantiation failed: %s", cudaGetErrorString(ei));
+    }
+    if (graph) cudaGraphDestroy(graph);
     if (r != FSEI_OK) {
-        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        cudaFree(tab);
         return r;
     }
-    if (e != cudaSuccess || !graph) return fail(FSEI_E_CUDA, "batch: capture failed: %s", cudaGetErrorString(e));
-    const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ei != cudaSuccess) return fail(FSEI_E_CUDA, "batch: graph instantiation failed: %s", cudaGetErrorString(ei));
+    *tab_out = tab;
+    B->ngroups = (int)groups.size();
     return FSEI_OK;
 }
 
@@ -1144,6 +1280,7 @@ fsei_status fsei_batch_create(const fsei_grid_desc *descs, int32_t nboxes, fsei_
             return fail(st, "box %d: %s", i, msg.c_str());
         }
         B->grids.push_back(g);
+        B->desc_key.push_back(desc_bytes(descs[i]));
     }
     const int nb = nboxes < 8 ? nboxes : 8;
     B->branches.resize(nb);
@@ -1242,8 +1379,8 @@ fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const 
         }
         if (key != B->key || !B->first) {
             batch_clear_graphs(B);
-            fsei_status r = batch_capture(B, states, forces, prm, true, &B->first);
-            if (r == FSEI_OK) r = batch_capture(B, states, forces, prm, false, &B->rest);
+            fsei_status r = batch_capture(B, states, forces, prm, true, &B->first, &B->tab_first);
+            if (r == FSEI_OK) r = batch_capture(B, states, forces, prm, false, &B->rest, &B->tab_rest);
             if (r != FSEI_OK) {
                 batch_clear_graphs(B);
                 return r;

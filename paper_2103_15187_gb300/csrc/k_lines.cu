@@ -170,7 +170,7 @@ __device__ __forceinline__ void sweep_reg_body(const GridDev &g, const Fields<T>
 }
 
 template <typename T, int L, int DIR, int MODE>
-__global__ void __launch_bounds__(L <= 16 ? 256 : 512, L <= 16 ? (sizeof(T) == 4 ? 3 : 2) : 1)
+FSEI_D void
 k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
             T *__restrict__ q2, TriPlan<T> pa, TriPlan<T> pb, int tx) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -193,7 +193,7 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
 // Single precision, L <= 16: 5 blocks per SM (48 registers, no spills;
 // 256^3: 84 -> 79 us against 4 blocks).
 template <typename T, int L, bool EXACT>
-__global__ void __launch_bounds__(256, L <= 16 ? (sizeof(T) == 4 ? 5 : 2) : (sizeof(T) == 4 ? 2 : 1))
+FSEI_D void
 k_sweep_y_uni(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
               const StepScalars *sc, int P, int tx) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -226,6 +226,16 @@ k_sweep_y_uni(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__
         if (active && i < len) qs[i * nx] = d[i];
 }
 
+// the kernels with their launch bounds
+template <typename T, int L, int DIR, int MODE>
+constexpr Kernel<k_sweep_reg<T, L, DIR, MODE>, (L <= 16 ? 256 : 512),
+                 (L <= 16 ? (sizeof(T) == 4 ? 3 : 2) : 1)>
+    K_sweep_reg{};
+template <typename T, int L, bool EXACT>
+constexpr Kernel<k_sweep_y_uni<T, L, EXACT>, 256,
+                 (L <= 16 ? (sizeof(T) == 4 ? 5 : 2) : (sizeof(T) == 4 ? 2 : 1))>
+    K_sweep_y_uni{};
+
 template <typename T, int L, int DIR, int MODE>
 void launch_reg(const GridDev &g, const Fields<T> &F, Work<T> &W, const TriPlan<T> &pa,
                 const TriPlan<T> &pb, int tx, cudaStream_t st) {
@@ -235,8 +245,8 @@ void launch_reg(const GridDev &g, const Fields<T> &F, Work<T> &W, const TriPlan<
     const size_t smem = sizeof(T) * ((size_t)tx * (2 * Pmax + 1) + plan_stage_words(nmax, Pmax));
     const int nxt = (g.nx + tx - 1) / tx;
     const int outer = DIR == 1 ? g.nz : g.ny;
-    launch_k(W.pdl != 0, k_sweep_reg<T, L, DIR, MODE>, dim3(3 * outer * nxt), dim3(threads), smem,
-             st, g, F, W.q0, W.q1, W.q2, pa, pb, tx);
+    K_sweep_reg<T, L, DIR, MODE>.launch(W.pdl != 0, dim3(3 * outer * nxt), dim3(threads), smem,
+                                        st, g, F, W.q0, W.q1, W.q2, pa, pb, tx);
 }
 
 template <typename T, int DIR, int MODE>
@@ -287,11 +297,11 @@ void launch_y_uni(const GridDev &g, Work<T> &W, const StepScalars *sc, cudaStrea
     const int threads = ((tx * P + 31) / 32) * 32;
     const size_t sm = 2 * sizeof(T) * tx * P;
     if (g.ny == L * P)
-        launch_k(W.pdl != 0, k_sweep_y_uni<T, L, true>, dim3(3 * g.nz * nxt), dim3(threads), sm, st,
-                 g, W.q0, W.q1, W.q2, sc, P, tx);
+        K_sweep_y_uni<T, L, true>.launch(W.pdl != 0, dim3(3 * g.nz * nxt), dim3(threads), sm, st, g,
+                                         W.q0, W.q1, W.q2, sc, P, tx);
     else
-        launch_k(W.pdl != 0, k_sweep_y_uni<T, L, false>, dim3(3 * g.nz * nxt), dim3(threads), sm,
-                 st, g, W.q0, W.q1, W.q2, sc, P, tx);
+        K_sweep_y_uni<T, L, false>.launch(W.pdl != 0, dim3(3 * g.nz * nxt), dim3(threads), sm, st,
+                                          g, W.q0, W.q1, W.q2, sc, P, tx);
 }
 
 template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, const StepScalars *sc,
@@ -315,18 +325,18 @@ template <typename T> void launch_sweep_z_adjoint(const GridDev &g, Work<T> &W, 
 template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T> &W) {
     (void)g;
     (void)W;
-    raise_smem_limit(k_sweep_y_uni<T, 8, false>);
-    raise_smem_limit(k_sweep_y_uni<T, 8, true>);
-    raise_smem_limit(k_sweep_y_uni<T, 16, false>);
-    raise_smem_limit(k_sweep_y_uni<T, 16, true>);
-    raise_smem_limit(k_sweep_y_uni<T, 32, false>);
-    raise_smem_limit(k_sweep_y_uni<T, 32, true>);
-    raise_smem_limit(k_sweep_reg<T, 8, 2, 0>);
-    raise_smem_limit(k_sweep_reg<T, 16, 2, 0>);
-    raise_smem_limit(k_sweep_reg<T, 32, 2, 0>);
-    raise_smem_limit(k_sweep_reg<T, 8, 2, 1>);
-    raise_smem_limit(k_sweep_reg<T, 16, 2, 1>);
-    raise_smem_limit(k_sweep_reg<T, 32, 2, 1>);
+    raise_smem_limit(K_sweep_y_uni<T, 8, false>.solo());
+    raise_smem_limit(K_sweep_y_uni<T, 8, true>.solo());
+    raise_smem_limit(K_sweep_y_uni<T, 16, false>.solo());
+    raise_smem_limit(K_sweep_y_uni<T, 16, true>.solo());
+    raise_smem_limit(K_sweep_y_uni<T, 32, false>.solo());
+    raise_smem_limit(K_sweep_y_uni<T, 32, true>.solo());
+    raise_smem_limit(K_sweep_reg<T, 8, 2, 0>.solo());
+    raise_smem_limit(K_sweep_reg<T, 16, 2, 0>.solo());
+    raise_smem_limit(K_sweep_reg<T, 32, 2, 0>.solo());
+    raise_smem_limit(K_sweep_reg<T, 8, 2, 1>.solo());
+    raise_smem_limit(K_sweep_reg<T, 16, 2, 1>.solo());
+    raise_smem_limit(K_sweep_reg<T, 32, 2, 1>.solo());
 }
 
 #define FSEI_INST(T)                                                                           \

@@ -57,7 +57,7 @@ FSEI_D void stage_x_twiddles(cplx<T> *TW, cplx<T> *TP, const cplx<T> *twx,
 // Single precision: 4 blocks per SM (64 registers, no spills; 256^3: 80 ->
 // 72 us against the compiler's 80 registers and 3 blocks).
 template <typename T, int MODE, int RY>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1)
+FSEI_D void
 k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
          const T *__restrict__ q2, const T *__restrict__ src, cplx<T> *__restrict__ spec,
          const cplx<T> *__restrict__ twx, const cplx<T> *__restrict__ twpost, FftPlanDev fp,
@@ -155,7 +155,7 @@ k_rfft_x(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
 // copied asynchronously into shared memory (rows of tkx values), transformed
 // with the line index fastest, and written back with 16-byte stores.
 template <typename T, int SIGN>
-__global__ void __launch_bounds__(256)
+FSEI_D void
 k_fft_y(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ twy, FftPlanDev fp,
         int tkx) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -189,7 +189,7 @@ k_fft_y(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ twy, 
 // second DFT and writes the result straight to the spectrum.  The block owns
 // its tile, so reading and writing in place is safe.
 template <typename T, int SIGN, int N1, int N2>
-__global__ void __launch_bounds__(256)
+FSEI_D void
 k_fft_y_2p(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ twy, int tkx) {
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_wait();
@@ -244,7 +244,7 @@ template <typename T> struct PoissonMat {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(512)
+FSEI_D void
 k_poisson_z(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
             const T *__restrict__ lamy, const unsigned char *__restrict__ exact, int tkx, int P,
             T scale) {
@@ -318,7 +318,7 @@ struct ExactMat {
 // afterwards (gauge); with compat its right-hand side first loses its own
 // dz-weighted mean (makes an arbitrary right-hand side compatible).
 template <typename T>
-__global__ void __launch_bounds__(64)
+FSEI_D void
 k_poisson_exact(GridDev g, cplx<T> *spec, const int *modes, const double *lamx,
                 const double *lamy, double scale, int compat, int P) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -516,7 +516,7 @@ __device__ __forceinline__ void exact_mode_solve(const GridDev &g, cplx<T> *spec
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32)
+FSEI_D void
 k_poisson_exact_f(GridDev g, cplx<T> *spec, const int *modes, const double *xa,
                   const double *xm, const double *xc, const double *xz, const double *xs,
                   double scale, int compat, double zlen) {
@@ -545,7 +545,7 @@ template <typename T> struct alignas(4 * sizeof(T)) ZCoef { T a, c, b0, pad; };
 // Single precision: 3 blocks per SM (80 registers; 256^3: 47 -> 44 us
 // against 117 registers and 2 blocks).
 template <typename T, int E, int LPL>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+FSEI_D void
 k_poisson_zl(GridDev g, cplx<T> *__restrict__ spec, const T *__restrict__ lamx,
              const T *__restrict__ lamy, const unsigned char *__restrict__ exact, T scale,
              int n_exact, const int *modes, const double *xa, const double *xm,
@@ -747,7 +747,7 @@ int exact_chunks(int nz) {
 // conj X_{mx-kx}), inverse transformed, and the complex result stored as the
 // interleaved real row.
 template <typename T, int RY>
-__global__ void __launch_bounds__(256)
+FSEI_D void
 k_irfft_x(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
           const cplx<T> *__restrict__ twx, const cplx<T> *__restrict__ twpost, FftPlanDev fp) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -803,7 +803,7 @@ k_irfft_x(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
 // Single precision: 3 blocks per SM (80 registers, no spills; 256^3: 45 ->
 // 39 us against 92 registers and 2 blocks).
 template <typename T, int RY, int N1, int N2>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
+FSEI_D void
 k_irfft_x_2p(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
              const cplx<T> *__restrict__ twx, const cplx<T> *__restrict__ twpost) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -868,6 +868,21 @@ k_irfft_x_2p(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
 }
 
 }  // namespace
+
+// the kernels with their launch bounds
+template <typename T, int MODE, int RY>
+constexpr Kernel<k_rfft_x<T, MODE, RY>, 256, (sizeof(T) == 4 ? 4 : 1)> K_rfft_x{};
+template <typename T, int SIGN> constexpr Kernel<k_fft_y<T, SIGN>, 256, 0> K_fft_y{};
+template <typename T, int SIGN, int N1, int N2>
+constexpr Kernel<k_fft_y_2p<T, SIGN, N1, N2>, 256, 0> K_fft_y_2p{};
+template <typename T> constexpr Kernel<k_poisson_z<T>, 512, 0> K_poisson_z{};
+template <typename T> constexpr Kernel<k_poisson_exact<T>, 64, 0> K_poisson_exact{};
+template <typename T> constexpr Kernel<k_poisson_exact_f<T>, 32, 0> K_poisson_exact_f{};
+template <typename T, int E, int LPL>
+constexpr Kernel<k_poisson_zl<T, E, LPL>, 256, (sizeof(T) == 4 ? 3 : 2)> K_poisson_zl{};
+template <typename T, int RY> constexpr Kernel<k_irfft_x<T, RY>, 256, 0> K_irfft_x{};
+template <typename T, int RY, int N1, int N2>
+constexpr Kernel<k_irfft_x_2p<T, RY, N1, N2>, 256, (sizeof(T) == 4 ? 3 : 1)> K_irfft_x_2p{};
 
 // x transforms: two line buffers, the twiddle tables and (inverse only) the
 // staged spectrum rows; ry rows per block
@@ -949,8 +964,8 @@ template <typename T> void poisson_geometry(const GridDev &g, Work<T> &W) {
 template <typename T, int MODE, int RY>
 void rfft_x_ry(const GridDev &g, Work<T> &W, const StepScalars *sc, const T *src, cudaStream_t st) {
     const int blocks = g.nz * (g.ny / RY);
-    launch_k(W.pdl != 0, k_rfft_x<T, MODE, RY>, dim3(blocks), dim3(256), smem_rfft_x<T>(g, RY), st,
-             g, W.q0, W.q1, W.q2, src, W.spec, W.twx, W.twpost, W.fpx, sc);
+    K_rfft_x<T, MODE, RY>.launch(W.pdl != 0, dim3(blocks), dim3(256), smem_rfft_x<T>(g, RY), st,
+                                 g, W.q0, W.q1, W.q2, src, W.spec, W.twx, W.twpost, W.fpx, sc);
 }
 
 template <typename T, int MODE>
@@ -979,26 +994,29 @@ bool fft_y_2p_launch(const GridDev &g, Work<T> &W, cudaStream_t st) {
     const int blocks = g.nz * (g.sk / tk);
     const size_t sm = sizeof(cplx<T>) * ((size_t)g.ny * tk + g.ny);
     const int thr = tk * n1;
-    void (*k)(GridDev, cplx<T> *, const cplx<T> *, int) = nullptr;
+    const bool pdl = W.pdl != 0;
     switch (g.ny) {
-    case 16: k = k_fft_y_2p<T, SIGN, 4, 4>; break;
-    case 32: k = k_fft_y_2p<T, SIGN, 8, 4>; break;
-    case 64: k = k_fft_y_2p<T, SIGN, 8, 8>; break;
-    case 128: k = k_fft_y_2p<T, SIGN, 16, 8>; break;
-    case 256: k = k_fft_y_2p<T, SIGN, 16, 16>; break;
+#define FSEI_FY(N1_, N2_)                                                                      \
+    K_fft_y_2p<T, SIGN, N1_, N2_>.launch(pdl, dim3(blocks), dim3(thr), sm, st, g, W.spec, W.twy, tk)
+    case 16: FSEI_FY(4, 4); return true;
+    case 32: FSEI_FY(8, 4); return true;
+    case 64: FSEI_FY(8, 8); return true;
+    case 128: FSEI_FY(16, 8); return true;
+    case 256: FSEI_FY(16, 16); return true;
+#undef FSEI_FY
     default: return false;
     }
-    launch_k(W.pdl != 0, k, dim3(blocks), dim3(thr), sm, st, g, W.spec, W.twy, tk);
-    return true;
 }
 
 template <typename T> void launch_fft_y(const GridDev &g, Work<T> &W, int inverse, cudaStream_t st) {
     if (inverse ? fft_y_2p_launch<T, 1>(g, W, st) : fft_y_2p_launch<T, -1>(g, W, st)) return;
     const int blocks = g.nz * (g.sk / W.tkx);
     if (inverse)
-        k_fft_y<T, 1><<<blocks, 256, smem_fft_y(g, W), st>>>(g, W.spec, W.twy, W.fpy, W.tkx);
+        K_fft_y<T, 1>.launch(false, dim3(blocks), dim3(256), smem_fft_y(g, W), st, g, W.spec, W.twy,
+                             W.fpy, W.tkx);
     else
-        k_fft_y<T, -1><<<blocks, 256, smem_fft_y(g, W), st>>>(g, W.spec, W.twy, W.fpy, W.tkx);
+        K_fft_y<T, -1>.launch(false, dim3(blocks), dim3(256), smem_fft_y(g, W), st, g, W.spec,
+                              W.twy, W.fpy, W.tkx);
 }
 
 template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaStream_t st,
@@ -1017,9 +1035,9 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
         const T tsc = T(scale);
 #define FSEI_ZL(E_, L_)                                                                        \
     if (W.zl_e == E_ && W.zl_lpl == L_) {                                                      \
-        launch_k(W.pdl != 0, k_poisson_zl<T, E_, L_>, dim3(grid), dim3(256), sm, st, g, W.spec,  \
-                 W.lamx, W.lamy, W.exact, tsc, W.n_nzm, W.nzm, W.xa, W.xm, W.xc, W.xz, W.xs,   \
-                 scale, compat, W.zlen);                                                      \
+        K_poisson_zl<T, E_, L_>.launch(W.pdl != 0, dim3(grid), dim3(256), sm, st, g, W.spec,     \
+                                       W.lamx, W.lamy, W.exact, tsc, W.n_nzm, W.nzm, W.xa,    \
+                                       W.xm, W.xc, W.xz, W.xs, scale, compat, W.zlen);        \
         return;                                                                                \
     }
         FSEI_ZL(4, 16) FSEI_ZL(6, 16) FSEI_ZL(8, 16) FSEI_ZL(8, 32)
@@ -1031,22 +1049,23 @@ template <typename T> void launch_poisson_z(const GridDev &g, Work<T> &W, cudaSt
     // exact modes first: they read the untouched right-hand side, and
     // k_poisson_z leaves them alone
     if (W.xa) {
-        k_poisson_exact_f<T><<<W.n_nzm, 32, sizeof(cplx<double>) * g.nz, st>>>(
-            g, W.spec, W.nzm, W.xa, W.xm, W.xc, W.xz, W.xs, scale, compat, W.zlen);
+        K_poisson_exact_f<T>.launch(false, dim3(W.n_nzm), dim3(32), sizeof(cplx<double>) * g.nz,
+                                    st, g, W.spec, W.nzm, W.xa, W.xm, W.xc, W.xz, W.xs, scale,
+                                    compat, W.zlen);
     } else {
         const int Pe = exact_chunks(g.nz);
-        k_poisson_exact<T><<<W.n_nzm, 64, smem_exact(g.nz, Pe), st>>>(
-            g, W.spec, W.nzm, W.lamx_d, W.lamy_d, scale, compat, Pe);
+        K_poisson_exact<T>.launch(false, dim3(W.n_nzm), dim3(64), smem_exact(g.nz, Pe), st, g,
+                                  W.spec, W.nzm, W.lamx_d, W.lamy_d, scale, compat, Pe);
     }
-    k_poisson_z<T><<<blocks, threads, smem_poisson(g, W), st>>>(
-        g, W.spec, W.lamx, W.lamy, W.exact, W.tkx, W.pz_poisson, T(scale));
+    K_poisson_z<T>.launch(false, dim3(blocks), dim3(threads), smem_poisson(g, W), st, g, W.spec,
+                          W.lamx, W.lamy, W.exact, W.tkx, W.pz_poisson, T(scale));
 }
 
 template <typename T, int RY>
 void irfft_x_ry(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
     const int blocks = g.nz * (g.ny / RY);
-    k_irfft_x<T, RY><<<blocks, 256, smem_irfft_x<T>(g, RY), st>>>(g, W.spec, dst, W.twx,
-                                                                  W.twpost, W.fpx);
+    K_irfft_x<T, RY>.launch(false, dim3(blocks), dim3(256), smem_irfft_x<T>(g, RY), st, g, W.spec,
+                            dst, W.twx, W.twpost, W.fpx);
 }
 
 template <typename T, int RY>
@@ -1056,17 +1075,19 @@ bool irfft_x_2p_launch(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
     const int blocks = g.nz * (g.ny / RY);
     const size_t sm = sizeof(cplx<T>) * ((size_t)RY * (g.mx / n1) * (n1 + 1) + 2 * g.mx + 1);
     const int thr = RY * n1;
-    void (*k)(GridDev, const cplx<T> *, T *, const cplx<T> *, const cplx<T> *) = nullptr;
+    const bool pdl = W.pdl != 0;
     switch (g.mx) {
-    case 16: k = k_irfft_x_2p<T, RY, 4, 4>; break;
-    case 32: k = k_irfft_x_2p<T, RY, 8, 4>; break;
-    case 64: k = k_irfft_x_2p<T, RY, 8, 8>; break;
-    case 128: k = k_irfft_x_2p<T, RY, 16, 8>; break;
-    case 256: k = k_irfft_x_2p<T, RY, 16, 16>; break;
+#define FSEI_IX(N1_, N2_)                                                                      \
+    K_irfft_x_2p<T, RY, N1_, N2_>.launch(pdl, dim3(blocks), dim3(thr), sm, st, g, W.spec, dst,   \
+                                         W.twx, W.twpost)
+    case 16: FSEI_IX(4, 4); return true;
+    case 32: FSEI_IX(8, 4); return true;
+    case 64: FSEI_IX(8, 8); return true;
+    case 128: FSEI_IX(16, 8); return true;
+    case 256: FSEI_IX(16, 16); return true;
+#undef FSEI_IX
     default: return false;
     }
-    launch_k(W.pdl != 0, k, dim3(blocks), dim3(thr), sm, st, g, W.spec, dst, W.twx, W.twpost);
-    return true;
 }
 
 template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
@@ -1082,54 +1103,54 @@ template <typename T> void launch_irfft_x(const GridDev &g, Work<T> &W, T *dst, 
 
 template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<T> &W) {
     (void)0;  // every kernel of this file gets an attribute below, which loads it
-    raise_smem_limit(k_rfft_x<T, 0, 1>);
-    raise_smem_limit(k_rfft_x<T, 0, 2>);
-    raise_smem_limit(k_rfft_x<T, 0, 4>);
-    raise_smem_limit(k_rfft_x<T, 0, 8>);
-    raise_smem_limit(k_rfft_x<T, 0, 16>);
-    raise_smem_limit(k_rfft_x<T, 1, 16>);
-    raise_smem_limit(k_irfft_x<T, 16>);
+    raise_smem_limit(K_rfft_x<T, 0, 1>.solo());
+    raise_smem_limit(K_rfft_x<T, 0, 2>.solo());
+    raise_smem_limit(K_rfft_x<T, 0, 4>.solo());
+    raise_smem_limit(K_rfft_x<T, 0, 8>.solo());
+    raise_smem_limit(K_rfft_x<T, 0, 16>.solo());
+    raise_smem_limit(K_rfft_x<T, 1, 16>.solo());
+    raise_smem_limit(K_irfft_x<T, 16>.solo());
     {
         constexpr int R = sizeof(T) == 4 ? 16 : 4;
-        raise_smem_limit(k_irfft_x_2p<T, R, 4, 4>);
-        raise_smem_limit(k_irfft_x_2p<T, R, 8, 4>);
-        raise_smem_limit(k_irfft_x_2p<T, R, 8, 8>);
-        raise_smem_limit(k_irfft_x_2p<T, R, 16, 8>);
-        raise_smem_limit(k_irfft_x_2p<T, R, 16, 16>);
+        raise_smem_limit(K_irfft_x_2p<T, R, 4, 4>.solo());
+        raise_smem_limit(K_irfft_x_2p<T, R, 8, 4>.solo());
+        raise_smem_limit(K_irfft_x_2p<T, R, 8, 8>.solo());
+        raise_smem_limit(K_irfft_x_2p<T, R, 16, 8>.solo());
+        raise_smem_limit(K_irfft_x_2p<T, R, 16, 16>.solo());
     }
-    raise_smem_limit(k_rfft_x<T, 1, 1>);
-    raise_smem_limit(k_rfft_x<T, 1, 2>);
-    raise_smem_limit(k_rfft_x<T, 1, 4>);
-    raise_smem_limit(k_rfft_x<T, 1, 8>);
-    raise_smem_limit(k_irfft_x<T, 1>);
-    raise_smem_limit(k_irfft_x<T, 2>);
-    raise_smem_limit(k_irfft_x<T, 4>);
-    raise_smem_limit(k_irfft_x<T, 8>);
-    raise_smem_limit(k_fft_y<T, 1>);
-    raise_smem_limit(k_fft_y<T, -1>);
-    raise_smem_limit(k_fft_y_2p<T, 1, 4, 4>);
-    raise_smem_limit(k_fft_y_2p<T, -1, 4, 4>);
-    raise_smem_limit(k_fft_y_2p<T, 1, 8, 4>);
-    raise_smem_limit(k_fft_y_2p<T, -1, 8, 4>);
-    raise_smem_limit(k_fft_y_2p<T, 1, 8, 8>);
-    raise_smem_limit(k_fft_y_2p<T, -1, 8, 8>);
-    raise_smem_limit(k_fft_y_2p<T, 1, 16, 8>);
-    raise_smem_limit(k_fft_y_2p<T, -1, 16, 8>);
-    raise_smem_limit(k_fft_y_2p<T, 1, 16, 16>);
-    raise_smem_limit(k_fft_y_2p<T, -1, 16, 16>);
-    raise_smem_limit(k_poisson_z<T>);
-    raise_smem_limit(k_poisson_exact<T>);
-    raise_smem_limit(k_poisson_exact_f<T>);
-    raise_smem_limit(k_poisson_zl<T, 4, 16>);
-    raise_smem_limit(k_poisson_zl<T, 6, 16>);
-    raise_smem_limit(k_poisson_zl<T, 8, 16>);
-    raise_smem_limit(k_poisson_zl<T, 8, 32>);
+    raise_smem_limit(K_rfft_x<T, 1, 1>.solo());
+    raise_smem_limit(K_rfft_x<T, 1, 2>.solo());
+    raise_smem_limit(K_rfft_x<T, 1, 4>.solo());
+    raise_smem_limit(K_rfft_x<T, 1, 8>.solo());
+    raise_smem_limit(K_irfft_x<T, 1>.solo());
+    raise_smem_limit(K_irfft_x<T, 2>.solo());
+    raise_smem_limit(K_irfft_x<T, 4>.solo());
+    raise_smem_limit(K_irfft_x<T, 8>.solo());
+    raise_smem_limit(K_fft_y<T, 1>.solo());
+    raise_smem_limit(K_fft_y<T, -1>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 4, 4>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 4, 4>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 8, 4>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 8, 4>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 8, 8>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 8, 8>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 16, 8>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 16, 8>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 16, 16>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 16, 16>.solo());
+    raise_smem_limit(K_poisson_z<T>.solo());
+    raise_smem_limit(K_poisson_exact<T>.solo());
+    raise_smem_limit(K_poisson_exact_f<T>.solo());
+    raise_smem_limit(K_poisson_zl<T, 4, 16>.solo());
+    raise_smem_limit(K_poisson_zl<T, 6, 16>.solo());
+    raise_smem_limit(K_poisson_zl<T, 8, 16>.solo());
+    raise_smem_limit(K_poisson_zl<T, 8, 32>.solo());
     if constexpr (sizeof(T) == 4) {
-        raise_smem_limit(k_poisson_zl<T, 12, 16>);
-        raise_smem_limit(k_poisson_zl<T, 16, 16>);
-        raise_smem_limit(k_poisson_zl<T, 24, 16>);
-        raise_smem_limit(k_poisson_zl<T, 16, 32>);
-        raise_smem_limit(k_poisson_zl<T, 24, 32>);
+        raise_smem_limit(K_poisson_zl<T, 12, 16>.solo());
+        raise_smem_limit(K_poisson_zl<T, 16, 16>.solo());
+        raise_smem_limit(K_poisson_zl<T, 24, 16>.solo());
+        raise_smem_limit(K_poisson_zl<T, 16, 32>.solo());
+        raise_smem_limit(K_poisson_zl<T, 24, 32>.solo());
     }
 }
 

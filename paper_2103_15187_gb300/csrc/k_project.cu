@@ -15,7 +15,7 @@ namespace {
 // One block per (j, k) row group: blockIdx.x = k * (ny / rows) + row tile,
 // threads stride over x.  No integer division per element.
 template <typename T>
-__global__ void __launch_bounds__(256)
+FSEI_D void
 k_project(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict__ q1,
           const T *__restrict__ q2, const T *__restrict__ phi, StepScalars *sc, int rows) {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -123,7 +123,7 @@ template <typename T> struct alignas(16) Vec16 {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+FSEI_D void
 k_project_vec(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restrict__ q1,
               const T *__restrict__ q2, const T *__restrict__ phi, StepScalars *sc, int rows) {
     pdl_wait();
@@ -247,6 +247,10 @@ k_project_vec(GridDev g, Fields<T> F, const T *__restrict__ q0, const T *__restr
     }
 }
 
+// the kernels with their launch bounds
+template <typename T> constexpr Kernel<k_project<T>, 256, 0> K_project{};
+template <typename T> constexpr Kernel<k_project_vec<T>, 256, 0> K_project_vec{};
+
 }  // namespace
 
 int project_rows(const GridDev &g) {
@@ -269,20 +273,20 @@ template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, 
         int rows = 1;
         for (int r = mult * rpp; r >= 1; --r)
             if (g.ny % r == 0) { rows = r; break; }
-        launch_k(W.pdl != 0, k_project_vec<T>, dim3(g.nz * (g.ny / rows)), dim3(128), 0, st, g, F,
-                 W.q0, W.q1, W.q2, W.phi, sc, rows);
+        K_project_vec<T>.launch(W.pdl != 0, dim3(g.nz * (g.ny / rows)), dim3(128), 0, st, g, F,
+                                W.q0, W.q1, W.q2, W.phi, sc, rows);
         return;
     }
     const int rows = project_rows(g);
     const int threads = g.nx >= 256 ? 256 : ((g.nx + 31) / 32) * 32;
-    k_project<T><<<g.nz * (g.ny / rows), threads, 0, st>>>(g, F, W.q0, W.q1, W.q2, W.phi, sc,
-                                                           rows);
+    K_project<T>.launch(false, dim3(g.nz * (g.ny / rows)), dim3(threads), 0, st, g, F, W.q0, W.q1,
+                        W.q2, W.phi, sc, rows);
 }
 
 template <typename T> void preload_project() {
     cudaFuncAttributes fa;
-    cudaFuncGetAttributes(&fa, k_project<T>);
-    cudaFuncGetAttributes(&fa, k_project_vec<T>);
+    cudaFuncGetAttributes(&fa, K_project<T>.solo());
+    cudaFuncGetAttributes(&fa, K_project_vec<T>.solo());
 }
 template void preload_project<float>();
 template void preload_project<double>();

@@ -32,7 +32,7 @@ template <typename T> struct alignas(16) Vec16 {
 // one block per group of rows (no integer division per element); per-cell
 // speed in the field precision, the grid-wide maximum in double
 template <typename T>
-__global__ void __launch_bounds__(256)
+FSEI_D void
 k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v, const T *__restrict__ w,
         StepScalars *sc, int rows) {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -73,7 +73,7 @@ k_speed(GridDev g, const T *__restrict__ u, const T *__restrict__ v, const T *__
 // tpr = nx / VW threads span a row, rpp = blockDim / tpr rows side by side;
 // needs nx % VW == 0.  Same per-cell arithmetic as k_speed.
 template <typename T>
-__global__ void __launch_bounds__(128)
+FSEI_D void
 k_speed_vec(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
             const T *__restrict__ w, StepScalars *sc, int rows) {
     constexpr int VW = 16 / (int)sizeof(T);
@@ -139,8 +139,7 @@ __device__ void uni_factors(double r, double &alpha, double &cinv) {
 // y factors, warp 2 1/dt, the advection weights and the reset of the step's
 // reductions.
 // Lane 0 of each warp stores.
-__global__ void __launch_bounds__(96) k_scalars(StepScalars *sc, StepArgs a, int euler,
-                                                double idx2, double idy2) {
+FSEI_D void k_scalars(StepScalars *sc, StepArgs a, int euler, double idx2, double idy2) {
     pdl_wait();
     pdl_trigger();
     const int wid = threadIdx.x >> 5;
@@ -226,7 +225,7 @@ struct SweepCoef {
 
 // one block per plan; thread p < P builds chunk p; thread 0 the reduced LU
 template <typename T>
-__global__ void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
+FSEI_D void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int kind = 2 + blockIdx.x;   // the z plans (x and y lines use uni_solve)
     const TriPlan<T> &pl = W.plan[kind];
@@ -484,7 +483,7 @@ FSEI_D void x_solve_store(T *sd, int es, int ry, int P, int nx, int ny, int k, i
 // take more registers.  General kernel (any nx): stencil values read from
 // global memory; the tiled kernel below is used where it applies.
 template <typename T, int L>
-__global__ void __launch_bounds__(256, L <= 16 ? (sizeof(T) == 4 ? 4 : 2) : (L <= 32 ? 2 : 1))
+FSEI_D void
 k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
         const StepScalars *sc, int ry, int P, T fc0, T fc1, T fc2, T inv_re) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -623,8 +622,7 @@ FSEI_D const T *tile_source(const TileRows &tr, int RY, int r, const Fields<T> &
 // point formula reads shared memory only.  Needs nx * sizeof(T) % 16 == 0.
 // Same arithmetic, in the same order, as k_rhs_x.
 template <typename T, int L, int RY>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (L <= 16 ? 4 : (L <= 32 ? 3 : 2))
-                                                      : (L <= 16 ? 2 : 1))
+FSEI_D void
 k_rhs_x_tile(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
              T *__restrict__ q2, const StepScalars *sc, int P, T fc0, T fc1, T fc2, T inv_re) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -943,7 +941,7 @@ FSEI_D void rhs_row_body(const GridDev &g, const Fields<T> &F, const RowSet<T> &
 // caches).  Needs nx = LPR CPL, CPL values spanning 8 bytes or a multiple of
 // 16, ny a multiple of rpb.
 template <typename T, int CPL, int LPR>
-__global__ void __launch_bounds__(LPR > 128 ? LPR : 128)
+FSEI_D void
 k_rhs_x_row(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
             T *__restrict__ q2, const StepScalars *sc, int rpb, T fc0, T fc1, T fc2, T inv_re) {
     __shared__ T xs[2 * 3 * (LPR > 128 ? LPR : 128) / 32];
@@ -973,6 +971,21 @@ k_rhs_x_row(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
 
 }  // namespace
 
+// the kernels with their launch bounds
+template <typename T> constexpr Kernel<k_speed<T>, 256, 0> K_speed{};
+template <typename T> constexpr Kernel<k_speed_vec<T>, 128, 0> K_speed_vec{};
+constexpr Kernel<k_scalars, 96, 0> K_scalars{};
+template <typename T> constexpr Kernel<k_plans<T>, 128, 0> K_plans{};
+template <typename T, int L>
+constexpr Kernel<k_rhs_x<T, L>, 256, (L <= 16 ? (sizeof(T) == 4 ? 4 : 2) : (L <= 32 ? 2 : 1))>
+    K_rhs_x{};
+template <typename T, int L, int RY>
+constexpr Kernel<k_rhs_x_tile<T, L, RY>, 256,
+                 (sizeof(T) == 4 ? (L <= 16 ? 4 : (L <= 32 ? 3 : 2)) : (L <= 16 ? 2 : 1))>
+    K_rhs_x_tile{};
+template <typename T, int CPL, int LPR>
+constexpr Kernel<k_rhs_x_row<T, CPL, LPR>, (LPR > 128 ? LPR : 128), 0> K_rhs_x_row{};
+
 // ------------------------------------------------------------- launchers --
 void uni_geometry(int n, int nl, int maxthr, int &P, int &chunk) {
     P = 1;
@@ -995,19 +1008,19 @@ template <typename T> void launch_speed(const GridDev &g, const T *u, const T *v
         int rows = 1;
         for (int r = 4 * rpp; r >= 1; --r)
             if (g.ny % r == 0) { rows = r; break; }
-        k_speed_vec<T><<<g.nz * (g.ny / rows), 128, 0, st>>>(g, u, v, w, sc, rows);
+        K_speed_vec<T>.launch(false, dim3(g.nz * (g.ny / rows)), dim3(128), 0, st, g, u, v, w, sc, rows);
         return;
     }
     int rows = 1;
     for (int r = 8; r >= 1; r /= 2)
         if (g.ny % r == 0) { rows = r; break; }
     const int threads = g.nx >= 256 ? 256 : ((g.nx + 31) / 32) * 32;
-    k_speed<T><<<g.nz * (g.ny / rows), threads, 0, st>>>(g, u, v, w, sc, rows);
+    K_speed<T>.launch(false, dim3(g.nz * (g.ny / rows)), dim3(threads), 0, st, g, u, v, w, sc, rows);
 }
 
 void launch_step_scalars(const GridDev &g, StepScalars *sc, const StepArgs &a, int euler,
                          cudaStream_t st, bool pdl) {
-    launch_k(pdl, k_scalars, dim3(1), dim3(96), 0, st, sc, a, euler, g.idx2, g.idy2);
+    K_scalars.launch(pdl, dim3(1), dim3(96), 0, st, sc, a, euler, g.idx2, g.idy2);
 }
 
 template <typename T> void launch_step_plans(const GridDev &g, Work<T> &W, const StepScalars *sc,
@@ -1018,8 +1031,8 @@ template <typename T> void launch_step_plans(const GridDev &g, Work<T> &W, const
         if (W.plan[q].P > maxp) maxp = W.plan[q].P;
     }
     const size_t sm = sizeof(double) * (2 * (size_t)maxn + 12 * (size_t)maxp);
-    int thr = ((2 * maxp + 31) / 32) * 32;
-    k_plans<T><<<2, thr, sm, st>>>(g, W, sc);
+    int thr = ((2 * maxp + 31) / 32) * 32;   // 2 P <= 64 threads
+    K_plans<T>.launch(false, dim3(2), dim3(thr), sm, st, g, W, sc);
 }
 
 template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepScalars *sc,
@@ -1038,9 +1051,9 @@ void rhs_x_L(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars
     const int row_threads = g.nx < 256 ? ((g.nx + 31) / 32) * 32 : 256;
     if (threads < row_threads) threads = row_threads;
     const int blocks = g.nz * (g.ny / W.ry);
-    k_rhs_x<T, L><<<blocks, threads, smem_rhs_x(g, W), st>>>(
-        g, F, W.q0, W.q1, W.q2, sc, W.ry, W.px, T(a.fconst[0]), T(a.fconst[1]), T(a.fconst[2]),
-        T(1.0 / a.re));
+    K_rhs_x<T, L>.launch(false, dim3(blocks), dim3(threads), smem_rhs_x(g, W), st, g, F, W.q0,
+                         W.q1, W.q2, sc, W.ry, W.px, T(a.fconst[0]), T(a.fconst[1]),
+                         T(a.fconst[2]), T(1.0 / a.re));
 }
 
 // Geometry of the tiled right-hand side: RY rows per block (2, else 1),
@@ -1067,9 +1080,9 @@ template <typename T> bool rhs_tile_geometry(const GridDev &g, int &RY, int &P, 
 template <typename T, int L, int RY>
 void rhs_tile_L(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
                 const StepArgs &a, int P, size_t smem, cudaStream_t st) {
-    k_rhs_x_tile<T, L, RY><<<g.nz * (g.ny / RY), 256, smem, st>>>(
-        g, F, W.q0, W.q1, W.q2, sc, P, T(a.fconst[0]), T(a.fconst[1]), T(a.fconst[2]),
-        T(1.0 / a.re));
+    K_rhs_x_tile<T, L, RY>.launch(false, dim3(g.nz * (g.ny / RY)), dim3(256), smem, st, g, F,
+                                  W.q0, W.q1, W.q2, sc, P, T(a.fconst[0]), T(a.fconst[1]),
+                                  T(a.fconst[2]), T(1.0 / a.re));
 }
 
 template <typename T, int RY>
@@ -1105,9 +1118,9 @@ bool rhs_row_geometry(const GridDev &g, int &cpl, int &lpr, int &rpb, int prefer
 template <typename T, int CPL, int LPR>
 void rhs_row_launch(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
                     const StepArgs &a, int rpb, cudaStream_t st) {
-    launch_k(W.pdl != 0, k_rhs_x_row<T, CPL, LPR>, dim3(g.nz * (g.ny / rpb)), dim3(rpb * LPR), 0,
-             st, g, F, W.q0, W.q1, W.q2, sc, rpb, T(a.fconst[0]), T(a.fconst[1]),
-             T(a.fconst[2]), T(1.0 / a.re));
+    K_rhs_x_row<T, CPL, LPR>.launch(W.pdl != 0, dim3(g.nz * (g.ny / rpb)), dim3(rpb * LPR), 0,
+                                    st, g, F, W.q0, W.q1, W.q2, sc, rpb, T(a.fconst[0]),
+                                    T(a.fconst[1]), T(a.fconst[2]), T(1.0 / a.re));
 }
 
 template <typename T, int CPL>
@@ -1162,47 +1175,47 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     // load every kernel of this file now: a kernel loaded lazily at its first
     // launch cannot be loaded inside a stream capture
     cudaFuncAttributes fa;
-    cudaFuncGetAttributes(&fa, k_speed<T>);
-    cudaFuncGetAttributes(&fa, k_speed_vec<T>);
-    cudaFuncGetAttributes(&fa, k_scalars);
-    cudaFuncGetAttributes(&fa, k_plans<T>);
+    cudaFuncGetAttributes(&fa, K_speed<T>.solo());
+    cudaFuncGetAttributes(&fa, K_speed_vec<T>.solo());
+    cudaFuncGetAttributes(&fa, K_scalars.solo());
+    cudaFuncGetAttributes(&fa, K_plans<T>.solo());
     (void)g;
     (void)W;
-    raise_smem_limit(k_rhs_x<T, 8>);
-    raise_smem_limit(k_rhs_x<T, 16>);
-    raise_smem_limit(k_rhs_x<T, 32>);
-    raise_smem_limit(k_rhs_x<T, 64>);
-    raise_smem_limit(k_rhs_x_tile<T, 8, 1>);
-    raise_smem_limit(k_rhs_x_tile<T, 16, 1>);
-    raise_smem_limit(k_rhs_x_tile<T, 32, 1>);
-    raise_smem_limit(k_rhs_x_tile<T, 64, 1>);
-    raise_smem_limit(k_rhs_x_tile<T, 8, 2>);
-    raise_smem_limit(k_rhs_x_tile<T, 16, 2>);
-    raise_smem_limit(k_rhs_x_tile<T, 32, 2>);
-    raise_smem_limit(k_rhs_x_tile<T, 64, 2>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 4>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 8>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 16>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 32>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 64>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 128>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, 4, 256>);
+    raise_smem_limit(K_rhs_x<T, 8>.solo());
+    raise_smem_limit(K_rhs_x<T, 16>.solo());
+    raise_smem_limit(K_rhs_x<T, 32>.solo());
+    raise_smem_limit(K_rhs_x<T, 64>.solo());
+    raise_smem_limit(K_rhs_x_tile<T, 8, 1>.solo());
+    raise_smem_limit(K_rhs_x_tile<T, 16, 1>.solo());
+    raise_smem_limit(K_rhs_x_tile<T, 32, 1>.solo());
+    raise_smem_limit(K_rhs_x_tile<T, 64, 1>.solo());
+    raise_smem_limit(K_rhs_x_tile<T, 8, 2>.solo());
+    raise_smem_limit(K_rhs_x_tile<T, 16, 2>.solo());
+    raise_smem_limit(K_rhs_x_tile<T, 32, 2>.solo());
+    raise_smem_limit(K_rhs_x_tile<T, 64, 2>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, 4, 4>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, 4, 8>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, 4, 16>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, 4, 32>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, 4, 64>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, 4, 128>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, 4, 256>.solo());
     constexpr int C = sizeof(T) == 4 ? 8 : 4;
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 4>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 8>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 16>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 32>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 64>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 128>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C, 256>);
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C, 4>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C, 8>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C, 16>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C, 32>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C, 64>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C, 128>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C, 256>.solo());
     constexpr int C2 = sizeof(T) == 4 ? 2 : 4;
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 4>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 8>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 16>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 32>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 64>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 128>);
-    cudaFuncGetAttributes(&fa, k_rhs_x_row<T, C2, 256>);
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 4>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 8>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 16>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 32>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 64>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 128>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 256>.solo());
 }
 
 #define FSEI_INST(T)                                                                           \

@@ -1,12 +1,167 @@
 // Launch interface between the host library (api.cu) and the kernels of one
 // fractional step.  Internal to libfsei.so.
 #pragma once
+#include <string.h>
+
+#include <cuda/std/tuple>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "fft.cuh"
 
 namespace fsei {
+
+// ------------------------------------------------------- kernel entries ----
+// The kernels of a step are __device__ bodies with two entry points: k_solo
+// runs a body for one grid with its arguments as kernel parameters; k_group
+// runs it for the boxes of a batch group at once, box blockIdx.z taking its
+// arguments from row blockIdx.z of a device table (every box of a group has
+// the same extents, so the same launch shape).  A Kernel<Body, MAXT, MINB>
+// names a body with the launch bounds of both entries.
+template <auto Body, int MAXT, int MINB, typename... P>
+__global__ void __launch_bounds__(MAXT, MINB) k_solo(P... p) { Body(p...); }
+
+template <auto Body, int MAXT, int MINB, typename... P>
+__global__ void __launch_bounds__(MAXT, MINB) k_group(const cuda::std::tuple<P...> *__restrict__ tab) {
+    cuda::std::apply(Body, tab[blockIdx.z]);
+}
+
+// One launch of a fractional step as recorded for a batch group: the entry
+// of its body, launch shape, stream and the bytes of its argument tuple (a
+// cuda::std::tuple of the body's parameter types, identical on the host and
+// the device); or a memset, or the fork / join of the grid's side stream.
+struct RecordedOp {
+    enum Kind { KERNEL, MEMSET, FORK, JOIN } kind;
+    cudaStream_t st;
+    const void *entry;   // solo entry of the body (identifies the kernel)
+    void (*launch_group)(const void *tab, int nbox, dim3 grid, dim3 block, size_t smem,
+                         cudaStream_t st, bool pdl);
+    void (*prepare_group)();   // loads the group entry, raises its smem limit
+    dim3 grid, block;
+    size_t smem;
+    bool pdl;
+    std::vector<unsigned char> args;
+    void *mem;
+    size_t mem_bytes;
+};
+struct LaunchRecorder {
+    std::vector<RecordedOp> ops;
+};
+// While a recorder is set on the calling host thread, Kernel::launch,
+// memset_async and the side-stream fork / join record instead of issuing.
+LaunchRecorder *&launch_recorder();
+
+// Launch of kernel k on st; with pdl, as a programmatic dependent launch:
+// the grid may be scheduled while the stream's previous kernel finishes (the
+// kernel's pdl_wait() holds its blocks until that kernel has completed), so
+// the launch latency and the block ramp-up overlap the predecessor's last
+// wave.  The launch error, if any, is left for cudaGetLastError.
+template <typename... KP, typename... A>
+inline void launch_k(bool pdl, void (*k)(KP...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, A &&...args) {
+    if (pdl) {
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...) == cudaSuccess) return;
+        cudaGetLastError();   // the ordinary launch below reports the error
+    }
+    k<<<grid, block, smem, st>>>(std::forward<A>(args)...);
+}
+
+// Largest dynamic shared memory a block may opt into on the current device.
+inline int smem_optin() {
+    int dev = 0, v = 48 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+// Raise a kernel's dynamic shared memory limit to what the device allows
+// next to the kernel's static shared memory.  Every kernel's
+// MaxDynamicSharedMemorySize attribute is raised to it: the attribute is per
+// kernel and process-wide, so a value sized for one grid would cap the
+// launches of another grid of the same kernel.
+template <typename F> inline void raise_smem_limit(F *kernel) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_optin() - (int)a.sharedSizeBytes);
+}
+
+template <auto Body, int MAXT, int MINB, typename... P>
+void group_launch_of(const void *tab, int nbox, dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, bool pdl) {
+    grid.z = (unsigned)nbox;
+    launch_k(pdl, k_group<Body, MAXT, MINB, P...>, grid, block, smem, st,
+             static_cast<const cuda::std::tuple<P...> *>(tab));
+}
+template <auto Body, int MAXT, int MINB, typename... P> void group_prepare_of() {
+    raise_smem_limit(k_group<Body, MAXT, MINB, P...>);
+}
+
+template <auto Body, int MAXT, int MINB, typename... P>
+constexpr auto solo_entry_of(void (*)(P...)) {
+    return &k_solo<Body, MAXT, MINB, P...>;
+}
+
+template <auto Body, int MAXT, int MINB, typename... P, typename... A>
+void launch_body(void (*)(P...), bool pdl, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                 A &&...args) {
+    if (LaunchRecorder *rec = launch_recorder()) {
+        using Tup = cuda::std::tuple<P...>;
+        const Tup t(static_cast<P>(args)...);
+        RecordedOp op = {};
+        op.kind = RecordedOp::KERNEL;
+        op.st = st;
+        op.entry = (const void *)&k_solo<Body, MAXT, MINB, P...>;
+        op.launch_group = &group_launch_of<Body, MAXT, MINB, P...>;
+        op.prepare_group = &group_prepare_of<Body, MAXT, MINB, P...>;
+        op.grid = grid;
+        op.block = block;
+        op.smem = smem;
+        op.pdl = pdl;
+        op.args.resize(sizeof(Tup));
+        memcpy(op.args.data(), &t, sizeof(Tup));
+        rec->ops.push_back(std::move(op));
+        return;
+    }
+    launch_k(pdl, &k_solo<Body, MAXT, MINB, P...>, grid, block, smem, st,
+             static_cast<P>(args)...);
+}
+
+template <auto Body, int MAXT, int MINB> struct Kernel {
+    // launch on st (pdl: as a programmatic dependent launch), or record it
+    template <typename... A>
+    void launch(bool pdl, dim3 grid, dim3 block, size_t smem, cudaStream_t st, A &&...args) const {
+        launch_body<Body, MAXT, MINB>(Body, pdl, grid, block, smem, st, std::forward<A>(args)...);
+    }
+    // the solo entry (for function attributes)
+    auto solo() const { return solo_entry_of<Body, MAXT, MINB>(Body); }
+};
+
+// cudaMemsetAsync, or recorded
+inline void memset_async(void *p, int v, size_t n, cudaStream_t st) {
+    if (LaunchRecorder *rec = launch_recorder()) {
+        RecordedOp op = {};
+        op.kind = RecordedOp::MEMSET;
+        op.st = st;
+        op.mem = p;
+        op.mem_bytes = n;
+        rec->ops.push_back(std::move(op));
+        (void)v;
+        return;
+    }
+    cudaMemsetAsync(p, v, n, st);
+}
 
 // Body force and state fields of one step (device pointers, caller-owned).
 template <typename T> struct Fields {
@@ -118,6 +273,31 @@ struct Overlap {
     cudaStream_t side;
     cudaEvent_t fork, join;
 };
+// Let o.side start after the work queued on st so far (fork), or let st
+// continue after the work queued on o.side (join); recorded when a
+// recorder is set.
+inline void fork_side(const Overlap &o, cudaStream_t st) {
+    if (LaunchRecorder *rec = launch_recorder()) {
+        RecordedOp op = {};
+        op.kind = RecordedOp::FORK;
+        op.st = st;
+        rec->ops.push_back(std::move(op));
+        return;
+    }
+    cudaEventRecord(o.fork, st);
+    cudaStreamWaitEvent(o.side, o.fork, 0);
+}
+inline void join_side(const Overlap &o, cudaStream_t st) {
+    if (LaunchRecorder *rec = launch_recorder()) {
+        RecordedOp op = {};
+        op.kind = RecordedOp::JOIN;
+        op.st = st;
+        rec->ops.push_back(std::move(op));
+        return;
+    }
+    cudaEventRecord(o.join, o.side);
+    cudaStreamWaitEvent(st, o.join, 0);
+}
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st);
 template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, const StepScalars *sc,
@@ -159,50 +339,6 @@ template <typename T> void preload_project();
 template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                           StepScalars *sc, cudaStream_t st);
 
-// Largest dynamic shared memory a block may opt into on the current device.
-// Launch of kernel k on st; with pdl, as a programmatic dependent launch:
-// the grid may be scheduled while the stream's previous kernel finishes (the
-// kernel's pdl_wait() holds its blocks until that kernel has completed), so
-// the launch latency and the block ramp-up overlap the predecessor's last
-// wave.  The launch error, if any, is left for cudaGetLastError.
-template <typename... KP, typename... A>
-inline void launch_k(bool pdl, void (*k)(KP...), dim3 grid, dim3 block, size_t smem,
-                     cudaStream_t st, A &&...args) {
-    if (pdl) {
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = grid;
-        cfg.blockDim = block;
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...) == cudaSuccess) return;
-        cudaGetLastError();   // the ordinary launch below reports the error
-    }
-    k<<<grid, block, smem, st>>>(std::forward<A>(args)...);
-}
-
-// Every kernel's MaxDynamicSharedMemorySize attribute is raised to it: the
-// attribute is per kernel and process-wide, so a value sized for one grid
-// would cap the launches of another grid of the same kernel.
-inline int smem_optin() {
-    int dev = 0, v = 48 * 1024;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return v;
-}
-
-// Raise a kernel's dynamic shared memory limit to what the device allows
-// next to the kernel's static shared memory.
-template <typename F> inline void raise_smem_limit(F *kernel) {
-    cudaFuncAttributes a;
-    if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess) return;
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem_optin() - (int)a.sharedSizeBytes);
-}
 
 // dynamic shared memory bytes of each kernel (host-side sizing helpers)
 template <typename T> size_t smem_rhs_x(const GridDev &g, const Work<T> &W);
