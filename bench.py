@@ -304,22 +304,18 @@ def run_gpu_arm(args, rank, world):
     return case, results, err, e2e
 
 
-def run_ensemble(args):
-    """64 independent boxes of uneven sizes (32^3, 64^3, 96x96x128, 128x128x192),
-    FP32 fields, one batched call per K steps (CUDA graph replayed per step),
-    against the same boxes advanced one after another with fsei_step."""
+def _time_batch(cases, K, autotune):
+    """ms per step of the boxes `cases` advanced together by fsei_batch_step
+    (grouped launches in a CUDA graph), and the last call's statistics."""
     import torch
-    from paper_2103_15187_gb300 import fsei, inputs
-    cases = inputs.case_ensemble(args.ensemble_boxes, steps=args.steps)
+    from paper_2103_15187_gb300 import fsei
     boxes = [dict(nx=c.nx, ny=c.ny, nz=c.nz, lx=c.lx, ly=c.ly, zbc=c.zbc, lz=c.lz,
                   stretch=c.stretch, prec=fsei.FSEI_MIXED) for c in cases]
     batch = fsei.Batch(boxes)
-    if not args.no_autotune:
+    if autotune:
         batch.autotune()
     states = [device_state(c, torch.float32) for c in cases]
     params = [dict(re=c.re, dt=c.dt, cfl=c.cfl, fconst=c.fconst) for c in cases]
-    cells = sum(c.cells for c in cases)
-    K = args.ensemble_steps
     # two warm-up calls: the first captures the graphs of a fresh state, the
     # second those of a state with history; the timed call reuses the latter
     fsei.batch_step(batch, states, None, params, nsteps=2, stats=False)
@@ -332,26 +328,58 @@ def run_ensemble(args):
     fsei.batch_step(batch, states, None, params, nsteps=K, stats=False)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
     st = fsei.batch_step(batch, states, None, params, nsteps=0, stats=True)
-    # the same boxes one after another (no graph, no overlap)
-    grids = [fsei.Grid(**b) for b in boxes]
-    solo = [device_state(c, torch.float32) for c in cases]
-    for g, s, p in zip(grids, solo, params):
-        fsei.step(g, s, None, nsteps=2, stats=False, **p)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for g, s, p in zip(grids, solo, params):
-        fsei.step(g, s, None, nsteps=K, stats=False, **p)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_seq = e0.elapsed_time(e1)
-    return {"value": round(cells * K / (ms * 1e-3) / 1e6, 2), "unit": "Mcell-updates/s",
-            "boxes": len(cases), "cells": cells, "steps": K, "ms_per_step": round(ms / K, 4),
-            "precision": "mixed", "max_div": max(x["max_div"] for x in st),
-            "sequential_fsei_step": {"value": round(cells * K / (ms_seq * 1e-3) / 1e6, 2),
-                                     "ms_per_step": round(ms_seq / K, 4)},
-            "sizes": "64 boxes from {32^3, 64^3, 96x96x128, 128x128x192}, seed 5"}
+    return e0.elapsed_time(e1) / K, st
+
+
+def run_ensemble(args):
+    """64 independent boxes of uneven sizes (32^3, 64^3, 96x96x128, 128x128x192),
+    FP32 fields, one batched call per K steps (CUDA graph replayed per step,
+    one launch per pass for the boxes of each size), against the same boxes
+    advanced one after another with fsei_step; and each size's boxes batched
+    on their own."""
+    import torch
+    from paper_2103_15187_gb300 import fsei, inputs
+    cases = inputs.case_ensemble(args.ensemble_boxes, steps=args.steps)
+    if args.ensemble_sizes:
+        keep = {tuple(int(v) for v in t.split("x")) for t in args.ensemble_sizes.split(",")}
+        cases = [c for c in cases if (c.nx, c.ny, c.nz) in keep]
+    cells = sum(c.cells for c in cases)
+    K = args.ensemble_steps
+    ms, st = _time_batch(cases, K, not args.no_autotune)
+    out = {"value": round(cells / (ms * 1e-3) / 1e6, 2), "unit": "Mcell-updates/s",
+           "boxes": len(cases), "cells": cells, "steps": K, "ms_per_step": round(ms, 4),
+           "precision": "mixed", "max_div": max(x["max_div"] for x in st),
+           "sizes": "%d boxes from {32^3, 64^3, 96x96x128, 128x128x192}, seed 5" % len(cases)}
+    by_size = {}
+    for size in sorted({(c.nx, c.ny, c.nz) for c in cases}):
+        sub = [c for c in cases if (c.nx, c.ny, c.nz) == size]
+        ms_s, _ = _time_batch(sub, K, not args.no_autotune)
+        csub = sum(c.cells for c in sub)
+        by_size["%dx%dx%d" % size] = {"boxes": len(sub), "ms_per_step": round(ms_s, 4),
+                                      "value": round(csub / (ms_s * 1e-3) / 1e6, 2)}
+    out["by_size"] = by_size
+    if not args.no_ensemble_seq:
+        # the same boxes one after another (no graph, no overlap)
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        grids = [fsei.Grid(nx=c.nx, ny=c.ny, nz=c.nz, lx=c.lx, ly=c.ly, zbc=c.zbc, lz=c.lz,
+                           stretch=c.stretch, prec=fsei.FSEI_MIXED) for c in cases]
+        solo = [device_state(c, torch.float32) for c in cases]
+        params = [dict(re=c.re, dt=c.dt, cfl=c.cfl, fconst=c.fconst) for c in cases]
+        for g, s, p in zip(grids, solo, params):
+            fsei.step(g, s, None, nsteps=2, stats=False, **p)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for g, s, p in zip(grids, solo, params):
+            fsei.step(g, s, None, nsteps=K, stats=False, **p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_seq = e0.elapsed_time(e1)
+        out["sequential_fsei_step"] = {"value": round(cells * K / (ms_seq * 1e-3) / 1e6, 2),
+                                       "ms_per_step": round(ms_seq / K, 4)}
+    return out
 
 
 def run_heart_scale(args, peak):
@@ -690,6 +718,11 @@ def main():
     ap.add_argument("--ensemble-boxes", type=int, default=64)
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-sizes", default=None,
+                    help="comma-separated NXxNYxNZ sizes of the ensemble to keep")
+    ap.add_argument("--no-ensemble-seq", action="store_true")
+    ap.add_argument("--ensemble-only", action="store_true",
+                    help="print only the ensemble object (profiling runs)")
     ap.add_argument("--heart-steps", type=int, default=50)
     ap.add_argument("--no-heart", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -710,6 +743,13 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference_arm(args, rank, world)
+    if args.ensemble_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"ensemble": run_ensemble(args)}), flush=True)
+        return 0
     if world > 1:
         import torch
         import torch.distributed as dist

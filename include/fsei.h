@@ -259,9 +259,12 @@ fsei_status fsei_adjoint_step(fsei_grid grid, const fsei_state *fwd,
  * grid description, Reynolds number, dt or CFL, body force and state).
  * fsei_batch_create creates one grid per box (as fsei_grid_create) plus the
  * streams and events of a CUDA graph.  fsei_batch_step advances every box by
- * nsteps fractional steps: one step of all boxes is captured into a CUDA
- * graph whose per-box kernel chains run on parallel branches, and the graph
- * is replayed once per step on cuda_stream.  The graph is re-captured when
+ * nsteps fractional steps.  Boxes with the same description and launch
+ * schedule form a group: each pass of the step is one kernel launch over all
+ * boxes of the group (the box in blockIdx.z, its arguments from a device
+ * table).  One step of all groups is captured into a CUDA graph, groups on
+ * parallel branches, and the graph is replayed once per step on
+ * cuda_stream.  The graph is re-captured when
  * the state pointers, forces, parameters or history flags differ from the
  * last capture (the first call, and the call after it, capture).
  *   states: nboxes fsei_state (device pointers per box, have_prev_h updated);
@@ -269,7 +272,9 @@ fsei_status fsei_adjoint_step(fsei_grid grid, const fsei_state *fwd,
  *   params: nboxes fsei_step_params;
  *   out: NULL or nboxes fsei_step_stats (the call then synchronises; the
  *        status reports the first box with a device flag).
- * Each box's results equal those of fsei_step on that box alone. */
+ * Each box's results agree with fsei_step on that box alone to rounding
+ * (the grouped launches run the same kernel bodies from another entry
+ * point, so the last bits may differ). */
 typedef struct fsei_batch_s *fsei_batch;
 fsei_status fsei_batch_create(const fsei_grid_desc *descs, int32_t nboxes,
                               fsei_batch *out);
