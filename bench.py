@@ -304,7 +304,7 @@ def run_gpu_arm(args, rank, world):
     return case, results, err, e2e
 
 
-def _time_batch(cases, K, autotune):
+def _time_batch(cases, K, autotune, max_group=None):
     """ms per step of the boxes `cases` advanced together by fsei_batch_step
     (grouped launches in a CUDA graph), and the last call's statistics."""
     import torch
@@ -314,6 +314,8 @@ def _time_batch(cases, K, autotune):
     batch = fsei.Batch(boxes)
     if autotune:
         batch.autotune()
+    if max_group is not None:
+        batch.set_max_group(max_group)
     states = [device_state(c, torch.float32) for c in cases]
     params = [dict(re=c.re, dt=c.dt, cfl=c.cfl, fconst=c.fconst) for c in cases]
     # two warm-up calls: the first captures the graphs of a fresh state, the
@@ -329,7 +331,7 @@ def _time_batch(cases, K, autotune):
     e1.record(stream)
     torch.cuda.synchronize()
     st = fsei.batch_step(batch, states, None, params, nsteps=0, stats=True)
-    return e0.elapsed_time(e1) / K, st
+    return e0.elapsed_time(e1) / K, st, batch.launch_groups
 
 
 def run_ensemble(args):
@@ -346,15 +348,23 @@ def run_ensemble(args):
         cases = [c for c in cases if (c.nx, c.ny, c.nz) in keep]
     cells = sum(c.cells for c in cases)
     K = args.ensemble_steps
-    ms, st = _time_batch(cases, K, not args.no_autotune)
+    ms, st, ng = _time_batch(cases, K, not args.no_autotune)
     out = {"value": round(cells / (ms * 1e-3) / 1e6, 2), "unit": "Mcell-updates/s",
            "boxes": len(cases), "cells": cells, "steps": K, "ms_per_step": round(ms, 4),
            "precision": "mixed", "max_div": max(x["max_div"] for x in st),
+           "launch_groups": ng,
            "sizes": "%d boxes from {32^3, 64^3, 96x96x128, 128x128x192}, seed 5" % len(cases)}
+    # boxes per launch group (0: every box of a description in one launch)
+    by_group = {}
+    for mg in (1, 2, 8, 0):
+        ms_g, _, ng_g = _time_batch(cases, K, not args.no_autotune, max_group=mg)
+        by_group[str(mg)] = {"launch_groups": ng_g, "ms_per_step": round(ms_g, 4),
+                             "value": round(cells / (ms_g * 1e-3) / 1e6, 2)}
+    out["by_max_group"] = by_group
     by_size = {}
     for size in sorted({(c.nx, c.ny, c.nz) for c in cases}):
         sub = [c for c in cases if (c.nx, c.ny, c.nz) == size]
-        ms_s, _ = _time_batch(sub, K, not args.no_autotune)
+        ms_s, _, _ = _time_batch(sub, K, not args.no_autotune, max_group=0)
         csub = sum(c.cells for c in sub)
         by_size["%dx%dx%d" % size] = {"boxes": len(sub), "ms_per_step": round(ms_s, 4),
                                       "value": round(csub / (ms_s * 1e-3) / 1e6, 2)}

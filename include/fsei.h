@@ -280,6 +280,15 @@ fsei_status fsei_batch_create(const fsei_grid_desc *descs, int32_t nboxes,
                               fsei_batch *out);
 void fsei_batch_destroy(fsei_batch batch);
 int32_t fsei_batch_size(fsei_batch batch);
+/* Boxes per launch group (default 4; 0: no limit): the boxes of one group
+ * (same description and schedule) are split into launch groups of at most
+ * max_boxes, each with its own kernel launches, spread over the graph's
+ * parallel branches.  Larger groups launch fewer, larger kernels; smaller
+ * ones let different passes of different groups run side by side.  Drops
+ * the captured graphs.  FSEI_E_ARG for a NULL batch or max_boxes < 0. */
+fsei_status fsei_batch_set_max_group(fsei_batch batch, int32_t max_boxes);
+/* Launch groups of the last captured graph (0 before the first capture). */
+int32_t fsei_batch_launch_groups(fsei_batch batch);
 /* fsei_grid_autotune for every box (one measurement per distinct shape;
  * flags as there).  Drops the captured graphs, which the next
  * fsei_batch_step captures again with the new schedules. */

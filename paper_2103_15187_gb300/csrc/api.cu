@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1051,6 +1052,11 @@ const char *fsei_kernel_name(int32_t kind) {
 // for boxes without history) and the following steps.  They are re-captured
 // when the state pointers, forces or parameters of a call differ from the
 // captured ones.
+// Boxes per launch group by default: groups of a few boxes on parallel
+// branches let the memory-bound passes of one group run beside the latency-
+// bound ones (the serial FP64 z-sweep factors, small transforms) of another.
+constexpr int kDefaultMaxGroup = 4;
+
 struct fsei_batch_s {
     std::vector<fsei_grid> grids;
     std::vector<std::vector<unsigned char>> desc_key;   // per box: its description
@@ -1062,7 +1068,8 @@ struct fsei_batch_s {
     cudaGraphExec_t first = nullptr, rest = nullptr;
     void *tab_first = nullptr, *tab_rest = nullptr;    // argument tables of the graphs
     std::vector<unsigned char> key;   // bytes of the captured call's arguments
-    int ngroups = 0;                  // groups of the last capture
+    int ngroups = 0;                  // launch groups of the last capture
+    int max_group = kDefaultMaxGroup; // boxes per launch group (0: no limit)
 };
 
 namespace {
@@ -1161,6 +1168,15 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
             gkeys.push_back(k);
         }
         groups[gi].push_back(i);
+    }
+    // at most max_group boxes per launch group
+    if (B->max_group > 0) {
+        std::vector<std::vector<size_t>> split;
+        for (const std::vector<size_t> &g : groups)
+            for (size_t a = 0; a < g.size(); a += (size_t)B->max_group)
+                split.emplace_back(g.begin() + a,
+                                   g.begin() + std::min(g.size(), a + (size_t)B->max_group));
+        groups.swap(split);
     }
     // 3. argument tables: for every kernel of a group, one row per box
     std::vector<std::vector<size_t>> tab_off(groups.size());
@@ -1315,6 +1331,20 @@ void fsei_batch_destroy(fsei_batch B) {
 }
 
 int32_t fsei_batch_size(fsei_batch B) { return B ? (int32_t)B->grids.size() : 0; }
+
+fsei_status fsei_batch_set_max_group(fsei_batch B, int32_t max_boxes) {
+    g_err.clear();
+    if (!B) return fail(FSEI_E_ARG, "fsei_batch_set_max_group: NULL batch");
+    if (max_boxes < 0) return fail(FSEI_E_ARG, "max_boxes must be >= 0");
+    if (max_boxes != B->max_group) {
+        DeviceGuard dg(B->device);
+        batch_clear_graphs(B);
+        B->max_group = max_boxes;
+    }
+    return FSEI_OK;
+}
+
+int32_t fsei_batch_launch_groups(fsei_batch B) { return B ? B->ngroups : 0; }
 
 fsei_status fsei_batch_autotune(fsei_batch B, int32_t flags, void *cuda_stream) {
     g_err.clear();

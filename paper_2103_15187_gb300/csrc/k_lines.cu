@@ -256,8 +256,12 @@ void dispatch(const GridDev &g, const Fields<T> &F, Work<T> &W, cudaStream_t st)
     const TriPlan<T> &pb = W.plan[3];
     const int chunk = W.chunk_z;
     const int tx = W.tx_z;
+    // chunks of exactly 12 or 24 rows (nz = 192, 384, 768 ...) get registers
+    // of their own length, so that those lines also take the guard-free path
     if (chunk <= 8) launch_reg<T, 8, DIR, MODE>(g, F, W, pa, pb, tx, st);
+    else if (chunk == 12) launch_reg<T, 12, DIR, MODE>(g, F, W, pa, pb, tx, st);
     else if (chunk <= 16) launch_reg<T, 16, DIR, MODE>(g, F, W, pa, pb, tx, st);
+    else if (chunk == 24) launch_reg<T, 24, DIR, MODE>(g, F, W, pa, pb, tx, st);
     else launch_reg<T, 32, DIR, MODE>(g, F, W, pa, pb, tx, st);
 }
 
@@ -307,6 +311,7 @@ void launch_y_uni(const GridDev &g, Work<T> &W, const StepScalars *sc, cudaStrea
 template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, const StepScalars *sc,
                                           cudaStream_t st) {
     if (W.chunk_y <= 8) launch_y_uni<T, 8>(g, W, sc, st);
+    else if (W.chunk_y == 12) launch_y_uni<T, 12>(g, W, sc, st);
     else if (W.chunk_y <= 16) launch_y_uni<T, 16>(g, W, sc, st);
     else launch_y_uni<T, 32>(g, W, sc, st);
 }
@@ -327,11 +332,17 @@ template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T>
     (void)W;
     raise_smem_limit(K_sweep_y_uni<T, 8, false>.solo());
     raise_smem_limit(K_sweep_y_uni<T, 8, true>.solo());
+    raise_smem_limit(K_sweep_y_uni<T, 12, false>.solo());
+    raise_smem_limit(K_sweep_y_uni<T, 12, true>.solo());
     raise_smem_limit(K_sweep_y_uni<T, 16, false>.solo());
     raise_smem_limit(K_sweep_y_uni<T, 16, true>.solo());
     raise_smem_limit(K_sweep_y_uni<T, 32, false>.solo());
     raise_smem_limit(K_sweep_y_uni<T, 32, true>.solo());
     raise_smem_limit(K_sweep_reg<T, 8, 2, 0>.solo());
+    raise_smem_limit(K_sweep_reg<T, 12, 2, 0>.solo());
+    raise_smem_limit(K_sweep_reg<T, 24, 2, 0>.solo());
+    raise_smem_limit(K_sweep_reg<T, 12, 2, 1>.solo());
+    raise_smem_limit(K_sweep_reg<T, 24, 2, 1>.solo());
     raise_smem_limit(K_sweep_reg<T, 16, 2, 0>.solo());
     raise_smem_limit(K_sweep_reg<T, 32, 2, 0>.solo());
     raise_smem_limit(K_sweep_reg<T, 8, 2, 1>.solo());

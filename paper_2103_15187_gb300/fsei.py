@@ -29,7 +29,8 @@ EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
            "fsei_batch_destroy", "fsei_batch_size", "fsei_batch_step", "fsei_set_kernel_timing",
            "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version",
            "fsei_grid_autotune", "fsei_grid_get_schedule", "fsei_grid_set_schedule",
-           "fsei_batch_autotune", "fsei_fp64_fma_rate")
+           "fsei_batch_autotune", "fsei_fp64_fma_rate", "fsei_batch_set_max_group",
+           "fsei_batch_launch_groups")
 FSEI_TUNE_FORCE = 1
 
 
@@ -142,6 +143,10 @@ def load(path=LIB_PATH):
     lib.fsei_grid_get_schedule.restype = ctypes.c_int
     lib.fsei_grid_set_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
     lib.fsei_grid_set_schedule.restype = ctypes.c_int
+    lib.fsei_batch_set_max_group.argtypes = [vp, ctypes.c_int32]
+    lib.fsei_batch_set_max_group.restype = ctypes.c_int
+    lib.fsei_batch_launch_groups.argtypes = [vp]
+    lib.fsei_batch_launch_groups.restype = ctypes.c_int32
     lib.fsei_batch_autotune.argtypes = [vp, ctypes.c_int32, vp]
     lib.fsei_batch_autotune.restype = ctypes.c_int
     lib.fsei_fp64_fma_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -311,6 +316,15 @@ class Batch:
         """fsei_batch_autotune: one measured schedule per distinct box shape."""
         _check(load().fsei_batch_autotune(self.handle, FSEI_TUNE_FORCE if force else 0,
                                           _stream_handle(stream)))
+
+    def set_max_group(self, max_boxes):
+        """fsei_batch_set_max_group: boxes per launch group (0: no limit)."""
+        _check(load().fsei_batch_set_max_group(self.handle, int(max_boxes)))
+
+    @property
+    def launch_groups(self):
+        """fsei_batch_launch_groups: launch groups of the last capture."""
+        return load().fsei_batch_launch_groups(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -27,28 +27,38 @@ def fsei():
 
 
 def _boxes():
+    """Eight boxes of five descriptions: three channels of one shape (other
+    seeds and Reynolds numbers) and two Taylor-Green boxes of one shape (other
+    time steps) share a description, so they are launched together."""
     cases = [inputs.case_taylor_green(32, steps=5),
              inputs.case_periodic_random(16, seed=7, steps=5),
              inputs.case_channel(48, 24, 20, steps=5, seed=8, re=900.0),
              inputs.case_channel(64, 64, 40, steps=5, seed=9, re=3000.0,
                                  blobs=dict(nblobs=3, sigma=3.0, amp=5.0)),
-             inputs.case_channel(24, 12, 18, steps=5, seed=10, re=600.0)]
+             inputs.case_channel(24, 12, 18, steps=5, seed=10, re=600.0),
+             inputs.case_channel(24, 12, 18, steps=5, seed=11, re=1500.0),
+             inputs.case_taylor_green(32, steps=5, dt=2e-3),
+             inputs.case_channel(24, 12, 18, steps=5, seed=12, re=300.0,
+                                 blobs=dict(nblobs=2, sigma=2.0, amp=4.0))]
     return cases
 
 
+@pytest.mark.parametrize("max_group,groups", [(0, 5), (1, 8), (2, 6)])
 @pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
-def test_batch_equals_solo_runs(fsei, prec_name):
+def test_batch_equals_solo_runs(fsei, prec_name, max_group, groups):
     import torch
     prec = fsei.FSEI_FP64 if prec_name == "fp64" else fsei.FSEI_MIXED
     dtype = torch.float64 if prec_name == "fp64" else torch.float32
     cases = _boxes()
     batch = fsei.Batch([dict(nx=c.nx, ny=c.ny, nz=c.nz, lx=c.lx, ly=c.ly, zbc=c.zbc, lz=c.lz,
                              stretch=c.stretch, prec=prec) for c in cases])
+    batch.set_max_group(max_group)
     states = [pu.to_device(pu.initial_state_np(c), dtype) for c in cases]
     forces = [pu.force_device(c, dtype) for c in cases]
     params = [pu.params(c) for c in cases]
     stats1 = fsei.batch_step(batch, states, forces, params, nsteps=3)
     fsei.batch_step(batch, states, forces, params, nsteps=2)
+    assert batch.launch_groups == groups
     assert all(s["max_div"] < (1e-9 if prec_name == "fp64" else 1e-2) for s in stats1)
     torch.cuda.synchronize()
     for c, st in zip(cases, states):
