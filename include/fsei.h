@@ -261,10 +261,10 @@ fsei_status fsei_adjoint_step(fsei_grid grid, const fsei_state *fwd,
  * streams and events of a CUDA graph.  fsei_batch_step advances every box by
  * nsteps fractional steps.  Boxes with the same description and launch
  * schedule form a group: each pass of the step is one kernel launch over all
- * boxes of the group (the box in blockIdx.z, its arguments from a device
- * table).  One step of all groups is captured into a CUDA graph, groups on
- * parallel branches, and the graph is replayed once per step on
- * cuda_stream.  The graph is re-captured when
+ * boxes of the group (the box in blockIdx.z, its arguments from a table
+ * passed with the launch).  One step of all groups is captured into a CUDA
+ * graph, groups on parallel branches, and the graph is replayed once per
+ * step on cuda_stream.  The graph is re-captured when
  * the state pointers, forces, parameters or history flags differ from the
  * last capture (the first call, and the call after it, capture).
  *   states: nboxes fsei_state (device pointers per box, have_prev_h updated);
@@ -280,7 +280,7 @@ fsei_status fsei_batch_create(const fsei_grid_desc *descs, int32_t nboxes,
                               fsei_batch *out);
 void fsei_batch_destroy(fsei_batch batch);
 int32_t fsei_batch_size(fsei_batch batch);
-/* Boxes per launch group (default 4; 0: no limit): the boxes of one group
+/* Boxes per launch group (default 0: no limit): the boxes of one group
  * (same description and schedule) are split into launch groups of at most
  * max_boxes, each with its own kernel launches, spread over the graph's
  * parallel branches.  Larger groups launch fewer, larger kernels; smaller

@@ -1045,17 +1045,20 @@ const char *fsei_kernel_name(int32_t kind) {
 // form a group: every pass of the step (scalars, z-sweep plans, RHS + x
 // sweep, y and z sweeps, the transforms and z Poisson solve, the projection)
 // is one launch over all boxes of the group, box b in blockIdx.z with its own
-// arguments (fields, workspace, step parameters) from a device table.  One
+// arguments (fields, workspace, step parameters) from a table passed as the
+// launch's parameter.  One
 // step of every group is captured into a CUDA graph, the groups on parallel
 // branches, and the graph is replayed once per step on the caller's stream.
 // Two graphs are kept: the first step of a call (CFL pre-pass, Euler start
 // for boxes without history) and the following steps.  They are re-captured
 // when the state pointers, forces or parameters of a call differ from the
 // captured ones.
-// Boxes per launch group by default: groups of a few boxes on parallel
-// branches let the memory-bound passes of one group run beside the latency-
-// bound ones (the serial FP64 z-sweep factors, small transforms) of another.
-constexpr int kDefaultMaxGroup = 4;
+// Boxes per launch group by default (0: every box of a description in one
+// launch group).  Smaller launch groups on parallel branches let the passes
+// of different groups run side by side; measured on the 64-box ensemble of
+// four shapes, one launch group per shape was the fastest (15.4 Gcell/s,
+// against 14.6 with one box per launch group).
+constexpr int kDefaultMaxGroup = 0;
 
 struct fsei_batch_s {
     std::vector<fsei_grid> grids;
@@ -1066,7 +1069,6 @@ struct fsei_batch_s {
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> joins;
     cudaGraphExec_t first = nullptr, rest = nullptr;
-    void *tab_first = nullptr, *tab_rest = nullptr;    // argument tables of the graphs
     std::vector<unsigned char> key;   // bytes of the captured call's arguments
     int ngroups = 0;                  // launch groups of the last capture
     int max_group = kDefaultMaxGroup; // boxes per launch group (0: no limit)
@@ -1075,13 +1077,9 @@ struct fsei_batch_s {
 namespace {
 
 void batch_clear_graphs(fsei_batch_s *B) {
-    if (B->tab_first || B->tab_rest) cudaDeviceSynchronize();   // no replay still reads them
     if (B->first) cudaGraphExecDestroy(B->first);
     if (B->rest) cudaGraphExecDestroy(B->rest);
-    if (B->tab_first) cudaFree(B->tab_first);
-    if (B->tab_rest) cudaFree(B->tab_rest);
     B->first = B->rest = nullptr;
-    B->tab_first = B->tab_rest = nullptr;
     B->key.clear();
 }
 
@@ -1121,8 +1119,7 @@ bool same_launches(const std::vector<RecordedOp> &a, const std::vector<RecordedO
 }
 
 fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const *forces,
-                          const fsei_step_params *prm, bool first, cudaGraphExec_t *out,
-                          void **tab_out) {
+                          const fsei_step_params *prm, bool first, cudaGraphExec_t *out) {
     const size_t nb = B->grids.size();
     // 1. one recorded step per box (nothing is launched)
     std::vector<std::vector<RecordedOp>> rec(nb);
@@ -1169,53 +1166,38 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
         }
         groups[gi].push_back(i);
     }
-    // at most max_group boxes per launch group
-    if (B->max_group > 0) {
+    // at most max_group boxes per launch group, and no more than the
+    // argument-table capacity of any of the group's kernels
+    {
         std::vector<std::vector<size_t>> split;
-        for (const std::vector<size_t> &g : groups)
-            for (size_t a = 0; a < g.size(); a += (size_t)B->max_group)
-                split.emplace_back(g.begin() + a,
-                                   g.begin() + std::min(g.size(), a + (size_t)B->max_group));
+        for (const std::vector<size_t> &g : groups) {
+            size_t cap = B->max_group > 0 ? (size_t)B->max_group : g.size();
+            for (const RecordedOp &op : rec[g[0]])
+                if (op.kind == RecordedOp::KERNEL) cap = std::min(cap, (size_t)op.group_cap);
+            for (size_t a = 0; a < g.size(); a += cap)
+                split.emplace_back(g.begin() + a, g.begin() + std::min(g.size(), a + cap));
+        }
         groups.swap(split);
     }
-    // 3. argument tables: for every kernel of a group, one row per box
-    std::vector<std::vector<size_t>> tab_off(groups.size());
-    size_t tab_bytes = 0;
+    // 3. argument rows: for every kernel of a launch group, the boxes'
+    // argument tuples back to back (they become the launch's parameter)
+    std::vector<std::vector<std::vector<unsigned char>>> rows(groups.size());
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         const std::vector<RecordedOp> &ops = rec[groups[gi][0]];
+        rows[gi].resize(ops.size());
         for (size_t o = 0; o < ops.size(); ++o) {
-            tab_off[gi].push_back(tab_bytes);
-            if (ops[o].kind == RecordedOp::KERNEL)
-                tab_bytes += (ops[o].args.size() * groups[gi].size() + 255) & ~size_t(255);
+            if (ops[o].kind != RecordedOp::KERNEL) continue;
+            for (size_t b : groups[gi])
+                rows[gi][o].insert(rows[gi][o].end(), rec[b][o].args.begin(), rec[b][o].args.end());
+            ops[o].prepare_group();   // load it outside the capture
         }
-    }
-    std::vector<unsigned char> host(tab_bytes ? tab_bytes : 1);
-    for (size_t gi = 0; gi < groups.size(); ++gi)
-        for (size_t o = 0; o < rec[groups[gi][0]].size(); ++o) {
-            if (rec[groups[gi][0]][o].kind != RecordedOp::KERNEL) continue;
-            size_t at = tab_off[gi][o];
-            for (size_t b : groups[gi]) {
-                const std::vector<unsigned char> &ab = rec[b][o].args;
-                memcpy(host.data() + at, ab.data(), ab.size());
-                at += ab.size();
-            }
-            rec[groups[gi][0]][o].prepare_group();   // load it outside the capture
-        }
-    void *tab = nullptr;
-    if (cudaMalloc(&tab, host.size()) != cudaSuccess)
-        return fail(FSEI_E_NOMEM, "batch: argument tables (%zu bytes)", host.size());
-    if (cudaMemcpy(tab, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(tab);
-        return fail(FSEI_E_CUDA, "batch: argument table upload failed");
     }
     // 4. capture: every group on a branch, its side stream for the plans
     cudaStream_t cs = B->capture;
     cudaGetLastError();
     cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-    if (ce != cudaSuccess) {
-        cudaFree(tab);
+    if (ce != cudaSuccess)
         return fail(FSEI_E_CUDA, "batch: cannot begin graph capture: %s", cudaGetErrorString(ce));
-    }
     ce = cudaEventRecord(B->fork, cs);
     for (cudaStream_t b : B->branches)
         if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b, B->fork, 0);
@@ -1232,8 +1214,8 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
             const cudaStream_t st = op.st == ov.side ? ov.side : mst;
             switch (op.kind) {
             case RecordedOp::KERNEL:
-                op.launch_group(static_cast<unsigned char *>(tab) + tab_off[gi][o], (int)bx.size(),
-                                op.grid, op.block, op.smem, st, op.pdl);
+                op.launch_group(rows[gi][o].data(), (int)bx.size(), op.grid, op.block, op.smem, st,
+                                op.pdl);
                 break;
             case RecordedOp::MEMSET:
                 for (size_t b : bx) cudaMemsetAsync(rec[b][o].mem, 0, rec[b][o].mem_bytes, st);
@@ -1269,10 +1251,8 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
     if (graph) cudaGraphDestroy(graph);
     if (r != FSEI_OK) {
         cudaGetLastError();
-        cudaFree(tab);
         return r;
     }
-    *tab_out = tab;
     B->ngroups = (int)groups.size();
     return FSEI_OK;
 }
@@ -1409,8 +1389,8 @@ fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const 
         }
         if (key != B->key || !B->first) {
             batch_clear_graphs(B);
-            fsei_status r = batch_capture(B, states, forces, prm, true, &B->first, &B->tab_first);
-            if (r == FSEI_OK) r = batch_capture(B, states, forces, prm, false, &B->rest, &B->tab_rest);
+            fsei_status r = batch_capture(B, states, forces, prm, true, &B->first);
+            if (r == FSEI_OK) r = batch_capture(B, states, forces, prm, false, &B->rest);
             if (r != FSEI_OK) {
                 batch_clear_graphs(B);
                 return r;

@@ -225,11 +225,11 @@ struct SweepCoef {
 
 // one block per plan; thread p < P builds chunk p; thread 0 the reduced LU
 template <typename T>
-FSEI_D void k_plans(GridDev g, Work<T> W, const StepScalars *sc) {
+FSEI_D void k_plans(GridDev g, ZPlans<T> Z, const StepScalars *sc) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int kind = 2 + blockIdx.x;   // the z plans (x and y lines use uni_solve)
-    const TriPlan<T> &pl = W.plan[kind];
-    const TriPlanStore<T> &st = W.store[kind];
+    const TriPlan<T> &pl = Z.plan[blockIdx.x];
+    const TriPlanStore<T> &st = Z.store[blockIdx.x];
     const int n = pl.n, P = pl.P;
     double *sat = reinterpret_cast<double *>(smraw);
     double *sct = sat + n;
@@ -1032,7 +1032,12 @@ template <typename T> void launch_step_plans(const GridDev &g, Work<T> &W, const
     }
     const size_t sm = sizeof(double) * (2 * (size_t)maxn + 12 * (size_t)maxp);
     int thr = ((2 * maxp + 31) / 32) * 32;   // 2 P <= 64 threads
-    K_plans<T>.launch(false, dim3(2), dim3(thr), sm, st, g, W, sc);
+    ZPlans<T> Z;
+    for (int q = 0; q < 2; ++q) {
+        Z.plan[q] = W.plan[2 + q];
+        Z.store[q] = W.store[2 + q];
+    }
+    K_plans<T>.launch(false, dim3(2), dim3(thr), sm, st, g, Z, sc);
 }
 
 template <typename T> void launch_step_begin(const GridDev &g, Work<T> &W, StepScalars *sc,

@@ -16,15 +16,30 @@ namespace fsei {
 // The kernels of a step are __device__ bodies with two entry points: k_solo
 // runs a body for one grid with its arguments as kernel parameters; k_group
 // runs it for the boxes of a batch group at once, box blockIdx.z taking its
-// arguments from row blockIdx.z of a device table (every box of a group has
-// the same extents, so the same launch shape).  A Kernel<Body, MAXT, MINB>
-// names a body with the launch bounds of both entries.
+// arguments from row blockIdx.z of a table that travels as one by-value
+// kernel parameter (every box of a group has the same extents, so the same
+// launch shape).  Both entries read their arguments from the constant bank,
+// so the group entry needs no more registers than the solo one.  A
+// Kernel<Body, MAXT, MINB> names a body with the launch bounds of both.
 template <auto Body, int MAXT, int MINB, typename... P>
 __global__ void __launch_bounds__(MAXT, MINB) k_solo(P... p) { Body(p...); }
 
+// boxes one group launch can take: kernel parameters are limited to 32764
+// bytes
+template <typename Tup> constexpr int group_capacity() {
+    constexpr int c = (int)(32000 / sizeof(Tup));
+    static_assert(c >= 1, "argument tuple too large for a group launch");
+    return c > 64 ? 64 : c;
+}
+template <typename Tup, int NB> struct GroupRows {
+    Tup row[NB];
+};
+
 template <auto Body, int MAXT, int MINB, typename... P>
-__global__ void __launch_bounds__(MAXT, MINB) k_group(const cuda::std::tuple<P...> *__restrict__ tab) {
-    cuda::std::apply(Body, tab[blockIdx.z]);
+__global__ void __launch_bounds__(MAXT, MINB)
+    k_group(const __grid_constant__ GroupRows<cuda::std::tuple<P...>,
+                                              group_capacity<cuda::std::tuple<P...>>()> rows) {
+    cuda::std::apply(Body, rows.row[blockIdx.z]);
 }
 
 // One launch of a fractional step as recorded for a batch group: the entry
@@ -35,9 +50,12 @@ struct RecordedOp {
     enum Kind { KERNEL, MEMSET, FORK, JOIN } kind;
     cudaStream_t st;
     const void *entry;   // solo entry of the body (identifies the kernel)
-    void (*launch_group)(const void *tab, int nbox, dim3 grid, dim3 block, size_t smem,
+    // launches the group entry for nbox <= group_cap boxes whose argument
+    // rows (args of each box, back to back) start at rows
+    void (*launch_group)(const void *rows, int nbox, dim3 grid, dim3 block, size_t smem,
                          cudaStream_t st, bool pdl);
     void (*prepare_group)();   // loads the group entry, raises its smem limit
+    int group_cap;
     dim3 grid, block;
     size_t smem;
     bool pdl;
@@ -98,11 +116,15 @@ template <typename F> inline void raise_smem_limit(F *kernel) {
 }
 
 template <auto Body, int MAXT, int MINB, typename... P>
-void group_launch_of(const void *tab, int nbox, dim3 grid, dim3 block, size_t smem,
+void group_launch_of(const void *rows, int nbox, dim3 grid, dim3 block, size_t smem,
                      cudaStream_t st, bool pdl) {
+    using Tup = cuda::std::tuple<P...>;
+    constexpr int NB = group_capacity<Tup>();
+    static thread_local GroupRows<Tup, NB> t;   // 32 KB at most
+    if (nbox < 1 || nbox > NB) return;
+    memcpy(&t, rows, sizeof(Tup) * (size_t)nbox);
     grid.z = (unsigned)nbox;
-    launch_k(pdl, k_group<Body, MAXT, MINB, P...>, grid, block, smem, st,
-             static_cast<const cuda::std::tuple<P...> *>(tab));
+    launch_k(pdl, k_group<Body, MAXT, MINB, P...>, grid, block, smem, st, t);
 }
 template <auto Body, int MAXT, int MINB, typename... P> void group_prepare_of() {
     raise_smem_limit(k_group<Body, MAXT, MINB, P...>);
@@ -125,6 +147,7 @@ void launch_body(void (*)(P...), bool pdl, dim3 grid, dim3 block, size_t smem, c
         op.entry = (const void *)&k_solo<Body, MAXT, MINB, P...>;
         op.launch_group = &group_launch_of<Body, MAXT, MINB, P...>;
         op.prepare_group = &group_prepare_of<Body, MAXT, MINB, P...>;
+        op.group_cap = group_capacity<Tup>();
         op.grid = grid;
         op.block = block;
         op.smem = smem;
@@ -167,6 +190,13 @@ inline void memset_async(void *p, int v, size_t n, cudaStream_t st) {
 template <typename T> struct Fields {
     T *u, *v, *w, *p, *hu, *hv, *hw;
     const T *fx, *fy, *fz;   // may be NULL
+};
+
+// The two z-sweep plans of a grid (centres, faces) and their storage: what
+// the per-step factorisation kernel needs of the workspace.
+template <typename T> struct ZPlans {
+    TriPlan<T> plan[2];
+    TriPlanStore<T> store[2];
 };
 
 // Library-owned workspace and launch configuration of one grid.
