@@ -20,6 +20,8 @@ paper by eye:
 * ``step``      -- one AB2 / Crank-Nicolson fractional step (Eq. 3) and its
                    third-order Runge-Kutta variant
 * ``adjoint``   -- the exact transpose of that step (discrete adjoint)
+* ``ib``        -- immersed-boundary forcing by moving least squares and the
+                   hydrodynamic loads on the immersed surface (Eqs. 4-7)
 
 Pins (tests/test_oracle_*.py) tie every function to something other than
 itself: dense direct solves, closed-form single-mode amplification factors,

@@ -311,3 +311,53 @@ def case_ensemble(nboxes=64, seed=5, steps=100, sizes=ENSEMBLE_SIZES):
         c.name = "box%02d_%s" % (b, c.name)
         cases.append(c)
     return cases
+
+
+# ------------------------------------------------- immersed surface (IB) ----
+def icosphere(level):
+    """Unit sphere triangulated by `level` midpoint subdivisions of the
+    icosahedron: (vertices (N x 3), triangles (F x 3), counter-clockwise seen
+    from outside)."""
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
+         (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(p, dtype=np.float64) / np.linalg.norm(p) for p in v]
+    tris = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+            (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+            (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        mid = {}
+
+        def midpoint(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                mid[key] = len(verts) - 1
+            return mid[key]
+        new = []
+        for a, b, c in tris:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            new += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        tris = new
+    return np.array(verts), np.array(tris, dtype=np.int64)
+
+
+def ib_surface(center, radius, level, omega=(0.0, 0.0, 0.0), velocity=(0.0, 0.0, 0.0),
+               two_sided=False):
+    """Triangulated sphere standing in for a wet surface: markers at the face
+    centroids, outward unit normals, face areas, the vertex list and the
+    prescribed rigid motion of every marker (U = velocity + omega x (x -
+    center)).  Returns a dict of numpy arrays."""
+    unit, tris = icosphere(level)
+    verts = np.asarray(center, dtype=np.float64) + radius * unit
+    a, b, c = verts[tris[:, 0]], verts[tris[:, 1]], verts[tris[:, 2]]
+    xf = (a + b + c) / 3.0
+    cr = np.cross(b - a, c - a)
+    area = 0.5 * np.linalg.norm(cr, axis=1)
+    nf = cr / (2.0 * area[:, None])
+    rel = xf - np.asarray(center, dtype=np.float64)
+    ub = np.asarray(velocity, dtype=np.float64)[None, :] + np.cross(
+        np.asarray(omega, dtype=np.float64)[None, :], rel)
+    return {"xf": xf, "nf": nf, "af": area, "tris": tris, "verts": verts, "ub": ub,
+            "two_sided": np.full(len(tris), bool(two_sided))}
