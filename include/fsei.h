@@ -255,6 +255,56 @@ fsei_status fsei_adjoint_step(fsei_grid grid, const fsei_state *fwd,
                               void *fbar_x, void *fbar_y, void *fbar_z,
                               void *cuda_stream);
 
+/* Immersed-boundary forcing (Sec. 2.1, Eq. 4; Sec. 3.2): the no-slip
+ * condition of a moving surface imposed on Lagrangian markers (the
+ * centroids of its triangles).  For every marker b and velocity component,
+ * the 3 x 3 x 3 nodes of that component's staggered grid nearest to x_b form
+ * its support; the transfer operators phi_k of a moving-least-squares fit
+ * (linear basis [1, x, y, z], weight exp(-r^2) with r the node offset over
+ * the nearest node's control extents dx, dy and dz_k (centre points) or
+ * hc_k (w faces)) interpolate the field, u(x_b) = sum_k phi_k u_k; the
+ * direct force F_b = (U_b - u(x_b)) / dt is spread back over the same nodes,
+ * f_k += phi_k F_b dV_b / dV_k (dV_k = dx dy dz_k, or dx dy hc_k for w), so
+ * that sum(f dV) = sum(F dV_b).  The fits run in double.
+ *   u, v, w: the velocity to interpolate (device fields of the grid's type);
+ *   xb, ub: device arrays of nmarkers x 3 doubles (positions, prescribed
+ *     velocities); dvb: nmarkers forcing volumes (e.g. face area times the
+ *     local cell size);
+ *   fx, fy, fz: device fields the force is added to (atomically; the sum
+ *     over markers does not depend on their order beyond rounding);
+ *   u_at: NULL or device nmarkers x 3 doubles, the interpolated velocity.
+ * A marker whose support would leave the interior z nodes of a walled grid
+ * (within about one cell of a wall) is skipped; with skipped != NULL the
+ * call synchronises and writes their count.  Positions outside the periodic
+ * box are wrapped.  FSEI_E_ARG for NULL fields, bad counts or dt <= 0. */
+fsei_status fsei_ib_forcing(fsei_grid grid, const void *u, const void *v, const void *w,
+                            const double *xb, const double *ub, const double *dvb,
+                            int32_t nmarkers, double dt, void *fx, void *fy, void *fz,
+                            double *u_at, void *cuda_stream, int32_t *skipped);
+
+/* Hydrodynamic loads on the wet faces (Sec. 2.1, Eqs. 5-7): the pressure
+ * and the viscous stress tau = Re^-1 (grad u + grad u^T) at the probe point
+ * x_f + probe n_f off each face, from the fits above (the gradient is the
+ * fit's linear coefficients); face load F_f = (-p n_f + tau . n_f) A_f
+ * (Eq. 6), for a two-sided face (valve leaflet) minus the same at
+ * x_f - probe n_f (Eq. 5); a third of F_f is added to each of the face's
+ * three nodes (Eq. 7).
+ *   p, u, v, w: device fields of the grid's type;
+ *   xf, nf: device nfaces x 3 doubles (centroids, unit normals pointing into
+ *     the fluid on the + side); af: nfaces areas; two_sided: NULL (all
+ *     one-sided) or nfaces flags;
+ *   face_force: device nfaces x 3 doubles, written;
+ *   tris, node_force: NULL, or nfaces x 3 node indices and nnodes x 3
+ *     doubles the nodal loads are added to.
+ * Faces whose probe support leaves the interior get zero load and are
+ * counted in skipped[0]; node indices outside [0, nnodes) are counted in
+ * skipped[1] (skipped: NULL or 2 ints; the call then synchronises). */
+fsei_status fsei_ib_loads(fsei_grid grid, const void *p, const void *u, const void *v,
+                          const void *w, const double *xf, const double *nf, const double *af,
+                          const int32_t *two_sided, const int32_t *tris, int32_t nfaces,
+                          int32_t nnodes, double probe, double re, double *face_force,
+                          double *node_force, void *cuda_stream, int32_t *skipped);
+
 /* Batched ensemble of independent boxes of uneven sizes (each with its own
  * grid description, Reynolds number, dt or CFL, body force and state).
  * fsei_batch_create creates one grid per box (as fsei_grid_create) plus the

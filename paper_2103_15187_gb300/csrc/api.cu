@@ -190,6 +190,7 @@ struct fsei_grid_s {
     Work<double> wd;
     StepScalars *sc = nullptr;      // device
     StepScalars *sc_host = nullptr; // pinned
+    int *ib_count = nullptr;        // device: skipped markers / faces, bad node indices
     KernelTimer timer;
     // side stream and fork/join events: the z-sweep plans run beside the
     // RHS and y sweep
@@ -428,6 +429,7 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     set_smem_limits_poisson<T>(g, W);
     set_smem_limits_adjoint<T>(g, W);
     preload_project<T>();
+    preload_ib<T>();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FSEI_E_CUDA, "grid setup: %s", cudaGetErrorString(e));
     return FSEI_OK;
@@ -769,8 +771,10 @@ fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
         if (end != cap && *end == '\0') M.limit = (size_t)v;
     }
     double *ddz = M.get<double>(nz), *didz = M.get<double>(nz), *dihc = M.get<double>(nz + 1);
+    double *dzf = M.get<double>(nz + 1);
     float *fdz = M.get<float>(nz), *fidz = M.get<float>(nz), *fihc = M.get<float>(nz + 1);
     G->sc = M.get<StepScalars>(1);
+    G->ib_count = M.get<int>(2);
     if (M.err != cudaSuccess) {
         M.release();
         delete G;
@@ -781,9 +785,9 @@ fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
         for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
         return o;
     };
-    upload(ddz, dz); upload(didz, idz); upload(dihc, ihc);
+    upload(ddz, dz); upload(didz, idz); upload(dihc, ihc); upload(dzf, zf);
     upload(fdz, tof(dz)); upload(fidz, tof(idz)); upload(fihc, tof(ihc));
-    g.dz = ddz; g.idz = didz; g.ihc = dihc;
+    g.dz = ddz; g.idz = didz; g.ihc = dihc; g.zf = dzf;
     g.dzf = fdz; g.idzf = fidz; g.ihcf = fihc;
     cudaMemset(G->sc, 0, sizeof(StepScalars));
     if (cudaMallocHost((void **)&G->sc_host, sizeof(StepScalars)) != cudaSuccess) {
@@ -1007,6 +1011,75 @@ fsei_status fsei_poisson_solve(fsei_grid G, const void *rhs, void *phi, void *cu
     cudaStream_t st = (cudaStream_t)cuda_stream;
     return G->prec == FSEI_FP64 ? run_poisson<double>(G, G->wd, rhs, phi, st)
                                 : run_poisson<float>(G, G->wf, rhs, phi, st);
+}
+
+// the launch check and skipped-count read-back of the two IB entry points
+static fsei_status ib_finish(fsei_grid_s *G, cudaStream_t st, int32_t *skipped, int count,
+                      const char *what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FSEI_E_CUDA, "%s launch: %s", what, cudaGetErrorString(e));
+    if (skipped) {
+        int h[2] = {0, 0};
+        if (cudaMemcpyAsync(h, G->ib_count, sizeof(int) * count, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return fail(FSEI_E_CUDA, "%s: read-back failed", what);
+        for (int i = 0; i < count; ++i) skipped[i] = h[i];
+    }
+    return FSEI_OK;
+}
+
+fsei_status fsei_ib_forcing(fsei_grid G, const void *u, const void *v, const void *w,
+                            const double *xb, const double *ub, const double *dvb,
+                            int32_t nmarkers, double dt, void *fx, void *fy, void *fz,
+                            double *u_at, void *cuda_stream, int32_t *skipped) {
+    g_err.clear();
+    cudaGetLastError();
+    if (!G || !u || !v || !w || !fx || !fy || !fz) return fail(FSEI_E_ARG, "fsei_ib_forcing: NULL argument");
+    if (nmarkers < 0 || (nmarkers > 0 && (!xb || !ub || !dvb)))
+        return fail(FSEI_E_ARG, "fsei_ib_forcing: bad marker arrays");
+    if (nmarkers > (1 << 29)) return fail(FSEI_E_ARG, "fsei_ib_forcing: too many markers");
+    if (!(dt > 0)) return fail(FSEI_E_ARG, "fsei_ib_forcing: dt must be > 0");
+    DeviceGuard dg(G->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaMemsetAsync(G->ib_count, 0, sizeof(int), st);
+    if (G->prec == FSEI_FP64)
+        launch_ib_force<double>(G->g, (const double *)u, (const double *)v, (const double *)w, xb,
+                                ub, dvb, nmarkers, dt, (double *)fx, (double *)fy, (double *)fz,
+                                u_at, G->ib_count, st);
+    else
+        launch_ib_force<float>(G->g, (const float *)u, (const float *)v, (const float *)w, xb, ub,
+                               dvb, nmarkers, dt, (float *)fx, (float *)fy, (float *)fz, u_at,
+                               G->ib_count, st);
+    return ib_finish(G, st, skipped, 1, "fsei_ib_forcing");
+}
+
+fsei_status fsei_ib_loads(fsei_grid G, const void *p, const void *u, const void *v,
+                          const void *w, const double *xf, const double *nf, const double *af,
+                          const int32_t *two_sided, const int32_t *tris, int32_t nfaces,
+                          int32_t nnodes, double probe, double re, double *face_force,
+                          double *node_force, void *cuda_stream, int32_t *skipped) {
+    g_err.clear();
+    cudaGetLastError();
+    if (!G || !p || !u || !v || !w) return fail(FSEI_E_ARG, "fsei_ib_loads: NULL field");
+    if (nfaces < 0 || (nfaces > 0 && (!xf || !nf || !af || !face_force)))
+        return fail(FSEI_E_ARG, "fsei_ib_loads: bad face arrays");
+    if (nfaces > (1 << 26)) return fail(FSEI_E_ARG, "fsei_ib_loads: too many faces");
+    if (node_force && (!tris || nnodes < 1))
+        return fail(FSEI_E_ARG, "fsei_ib_loads: nodal loads need tris and nnodes >= 1");
+    if (!(probe > 0) || !(re > 0)) return fail(FSEI_E_ARG, "fsei_ib_loads: probe and re must be > 0");
+    DeviceGuard dg(G->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaMemsetAsync(G->ib_count, 0, 2 * sizeof(int), st);
+    if (G->prec == FSEI_FP64)
+        launch_ib_loads<double>(G->g, (const double *)p, (const double *)u, (const double *)v,
+                                (const double *)w, xf, nf, af, two_sided, tris, nfaces, nnodes,
+                                probe, 1.0 / re, face_force, node_force, G->ib_count, st);
+    else
+        launch_ib_loads<float>(G->g, (const float *)p, (const float *)u, (const float *)v,
+                               (const float *)w, xf, nf, af, two_sided, tris, nfaces, nnodes,
+                               probe, 1.0 / re, face_force, node_force, G->ib_count, st);
+    return ib_finish(G, st, skipped, 2, "fsei_ib_loads");
 }
 
 fsei_status fsei_set_kernel_timing(fsei_grid G, int32_t enable) {

@@ -48,6 +48,8 @@ struct GridDev {
     int sk;             // row stride (complex elements) of the spectrum
     double dx, dy, idx, idy, idx2, idy2;
     const double *dz, *idz, *ihc;   // dz[nz], 1/dz[nz], 1/hc[nz+1]
+    const double *zf;               // the z faces z_0 .. z_nz (nz + 1; NULL
+                                    // where no kernel needs them)
     const float *dzf, *idzf, *ihcf;
     // float roundings of dx, dy, idx, idy, idx2, idy2 and dx dy (the
     // single-precision kernels read these rather than convert per thread:

@@ -365,6 +365,22 @@ void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T 
                          T *fby, T *fbz, double re, cudaStream_t st,
                          const LaunchHook *hook = nullptr);
 template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<T> &W);
+// immersed-boundary forcing of nm markers (k_ib.cu): interpolate, force,
+// spread into fx, fy, fz (+=); u_at (nullable): interpolated velocities
+// (nm x 3); skipped[0] counts markers whose support leaves the interior
+template <typename T>
+void launch_ib_force(const GridDev &g, const T *u, const T *v, const T *w, const double *xb,
+                     const double *ub, const double *dvb, int nm, double dt, T *fx, T *fy,
+                     T *fz, double *u_at, int *skipped, cudaStream_t st);
+// face loads (face_force written, node_force += a third per node);
+// skipped[0] counts faces whose probe support leaves the interior,
+// skipped[1] node indices outside [0, nnodes)
+template <typename T>
+void launch_ib_loads(const GridDev &g, const T *p, const T *u, const T *v, const T *w,
+                     const double *xf, const double *nf, const double *af, const int *two_sided,
+                     const int *tris, int nfaces, int nnodes, double probe, double inv_re,
+                     double *face_force, double *node_force, int *skipped, cudaStream_t st);
+template <typename T> void preload_ib();
 template <typename T> void preload_project();
 template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                           StepScalars *sc, cudaStream_t st);

@@ -30,7 +30,7 @@ EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
            "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version",
            "fsei_grid_autotune", "fsei_grid_get_schedule", "fsei_grid_set_schedule",
            "fsei_batch_autotune", "fsei_fp64_fma_rate", "fsei_batch_set_max_group",
-           "fsei_batch_launch_groups")
+           "fsei_batch_launch_groups", "fsei_ib_forcing", "fsei_ib_loads")
 FSEI_TUNE_FORCE = 1
 
 
@@ -143,6 +143,16 @@ def load(path=LIB_PATH):
     lib.fsei_grid_get_schedule.restype = ctypes.c_int
     lib.fsei_grid_set_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
     lib.fsei_grid_set_schedule.restype = ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    lib.fsei_ib_forcing.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.c_int32, ctypes.c_double,
+                                    vp, vp, vp, vp, vp, ip]
+    lib.fsei_ib_forcing.restype = ctypes.c_int
+    lib.fsei_ib_loads.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int32,
+                                  ctypes.c_int32, ctypes.c_double, ctypes.c_double, vp, vp, vp,
+                                  ip]
+    lib.fsei_ib_loads.restype = ctypes.c_int
+    del dp
     lib.fsei_batch_set_max_group.argtypes = [vp, ctypes.c_int32]
     lib.fsei_batch_set_max_group.restype = ctypes.c_int
     lib.fsei_batch_launch_groups.argtypes = [vp]
@@ -369,6 +379,39 @@ def batch_step(batch, states, forces, params, nsteps=1, stream=None, stats=True)
     res = [o.as_dict() for o in out] if out is not None else None
     _check(status, res)
     return res
+
+
+def ib_forcing(grid, vel, markers, dt, f, u_at=None, stream=None):
+    """fsei_ib_forcing.  vel: (u, v, w) device tensors; markers: dict of
+    device float64 tensors xb (M x 3), ub (M x 3), dvb (M); f: (fx, fy, fz)
+    device tensors the force is added to; u_at: None or a device (M x 3)
+    float64 tensor for the interpolated velocity.  Returns the number of
+    skipped markers (the call synchronises)."""
+    n = int(markers["xb"].shape[0])
+    sk = ctypes.c_int32(0)
+    _check(load().fsei_ib_forcing(grid.handle, _ptr(vel[0]), _ptr(vel[1]), _ptr(vel[2]),
+                                  _ptr(markers["xb"]), _ptr(markers["ub"]), _ptr(markers["dvb"]),
+                                  n, float(dt), _ptr(f[0]), _ptr(f[1]), _ptr(f[2]), _ptr(u_at),
+                                  _stream_handle(stream), ctypes.byref(sk)))
+    return sk.value
+
+
+def ib_loads(grid, p, vel, surface, probe, re, node_force=None, stream=None):
+    """fsei_ib_loads.  surface: dict of device tensors xf, nf (F x 3 float64),
+    af (F, float64), optionally two_sided (F, int32) and tris (F x 3, int32)
+    with nnodes; node_force: None or an (nnodes x 3) float64 tensor added to.
+    Returns (face_force (F x 3 device tensor), skipped faces, bad node
+    indices)."""
+    import torch
+    nf = int(surface["xf"].shape[0])
+    ff = torch.empty((nf, 3), dtype=torch.float64, device=surface["xf"].device)
+    sk = (ctypes.c_int32 * 2)()
+    _check(load().fsei_ib_loads(grid.handle, _ptr(p), _ptr(vel[0]), _ptr(vel[1]), _ptr(vel[2]),
+                                _ptr(surface["xf"]), _ptr(surface["nf"]), _ptr(surface["af"]),
+                                _ptr(surface.get("two_sided")), _ptr(surface.get("tris")), nf,
+                                int(surface.get("nnodes", 0)), float(probe), float(re), _ptr(ff),
+                                _ptr(node_force), _stream_handle(stream), sk))
+    return ff, sk[0], sk[1]
 
 
 def set_kernel_timing(grid, enable):
