@@ -14,7 +14,10 @@ the rest to its citations; the readings used here (and by the CUDA path):
 
 * support: per axis the node of the component's grid nearest to the point
   and its two neighbours (periodic x, y; with walls the support must stay
-  on interior nodes);
+  on interior nodes); a point exactly halfway between two nodes takes the
+  one whose control volume, taken half-open [lower end, upper end), holds
+  it (control volumes end at the faces for centre nodes and at the centres
+  for face nodes);
 * weight w_k = exp(-r_k^2), r_k^2 = sum_d ((x_k,d - x_d) / h_d)^2, h_d the
   extent along axis d of the nearest node's control volume (dx, dy; dz_k
   for centre points, hc_k for w faces);
@@ -48,11 +51,39 @@ def _axis_nodes(g, loc, axis):
     return g.zf[:-1] if loc == W else g.zc
 
 
-def _nearest(coords, x, periodic, length):
+def _nearest(coords, bounds, x, periodic, length):
+    """Index of the node nearest to x; on a tie the node whose control
+    volume [bounds[i], bounds[i+1]) holds x (periodic: x taken into the
+    box first)."""
     if periodic:
-        d = (coords - x + 0.5 * length) % length - 0.5 * length
-        return int(np.argmin(np.abs(d)))
-    return int(np.argmin(np.abs(coords - x)))
+        x = bounds[0] + (x - bounds[0]) % length
+        d = np.abs((coords - x + 0.5 * length) % length - 0.5 * length)
+    else:
+        d = np.abs(coords - x)
+    cand = np.flatnonzero(d == d.min())
+    if len(cand) == 1:
+        return int(cand[0])
+    for i in cand:
+        lo, hi = bounds[i], bounds[i + 1]
+        if lo <= x < hi:
+            return int(i)
+    return int(cand[-1])
+
+
+def _axis_bounds(g, loc, axis):
+    """Control-volume ends of the component's nodes along one axis: faces
+    for centre nodes, centres for face nodes (one more entry than nodes)."""
+    if axis == 0:
+        return (np.arange(g.nx + 1) - (0.5 if loc == U else 0.0)) * g.dx
+    if axis == 1:
+        return (np.arange(g.ny + 1) - (0.5 if loc == V else 0.0)) * g.dy
+    if loc != W:
+        return g.zf
+    zc = g.zc
+    if g.walls:
+        return np.concatenate([[2 * g.zf[0] - zc[0]], zc])
+    lz = g.zf[-1] - g.zf[0]
+    return np.concatenate([[zc[-1] - lz], zc])
 
 
 def support(g, loc, xb):
@@ -62,7 +93,8 @@ def support(g, loc, xb):
     nodes = [_axis_nodes(g, loc, a) for a in range(3)]
     lengths = (g.lx, g.ly, g.zf[-1] - g.zf[0])
     periodic = (True, True, not g.walls)
-    c = [_nearest(nodes[a], xb[a], periodic[a], lengths[a]) for a in range(3)]
+    c = [_nearest(nodes[a], _axis_bounds(g, loc, a), xb[a], periodic[a], lengths[a])
+         for a in range(3)]
     n = (g.nx, g.ny, g.nz)
     if g.walls:
         lo = 1 if loc == W else 0

@@ -16,7 +16,9 @@
 //                tau = Re^-1 (grad u + grad u^T); face load times the area,
 //                a third of it added to each of the face's nodes.
 //
-// Readings (where the paper defers to its citations): weight exp(-r^2), r
+// Readings (where the paper defers to its citations): the support centred on
+// the nearest node (a point exactly halfway between two nodes takes the one
+// whose half-open control volume [lower, upper) holds it); weight exp(-r^2), r
 // the node offset over the nearest node's control extents (dx, dy; dz_k for
 // centre points, hc_k for w faces); basis [1, x, y, z] centred and scaled at
 // the evaluation point; dV_k = dx dy dz_k (u, v) or dx dy hc_k (w).  A support
@@ -70,7 +72,9 @@ FSEI_D bool support_node(const GridDev &g, int loc, const double x[3], int lane,
     }
     int c;
     if (loc == LOC_W) {
-        c = (z - g.zf[lo] <= g.zf[lo + 1] - z) ? lo : lo + 1;
+        // a tie (z on the centre between the two faces) goes to the upper
+        // face, whose control volume [zc_lo, zc_lo+1) holds z
+        c = (z - g.zf[lo] < g.zf[lo + 1] - z) ? lo : lo + 1;
     } else {
         c = lo;
         const double zc = 0.5 * (g.zf[lo] + g.zf[lo + 1]);

@@ -191,3 +191,17 @@ def test_nodal_loads_and_closed_surface():
     # a uniform pressure pushes a closed surface nowhere: sum n_f A_f = 0
     Fp = -2.5 * surf["nf"] * surf["af"][:, None]
     assert np.max(np.abs(Fp.sum(axis=0))) < 1e-13
+
+
+def test_support_tie_goes_to_the_node_whose_volume_holds_the_point():
+    """A point exactly on the x face i dx is halfway between centres i - 1
+    and i: it lies in cell i, so the centre support is centred on i; exactly
+    on the centre (i + 1/2) dx it is halfway between faces i and i + 1 and
+    lies in the control volume [(i + 1/2) dx, (i + 3/2) dx) of face i + 1."""
+    g = Grid(16, 16, 16, 1.0, 1.0, Z_PERIODIC, lz=1.0)
+    x = np.array([5 / 16, 0.43, 0.51])
+    idx, _, _ = ib.support(g, ib.V, x)      # v: x at the centres
+    assert idx[13][2] == 5
+    x = np.array([5.5 / 16, 0.43, 0.51])
+    idx, _, _ = ib.support(g, ib.U, x)      # u: x at the faces
+    assert idx[13][2] == 6
