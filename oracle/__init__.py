@@ -20,6 +20,8 @@ paper by eye:
 * ``step``      -- one AB2 / Crank-Nicolson fractional step (Eq. 3) and its
                    third-order Runge-Kutta variant
 * ``adjoint``   -- the exact transpose of that step (discrete adjoint)
+* ``rheology``  -- the Carreau-Yasuda (shear-thinning) stress, as an explicit
+                   remainder beside the implicit Newtonian viscous term
 * ``ib``        -- immersed-boundary forcing by moving least squares and the
                    hydrodynamic loads on the immersed surface (Eqs. 4-7)
 

@@ -27,6 +27,7 @@ import numpy as np
 
 from . import operators as op
 from .poisson import oracle_poisson
+from .rheology import non_newtonian_term
 from .tridiag import thomas, cyclic_thomas
 
 
@@ -106,10 +107,12 @@ def sweep_z_face(g, beta, d):
 
 # ----------------------------------------------------------------- step ----
 def oracle_step(g, state, f=None, re=100.0, dt=1e-3, cfl=0.0, gamma=1.5,
-                rho=-0.5, fconst=(0.0, 0.0, 0.0)):
+                rho=-0.5, fconst=(0.0, 0.0, 0.0), rheology=None):
     """One step n -> n+1.  `state` is a dict with float64 arrays u, v, w, p,
     hu, hv, hw (H^{n-1}) and the flag have_prev_h; `f` is None or a tuple
-    (fx, fy, fz).  Returns (new_state, stats)."""
+    (fx, fy, fz).  rheology: None (Newtonian) or a dict lam, n, a, eta_inf of
+    the Carreau-Yasuda law, whose explicit remainder joins H (see
+    rheology.py).  Returns (new_state, stats)."""
     u, v, w, p = state["u"], state["v"], state["w"], state["p"]
     w = op.wall_w(g, w)
     if cfl > 0.0:
@@ -119,6 +122,9 @@ def oracle_step(g, state, f=None, re=100.0, dt=1e-3, cfl=0.0, gamma=1.5,
     beta = dt / (2.0 * re)
 
     hu, hv, hw = op.advection(g, u, v, w)
+    if rheology is not None:
+        nu_u, nu_v, nu_w = non_newtonian_term(g, u, v, w, re, **rheology)
+        hu, hv, hw = hu + nu_u, hv + nu_v, hw + nu_w
     lu, lv, lw = op.viscous(g, u, v, w)
     gx, gy, gz = op.gradient(g, p)
     if f is None:
