@@ -121,6 +121,25 @@ typedef struct {
  *     the full step's; H of the last sub-step is stored as the history. */
 typedef enum { FSEI_AB2_CN = 0, FSEI_RK3_CN = 1 } fsei_scheme;
 
+/* Constitutive law of fsei_step_params.rheology (Sec. 2.1).
+ *   FSEI_NEWTONIAN: tau = 2 Re^-1 E;
+ *   FSEI_CARREAU_YASUDA: shear-thinning blood, tau = 2 Re^-1 eta(gdot) E
+ *     with eta = eta_inf + (1 - eta_inf) (1 + (lambda gdot)^a)^((n - 1) / a)
+ *     relative to the zero-shear viscosity (Re built on it), gdot =
+ *     sqrt(2 E:E).  The Newtonian part stays in the implicit Crank-Nicolson
+ *     sweeps; the remainder div(2 Re^-1 (eta - 1) E) of u^n is explicit and
+ *     joins the advection term H (same Adams-Bashforth weights, stored in
+ *     the history).  Strain rates at the centres and at the advection's
+ *     edge points, gdot at the centres, the excess viscosity averaged back
+ *     to the edges.  Adams-Bashforth scheme only. */
+typedef enum { FSEI_NEWTONIAN = 0, FSEI_CARREAU_YASUDA = 1 } fsei_rheology;
+typedef struct {
+    double lambda;     /* time constant (in the flow's time unit), >= 0 */
+    double n;          /* power-law index, > 0 */
+    double a;          /* Yasuda exponent, > 0 */
+    double eta_inf;    /* infinite-shear viscosity over the zero-shear one, in [0, 1] */
+} fsei_carreau_yasuda;
+
 typedef struct {
     double re;          /* Reynolds number (> 0) */
     double dt;          /* time step when cfl <= 0 */
@@ -132,6 +151,8 @@ typedef struct {
     double fconst[3];   /* uniform body force added to f (e.g. a channel's
                            pressure-gradient drive 2/Re in x) */
     int32_t scheme;     /* fsei_scheme (0: Adams-Bashforth, Eq. 3) */
+    int32_t rheology;   /* fsei_rheology (0: Newtonian) */
+    fsei_carreau_yasuda cy;   /* FSEI_CARREAU_YASUDA parameters */
 } fsei_step_params;
 
 typedef struct {

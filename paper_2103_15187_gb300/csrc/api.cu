@@ -102,7 +102,7 @@ struct DevAllocs {
 
 enum KernelKind {
     KK_SPEED, KK_BEGIN, KK_RHS_X, KK_SWEEP_Y, KK_SWEEP_Z, KK_RFFT_X, KK_FFT_Y, KK_POISSON_Z,
-    KK_IFFT_Y, KK_IRFFT_X, KK_PROJECT, KK_PLANS,
+    KK_IFFT_Y, KK_IRFFT_X, KK_PROJECT, KK_PLANS, KK_NN,
     // the adjoint step's launch groups (AdjointKind order)
     KK_ADJ_FIRST, KK_COUNT = KK_ADJ_FIRST + AK_COUNT
 };
@@ -111,6 +111,7 @@ const char *const kKernelNames[KK_COUNT] = {
     "sweep_y", "sweep_z (+ u*)", "rfft_x (div + x R2C)", "fft_y (forward)",
     "poisson_z (+ exact modes)", "fft_y (inverse)", "irfft_x (x C2R)",
     "project (+ p update, stats)", "z-sweep plans (side stream)",
+    "non-Newtonian remainder (2 launches)",
     "adj_phibar", "adj_poisson (5 launches)", "adj_ustar", "adj_sweep_z", "adj_sweep_y",
     "adj_sweep_x", "adj_hist", "adj_gather"};
 
@@ -430,8 +431,21 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     set_smem_limits_adjoint<T>(g, W);
     preload_project<T>();
     preload_ib<T>();
+    preload_rheology<T>();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FSEI_E_CUDA, "grid setup: %s", cudaGetErrorString(e));
+    return FSEI_OK;
+}
+
+// the rheology fields of a caller's parameters
+fsei_status check_rheology(const fsei_step_params &p, const char *who) {
+    if (p.rheology == FSEI_NEWTONIAN) return FSEI_OK;
+    if (p.rheology != FSEI_CARREAU_YASUDA) return fail(FSEI_E_ARG, "%s: unknown rheology %d", who, p.rheology);
+    if (p.scheme != FSEI_AB2_CN)
+        return fail(FSEI_E_UNSUPPORTED, "%s: the Carreau-Yasuda law runs with the Adams-Bashforth scheme only", who);
+    if (!(p.cy.lambda >= 0) || !(p.cy.n > 0) || !(p.cy.a > 0) || !(p.cy.eta_inf >= 0) ||
+        !(p.cy.eta_inf <= 1))
+        return fail(FSEI_E_ARG, "%s: Carreau-Yasuda needs lambda >= 0, n > 0, a > 0, 0 <= eta_inf <= 1", who);
     return FSEI_OK;
 }
 
@@ -442,6 +456,8 @@ StepArgs step_args(const fsei_step_params &p) {
     a.re = p.re; a.dt = p.dt; a.cfl = p.cfl; a.gamma = p.gamma; a.rho = p.rho;
     for (int i = 0; i < 3; ++i) a.fconst[i] = p.fconst[i];
     a.scheme = p.scheme;
+    a.rheology = p.rheology;
+    a.cy[0] = p.cy.lambda; a.cy[1] = p.cy.n; a.cy[2] = p.cy.a; a.cy[3] = p.cy.eta_inf;
     a.alpha = 1.0;
     a.substep = 0;
     return a;
@@ -455,6 +471,22 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
     F.u = (T *)s->u; F.v = (T *)s->v; F.w = (T *)s->w; F.p = (T *)s->p;
     F.hu = (T *)s->hu; F.hv = (T *)s->hv; F.hw = (T *)s->hw;
     F.fx = (const T *)fx; F.fy = (const T *)fy; F.fz = (const T *)fz;
+    F.hx = F.hy = F.hz = nullptr;
+    if (a.rheology == FSEI_CARREAU_YASUDA) {
+        if (!W.nn0) {
+            const size_t ncell = (size_t)G->g.nx * G->g.ny * G->g.nz;
+            W.nn0 = G->mem.get<T>(ncell);
+            W.nn1 = G->mem.get<T>(ncell);
+            W.nn2 = G->mem.get<T>(ncell);
+            W.nuc = G->mem.get<T>(ncell);
+            if (G->mem.err != cudaSuccess) {
+                W.nn0 = W.nn1 = W.nn2 = W.nuc = nullptr;
+                G->mem.err = cudaSuccess;
+                return fail(FSEI_E_NOMEM, "non-Newtonian workspace allocation failed");
+            }
+        }
+        F.hx = W.nn0; F.hy = W.nn1; F.hz = W.nn2;
+    }
     const GridDev &g = G->g;
     KernelTimer &tm = G->timer;
     // programmatic dependent launches between the step's kernels (in a
@@ -487,6 +519,10 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
         const Overlap &op = G->ov_plans;
         fork_side(op, st);
         tm.run(KK_PLANS, op.side, [&] { launch_step_plans<T>(g, W, G->sc, op.side); });
+        if (F.hx)
+            tm.run(KK_NN, st, [&] {
+                launch_non_newtonian<T>(g, F.u, F.v, F.w, W, a.re, a.cy, st);
+            });
         tm.run(KK_RHS_X, st, [&] { launch_rhs_x<T>(g, F, W, G->sc, b, st); });
         tm.run(KK_SWEEP_Y, st, [&] { launch_sweep_y<T>(g, W, G->sc, st); });
         join_side(op, st);
@@ -915,6 +951,10 @@ fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy
     if (!(prm->cfl > 0) && !(prm->dt > 0)) return fail(FSEI_E_ARG, "need dt > 0 or cfl > 0");
     if (prm->scheme != FSEI_AB2_CN && prm->scheme != FSEI_RK3_CN)
         return fail(FSEI_E_ARG, "unknown scheme %d", prm->scheme);
+    {
+        const fsei_status rs = check_rheology(*prm, "fsei_step");
+        if (rs != FSEI_OK) return rs;
+    }
     const StepArgs a = step_args(*prm);
     DeviceGuard dg(G->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -964,6 +1004,8 @@ fsei_status fsei_adjoint_step(fsei_grid G, const fsei_state *fwd, const fsei_ste
     if (prm->scheme != FSEI_AB2_CN)
         return fail(prm->scheme == FSEI_RK3_CN ? FSEI_E_UNSUPPORTED : FSEI_E_ARG,
                     "the adjoint step is implemented for the Adams-Bashforth scheme only");
+    if (prm->rheology != FSEI_NEWTONIAN)
+        return fail(FSEI_E_UNSUPPORTED, "the adjoint step is implemented for the Newtonian stress only");
     StepArgs a = step_args(*prm);
     a.cfl = 0.0;
     DeviceGuard dg(G->device);
@@ -1441,6 +1483,11 @@ fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const 
         if (!(prm[i].cfl > 0) && !(prm[i].dt > 0)) return fail(FSEI_E_ARG, "box %zu: need dt > 0 or cfl > 0", i);
         if (prm[i].scheme != FSEI_AB2_CN && prm[i].scheme != FSEI_RK3_CN)
             return fail(FSEI_E_ARG, "box %zu: unknown scheme %d", i, prm[i].scheme);
+        if (check_rheology(prm[i], "fsei_batch_step") != FSEI_OK) {
+            const std::string msg = g_err;
+            return fail(prm[i].rheology == FSEI_CARREAU_YASUDA && prm[i].scheme != FSEI_AB2_CN
+                            ? FSEI_E_UNSUPPORTED : FSEI_E_ARG, "box %zu: %s", i, msg.c_str());
+        }
     }
     DeviceGuard dg(B->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;

@@ -371,6 +371,22 @@ template <typename T> struct RhsCoef {
 // two-point averages at the cell centres and edges, differenced) and RHS =
 // dt [gamma H^n + rho H^{n-1} + Re^-1 L u^n - G p^n + f] (Eq. 3).  On the
 // bottom wall face (wall_face) H_w and RHS_w are 0.
+// the explicit extra term of F (if any) added to H and, with this step's
+// weight dt gamma, to the right-hand side (0 on the bottom wall face)
+template <typename T>
+FSEI_D void add_extra_h(const Fields<T> &F, size_t c0, const RhsCoef<T> &c, T &Hu, T &Hv, T &Hw,
+                        T &ru, T &rv, T &rw) {
+    if (!F.hx) return;
+    const T a = F.hx[c0], b = F.hy[c0], e = c.wall_face ? T(0) : F.hz[c0];
+    const T dg = c.dt * c.gam;
+    Hu += a;
+    Hv += b;
+    Hw += e;
+    ru += dg * a;
+    rv += dg * b;
+    rw += dg * e;
+}
+
 template <typename T>
 FSEI_D void rhs_point(const Stencil<T> &s, const RhsCoef<T> &c, T hu1, T hv1, T hw1, T fx, T fy,
                       T fz, T &Hu, T &Hv, T &Hw, T &ru, T &rv, T &rw) {
@@ -539,6 +555,7 @@ k_rhs_x(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1, T *__res
         const T fz = (F.fz && !cf.wall_face) ? F.fz[c0] : z0;
         T Hu, Hv, Hw, ru, rv, rw;
         rhs_point(s, cf, F.hu[c0], F.hv[c0], F.hw[c0], fx, fy, fz, Hu, Hv, Hw, ru, rv, rw);
+        add_extra_h(F, c0, cf, Hu, Hv, Hw, ru, rv, rw);
         F.hu[c0] = Hu;
         F.hv[c0] = Hv;
         F.hw[c0] = Hw;
@@ -707,6 +724,7 @@ k_rhs_x_tile(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
             const T fz = (F.fz && !cf.wall_face) ? F.fz[c0] : z0;
             T Hu, Hv, Hw, ru, rv, rw;
             rhs_point(s, cf, Hu1[i], Hv1[i], Hw1[i], fx, fy, fz, Hu, Hv, Hw, ru, rv, rw);
+            add_extra_h(F, c0, cf, Hu, Hv, Hw, ru, rv, rw);
             F.hu[c0] = Hu;
             F.hv[c0] = Hv;
             F.hw[c0] = Hw;
@@ -921,6 +939,23 @@ FSEI_D void rhs_row_body(const GridDev &g, const Fields<T> &F, const RowSet<T> &
             }
             Hn[2][e] = Hw;
             R[2][e] = rw;
+        }
+    }
+    // the explicit extra term (the non-Newtonian remainder), if any, joins
+    // H and, weighted dt gamma, the right-hand side
+    if (F.hx) {
+        const T dg = cf.dt * cf.gam;
+        const T *ex[3] = {F.hx, F.hy, cf.wall_face ? nullptr : F.hz};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            if (!ex[m]) continue;
+            T X[CPL];
+            ldrow(X, ex[m] + oc + i0);
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) {
+                Hn[m][e] += X[e];
+                R[m][e] += dg * X[e];
+            }
         }
     }
     // every load above precedes the first store (the row pointers may alias

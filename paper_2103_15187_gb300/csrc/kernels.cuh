@@ -190,6 +190,9 @@ inline void memset_async(void *p, int v, size_t n, cudaStream_t st) {
 template <typename T> struct Fields {
     T *u, *v, *w, *p, *hu, *hv, *hw;
     const T *fx, *fy, *fz;   // may be NULL
+    // an explicit term added to H at the u, v, w points (the non-Newtonian
+    // stress remainder), or NULL
+    const T *hx, *hy, *hz;
 };
 
 // The two z-sweep plans of a grid (centres, faces) and their storage: what
@@ -223,6 +226,9 @@ template <typename T> struct Work {
     double zlen;             // z extent (sum of dz)
     const unsigned char *exact;   // [ny][sk]: 1 for the modes in nzm
     T *adj0, *adj1, *adj2;   // adjoint workspace (allocated on first use)
+    T *nn0, *nn1, *nn2, *nuc;   // non-Newtonian remainder at the u, v, w points
+                                // and the excess viscosity at the centres
+                                // (allocated on first use)
     int ry;                  // rows per block of the x-line solves
     int ry_fft;              // rows per block of the x transforms
     int chunk_y, chunk_z;    // register chunk length of the y / z sweeps
@@ -275,6 +281,8 @@ struct StepArgs {
     double re, dt, cfl, gamma, rho;
     double fconst[3];
     int scheme;      // fsei_scheme
+    int rheology;    // fsei_rheology
+    double cy[4];    // Carreau-Yasuda lambda, n, a, eta_inf
     double alpha;    // fraction of dt_n this fractional step covers
     int substep;     // 0: forms dt_n; > 0: reuses it
 };
@@ -381,6 +389,12 @@ void launch_ib_loads(const GridDev &g, const T *p, const T *u, const T *v, const
                      const int *tris, int nfaces, int nnodes, double probe, double inv_re,
                      double *face_force, double *node_force, int *skipped, cudaStream_t st);
 template <typename T> void preload_ib();
+// the Carreau-Yasuda remainder div(2 Re^-1 (eta - 1) E) of (u, v, w) into
+// W.nn0..2 (k_rheology.cu); cy: lambda, n, a, eta_inf
+template <typename T>
+void launch_non_newtonian(const GridDev &g, const T *u, const T *v, const T *w, Work<T> &W,
+                          double re, const double cy[4], cudaStream_t st);
+template <typename T> void preload_rheology();
 template <typename T> void preload_project();
 template <typename T> void launch_project(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                           StepScalars *sc, cudaStream_t st);

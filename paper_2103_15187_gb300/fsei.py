@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "FSEI_OK", 1: "FSEI_E_ARG", 2: "FSEI_E_SHAPE",
 FSEI_FP64, FSEI_MIXED = 0, 1
 FSEI_Z_PERIODIC, FSEI_Z_WALLS = 0, 1
 FSEI_AB2_CN, FSEI_RK3_CN = 0, 1
+FSEI_NEWTONIAN, FSEI_CARREAU_YASUDA = 0, 1
 FLAG_NONFINITE, FLAG_CFL = 1, 2
 
 # exported symbols and their C signatures (kept in step with include/fsei.h)
@@ -63,10 +64,23 @@ class State(ctypes.Structure):
                 ("hw", ctypes.c_void_p), ("have_prev_h", ctypes.c_int32)]
 
 
+class CarreauYasuda(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_double), ("n", ctypes.c_double), ("a", ctypes.c_double),
+                ("eta_inf", ctypes.c_double)]
+
+
 class StepParams(ctypes.Structure):
     _fields_ = [("re", ctypes.c_double), ("dt", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("rho", ctypes.c_double),
-                ("fconst", ctypes.c_double * 3), ("scheme", ctypes.c_int32)]
+                ("fconst", ctypes.c_double * 3), ("scheme", ctypes.c_int32),
+                ("rheology", ctypes.c_int32), ("cy", CarreauYasuda)]
+
+
+def _rheology(cy):
+    """(rheology flag, CarreauYasuda) of None or a dict lam, n, a, eta_inf."""
+    if cy is None:
+        return FSEI_NEWTONIAN, CarreauYasuda(0.0, 1.0, 1.0, 1.0)
+    return FSEI_CARREAU_YASUDA, CarreauYasuda(cy["lam"], cy["n"], cy["a"], cy["eta_inf"])
 
 
 class StepStats(ctypes.Structure):
@@ -254,17 +268,20 @@ def grid_create(**kw):
 
 
 def step(grid, state, f=None, re=100.0, dt=1e-3, cfl=0.0, gamma=1.5, rho=-0.5,
-         fconst=(0.0, 0.0, 0.0), nsteps=1, stream=None, stats=True, scheme=FSEI_AB2_CN):
+         fconst=(0.0, 0.0, 0.0), nsteps=1, stream=None, stats=True, scheme=FSEI_AB2_CN,
+         rheology=None):
     """fsei_step on a dict of torch tensors u, v, w, p, hu, hv, hw and the
     key have_prev_h (updated in place).  f: None or (fx, fy, fz) tensors.
     scheme: FSEI_AB2_CN (Eq. 3) or FSEI_RK3_CN (three sub-steps per step).
+    rheology: None (Newtonian) or a dict lam, n, a, eta_inf (Carreau-Yasuda).
     Returns the statistics dict of the last step when stats=True (the call
     then synchronises the stream), else None."""
     lib = load()
     st = State(_ptr(state["u"]), _ptr(state["v"]), _ptr(state["w"]), _ptr(state["p"]),
                _ptr(state["hu"]), _ptr(state["hv"]), _ptr(state["hw"]),
                int(state.get("have_prev_h", 0)))
-    prm = StepParams(re, dt, cfl, gamma, rho, (ctypes.c_double * 3)(*fconst), int(scheme))
+    rh, cy = _rheology(rheology)
+    prm = StepParams(re, dt, cfl, gamma, rho, (ctypes.c_double * 3)(*fconst), int(scheme), rh, cy)
     fx, fy, fz = (None, None, None) if f is None else f
     out = StepStats() if stats else None
     status = lib.fsei_step(grid.handle, ctypes.byref(st), _ptr(fx), _ptr(fy), _ptr(fz),
@@ -370,7 +387,7 @@ def batch_step(batch, states, forces, params, nsteps=1, stream=None, stats=True)
         prm[i] = StepParams(p.get("re", 100.0), p.get("dt", 0.0), p.get("cfl", 0.0),
                             p.get("gamma", 1.5), p.get("rho", -0.5),
                             (ctypes.c_double * 3)(*p.get("fconst", (0.0, 0.0, 0.0))),
-                            int(p.get("scheme", FSEI_AB2_CN)))
+                            int(p.get("scheme", FSEI_AB2_CN)), *_rheology(p.get("rheology")))
     out = (StepStats * n)() if stats else None
     status = lib.fsei_batch_step(batch.handle, st, fp, prm, int(nsteps), _stream_handle(stream),
                                  out)
