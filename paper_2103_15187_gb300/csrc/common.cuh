@@ -106,6 +106,10 @@ struct StepScalars {
     // float roundings of dt, beta, gamma, rho, 1/dt and the four factors
     // above, for the single-precision kernels
     float fdt, fbeta, fgamma, frho, finvdt, fax, fcix, fay, fciy;
+    // decay length of the x factor: the least n with |alpha_x|^n <= 2^-32
+    // (single precision) and <= 2^-62 (double); the carry of an x line
+    // across more unknowns than that is below the precision's rounding
+    int ndecx_f, ndecx_d;
 };
 
 // --------------------------------------------- partitioned tridiagonal -----

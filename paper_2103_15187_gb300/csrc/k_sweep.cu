@@ -132,6 +132,16 @@ __device__ void uni_factors(double r, double &alpha, double &cinv) {
     cinv = 1.0 / c;
 }
 
+// least n with alpha^n <= 2^-bits (0 <= alpha < 1), one more for the
+// rounding of the logarithm; a large count where alpha is near 1
+__device__ int decay_length(double alpha, int bits) {
+    const double a = fabs(alpha);
+    if (a == 0.0) return 1;
+    const double l = -log2(a);
+    if (!(l * (1 << 20) > bits)) return 1 << 20;
+    return (int)ceil(bits / l) + 1;
+}
+
 // Three warps, so that the serial double-precision chains (each a division
 // or square root at a time on GB300's narrow FP64 pipe) run side by side:
 // every warp forms dt and beta (alpha dt_n, dt_n from dt or the CFL rule at
@@ -163,6 +173,8 @@ FSEI_D void k_scalars(StepScalars *sc, StepArgs a, int euler, double idx2, doubl
             sc->cix = ci;
             sc->fax = (float)al;
             sc->fcix = (float)ci;
+            sc->ndecx_f = decay_length(al, 32);
+            sc->ndecx_d = decay_length(al, 62);
         }
     } else if (wid == 1) {
         double al, ci;
@@ -963,7 +975,8 @@ FSEI_D void rhs_row_body(const GridDev &g, const Fields<T> &F, const RowSet<T> &
     strow(F.hu + oc + i0, Hn[0]);
     strow(F.hv + oc + i0, Hn[1]);
     strow(F.hw + oc + i0, Hn[2]);
-    line_solve_uni<T, CPL, LPR, 3>(R, fpick<T>(sc->ax, sc->fax), fpick<T>(sc->cix, sc->fcix), xs);
+    line_solve_uni<T, CPL, LPR, 3>(R, fpick<T>(sc->ax, sc->fax), fpick<T>(sc->cix, sc->fcix),
+                                   sizeof(T) == 4 ? sc->ndecx_f : sc->ndecx_d, xs);
     strow(q0 + oc + i0, R[0]);
     strow(q1 + oc + i0, R[1]);
     strow(q2 + oc + i0, R[2]);
@@ -979,7 +992,9 @@ template <typename T, int CPL, int LPR>
 FSEI_D void
 k_rhs_x_row(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
             T *__restrict__ q2, const StepScalars *sc, int rpb, T fc0, T fc1, T fc2, T inv_re) {
-    __shared__ T xs[2 * 3 * (LPR > 128 ? LPR : 128) / 32];
+    // carries of the line solve: 2 x 3 values per thread (lines longer
+    // than a warp; per warp on the exact scan)
+    __shared__ T xs[LPR > 32 ? 2 * 3 * (LPR > 128 ? LPR : 128) : 1];
     pdl_wait();
     pdl_trigger();
     const int nx = g.nx, ny = g.ny, nz = g.nz;

@@ -469,20 +469,77 @@ FSEI_D void line_carries(T (&v)[NV], T g, T *xs) {
     }
 }
 
+// The carries of line_carries where the slope decays fast: with |g|^D
+// below the precision's tolerance (D <= kNearMax), Z_{p+1} (BACK) is
+// sum_{k<D} g^k v_{p+1+k} and X_{p-1} is sum_{k<D} g^k v_{p-1-k} (lane
+// indices mod LPR), the rest of the cyclic series dropped: each dropped
+// term is at most |g|^D max|v|, and |g| <= 2^-4 makes their sum at most
+// (16/15) |g|^D max|v|.  Lines within a warp read their neighbours by
+// shuffles; longer ones through xs (NV values per thread of the block,
+// BACK and forward in separate halves, so one barrier per call).  Every
+// thread of the block calls it.
+constexpr int kNearMax = 8;
+template <typename T, int LPR, int BACK, int NV>
+FSEI_D void line_carries_near(T (&v)[NV], T g, int D, T *xs) {
+    if (LPR <= 32) {
+        constexpr int W = LPR;
+        const int p = threadIdx.x & (W - 1);
+        T acc[NV];
+#pragma unroll
+        for (int m = 0; m < NV; ++m) acc[m] = T(0);
+#pragma unroll
+        for (int k = kNearMax - 1; k >= 0; --k) {
+            if (k >= D) continue;   // uniform over the block
+            const int src = BACK ? ((p + 1 + k) & (W - 1)) : ((p - 1 - k) & (W - 1));
+#pragma unroll
+            for (int m = 0; m < NV; ++m)
+                acc[m] = __shfl_sync(0xffffffffu, v[m], src, W) + g * acc[m];
+        }
+#pragma unroll
+        for (int m = 0; m < NV; ++m) v[m] = acc[m];
+    } else {
+        const int nt = (int)blockDim.x;
+        const int r = (int)threadIdx.x & (LPR - 1), base = (int)threadIdx.x - r;
+        T *buf = xs + (BACK ? 0 : NV * nt);
+#pragma unroll
+        for (int m = 0; m < NV; ++m) buf[m * nt + threadIdx.x] = v[m];
+        __syncthreads();
+        T acc[NV];
+#pragma unroll
+        for (int m = 0; m < NV; ++m) acc[m] = T(0);
+#pragma unroll
+        for (int k = kNearMax - 1; k >= 0; --k) {
+            if (k >= D) continue;
+            const int src = base + (BACK ? ((r + 1 + k) & (LPR - 1)) : ((r - 1 - k) & (LPR - 1)));
+#pragma unroll
+            for (int m = 0; m < NV; ++m) acc[m] = buf[m * nt + src] + g * acc[m];
+        }
+#pragma unroll
+        for (int m = 0; m < NV; ++m) v[m] = acc[m];
+    }
+}
+
 // Solve NV constant-coefficient periodic lines (I - beta L) x = y with the
 // factorised inverse of uni_solve: z_i = y_i + alpha z_{i+1}, x'_i = z_i +
 // alpha x'_{i-1}, x = x' / c, each recurrence evaluated lane by lane from a
 // zero carry and corrected with the carries of line_carries.  d[m][e]:
-// unknown CPL r + e of line m at lane r of the line.  Every thread of the
-// block calls it.
+// unknown CPL r + e of line m at lane r of the line.  ndec: the decay
+// length of alpha (the least n with |alpha|^n below the precision's
+// tolerance); where ndec / CPL lanes are at most kNearMax the carries take
+// line_carries_near (xs: 2 NV values per thread of the block), else the
+// exact scan (xs: 2 NV values per warp).  Every thread of the block calls
+// it.
 template <typename T, int CPL, int LPR, int NV>
-FSEI_D void line_solve_uni(T (&d)[NV][CPL], T alpha, T cinv, T *xs) {
+FSEI_D void line_solve_uni(T (&d)[NV][CPL], T alpha, T cinv, int ndec, T *xs) {
     T g = T(1), a = alpha;
 #pragma unroll
     for (int e = CPL; e > 0; e >>= 1) {    // alpha^CPL by squaring
         if (e & 1) g *= a;
         a *= a;
     }
+    int D = (ndec + CPL - 1) / CPL;
+    if (D < 1) D = 1;
+    const bool near = D <= kNearMax;   // uniform over the grid
     T c[NV];
 #pragma unroll
     for (int m = 0; m < NV; ++m) {
@@ -494,7 +551,8 @@ FSEI_D void line_solve_uni(T (&d)[NV][CPL], T alpha, T cinv, T *xs) {
         }
         c[m] = z;
     }
-    line_carries<T, LPR, 1, NV>(c, g, xs);
+    if (near) line_carries_near<T, LPR, 1, NV>(c, g, D, xs);
+    else line_carries<T, LPR, 1, NV>(c, g, xs);
 #pragma unroll
     for (int m = 0; m < NV; ++m) {
         T pw = c[m];
@@ -511,7 +569,8 @@ FSEI_D void line_solve_uni(T (&d)[NV][CPL], T alpha, T cinv, T *xs) {
         }
         c[m] = x;
     }
-    line_carries<T, LPR, 0, NV>(c, g, xs);
+    if (near) line_carries_near<T, LPR, 0, NV>(c, g, D, xs);
+    else line_carries<T, LPR, 0, NV>(c, g, xs);
 #pragma unroll
     for (int m = 0; m < NV; ++m) {
         T pw = c[m];

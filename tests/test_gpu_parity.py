@@ -132,6 +132,39 @@ def test_strongly_viscous_forced_channel(fsei, prec_name):
         assert vel <= 1e-5, (vel, pu.compare(gpu, ref))
 
 
+@pytest.mark.parametrize("nx", [64, 256])
+@pytest.mark.parametrize("alpha", [0.02, 0.2, 0.45, 0.8])
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+def test_x_line_carries_across_decay_lengths(fsei, nx, alpha, prec_name):
+    """The register x solve sums the carries of the nearest D lanes where
+    |alpha|^(4 D) is below the precision's tolerance (2^-32 single, 2^-62
+    double) and D <= 8, and scans the whole cycle otherwise.  Re is set so
+    that the x factor is alpha (beta/dx^2 = alpha / (1 - alpha)^2): in single
+    precision D = 2, 4, 8 and the full scan, in double D = 3, 7 and the full
+    scan twice; 64-wide rows put a line in 16 lanes of a warp, 256-wide ones
+    across two warps.  Two steps from rest under a random force, against the
+    oracle: 1e-12 per field in FP64, 1e-5 in velocity for mixed precision."""
+    from paper_2103_15187_gb300.inputs import Case
+    ny, nz, lx, dt = 8, 8, 2.0, 1e-2
+    b = alpha / (1.0 - alpha) ** 2
+    re = dt / (2.0 * b * (lx / nx) ** 2)
+    rng = np.random.default_rng(nx + int(100 * alpha))
+    z = np.zeros((nz, ny, nx))
+    f = tuple(rng.standard_normal((nz, ny, nx)) for _ in range(3))
+    f[2][0] = 0.0
+    case = Case("carries", nx, ny, nz, lx, 1.0, Z_WALLS, 2.0, 1.5, re, dt, 0.0, 1,
+                z, z.copy(), z.copy(), z.copy(), f)
+    prec = fsei.FSEI_FP64 if prec_name == "fp64" else fsei.FSEI_MIXED
+    gpu, _ = pu.run_gpu(case, 2, prec)
+    ref, _ = pu.run_oracle(case, 2)
+    if prec_name == "fp64":
+        _assert_fp64(gpu, ref)
+    else:
+        vel = np.sqrt(sum(np.linalg.norm(gpu[k] - ref[k]) ** 2 for k in "uvw")
+                      / sum(np.linalg.norm(ref[k]) ** 2 for k in "uvw"))
+        assert vel <= 1e-5, (vel, pu.compare(gpu, ref))
+
+
 def test_taylor_green_fp64_10_steps(fsei):
     """32^3 triply periodic Taylor-Green, Re 100, dt 1e-3, 10 steps."""
     case = inputs.case_taylor_green(32, steps=10)
