@@ -186,6 +186,11 @@ int64_t fsei_grid_workspace_bytes(fsei_grid grid);
  * whose kernel does not apply to the grid's extents.
  *   rhs_cells_per_lane: RHS + x sweep (Eq. 3, Sec. 3.1), cells of a grid row
  *     per lane of the row-resident kernel (4, or 2 or 8 in FSEI_MIXED);
+ *   rhs_rows_per_strip: 0 for one grid row per lane; 4, 8 or 16 (where ny
+ *     allows) for lanes that march that many consecutive rows of a plane,
+ *     reusing the stencil rows two neighbours share and fetching the next
+ *     row's while computing one (16 or 32 bytes per lane, 16 to 128 lanes
+ *     per row);
  *   poisson_lanes_per_line, poisson_rows_per_lane: z tridiagonal solve of
  *     each Fourier mode of the pressure equation (Sec. 2.1; Sec. 3.1 and
  *     Sec. 4 on its parallel solve): lanes that share a line (reduction
@@ -202,6 +207,7 @@ typedef struct {
     int32_t rfft_rows_per_block;
     int32_t ffty_columns_per_block;
     int32_t project_passes_per_thread;
+    int32_t rhs_rows_per_strip;
 } fsei_schedule;
 
 /* fsei_grid_autotune flag: measure again although this process already

@@ -426,6 +426,7 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
     }
     if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "table allocation failed");
     set_smem_limits_sweep<T>(g, W);
+    set_smem_limits_march<T>(g, W);
     set_smem_limits_lines<T>(g, W);
     set_smem_limits_poisson<T>(g, W);
     set_smem_limits_adjoint<T>(g, W);
@@ -593,7 +594,7 @@ double knob_ms(const KernelTimer &tm, int knob) {
 
 void set_knob(Schedule &s, int knob, const int v[2]) {
     switch (knob) {
-    case SK_RHS: s.rhs_cpl = v[0]; break;
+    case SK_RHS: s.rhs_cpl = v[0]; s.rhs_strip = v[1]; break;
     case SK_ZL: s.zl_lpl = v[0]; s.zl_e = v[1]; break;
     case SK_RFFT: s.ry_rfft = v[0]; break;
     case SK_FFTY: s.tkx_fft = v[0]; break;
@@ -680,6 +681,7 @@ fsei_status tune_grid(fsei_grid_s *G, Work<T> &W, int reps, cudaStream_t st) {
 
 void to_public(const Schedule &s, fsei_schedule *o) {
     o->rhs_cells_per_lane = s.rhs_cpl;
+    o->rhs_rows_per_strip = s.rhs_strip;
     o->poisson_lanes_per_line = s.zl_lpl;
     o->poisson_rows_per_lane = s.zl_e;
     o->rfft_rows_per_block = s.ry_rfft;
@@ -705,7 +707,7 @@ bool schedule_valid(const fsei_grid_s *G, const Schedule &s) {
                                             : schedule_candidates<float>(G->g, knob, cand, 16);
         int v0 = 0, v1 = 0;
         switch (knob) {
-        case SK_RHS: v0 = s.rhs_cpl; break;
+        case SK_RHS: v0 = s.rhs_cpl; v1 = s.rhs_strip; break;
         case SK_ZL: v0 = s.zl_lpl; v1 = s.zl_e; break;
         case SK_RFFT: v0 = s.ry_rfft; break;
         case SK_FFTY: v0 = s.tkx_fft; break;
@@ -714,7 +716,7 @@ bool schedule_valid(const fsei_grid_s *G, const Schedule &s) {
         }
         bool ok = nc == 0 && v0 == 0 && v1 == 0;
         for (int c = 0; c < nc && !ok; ++c)
-            ok = cand[c][0] == v0 && (knob != SK_ZL || cand[c][1] == v1);
+            ok = cand[c][0] == v0 && cand[c][1] == v1;
         if (!ok) return false;
     }
     return true;
@@ -921,6 +923,7 @@ fsei_status fsei_grid_set_schedule(fsei_grid G, const fsei_schedule *in) {
     if (!G || !in) return fail(FSEI_E_ARG, "fsei_grid_set_schedule: NULL argument");
     Schedule s;
     s.rhs_cpl = in->rhs_cells_per_lane;
+    s.rhs_strip = in->rhs_rows_per_strip;
     s.zl_lpl = in->poisson_lanes_per_line;
     s.zl_e = in->poisson_rows_per_lane;
     s.ry_rfft = in->rfft_rows_per_block;

@@ -185,6 +185,11 @@ FSEI_D void cp_async4(void *smem, const void *gmem) {
 // wait for every copy this thread has issued (a barrier must follow before
 // other threads read them)
 FSEI_D void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// close the group of copies issued since the last commit; wait until at
+// most one of this thread's groups is still in flight (the ones before it
+// have landed; visible to this thread without a barrier)
+FSEI_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+FSEI_D void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Copy rows of row_bytes bytes (row r: gsrc + r gstride -> sdst + r sstride)
 // with every thread of the block issuing copies.  16-byte copies when the

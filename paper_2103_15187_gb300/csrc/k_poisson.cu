@@ -1167,15 +1167,22 @@ template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*
     };
     switch (knob) {
     case SK_RHS: {
-        // the default (8 cells per lane in single precision on rows wider
-        // than 256 cells, 4 otherwise) first
+        // (cells per lane, rows per strip): the default (8 cells per lane in
+        // single precision on rows wider than 256 cells, 4 otherwise; one
+        // row per lane) first, then the strips of the marched kernel
         int c[3];
         const int m = rhs_cpl_candidates(g, tsz, c, 3);
         const int def = (tsz == 4 && g.nx > 256) ? 8 : 4;
+        int order[3], no = 0;
         for (int i = 0; i < m; ++i)
-            if (c[i] == def) put(c[i], 0);
+            if (c[i] == def) order[no++] = c[i];
         for (int i = 0; i < m; ++i)
-            if (c[i] != def) put(c[i], 0);
+            if (c[i] != def) order[no++] = c[i];
+        for (int i = 0; i < no; ++i) put(order[i], 0);
+        const int strips[3] = {8, 4, 16};
+        for (int i = 0; i < no; ++i)
+            for (int S : strips)
+                if (rhs_strip_admissible(g, tsz, order[i], S)) put(order[i], S);
         break;
     }
     case SK_ZL: {
@@ -1227,8 +1234,10 @@ template <typename T> Schedule schedule_of(const GridDev &g, const Work<T> &W) {
     Schedule s;
     memset(&s, 0, sizeof s);
     int c[1][2];
-    if (schedule_candidates<T>(g, SK_RHS, c, 1))
+    if (schedule_candidates<T>(g, SK_RHS, c, 1)) {
         s.rhs_cpl = W.rhs_cpl ? W.rhs_cpl : c[0][0];
+        s.rhs_strip = W.rhs_strip;
+    }
     s.zl_lpl = W.zl_lpl;
     s.zl_e = W.zl_e;
     s.ry_rfft = W.ry_rfft;
@@ -1239,6 +1248,7 @@ template <typename T> Schedule schedule_of(const GridDev &g, const Work<T> &W) {
 
 template <typename T> void apply_schedule(Work<T> &W, const Schedule &s) {
     W.rhs_cpl = s.rhs_cpl;
+    W.rhs_strip = s.rhs_strip;
     W.zl_lpl = s.zl_lpl;
     W.zl_e = s.zl_e;
     if (s.ry_rfft) W.ry_rfft = s.ry_rfft;

@@ -241,6 +241,8 @@ template <typename T> struct Work {
                              // rows per lane (0: not used)
     int rhs_cpl;             // cells per lane of the row-resident RHS (2, 4
                              // or 8; 0: by row width)
+    int rhs_strip;           // rows per strip of the RHS marched along y
+                             // (0: one row per lane, k_rhs_x_row)
     int proj_mult;           // row passes per thread of the projection (0: 4)
     int ry_rfft;             // rows per block of the forward x transform
     int tkx_fft;             // kx columns per block of the two-pass y
@@ -256,6 +258,7 @@ template <typename T> struct Work {
 // kernel does not apply to the grid.
 struct Schedule {
     int rhs_cpl;    // RHS + x sweep: cells per lane of the row-resident kernel
+    int rhs_strip;  // and rows per strip when marched along y (0: not)
     int zl_lpl;     // z Poisson: lanes per mode line (the reduction across
                     // lanes); zl_e: rows per lane (the elimination in a lane)
     int zl_e;
@@ -265,7 +268,8 @@ struct Schedule {
 };
 enum ScheduleKnob { SK_RHS, SK_ZL, SK_RFFT, SK_FFTY, SK_PROJ, SK_COUNT };
 // the values knob k may take on this grid (pairs (lanes, rows) for SK_ZL,
-// single values in out[i][0] otherwise), the default first; their count
+// (cells per lane, rows per strip) for SK_RHS, single values in out[i][0]
+// otherwise), the default first; their count
 template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*out)[2], int cap);
 template <typename T> Schedule schedule_of(const GridDev &g, const Work<T> &W);
 template <typename T> void apply_schedule(Work<T> &W, const Schedule &s);
@@ -338,6 +342,11 @@ inline void join_side(const Overlap &o, cudaStream_t st) {
 }
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st);
+// the marched RHS (k_rhs_march.cu) with W.rhs_cpl and W.rhs_strip; false
+// (nothing launched) where that layout does not apply
+template <typename T>
+bool launch_rhs_x_march(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
+                        const StepArgs &a, cudaStream_t st);
 template <typename T> void launch_sweep_y(const GridDev &g, Work<T> &W, const StepScalars *sc,
                                           cudaStream_t st);
 template <typename T> void launch_sweep_z(const GridDev &g, const Fields<T> &F, Work<T> &W,
@@ -406,6 +415,7 @@ template <typename T> size_t smem_fft_x(const GridDev &g, const Work<T> &W);
 template <typename T> size_t smem_fft_y(const GridDev &g, const Work<T> &W);
 template <typename T> size_t smem_poisson(const GridDev &g, const Work<T> &W);
 template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T> &W);
+template <typename T> void set_smem_limits_march(const GridDev &g, const Work<T> &W);
 template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T> &W);
 // chunk length, chunks per line and x columns per block of the register
 // sweeps for lines of n unknowns
@@ -426,5 +436,13 @@ int zl_candidates(const GridDev &g, int elem_size, int (*out)[2], int cap);
 // cells per lane of the row-resident RHS that apply to this grid (at most
 // cap); their count
 int rhs_cpl_candidates(const GridDev &g, int elem_size, int *out, int cap);
+// row layout of the row-resident RHS: cpl cells per lane (prefer, or by
+// row width), lpr lanes per row, rpb rows per block; false where it does not
+// apply
+template <typename T>
+bool rhs_row_geometry(const GridDev &g, int &cpl, int &lpr, int &rpb, int prefer = 0);
+// whether the marched RHS takes strips of S rows with cpl cells per lane
+// (0: by row width) on this grid
+bool rhs_strip_admissible(const GridDev &g, int elem_size, int cpl, int S);
 
 }  // namespace fsei

@@ -98,7 +98,8 @@ class Schedule(ctypes.Structure):
                 ("poisson_rows_per_lane", ctypes.c_int32),
                 ("rfft_rows_per_block", ctypes.c_int32),
                 ("ffty_columns_per_block", ctypes.c_int32),
-                ("project_passes_per_thread", ctypes.c_int32)]
+                ("project_passes_per_thread", ctypes.c_int32),
+                ("rhs_rows_per_strip", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -269,17 +269,23 @@ def case_heart_scale(nx=512, ny=512, nz=768, steps=50, seed=3):
 
 
 def case_periodic_random(n=32, seed=0, re=1000.0, cfl=0.5, steps=100,
-                         ke_target=0.25):
+                         ke_target=0.25, ny=None, nz=None):
     """Triply periodic 2 pi box with a solenoidal random field (|k| in [1, 8])
-    scaled to the Taylor-Green kinetic energy (mean |u|^2 = ke_target)."""
+    scaled to the Taylor-Green kinetic energy (mean |u|^2 = ke_target).  With
+    ny or nz given the box is n x ny x nz cells of the same spacing 2 pi / n
+    (lengths 2 pi ny / n, 2 pi nz / n)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    zf = z_faces(n, Z_PERIODIC, 2 * np.pi)
-    u, v, w = solenoidal_field(rng, n, n, n, 2 * np.pi, 2 * np.pi, zf,
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    ly, lz = 2 * np.pi * ny / n, 2 * np.pi * nz / n
+    zf = z_faces(nz, Z_PERIODIC, lz)
+    u, v, w = solenoidal_field(rng, n, ny, nz, 2 * np.pi, ly, zf,
                                Z_PERIODIC, 1.0, 8.0, 0.0, rms=1.0)
     s = np.sqrt(ke_target / np.mean(u * u + v * v + w * w))
-    return Case("periodic_random_%d" % n, n, n, n, 2 * np.pi, 2 * np.pi,
-                Z_PERIODIC, 2 * np.pi, 0.0, re, 0.0, cfl, steps, u * s, v * s,
-                w * s, np.zeros_like(u))
+    name = ("periodic_random_%d" % n if ny == n and nz == n
+            else "periodic_random_%dx%dx%d" % (n, ny, nz))
+    return Case(name, n, ny, nz, 2 * np.pi, ly, Z_PERIODIC, lz, 0.0, re, 0.0,
+                cfl, steps, u * s, v * s, w * s, np.zeros_like(u))
 
 
 ENSEMBLE_SIZES = ((32, 32, 32), (64, 64, 64), (96, 96, 128), (128, 128, 192))

@@ -23,6 +23,7 @@ MIXED_VEL_TOL = 1e-5
 # values tried per field: the admissible ones and some that never are
 TRIALS = {
     "rhs_cells_per_lane": [4, 8, 2, 5, 16],
+    "rhs_march": [(4, 4), (4, 8), (8, 4), (2, 4), (4, 3)],
     "poisson": [(16, 16), (32, 8), (16, 8), (8, 32), (64, 4)],
     "rfft_rows_per_block": [1, 2, 4, 8, 16, 3, 32],
     "ffty_columns_per_block": [2, 4, 8, 16, 32, 3, 64],
@@ -62,6 +63,8 @@ def _check(fsei, prec, gpu, ref):
 def _variants(key, value):
     if key == "poisson":
         return {"poisson_lanes_per_line": value[0], "poisson_rows_per_lane": value[1]}
+    if key == "rhs_march":
+        return {"rhs_cells_per_lane": value[0], "rhs_rows_per_strip": value[1]}
     return {key: value}
 
 
@@ -88,11 +91,15 @@ def test_every_admissible_schedule_at_parity(fsei, channel, prec_name, key):
         _check(fsei, prec, gpu, ref)
     # the values that are never admissible stayed out; the fields with
     # choices on this grid offered at least two
-    never = {"rhs_cells_per_lane": [5, 16], "poisson": [(16, 8), (8, 32), (64, 4)],
+    # (strips of 8 need ny = 64 with 8 rows per block; 8 cells per lane leave
+    # 8 lanes per row; 2 floats are 8 bytes per lane)
+    never = {"rhs_cells_per_lane": [5, 16], "rhs_march": [(4, 8), (8, 4), (2, 4), (4, 3)],
+             "poisson": [(16, 8), (8, 32), (64, 4)],
              "rfft_rows_per_block": [3, 32], "ffty_columns_per_block": [3, 64],
              "project_passes_per_thread": [3, 16]}[key]
     assert not set(admitted) & set(never), admitted
-    multi = {"rhs_cells_per_lane": prec_name == "mixed", "poisson": prec_name == "mixed",
+    multi = {"rhs_cells_per_lane": prec_name == "mixed", "rhs_march": False,
+             "poisson": prec_name == "mixed",
              "rfft_rows_per_block": True, "ffty_columns_per_block": True,
              "project_passes_per_thread": True}[key]
     assert len(admitted) >= (2 if multi else 1), admitted
