@@ -69,12 +69,22 @@ def step_words_model(with_force):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
-# of the dominant kernel, from an ncu --set full capture of the 256^3
-# channel workload; reported only for that workload and that kernel build
+# of a kernel, from an ncu --set full capture of the 256^3 channel workload,
+# keyed by the kernel's name as ncu prints it; reported only for that
+# workload and only while the kernel is the one the schedule launches
 MEASURED_TRAFFIC = {
-    "rhs_x (RHS + x sweep)": {"bytes": 826.5e6, "cells": 256 ** 3,
-                              "kernel": "k_rhs_x_row<float, 4, 64>"},
+    "k_rhs_x_march<float, 8, 32>": {"bytes": 845.5e6, "cells": 256 ** 3},
 }
+
+
+def rhs_kernel_name(sched, nx, elem):
+    """The RHS + x sweep kernel a single-grid schedule launches (the
+    row-resident or the y-marched one; cells and lanes per row)."""
+    cpl = sched.get("rhs_cells_per_lane", 0)
+    if not cpl:
+        return None
+    kind = "k_rhs_x_march" if sched.get("rhs_rows_per_strip", 0) else "k_rhs_x_row"
+    return "%s<%s, %d, %d>" % (kind, elem, cpl, nx // cpl)
 
 # FP64 instructions of one FP64 step per cell (DFMA + DADD + DMUL thread
 # instructions, the CFL pre-pass excluded), from one ncu capture of the FP64
@@ -82,7 +92,7 @@ MEASURED_TRAFFIC = {
 # The FP64 step is bound by the FP64 pipe; its peak is measured in the run
 # (fsei_fp64_fma_rate: DFMA thread instructions per second with every SM
 # busy), and each of DFMA, DADD and DMUL takes one slot of that pipe.
-FP64_INSTR_PER_CELL = 342.6
+FP64_INSTR_PER_CELL = 329.8
 
 
 def measured_peaks():
@@ -488,6 +498,23 @@ def run_heart_scale(args, peak):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     stats = fsei.step(grid, st, f, nsteps=0, **prm)
+    # per-kernel device time over 3 more steps (event pairs on the stream)
+    fsei.set_kernel_timing(grid, True)
+    fsei.step(grid, st, f, nsteps=3, stats=False, **prm)
+    kt = fsei.kernel_times(grid)
+    fsei.set_kernel_timing(grid, False)
+    kwords = algorithmic_words(case.nx, case.ny, case.nz, True)
+    table = {}
+    for name, (tot_ms, n) in kt.items():
+        if n == 0:
+            continue
+        entry = {"avg_ms": round(tot_ms / n, 5), "launches": n}
+        if name in kwords:
+            b = kwords[name] * 4 * case.cells
+            entry["alg_bytes"] = b
+            entry["gbs"] = round(b / (tot_ms / n * 1e-3) / 1e9, 1)
+            entry["frac"] = round(entry["gbs"] / peak, 4)
+        table[name] = entry
     words = step_words_model(True)
     mcups = case.cells * args.heart_steps / (ms * 1e-3) / 1e6
     gbs = words * 4 * mcups * 1e6 / 1e9
@@ -495,6 +522,7 @@ def run_heart_scale(args, peak):
             "steps": args.heart_steps, "ms_per_step": round(ms / args.heart_steps, 4),
             "precision": "mixed", "step_hbm_frac": round(gbs / peak, 4),
             "alg_words_per_cell": round(words, 3), "max_div": stats["max_div"],
+            "schedule": grid.schedule, "kernels": table,
             "workload": "512x512x768, Lx=Ly=2*96/156, tanh walls 2.0, Re 3000, CFL 0.5, "
                         "k^-5/3 field (|k|<=32, unit RMS) + 20 Gaussian force blobs"}
 
@@ -617,15 +645,18 @@ def roofline_of(res, nx, ny, nz, bytes_per_word, peak_gbs, peak_kind):
         if name in words and (best is None or tot_ms > res["kernels"][best][0]):
             best = name
     e = table[best]
-    tr = MEASURED_TRAFFIC.get(best)
-    traffic = tr["bytes"] if (tr and tr["cells"] == nx * ny * nz and bytes_per_word == 4) else None
+    kname = None
+    if best == "rhs_x (RHS + x sweep)" and res.get("schedule"):
+        kname = rhs_kernel_name(res["schedule"], nx, "float" if bytes_per_word == 4 else "double")
+    tr = MEASURED_TRAFFIC.get(kname)
+    traffic = tr["bytes"] if (tr and tr["cells"] == nx * ny * nz) else None
     roof = {"bound": "hbm", "kernel": best, "achieved": round(e["gbs"], 1),
             "peak": peak_gbs, "unit": "GB/s", "frac": round(e["frac"], 4),
             "traffic": traffic, "alg_bytes": e["alg_bytes"],
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else peak_kind}
-    if traffic is not None:
-        roof["traffic_kernel"] = tr["kernel"]
+    if kname:
+        roof["kernel_launched"] = kname
     step_words = sum(words.values())
     return roof, table, step_words
 

@@ -351,7 +351,8 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
         s.at = M.get<T>(n); s.ct = M.get<T>(n);
         s.rlo = M.get<T>(m); s.rinv = M.get<T>(m); s.rcp = M.get<T>(m);
         s.rz = M.get<T>(m); s.rsc = M.get<T>(2);
-        s.pk1 = M.get<T>(5 * m); s.pk2 = M.get<T>(5 * m); s.pdinv = M.get<T>(m);
+        s.pk1 = M.get<T>(kPcrLevels * m); s.pk2 = M.get<T>(kPcrLevels * m);
+        s.pdinv = M.get<T>(m);
         TriPlan<T> &p = W.plan[q];
         p.n = n;
         p.P = Ps[q];
@@ -362,7 +363,7 @@ fsei_status setup_work(fsei_grid_s *G, Work<T> &W, const std::vector<double> &la
         p.rlo = s.rlo; p.rinv = s.rinv; p.rcp = s.rcp; p.rz = s.rz; p.rsc = s.rsc;
         p.pk1 = s.pk1; p.pk2 = s.pk2; p.pdinv = s.pdinv;
         p.levels = 0;
-        if (m <= 32 && (m & (m - 1)) == 0)
+        if (m <= 128 && (m & (m - 1)) == 0)
             while ((1 << p.levels) < m) ++p.levels;
     }
     if (M.err != cudaSuccess) return fail(FSEI_E_NOMEM, "plan allocation failed");

@@ -131,12 +131,16 @@ template <typename T> struct TriPlan {
     const T *rlo, *rinv, *rcp, *rz; // reduced system (2P): couplings and LU
     const T *rsc;            // [0] = a_0/g (cyclic), [1] = 1/(1+v.z)
     // Parallel cyclic reduction of the reduced system (when 2P is a power of
-    // two <= 32): level l combines equation i with i -/+ 2^l through the
+    // two <= 128): level l combines equation i with i -/+ 2^l through the
     // multipliers pk1, pk2 [l * 2P + i]; pdinv are the final reciprocal
     // diagonals.  levels = 0 selects the Thomas path above.
     int levels;
     const T *pk1, *pk2, *pdinv;
 };
+
+// Levels of parallel cyclic reduction a plan stores multipliers for (2P <=
+// 2^kPcrLevels).
+constexpr int kPcrLevels = 7;
 
 // Raw (mutable) storage of one plan inside the workspace.
 template <typename T> struct TriPlanStore {

@@ -145,9 +145,11 @@ FSEI_D void dft_reg(cplx<T> (&x)[B], const cplx<T> *tw, int N) {
     }
 }
 
-// Split N = N1 N2 of the two-pass transforms below (N1 >= N2, both powers of
-// two <= 16: the register arrays stay small), 0 for lengths that take the
-// Stockham passes of fft_lines.
+// Split N = N1 N2 of the two-pass transforms (N1 >= N2, powers of two, N1
+// <= 32 and N2 <= 16: the register arrays stay small), 0 for lengths that
+// take the Stockham passes of fft_lines.  Length 512 (32 x 16) is split for
+// the y transform only (k_fft_y_2p); the shared-memory two-pass of
+// fft_lines_fast stops at 256.
 FSEI_HD int fft_split_n1(int n) {
     switch (n) {
     case 16: return 4;
@@ -155,6 +157,7 @@ FSEI_HD int fft_split_n1(int n) {
     case 64: return 8;
     case 128: return 16;
     case 256: return 16;
+    case 512: return 32;
     default: return 0;
     }
 }

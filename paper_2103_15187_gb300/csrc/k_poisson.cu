@@ -1003,6 +1003,7 @@ bool fft_y_2p_launch(const GridDev &g, Work<T> &W, cudaStream_t st) {
     case 64: FSEI_FY(8, 8); return true;
     case 128: FSEI_FY(16, 8); return true;
     case 256: FSEI_FY(16, 16); return true;
+    case 512: FSEI_FY(32, 16); return true;
 #undef FSEI_FY
     default: return false;
     }
@@ -1138,6 +1139,8 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     raise_smem_limit(K_fft_y_2p<T, -1, 16, 8>.solo());
     raise_smem_limit(K_fft_y_2p<T, 1, 16, 16>.solo());
     raise_smem_limit(K_fft_y_2p<T, -1, 16, 16>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 32, 16>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 32, 16>.solo());
     raise_smem_limit(K_poisson_z<T>.solo());
     raise_smem_limit(K_poisson_exact<T>.solo());
     raise_smem_limit(K_poisson_exact_f<T>.solo());
@@ -1170,10 +1173,10 @@ template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*
         // (cells per lane, rows per strip): the default (8 cells per lane in
         // single precision on rows wider than 256 cells, 4 otherwise; one
         // row per lane) first, then the strips of the marched kernel
-        int c[3];
-        const int m = rhs_cpl_candidates(g, tsz, c, 3);
+        int c[5];
+        const int m = rhs_cpl_candidates(g, tsz, c, 5);
         const int def = (tsz == 4 && g.nx > 256) ? 8 : 4;
-        int order[3], no = 0;
+        int order[5], no = 0;
         for (int i = 0; i < m; ++i)
             if (c[i] == def) order[no++] = c[i];
         for (int i = 0; i < m; ++i)

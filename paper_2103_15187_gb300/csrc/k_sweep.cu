@@ -886,13 +886,21 @@ void rhs_tile_ry(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepSca
 template <typename T>
 bool rhs_row_geometry(const GridDev &g, int &cpl, int &lpr, int &rpb, int prefer) {
     // 4 cells per lane (2 doubles or 4 floats: fewer registers, more warps);
-    // floats on rows wider than 256 cells take 8; `prefer` (4, or 2 or 8 in
-    // single precision, from the grid's autotuner) overrides
+    // floats on rows wider than 256 cells take 8; rows of 3 x 2^m cells
+    // take 24-byte lanes (6 floats, 3 doubles); `prefer` (4 or the 24-byte
+    // count, or 2 or 8 in single precision, from the grid's autotuner)
+    // overrides
+    auto fits = [&](int c) {
+        const int l = g.nx % c ? 0 : g.nx / c;
+        return l >= 4 && l <= 256 && (l & (l - 1)) == 0;
+    };
+    const int c24 = sizeof(T) == 4 ? 6 : 3;
     cpl = (sizeof(T) == 4 && g.nx > 256) ? 8 : 4;
-    if (prefer == 4 || ((prefer == 8 || prefer == 2) && sizeof(T) == 4)) cpl = prefer;
-    if (g.nx % cpl) return false;
+    if (!fits(cpl) && fits(c24)) cpl = c24;
+    if (prefer == 4 || prefer == c24 || ((prefer == 8 || prefer == 2) && sizeof(T) == 4))
+        cpl = prefer;
+    if (!fits(cpl) || (cpl == c24 && (g.nx / cpl < 8 || g.nx / cpl > 128))) return false;
     lpr = g.nx / cpl;
-    if (lpr < 4 || lpr > 256 || (lpr & (lpr - 1))) return false;
     const int bmax = lpr > 128 ? lpr : 128;
     for (rpb = bmax / lpr; rpb >= 1; rpb /= 2)
         if (g.ny % rpb == 0 && rpb * lpr >= 32) return true;
@@ -922,6 +930,21 @@ bool rhs_row_dispatch(const GridDev &g, const Fields<T> &F, Work<T> &W, const St
     }
 }
 
+// 24-byte lanes (rows of 3 x 2^m cells): 8 to 128 lanes per row
+template <typename T>
+bool rhs_row_dispatch24(const GridDev &g, const Fields<T> &F, Work<T> &W, const StepScalars *sc,
+                        const StepArgs &a, int lpr, int rpb, cudaStream_t st) {
+    constexpr int C = sizeof(T) == 4 ? 6 : 3;
+    switch (lpr) {
+    case 8: rhs_row_launch<T, C, 8>(g, F, W, sc, a, rpb, st); return true;
+    case 16: rhs_row_launch<T, C, 16>(g, F, W, sc, a, rpb, st); return true;
+    case 32: rhs_row_launch<T, C, 32>(g, F, W, sc, a, rpb, st); return true;
+    case 64: rhs_row_launch<T, C, 64>(g, F, W, sc, a, rpb, st); return true;
+    case 128: rhs_row_launch<T, C, 128>(g, F, W, sc, a, rpb, st); return true;
+    default: return false;
+    }
+}
+
 template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Work<T> &W,
                                         const StepScalars *sc, const StepArgs &a, cudaStream_t st) {
     if (W.rhs_strip > 0 && launch_rhs_x_march<T>(g, F, W, sc, a, st)) return;
@@ -929,7 +952,8 @@ template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Wo
     if (rhs_row_geometry<T>(g, cpl, lpr, rpb, W.rhs_cpl) &&
         (cpl == 4   ? rhs_row_dispatch<T, 4>(g, F, W, sc, a, lpr, rpb, st)
          : cpl == 8 ? rhs_row_dispatch<T, sizeof(T) == 4 ? 8 : 4>(g, F, W, sc, a, lpr, rpb, st)
-                    : rhs_row_dispatch<T, sizeof(T) == 4 ? 2 : 4>(g, F, W, sc, a, lpr, rpb, st)))
+         : cpl == 2 ? rhs_row_dispatch<T, sizeof(T) == 4 ? 2 : 4>(g, F, W, sc, a, lpr, rpb, st)
+                    : rhs_row_dispatch24<T>(g, F, W, sc, a, lpr, rpb, st)))
         return;
     int RY = 0, P = 0;
     size_t smem = 0;
@@ -946,7 +970,7 @@ template <typename T> void launch_rhs_x(const GridDev &g, const Fields<T> &F, Wo
 
 int rhs_cpl_candidates(const GridDev &g, int elem_size, int *out, int cap) {
     int n = 0;
-    const int opts[3] = {4, 8, 2};
+    const int opts[5] = {4, 8, 2, 6, 3};
     for (int c : opts) {
         int cpl = 0, lpr = 0, rpb = 0;
         const bool ok = elem_size == 4 ? rhs_row_geometry<float>(g, cpl, lpr, rpb, c)
@@ -1001,6 +1025,12 @@ template <typename T> void set_smem_limits_sweep(const GridDev &g, const Work<T>
     cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 64>.solo());
     cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 128>.solo());
     cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C2, 256>.solo());
+    constexpr int C24 = sizeof(T) == 4 ? 6 : 3;
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C24, 8>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C24, 16>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C24, 32>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C24, 64>.solo());
+    cudaFuncGetAttributes(&fa, K_rhs_x_row<T, C24, 128>.solo());
 }
 
 #define FSEI_INST(T)                                                                           \

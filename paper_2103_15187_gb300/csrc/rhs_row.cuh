@@ -52,16 +52,21 @@ FSEI_D RhsCoef<T> rhs_coef(const GridDev &g, const StepScalars *sc, int k, T fc0
 }
 
 // Helpers of the row-resident right-hand side (k_rhs_x_row below): CPL
-// consecutive values of a row as 16-byte vectors (one 8-byte vector when the
-// lane holds 8 bytes), from and to global memory (neighbour rows are served
-// by the caches).
+// consecutive values of a row as 16-byte vectors where the lane holds a
+// multiple of 16 bytes, as 8-byte vectors otherwise (8 or 24 bytes), from and
+// to global memory (neighbour rows are served by the caches).
 template <typename T> struct alignas(8) Vec8 { T v[8 / sizeof(T)]; };
 template <typename T, int CPL>
 FSEI_D void ldrow(T (&a)[CPL], const T *p) {
-    if constexpr (CPL * sizeof(T) == 8) {
-        const Vec8<T> v = *reinterpret_cast<const Vec8<T> *>(p);
+    static_assert((CPL * sizeof(T)) % 8 == 0, "8-byte multiple per lane");
+    if constexpr ((CPL * sizeof(T)) % 16 != 0) {
+        constexpr int VW = 8 / (int)sizeof(T);
 #pragma unroll
-        for (int e = 0; e < CPL; ++e) a[e] = v.v[e];
+        for (int c = 0; c < CPL / VW; ++c) {
+            const Vec8<T> v = *reinterpret_cast<const Vec8<T> *>(p + c * VW);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) a[c * VW + e] = v.v[e];
+        }
     } else {
         constexpr int VW = 16 / (int)sizeof(T);
 #pragma unroll
@@ -74,11 +79,15 @@ FSEI_D void ldrow(T (&a)[CPL], const T *p) {
 }
 template <typename T, int CPL>
 FSEI_D void strow(T *p, const T (&a)[CPL]) {
-    if constexpr (CPL * sizeof(T) == 8) {
-        Vec8<T> v;
+    if constexpr ((CPL * sizeof(T)) % 16 != 0) {
+        constexpr int VW = 8 / (int)sizeof(T);
 #pragma unroll
-        for (int e = 0; e < CPL; ++e) v.v[e] = a[e];
-        *reinterpret_cast<Vec8<T> *>(p) = v;
+        for (int c = 0; c < CPL / VW; ++c) {
+            Vec8<T> v;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) v.v[e] = a[c * VW + e];
+            *reinterpret_cast<Vec8<T> *>(p + c * VW) = v;
+        }
     } else {
         constexpr int VW = 16 / (int)sizeof(T);
 #pragma unroll

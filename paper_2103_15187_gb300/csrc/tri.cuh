@@ -38,15 +38,68 @@ template <typename T> FSEI_D T addv(T a, T b) { return a + b; }
 template <typename T> FSEI_D cplx<T> addv(cplx<T> a, cplx<T> b) { return a + b; }
 
 // Shared-memory words needed by stage_plan for a plan of n unknowns and P
-// chunks (factors, reduced LU, PCR multipliers of up to 5 levels).
-FSEI_HD int plan_stage_words(int n, int P) { return 5 * n + 8 * P + 2 + 22 * P; }
+// chunks (factors, reduced LU, PCR multipliers of up to kPcrLevels levels).
+FSEI_HD int plan_stage_words(int n, int P) {
+    return 5 * n + 8 * P + 2 + 2 * kPcrLevels * 2 * P + 2 * P;
+}
 
 // Reduced system of one line solved by one warp with parallel cyclic
-// reduction (lane i holds unknown i; 2P <= 32, a power of two).  Every lane
-// of the warp must call it.
+// reduction: m = 2P unknowns, a power of two <= 128; lane l holds unknowns
+// l + 32 q (q < NQ = m / 32), or unknown l alone when m <= 32.  Level s =
+// 2^lev adds pk1 times unknown i - s and pk2 times unknown i + s (indices
+// mod m) to unknown i; a shift s = 32 q' + s' reads lane l -/+ s' of the
+// same or the neighbouring register slot.  Every lane of the warp must call
+// it.
+template <typename T, int NQ>
+__device__ __forceinline__ void pcr_warp_slots(T *r, const TriPlan<T> &pl, int lane) {
+    constexpr int m = 32 * NQ;
+    T x[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) x[q] = r[lane + 32 * q];
+    // v[(q + d) mod NQ] without indexing registers at run time
+    auto pick = [](const T (&v)[NQ], int q) {
+        q &= NQ - 1;
+        T o = v[0];
+#pragma unroll
+        for (int u = 1; u < NQ; ++u) o = q == u ? v[u] : o;
+        return o;
+    };
+    for (int lev = 0; lev < pl.levels; ++lev) {
+        const int s = 1 << lev, sq = s >> 5, sl = s & 31;
+        T tm[NQ], tp[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            tm[q] = __shfl_sync(0xffffffffu, x[q], (lane - sl) & 31);
+            tp[q] = __shfl_sync(0xffffffffu, x[q], (lane + sl) & 31);
+        }
+        // unknown i = lane + 32 q: i - s sits in slot q - sq of lane lane -
+        // sl, one slot lower where that lane wraps below 0; i + s likewise
+        const int dm = lane >= sl ? -sq : -sq - 1, dp = lane + sl < 32 ? sq : sq + 1;
+        T nx[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int i = lane + 32 * q;
+            nx[q] = x[q] + pl.pk1[lev * m + i] * pick(tm, q + dm) +
+                    pl.pk2[lev * m + i] * pick(tp, q + dp);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) x[q] = nx[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) r[lane + 32 * q] = x[q] * pl.pdinv[lane + 32 * q];
+}
+
 template <typename T>
 __device__ __forceinline__ void pcr_warp_solve(T *r, const TriPlan<T> &pl, int lane) {
     const int m = 2 * pl.P;
+    if (m == 64) {
+        pcr_warp_slots<T, 2>(r, pl, lane);
+        return;
+    }
+    if (m == 128) {
+        pcr_warp_slots<T, 4>(r, pl, lane);
+        return;
+    }
     T x = lane < m ? r[lane] : T(0);
     for (int lev = 0; lev < pl.levels; ++lev) {
         const int s = 1 << lev;
@@ -97,7 +150,7 @@ __device__ TriPlan<T> stage_plan(const TriPlan<T> &in, T *sm) {
     TriPlan<T> out = in;
     T *a = sm, *c = a + n, *inv = c + n, *at = inv + n, *ct = at + n;
     T *rlo = ct + n, *rinv = rlo + m, *rcp = rinv + m, *rz = rcp + m, *rsc = rz + m;
-    T *pk1 = rsc + 2, *pk2 = pk1 + 5 * m, *pdinv = pk2 + 5 * m;
+    T *pk1 = rsc + 2, *pk2 = pk1 + kPcrLevels * m, *pdinv = pk2 + kPcrLevels * m;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         a[i] = in.a[i];
         c[i] = in.c[i];

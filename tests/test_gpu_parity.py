@@ -165,6 +165,33 @@ def test_x_line_carries_across_decay_lengths(fsei, nx, alpha, prec_name):
         assert vel <= 1e-5, (vel, pu.compare(gpu, ref))
 
 
+@pytest.mark.parametrize("nx,ny,nz,walls", [(96, 24, 16, True), (48, 16, 12, False),
+                                             (192, 12, 10, True), (384, 8, 8, True)])
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+def test_rows_of_three_times_power_of_two(fsei, nx, ny, nz, walls, prec_name):
+    """Rows of 3 x 2^m cells take 24-byte lanes in the row-resident RHS + x
+    sweep (6 floats or 3 doubles per lane, nx / 6 or nx / 3 lanes, lines
+    across up to four warps); body forces on the wall-bounded cases.  Three
+    steps against the oracle: 1e-12 per field in FP64, 1e-5 in velocity for
+    mixed precision; the schedule names the lane width."""
+    if walls:
+        case = inputs.case_channel(nx, ny, nz, steps=3, kmax=4.0, rms=0.3, seed=nx + nz,
+                                   re=500.0, blobs=dict(nblobs=2, sigma=2.0, amp=3.0))
+    else:
+        case = inputs.case_periodic_random(nx, seed=nx, steps=3, re=400.0, ny=ny, nz=nz)
+    prec = fsei.FSEI_FP64 if prec_name == "fp64" else fsei.FSEI_MIXED
+    grid = pu.gpu_grid(case, prec)
+    assert grid.schedule["rhs_cells_per_lane"] == (3 if prec_name == "fp64" else 6)
+    gpu, _ = pu.run_gpu(case, 3, prec, grid=grid)
+    ref, _ = pu.run_oracle(case, 3)
+    if prec_name == "fp64":
+        _assert_fp64(gpu, ref)
+    else:
+        vel = np.sqrt(sum(np.linalg.norm(gpu[k] - ref[k]) ** 2 for k in "uvw")
+                      / sum(np.linalg.norm(ref[k]) ** 2 for k in "uvw"))
+        assert vel <= 1e-5, (vel, pu.compare(gpu, ref))
+
+
 def test_taylor_green_fp64_10_steps(fsei):
     """32^3 triply periodic Taylor-Green, Re 100, dt 1e-3, 10 steps."""
     case = inputs.case_taylor_green(32, steps=10)

@@ -22,7 +22,7 @@ MIXED_VEL_TOL = 1e-5
 
 # values tried per field: the admissible ones and some that never are
 TRIALS = {
-    "rhs_cells_per_lane": [4, 8, 2, 5, 16],
+    "rhs_cells_per_lane": [4, 8, 2, 5, 16, 6, 3],
     "rhs_march": [(4, 4), (4, 8), (8, 4), (2, 4), (4, 3)],
     "poisson": [(16, 16), (32, 8), (16, 8), (8, 32), (64, 4)],
     "rfft_rows_per_block": [1, 2, 4, 8, 16, 3, 32],
@@ -93,7 +93,7 @@ def test_every_admissible_schedule_at_parity(fsei, channel, prec_name, key):
     # choices on this grid offered at least two
     # (strips of 8 need ny = 64 with 8 rows per block; 8 cells per lane leave
     # 8 lanes per row; 2 floats are 8 bytes per lane)
-    never = {"rhs_cells_per_lane": [5, 16], "rhs_march": [(4, 8), (8, 4), (2, 4), (4, 3)],
+    never = {"rhs_cells_per_lane": [5, 16, 6, 3], "rhs_march": [(4, 8), (8, 4), (2, 4), (4, 3)],
              "poisson": [(16, 8), (8, 32), (64, 4)],
              "rfft_rows_per_block": [3, 32], "ffty_columns_per_block": [3, 64],
              "project_passes_per_thread": [3, 16]}[key]
