@@ -280,38 +280,36 @@ def run_gpu_arm(args, rank, world):
         err = (num / den) ** 0.5
         log("mixed vs fp64 velocity rel L2 after %d steps: %.3e" % (args.error_steps, err))
 
-    # end to end through the public API with host buffers: per step the
-    # state goes host -> device, one step runs, the new state comes back
+    # end to end through the public API with host buffers: per step
+    # fsei_step_host copies the state (7 fields) from pinned host memory into
+    # device buffers, runs one step and copies the new state back (the
+    # history fields under the rest of the step); step_host_join orders the
+    # stream after the last copies back before the closing event
     mixed_res, mgrid, _ = results["mixed"]
     e2e = None
     if args.e2e_steps > 0:
-        host = {k: torch.empty((case.nz, case.ny, case.nx), dtype=torch.float32).pin_memory()
-                for k in FIELDS}
-        dst = device_state(case, torch.float32)
-        for k in FIELDS:
-            host[k].copy_(dst[k].cpu())
+        init = device_state(case, torch.float32)
+        host = {k: init[k].cpu().pin_memory() for k in FIELDS}
+        host["have_prev_h"] = 0
+        dst = {k: torch.empty_like(init[k]) for k in FIELDS}
+        del init
         stream = torch.cuda.current_stream()
-
-        def e2e_step(have):
-            for k in FIELDS:
-                dst[k].copy_(host[k], non_blocking=True)
-            dst["have_prev_h"] = have
-            fsei.step(mgrid, dst, None, nsteps=1, stats=False, **prm)
-            for k in FIELDS:
-                host[k].copy_(dst[k], non_blocking=True)
-
-        for w in range(2):      # untimed: first copies and launches
-            e2e_step(w)
+        for _ in range(2):      # untimed: first copies and launches
+            fsei.step_host(mgrid, host, dst, None, nsteps=1, stats=False, **prm)
+        fsei.step_host_join(mgrid)
+        torch.cuda.synchronize()
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.e2e_steps):
-            e2e_step(1)
+            fsei.step_host(mgrid, host, dst, None, nsteps=1, stats=False, **prm)
+        fsei.step_host_join(mgrid)
         e1.record(stream)
         barrier()
         ms = max_over_ranks(e0.elapsed_time(e1))
         nbytes = sum(host[k].numel() * 4 for k in FIELDS)
+        assert host["have_prev_h"] == 1
         e2e = {"value": cells * args.e2e_steps * world / (ms * 1e-3) / 1e6,
                "unit": "Mcell-updates/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}

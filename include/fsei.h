@@ -253,6 +253,38 @@ fsei_status fsei_step(fsei_grid grid, fsei_state *state, const void *fx,
                       const fsei_step_params *params, int32_t nsteps,
                       void *cuda_stream, fsei_step_stats *out);
 
+/* fsei_step on a state held in host memory: the seven fields of `host` are
+ * copied into the device buffers of `dev`, nsteps steps run on them exactly
+ * as fsei_step would run them (the same kernels, the same results), and the
+ * seven fields are copied back into `host`.  host->have_prev_h plays the
+ * role of state->have_prev_h (dev->have_prev_h is ignored).
+ *   host: nx*ny*nz values of the grid's precision per field (pinned memory,
+ *     cudaHostAlloc or cudaHostRegister, for asynchronous copies; pageable
+ *     memory works, with copies that block the calling thread);
+ *   dev: caller-owned device buffers of the same sizes, 16-byte aligned,
+ *     used as the step's state; every field is overwritten by the copy in.
+ * Ordering: the copies in wait for the work queued on cuda_stream before
+ * the call and, field by field, for that field's copy back from the
+ * previous fsei_step_host call on this grid; the steps wait for the copies
+ * in.  The copies back run on the grid's own copy stream: the history
+ * fields H^n as soon as the last step's right-hand side has written them
+ * (under the rest of that step), u, v, w, p after the step; they are not
+ * ordered before work queued on cuda_stream after the call unless out is
+ * given or fsei_step_host_join is called.  Neither `host` nor `dev` may be
+ * touched by other work until then.  out: as in fsei_step (the call then
+ * also waits for the copies back).  Errors as fsei_step; FSEI_E_ARG for
+ * NULL fields or a misaligned device field. */
+fsei_status fsei_step_host(fsei_grid grid, fsei_state *host, const fsei_state *dev,
+                           const void *fx, const void *fy, const void *fz,
+                           const fsei_step_params *params, int32_t nsteps,
+                           void *cuda_stream, fsei_step_stats *out);
+
+/* Order the work queued on cuda_stream after this call behind the copies
+ * back of the last fsei_step_host call on the grid (no-op before the first
+ * such call).  Synchronising cuda_stream afterwards makes the host fields
+ * complete. */
+fsei_status fsei_step_host_join(fsei_grid grid, void *cuda_stream);
+
 /* Pressure-increment Poisson solve of the fractional step (Sec. 2.1: the
  * elliptic equation whose solution makes u^{n+1} solenoidal; Sec. 4: solved
  * with transforms in the two periodic directions): phi with

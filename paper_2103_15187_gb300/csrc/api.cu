@@ -196,6 +196,14 @@ struct fsei_grid_s {
     // side stream and fork/join events: the z-sweep plans run beside the
     // RHS and y sweep
     Overlap ov_plans{};
+    // fsei_step_host: copy streams and events, created at its first call
+    struct HostLink {
+        cudaStream_t h2d = nullptr, d2h = nullptr;
+        cudaEvent_t back[7] = {};   // field f's copy to the host has landed
+        bool back_valid = false;    // a previous call recorded back[]
+        cudaEvent_t entry = nullptr, in = nullptr, rhs = nullptr, step = nullptr, out = nullptr;
+        bool out_valid = false;     // out was recorded by a call
+    } host;
 };
 
 namespace {
@@ -210,6 +218,31 @@ fsei_status create_overlap(fsei_grid_s *G) {
         if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
             return fail(FSEI_E_CUDA, "event creation failed");
     return FSEI_OK;
+}
+
+fsei_status create_host_link(fsei_grid_s *G) {
+    auto &H = G->host;
+    if (H.h2d) return FSEI_OK;
+    if (cudaStreamCreateWithFlags(&H.h2d, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&H.d2h, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(FSEI_E_CUDA, "copy stream creation failed");
+    cudaEvent_t *evs[12] = {&H.entry, &H.in, &H.rhs, &H.step, &H.out};
+    for (int f = 0; f < 7; ++f) evs[5 + f] = &H.back[f];
+    for (cudaEvent_t *e : evs)
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
+            return fail(FSEI_E_CUDA, "event creation failed");
+    return FSEI_OK;
+}
+
+void destroy_host_link(fsei_grid_s *G) {
+    auto &H = G->host;
+    cudaEvent_t evs[12] = {H.entry, H.in, H.rhs, H.step, H.out};
+    for (int f = 0; f < 7; ++f) evs[5 + f] = H.back[f];
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (H.h2d) cudaStreamDestroy(H.h2d);
+    if (H.d2h) cudaStreamDestroy(H.d2h);
+    H = fsei_grid_s::HostLink{};
 }
 
 void destroy_overlap(fsei_grid_s *G) {
@@ -468,7 +501,7 @@ StepArgs step_args(const fsei_step_params &p) {
 template <typename T>
 fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx, const void *fy,
                       const void *fz, const StepArgs &a, int nsteps, cudaStream_t st,
-                      bool with_speed = true) {
+                      bool with_speed = true, cudaEvent_t after_rhs = nullptr) {
     Fields<T> F;
     F.u = (T *)s->u; F.v = (T *)s->v; F.w = (T *)s->w; F.p = (T *)s->p;
     F.hu = (T *)s->hu; F.hv = (T *)s->hv; F.hw = (T *)s->hw;
@@ -526,6 +559,8 @@ fsei_status run_steps(fsei_grid_s *G, Work<T> &W, fsei_state *s, const void *fx,
                 launch_non_newtonian<T>(g, F.u, F.v, F.w, W, a.re, a.cy, st);
             });
         tm.run(KK_RHS_X, st, [&] { launch_rhs_x<T>(g, F, W, G->sc, b, st); });
+        // H^n is final once the last (sub)step's RHS has run
+        if (after_rhs && n == nsteps * subs - 1) cudaEventRecord(after_rhs, st);
         tm.run(KK_SWEEP_Y, st, [&] { launch_sweep_y<T>(g, W, G->sc, st); });
         join_side(op, st);
         tm.run(KK_SWEEP_Z, st, [&] { launch_sweep_z<T>(g, F, W, st); });
@@ -885,6 +920,7 @@ void fsei_grid_destroy(fsei_grid G) {
     DeviceGuard dg(G->device);
     cudaDeviceSynchronize();
     destroy_overlap(G);
+    destroy_host_link(G);
     if (G->sc_host) cudaFreeHost(G->sc_host);
     G->mem.release();
     delete G;
@@ -936,18 +972,13 @@ fsei_status fsei_grid_set_schedule(fsei_grid G, const fsei_schedule *in) {
     return FSEI_OK;
 }
 
-fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy, const void *fz,
-                      const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,
-                      fsei_step_stats *out) {
-    g_err.clear();
-    cudaGetLastError();   // an error left by an unrelated earlier call is not ours
-    if (!G || !s || !prm) return fail(FSEI_E_ARG, "fsei_step: NULL argument");
-    if (nsteps < 0) return fail(FSEI_E_ARG, "nsteps < 0");
-    const void *req[7] = {s->u, s->v, s->w, s->p, s->hu, s->hv, s->hw};
-    for (int i = 0; i < 7; ++i) {
-        if (!req[i]) return fail(FSEI_E_ARG, "state field %d is NULL", i);
-        if (!aligned16(req[i])) return fail(FSEI_E_ARG, "state field %d not 16-byte aligned", i);
-    }
+namespace {
+
+// the checks fsei_step and fsei_step_host share: force alignment and the
+// step parameters
+fsei_status check_step_call(const void *fx, const void *fy, const void *fz,
+                            const fsei_step_params *prm, int32_t nsteps, const char *who) {
+    if (nsteps < 0) return fail(FSEI_E_ARG, "%s: nsteps < 0", who);
     const void *fo[3] = {fx, fy, fz};
     for (int i = 0; i < 3; ++i)
         if (fo[i] && !aligned16(fo[i])) return fail(FSEI_E_ARG, "force %d not 16-byte aligned", i);
@@ -955,8 +986,43 @@ fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy
     if (!(prm->cfl > 0) && !(prm->dt > 0)) return fail(FSEI_E_ARG, "need dt > 0 or cfl > 0");
     if (prm->scheme != FSEI_AB2_CN && prm->scheme != FSEI_RK3_CN)
         return fail(FSEI_E_ARG, "unknown scheme %d", prm->scheme);
+    return check_rheology(*prm, who);
+}
+
+// synchronise st and fill the statistics of the last step; the status
+// reports the device flags (non-finite first, then CFL)
+fsei_status step_stats(fsei_grid_s *G, cudaStream_t st, fsei_step_stats *out, const char *who) {
+    cudaMemcpyAsync(G->sc_host, G->sc, sizeof(StepScalars), cudaMemcpyDeviceToHost, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(FSEI_E_CUDA, "%s: %s", who, cudaGetErrorString(e));
+    const StepScalars &h = *G->sc_host;
+    out->dt_used = h.dt_step;
+    const double spd = __builtin_bit_cast(double, h.speed_next);
+    out->cfl = h.dt_step * spd;
+    out->max_div = __builtin_bit_cast(double, h.maxdiv);
+    out->kinetic_energy = h.ke;
+    out->flags = h.flags;
+    if (out->cfl > 1.0) out->flags |= FSEI_FLAG_CFL;
+    if (out->flags & FSEI_FLAG_NONFINITE) return fail(FSEI_E_NONFINITE, "non-finite value in the new state");
+    if (out->flags & FSEI_FLAG_CFL) return fail(FSEI_E_CFL, "CFL number %g above 1", out->cfl);
+    return FSEI_OK;
+}
+
+}  // namespace
+
+fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy, const void *fz,
+                      const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,
+                      fsei_step_stats *out) {
+    g_err.clear();
+    cudaGetLastError();   // an error left by an unrelated earlier call is not ours
+    if (!G || !s || !prm) return fail(FSEI_E_ARG, "fsei_step: NULL argument");
+    const void *req[7] = {s->u, s->v, s->w, s->p, s->hu, s->hv, s->hw};
+    for (int i = 0; i < 7; ++i) {
+        if (!req[i]) return fail(FSEI_E_ARG, "state field %d is NULL", i);
+        if (!aligned16(req[i])) return fail(FSEI_E_ARG, "state field %d not 16-byte aligned", i);
+    }
     {
-        const fsei_status rs = check_rheology(*prm, "fsei_step");
+        const fsei_status rs = check_step_call(fx, fy, fz, prm, nsteps, "fsei_step");
         if (rs != FSEI_OK) return rs;
     }
     const StepArgs a = step_args(*prm);
@@ -969,21 +1035,86 @@ fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy
         if (r != FSEI_OK) return r;
         s->have_prev_h = 1;
     }
-    if (out) {
-        cudaMemcpyAsync(G->sc_host, G->sc, sizeof(StepScalars), cudaMemcpyDeviceToHost, st);
-        const cudaError_t e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return fail(FSEI_E_CUDA, "fsei_step: %s", cudaGetErrorString(e));
-        const StepScalars &h = *G->sc_host;
-        out->dt_used = h.dt_step;
-        const double spd = __builtin_bit_cast(double, h.speed_next);
-        out->cfl = h.dt_step * spd;
-        out->max_div = __builtin_bit_cast(double, h.maxdiv);
-        out->kinetic_energy = h.ke;
-        out->flags = h.flags;
-        if (out->cfl > 1.0) out->flags |= FSEI_FLAG_CFL;
-        if (out->flags & FSEI_FLAG_NONFINITE) return fail(FSEI_E_NONFINITE, "non-finite value in the new state");
-        if (out->flags & FSEI_FLAG_CFL) return fail(FSEI_E_CFL, "CFL number %g above 1", out->cfl);
+    return out ? step_stats(G, st, out, "fsei_step") : FSEI_OK;
+}
+
+fsei_status fsei_step_host(fsei_grid G, fsei_state *host, const fsei_state *dev, const void *fx,
+                           const void *fy, const void *fz, const fsei_step_params *prm,
+                           int32_t nsteps, void *cuda_stream, fsei_step_stats *out) {
+    g_err.clear();
+    cudaGetLastError();
+    if (!G || !host || !dev || !prm) return fail(FSEI_E_ARG, "fsei_step_host: NULL argument");
+    void *hf[7] = {host->u, host->v, host->w, host->p, host->hu, host->hv, host->hw};
+    void *df[7] = {dev->u, dev->v, dev->w, dev->p, dev->hu, dev->hv, dev->hw};
+    for (int i = 0; i < 7; ++i) {
+        if (!hf[i]) return fail(FSEI_E_ARG, "host field %d is NULL", i);
+        if (!df[i]) return fail(FSEI_E_ARG, "device field %d is NULL", i);
+        if (!aligned16(df[i])) return fail(FSEI_E_ARG, "device field %d not 16-byte aligned", i);
     }
+    {
+        const fsei_status rs = check_step_call(fx, fy, fz, prm, nsteps, "fsei_step_host");
+        if (rs != FSEI_OK) return rs;
+    }
+    const StepArgs a = step_args(*prm);
+    DeviceGuard dg(G->device);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    {
+        const fsei_status rs = create_host_link(G);
+        if (rs != FSEI_OK) return rs;
+    }
+    auto &H = G->host;
+    const size_t bytes = (size_t)G->g.nx * G->g.ny * G->g.nz * (G->prec == FSEI_FP64 ? 8 : 4);
+    // in: after the work queued on st so far (the device buffers are free),
+    // the history fields first (their copies back from the previous call
+    // land first), each field after its own copy back
+    cudaEventRecord(H.entry, st);
+    cudaStreamWaitEvent(H.h2d, H.entry, 0);
+    const int in_order[7] = {4, 5, 6, 0, 1, 2, 3};
+    for (int f : in_order) {
+        if (H.back_valid) cudaStreamWaitEvent(H.h2d, H.back[f], 0);
+        cudaMemcpyAsync(df[f], hf[f], bytes, cudaMemcpyHostToDevice, H.h2d);
+    }
+    cudaEventRecord(H.in, H.h2d);
+    cudaStreamWaitEvent(st, H.in, 0);
+    fsei_state ds = *dev;
+    ds.have_prev_h = host->have_prev_h;
+    if (nsteps > 0) {
+        const fsei_status r =
+            G->prec == FSEI_FP64
+                ? run_steps<double>(G, G->wd, &ds, fx, fy, fz, a, nsteps, st, true, H.rhs)
+                : run_steps<float>(G, G->wf, &ds, fx, fy, fz, a, nsteps, st, true, H.rhs);
+        if (r != FSEI_OK) return r;
+        host->have_prev_h = 1;
+    }
+    cudaEventRecord(H.step, st);
+    // out: H^n once the last right-hand side has written it (under the rest
+    // of the step), then u, v, w, p after the step
+    cudaStreamWaitEvent(H.d2h, nsteps > 0 ? H.rhs : H.step, 0);
+    for (int f = 4; f < 7; ++f) {
+        cudaMemcpyAsync(hf[f], df[f], bytes, cudaMemcpyDeviceToHost, H.d2h);
+        cudaEventRecord(H.back[f], H.d2h);
+    }
+    cudaStreamWaitEvent(H.d2h, H.step, 0);
+    for (int f = 0; f < 4; ++f) {
+        cudaMemcpyAsync(hf[f], df[f], bytes, cudaMemcpyDeviceToHost, H.d2h);
+        cudaEventRecord(H.back[f], H.d2h);
+    }
+    H.back_valid = true;
+    cudaEventRecord(H.out, H.d2h);
+    H.out_valid = true;
+    if (out) cudaStreamWaitEvent(st, H.out, 0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FSEI_E_CUDA, "fsei_step_host: %s", cudaGetErrorString(e));
+    return out ? step_stats(G, st, out, "fsei_step_host") : FSEI_OK;
+}
+
+fsei_status fsei_step_host_join(fsei_grid G, void *cuda_stream) {
+    g_err.clear();
+    if (!G) return fail(FSEI_E_ARG, "fsei_step_host_join: NULL grid");
+    DeviceGuard dg(G->device);
+    if (G->host.out_valid) cudaStreamWaitEvent((cudaStream_t)cuda_stream, G->host.out, 0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FSEI_E_CUDA, "fsei_step_host_join: %s", cudaGetErrorString(e));
     return FSEI_OK;
 }
 

@@ -26,7 +26,7 @@ FLAG_NONFINITE, FLAG_CFL = 1, 2
 
 # exported symbols and their C signatures (kept in step with include/fsei.h)
 EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
-           "fsei_step", "fsei_poisson_solve", "fsei_adjoint_step", "fsei_batch_create",
+           "fsei_step", "fsei_step_host", "fsei_step_host_join", "fsei_poisson_solve", "fsei_adjoint_step", "fsei_batch_create",
            "fsei_batch_destroy", "fsei_batch_size", "fsei_batch_step", "fsei_set_kernel_timing",
            "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version",
            "fsei_grid_autotune", "fsei_grid_get_schedule", "fsei_grid_set_schedule",
@@ -130,6 +130,12 @@ def load(path=LIB_PATH):
                               ctypes.POINTER(StepParams), ctypes.c_int32, vp,
                               ctypes.POINTER(StepStats)]
     lib.fsei_step.restype = ctypes.c_int
+    lib.fsei_step_host.argtypes = [vp, ctypes.POINTER(State), ctypes.POINTER(State), vp, vp, vp,
+                                   ctypes.POINTER(StepParams), ctypes.c_int32, vp,
+                                   ctypes.POINTER(StepStats)]
+    lib.fsei_step_host.restype = ctypes.c_int
+    lib.fsei_step_host_join.argtypes = [vp, vp]
+    lib.fsei_step_host_join.restype = ctypes.c_int
     lib.fsei_poisson_solve.argtypes = [vp, vp, vp, vp]
     lib.fsei_poisson_solve.restype = ctypes.c_int
     lib.fsei_adjoint_step.argtypes = [vp, ctypes.POINTER(State), ctypes.POINTER(StepParams),
@@ -292,6 +298,42 @@ def step(grid, state, f=None, re=100.0, dt=1e-3, cfl=0.0, gamma=1.5, rho=-0.5,
     res = out.as_dict() if out is not None else None
     _check(status, res)
     return res
+
+
+def step_host(grid, host, dev, f=None, re=100.0, dt=1e-3, cfl=0.0, gamma=1.5, rho=-0.5,
+              fconst=(0.0, 0.0, 0.0), nsteps=1, stream=None, stats=True, scheme=FSEI_AB2_CN,
+              rheology=None):
+    """fsei_step_host: host is a dict of CPU tensors u, v, w, p, hu, hv, hw
+    (pinned for asynchronous copies) and the key have_prev_h (updated in
+    place); dev a dict of device tensors of the same shapes, the staging
+    state.  With stats=True the call waits for the copies back and returns
+    the statistics dict; else the copies back finish on the grid's copy
+    stream (step_host_join orders a stream after them)."""
+    lib = load()
+
+    def st_of(d, have):
+        return State(_ptr(d["u"]), _ptr(d["v"]), _ptr(d["w"]), _ptr(d["p"]),
+                     _ptr(d["hu"]), _ptr(d["hv"]), _ptr(d["hw"]), have)
+    hs = st_of(host, int(host.get("have_prev_h", 0)))
+    ds = st_of(dev, 0)
+    rh, cy = _rheology(rheology)
+    prm = StepParams(re, dt, cfl, gamma, rho, (ctypes.c_double * 3)(*fconst), int(scheme), rh, cy)
+    fx, fy, fz = (None, None, None) if f is None else f
+    out = StepStats() if stats else None
+    status = lib.fsei_step_host(grid.handle, ctypes.byref(hs), ctypes.byref(ds), _ptr(fx),
+                                _ptr(fy), _ptr(fz), ctypes.byref(prm), int(nsteps),
+                                _stream_handle(stream),
+                                ctypes.byref(out) if out is not None else None)
+    host["have_prev_h"] = hs.have_prev_h
+    res = out.as_dict() if out is not None else None
+    _check(status, res)
+    return res
+
+
+def step_host_join(grid, stream=None):
+    """fsei_step_host_join: order the stream after the last step_host call's
+    copies back."""
+    _check(load().fsei_step_host_join(grid.handle, _stream_handle(stream)))
 
 
 def poisson_solve(grid, rhs, phi, stream=None):

@@ -63,6 +63,9 @@ def test_bad_arguments_rejected(lib):
     prm = fsei.StepParams(100.0, 1e-3, 0.0, 1.5, -0.5, (ctypes.c_double * 3)())
     assert lib.fsei_step(None, None, None, None, None, ctypes.byref(prm), 1, None, None) == 1
     assert lib.fsei_poisson_solve(None, None, None, None) == 1
+    assert lib.fsei_step_host(None, None, None, None, None, None, ctypes.byref(prm), 1, None,
+                              None) == 1
+    assert lib.fsei_step_host_join(None, None) == 1
     lib.fsei_grid_destroy(None)
 
 
