@@ -199,7 +199,10 @@ int64_t fsei_grid_workspace_bytes(fsei_grid grid);
  *   rfft_rows_per_block: forward x transform, grid rows per thread block;
  *   ffty_columns_per_block: y transforms, kx columns per thread block;
  *   project_passes_per_thread: projection and pressure update (Eq. 3),
- *     row passes per thread. */
+ *     row passes per thread;
+ *   zsweep_columns_per_lane: z sweep (Sec. 3.1), x columns each lane
+ *     solves (1, or 2 with one chunk's factors read once for both, where
+ *     the z lines split into chunks of at most 16 rows). */
 typedef struct {
     int32_t rhs_cells_per_lane;
     int32_t poisson_lanes_per_line;
@@ -208,6 +211,7 @@ typedef struct {
     int32_t ffty_columns_per_block;
     int32_t project_passes_per_thread;
     int32_t rhs_rows_per_strip;
+    int32_t zsweep_columns_per_lane;
 } fsei_schedule;
 
 /* fsei_grid_autotune flag: measure again although this process already
@@ -399,8 +403,18 @@ fsei_status fsei_batch_set_max_group(fsei_batch batch, int32_t max_boxes);
 /* Launch groups of the last captured graph (0 before the first capture). */
 int32_t fsei_batch_launch_groups(fsei_batch batch);
 /* fsei_grid_autotune for every box (one measurement per distinct shape;
- * flags as there).  Drops the captured graphs, which the next
- * fsei_batch_step captures again with the new schedules. */
+ * flags as there), then, for each description shared by two or more boxes,
+ * a second pass timed as that group's launches: knob by knob, every
+ * admissible value applied to all of the group's boxes, one step of the
+ * group captured into a graph on stand-in fields (7 per box, allocated and
+ * freed by the call; the pass is skipped for a group whose stand-ins do not
+ * fit) and replayed seven times; the value of least median time is kept (a
+ * challenger must be 0.5 % faster) and remembered for the shape as
+ * fsei_grid_autotune remembers its choice; a group of the same shape and
+ * box count is measured once per process unless flags has
+ * FSEI_TUNE_FORCE.  Synchronises the device.
+ * Drops the captured graphs, which the next fsei_batch_step captures again
+ * with the new schedules. */
 fsei_status fsei_batch_autotune(fsei_batch batch, int32_t flags, void *cuda_stream);
 fsei_status fsei_batch_step(fsei_batch batch, fsei_state *states,
                             const void *const *forces,

@@ -624,6 +624,7 @@ double knob_ms(const KernelTimer &tm, int knob) {
     case SK_RFFT: return tm.ms[KK_RFFT_X];
     case SK_FFTY: return tm.ms[KK_FFT_Y] + tm.ms[KK_IFFT_Y];
     case SK_PROJ: return tm.ms[KK_PROJECT];
+    case SK_ZSW: return tm.ms[KK_SWEEP_Z];
     default: return 0.0;
     }
 }
@@ -635,6 +636,7 @@ void set_knob(Schedule &s, int knob, const int v[2]) {
     case SK_RFFT: s.ry_rfft = v[0]; break;
     case SK_FFTY: s.tkx_fft = v[0]; break;
     case SK_PROJ: s.proj_mult = v[0]; break;
+    case SK_ZSW: s.zsw_cols = v[0]; break;
     default: break;
     }
 }
@@ -718,6 +720,7 @@ fsei_status tune_grid(fsei_grid_s *G, Work<T> &W, int reps, cudaStream_t st) {
 void to_public(const Schedule &s, fsei_schedule *o) {
     o->rhs_cells_per_lane = s.rhs_cpl;
     o->rhs_rows_per_strip = s.rhs_strip;
+    o->zsweep_columns_per_lane = s.zsw_cols;
     o->poisson_lanes_per_line = s.zl_lpl;
     o->poisson_rows_per_lane = s.zl_e;
     o->rfft_rows_per_block = s.ry_rfft;
@@ -748,6 +751,7 @@ bool schedule_valid(const fsei_grid_s *G, const Schedule &s) {
         case SK_RFFT: v0 = s.ry_rfft; break;
         case SK_FFTY: v0 = s.tkx_fft; break;
         case SK_PROJ: v0 = s.proj_mult; break;
+        case SK_ZSW: v0 = s.zsw_cols; break;
         default: break;
         }
         bool ok = nc == 0 && v0 == 0 && v1 == 0;
@@ -961,6 +965,7 @@ fsei_status fsei_grid_set_schedule(fsei_grid G, const fsei_schedule *in) {
     Schedule s;
     s.rhs_cpl = in->rhs_cells_per_lane;
     s.rhs_strip = in->rhs_rows_per_strip;
+    s.zsw_cols = in->zsweep_columns_per_lane;
     s.zl_lpl = in->poisson_lanes_per_line;
     s.zl_e = in->poisson_rows_per_lane;
     s.ry_rfft = in->rfft_rows_per_block;
@@ -1507,6 +1512,124 @@ fsei_status batch_capture(fsei_batch_s *B, fsei_state *states, const void *const
     return FSEI_OK;
 }
 
+// Refine the schedule of the boxes idx (one shape, two or more boxes) by
+// timing their grouped launches: knob by knob, every candidate applied to
+// all of them, one step of the group captured into a graph on stand-in
+// fields and replayed; the median replay time decides (a challenger must
+// be 0.5 % faster).  A solo grid of a shape tunes each kernel for a launch
+// of that grid alone; in a group every launch covers all boxes, which
+// moves the best tile shapes (more rows per block pay once the blocks of
+// many boxes fill the GPU).  Skipped, not failed, when the stand-in fields
+// do not fit.
+std::mutex g_group_mu;
+std::vector<std::pair<ScheduleKey, size_t>> g_group_tuned;   // (shape, boxes) measured
+
+fsei_status tune_group(fsei_batch_s *B, const std::vector<size_t> &idx, cudaStream_t st,
+                       bool force) {
+    fsei_grid_s *G0 = B->grids[idx[0]];
+    const std::pair<ScheduleKey, size_t> gk(schedule_key(G0), idx.size());
+    {
+        std::lock_guard<std::mutex> lk(g_group_mu);
+        const bool seen = std::find(g_group_tuned.begin(), g_group_tuned.end(), gk) != g_group_tuned.end();
+        if (seen && !force) return FSEI_OK;   // the cached schedule is the group's
+        if (!seen) g_group_tuned.push_back(gk);
+    }
+    const size_t ncell = (size_t)G0->g.nx * G0->g.ny * G0->g.nz;
+    const size_t esz = G0->prec == FSEI_FP64 ? 8 : 4;
+    std::vector<void *> bufs;
+    std::vector<fsei_state> states(idx.size());
+    bool fits = true;
+    for (size_t b = 0; b < idx.size() && fits; ++b) {
+        void *p = nullptr;
+        fits = cudaMalloc(&p, 7 * ncell * esz) == cudaSuccess;
+        if (!fits) break;
+        bufs.push_back(p);
+        cudaMemsetAsync(p, 0x3c, 7 * ncell * esz, st);
+        unsigned char *c = static_cast<unsigned char *>(p);
+        fsei_state &s = states[b];
+        s.u = c; s.v = c + ncell * esz; s.w = c + 2 * ncell * esz; s.p = c + 3 * ncell * esz;
+        s.hu = c + 4 * ncell * esz; s.hv = c + 5 * ncell * esz; s.hw = c + 6 * ncell * esz;
+        s.have_prev_h = 1;
+    }
+    auto release = [&] {
+        cudaStreamSynchronize(st);
+        for (void *p : bufs) cudaFree(p);
+        cudaGetLastError();
+    };
+    if (!fits) {
+        release();
+        return FSEI_OK;
+    }
+    // a view of the shape's boxes on the batch's capture stream and first
+    // branch (it owns nothing: never passed to fsei_batch_destroy)
+    fsei_batch_s sub;
+    sub.device = B->device;
+    for (size_t b : idx) {
+        sub.grids.push_back(B->grids[b]);
+        sub.desc_key.push_back(B->desc_key[b]);
+    }
+    sub.branches.assign(1, B->branches[0]);
+    sub.joins.assign(1, B->joins[0]);
+    sub.capture = B->capture;
+    sub.fork = B->fork;
+    sub.max_group = B->max_group;
+    fsei_step_params tp = {};
+    tp.re = 1000.0; tp.dt = 1e-4; tp.gamma = 1.5; tp.rho = -0.5;
+    std::vector<fsei_step_params> prm(idx.size(), tp);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // median device time of one replayed step of the group with schedule s;
+    // < 0 where the group cannot be captured with it
+    auto trial = [&](const Schedule &sch) -> double {
+        for (fsei_grid_s *G : sub.grids) grid_apply(G, sch);
+        cudaGraphExec_t ge = nullptr;
+        if (batch_capture(&sub, states.data(), nullptr, prm.data(), false, &ge) != FSEI_OK) {
+            g_err.clear();
+            cudaGetLastError();
+            return -1.0;
+        }
+        cudaGraphLaunch(ge, st);
+        float t[7];
+        for (int r = 0; r < 7; ++r) {
+            cudaEventRecord(e0, st);
+            cudaGraphLaunch(ge, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            t[r] = 0.0f;
+            cudaEventElapsedTime(&t[r], e0, e1);
+        }
+        cudaGraphExecDestroy(ge);
+        std::sort(t, t + 7);
+        return cudaGetLastError() == cudaSuccess ? (double)t[3] : -1.0;
+    };
+    Schedule cur = grid_schedule(G0);
+    for (int knob = 0; knob < SK_COUNT; ++knob) {
+        int cand[16][2];
+        const int nc = G0->prec == FSEI_FP64 ? schedule_candidates<double>(G0->g, knob, cand, 16)
+                                             : schedule_candidates<float>(G0->g, knob, cand, 16);
+        if (nc < 2) continue;
+        double best_ms = trial(cur);
+        for (int c = 0; c < nc; ++c) {
+            Schedule s = cur;
+            set_knob(s, knob, cand[c]);
+            if (memcmp(&s, &cur, sizeof s) == 0) continue;
+            const double t = trial(s);
+            if (t > 0.0 && (best_ms <= 0.0 || t < 0.995 * best_ms)) {
+                best_ms = t;
+                cur = s;
+            }
+        }
+    }
+    for (fsei_grid_s *G : sub.grids) grid_apply(G, cur);
+    store_schedule(G0, cur);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    sub.grids.clear();
+    return FSEI_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1596,6 +1719,21 @@ fsei_status fsei_batch_autotune(fsei_batch B, int32_t flags, void *cuda_stream) 
         }
         done.push_back(k);
     }
+    // then each shape with two or more boxes, timed as its grouped launches
+    std::vector<ScheduleKey> keys;
+    for (size_t i = 0; i < B->grids.size(); ++i) {
+        const ScheduleKey k = schedule_key(B->grids[i]);
+        if (std::find(keys.begin(), keys.end(), k) != keys.end()) continue;
+        keys.push_back(k);
+        std::vector<size_t> idx;
+        for (size_t j = i; j < B->grids.size(); ++j)
+            if (schedule_key(B->grids[j]) == k && B->desc_key[j] == B->desc_key[i]) idx.push_back(j);
+        if (idx.size() < 2) continue;
+        const fsei_status r =
+            tune_group(B, idx, (cudaStream_t)cuda_stream, (flags & FSEI_TUNE_FORCE) != 0);
+        if (r != FSEI_OK) return r;
+    }
+    batch_clear_graphs(B);
     return FSEI_OK;
 }
 

@@ -107,56 +107,102 @@ __device__ cplx<T> *fft_lines(cplx<T> *a, cplx<T> *b, int es, int ls, int nl,
     return src;
 }
 
-// In-register DFT of length B (a power of two, B <= 32): iterative radix-2
+// In-register DFT of length B: a power of two (B <= 32), iterative radix-2
 // with bit-reversed input order, every index a compile-time constant once
-// unrolled.  tw: table of w^m = exp(-2 pi i m / N), m < N, for a transform
-// length N that B divides (stage twiddles are tw[k N / (2h)]).
+// unrolled; 3; or 3 M with M a power of two (M DFTs of the residues n mod
+// 3, the twiddles w_B^(r k'), then DFTs of length 3).  tw: table of w^m =
+// exp(-2 pi i m / N), m < N, for a transform length N that B divides (stage
+// twiddles are tw[k N / (2h)], w_3 = tw[N / 3], w_B^j = tw[j N / B]).
 template <int B> struct Log2 { static constexpr int v = 1 + Log2<B / 2>::v; };
 template <> struct Log2<1> { static constexpr int v = 0; };
 
 template <typename T, int B, int SIGN>
 FSEI_D void dft_reg(cplx<T> (&x)[B], const cplx<T> *tw, int N) {
-    constexpr int LB = Log2<B>::v;
+    if constexpr (B == 3) {
+        // y1 = x0 + w x1 + w* x2, y2 = x0 + w* x1 + w x2 (w^2 = w*)
+        cplx<T> w = tw[N / 3];
+        if (SIGN > 0) w = conj(w);
+        const cplx<T> s = x[1] + x[2], d = x[1] - x[2];
+        const cplx<T> m{x[0].re + w.re * s.re, x[0].im + w.re * s.im};
+        const cplx<T> j{-w.im * d.im, w.im * d.re};   // i w.im d
+        x[0] = x[0] + s;
+        x[1] = m + j;
+        x[2] = m - j;
+    } else if constexpr (B % 3 == 0) {
+        constexpr int M = B / 3;
+        cplx<T> y[3][M];
 #pragma unroll
-    for (int i = 0; i < B; ++i) {
-        int r = 0;
+        for (int r = 0; r < 3; ++r) {
 #pragma unroll
-        for (int b = 0; b < LB; ++b) r |= ((i >> b) & 1) << (LB - 1 - b);
-        if (r > i) {
-            const cplx<T> t = x[i];
-            x[i] = x[r];
-            x[r] = t;
+            for (int m = 0; m < M; ++m) y[r][m] = x[3 * m + r];
+            dft_reg<T, M, SIGN>(y[r], tw, N);
         }
-    }
 #pragma unroll
-    for (int h = 1; h < B; h *= 2) {
+        for (int kp = 0; kp < M; ++kp) {
+            cplx<T> z[3];
+            z[0] = y[0][kp];
 #pragma unroll
-        for (int g0 = 0; g0 < B; g0 += 2 * h) {
-#pragma unroll
-            for (int k = 0; k < h; ++k) {
-                cplx<T> w = tw[k * (N / (2 * h))];
+            for (int r = 1; r < 3; ++r) {
+                cplx<T> w = tw[(N / B) * r * kp];
                 if (SIGN > 0) w = conj(w);
-                const cplx<T> a = x[g0 + k];
-                const cplx<T> b = (k == 0) ? x[g0 + k + h] : x[g0 + k + h] * w;
-                x[g0 + k] = a + b;
-                x[g0 + k + h] = a - b;
+                z[r] = kp == 0 ? y[r][kp] : y[r][kp] * w;
+            }
+            dft_reg<T, 3, SIGN>(z, tw, N);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) x[kp + M * q] = z[q];
+        }
+    } else {
+        constexpr int LB = Log2<B>::v;
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            int r = 0;
+#pragma unroll
+            for (int b = 0; b < LB; ++b) r |= ((i >> b) & 1) << (LB - 1 - b);
+            if (r > i) {
+                const cplx<T> t = x[i];
+                x[i] = x[r];
+                x[r] = t;
+            }
+        }
+#pragma unroll
+        for (int h = 1; h < B; h *= 2) {
+#pragma unroll
+            for (int g0 = 0; g0 < B; g0 += 2 * h) {
+#pragma unroll
+                for (int k = 0; k < h; ++k) {
+                    cplx<T> w = tw[k * (N / (2 * h))];
+                    if (SIGN > 0) w = conj(w);
+                    const cplx<T> a = x[g0 + k];
+                    const cplx<T> b = (k == 0) ? x[g0 + k + h] : x[g0 + k + h] * w;
+                    x[g0 + k] = a + b;
+                    x[g0 + k + h] = a - b;
+                }
             }
         }
     }
 }
 
-// Split N = N1 N2 of the two-pass transforms (N1 >= N2, powers of two, N1
-// <= 32 and N2 <= 16: the register arrays stay small), 0 for lengths that
-// take the Stockham passes of fft_lines.  Length 512 (32 x 16) is split for
-// the y transform only (k_fft_y_2p); the shared-memory two-pass of
-// fft_lines_fast stops at 256.
+// Split N = N1 N2 of the two-pass transforms (N1 >= N2; N1 <= 32 and N2 <=
+// 24 so that the register arrays stay small; each a power of two, 3, or 3
+// times a power of two), 0 for lengths that take the Stockham passes of
+// fft_lines.  The shared-memory two-pass of fft_lines_fast (the forward x
+// transform) takes the powers of two up to 256 only: every length it lists
+// is compiled into each kernel that calls it, and more cases there cost
+// those kernels registers; the y transforms (k_fft_y_2p) and the inverse x
+// transform (k_irfft_x_2p, up to 256) are instantiated per split.
 FSEI_HD int fft_split_n1(int n) {
     switch (n) {
+    case 12: return 4;
     case 16: return 4;
+    case 24: return 6;
     case 32: return 8;
+    case 48: return 8;
     case 64: return 8;
+    case 96: return 12;
     case 128: return 16;
+    case 192: return 16;
     case 256: return 16;
+    case 384: return 24;
     case 512: return 32;
     default: return 0;
     }

@@ -27,41 +27,72 @@ namespace {
 // "i == len - 1": the compiler folds an equality chain over an unrolled loop
 // into an array access at a run-time index, which moves d[] to local memory.
 // Chunks hold at least three unknowns.
-template <typename T, int L>
-__device__ __forceinline__ void chunk_forward(T (&d)[L], int len, const TriPlan<T> &pl, int s0,
-                                              T &rF, T &rE) {
-    // interior rows 1 .. len-2 of the chunk (positions s0+1 .. s0+len-2)
-    d[1] = pl.inv[s0 + 1] * d[1];
+template <typename T, int L, int CX>
+__device__ __forceinline__ void chunk_forward(T (&d)[CX][L], int len, const TriPlan<T> &pl,
+                                              int s0, T (&rF)[CX], T (&rE)[CX]) {
+    // interior rows 1 .. len-2 of the chunk (positions s0+1 .. s0+len-2);
+    // the CX columns of the lane share every factor
+    {
+        const T inv = pl.inv[s0 + 1];
+#pragma unroll
+        for (int c = 0; c < CX; ++c) d[c][1] = inv * d[c][1];
+    }
 #pragma unroll
     for (int i = 2; i < L - 1; ++i)
-        if (i < len - 1) d[i] = pl.inv[s0 + i] * (d[i] - pl.a[s0 + i] * d[i - 1]);
+        if (i < len - 1) {
+            const T inv = pl.inv[s0 + i], a = pl.a[s0 + i];
+#pragma unroll
+            for (int c = 0; c < CX; ++c) d[c][i] = inv * (d[c][i] - a * d[c][i - 1]);
+        }
     // upward pass for the right-hand side part of x_{s0+1}; dh starts at 0,
     // so at i = len-2 it takes d[len-2]
-    T dh = T(0), dhe = T(0), last = T(0);
+    T dh[CX], dhe[CX], last[CX];
+#pragma unroll
+    for (int c = 0; c < CX; ++c) dh[c] = dhe[c] = last[c] = T(0);
 #pragma unroll
     for (int i = L - 2; i >= 1; --i) {
-        if (i >= len - 2) dhe = d[i];
-        if (i <= len - 2) dh = d[i] - pl.ct[s0 + i] * dh;
+        const T ct = pl.ct[s0 + i];
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            if (i >= len - 2) dhe[c] = d[c][i];
+            if (i <= len - 2) dh[c] = d[c][i] - ct * dh[c];
+        }
     }
 #pragma unroll
     for (int i = 0; i < L; ++i)
-        if (i <= len - 1) last = d[i];
-    rF = d[0] - pl.c[s0] * dh;
-    rE = last - pl.a[s0 + len - 1] * dhe;
+        if (i <= len - 1) {
+#pragma unroll
+            for (int c = 0; c < CX; ++c) last[c] = d[c][i];
+        }
+    const T c0 = pl.c[s0], ae = pl.a[s0 + len - 1];
+#pragma unroll
+    for (int c = 0; c < CX; ++c) {
+        rF[c] = d[c][0] - c0 * dh[c];
+        rE[c] = last[c] - ae * dhe[c];
+    }
 }
 
-template <typename T, int L>
-__device__ __forceinline__ void chunk_backward(T (&d)[L], int len, const TriPlan<T> &pl, int s0,
-                                               T F, T E) {
-    d[0] = F;
-    T x = E;
+template <typename T, int L, int CX>
+__device__ __forceinline__ void chunk_backward(T (&d)[CX][L], int len, const TriPlan<T> &pl,
+                                               int s0, const T (&F)[CX], const T (&E)[CX]) {
+    T x[CX];
+#pragma unroll
+    for (int c = 0; c < CX; ++c) {
+        d[c][0] = F[c];
+        x[c] = E[c];
+    }
 #pragma unroll
     for (int i = L - 1; i >= 1; --i) {
         if (i >= len - 1) {
-            d[i] = E;    // rows past the chunk are not stored
+#pragma unroll
+            for (int c = 0; c < CX; ++c) d[c][i] = E[c];   // rows past the chunk are not stored
         } else {
-            x = d[i] - pl.at[s0 + i] * F - pl.ct[s0 + i] * x;
-            d[i] = x;
+            const T at = pl.at[s0 + i], ct = pl.ct[s0 + i];
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                x[c] = d[c][i] - at * F[c] - ct * x[c];
+                d[c][i] = x[c];
+            }
         }
     }
 }
@@ -73,13 +104,21 @@ __device__ __forceinline__ void chunk_backward(T (&d)[L], int len, const TriPlan
 // (sweep_geometry); the minimum-blocks hint leaves room for the chunk, and in
 // single precision for the prefetched u^n, in registers.
 // EXACT: every chunk of the line holds L unknowns (n = L P).
-template <typename T, int L, int DIR, int MODE, bool EXACT>
+// CX: x columns per lane (1, or 2 as one 8- or 16-byte vector per row): the
+// chunk's factors, read from shared memory once per row, serve both, and a
+// warp's loads cover 2 tx consecutive columns.
+template <typename T, int CX> struct ColVec;
+template <typename T> struct ColVec<T, 1> { T v[1]; };
+template <typename T> struct alignas(2 * sizeof(T)) ColVec<T, 2> { T v[2]; };
+
+template <typename T, int L, int DIR, int MODE, bool EXACT, int CX>
 __device__ __forceinline__ void sweep_reg_body(const GridDev &g, const Fields<T> &F,
                                                T *__restrict__ q0, T *__restrict__ q1,
                                                T *__restrict__ q2, const TriPlan<T> &pa,
                                                const TriPlan<T> &pb, int tx, T *sm) {
+    using V = ColVec<T, CX>;
     const int nx = g.nx, ny = g.ny;
-    const int nxt = (nx + tx - 1) / tx;
+    const int nxt = (nx + tx * CX - 1) / (tx * CX);
     int b = blockIdx.x;
     const int xt = b % nxt;
     b /= nxt;
@@ -94,16 +133,16 @@ __device__ __forceinline__ void sweep_reg_body(const GridDev &g, const Fields<T>
     const size_t stride = DIR == 1 ? (size_t)nx : (size_t)nx * ny;
     const int t = threadIdx.x;
     const int l = t % tx, p = t / tx;
-    const int x = xt * tx + l;
+    const int x = (xt * tx + l) * CX;   // nx is even, so x < nx covers the pair
     const bool active = p < src.P && x < nx;
     const size_t base = (DIR == 1 ? (size_t)row * ny * nx : (size_t)row * nx) + x +
                         (size_t)src.off * stride;
     int s0 = 0, len = 0;
-    T d[L];
+    T d[CX][L];
     // u^n of the step's z sweep is prefetched with the chunk in single
     // precision (in double it would cost the registers of a second chunk)
     constexpr bool kPrefetch = DIR == 2 && MODE == 0 && sizeof(T) == 4;
-    T un_pre[kPrefetch ? L : 1];
+    V un_pre[kPrefetch ? L : 1];
     // issue the chunk's loads first; staging the plan below overlaps them
     // lastpad: the chunk ends with the plan's padding unknown (0, not stored)
     bool lastpad = false;
@@ -116,60 +155,72 @@ __device__ __forceinline__ void sweep_reg_body(const GridDev &g, const Fields<T>
         lastpad = src.pad && s0 + (EXACT ? L : len) == src.n;
         const T *qp = q + base + (size_t)s0 * stride;
 #pragma unroll
-        for (int i = 0; i < L; ++i)
-            if (keep(i)) d[i] = qp[(size_t)i * stride];
-            else d[i] = T(0);
+        for (int i = 0; i < L; ++i) {
+            V v;
+            if (keep(i)) v = *reinterpret_cast<const V *>(qp + (size_t)i * stride);
+            else for (int c = 0; c < CX; ++c) v.v[c] = T(0);
+#pragma unroll
+            for (int c = 0; c < CX; ++c) d[c][i] = v.v[c];
+        }
         if constexpr (kPrefetch) {
             const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
             const T *up = un + base + (size_t)s0 * stride;
 #pragma unroll
             for (int i = 0; i < L; ++i)
-                if (keep(i)) un_pre[i] = up[(size_t)i * stride];
+                if (keep(i)) un_pre[i] = *reinterpret_cast<const V *>(up + (size_t)i * stride);
         }
     }
-    const TriPlan<T> pl = stage_plan(src, red + (size_t)tx * rs);
+    const TriPlan<T> pl = stage_plan(src, red + (size_t)tx * CX * rs);
     if (active) {
-        T rF, rE;
-        chunk_forward<T, L>(d, EXACT ? L : len, pl, s0, rF, rE);
-        red[l * rs + 2 * p] = rF;
-        red[l * rs + 2 * p + 1] = rE;
+        T rF[CX], rE[CX];
+        chunk_forward<T, L, CX>(d, EXACT ? L : len, pl, s0, rF, rE);
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            red[(l * CX + c) * rs + 2 * p] = rF[c];
+            red[(l * CX + c) * rs + 2 * p + 1] = rE[c];
+        }
     }
     __syncthreads();
-    reduced_lines<T>(red, rs, tx, pl);
+    reduced_lines<T>(red, rs, tx * CX, pl);
     __syncthreads();
     if (active) {
-        chunk_backward<T, L>(d, EXACT ? L : len, pl, s0, red[l * rs + 2 * p],
-                             red[l * rs + 2 * p + 1]);
+        T Fv[CX], Ev[CX];
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            Fv[c] = red[(l * CX + c) * rs + 2 * p];
+            Ev[c] = red[(l * CX + c) * rs + 2 * p + 1];
+        }
+        chunk_backward<T, L, CX>(d, EXACT ? L : len, pl, s0, Fv, Ev);
         T *qp = fresh(q) + base + (size_t)s0 * stride;
-        if (DIR == 1) {
 #pragma unroll
-            for (int i = 0; i < L; ++i)
-                if (keep(i)) qp[(size_t)i * stride] = d[i];
-        } else if (MODE == 0) {
-            if constexpr (kPrefetch) {
+        for (int i = 0; i < L; ++i) {
+            if (!keep(i)) continue;
+            V v;
+            if (DIR == 1) {
 #pragma unroll
-                for (int i = 0; i < L; ++i)
-                    if (keep(i)) qp[(size_t)i * stride] = un_pre[i] + d[i];
-            } else {
-                const T *un = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
-                const T *up = un + base + (size_t)s0 * stride;
-#pragma unroll
-                for (int i = 0; i < L; ++i)
-                    if (keep(i)) qp[(size_t)i * stride] = up[(size_t)i * stride] + d[i];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < L; ++i)
-                if (keep(i)) {
-                    const int k = s0 + i + pl.off;
-                    const T wk = comp < 2 ? Metric<T>::dz(g)[k] : T(1) / Metric<T>::ihc(g)[k];
-                    qp[(size_t)i * stride] = wk * d[i];
+                for (int c = 0; c < CX; ++c) v.v[c] = d[c][i];
+            } else if (MODE == 0) {
+                V un;
+                if constexpr (kPrefetch) {
+                    un = un_pre[i];
+                } else {
+                    const T *unf = comp == 0 ? F.u : (comp == 1 ? F.v : F.w);
+                    un = *reinterpret_cast<const V *>(unf + base + (size_t)(s0 + i) * stride);
                 }
+#pragma unroll
+                for (int c = 0; c < CX; ++c) v.v[c] = un.v[c] + d[c][i];
+            } else {
+                const int k = s0 + i + pl.off;
+                const T wk = comp < 2 ? Metric<T>::dz(g)[k] : T(1) / Metric<T>::ihc(g)[k];
+#pragma unroll
+                for (int c = 0; c < CX; ++c) v.v[c] = wk * d[c][i];
+            }
+            *reinterpret_cast<V *>(qp + (size_t)i * stride) = v;
         }
     }
 }
 
-template <typename T, int L, int DIR, int MODE>
+template <typename T, int L, int DIR, int MODE, int CX>
 FSEI_D void
 k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
             T *__restrict__ q2, TriPlan<T> pa, TriPlan<T> pb, int tx) {
@@ -180,12 +231,12 @@ k_sweep_reg(GridDev g, Fields<T> F, T *__restrict__ q0, T *__restrict__ q1,
     // the component of this block picks its plan; lines of L P unknowns take
     // the guard-free path
     const int outer = DIR == 1 ? g.nz : g.ny;
-    const int comp = (int)blockIdx.x / ((g.nx + tx - 1) / tx) / outer;
+    const int comp = (int)blockIdx.x / ((g.nx + tx * CX - 1) / (tx * CX)) / outer;
     const TriPlan<T> &src = (DIR == 2 && comp == 2) ? pb : pa;
     if (src.n == L * src.P)
-        sweep_reg_body<T, L, DIR, MODE, true>(g, F, q0, q1, q2, pa, pb, tx, sm);
+        sweep_reg_body<T, L, DIR, MODE, true, CX>(g, F, q0, q1, q2, pa, pb, tx, sm);
     else
-        sweep_reg_body<T, L, DIR, MODE, false>(g, F, q0, q1, q2, pa, pb, tx, sm);
+        sweep_reg_body<T, L, DIR, MODE, false, CX>(g, F, q0, q1, q2, pa, pb, tx, sm);
 }
 
 // y sweep of plane k: q = (I - beta L_y)^-1 q for the three components.
@@ -227,26 +278,32 @@ k_sweep_y_uni(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__
 }
 
 // the kernels with their launch bounds
-template <typename T, int L, int DIR, int MODE>
-constexpr Kernel<k_sweep_reg<T, L, DIR, MODE>, (L <= 16 ? 256 : 512),
-                 (L <= 16 ? (sizeof(T) == 4 ? 3 : 2) : 1)>
+// blocks per SM the z sweep is compiled for: room for the chunk (and in
+// single precision the prefetched u^n) of CX columns in registers
+constexpr int sweep_min_blocks(int L, int tsz, int CX) {
+    return L > 16 ? 1 : (CX == 1 ? (tsz == 4 ? 3 : 2) : (tsz == 4 ? 2 : 1));
+}
+template <typename T, int L, int DIR, int MODE, int CX = 1>
+constexpr Kernel<k_sweep_reg<T, L, DIR, MODE, CX>, (L <= 16 ? 256 : 512),
+                 sweep_min_blocks(L, (int)sizeof(T), CX)>
     K_sweep_reg{};
 template <typename T, int L, bool EXACT>
 constexpr Kernel<k_sweep_y_uni<T, L, EXACT>, 256,
                  (L <= 16 ? (sizeof(T) == 4 ? 5 : 2) : (sizeof(T) == 4 ? 2 : 1))>
     K_sweep_y_uni{};
 
-template <typename T, int L, int DIR, int MODE>
+template <typename T, int L, int DIR, int MODE, int CX>
 void launch_reg(const GridDev &g, const Fields<T> &F, Work<T> &W, const TriPlan<T> &pa,
                 const TriPlan<T> &pb, int tx, cudaStream_t st) {
     const int Pmax = pa.P > pb.P ? pa.P : pb.P;
     const int nmax = pa.n > pb.n ? pa.n : pb.n;
     const int threads = ((tx * Pmax + 31) / 32) * 32;
-    const size_t smem = sizeof(T) * ((size_t)tx * (2 * Pmax + 1) + plan_stage_words(nmax, Pmax));
-    const int nxt = (g.nx + tx - 1) / tx;
+    const size_t smem =
+        sizeof(T) * ((size_t)tx * CX * (2 * Pmax + 1) + plan_stage_words(nmax, Pmax));
+    const int nxt = (g.nx + tx * CX - 1) / (tx * CX);
     const int outer = DIR == 1 ? g.nz : g.ny;
-    K_sweep_reg<T, L, DIR, MODE>.launch(W.pdl != 0, dim3(3 * outer * nxt), dim3(threads), smem,
-                                        st, g, F, W.q0, W.q1, W.q2, pa, pb, tx);
+    K_sweep_reg<T, L, DIR, MODE, CX>.launch(W.pdl != 0, dim3(3 * outer * nxt), dim3(threads),
+                                            smem, st, g, F, W.q0, W.q1, W.q2, pa, pb, tx);
 }
 
 template <typename T, int DIR, int MODE>
@@ -256,13 +313,20 @@ void dispatch(const GridDev &g, const Fields<T> &F, Work<T> &W, cudaStream_t st)
     const TriPlan<T> &pb = W.plan[3];
     const int chunk = W.chunk_z;
     const int tx = W.tx_z;
+    // two columns per lane (a schedule choice) for chunks of up to 16 rows
+    if (W.zsw_cols == 2 && chunk <= 16) {
+        if (chunk <= 8) launch_reg<T, 8, DIR, MODE, 2>(g, F, W, pa, pb, tx, st);
+        else if (chunk == 12) launch_reg<T, 12, DIR, MODE, 2>(g, F, W, pa, pb, tx, st);
+        else launch_reg<T, 16, DIR, MODE, 2>(g, F, W, pa, pb, tx, st);
+        return;
+    }
     // chunks of exactly 12 or 24 rows (nz = 192, 384, 768 ...) get registers
     // of their own length, so that those lines also take the guard-free path
-    if (chunk <= 8) launch_reg<T, 8, DIR, MODE>(g, F, W, pa, pb, tx, st);
-    else if (chunk == 12) launch_reg<T, 12, DIR, MODE>(g, F, W, pa, pb, tx, st);
-    else if (chunk <= 16) launch_reg<T, 16, DIR, MODE>(g, F, W, pa, pb, tx, st);
-    else if (chunk == 24) launch_reg<T, 24, DIR, MODE>(g, F, W, pa, pb, tx, st);
-    else launch_reg<T, 32, DIR, MODE>(g, F, W, pa, pb, tx, st);
+    if (chunk <= 8) launch_reg<T, 8, DIR, MODE, 1>(g, F, W, pa, pb, tx, st);
+    else if (chunk == 12) launch_reg<T, 12, DIR, MODE, 1>(g, F, W, pa, pb, tx, st);
+    else if (chunk <= 16) launch_reg<T, 16, DIR, MODE, 1>(g, F, W, pa, pb, tx, st);
+    else if (chunk == 24) launch_reg<T, 24, DIR, MODE, 1>(g, F, W, pa, pb, tx, st);
+    else launch_reg<T, 32, DIR, MODE, 1>(g, F, W, pa, pb, tx, st);
 }
 
 }  // namespace
@@ -348,6 +412,12 @@ template <typename T> void set_smem_limits_lines(const GridDev &g, const Work<T>
     raise_smem_limit(K_sweep_reg<T, 8, 2, 1>.solo());
     raise_smem_limit(K_sweep_reg<T, 16, 2, 1>.solo());
     raise_smem_limit(K_sweep_reg<T, 32, 2, 1>.solo());
+    raise_smem_limit(K_sweep_reg<T, 8, 2, 0, 2>.solo());
+    raise_smem_limit(K_sweep_reg<T, 12, 2, 0, 2>.solo());
+    raise_smem_limit(K_sweep_reg<T, 16, 2, 0, 2>.solo());
+    raise_smem_limit(K_sweep_reg<T, 8, 2, 1, 2>.solo());
+    raise_smem_limit(K_sweep_reg<T, 12, 2, 1, 2>.solo());
+    raise_smem_limit(K_sweep_reg<T, 16, 2, 1, 2>.solo());
 }
 
 #define FSEI_INST(T)                                                                           \

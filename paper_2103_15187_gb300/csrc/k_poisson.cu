@@ -878,8 +878,11 @@ constexpr Kernel<k_fft_y_2p<T, SIGN, N1, N2>, 256, 0> K_fft_y_2p{};
 template <typename T> constexpr Kernel<k_poisson_z<T>, 512, 0> K_poisson_z{};
 template <typename T> constexpr Kernel<k_poisson_exact<T>, 64, 0> K_poisson_exact{};
 template <typename T> constexpr Kernel<k_poisson_exact_f<T>, 32, 0> K_poisson_exact_f{};
+// single precision: 3 blocks per SM for chunks of up to 16 rows; longer
+// chunks (24 rows of the 768-row lines) need the registers of 2 blocks
 template <typename T, int E, int LPL>
-constexpr Kernel<k_poisson_zl<T, E, LPL>, 256, (sizeof(T) == 4 ? 3 : 2)> K_poisson_zl{};
+constexpr Kernel<k_poisson_zl<T, E, LPL>, 256, (sizeof(T) == 4 && E <= 16 ? 3 : 2)>
+    K_poisson_zl{};
 template <typename T, int RY> constexpr Kernel<k_irfft_x<T, RY>, 256, 0> K_irfft_x{};
 template <typename T, int RY, int N1, int N2>
 constexpr Kernel<k_irfft_x_2p<T, RY, N1, N2>, 256, (sizeof(T) == 4 ? 3 : 1)> K_irfft_x_2p{};
@@ -1004,6 +1007,12 @@ bool fft_y_2p_launch(const GridDev &g, Work<T> &W, cudaStream_t st) {
     case 128: FSEI_FY(16, 8); return true;
     case 256: FSEI_FY(16, 16); return true;
     case 512: FSEI_FY(32, 16); return true;
+    case 12: FSEI_FY(4, 3); return true;
+    case 24: FSEI_FY(6, 4); return true;
+    case 48: FSEI_FY(8, 6); return true;
+    case 96: FSEI_FY(12, 8); return true;
+    case 192: FSEI_FY(16, 12); return true;
+    case 384: FSEI_FY(24, 16); return true;
 #undef FSEI_FY
     default: return false;
     }
@@ -1086,6 +1095,11 @@ bool irfft_x_2p_launch(const GridDev &g, Work<T> &W, T *dst, cudaStream_t st) {
     case 64: FSEI_IX(8, 8); return true;
     case 128: FSEI_IX(16, 8); return true;
     case 256: FSEI_IX(16, 16); return true;
+    case 12: FSEI_IX(4, 3); return true;
+    case 24: FSEI_IX(6, 4); return true;
+    case 48: FSEI_IX(8, 6); return true;
+    case 96: FSEI_IX(12, 8); return true;
+    case 192: FSEI_IX(16, 12); return true;
 #undef FSEI_IX
     default: return false;
     }
@@ -1118,6 +1132,11 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
         raise_smem_limit(K_irfft_x_2p<T, R, 8, 8>.solo());
         raise_smem_limit(K_irfft_x_2p<T, R, 16, 8>.solo());
         raise_smem_limit(K_irfft_x_2p<T, R, 16, 16>.solo());
+        raise_smem_limit(K_irfft_x_2p<T, R, 4, 3>.solo());
+        raise_smem_limit(K_irfft_x_2p<T, R, 6, 4>.solo());
+        raise_smem_limit(K_irfft_x_2p<T, R, 8, 6>.solo());
+        raise_smem_limit(K_irfft_x_2p<T, R, 12, 8>.solo());
+        raise_smem_limit(K_irfft_x_2p<T, R, 16, 12>.solo());
     }
     raise_smem_limit(K_rfft_x<T, 1, 1>.solo());
     raise_smem_limit(K_rfft_x<T, 1, 2>.solo());
@@ -1141,6 +1160,18 @@ template <typename T> void set_smem_limits_poisson(const GridDev &g, const Work<
     raise_smem_limit(K_fft_y_2p<T, -1, 16, 16>.solo());
     raise_smem_limit(K_fft_y_2p<T, 1, 32, 16>.solo());
     raise_smem_limit(K_fft_y_2p<T, -1, 32, 16>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 4, 3>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 4, 3>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 6, 4>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 6, 4>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 8, 6>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 8, 6>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 12, 8>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 12, 8>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 16, 12>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 16, 12>.solo());
+    raise_smem_limit(K_fft_y_2p<T, 1, 24, 16>.solo());
+    raise_smem_limit(K_fft_y_2p<T, -1, 24, 16>.solo());
     raise_smem_limit(K_poisson_z<T>.solo());
     raise_smem_limit(K_poisson_exact<T>.solo());
     raise_smem_limit(K_poisson_exact_f<T>.solo());
@@ -1221,6 +1252,17 @@ template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*
                 put(t, 0);
         break;
     }
+    case SK_ZSW: {
+        // x columns per lane of the z sweep: 1 first, 2 for chunks of up to
+        // 16 rows
+        int chunk, P, tx;
+        sweep_geometry(g.nz, chunk, P, tx);
+        if (chunk <= 16) {
+            put(1, 0);
+            put(2, 0);
+        }
+        break;
+    }
     case SK_PROJ: {
         // row passes per thread of the 16-byte vector projection
         if (g.nx % (16 / tsz)) break;
@@ -1246,6 +1288,7 @@ template <typename T> Schedule schedule_of(const GridDev &g, const Work<T> &W) {
     s.ry_rfft = W.ry_rfft;
     if (schedule_candidates<T>(g, SK_FFTY, c, 1)) s.tkx_fft = W.tkx_fft;
     if (schedule_candidates<T>(g, SK_PROJ, c, 1)) s.proj_mult = W.proj_mult ? W.proj_mult : 4;
+    if (schedule_candidates<T>(g, SK_ZSW, c, 1)) s.zsw_cols = W.zsw_cols ? W.zsw_cols : 1;
     return s;
 }
 
@@ -1257,6 +1300,7 @@ template <typename T> void apply_schedule(Work<T> &W, const Schedule &s) {
     if (s.ry_rfft) W.ry_rfft = s.ry_rfft;
     if (s.tkx_fft) W.tkx_fft = s.tkx_fft;
     W.proj_mult = s.proj_mult;
+    W.zsw_cols = s.zsw_cols;
 }
 
 #define FSEI_INST(T)                                                                           \

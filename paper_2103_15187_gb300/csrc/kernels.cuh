@@ -232,7 +232,9 @@ template <typename T> struct Work {
     int ry;                  // rows per block of the x-line solves
     int ry_fft;              // rows per block of the x transforms
     int chunk_y, chunk_z;    // register chunk length of the y / z sweeps
-    int tx_y, tx_z;          // x columns per block of the y / z sweeps
+    int tx_y, tx_z;          // x lanes per block of the y / z sweeps
+    int zsw_cols;            // x columns per lane of the z sweep (1 or 2;
+                             // 0: 1)
     int py;                  // chunks per y line
     int px, chunk_x;         // chunks per x line and their length (x solves)
     int tkx;                 // kx columns per block of the y FFT / z Poisson
@@ -259,6 +261,7 @@ template <typename T> struct Work {
 struct Schedule {
     int rhs_cpl;    // RHS + x sweep: cells per lane of the row-resident kernel
     int rhs_strip;  // and rows per strip when marched along y (0: not)
+    int zsw_cols;   // z sweep: x columns per lane (1 or 2)
     int zl_lpl;     // z Poisson: lanes per mode line (the reduction across
                     // lanes); zl_e: rows per lane (the elimination in a lane)
     int zl_e;
@@ -266,7 +269,7 @@ struct Schedule {
     int tkx_fft;    // y transforms: kx columns per block
     int proj_mult;  // projection: row passes per thread
 };
-enum ScheduleKnob { SK_RHS, SK_ZL, SK_RFFT, SK_FFTY, SK_PROJ, SK_COUNT };
+enum ScheduleKnob { SK_RHS, SK_ZL, SK_RFFT, SK_FFTY, SK_PROJ, SK_ZSW, SK_COUNT };
 // the values knob k may take on this grid (pairs (lanes, rows) for SK_ZL,
 // (cells per lane, rows per strip) for SK_RHS, single values in out[i][0]
 // otherwise), the default first; their count

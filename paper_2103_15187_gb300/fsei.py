@@ -99,7 +99,8 @@ class Schedule(ctypes.Structure):
                 ("rfft_rows_per_block", ctypes.c_int32),
                 ("ffty_columns_per_block", ctypes.c_int32),
                 ("project_passes_per_thread", ctypes.c_int32),
-                ("rhs_rows_per_strip", ctypes.c_int32)]
+                ("rhs_rows_per_strip", ctypes.c_int32),
+                ("zsweep_columns_per_lane", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -383,7 +384,9 @@ class Batch:
         self.n = len(boxes)
 
     def autotune(self, force=False, stream=None):
-        """fsei_batch_autotune: one measured schedule per distinct box shape."""
+        """fsei_batch_autotune: one measured schedule per distinct box shape,
+        refined for shapes shared by several boxes by timing their grouped
+        launches."""
         _check(load().fsei_batch_autotune(self.handle, FSEI_TUNE_FORCE if force else 0,
                                           _stream_handle(stream)))
 
