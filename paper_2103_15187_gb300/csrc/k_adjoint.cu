@@ -18,6 +18,7 @@
 //   k_adj_gather   u-bar = u*-bar + dt/Re L^T q + J_A(u^n)^T Hb;
 //                  p-bar -= dt G^T q
 #include "kernels.cuh"
+#include "rhs_row.cuh"
 #include "tri.cuh"
 
 namespace fsei {
@@ -176,6 +177,11 @@ k_adj_hist(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
 
 // u-bar += dt/Re L^T q + J_A(u^n)^T Hb (one component per call of the
 // helpers below); p-bar -= dt G^T q.
+// The gather at the u, v, w and p points of one grid row (j, k): every value
+// it reads lies within one cell of (i, j, k) in each direction, so the row
+// offsets of (j + dj, k + dk) (-1 beyond a wall) and the wrapped columns
+// i - 1, i, i + 1 are formed once, and the stencil accessors take the
+// offsets (di, dj, dk) in -1 .. 1.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
@@ -184,7 +190,7 @@ k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
              const T *__restrict__ H2, T *__restrict__ ub, T *__restrict__ vb,
              T *__restrict__ wb, T *__restrict__ pb, const StepScalars *sc, T inv_re) {
     const Nb N{g.nx, g.ny, g.nz, g.walls};
-    const int nz = g.nz;
+    const int nx = g.nx, nz = g.nz;
     const bool walls = g.walls != 0;
     const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
     const T dt = fpick<T>(sc->dt, sc->fdt);
@@ -192,78 +198,100 @@ k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
     const T idx2 = fpick<T>(g.idx2, g.fidx2), idy2 = fpick<T>(g.idy2, g.fidy2);
     const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
     const T h = T(0.5);
-    auto IDZ = [&](int kk) { return idz[N.wzi(kk)]; };
-    auto IHC = [&](int kk) { return ihc[kk < 0 ? kk + nz : (kk > nz ? kk - nz : kk)]; };
-    // cotangents of the advection term, with the sign of -div(uu) folded in
-    auto A = [&](int i, int jj, int kk) { return -N.at(H0, i, jj, kk); };
-    auto B = [&](int i, int jj, int kk) { return -N.at(H1, i, jj, kk); };
-    auto C = [&](int i, int jj, int kk) {
-        if (walls && (kk <= 0 || kk >= nz)) return T(0);
-        return -N.at(H2, i, jj, kk);
+    int ro[3][3];   // [dj + 1][dk + 1]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int kk = k + b - 1;
+            ro[a][b] = N.zin(kk) ? (N.wzi(kk) * g.ny + N.wyi(j + a - 1)) * nx : -1;
+        }
+    auto IDZ = [&](int dk) { return idz[N.wzi(k + dk)]; };
+    auto IHC = [&](int dk) {
+        const int kk = k + dk;
+        return ihc[kk < 0 ? kk + nz : (kk > nz ? kk - nz : kk)];
     };
-    // flux cotangents at centres and edges
-    auto Qb = [&](int i, int jj, int kk) { return (A(i, jj, kk) - A(i + 1, jj, kk)) * idx; };
-    auto Rb = [&](int i, int jj, int kk) { return (B(i, jj, kk) - B(i, jj + 1, kk)) * idy; };
-    auto Sb = [&](int i, int jj, int kk) {
-        return C(i, jj, kk) * IHC(kk) - C(i, jj, kk + 1) * IHC(kk + 1);
-    };
-    auto Euv = [&](int i, int jj, int kk) {
-        return (A(i, jj - 1, kk) - A(i, jj, kk)) * idy + (B(i - 1, jj, kk) - B(i, jj, kk)) * idx;
-    };
-    auto Euw = [&](int i, int jj, int kk) {
-        if (walls && (kk <= 0 || kk >= nz)) return T(0);
-        return (A(i, jj, kk - 1) * IDZ(kk - 1) - A(i, jj, kk) * IDZ(kk)) +
-               (C(i - 1, jj, kk) - C(i, jj, kk)) * idx;
-    };
-    auto Evw = [&](int i, int jj, int kk) {
-        if (walls && (kk <= 0 || kk >= nz)) return T(0);
-        return (B(i, jj, kk - 1) * IDZ(kk - 1) - B(i, jj, kk) * IDZ(kk)) +
-               (C(i, jj - 1, kk) - C(i, jj, kk)) * idy;
-    };
-    // forward averages
-    auto U = [&](int i, int jj, int kk) { return N.at(u, i, jj, kk); };
-    auto V = [&](int i, int jj, int kk) { return N.at(v, i, jj, kk); };
-    auto Wf = [&](int i, int jj, int kk) {
-        if (walls && (kk <= 0 || kk >= nz)) return T(0);
-        return N.at(w, i, jj, kk);
-    };
-    const int kd = N.wzi(k - 1), ku = N.wzi(k + 1);
-    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+    // beyond a wall: the face k + dk is a wall face or outside
+    auto wallface = [&](int dk) { return walls && (k + dk <= 0 || k + dk >= nz); };
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int ci[3] = {i == 0 ? nx - 1 : i - 1, i, i == nx - 1 ? 0 : i + 1};
+        auto at = [&](const T *f, int di, int dj, int dk) {
+            const int o = ro[dj + 1][dk + 1];
+            return o < 0 ? T(0) : f[o + ci[di + 1]];
+        };
+        // cotangents of the advection term, with the sign of -div(uu) folded in
+        auto A = [&](int di, int dj, int dk) { return -at(H0, di, dj, dk); };
+        auto B = [&](int di, int dj, int dk) { return -at(H1, di, dj, dk); };
+        auto C = [&](int di, int dj, int dk) {
+            if (wallface(dk)) return T(0);
+            return -at(H2, di, dj, dk);
+        };
+        // flux cotangents at centres and edges
+        auto Qb = [&](int di, int dj, int dk) {
+            return (A(di, dj, dk) - A(di + 1, dj, dk)) * idx;
+        };
+        auto Rb = [&](int di, int dj, int dk) {
+            return (B(di, dj, dk) - B(di, dj + 1, dk)) * idy;
+        };
+        auto Sb = [&](int di, int dj, int dk) {
+            return C(di, dj, dk) * IHC(dk) - C(di, dj, dk + 1) * IHC(dk + 1);
+        };
+        auto Euv = [&](int di, int dj, int dk) {
+            return (A(di, dj - 1, dk) - A(di, dj, dk)) * idy +
+                   (B(di - 1, dj, dk) - B(di, dj, dk)) * idx;
+        };
+        auto Euw = [&](int di, int dj, int dk) {
+            if (wallface(dk)) return T(0);
+            return (A(di, dj, dk - 1) * IDZ(dk - 1) - A(di, dj, dk) * IDZ(dk)) +
+                   (C(di - 1, dj, dk) - C(di, dj, dk)) * idx;
+        };
+        auto Evw = [&](int di, int dj, int dk) {
+            if (wallface(dk)) return T(0);
+            return (B(di, dj, dk - 1) * IDZ(dk - 1) - B(di, dj, dk) * IDZ(dk)) +
+                   (C(di, dj - 1, dk) - C(di, dj, dk)) * idy;
+        };
+        // forward averages
+        auto U = [&](int di, int dj, int dk) { return at(u, di, dj, dk); };
+        auto V = [&](int di, int dj, int dk) { return at(v, di, dj, dk); };
+        auto Wf = [&](int di, int dj, int dk) {
+            if (wallface(dk)) return T(0);
+            return at(w, di, dj, dk);
+        };
         const size_t c = fid(i, j, k, g.nx, g.ny);
         // ---- u
         {
-            const T uc0 = h * (U(i, j, k) + U(i + 1, j, k));
-            const T ucm = h * (U(i - 1, j, k) + U(i, j, k));
-            T a = h * (T(2) * uc0 * Qb(i, j, k) + T(2) * ucm * Qb(i - 1, j, k));
-            a += h * (Euv(i, j, k) * h * (V(i, j, k) + V(i - 1, j, k)) +
-                      Euv(i, j + 1, k) * h * (V(i, j + 1, k) + V(i - 1, j + 1, k)));
-            a += h * (Euw(i, j, k) * h * (Wf(i, j, k) + Wf(i - 1, j, k)) +
-                      Euw(i, j, k + 1) * h * (Wf(i, j, k + 1) + Wf(i - 1, j, k + 1)));
+            const T uc0 = h * (U(0, 0, 0) + U(1, 0, 0));
+            const T ucm = h * (U(-1, 0, 0) + U(0, 0, 0));
+            T a = h * (T(2) * uc0 * Qb(0, 0, 0) + T(2) * ucm * Qb(-1, 0, 0));
+            a += h * (Euv(0, 0, 0) * h * (V(0, 0, 0) + V(-1, 0, 0)) +
+                      Euv(0, 1, 0) * h * (V(0, 1, 0) + V(-1, 1, 0)));
+            a += h * (Euw(0, 0, 0) * h * (Wf(0, 0, 0) + Wf(-1, 0, 0)) +
+                      Euw(0, 0, 1) * h * (Wf(0, 0, 1) + Wf(-1, 0, 1)));
             // viscous: lap_xy(q) + dz_k lapz_centre(q / dz)
-            const T qc = N.at(q0, i, j, k);
-            const T lxy = (N.at(q0, i + 1, j, k) - T(2) * qc + N.at(q0, i - 1, j, k)) * idx2 +
-                          (N.at(q0, i, j + 1, k) - T(2) * qc + N.at(q0, i, j - 1, k)) * idy2;
+            const T qc = at(q0, 0, 0, 0);
+            const T lxy = (at(q0, 1, 0, 0) - T(2) * qc + at(q0, -1, 0, 0)) * idx2 +
+                          (at(q0, 0, 1, 0) - T(2) * qc + at(q0, 0, -1, 0)) * idy2;
             const T sq = qc * idz[k];
-            const T sup = N.zin(k + 1) ? N.at(q0, i, j, k + 1) * idz[ku] : T(0);
-            const T sdn = N.zin(k - 1) ? N.at(q0, i, j, k - 1) * idz[kd] : T(0);
+            const T sup = ro[1][2] >= 0 ? at(q0, 0, 0, 1) * IDZ(1) : T(0);
+            const T sdn = ro[1][0] >= 0 ? at(q0, 0, 0, -1) * IDZ(-1) : T(0);
             const T lz = ((sup - sq) * ihc[k + 1] - (sq - sdn) * ihc[k]) * idz[k];
             ub[c] = ub[c] + dt * inv_re * (lxy + dz[k] * lz) + a;
         }
         // ---- v
         {
-            const T vc0 = h * (V(i, j, k) + V(i, j + 1, k));
-            const T vcm = h * (V(i, j - 1, k) + V(i, j, k));
-            T a = h * (T(2) * vc0 * Rb(i, j, k) + T(2) * vcm * Rb(i, j - 1, k));
-            a += h * (Euv(i, j, k) * h * (U(i, j, k) + U(i, j - 1, k)) +
-                      Euv(i + 1, j, k) * h * (U(i + 1, j, k) + U(i + 1, j - 1, k)));
-            a += h * (Evw(i, j, k) * h * (Wf(i, j, k) + Wf(i, j - 1, k)) +
-                      Evw(i, j, k + 1) * h * (Wf(i, j, k + 1) + Wf(i, j - 1, k + 1)));
-            const T qc = N.at(q1, i, j, k);
-            const T lxy = (N.at(q1, i + 1, j, k) - T(2) * qc + N.at(q1, i - 1, j, k)) * idx2 +
-                          (N.at(q1, i, j + 1, k) - T(2) * qc + N.at(q1, i, j - 1, k)) * idy2;
+            const T vc0 = h * (V(0, 0, 0) + V(0, 1, 0));
+            const T vcm = h * (V(0, -1, 0) + V(0, 0, 0));
+            T a = h * (T(2) * vc0 * Rb(0, 0, 0) + T(2) * vcm * Rb(0, -1, 0));
+            a += h * (Euv(0, 0, 0) * h * (U(0, 0, 0) + U(0, -1, 0)) +
+                      Euv(1, 0, 0) * h * (U(1, 0, 0) + U(1, -1, 0)));
+            a += h * (Evw(0, 0, 0) * h * (Wf(0, 0, 0) + Wf(0, -1, 0)) +
+                      Evw(0, 0, 1) * h * (Wf(0, 0, 1) + Wf(0, -1, 1)));
+            const T qc = at(q1, 0, 0, 0);
+            const T lxy = (at(q1, 1, 0, 0) - T(2) * qc + at(q1, -1, 0, 0)) * idx2 +
+                          (at(q1, 0, 1, 0) - T(2) * qc + at(q1, 0, -1, 0)) * idy2;
             const T sq = qc * idz[k];
-            const T sup = N.zin(k + 1) ? N.at(q1, i, j, k + 1) * idz[ku] : T(0);
-            const T sdn = N.zin(k - 1) ? N.at(q1, i, j, k - 1) * idz[kd] : T(0);
+            const T sup = ro[1][2] >= 0 ? at(q1, 0, 0, 1) * IDZ(1) : T(0);
+            const T sdn = ro[1][0] >= 0 ? at(q1, 0, 0, -1) * IDZ(-1) : T(0);
             const T lz = ((sup - sq) * ihc[k + 1] - (sq - sdn) * ihc[k]) * idz[k];
             vb[c] = vb[c] + dt * inv_re * (lxy + dz[k] * lz) + a;
         }
@@ -271,35 +299,84 @@ k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
         if (walls && k == 0) {
             wb[c] = T(0);
         } else {
-            const T wc0 = h * (Wf(i, j, k) + Wf(i, j, k + 1));
-            const T wcm = h * (Wf(i, j, k - 1) + Wf(i, j, k));
-            T a = h * (T(2) * wc0 * Sb(i, j, k) + T(2) * wcm * Sb(i, j, k - 1));
-            a += h * (Euw(i, j, k) * h * (U(i, j, k) + U(i, j, k - 1)) +
-                      Euw(i + 1, j, k) * h * (U(i + 1, j, k) + U(i + 1, j, k - 1)));
-            a += h * (Evw(i, j, k) * h * (V(i, j, k) + V(i, j, k - 1)) +
-                      Evw(i, j + 1, k) * h * (V(i, j + 1, k) + V(i, j + 1, k - 1)));
+            const T wc0 = h * (Wf(0, 0, 0) + Wf(0, 0, 1));
+            const T wcm = h * (Wf(0, 0, -1) + Wf(0, 0, 0));
+            T a = h * (T(2) * wc0 * Sb(0, 0, 0) + T(2) * wcm * Sb(0, 0, -1));
+            a += h * (Euw(0, 0, 0) * h * (U(0, 0, 0) + U(0, 0, -1)) +
+                      Euw(1, 0, 0) * h * (U(1, 0, 0) + U(1, 0, -1)));
+            a += h * (Evw(0, 0, 0) * h * (V(0, 0, 0) + V(0, 0, -1)) +
+                      Evw(0, 1, 0) * h * (V(0, 1, 0) + V(0, 1, -1)));
             // viscous: lap_xy(q) + hc_k lapz_face(q / hc), q = 0 on the walls
-            auto QW = [&](int ii, int jj, int kk) {
-                if (walls && (kk <= 0 || kk >= nz)) return T(0);
-                return N.at(q2, ii, jj, kk);
+            auto QW = [&](int di, int dj, int dk) {
+                if (wallface(dk)) return T(0);
+                return at(q2, di, dj, dk);
             };
-            const T qc = QW(i, j, k);
-            const T lxy = (QW(i + 1, j, k) - T(2) * qc + QW(i - 1, j, k)) * idx2 +
-                          (QW(i, j + 1, k) - T(2) * qc + QW(i, j - 1, k)) * idy2;
+            const T qc = QW(0, 0, 0);
+            const T lxy = (QW(1, 0, 0) - T(2) * qc + QW(-1, 0, 0)) * idx2 +
+                          (QW(0, 1, 0) - T(2) * qc + QW(0, -1, 0)) * idy2;
             const T sq = qc * ihc[k];
-            const T sup = QW(i, j, k + 1) * IHC(k + 1 == nz ? (walls ? nz : 0) : k + 1);
-            const T sdn = QW(i, j, k - 1) * IHC(k - 1 < 0 ? nz - 1 : k - 1);
-            const T lz = ((sup - sq) * idz[k] - (sq - sdn) * idz[kd]) * ihc[k];
+            const T sup = QW(0, 0, 1) * ihc[k + 1 == nz ? (walls ? nz : 0) : k + 1];
+            const T sdn = QW(0, 0, -1) * ihc[k - 1 < 0 ? nz - 1 : k - 1];
+            const T lz = ((sup - sq) * idz[k] - (sq - sdn) * IDZ(-1)) * ihc[k];
             wb[c] = wb[c] + dt * inv_re * (lxy + lz / ihc[k]) + a;
         }
         // ---- p: p-bar -= dt G^T q
         {
-            const T cz0 = (walls && k == 0) ? T(0) : N.at(q2, i, j, k) * ihc[k];
-            const T cz1 = (walls && k == nz - 1) ? T(0) : N.at(q2, i, j, k + 1) * ihc[k + 1];
-            const T gtq = (N.at(q0, i, j, k) - N.at(q0, i + 1, j, k)) * idx +
-                          (N.at(q1, i, j, k) - N.at(q1, i, j + 1, k)) * idy + (cz0 - cz1);
+            const T cz0 = (walls && k == 0) ? T(0) : at(q2, 0, 0, 0) * ihc[k];
+            const T cz1 = (walls && k == nz - 1) ? T(0) : at(q2, 0, 0, 1) * ihc[k + 1];
+            const T gtq = (at(q0, 0, 0, 0) - at(q0, 1, 0, 0)) * idx +
+                          (at(q1, 0, 0, 0) - at(q1, 0, 1, 0)) * idy + (cz0 - cz1);
             pb[c] = pb[c] - dt * gtq;
         }
+    }
+}
+
+// (I - beta L_x)^-1 of q0, q1, q2 row by row, the row-resident layout of the
+// forward RHS (LPR lanes per row, 4 cells per lane in registers, rpb rows
+// per block) and its register line solve: the x operator is symmetric, so
+// the adjoint x sweep is the forward one without the right-hand side.
+template <typename T, int LPR>
+__global__ void __launch_bounds__(LPR > 128 ? LPR : 128)
+k_sweep_x_row(GridDev g, T *__restrict__ q0, T *__restrict__ q1, T *__restrict__ q2,
+              const StepScalars *sc, int rpb) {
+    constexpr int CPL = 4;
+    __shared__ T xs[LPR > 32 ? 2 * 3 * (LPR > 128 ? LPR : 128) : 1];
+    const int nx = g.nx, ny = g.ny;
+    const int nby = ny / rpb;
+    const int k = blockIdx.x / nby;
+    const int j = (blockIdx.x % nby) * rpb + (int)threadIdx.x / LPR;
+    const size_t o = ((size_t)k * ny + j) * nx + ((int)threadIdx.x & (LPR - 1)) * CPL;
+    T R[3][CPL];
+    ldrow(R[0], q0 + o);
+    ldrow(R[1], q1 + o);
+    ldrow(R[2], q2 + o);
+    line_solve_uni<T, CPL, LPR, 3>(R, fpick<T>(sc->ax, sc->fax), fpick<T>(sc->cix, sc->fcix),
+                                   sizeof(T) == 4 ? sc->ndecx_f : sc->ndecx_d, xs);
+    strow(q0 + o, R[0]);
+    strow(q1 + o, R[1]);
+    strow(q2 + o, R[2]);
+}
+
+template <typename T, int LPR>
+void sweep_x_row_launch(const GridDev &g, Work<T> &W, const StepScalars *sc, int rpb,
+                        cudaStream_t st) {
+    k_sweep_x_row<T, LPR><<<g.nz * (g.ny / rpb), rpb * LPR, 0, st>>>(g, W.q0, W.q1, W.q2, sc, rpb);
+}
+
+// the row-resident adjoint x sweep where rows split into lanes of 4 cells
+template <typename T>
+bool sweep_x_row_any(const GridDev &g, Work<T> &W, const StepScalars *sc, cudaStream_t st) {
+    int cpl = 0, lpr = 0, rpb = 0;
+    if (!rhs_row_geometry<T>(g, cpl, lpr, rpb, 4) || cpl != 4) return false;
+    switch (lpr) {
+    case 4: sweep_x_row_launch<T, 4>(g, W, sc, rpb, st); return true;
+    case 8: sweep_x_row_launch<T, 8>(g, W, sc, rpb, st); return true;
+    case 16: sweep_x_row_launch<T, 16>(g, W, sc, rpb, st); return true;
+    case 32: sweep_x_row_launch<T, 32>(g, W, sc, rpb, st); return true;
+    case 64: sweep_x_row_launch<T, 64>(g, W, sc, rpb, st); return true;
+    case 128: sweep_x_row_launch<T, 128>(g, W, sc, rpb, st); return true;
+    case 256: sweep_x_row_launch<T, 256>(g, W, sc, rpb, st); return true;
+    default: return false;
     }
 }
 
@@ -321,6 +398,7 @@ void sweep_x_L(const GridDev &g, Work<T> &W, const StepScalars *sc, int P, cudaS
 
 template <typename T>
 void launch_sweep_x_adjoint(const GridDev &g, Work<T> &W, const StepScalars *sc, cudaStream_t st) {
+    if (sweep_x_row_any<T>(g, W, sc, st)) return;
     int P, chunk;
     sweep_x_geometry(g, W, P, chunk);
     if (chunk <= 8) sweep_x_L<T, 8>(g, W, sc, P, st);
