@@ -442,8 +442,10 @@ fsei_status fsei_batch_step(fsei_batch batch, fsei_state *states,
  * more scratch than the array holds (e.g. FP64 up to about 128^3 cells),
  * FSEI_E_ARG for bad arguments, FSEI_E_CUDA if a CUDA call fails.  It does
  * not set fsei_last_error().  The first call on a device (made with that
- * device current) looks up the array's device address; make that first call
- * before any stream capture.  All calls share the array, which keeps the
+ * device current) looks up the array's device address.  A call on a stream
+ * that is being captured is refused with FSEI_E_ARG (a captured copy would
+ * read the static host buffer at replay, after later calls have rewritten
+ * it).  All calls share the array, which keeps the
  * last call's contents (the spectrum is cleared on every call); calls whose
  * GPU work overlaps -- on different streams or from different host
  * threads -- race on it and must be serialised by the caller.  The tables

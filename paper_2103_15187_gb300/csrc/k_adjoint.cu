@@ -177,79 +177,109 @@ k_adj_hist(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
 
 // u-bar += dt/Re L^T q + J_A(u^n)^T Hb (one component per call of the
 // helpers below); p-bar -= dt G^T q.
-// The gather at the u, v, w and p points of one grid row (j, k): every value
-// it reads lies within one cell of (i, j, k) in each direction, so the row
-// offsets of (j + dj, k + dk) (-1 beyond a wall) and the wrapped columns
-// i - 1, i, i + 1 are formed once, and the stencil accessors take the
-// offsets (di, dj, dk) in -1 .. 1.
+// The window of one grid row (j, k) read by the two gather kernels: every
+// value lies within one cell of (i, j, k) in each direction, so the row
+// offsets of (j + dj, k + dk) (-1 beyond a wall) are formed once per block
+// and the wrapped columns i - 1, i, i + 1 once per thread; the accessors take
+// the offsets (di, dj, dk) in -1 .. 1.
+struct Window {
+    int nx, ny, nz, j, k;
+    bool walls;
+    int ro[3][3];   // [dj + 1][dk + 1]
+    FSEI_D Window(const GridDev &g, int j_, int k_)
+        : nx(g.nx), ny(g.ny), nz(g.nz), j(j_), k(k_), walls(g.walls != 0) {
+        const Nb N{g.nx, g.ny, g.nz, g.walls};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int kk = k + b - 1;
+                ro[a][b] = N.zin(kk) ? (N.wzi(kk) * ny + N.wyi(j + a - 1)) * nx : -1;
+            }
+    }
+    // the face k + dk is a wall face or lies beyond one
+    FSEI_D bool wallface(int dk) const { return walls && (k + dk <= 0 || k + dk >= nz); }
+    FSEI_D int zw(int kk) const { return kk < 0 ? kk + nz : (kk >= nz ? kk - nz : kk); }
+};
+
+// Pass 1 of the gather: the cotangents of the advection fluxes at the cell
+// centres (Qb, Rb, Sb) and edges (Euv, Euw, Evw) from H-bar, each formed
+// once per point (pass 2 reads each of them at up to eight points).
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
-             const T *__restrict__ w, const T *__restrict__ q0, const T *__restrict__ q1,
-             const T *__restrict__ q2, const T *__restrict__ H0, const T *__restrict__ H1,
-             const T *__restrict__ H2, T *__restrict__ ub, T *__restrict__ vb,
-             T *__restrict__ wb, T *__restrict__ pb, const StepScalars *sc, T inv_re) {
-    const Nb N{g.nx, g.ny, g.nz, g.walls};
-    const int nx = g.nx, nz = g.nz;
-    const bool walls = g.walls != 0;
-    const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
-    const T dt = fpick<T>(sc->dt, sc->fdt);
+k_adj_flux(GridDev g, const T *__restrict__ H0, const T *__restrict__ H1,
+           const T *__restrict__ H2, T *__restrict__ fl) {
+    const Window Wn(g, blockIdx.x % g.ny, blockIdx.x / g.ny);
+    const int nx = g.nx, k = Wn.k;
+    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
     const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
-    const T idx2 = fpick<T>(g.idx2, g.fidx2), idy2 = fpick<T>(g.idy2, g.fidy2);
-    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
-    const T h = T(0.5);
-    int ro[3][3];   // [dj + 1][dk + 1]
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const int kk = k + b - 1;
-            ro[a][b] = N.zin(kk) ? (N.wzi(kk) * g.ny + N.wyi(j + a - 1)) * nx : -1;
-        }
-    auto IDZ = [&](int dk) { return idz[N.wzi(k + dk)]; };
+    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
+    auto IDZ = [&](int dk) { return idz[Wn.zw(k + dk)]; };
     auto IHC = [&](int dk) {
         const int kk = k + dk;
-        return ihc[kk < 0 ? kk + nz : (kk > nz ? kk - nz : kk)];
+        return ihc[kk < 0 ? kk + Wn.nz : (kk > Wn.nz ? kk - Wn.nz : kk)];
     };
-    // beyond a wall: the face k + dk is a wall face or outside
-    auto wallface = [&](int dk) { return walls && (k + dk <= 0 || k + dk >= nz); };
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const int ci[3] = {i == 0 ? nx - 1 : i - 1, i, i == nx - 1 ? 0 : i + 1};
+        const int cm = i == 0 ? nx - 1 : i - 1, cp = i == nx - 1 ? 0 : i + 1;
         auto at = [&](const T *f, int di, int dj, int dk) {
-            const int o = ro[dj + 1][dk + 1];
-            return o < 0 ? T(0) : f[o + ci[di + 1]];
+            const int o = Wn.ro[dj + 1][dk + 1];
+            return o < 0 ? T(0) : f[o + (di < 0 ? cm : (di > 0 ? cp : i))];
         };
         // cotangents of the advection term, with the sign of -div(uu) folded in
         auto A = [&](int di, int dj, int dk) { return -at(H0, di, dj, dk); };
         auto B = [&](int di, int dj, int dk) { return -at(H1, di, dj, dk); };
         auto C = [&](int di, int dj, int dk) {
-            if (wallface(dk)) return T(0);
+            if (Wn.wallface(dk)) return T(0);
             return -at(H2, di, dj, dk);
         };
-        // flux cotangents at centres and edges
-        auto Qb = [&](int di, int dj, int dk) {
-            return (A(di, dj, dk) - A(di + 1, dj, dk)) * idx;
+        const size_t c = fid(i, Wn.j, k, g.nx, g.ny);
+        // Qb, Rb, Sb at the centre; Euv, Euw, Evw at the edges of (i, j, k)
+        fl[c] = (A(0, 0, 0) - A(1, 0, 0)) * idx;
+        fl[ncell + c] = (B(0, 0, 0) - B(0, 1, 0)) * idy;
+        fl[2 * ncell + c] = C(0, 0, 0) * IHC(0) - C(0, 0, 1) * IHC(1);
+        fl[3 * ncell + c] = (A(0, -1, 0) - A(0, 0, 0)) * idy + (B(-1, 0, 0) - B(0, 0, 0)) * idx;
+        fl[4 * ncell + c] = Wn.wallface(0) ? T(0)
+                                           : (A(0, 0, -1) * IDZ(-1) - A(0, 0, 0) * IDZ(0)) +
+                                                 (C(-1, 0, 0) - C(0, 0, 0)) * idx;
+        fl[5 * ncell + c] = Wn.wallface(0) ? T(0)
+                                           : (B(0, 0, -1) * IDZ(-1) - B(0, 0, 0) * IDZ(0)) +
+                                                 (C(0, -1, 0) - C(0, 0, 0)) * idy;
+    }
+}
+
+// Pass 2: u-bar += dt/Re L^T q + J_A(u^n)^T Hb from the flux cotangents of
+// pass 1 and the forward velocities; p-bar -= dt G^T q.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
+             const T *__restrict__ w, const T *__restrict__ q0, const T *__restrict__ q1,
+             const T *__restrict__ q2, const T *__restrict__ fl, T *__restrict__ ub,
+             T *__restrict__ vb, T *__restrict__ wb, T *__restrict__ pb, const StepScalars *sc,
+             T inv_re) {
+    const Window Wn(g, blockIdx.x % g.ny, blockIdx.x / g.ny);
+    const int nx = g.nx, nz = g.nz, j = Wn.j, k = Wn.k;
+    const bool walls = Wn.walls;
+    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
+    const T dt = fpick<T>(sc->dt, sc->fdt);
+    const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
+    const T idx2 = fpick<T>(g.idx2, g.fidx2), idy2 = fpick<T>(g.idy2, g.fidy2);
+    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
+    const T h = T(0.5);
+    auto IDZ = [&](int dk) { return idz[Wn.zw(k + dk)]; };
+    auto wallface = [&](int dk) { return Wn.wallface(dk); };
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int cm = i == 0 ? nx - 1 : i - 1, cp = i == nx - 1 ? 0 : i + 1;
+        auto at = [&](const T *f, int di, int dj, int dk) {
+            const int o = Wn.ro[dj + 1][dk + 1];
+            return o < 0 ? T(0) : f[o + (di < 0 ? cm : (di > 0 ? cp : i))];
         };
-        auto Rb = [&](int di, int dj, int dk) {
-            return (B(di, dj, dk) - B(di, dj + 1, dk)) * idy;
-        };
-        auto Sb = [&](int di, int dj, int dk) {
-            return C(di, dj, dk) * IHC(dk) - C(di, dj, dk + 1) * IHC(dk + 1);
-        };
-        auto Euv = [&](int di, int dj, int dk) {
-            return (A(di, dj - 1, dk) - A(di, dj, dk)) * idy +
-                   (B(di - 1, dj, dk) - B(di, dj, dk)) * idx;
-        };
-        auto Euw = [&](int di, int dj, int dk) {
-            if (wallface(dk)) return T(0);
-            return (A(di, dj, dk - 1) * IDZ(dk - 1) - A(di, dj, dk) * IDZ(dk)) +
-                   (C(di - 1, dj, dk) - C(di, dj, dk)) * idx;
-        };
-        auto Evw = [&](int di, int dj, int dk) {
-            if (wallface(dk)) return T(0);
-            return (B(di, dj, dk - 1) * IDZ(dk - 1) - B(di, dj, dk) * IDZ(dk)) +
-                   (C(di, dj - 1, dk) - C(di, dj, dk)) * idy;
-        };
+        // the flux cotangents of pass 1 (0 beyond a wall, as there)
+        auto Qb = [&](int di, int dj, int dk) { return at(fl, di, dj, dk); };
+        auto Rb = [&](int di, int dj, int dk) { return at(fl + ncell, di, dj, dk); };
+        auto Sb = [&](int di, int dj, int dk) { return at(fl + 2 * ncell, di, dj, dk); };
+        auto Euv = [&](int di, int dj, int dk) { return at(fl + 3 * ncell, di, dj, dk); };
+        auto Euw = [&](int di, int dj, int dk) { return at(fl + 4 * ncell, di, dj, dk); };
+        auto Evw = [&](int di, int dj, int dk) { return at(fl + 5 * ncell, di, dj, dk); };
         // forward averages
         auto U = [&](int di, int dj, int dk) { return at(u, di, dj, dk); };
         auto V = [&](int di, int dj, int dk) { return at(v, di, dj, dk); };
@@ -272,8 +302,8 @@ k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
             const T lxy = (at(q0, 1, 0, 0) - T(2) * qc + at(q0, -1, 0, 0)) * idx2 +
                           (at(q0, 0, 1, 0) - T(2) * qc + at(q0, 0, -1, 0)) * idy2;
             const T sq = qc * idz[k];
-            const T sup = ro[1][2] >= 0 ? at(q0, 0, 0, 1) * IDZ(1) : T(0);
-            const T sdn = ro[1][0] >= 0 ? at(q0, 0, 0, -1) * IDZ(-1) : T(0);
+            const T sup = Wn.ro[1][2] >= 0 ? at(q0, 0, 0, 1) * IDZ(1) : T(0);
+            const T sdn = Wn.ro[1][0] >= 0 ? at(q0, 0, 0, -1) * IDZ(-1) : T(0);
             const T lz = ((sup - sq) * ihc[k + 1] - (sq - sdn) * ihc[k]) * idz[k];
             ub[c] = ub[c] + dt * inv_re * (lxy + dz[k] * lz) + a;
         }
@@ -290,8 +320,8 @@ k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
             const T lxy = (at(q1, 1, 0, 0) - T(2) * qc + at(q1, -1, 0, 0)) * idx2 +
                           (at(q1, 0, 1, 0) - T(2) * qc + at(q1, 0, -1, 0)) * idy2;
             const T sq = qc * idz[k];
-            const T sup = ro[1][2] >= 0 ? at(q1, 0, 0, 1) * IDZ(1) : T(0);
-            const T sdn = ro[1][0] >= 0 ? at(q1, 0, 0, -1) * IDZ(-1) : T(0);
+            const T sup = Wn.ro[1][2] >= 0 ? at(q1, 0, 0, 1) * IDZ(1) : T(0);
+            const T sdn = Wn.ro[1][0] >= 0 ? at(q1, 0, 0, -1) * IDZ(-1) : T(0);
             const T lz = ((sup - sq) * ihc[k + 1] - (sq - sdn) * ihc[k]) * idz[k];
             vb[c] = vb[c] + dt * inv_re * (lxy + dz[k] * lz) + a;
         }
@@ -437,8 +467,9 @@ void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T 
                                             W.adj2, fbx, fby, fbz, sc);
     });
     group(AK_GATHER, [&] {
-        k_adj_gather<T><<<rows, thr, 0, st>>>(g, u, v, w, W.q0, W.q1, W.q2, W.adj0, W.adj1,
-                                              W.adj2, ub, vb, wb, pb, sc, T(1.0 / re));
+        k_adj_flux<T><<<rows, thr, 0, st>>>(g, W.adj0, W.adj1, W.adj2, W.adjf);
+        k_adj_gather<T><<<rows, thr, 0, st>>>(g, u, v, w, W.q0, W.q1, W.q2, W.adjf, ub, vb, wb,
+                                              pb, sc, T(1.0 / re));
     });
 }
 
@@ -447,6 +478,7 @@ template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<
     cudaFuncGetAttributes(&fa, k_adj_phibar<T>);
     cudaFuncGetAttributes(&fa, k_adj_ustar<T>);
     cudaFuncGetAttributes(&fa, k_adj_hist<T>);
+    cudaFuncGetAttributes(&fa, k_adj_flux<T>);
     cudaFuncGetAttributes(&fa, k_adj_gather<T>);
     raise_smem_limit(k_sweep_x<T, 8>);
     raise_smem_limit(k_sweep_x<T, 16>);

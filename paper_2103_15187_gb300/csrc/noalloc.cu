@@ -268,6 +268,13 @@ extern "C" fsei_status fsei_poisson_solve_noalloc(const fsei_grid_desc *d, const
     if (d->prec != FSEI_FP64 && d->prec != FSEI_MIXED) return FSEI_E_ARG;
     if (d->zbc == FSEI_Z_PERIODIC && (!(d->lz > 0) || d->zfaces)) return FSEI_E_ARG;
     if (!(d->stretch >= 0)) return FSEI_E_ARG;
+    // a captured call would record copies from the static host buffer,
+    // which later calls overwrite: capture is refused
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cs) != cudaSuccess) return FSEI_E_CUDA;
+        if (cs != cudaStreamCaptureStatusNone) return FSEI_E_ARG;
+    }
 
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     int dev = 0;

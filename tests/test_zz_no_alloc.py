@@ -90,3 +90,30 @@ def test_noalloc_rejects_grids_beyond_the_static_scratch():
     # 16-byte aligned non-null stand-ins: the size check comes before any
     # device work, so nothing is read or written through them
     assert fn(ctypes.byref(d), ctypes.c_void_p(256), ctypes.c_void_p(256), None) == 2
+
+
+def test_noalloc_refuses_stream_capture():
+    """A call on a stream being captured is refused (its copies from the
+    static host buffer would replay after later calls rewrote it)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_15187_gb300 import fsei
+    lib = fsei.load()
+    fn = lib.fsei_poisson_solve_noalloc
+    fn.argtypes = [ctypes.POINTER(fsei.GridDesc), ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    d = fsei.GridDesc()
+    d.nx, d.ny, d.nz = 32, 24, 40
+    d.lx, d.ly, d.zbc, d.lz, d.stretch = 2 * np.pi, np.pi, 1, 2.0, 2.0
+    d.prec = fsei.FSEI_FP64
+    rhs = torch.zeros((40, 24, 32), dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(rhs)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            st = fn(ctypes.byref(d), ctypes.c_void_p(rhs.data_ptr()),
+                    ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(side.cuda_stream))
+    assert st == 1
