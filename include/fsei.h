@@ -59,7 +59,9 @@ typedef enum {
     FSEI_E_NOMEM = 4,       /* device allocation failed                      */
     FSEI_E_CUDA = 5,        /* a CUDA runtime call failed                    */
     FSEI_E_NONFINITE = 6,   /* a NaN/Inf appeared in the new state           */
-    FSEI_E_CFL = 7          /* CFL number of the new state above 1           */
+    FSEI_E_CFL = 7,         /* CFL number of the new state above 1           */
+    FSEI_E_BOUNDS = 8       /* bounds-checking mode: a kernel wrote outside a
+                               workspace buffer (fsei_grid_check_bounds)     */
 } fsei_status;
 
 typedef enum {
@@ -169,7 +171,9 @@ typedef struct {
  * environment variable FSEI_WORKSPACE_LIMIT_BYTES holds a decimal number at
  * the call, the handle's device allocations may not exceed that many bytes
  * in total; a grid that needs more fails with FSEI_E_NOMEM (a memory budget
- * for a process that shares the GPU). */
+ * for a process that shares the GPU).  When FSEI_CHECK_BOUNDS is set to a
+ * value other than "0" at the call, the grid runs in bounds-checking mode
+ * (see fsei_grid_check_bounds). */
 fsei_status fsei_grid_create(const fsei_grid_desc *desc, fsei_grid *out);
 
 /* Release a handle (NULL is a no-op).  Synchronises the device first. */
@@ -454,6 +458,22 @@ fsei_status fsei_batch_step(fsei_batch batch, fsei_state *states,
 fsei_status fsei_poisson_solve_noalloc(const fsei_grid_desc *desc,
                                        const void *rhs, void *phi,
                                        void *cuda_stream);
+
+/* Bounds-checking mode, a debugging aid with no counterpart in the paper
+ * (it stands in for a memory checker where none can run).  A grid created
+ * with FSEI_CHECK_BOUNDS set places a guard zone before and after every
+ * buffer of its workspace (1/16 of the buffer, at least 64 KiB, at most
+ * 1 MiB), filled with all-ones bytes for floating-point buffers (a NaN: a
+ * kernel that reads a guard makes its results non-finite, which the step
+ * flags as FSEI_E_NONFINITE) and zero bytes for integer ones.  This call
+ * synchronises the device and returns FSEI_E_BOUNDS, with the buffer, side
+ * and distance in fsei_last_error(), if any guard byte changed (a write past
+ * the end of a buffer), FSEI_OK otherwise; FSEI_E_UNSUPPORTED for a grid
+ * created without the mode.  In the mode, fsei_step, fsei_step_host,
+ * fsei_poisson_solve, fsei_adjoint_step, fsei_ib_forcing, fsei_ib_loads and
+ * fsei_batch_step (every box) run this check before they return, so they
+ * synchronise.  The caller's own fields are not guarded. */
+fsei_status fsei_grid_check_bounds(fsei_grid grid);
 
 /* Per-kernel timing, for measurement tools.  While enabled, fsei_step and
  * fsei_poisson_solve record a CUDA event pair on the call's stream around

@@ -2,6 +2,7 @@
 // metrics, FFT twiddle tables, Fourier-mode tables and workspace of a grid,
 // and sequences the kernels of a fractional step (Sec. 2.1, Eq. 3; Sec. 3.1).
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdlib.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -70,14 +71,39 @@ void twiddles(int n, int count, std::vector<double> &re, std::vector<double> &im
     }
 }
 
+// Byte pattern of the guard zones around a buffer of element type X in the
+// bounds-checking mode: all-ones bytes (a NaN in float and double, so a read
+// of a guard turns the results it feeds non-finite) for floating-point
+// buffers; zero bytes for integer and mixed ones, so that an index read from
+// a guard is still an index inside the grid.
+template <typename X> struct GuardFill { static constexpr unsigned char value = 0x00; };
+template <> struct GuardFill<float> { static constexpr unsigned char value = 0xFF; };
+template <> struct GuardFill<double> { static constexpr unsigned char value = 0xFF; };
+template <> struct GuardFill<cplx<float>> { static constexpr unsigned char value = 0xFF; };
+template <> struct GuardFill<cplx<double>> { static constexpr unsigned char value = 0xFF; };
+
 // Device allocations of one grid.  limit caps their sum: an allocation
 // that would pass it fails like a cudaMalloc without room (a grid created
 // under FSEI_WORKSPACE_LIMIT_BYTES, see fsei_grid_create).
+//
+// Bounds-checking mode (guard = true; FSEI_CHECK_BOUNDS=1 in the
+// environment when the grid is created): every buffer sits between two
+// guard zones of G = clamp(bytes / 16, 64 KiB, 1 MiB) bytes, rounded to 256,
+// filled with the buffer type's GuardFill pattern.  check_guards() reads
+// them back: a kernel that wrote up to G bytes past either end of a buffer
+// has changed one.  The returned address stays 256-byte aligned.
 struct DevAllocs {
     std::vector<void *> ptrs;
     size_t bytes = 0;
     size_t limit = ~size_t(0);
     cudaError_t err = cudaSuccess;
+    bool guard = false;
+    struct Zone {
+        const unsigned char *front, *back;   // device addresses
+        size_t gbytes, bytes;                 // guard size, buffer size
+        unsigned char fill;
+    };
+    std::vector<Zone> zones;
     template <typename X> X *get(size_t count) {
         void *p = nullptr;
         const size_t b = (count ? count : 1) * sizeof(X);
@@ -85,18 +111,61 @@ struct DevAllocs {
             err = cudaErrorMemoryAllocation;
             return nullptr;
         }
-        cudaError_t e = cudaMalloc(&p, b);
+        const size_t gb = guard ? std::min<size_t>(std::max<size_t>((b / 16 + 255) & ~size_t(255),
+                                                                    size_t(64) << 10),
+                                                   size_t(1) << 20)
+                                : 0;
+        cudaError_t e = cudaMalloc(&p, b + 2 * gb);
         if (e != cudaSuccess) {
             err = e;
             return nullptr;
         }
         ptrs.push_back(p);
         bytes += b;
-        return static_cast<X *>(p);
+        if (!guard) return static_cast<X *>(p);
+        unsigned char *base = static_cast<unsigned char *>(p);
+        const unsigned char fill = GuardFill<X>::value;
+        e = cudaMemset(base, fill, gb);
+        if (e == cudaSuccess) e = cudaMemset(base + gb + b, fill, gb);
+        if (e != cudaSuccess) {
+            err = e;
+            return nullptr;
+        }
+        zones.push_back({base, base + gb + b, gb, b, fill});
+        return reinterpret_cast<X *>(base + gb);
+    }
+    // First changed guard byte: buffer index (allocation order), side
+    // (0 before, 1 after the buffer) and byte offset from the buffer's
+    // edge; false when every guard is intact.  Synchronises the device.
+    bool check_guards(size_t *buf, int *side, size_t *offset, cudaError_t *cerr) const {
+        *cerr = cudaDeviceSynchronize();
+        if (*cerr != cudaSuccess) return false;
+        std::vector<unsigned char> h;
+        for (size_t i = 0; i < zones.size(); ++i) {
+            const Zone &z = zones[i];
+            h.resize(z.gbytes);
+            for (int sd = 0; sd < 2; ++sd) {
+                *cerr = cudaMemcpy(h.data(), sd ? z.back : z.front, z.gbytes,
+                                   cudaMemcpyDeviceToHost);
+                if (*cerr != cudaSuccess) return false;
+                // nearest the buffer first: the back guard from its start,
+                // the front guard from its end
+                for (size_t d = 0; d < z.gbytes; ++d) {
+                    if (h[sd ? d : z.gbytes - 1 - d] != z.fill) {
+                        *buf = i;
+                        *side = sd;
+                        *offset = d;
+                        return true;
+                    }
+                }
+            }
+        }
+        return false;
     }
     void release() {
         for (void *p : ptrs) cudaFree(p);
         ptrs.clear();
+        zones.clear();
     }
 };
 
@@ -114,6 +183,17 @@ const char *const kKernelNames[KK_COUNT] = {
     "non-Newtonian remainder (2 launches)",
     "adj_phibar", "adj_poisson (5 launches)", "adj_ustar", "adj_sweep_z", "adj_sweep_y",
     "adj_sweep_x", "adj_hist", "adj_gather"};
+
+// NVTX ranges: one per public call and one per pass of the step (named as
+// the kernel table above names it), so a profiler's timeline shows which
+// pass a kernel belongs to.  Host-side annotations only; without an attached
+// tool each push or pop is a check of a null function pointer.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Event pairs recorded around kernel launches while timing is enabled.
 struct KernelTimer {
@@ -135,6 +215,7 @@ struct KernelTimer {
     int fail_kind = -1;
     cudaError_t fail_err = cudaSuccess;
     template <class F> void run(int kind, cudaStream_t st, F &&f) {
+        NvtxRange range(kKernelNames[kind]);
         if (check) {
             f();
             const cudaError_t e = cudaPeekAtLastError();
@@ -151,12 +232,14 @@ struct KernelTimer {
     }
     // the two halves of run(), for launchers in other files (LaunchHook)
     void begin(int kind, cudaStream_t st) {
+        nvtxRangePushA(kKernelNames[kind]);
         if (!on) return;
         const size_t i = kinds.size();
         cudaEventRecord(ev(2 * i), st);
         kinds.push_back(kind);
     }
     void end(cudaStream_t st) {
+        nvtxRangePop();
         if (!on || kinds.empty()) return;
         cudaEventRecord(ev(2 * kinds.size() - 1), st);
     }
@@ -784,6 +867,7 @@ const char *fsei_last_error(void) { return g_err.c_str(); }
 const char *fsei_version(void) { return "fsei-gb300 0.1 (sm_103a)"; }
 
 fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
+    NvtxRange nvtx_call("fsei_grid_create");
     g_err.clear();
     if (!d || !out) return fail(FSEI_E_ARG, "fsei_grid_create: NULL argument");
     *out = nullptr;
@@ -848,6 +932,7 @@ fsei_status fsei_grid_create(const fsei_grid_desc *d, fsei_grid *out) {
         const unsigned long long v = strtoull(cap, &end, 10);
         if (end != cap && *end == '\0') M.limit = (size_t)v;
     }
+    if (const char *chk = getenv("FSEI_CHECK_BOUNDS")) M.guard = chk[0] != '\0' && chk[0] != '0';
     double *ddz = M.get<double>(nz), *didz = M.get<double>(nz), *dihc = M.get<double>(nz + 1);
     double *dzf = M.get<double>(nz + 1);
     float *fdz = M.get<float>(nz), *fidz = M.get<float>(nz), *fihc = M.get<float>(nz + 1);
@@ -934,6 +1019,7 @@ void fsei_grid_destroy(fsei_grid G) {
 int64_t fsei_grid_workspace_bytes(fsei_grid G) { return G ? (int64_t)G->mem.bytes : 0; }
 
 fsei_status fsei_grid_autotune(fsei_grid G, int32_t flags, void *cuda_stream, fsei_schedule *out) {
+    NvtxRange nvtx_call("fsei_grid_autotune");
     g_err.clear();
     cudaGetLastError();
     if (!G) return fail(FSEI_E_ARG, "fsei_grid_autotune: NULL grid");
@@ -1013,11 +1099,37 @@ fsei_status step_stats(fsei_grid_s *G, cudaStream_t st, fsei_step_stats *out, co
     return FSEI_OK;
 }
 
+// Bounds-checking mode: after the grid's work queued so far has finished,
+// FSEI_E_BOUNDS if a guard zone of its workspace changed (FSEI_OK when the
+// grid was created without guards).
+fsei_status guard_status(const fsei_grid_s *G, const char *who) {
+    if (!G->mem.guard) return FSEI_OK;
+    size_t buf = 0, off = 0;
+    int side = 0;
+    cudaError_t e = cudaSuccess;
+    if (G->mem.check_guards(&buf, &side, &off, &e))
+        return fail(FSEI_E_BOUNDS,
+                    "%s: the guard zone %s workspace buffer %zu (%zu bytes) was written %zu "
+                    "bytes from the buffer's edge",
+                    who, side ? "after" : "before", buf, G->mem.zones[buf].bytes, off);
+    if (e != cudaSuccess) return fail(FSEI_E_CUDA, "%s: %s", who, cudaGetErrorString(e));
+    return FSEI_OK;
+}
+
+// the status of a call that ran work on the grid, with the guard check of
+// the bounds-checking mode taking precedence
+fsei_status with_guards(const fsei_grid_s *G, fsei_status st, const char *who) {
+    if (!G->mem.guard) return st;
+    const fsei_status g = guard_status(G, who);
+    return g != FSEI_OK ? g : st;
+}
+
 }  // namespace
 
 fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy, const void *fz,
                       const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,
                       fsei_step_stats *out) {
+    NvtxRange nvtx_call("fsei_step");
     g_err.clear();
     cudaGetLastError();   // an error left by an unrelated earlier call is not ours
     if (!G || !s || !prm) return fail(FSEI_E_ARG, "fsei_step: NULL argument");
@@ -1040,12 +1152,13 @@ fsei_status fsei_step(fsei_grid G, fsei_state *s, const void *fx, const void *fy
         if (r != FSEI_OK) return r;
         s->have_prev_h = 1;
     }
-    return out ? step_stats(G, st, out, "fsei_step") : FSEI_OK;
+    return with_guards(G, out ? step_stats(G, st, out, "fsei_step") : FSEI_OK, "fsei_step");
 }
 
 fsei_status fsei_step_host(fsei_grid G, fsei_state *host, const fsei_state *dev, const void *fx,
                            const void *fy, const void *fz, const fsei_step_params *prm,
                            int32_t nsteps, void *cuda_stream, fsei_step_stats *out) {
+    NvtxRange nvtx_call("fsei_step_host");
     g_err.clear();
     cudaGetLastError();
     if (!G || !host || !dev || !prm) return fail(FSEI_E_ARG, "fsei_step_host: NULL argument");
@@ -1110,7 +1223,8 @@ fsei_status fsei_step_host(fsei_grid G, fsei_state *host, const fsei_state *dev,
     if (out) cudaStreamWaitEvent(st, H.out, 0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FSEI_E_CUDA, "fsei_step_host: %s", cudaGetErrorString(e));
-    return out ? step_stats(G, st, out, "fsei_step_host") : FSEI_OK;
+    return with_guards(G, out ? step_stats(G, st, out, "fsei_step_host") : FSEI_OK,
+                       "fsei_step_host");
 }
 
 fsei_status fsei_step_host_join(fsei_grid G, void *cuda_stream) {
@@ -1126,6 +1240,7 @@ fsei_status fsei_step_host_join(fsei_grid G, void *cuda_stream) {
 fsei_status fsei_adjoint_step(fsei_grid G, const fsei_state *fwd, const fsei_step_params *prm,
                               fsei_state *adj, void *fbar_x, void *fbar_y, void *fbar_z,
                               void *cuda_stream) {
+    NvtxRange nvtx_call("fsei_adjoint_step");
     g_err.clear();
     cudaGetLastError();   // an error left by an unrelated earlier call is not ours
     if (!G || !fwd || !prm || !adj) return fail(FSEI_E_ARG, "fsei_adjoint_step: NULL argument");
@@ -1177,23 +1292,27 @@ fsei_status fsei_adjoint_step(fsei_grid G, const fsei_state *fwd, const fsei_ste
                                (const T *)fwd->w, (T *)adj->u, (T *)adj->v, (T *)adj->w,
                                (T *)adj->p, (T *)adj->hu, (T *)adj->hv, (T *)adj->hw,
                                (T *)fbar_x, (T *)fbar_y, (T *)fbar_z, prm->re, st,
-                               tm.on ? &hook : nullptr);
+                               &hook);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(FSEI_E_CUDA, "adjoint launch: %s", cudaGetErrorString(e));
         return FSEI_OK;
     };
-    return G->prec == FSEI_FP64 ? run(G->wd, double(0)) : run(G->wf, float(0));
+    return with_guards(G, G->prec == FSEI_FP64 ? run(G->wd, double(0)) : run(G->wf, float(0)),
+                       "fsei_adjoint_step");
 }
 
 fsei_status fsei_poisson_solve(fsei_grid G, const void *rhs, void *phi, void *cuda_stream) {
+    NvtxRange nvtx_call("fsei_poisson_solve");
     g_err.clear();
     cudaGetLastError();   // an error left by an unrelated earlier call is not ours
     if (!G || !rhs || !phi) return fail(FSEI_E_ARG, "fsei_poisson_solve: NULL argument");
     if (!aligned16(rhs) || !aligned16(phi)) return fail(FSEI_E_ARG, "rhs/phi not 16-byte aligned");
     DeviceGuard dg(G->device);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    return G->prec == FSEI_FP64 ? run_poisson<double>(G, G->wd, rhs, phi, st)
-                                : run_poisson<float>(G, G->wf, rhs, phi, st);
+    return with_guards(G,
+                       G->prec == FSEI_FP64 ? run_poisson<double>(G, G->wd, rhs, phi, st)
+                                            : run_poisson<float>(G, G->wf, rhs, phi, st),
+                       "fsei_poisson_solve");
 }
 
 // the launch check and skipped-count read-back of the two IB entry points
@@ -1216,6 +1335,7 @@ fsei_status fsei_ib_forcing(fsei_grid G, const void *u, const void *v, const voi
                             const double *xb, const double *ub, const double *dvb,
                             int32_t nmarkers, double dt, void *fx, void *fy, void *fz,
                             double *u_at, void *cuda_stream, int32_t *skipped) {
+    NvtxRange nvtx_call("fsei_ib_forcing");
     g_err.clear();
     cudaGetLastError();
     if (!G || !u || !v || !w || !fx || !fy || !fz) return fail(FSEI_E_ARG, "fsei_ib_forcing: NULL argument");
@@ -1234,7 +1354,7 @@ fsei_status fsei_ib_forcing(fsei_grid G, const void *u, const void *v, const voi
         launch_ib_force<float>(G->g, (const float *)u, (const float *)v, (const float *)w, xb, ub,
                                dvb, nmarkers, dt, (float *)fx, (float *)fy, (float *)fz, u_at,
                                G->ib_count, st);
-    return ib_finish(G, st, skipped, 1, "fsei_ib_forcing");
+    return with_guards(G, ib_finish(G, st, skipped, 1, "fsei_ib_forcing"), "fsei_ib_forcing");
 }
 
 fsei_status fsei_ib_loads(fsei_grid G, const void *p, const void *u, const void *v,
@@ -1242,6 +1362,7 @@ fsei_status fsei_ib_loads(fsei_grid G, const void *p, const void *u, const void 
                           const int32_t *two_sided, const int32_t *tris, int32_t nfaces,
                           int32_t nnodes, double probe, double re, double *face_force,
                           double *node_force, void *cuda_stream, int32_t *skipped) {
+    NvtxRange nvtx_call("fsei_ib_loads");
     g_err.clear();
     cudaGetLastError();
     if (!G || !p || !u || !v || !w) return fail(FSEI_E_ARG, "fsei_ib_loads: NULL field");
@@ -1262,7 +1383,16 @@ fsei_status fsei_ib_loads(fsei_grid G, const void *p, const void *u, const void 
         launch_ib_loads<float>(G->g, (const float *)p, (const float *)u, (const float *)v,
                                (const float *)w, xf, nf, af, two_sided, tris, nfaces, nnodes,
                                probe, 1.0 / re, face_force, node_force, G->ib_count, st);
-    return ib_finish(G, st, skipped, 2, "fsei_ib_loads");
+    return with_guards(G, ib_finish(G, st, skipped, 2, "fsei_ib_loads"), "fsei_ib_loads");
+}
+
+fsei_status fsei_grid_check_bounds(fsei_grid G) {
+    g_err.clear();
+    if (!G) return fail(FSEI_E_ARG, "fsei_grid_check_bounds: NULL grid");
+    if (!G->mem.guard)
+        return fail(FSEI_E_UNSUPPORTED, "the grid was created without FSEI_CHECK_BOUNDS=1");
+    DeviceGuard dg(G->device);
+    return guard_status(G, "fsei_grid_check_bounds");
 }
 
 fsei_status fsei_set_kernel_timing(fsei_grid G, int32_t enable) {
@@ -1636,6 +1766,7 @@ fsei_status tune_group(fsei_batch_s *B, const std::vector<size_t> &idx, cudaStre
 extern "C" {
 
 fsei_status fsei_batch_create(const fsei_grid_desc *descs, int32_t nboxes, fsei_batch *out) {
+    NvtxRange nvtx_call("fsei_batch_create");
     g_err.clear();
     if (!descs || !out || nboxes < 1) return fail(FSEI_E_ARG, "fsei_batch_create: bad arguments");
     *out = nullptr;
@@ -1701,6 +1832,7 @@ fsei_status fsei_batch_set_max_group(fsei_batch B, int32_t max_boxes) {
 int32_t fsei_batch_launch_groups(fsei_batch B) { return B ? B->ngroups : 0; }
 
 fsei_status fsei_batch_autotune(fsei_batch B, int32_t flags, void *cuda_stream) {
+    NvtxRange nvtx_call("fsei_batch_autotune");
     g_err.clear();
     if (!B) return fail(FSEI_E_ARG, "fsei_batch_autotune: NULL batch");
     DeviceGuard dg(B->device);
@@ -1738,9 +1870,19 @@ fsei_status fsei_batch_autotune(fsei_batch B, int32_t flags, void *cuda_stream) 
     return FSEI_OK;
 }
 
+// bounds-checking mode: the first box whose workspace guards changed
+static fsei_status batch_guards(const fsei_batch_s *B, fsei_status st) {
+    for (size_t i = 0; i < B->grids.size(); ++i) {
+        const fsei_status g = guard_status(B->grids[i], "fsei_batch_step");
+        if (g != FSEI_OK) return fail(g, "box %zu: %s", i, std::string(g_err).c_str());
+    }
+    return st;
+}
+
 fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const *forces,
                             const fsei_step_params *prm, int32_t nsteps, void *cuda_stream,
                             fsei_step_stats *out) {
+    NvtxRange nvtx_call("fsei_batch_step");
     g_err.clear();
     cudaGetLastError();   // an error left by an unrelated earlier call is not ours
     if (!B || !states || !prm) return fail(FSEI_E_ARG, "fsei_batch_step: NULL argument");
@@ -1816,9 +1958,9 @@ fsei_status fsei_batch_step(fsei_batch B, fsei_state *states, const void *const 
             if ((out[i].flags & FSEI_FLAG_NONFINITE) && worst == FSEI_OK) worst = fail(FSEI_E_NONFINITE, "box %zu: non-finite state", i);
             else if ((out[i].flags & FSEI_FLAG_CFL) && worst == FSEI_OK) worst = fail(FSEI_E_CFL, "box %zu: CFL %g above 1", i, out[i].cfl);
         }
-        return worst;
+        return batch_guards(B, worst);
     }
-    return FSEI_OK;
+    return batch_guards(B, FSEI_OK);
 }
 
 }  // extern "C"

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libfsei.so")
 FSEI_OK = 0
 STATUS_NAMES = {0: "FSEI_OK", 1: "FSEI_E_ARG", 2: "FSEI_E_SHAPE",
                 3: "FSEI_E_UNSUPPORTED", 4: "FSEI_E_NOMEM", 5: "FSEI_E_CUDA",
-                6: "FSEI_E_NONFINITE", 7: "FSEI_E_CFL"}
+                6: "FSEI_E_NONFINITE", 7: "FSEI_E_CFL", 8: "FSEI_E_BOUNDS"}
 FSEI_FP64, FSEI_MIXED = 0, 1
 FSEI_Z_PERIODIC, FSEI_Z_WALLS = 0, 1
 FSEI_AB2_CN, FSEI_RK3_CN = 0, 1
@@ -31,7 +31,8 @@ EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
            "fsei_kernel_times", "fsei_kernel_name", "fsei_last_error", "fsei_version",
            "fsei_grid_autotune", "fsei_grid_get_schedule", "fsei_grid_set_schedule",
            "fsei_batch_autotune", "fsei_fp64_fma_rate", "fsei_batch_set_max_group",
-           "fsei_batch_launch_groups", "fsei_ib_forcing", "fsei_ib_loads")
+           "fsei_batch_launch_groups", "fsei_ib_forcing", "fsei_ib_loads",
+           "fsei_grid_check_bounds")
 FSEI_TUNE_FORCE = 1
 
 
@@ -152,6 +153,8 @@ def load(path=LIB_PATH):
                                     ctypes.POINTER(StepParams), ctypes.c_int32, vp,
                                     ctypes.POINTER(StepStats)]
     lib.fsei_batch_step.restype = ctypes.c_int
+    lib.fsei_grid_check_bounds.argtypes = [vp]
+    lib.fsei_grid_check_bounds.restype = ctypes.c_int
     lib.fsei_set_kernel_timing.argtypes = [vp, ctypes.c_int32]
     lib.fsei_set_kernel_timing.restype = ctypes.c_int
     lib.fsei_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -475,6 +478,12 @@ def ib_loads(grid, p, vel, surface, probe, re, node_force=None, stream=None):
                                 int(surface.get("nnodes", 0)), float(probe), float(re), _ptr(ff),
                                 _ptr(node_force), _stream_handle(stream), sk))
     return ff, sk[0], sk[1]
+
+
+def check_bounds(grid):
+    """fsei_grid_check_bounds: raises FseiError(FSEI_E_BOUNDS) if a guard
+    zone of a grid created with FSEI_CHECK_BOUNDS=1 was written."""
+    _check(load().fsei_grid_check_bounds(grid.handle))
 
 
 def set_kernel_timing(grid, enable):

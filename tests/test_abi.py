@@ -158,3 +158,9 @@ def test_status_names_match_header_enum():
     body = re.search(r"typedef enum \{(.*?)\} fsei_status;", text, re.S).group(1)
     enum = {int(v): n for n, v in re.findall(r"(FSEI_\w+)\s*=\s*(\d+)", body)}
     assert enum == fsei.STATUS_NAMES
+
+
+def test_bounds_check_rejects_a_null_handle(lib):
+    lib.fsei_grid_check_bounds.argtypes = [ctypes.c_void_p]
+    lib.fsei_grid_check_bounds.restype = ctypes.c_int
+    assert lib.fsei_grid_check_bounds(None) == 1
