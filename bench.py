@@ -565,6 +565,8 @@ def run_adjoint(args, peak):
         grid = g64 if prec == fsei.FSEI_FP64 else fsei.Grid(
             case.nx, case.ny, case.nz, case.lx, case.ly, zbc=case.zbc, lz=case.lz,
             stretch=case.stretch, prec=prec)
+        if not args.no_autotune:
+            grid.autotune()
 
         def once(timing=False):
             xs = [torch.tensor(a, dtype=dtype, device="cuda").requires_grad_(True)

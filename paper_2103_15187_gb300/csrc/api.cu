@@ -1272,9 +1272,8 @@ fsei_status fsei_adjoint_step(fsei_grid G, const fsei_state *fwd, const fsei_ste
             W.adj0 = G->mem.get<T>(ncell);
             W.adj1 = G->mem.get<T>(ncell);
             W.adj2 = G->mem.get<T>(ncell);
-            W.adjf = G->mem.get<T>(6 * ncell);
             if (G->mem.err != cudaSuccess) {
-                W.adj0 = W.adj1 = W.adj2 = W.adjf = nullptr;
+                W.adj0 = W.adj1 = W.adj2 = nullptr;
                 G->mem.err = cudaSuccess;
                 return fail(FSEI_E_NOMEM, "adjoint workspace allocation failed");
             }

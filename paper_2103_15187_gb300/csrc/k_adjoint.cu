@@ -15,7 +15,8 @@
 //   k_sweep_x      q = (I - beta L_x)^-1 q      (= RHS-bar)
 //   k_adj_hist     Hb = dt gamma q + H-bar;  H-bar_out = dt rho q;
 //                  f-bar += dt q
-//   k_adj_gather   u-bar = u*-bar + dt/Re L^T q + J_A(u^n)^T Hb;
+//   k_adj_gather_tile
+//                  u-bar = u*-bar + dt/Re L^T q + J_A(u^n)^T Hb;
 //                  p-bar -= dt G^T q
 #include "kernels.cuh"
 #include "rhs_row.cuh"
@@ -48,32 +49,41 @@ __global__ void __launch_bounds__(256)
 k_adj_phibar(GridDev g, const T *__restrict__ ub, const T *__restrict__ vb,
              const T *__restrict__ wb, const T *__restrict__ pb, T *__restrict__ x,
              const StepScalars *sc) {
-    const Nb N{g.nx, g.ny, g.nz, g.walls};
-    const int j = blockIdx.x % g.ny, k = blockIdx.x / g.ny;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int j = blockIdx.x % ny, k = blockIdx.x / ny;
+    const bool walls = g.walls != 0;
     const T dt = fpick<T>(sc->dt, sc->fdt), beta = fpick<T>(sc->beta, sc->fbeta);
     const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
     const T idx2 = fpick<T>(g.idx2, g.fidx2), idy2 = fpick<T>(g.idy2, g.fidy2);
     const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
-    const int nz = g.nz;
-    const bool walls = g.walls != 0;
-    const int kd = N.wzi(k - 1), ku = N.wzi(k + 1);
-    const T inv_vol = T(g.idx * g.idy) * idz[k];
-    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+    const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
+    const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
+    // 32-bit offsets of the rows (j, k), (j -/+ 1, k), (j, k -/+ 1) and the
+    // metric values of plane k, once per block (the planes beyond a wall
+    // are never read)
+    const int oc = (k * ny + j) * nx, ojm = (k * ny + jm) * nx, ojp = (k * ny + jp) * nx;
+    const int okd = (kd * ny + j) * nx, oku = (ku * ny + j) * nx;
+    const bool bot = walls && k == 0, top = walls && k == nz - 1;
+    const T ihck = ihc[k], ihcu = ihc[k + 1], idzk = idz[k], idzd = idz[kd], idzu = idz[ku];
+    const T dzk = dz[k];
+    const T inv_vol = T(g.idx * g.idy) * idzk;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int im = i == 0 ? nx - 1 : i - 1, ip = i == nx - 1 ? 0 : i + 1;
         // G^T u-bar
-        const T cz0 = (walls && k == 0) ? T(0) : N.at(wb, i, j, k) * ihc[k];
-        const T cz1 = (walls && k == nz - 1) ? T(0) : N.at(wb, i, j, k + 1) * ihc[k + 1];
-        const T gtu = (N.at(ub, i, j, k) - N.at(ub, i + 1, j, k)) * idx +
-                      (N.at(vb, i, j, k) - N.at(vb, i, j + 1, k)) * idy + (cz0 - cz1);
+        const T cz0 = bot ? T(0) : wb[oc + i] * ihck;
+        const T cz1 = top ? T(0) : wb[oku + i] * ihcu;
+        const T gtu = (ub[oc + i] - ub[oc + ip]) * idx + (vb[oc + i] - vb[ojp + i]) * idy +
+                      (cz0 - cz1);
         // (DG)^T p-bar = lap_xy(p-bar) + dz_k lapz((p-bar) / dz)
-        const T p0 = N.at(pb, i, j, k);
-        const T lxy = (N.at(pb, i + 1, j, k) - T(2) * p0 + N.at(pb, i - 1, j, k)) * idx2 +
-                      (N.at(pb, i, j + 1, k) - T(2) * p0 + N.at(pb, i, j - 1, k)) * idy2;
-        const T q0 = p0 * idz[k];
-        const T fup = (walls && k == nz - 1) ? T(0) : (N.at(pb, i, j, k + 1) * idz[ku] - q0) * ihc[k + 1];
-        const T fdn = (walls && k == 0) ? T(0) : (q0 - N.at(pb, i, j, k - 1) * idz[kd]) * ihc[k];
-        const T lp = lxy + dz[k] * (fup - fdn) * idz[k];
+        const T p0 = pb[oc + i];
+        const T lxy = (pb[oc + ip] - T(2) * p0 + pb[oc + im]) * idx2 +
+                      (pb[ojp + i] - T(2) * p0 + pb[ojm + i]) * idy2;
+        const T q0 = p0 * idzk;
+        const T fup = top ? T(0) : (pb[oku + i] * idzu - q0) * ihcu;
+        const T fdn = bot ? T(0) : (q0 - pb[okd + i] * idzd) * ihck;
+        const T lp = lxy + dzk * (fup - fdn) * idzk;
         const T phib = -dt * gtu + p0 - beta * lp;
-        x[fid(i, j, k, g.nx, g.ny)] = phib * inv_vol;
+        x[oc + i] = phib * inv_vol;
     }
 }
 
@@ -175,190 +185,230 @@ k_adj_hist(GridDev g, const T *__restrict__ q0, const T *__restrict__ q1,
     }
 }
 
-// u-bar += dt/Re L^T q + J_A(u^n)^T Hb (one component per call of the
-// helpers below); p-bar -= dt G^T q.
-// The window of one grid row (j, k) read by the two gather kernels: every
-// value lies within one cell of (i, j, k) in each direction, so the row
-// offsets of (j + dj, k + dk) (-1 beyond a wall) are formed once per block
-// and the wrapped columns i - 1, i, i + 1 once per thread; the accessors take
-// the offsets (di, dj, dk) in -1 .. 1.
-struct Window {
-    int nx, ny, nz, j, k;
-    bool walls;
-    int ro[3][3];   // [dj + 1][dk + 1]
-    FSEI_D Window(const GridDev &g, int j_, int k_)
-        : nx(g.nx), ny(g.ny), nz(g.nz), j(j_), k(k_), walls(g.walls != 0) {
-        const Nb N{g.nx, g.ny, g.nz, g.walls};
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const int kk = k + b - 1;
-                ro[a][b] = N.zin(kk) ? (N.wzi(kk) * ny + N.wyi(j + a - 1)) * nx : -1;
-            }
-    }
-    // the face k + dk is a wall face or lies beyond one
-    FSEI_D bool wallface(int dk) const { return walls && (k + dk <= 0 || k + dk >= nz); }
-    FSEI_D int zw(int kk) const { return kk < 0 ? kk + nz : (kk >= nz ? kk - nz : kk); }
-};
+// The gather in one pass, tiled and marched along z: a block owns a tile of
+// TX x TY columns (i, j) and walks a chunk of consecutive planes k.  The nine
+// fields the gather reads around a cell -- H-bar (H0, H1, H2), u^n, v^n, w^n
+// and q0, q1, q2 -- are staged plane by plane in shared memory on the tile
+// extended by one column and one row on every side (x, y periodic, wrapped
+// by global index), in a ring of NS planes: the planes k - 1, k, k + 1 the
+// cell needs and the NS - 3 planes after them, copied with cp.async while
+// plane k is computed.  Planes beyond a wall are staged as zeros, and the
+// wall faces too for the face fields (H2, w, q2), which is what the
+// two-pass formulation reads there.  Each cell evaluates the flux
+// cotangents it needs (at most nine points of the 3 x 3 x 3 window) from the
+// staged H-bar directly -- the cotangents of the advection fluxes at the
+// cell centres (Qb, Rb, Sb) and edges (Euv, Euw, Evw) -- then
+//   u-bar += dt/Re L^T q + J_A(u^n)^T Hb,   p-bar -= dt G^T q,
+// so no flux field goes through global memory.  The cotangents it updates
+// and the plane's metric values are read before the wait for the staged
+// planes, so their latency overlaps it.
+enum GatherField { GF_H0, GF_H1, GF_H2, GF_U, GF_V, GF_W, GF_Q0, GF_Q1, GF_Q2, GF_COUNT };
 
-// Pass 1 of the gather: the cotangents of the advection fluxes at the cell
-// centres (Qb, Rb, Sb) and edges (Euv, Euw, Evw) from H-bar, each formed
-// once per point (pass 2 reads each of them at up to eight points).
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_adj_flux(GridDev g, const T *__restrict__ H0, const T *__restrict__ H1,
-           const T *__restrict__ H2, T *__restrict__ fl) {
-    const Window Wn(g, blockIdx.x % g.ny, blockIdx.x / g.ny);
-    const int nx = g.nx, k = Wn.k;
-    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
-    const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
-    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g);
-    auto IDZ = [&](int dk) { return idz[Wn.zw(k + dk)]; };
-    auto IHC = [&](int dk) {
-        const int kk = k + dk;
-        return ihc[kk < 0 ? kk + Wn.nz : (kk > Wn.nz ? kk - Wn.nz : kk)];
-    };
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const int cm = i == 0 ? nx - 1 : i - 1, cp = i == nx - 1 ? 0 : i + 1;
-        auto at = [&](const T *f, int di, int dj, int dk) {
-            const int o = Wn.ro[dj + 1][dk + 1];
-            return o < 0 ? T(0) : f[o + (di < 0 ? cm : (di > 0 ? cp : i))];
-        };
-        // cotangents of the advection term, with the sign of -div(uu) folded in
-        auto A = [&](int di, int dj, int dk) { return -at(H0, di, dj, dk); };
-        auto B = [&](int di, int dj, int dk) { return -at(H1, di, dj, dk); };
-        auto C = [&](int di, int dj, int dk) {
-            if (Wn.wallface(dk)) return T(0);
-            return -at(H2, di, dj, dk);
-        };
-        const size_t c = fid(i, Wn.j, k, g.nx, g.ny);
-        // Qb, Rb, Sb at the centre; Euv, Euw, Evw at the edges of (i, j, k)
-        fl[c] = (A(0, 0, 0) - A(1, 0, 0)) * idx;
-        fl[ncell + c] = (B(0, 0, 0) - B(0, 1, 0)) * idy;
-        fl[2 * ncell + c] = C(0, 0, 0) * IHC(0) - C(0, 0, 1) * IHC(1);
-        fl[3 * ncell + c] = (A(0, -1, 0) - A(0, 0, 0)) * idy + (B(-1, 0, 0) - B(0, 0, 0)) * idx;
-        fl[4 * ncell + c] = Wn.wallface(0) ? T(0)
-                                           : (A(0, 0, -1) * IDZ(-1) - A(0, 0, 0) * IDZ(0)) +
-                                                 (C(-1, 0, 0) - C(0, 0, 0)) * idx;
-        fl[5 * ncell + c] = Wn.wallface(0) ? T(0)
-                                           : (B(0, 0, -1) * IDZ(-1) - B(0, 0, 0) * IDZ(0)) +
-                                                 (C(0, -1, 0) - C(0, 0, 0)) * idy;
-    }
+template <int TX, int TY> constexpr int gather_plane() { return (TX + 2) * (TY + 2); }
+
+// Single precision: 4 blocks of 256 per SM with four planes in the ring (63
+// registers, no spills; at 128 x 128 x 192 92 us against 96 us for five
+// planes at 3 blocks); double precision: 2 (the ring takes 98 KB).
+template <typename T, int NS> constexpr int gather_min_blocks() {
+    return sizeof(T) == 4 ? (NS == 4 ? 4 : 3) : 2;
 }
 
-// Pass 2: u-bar += dt/Re L^T q + J_A(u^n)^T Hb from the flux cotangents of
-// pass 1 and the forward velocities; p-bar -= dt G^T q.
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_adj_gather(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
-             const T *__restrict__ w, const T *__restrict__ q0, const T *__restrict__ q1,
-             const T *__restrict__ q2, const T *__restrict__ fl, T *__restrict__ ub,
-             T *__restrict__ vb, T *__restrict__ wb, T *__restrict__ pb, const StepScalars *sc,
-             T inv_re) {
-    const Window Wn(g, blockIdx.x % g.ny, blockIdx.x / g.ny);
-    const int nx = g.nx, nz = g.nz, j = Wn.j, k = Wn.k;
-    const bool walls = Wn.walls;
-    const size_t ncell = (size_t)g.nx * g.ny * g.nz;
+template <typename T, int TX, int TY, int NS>
+__global__ void __launch_bounds__(TX * TY, (gather_min_blocks<T, NS>()))
+k_adj_gather_tile(GridDev g, const T *__restrict__ u, const T *__restrict__ v,
+                  const T *__restrict__ w, const T *__restrict__ q0, const T *__restrict__ q1,
+                  const T *__restrict__ q2, const T *__restrict__ H0, const T *__restrict__ H1,
+                  const T *__restrict__ H2, T *__restrict__ ub, T *__restrict__ vb,
+                  T *__restrict__ wb, T *__restrict__ pb, const StepScalars *sc, T inv_re,
+                  int kc) {
+    static_assert(NS == 4 || NS == 5, "ring of 4 or 5 planes");
+    constexpr int LEAD = NS - 3;
+    extern __shared__ __align__(16) unsigned char gather_smem[];
+    T *const sm = reinterpret_cast<T *>(gather_smem);
+    constexpr int PW = TX + 2, PL = gather_plane<TX, TY>(), SLOT = GF_COUNT * PL;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const bool walls = g.walls != 0;
+    const int tx = (int)threadIdx.x % TX, ty = (int)threadIdx.x / TX;
+    const int i0 = (int)blockIdx.x * TX, j0 = (int)blockIdx.y * TY;
+    const int k0 = (int)blockIdx.z * kc, k1 = min(k0 + kc, nz);
+    const int i = i0 + tx, j = j0 + ty;
+    const bool mine = i < nx && j < ny;
+    const T *const src[GF_COUNT] = {H0, H1, H2, u, v, w, q0, q1, q2};
+    // ring slot of plane kk (kk >= -1)
+    auto slot = [](int kk) { return NS == 4 ? (kk & 3) : (kk + NS) % NS; };
+    // copies of plane kk (wrapped, or zeros beyond a wall) into its slot
+    auto stage = [&](int kk) {
+        T *d = sm + slot(kk) * SLOT;
+        const bool out = walls && (kk < 0 || kk >= nz);
+        const bool face0 = walls && (kk <= 0 || kk >= nz);
+        const int kw = kk < 0 ? kk + nz : (kk >= nz ? kk - nz : kk);
+        for (int e = threadIdx.x; e < PL; e += TX * TY) {
+            const int r = e / PW, c = e - r * PW;
+            int gj = j0 + r - 1, gi = i0 + c - 1;
+            gj = gj < 0 ? gj + ny : (gj >= ny ? gj % ny : gj);
+            gi = gi < 0 ? gi + nx : (gi >= nx ? gi % nx : gi);
+            const size_t o = ((size_t)kw * ny + gj) * nx + gi;
+#pragma unroll
+            for (int f = 0; f < GF_COUNT; ++f) {
+                const bool face = f == GF_H2 || f == GF_W || f == GF_Q2;
+                T *dst = d + f * PL + e;
+                if (face ? face0 : out) {
+                    *dst = T(0);
+                } else if constexpr (sizeof(T) == 8) {
+                    cp_async8(dst, src[f] + o);
+                } else {
+                    cp_async4(dst, src[f] + o);
+                }
+            }
+        }
+    };
     const T dt = fpick<T>(sc->dt, sc->fdt);
     const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
     const T idx2 = fpick<T>(g.idx2, g.fidx2), idy2 = fpick<T>(g.idy2, g.fidy2);
     const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
     const T h = T(0.5);
-    auto IDZ = [&](int dk) { return idz[Wn.zw(k + dk)]; };
-    auto wallface = [&](int dk) { return Wn.wallface(dk); };
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const int cm = i == 0 ? nx - 1 : i - 1, cp = i == nx - 1 ? 0 : i + 1;
-        auto at = [&](const T *f, int di, int dj, int dk) {
-            const int o = Wn.ro[dj + 1][dk + 1];
-            return o < 0 ? T(0) : f[o + (di < 0 ? cm : (di > 0 ? cp : i))];
+    const int me = (ty + 1) * PW + tx + 1;
+    stage(k0 - 1);
+    stage(k0);
+    stage(k0 + 1);
+    cp_async_commit();
+#pragma unroll
+    for (int l = 1; l < LEAD; ++l) {
+        if (k0 + 1 + l <= k1) stage(k0 + 1 + l);
+        cp_async_commit();
+    }
+    for (int k = k0; k < k1; ++k) {
+        const size_t c = ((size_t)k * ny + j) * nx + i;
+        // the cotangents this cell updates and the metric values of plane k
+        T ub0 = T(0), vb0 = T(0), wb0 = T(0), pb0 = T(0);
+        if (mine) {
+            ub0 = ub[c];
+            vb0 = vb[c];
+            wb0 = wb[c];
+            pb0 = pb[c];
+        }
+        const int kmw = k == 0 ? nz - 1 : k - 1, kpw = k == nz - 1 ? 0 : k + 1;
+        const T idzk = idz[k], idzm = idz[kmw], idzp = idz[kpw], dzk = dz[k];
+        const T ihck = ihc[k], ihcp = ihc[k + 1], ihcm = ihc[kmw];
+        const T ihcw = ihc[k + 1 == nz ? (walls ? nz : 0) : k + 1];
+        if (LEAD == 1) cp_async_wait_all();
+        else cp_async_wait_prior();
+        __syncthreads();           // plane k + 1 landed; the slot of k - 2 is free
+        if (k + 1 + LEAD <= k1) stage(k + 1 + LEAD);
+        cp_async_commit();
+        const T *const P[3] = {sm + slot(k - 1) * SLOT + me, sm + slot(k) * SLOT + me,
+                               sm + slot(k + 1) * SLOT + me};
+        // the staged value of field f at (i + di, j + dj, k + dk)
+        auto S = [&](int f, int di, int dj, int dk) { return P[dk + 1][f * PL + dj * PW + di]; };
+        // idz of the plane k + dk (dk in -2 .. 1), wrapped
+        auto IDZ = [&](int dk) {
+            return dk == 0 ? idzk : (dk == 1 ? idzp : (dk == -1 ? idzm : idz[(k - 2 + 2 * nz) % nz]));
         };
-        // the flux cotangents of pass 1 (0 beyond a wall, as there)
-        auto Qb = [&](int di, int dj, int dk) { return at(fl, di, dj, dk); };
-        auto Rb = [&](int di, int dj, int dk) { return at(fl + ncell, di, dj, dk); };
-        auto Sb = [&](int di, int dj, int dk) { return at(fl + 2 * ncell, di, dj, dk); };
-        auto Euv = [&](int di, int dj, int dk) { return at(fl + 3 * ncell, di, dj, dk); };
-        auto Euw = [&](int di, int dj, int dk) { return at(fl + 4 * ncell, di, dj, dk); };
-        auto Evw = [&](int di, int dj, int dk) { return at(fl + 5 * ncell, di, dj, dk); };
-        // forward averages
-        auto U = [&](int di, int dj, int dk) { return at(u, di, dj, dk); };
-        auto V = [&](int di, int dj, int dk) { return at(v, di, dj, dk); };
-        auto Wf = [&](int di, int dj, int dk) {
+        auto wallface = [&](int dk) { return walls && (k + dk <= 0 || k + dk >= nz); };
+        // advection cotangents with the sign of -div(uu) folded in (wall
+        // faces of H2 are staged as 0)
+        auto A = [&](int di, int dj, int dk) { return -S(GF_H0, di, dj, dk); };
+        auto B = [&](int di, int dj, int dk) { return -S(GF_H1, di, dj, dk); };
+        auto C = [&](int di, int dj, int dk) { return -S(GF_H2, di, dj, dk); };
+        // flux cotangents at the point (i + di, j + dj, k + dk)
+        auto Qb = [&](int di, int dj, int dk) {
+            return (A(di, dj, dk) - A(di + 1, dj, dk)) * idx;
+        };
+        auto Rb = [&](int di, int dj, int dk) {
+            return (B(di, dj, dk) - B(di, dj + 1, dk)) * idy;
+        };
+        // Sb at the point k (dk = 0) or k - 1 (dk = -1; 0 below a wall)
+        auto Sb = [&](int dk) {
+            if (dk == 0) return C(0, 0, 0) * ihck - C(0, 0, 1) * ihcp;
+            if (walls && k == 0) return T(0);
+            return C(0, 0, -1) * ihc[k == 0 ? nz - 1 : k - 1] - C(0, 0, 0) * ihc[k == 0 ? nz : k];
+        };
+        auto Euv = [&](int di, int dj, int dk) {
+            return (A(di, dj - 1, dk) - A(di, dj, dk)) * idy +
+                   (B(di - 1, dj, dk) - B(di, dj, dk)) * idx;
+        };
+        auto Euw = [&](int di, int dj, int dk) {
             if (wallface(dk)) return T(0);
-            return at(w, di, dj, dk);
+            return (A(di, dj, dk - 1) * IDZ(dk - 1) - A(di, dj, dk) * IDZ(dk)) +
+                   (C(di - 1, dj, dk) - C(di, dj, dk)) * idx;
         };
-        const size_t c = fid(i, j, k, g.nx, g.ny);
-        // ---- u
-        {
-            const T uc0 = h * (U(0, 0, 0) + U(1, 0, 0));
-            const T ucm = h * (U(-1, 0, 0) + U(0, 0, 0));
-            T a = h * (T(2) * uc0 * Qb(0, 0, 0) + T(2) * ucm * Qb(-1, 0, 0));
-            a += h * (Euv(0, 0, 0) * h * (V(0, 0, 0) + V(-1, 0, 0)) +
-                      Euv(0, 1, 0) * h * (V(0, 1, 0) + V(-1, 1, 0)));
-            a += h * (Euw(0, 0, 0) * h * (Wf(0, 0, 0) + Wf(-1, 0, 0)) +
-                      Euw(0, 0, 1) * h * (Wf(0, 0, 1) + Wf(-1, 0, 1)));
-            // viscous: lap_xy(q) + dz_k lapz_centre(q / dz)
-            const T qc = at(q0, 0, 0, 0);
-            const T lxy = (at(q0, 1, 0, 0) - T(2) * qc + at(q0, -1, 0, 0)) * idx2 +
-                          (at(q0, 0, 1, 0) - T(2) * qc + at(q0, 0, -1, 0)) * idy2;
-            const T sq = qc * idz[k];
-            const T sup = Wn.ro[1][2] >= 0 ? at(q0, 0, 0, 1) * IDZ(1) : T(0);
-            const T sdn = Wn.ro[1][0] >= 0 ? at(q0, 0, 0, -1) * IDZ(-1) : T(0);
-            const T lz = ((sup - sq) * ihc[k + 1] - (sq - sdn) * ihc[k]) * idz[k];
-            ub[c] = ub[c] + dt * inv_re * (lxy + dz[k] * lz) + a;
-        }
-        // ---- v
-        {
-            const T vc0 = h * (V(0, 0, 0) + V(0, 1, 0));
-            const T vcm = h * (V(0, -1, 0) + V(0, 0, 0));
-            T a = h * (T(2) * vc0 * Rb(0, 0, 0) + T(2) * vcm * Rb(0, -1, 0));
-            a += h * (Euv(0, 0, 0) * h * (U(0, 0, 0) + U(0, -1, 0)) +
-                      Euv(1, 0, 0) * h * (U(1, 0, 0) + U(1, -1, 0)));
-            a += h * (Evw(0, 0, 0) * h * (Wf(0, 0, 0) + Wf(0, -1, 0)) +
-                      Evw(0, 0, 1) * h * (Wf(0, 0, 1) + Wf(0, -1, 1)));
-            const T qc = at(q1, 0, 0, 0);
-            const T lxy = (at(q1, 1, 0, 0) - T(2) * qc + at(q1, -1, 0, 0)) * idx2 +
-                          (at(q1, 0, 1, 0) - T(2) * qc + at(q1, 0, -1, 0)) * idy2;
-            const T sq = qc * idz[k];
-            const T sup = Wn.ro[1][2] >= 0 ? at(q1, 0, 0, 1) * IDZ(1) : T(0);
-            const T sdn = Wn.ro[1][0] >= 0 ? at(q1, 0, 0, -1) * IDZ(-1) : T(0);
-            const T lz = ((sup - sq) * ihc[k + 1] - (sq - sdn) * ihc[k]) * idz[k];
-            vb[c] = vb[c] + dt * inv_re * (lxy + dz[k] * lz) + a;
-        }
-        // ---- w
-        if (walls && k == 0) {
-            wb[c] = T(0);
-        } else {
-            const T wc0 = h * (Wf(0, 0, 0) + Wf(0, 0, 1));
-            const T wcm = h * (Wf(0, 0, -1) + Wf(0, 0, 0));
-            T a = h * (T(2) * wc0 * Sb(0, 0, 0) + T(2) * wcm * Sb(0, 0, -1));
-            a += h * (Euw(0, 0, 0) * h * (U(0, 0, 0) + U(0, 0, -1)) +
-                      Euw(1, 0, 0) * h * (U(1, 0, 0) + U(1, 0, -1)));
-            a += h * (Evw(0, 0, 0) * h * (V(0, 0, 0) + V(0, 0, -1)) +
-                      Evw(0, 1, 0) * h * (V(0, 1, 0) + V(0, 1, -1)));
-            // viscous: lap_xy(q) + hc_k lapz_face(q / hc), q = 0 on the walls
-            auto QW = [&](int di, int dj, int dk) {
-                if (wallface(dk)) return T(0);
-                return at(q2, di, dj, dk);
-            };
-            const T qc = QW(0, 0, 0);
-            const T lxy = (QW(1, 0, 0) - T(2) * qc + QW(-1, 0, 0)) * idx2 +
-                          (QW(0, 1, 0) - T(2) * qc + QW(0, -1, 0)) * idy2;
-            const T sq = qc * ihc[k];
-            const T sup = QW(0, 0, 1) * ihc[k + 1 == nz ? (walls ? nz : 0) : k + 1];
-            const T sdn = QW(0, 0, -1) * ihc[k - 1 < 0 ? nz - 1 : k - 1];
-            const T lz = ((sup - sq) * idz[k] - (sq - sdn) * IDZ(-1)) * ihc[k];
-            wb[c] = wb[c] + dt * inv_re * (lxy + lz / ihc[k]) + a;
-        }
-        // ---- p: p-bar -= dt G^T q
-        {
-            const T cz0 = (walls && k == 0) ? T(0) : at(q2, 0, 0, 0) * ihc[k];
-            const T cz1 = (walls && k == nz - 1) ? T(0) : at(q2, 0, 0, 1) * ihc[k + 1];
-            const T gtq = (at(q0, 0, 0, 0) - at(q0, 1, 0, 0)) * idx +
-                          (at(q1, 0, 0, 0) - at(q1, 0, 1, 0)) * idy + (cz0 - cz1);
-            pb[c] = pb[c] - dt * gtq;
+        auto Evw = [&](int di, int dj, int dk) {
+            if (wallface(dk)) return T(0);
+            return (B(di, dj, dk - 1) * IDZ(dk - 1) - B(di, dj, dk) * IDZ(dk)) +
+                   (C(di, dj - 1, dk) - C(di, dj, dk)) * idy;
+        };
+        auto U = [&](int di, int dj, int dk) { return S(GF_U, di, dj, dk); };
+        auto V = [&](int di, int dj, int dk) { return S(GF_V, di, dj, dk); };
+        auto Wf = [&](int di, int dj, int dk) { return S(GF_W, di, dj, dk); };
+        if (mine) {
+            // ---- u
+            {
+                const T uc0 = h * (U(0, 0, 0) + U(1, 0, 0));
+                const T ucm = h * (U(-1, 0, 0) + U(0, 0, 0));
+                T a = h * (T(2) * uc0 * Qb(0, 0, 0) + T(2) * ucm * Qb(-1, 0, 0));
+                a += h * (Euv(0, 0, 0) * h * (V(0, 0, 0) + V(-1, 0, 0)) +
+                          Euv(0, 1, 0) * h * (V(0, 1, 0) + V(-1, 1, 0)));
+                a += h * (Euw(0, 0, 0) * h * (Wf(0, 0, 0) + Wf(-1, 0, 0)) +
+                          Euw(0, 0, 1) * h * (Wf(0, 0, 1) + Wf(-1, 0, 1)));
+                const T qc = S(GF_Q0, 0, 0, 0);
+                const T lxy = (S(GF_Q0, 1, 0, 0) - T(2) * qc + S(GF_Q0, -1, 0, 0)) * idx2 +
+                              (S(GF_Q0, 0, 1, 0) - T(2) * qc + S(GF_Q0, 0, -1, 0)) * idy2;
+                const T sq = qc * idzk;
+                const T sup = S(GF_Q0, 0, 0, 1) * idzp;
+                const T sdn = S(GF_Q0, 0, 0, -1) * idzm;
+                const T lz = ((sup - sq) * ihcp - (sq - sdn) * ihck) * idzk;
+                ub[c] = ub0 + dt * inv_re * (lxy + dzk * lz) + a;
+            }
+            // ---- v
+            {
+                const T vc0 = h * (V(0, 0, 0) + V(0, 1, 0));
+                const T vcm = h * (V(0, -1, 0) + V(0, 0, 0));
+                T a = h * (T(2) * vc0 * Rb(0, 0, 0) + T(2) * vcm * Rb(0, -1, 0));
+                a += h * (Euv(0, 0, 0) * h * (U(0, 0, 0) + U(0, -1, 0)) +
+                          Euv(1, 0, 0) * h * (U(1, 0, 0) + U(1, -1, 0)));
+                a += h * (Evw(0, 0, 0) * h * (Wf(0, 0, 0) + Wf(0, -1, 0)) +
+                          Evw(0, 0, 1) * h * (Wf(0, 0, 1) + Wf(0, -1, 1)));
+                const T qc = S(GF_Q1, 0, 0, 0);
+                const T lxy = (S(GF_Q1, 1, 0, 0) - T(2) * qc + S(GF_Q1, -1, 0, 0)) * idx2 +
+                              (S(GF_Q1, 0, 1, 0) - T(2) * qc + S(GF_Q1, 0, -1, 0)) * idy2;
+                const T sq = qc * idzk;
+                const T sup = S(GF_Q1, 0, 0, 1) * idzp;
+                const T sdn = S(GF_Q1, 0, 0, -1) * idzm;
+                const T lz = ((sup - sq) * ihcp - (sq - sdn) * ihck) * idzk;
+                vb[c] = vb0 + dt * inv_re * (lxy + dzk * lz) + a;
+            }
+            // ---- w
+            if (walls && k == 0) {
+                wb[c] = T(0);
+            } else {
+                const T wc0 = h * (Wf(0, 0, 0) + Wf(0, 0, 1));
+                const T wcm = h * (Wf(0, 0, -1) + Wf(0, 0, 0));
+                T a = h * (T(2) * wc0 * Sb(0) + T(2) * wcm * Sb(-1));
+                a += h * (Euw(0, 0, 0) * h * (U(0, 0, 0) + U(0, 0, -1)) +
+                          Euw(1, 0, 0) * h * (U(1, 0, 0) + U(1, 0, -1)));
+                a += h * (Evw(0, 0, 0) * h * (V(0, 0, 0) + V(0, 0, -1)) +
+                          Evw(0, 1, 0) * h * (V(0, 1, 0) + V(0, 1, -1)));
+                // viscous: lap_xy(q) + hc_k lapz_face(q / hc), q = 0 on the walls
+                const T qc = S(GF_Q2, 0, 0, 0);
+                const T lxy = (S(GF_Q2, 1, 0, 0) - T(2) * qc + S(GF_Q2, -1, 0, 0)) * idx2 +
+                              (S(GF_Q2, 0, 1, 0) - T(2) * qc + S(GF_Q2, 0, -1, 0)) * idy2;
+                const T sq = qc * ihck;
+                const T sup = S(GF_Q2, 0, 0, 1) * ihcw;
+                const T sdn = S(GF_Q2, 0, 0, -1) * ihcm;
+                const T lz = ((sup - sq) * idzk - (sq - sdn) * idzm) * ihck;
+                wb[c] = wb0 + dt * inv_re * (lxy + lz / ihck) + a;
+            }
+            // ---- p: p-bar -= dt G^T q
+            {
+                const T cz0 = (walls && k == 0) ? T(0) : S(GF_Q2, 0, 0, 0) * ihck;
+                const T cz1 = (walls && k == nz - 1) ? T(0) : S(GF_Q2, 0, 0, 1) * ihcp;
+                const T gtq = (S(GF_Q0, 0, 0, 0) - S(GF_Q0, 1, 0, 0)) * idx +
+                              (S(GF_Q1, 0, 0, 0) - S(GF_Q1, 0, 1, 0)) * idy + (cz0 - cz1);
+                pb[c] = pb0 - dt * gtq;
+            }
         }
     }
+    cp_async_wait_all();
 }
 
 // (I - beta L_x)^-1 of q0, q1, q2 row by row, the row-resident layout of the
@@ -437,6 +487,22 @@ void launch_sweep_x_adjoint(const GridDev &g, Work<T> &W, const StepScalars *sc,
     else sweep_x_L<T, 64>(g, W, sc, P, st);
 }
 
+// shared memory of k_adj_gather_tile: a ring of NS staged planes
+template <typename T, int TX, int TY, int NS> constexpr size_t gather_smem_bytes() {
+    return NS * (size_t)GF_COUNT * gather_plane<TX, TY>() * sizeof(T);
+}
+
+// planes per block of k_adj_gather_tile: chunks of at least 8 planes (the
+// two extra planes each block stages cost at most a quarter more reads),
+// as few as leave about four blocks per SM of work
+inline int gather_chunk(const GridDev &g, int tx, int ty) {
+    const long tiles = (long)((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty);
+    const long want = 4L * 152;
+    int kc = g.nz;
+    while (kc > 8 && tiles * ((g.nz + kc - 1) / kc) < want) kc = (kc + 1) / 2;
+    return kc < 8 ? (g.nz < 8 ? g.nz : 8) : kc;
+}
+
 template <typename T>
 void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T *u, const T *v,
                          const T *w, T *ub, T *vb, T *wb, T *pb, T *hbu, T *hbv, T *hbw, T *fbx,
@@ -467,9 +533,12 @@ void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T 
                                             W.adj2, fbx, fby, fbz, sc);
     });
     group(AK_GATHER, [&] {
-        k_adj_flux<T><<<rows, thr, 0, st>>>(g, W.adj0, W.adj1, W.adj2, W.adjf);
-        k_adj_gather<T><<<rows, thr, 0, st>>>(g, u, v, w, W.q0, W.q1, W.q2, W.adjf, ub, vb, wb,
-                                              pb, sc, T(1.0 / re));
+        constexpr int TX = 32, TY = 8;
+        const int kc = gather_chunk(g, TX, TY);
+        const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + kc - 1) / kc);
+        k_adj_gather_tile<T, TX, TY, 4><<<grid, TX * TY, gather_smem_bytes<T, TX, TY, 4>(), st>>>(
+            g, u, v, w, W.q0, W.q1, W.q2, W.adj0, W.adj1, W.adj2, ub, vb, wb, pb, sc, T(1.0 / re),
+            kc);
     });
 }
 
@@ -478,8 +547,7 @@ template <typename T> void set_smem_limits_adjoint(const GridDev &g, const Work<
     cudaFuncGetAttributes(&fa, k_adj_phibar<T>);
     cudaFuncGetAttributes(&fa, k_adj_ustar<T>);
     cudaFuncGetAttributes(&fa, k_adj_hist<T>);
-    cudaFuncGetAttributes(&fa, k_adj_flux<T>);
-    cudaFuncGetAttributes(&fa, k_adj_gather<T>);
+    raise_smem_limit(k_adj_gather_tile<T, 32, 8, 4>);
     raise_smem_limit(k_sweep_x<T, 8>);
     raise_smem_limit(k_sweep_x<T, 16>);
     raise_smem_limit(k_sweep_x<T, 32>);
