@@ -226,7 +226,6 @@ template <typename T> struct Work {
     double zlen;             // z extent (sum of dz)
     const unsigned char *exact;   // [ny][sk]: 1 for the modes in nzm
     T *adj0, *adj1, *adj2;   // adjoint workspace (allocated on first use)
-    T *adjf;                 // the adjoint's flux cotangents, 6 fields
     T *nn0, *nn1, *nn2, *nuc;   // non-Newtonian remainder at the u, v, w points
                                 // and the excess viscosity at the centres
                                 // (allocated on first use)
