@@ -107,6 +107,10 @@ __device__ __forceinline__ void chunk_backward(T (&d)[CX][L], int len, const Tri
 // CX: x columns per lane (1, or 2 as one 8- or 16-byte vector per row): the
 // chunk's factors, read from shared memory once per row, serve both, and a
 // warp's loads cover 2 tx consecutive columns.
+// whether a register sweep of chunks of L rows stages its plan in shared
+// memory (sweep_reg_body)
+template <int L> constexpr bool kStagePlan = L <= 16;
+
 template <typename T, int CX> struct ColVec;
 template <typename T> struct ColVec<T, 1> { T v[1]; };
 template <typename T> struct alignas(2 * sizeof(T)) ColVec<T, 2> { T v[2]; };
@@ -170,7 +174,13 @@ __device__ __forceinline__ void sweep_reg_body(const GridDev &g, const Fields<T>
                 if (keep(i)) un_pre[i] = *reinterpret_cast<const V *>(up + (size_t)i * stride);
         }
     }
-    const TriPlan<T> pl = stage_plan(src, red + (size_t)tx * CX * rs);
+    // chunks of up to 16 rows: the plan's factors staged in shared memory
+    // once per block; longer chunks (the 768-row lines) read them through
+    // the L1 cache instead -- their blocks are half as many again per line
+    // and the staging of 768 rows' factors cost more than it saved (512 x
+    // 512 x 768: 2.31 -> 2.16 ms; at 256^3 staging stays faster, 121
+    // against 129 us)
+    const TriPlan<T> pl = kStagePlan<L> ? stage_plan(src, red + (size_t)tx * CX * rs) : src;
     if (active) {
         T rF[CX], rE[CX];
         chunk_forward<T, L, CX>(d, EXACT ? L : len, pl, s0, rF, rE);
@@ -299,7 +309,8 @@ void launch_reg(const GridDev &g, const Fields<T> &F, Work<T> &W, const TriPlan<
     const int nmax = pa.n > pb.n ? pa.n : pb.n;
     const int threads = ((tx * Pmax + 31) / 32) * 32;
     const size_t smem =
-        sizeof(T) * ((size_t)tx * CX * (2 * Pmax + 1) + plan_stage_words(nmax, Pmax));
+        sizeof(T) * ((size_t)tx * CX * (2 * Pmax + 1) +
+                     (kStagePlan<L> ? plan_stage_words(nmax, Pmax) : 0));
     const int nxt = (g.nx + tx * CX - 1) / (tx * CX);
     const int outer = DIR == 1 ? g.nz : g.ny;
     K_sweep_reg<T, L, DIR, MODE, CX>.launch(W.pdl != 0, dim3(3 * outer * nxt), dim3(threads),
