@@ -87,6 +87,68 @@ k_adj_phibar(GridDev g, const T *__restrict__ ub, const T *__restrict__ vb,
     }
 }
 
+// The same with 16-byte vectors: a thread owns W = 16 / sizeof(T)
+// consecutive cells of a row (x neighbours beyond its vector as scalars), a
+// block of 256 threads covers 256 W / nx rows of plane k.  The arithmetic of
+// each cell is that of k_adj_phibar, in the same order.  Needs nx % W == 0.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_phibar_vec(GridDev g, const T *__restrict__ ub, const T *__restrict__ vb,
+                 const T *__restrict__ wb, const T *__restrict__ pb, T *__restrict__ x,
+                 const StepScalars *sc) {
+    using V = Vec16<T>;
+    constexpr int W = V::W;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int tpr = nx / W, rpb = (int)blockDim.x / tpr;
+    const int nbj = (ny + rpb - 1) / rpb;
+    const int k = blockIdx.x / nbj;
+    const int j = (blockIdx.x % nbj) * rpb + (int)threadIdx.x / tpr;
+    const int i0 = ((int)threadIdx.x % tpr) * W;
+    if (j >= ny || (int)threadIdx.x >= tpr * rpb) return;
+    const bool walls = g.walls != 0;
+    const T dt = fpick<T>(sc->dt, sc->fdt), beta = fpick<T>(sc->beta, sc->fbeta);
+    const T idx = fpick<T>(g.idx, g.fidx), idy = fpick<T>(g.idy, g.fidy);
+    const T idx2 = fpick<T>(g.idx2, g.fidx2), idy2 = fpick<T>(g.idy2, g.fidy2);
+    const T *idz = Metric<T>::idz(g), *ihc = Metric<T>::ihc(g), *dz = Metric<T>::dz(g);
+    const int kd = k == 0 ? nz - 1 : k - 1, ku = k == nz - 1 ? 0 : k + 1;
+    const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
+    const int oc = (k * ny + j) * nx, ojm = (k * ny + jm) * nx, ojp = (k * ny + jp) * nx;
+    const int okd = (kd * ny + j) * nx, oku = (ku * ny + j) * nx;
+    const bool bot = walls && k == 0, top = walls && k == nz - 1;
+    const T ihck = ihc[k], ihcu = ihc[k + 1], idzk = idz[k], idzd = idz[kd], idzu = idz[ku];
+    const T dzk = dz[k];
+    const T inv_vol = T(g.idx * g.idy) * idzk;
+    auto ld = [](const T *p) { return *reinterpret_cast<const V *>(p); };
+    const int iw = i0 + W == nx ? 0 : i0 + W, im0 = i0 == 0 ? nx - 1 : i0 - 1;
+    const V u0 = ld(ub + oc + i0), v0 = ld(vb + oc + i0), v1 = ld(vb + ojp + i0);
+    const V p0 = ld(pb + oc + i0), pjp = ld(pb + ojp + i0), pjm = ld(pb + ojm + i0);
+    V w0, w1, pku, pkd;
+    if (!bot) { w0 = ld(wb + oc + i0); pkd = ld(pb + okd + i0); }
+    if (!top) { w1 = ld(wb + oku + i0); pku = ld(pb + oku + i0); }
+    const T uW = ub[oc + iw], pW = pb[oc + iw], pM = pb[oc + im0];
+    V out;
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        const T up = e == W - 1 ? uW : u0.v[e + 1];
+        const T pp = e == W - 1 ? pW : p0.v[e + 1];
+        const T pm = e == 0 ? pM : p0.v[e - 1];
+        // G^T u-bar
+        const T cz0 = bot ? T(0) : w0.v[e] * ihck;
+        const T cz1 = top ? T(0) : w1.v[e] * ihcu;
+        const T gtu = (u0.v[e] - up) * idx + (v0.v[e] - v1.v[e]) * idy + (cz0 - cz1);
+        // (DG)^T p-bar = lap_xy(p-bar) + dz_k lapz((p-bar) / dz)
+        const T pc = p0.v[e];
+        const T lxy = (pp - T(2) * pc + pm) * idx2 + (pjp.v[e] - T(2) * pc + pjm.v[e]) * idy2;
+        const T q0 = pc * idzk;
+        const T fup = top ? T(0) : (pku.v[e] * idzu - q0) * ihcu;
+        const T fdn = bot ? T(0) : (q0 - pkd.v[e] * idzd) * ihck;
+        const T lp = lxy + dzk * (fup - fdn) * idzk;
+        const T phib = -dt * gtu + pc - beta * lp;
+        out.v[e] = phib * inv_vol;
+    }
+    *reinterpret_cast<V *>(x + oc + i0) = out;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_adj_ustar(GridDev g, T *__restrict__ ub, T *__restrict__ vb, T *__restrict__ wb,
@@ -514,7 +576,17 @@ void launch_adjoint_step(const GridDev &g, Work<T> &W, StepScalars *sc, const T 
         launch();
         if (hook) hook->after(hook->ctx, kind, st);
     };
-    group(AK_PHIBAR, [&] { k_adj_phibar<T><<<rows, thr, 0, st>>>(g, ub, vb, wb, pb, W.phi, sc); });
+    group(AK_PHIBAR, [&] {
+        constexpr int VW = 16 / (int)sizeof(T);
+        const int tpr = g.nx / VW;
+        if (g.nx % VW == 0 && tpr <= 256) {
+            const int rpb = 256 / tpr;
+            const int blocks = g.nz * ((g.ny + rpb - 1) / rpb);
+            k_adj_phibar_vec<T><<<blocks, 256, 0, st>>>(g, ub, vb, wb, pb, W.phi, sc);
+        } else {
+            k_adj_phibar<T><<<rows, thr, 0, st>>>(g, ub, vb, wb, pb, W.phi, sc);
+        }
+    });
     group(AK_POISSON, [&] {
         launch_rfft_x<T>(g, W, sc, W.phi, 1, st);
         launch_fft_y<T>(g, W, 0, st);
