@@ -202,29 +202,38 @@ k_fft_y_2p(GridDev g, cplx<T> *__restrict__ spec, const cplx<T> *__restrict__ tw
     const int k = blockIdx.x / nkt, x0 = (blockIdx.x % nkt) * tkx;
     cplx<T> *base = spec + (size_t)k * N * sk + x0;
     const int t = threadIdx.x;
-    const bool on1 = t < tkx * N2;
-    const int n2 = ddiv(t, tkx), l1 = t - n2 * tkx;
-    cplx<T> x[N1];
-    if (on1) {
+    const int nt = (int)blockDim.x;
+    // pass 1: (n2, line) pairs, in turn when there are more than threads
+    auto pass1_load = [&](int task, cplx<T> (&x)[N1]) {
+        const int m2 = ddiv(task, tkx), m1 = task - m2 * tkx;
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) x[n1] = base[(size_t)(n1 * N2 + n2) * sk + l1];
-    }
-    for (int m = t; m < N; m += blockDim.x) TW[m] = twy[m];
-    __syncthreads();
-    if (on1) {
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = base[(size_t)(n1 * N2 + m2) * sk + m1];
+    };
+    auto pass1_rest = [&](int task, cplx<T> (&x)[N1]) {
+        const int m2 = ddiv(task, tkx), m1 = task - m2 * tkx;
         dft_reg<T, N1, SIGN>(x, TW, N);
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) {
-            cplx<T> w = TW[n2 * k1];
+            cplx<T> w = TW[m2 * k1];
             if (SIGN > 0) w = conj(w);
             x[k1] = x[k1] * w;
         }
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) B[(n2 * N1 + k1) * tkx + l1] = x[k1];
+        for (int k1 = 0; k1 < N1; ++k1) B[(m2 * N1 + k1) * tkx + m1] = x[k1];
+    };
+    const bool on1 = t < tkx * N2;
+    cplx<T> x[N1];
+    if (on1) pass1_load(t, x);
+    for (int m = t; m < N; m += nt) TW[m] = twy[m];
+    __syncthreads();
+    if (on1) pass1_rest(t, x);
+    for (int task = t + nt; task < tkx * N2; task += nt) {
+        pass1_load(task, x);
+        pass1_rest(task, x);
     }
     __syncthreads();
-    if (t < tkx * N1) {
-        const int k1 = ddiv(t, tkx), l2 = t - k1 * tkx;
+    for (int task = t; task < tkx * N1; task += nt) {
+        const int k1 = ddiv(task, tkx), l2 = task - k1 * tkx;
         cplx<T> y[N2];
 #pragma unroll
         for (int q = 0; q < N2; ++q) y[q] = B[(q * N1 + k1) * tkx + l2];
@@ -873,8 +882,11 @@ k_irfft_x_2p(GridDev g, const cplx<T> *__restrict__ spec, T *__restrict__ dst,
 template <typename T, int MODE, int RY>
 constexpr Kernel<k_rfft_x<T, MODE, RY>, 256, (sizeof(T) == 4 ? 4 : 1)> K_rfft_x{};
 template <typename T, int SIGN> constexpr Kernel<k_fft_y<T, SIGN>, 256, 0> K_fft_y{};
+// single precision, first-pass DFTs of up to 16 points: 4 blocks per SM (64
+// registers, as without the second turn of pairs the wider tiles need)
 template <typename T, int SIGN, int N1, int N2>
-constexpr Kernel<k_fft_y_2p<T, SIGN, N1, N2>, 256, 0> K_fft_y_2p{};
+constexpr Kernel<k_fft_y_2p<T, SIGN, N1, N2>, 256, (sizeof(T) == 4 && N1 <= 16 ? 4 : 0)>
+    K_fft_y_2p{};
 template <typename T> constexpr Kernel<k_poisson_z<T>, 512, 0> K_poisson_z{};
 template <typename T> constexpr Kernel<k_poisson_exact<T>, 64, 0> K_poisson_exact{};
 template <typename T> constexpr Kernel<k_poisson_exact_f<T>, 32, 0> K_poisson_exact_f{};
@@ -993,10 +1005,11 @@ template <typename T, int SIGN>
 bool fft_y_2p_launch(const GridDev &g, Work<T> &W, cudaStream_t st) {
     const int tk = W.tkx_fft;
     const int n1 = fft_split_n1(g.ny);
-    if (!n1 || tk < 1 || g.sk % tk || tk * n1 > 256) return false;
+    if (!n1 || tk < 1 || g.sk % tk || tk * n1 > 512 || tk * (g.ny / n1) > 512) return false;
     const int blocks = g.nz * (g.sk / tk);
     const size_t sm = sizeof(cplx<T>) * ((size_t)g.ny * tk + g.ny);
-    const int thr = tk * n1;
+    // at most 256 threads: wider tiles take their pairs in two turns
+    const int thr = tk * n1 < 256 ? tk * n1 : 256;
     const bool pdl = W.pdl != 0;
     switch (g.ny) {
 #define FSEI_FY(N1_, N2_)                                                                      \
@@ -1238,8 +1251,8 @@ template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*
         break;
     }
     case SK_FFTY: {
-        // kx columns per block of the two-pass y transform (power-of-two ny
-        // up to 256): tkx N1 threads, 32 to 256
+        // kx columns per block of the two-pass y transform: tkx N1 pairs of
+        // the second pass, 32 to 512 (at most 256 threads, two turns above)
         const int n1 = fft_split_n1(g.ny);
         if (!n1) break;
         Work<T> W;
@@ -1247,7 +1260,8 @@ template <typename T> int schedule_candidates(const GridDev &g, int knob, int (*
         poisson_geometry<T>(g, W);
         put(W.tkx_fft, 0);
         for (int t = 32; t >= 2; t /= 2)
-            if (t != W.tkx_fft && g.sk % t == 0 && t * n1 <= 256 && t * n1 >= 32 &&
+            if (t != W.tkx_fft && g.sk % t == 0 && t * n1 <= 512 && t * (g.ny / n1) <= 512 &&
+                t * n1 >= 32 &&
                 sizeof(cplx<T>) * ((size_t)g.ny * t + g.ny) <= lim)
                 put(t, 0);
         break;

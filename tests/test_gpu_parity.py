@@ -276,16 +276,27 @@ def test_heart_scale_rows_and_y_transforms_against_oracle(fsei, prec_name):
     1e-5 in velocity for mixed precision."""
     case = inputs.case_heart_scale(512, 512, 16, steps=3)
     prec = fsei.FSEI_FP64 if prec_name == "fp64" else fsei.FSEI_MIXED
-    grid = pu.gpu_grid(case, prec)
-    if prec_name == "mixed":
-        assert grid.schedule["rhs_cells_per_lane"] == 8
-    gpu, st = pu.run_gpu(case, 3, prec, grid=grid)
     ref, _ = pu.run_oracle(case, 3)
-    if prec_name == "fp64":
-        _assert_fp64(gpu, ref)
-    else:
-        err = _vel_err(gpu, ref)
-        assert err <= 1e-5, (err, pu.compare(gpu, ref))
+    # every admissible width of the y transforms' tiles: 16 kx columns take
+    # the second pass's pairs in two turns of 256 threads
+    tried = []
+    for cols in (None, 4, 8, 16):
+        grid = pu.gpu_grid(case, prec)
+        if prec_name == "mixed":
+            assert grid.schedule["rhs_cells_per_lane"] == 8
+        if cols is not None:
+            try:
+                grid.set_schedule({"ffty_columns_per_block": cols})
+            except fsei.FseiError:
+                continue
+        tried.append(grid.schedule["ffty_columns_per_block"])
+        gpu, st = pu.run_gpu(case, 3, prec, grid=grid)
+        if prec_name == "fp64":
+            _assert_fp64(gpu, ref)
+        else:
+            err = _vel_err(gpu, ref)
+            assert err <= 1e-5, (cols, err, pu.compare(gpu, ref))
+    assert 16 in tried, tried
 
 
 def _poisson_768(fsei, prec_name, zbc):
