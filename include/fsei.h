@@ -475,6 +475,15 @@ fsei_status fsei_poisson_solve_noalloc(const fsei_grid_desc *desc,
  * synchronise.  The caller's own fields are not guarded. */
 fsei_status fsei_grid_check_bounds(fsei_grid grid);
 
+/* Test hook of the bounds-checking mode (no counterpart in the paper):
+ * changes the guard byte `offset` bytes from the edge of workspace buffer
+ * `buffer` (allocation order), before it (side 0) or after it (side 1), so
+ * that a test can check that fsei_grid_check_bounds reports the write.  The
+ * byte lies inside the library's own allocation.  Synchronises the device.
+ * FSEI_E_UNSUPPORTED without the mode, FSEI_E_ARG for a zone or offset that
+ * does not exist. */
+fsei_status fsei_grid_poke_guard(fsei_grid grid, int32_t buffer, int32_t side, int64_t offset);
+
 /* Per-kernel timing, for measurement tools.  While enabled, fsei_step and
  * fsei_poisson_solve record a CUDA event pair on the call's stream around
  * every kernel they launch.  fsei_kernel_times synchronises the device,

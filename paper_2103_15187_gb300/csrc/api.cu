@@ -1394,6 +1394,25 @@ fsei_status fsei_grid_check_bounds(fsei_grid G) {
     return guard_status(G, "fsei_grid_check_bounds");
 }
 
+fsei_status fsei_grid_poke_guard(fsei_grid G, int32_t buffer, int32_t side, int64_t offset) {
+    g_err.clear();
+    if (!G) return fail(FSEI_E_ARG, "fsei_grid_poke_guard: NULL grid");
+    if (!G->mem.guard)
+        return fail(FSEI_E_UNSUPPORTED, "the grid was created without FSEI_CHECK_BOUNDS=1");
+    if (buffer < 0 || (size_t)buffer >= G->mem.zones.size() || (side != 0 && side != 1))
+        return fail(FSEI_E_ARG, "fsei_grid_poke_guard: no guard zone %d/%d", buffer, side);
+    const DevAllocs::Zone &z = G->mem.zones[(size_t)buffer];
+    if (offset < 0 || (size_t)offset >= z.gbytes)
+        return fail(FSEI_E_ARG, "fsei_grid_poke_guard: offset %lld outside the zone",
+                    (long long)offset);
+    DeviceGuard dg(G->device);
+    // the byte `offset` bytes from the buffer's edge, inside the zone
+    const unsigned char *p = side ? z.back + offset : z.front + (z.gbytes - 1 - (size_t)offset);
+    const cudaError_t e = cudaMemset(const_cast<unsigned char *>(p), z.fill ^ 0x5A, 1);
+    if (e == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess) return FSEI_OK;
+    return fail(FSEI_E_CUDA, "fsei_grid_poke_guard: %s", cudaGetErrorString(cudaGetLastError()));
+}
+
 fsei_status fsei_set_kernel_timing(fsei_grid G, int32_t enable) {
     g_err.clear();
     if (!G) return fail(FSEI_E_ARG, "fsei_set_kernel_timing: NULL grid");

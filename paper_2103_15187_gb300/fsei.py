@@ -32,7 +32,7 @@ EXPORTS = ("fsei_grid_create", "fsei_grid_destroy", "fsei_grid_workspace_bytes",
            "fsei_grid_autotune", "fsei_grid_get_schedule", "fsei_grid_set_schedule",
            "fsei_batch_autotune", "fsei_fp64_fma_rate", "fsei_batch_set_max_group",
            "fsei_batch_launch_groups", "fsei_ib_forcing", "fsei_ib_loads",
-           "fsei_grid_check_bounds")
+           "fsei_grid_check_bounds", "fsei_grid_poke_guard")
 FSEI_TUNE_FORCE = 1
 
 
@@ -155,6 +155,8 @@ def load(path=LIB_PATH):
     lib.fsei_batch_step.restype = ctypes.c_int
     lib.fsei_grid_check_bounds.argtypes = [vp]
     lib.fsei_grid_check_bounds.restype = ctypes.c_int
+    lib.fsei_grid_poke_guard.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
+    lib.fsei_grid_poke_guard.restype = ctypes.c_int
     lib.fsei_set_kernel_timing.argtypes = [vp, ctypes.c_int32]
     lib.fsei_set_kernel_timing.restype = ctypes.c_int
     lib.fsei_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -484,6 +486,12 @@ def check_bounds(grid):
     """fsei_grid_check_bounds: raises FseiError(FSEI_E_BOUNDS) if a guard
     zone of a grid created with FSEI_CHECK_BOUNDS=1 was written."""
     _check(load().fsei_grid_check_bounds(grid.handle))
+
+
+def poke_guard(grid, buffer, side, offset):
+    """fsei_grid_poke_guard: change one guard byte of a grid in the
+    bounds-checking mode (for tests of the detector)."""
+    _check(load().fsei_grid_poke_guard(grid.handle, int(buffer), int(side), int(offset)))
 
 
 def set_kernel_timing(grid, enable):

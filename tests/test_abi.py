@@ -164,3 +164,10 @@ def test_bounds_check_rejects_a_null_handle(lib):
     lib.fsei_grid_check_bounds.argtypes = [ctypes.c_void_p]
     lib.fsei_grid_check_bounds.restype = ctypes.c_int
     assert lib.fsei_grid_check_bounds(None) == 1
+
+
+def test_poke_guard_rejects_a_null_handle(lib):
+    lib.fsei_grid_poke_guard.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int64]
+    lib.fsei_grid_poke_guard.restype = ctypes.c_int
+    assert lib.fsei_grid_poke_guard(None, 0, 0, 0) == 1

@@ -243,3 +243,40 @@ def test_batch_and_host_state_in_bounds(fsei, checked):
     errs = pu.compare({k: host[k].numpy() for k in pu.FIELDS}, ref,
                       fields=("u", "v", "w", "p"))
     assert all(e <= 1e-12 for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("buffer,side,offset", [(0, 0, 0), (5, 1, 0), (9, 1, 4000)])
+def test_a_changed_guard_byte_is_reported(fsei, checked, buffer, side, offset):
+    """The detector itself: one guard byte changed (inside the library's own
+    allocation, by the test hook) is reported by fsei_grid_check_bounds and
+    by the next call that launches work, with the buffer, side and
+    distance."""
+    import torch
+    case = inputs.case_channel(24, 12, 18, steps=1, kmax=3.0, rms=0.2, seed=67)
+    grid = pu.gpu_grid(case, fsei.FSEI_FP64)
+    fsei.check_bounds(grid)
+    fsei.poke_guard(grid, buffer, side, offset)
+    with pytest.raises(fsei.FseiError) as ei:
+        fsei.check_bounds(grid)
+    assert ei.value.status == 8, ei.value
+    msg = str(ei.value)
+    assert ("after" if side else "before") in msg and "buffer %d " % buffer in msg, msg
+    assert "%d bytes from" % offset in msg, msg
+    st = pu.to_device(pu.initial_state_np(case), torch.float64)
+    with pytest.raises(fsei.FseiError) as ei:
+        fsei.step(grid, st, None, nsteps=1, **pu.params(case))
+    assert ei.value.status == 8, ei.value
+
+
+def test_poke_guard_rejects_what_does_not_exist(fsei, checked, monkeypatch):
+    grid = fsei.Grid(16, 12, 10, 1.0, 1.0, zbc=fsei.FSEI_Z_WALLS, stretch=1.5)
+    for args in ((-1, 0, 0), (10 ** 6, 0, 0), (0, 2, 0), (0, 0, 1 << 40)):
+        with pytest.raises(fsei.FseiError) as ei:
+            fsei.poke_guard(grid, *args)
+        assert ei.value.status == 1, (args, ei.value)
+    fsei.check_bounds(grid)
+    monkeypatch.delenv("FSEI_CHECK_BOUNDS")
+    plain = fsei.Grid(16, 12, 10, 1.0, 1.0, zbc=fsei.FSEI_Z_WALLS, stretch=1.5)
+    with pytest.raises(fsei.FseiError) as ei:
+        fsei.poke_guard(plain, 0, 0, 0)
+    assert ei.value.status == 3
