@@ -91,3 +91,38 @@ def test_residual_and_gauge_at_larger_size(zbc):
     assert np.max(np.abs(res)) <= 1e-11 * np.max(np.abs(s))
     mean = (phi * g.cell_volume_uvp()).sum()
     assert abs(mean) <= 1e-12 * np.abs(phi * g.cell_volume_uvp()).sum()
+
+
+def _naive_dft(n):
+    """The O(n^2) DFT matrix, forward sign e^{-i}, unnormalised."""
+    j = np.arange(n)
+    return np.exp(-2j * np.pi * np.outer(j, j) / n)
+
+
+@pytest.mark.parametrize("n", [32, 64, 96, 128])
+def test_fft_step_against_naive_dft(n):
+    """The transform the oracle's Poisson solve applies (numpy's FFT, a
+    library step) against the naive O(n^2) DFT: forward e^{-i} unnormalised,
+    inverse with 1/n; and that DFT diagonalises the periodic second
+    difference with the oracle's modified wavenumbers, -lambda_m."""
+    from oracle.poisson import modified_wavenumbers
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    F = _naive_dft(n)
+    ref = F @ x
+    assert np.linalg.norm(np.fft.fft(x) - ref) <= 1e-13 * np.linalg.norm(ref)
+    assert np.linalg.norm(np.fft.ifft(ref) - x) <= 1e-13 * np.linalg.norm(x)
+    h = 2 * np.pi / n
+    d2 = (np.roll(np.eye(n), 1, axis=1) + np.roll(np.eye(n), -1, axis=1) - 2 * np.eye(n)) / h ** 2
+    lam = modified_wavenumbers(n, h)
+    diag = F @ d2 @ np.linalg.inv(F)
+    assert np.max(np.abs(diag - np.diag(-lam))) <= 1e-10 * lam.max()
+
+
+def test_fft2_axes_are_y_and_x():
+    """The oracle's two-dimensional transform runs along y and x of a
+    [nz][ny][nx] field (axes 1 and 2), not along z."""
+    rng = np.random.default_rng(7)
+    s = rng.standard_normal((3, 6, 8))
+    ref = np.einsum("ab,kbc,dc->kad", _naive_dft(6), s, _naive_dft(8))
+    assert np.max(np.abs(np.fft.fft2(s, axes=(1, 2)) - ref)) <= 1e-12
