@@ -186,6 +186,40 @@ def device_state(case, dtype):
     return st
 
 
+class ReplicaSync:
+    """Barrier and max-over-ranks of the N-replica run: one process per GPU,
+    each advancing its own copy of the workload (the step has no sharding,
+    so no data moves between replicas; only these timing collectives run).
+    dist: torch.distributed or None (one process); device: where the
+    collective's scalar lives ("cuda" with NCCL, "cpu" with gloo)."""
+
+    def __init__(self, dist=None, device="cuda"):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        import torch
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.device == "cuda":
+            torch.cuda.synchronize()
+
+    def max(self, x):
+        import torch
+        if self.dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_rate(cells, steps, world, ms):
+    """Cell updates per second of all replicas together, in millions: every
+    replica advanced `cells` cells `steps` times in at most `ms` ms (the
+    maximum over ranks)."""
+    return cells * steps * world / (ms * 1e-3) / 1e6
+
+
 def run_gpu_arm(args, rank, world):
     import torch
     from paper_2103_15187_gb300 import fsei
@@ -200,18 +234,8 @@ def run_gpu_arm(args, rank, world):
     dist = None
     if world > 1:
         import torch.distributed as dist
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    sync = ReplicaSync(dist, "cuda")
+    barrier, max_over_ranks = sync.barrier, sync.max
 
     results = {}
     for prec_name, prec, dtype in (("mixed", fsei.FSEI_MIXED, torch.float32),
@@ -250,7 +274,7 @@ def run_gpu_arm(args, rank, world):
         ms = float(np.median(blocks))
         stats = fsei.step(grid, st, None, nsteps=0, **prm)
         res = {"ms_total": ms, "ms_per_step": ms / K, "cells": cells,
-               "mcups": cells * K * world / (ms * 1e-3) / 1e6, "clocks": clk.summary(),
+               "mcups": whole_job_rate(cells, K, world, ms), "clocks": clk.summary(),
                "last_stats": stats, "blocks": len(blocks),
                "block_ms": {"median": ms, "min": float(min(blocks)), "max": float(max(blocks))}}
         # per-kernel device time over K more steps (event pairs on the stream)
@@ -310,7 +334,7 @@ def run_gpu_arm(args, rank, world):
         ms = max_over_ranks(e0.elapsed_time(e1))
         nbytes = sum(host[k].numel() * 4 for k in FIELDS)
         assert host["have_prev_h"] == 1
-        e2e = {"value": cells * args.e2e_steps * world / (ms * 1e-3) / 1e6,
+        e2e = {"value": whole_job_rate(cells, args.e2e_steps, world, ms),
                "unit": "Mcell-updates/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
     return case, results, err, e2e
