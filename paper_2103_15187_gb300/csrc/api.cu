@@ -215,6 +215,12 @@ struct KernelTimer {
     int fail_kind = -1;
     cudaError_t fail_err = cudaSuccess;
     template <class F> void run(int kind, cudaStream_t st, F &&f) {
+        if (on && !check) {
+            begin(kind, st);   // the pass's NVTX range and event pair
+            f();
+            end(st);
+            return;
+        }
         NvtxRange range(kKernelNames[kind]);
         if (check) {
             f();
@@ -225,10 +231,7 @@ struct KernelTimer {
             }
             return;
         }
-        if (!on) { f(); return; }
-        begin(kind, st);
         f();
-        end(st);
     }
     // the two halves of run(), for launchers in other files (LaunchHook)
     void begin(int kind, cudaStream_t st) {
